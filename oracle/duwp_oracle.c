@@ -1,0 +1,923 @@
+/*
+ * duwp_oracle.c -- plain, slow, single-threaded FP64 restatement of the direct
+ * unified wave-particle (DUWP) time step (Cao, Liu, Yang, Zhong, arXiv 2305.12071).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may build, load or call this file.  The CUDA
+ * library never links it and shares no source with it: the Philox generator,
+ * the moment definitions, the NS flux, the collision and streaming arithmetic
+ * are all written out again here, from the paper and from the published
+ * generator description, in the order the paper gives them.
+ *
+ * Step of one instance (Sec. 3.4, "Algorithm of DUWP", Steps 1-4):
+ *   1. total state  Psi_t = Psi_w + Psi_p  per cell                  (Step 1)
+ *   2. per cell: P from Eq. (p); each particle absorbed with prob. P;
+ *      (1-P) of the wave mass re-sampled as Maxwellian particles at the
+ *      total state (Eq. maxsample); NTC/VHS collisions (Appendix A)  (Step 2)
+ *   3. free transport x += xi*dt, particle flux Eq. (fp) as the change of
+ *      the per-cell particle moments, wave flux by an NS solver, and the
+ *      conservative update Eq. (r1)                                  (Step 3)
+ *
+ * Readings of points the paper leaves open (wave-flux scheme, flux weight,
+ * rounding of particle counts, boundary handling, RNG layout) are listed in
+ * the design notes of the repository; each one is marked "reading" below.
+ *
+ * Precision: all arithmetic is FP64.  With `fp32 = 1` the particle record
+ * (cell-local position and velocity) is STORED in single precision: every
+ * value written to a particle is rounded to float, and the free-transport
+ * position update (the one floating-point result that decides an integer,
+ * the new cell) is taken in single precision with one fused multiply-add,
+ * the way the single-precision particle store evaluates it.
+ *
+ * Parity pins: tests/test_oracle_*.py check this file against closed forms,
+ * conservation identities, brute force and published generator vectors.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared -o liboracle.so duwp_oracle.c -lm
+ * (-ffp-contract=off: no silent fused multiply-adds; the fused ones are explicit.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_PI 3.14159265358979323846
+#define ORA_TWO_PI 6.283185307179586
+
+/* ------------------------------------------------------------------------- */
+/* Philox-4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,         */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11, Sec. 5):              */
+/* 10 rounds of two 32x32->64 multiplies with a key schedule bumped by the     */
+/* Weyl constants between rounds.                                              */
+/* ------------------------------------------------------------------------- */
+void ora_philox(uint32_t k0, uint32_t k1, const uint32_t ctr[4], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* 53-bit uniform in [0,1) from two words: the top 32 bits from a, 21 from b. */
+double ora_u53(uint32_t a, uint32_t b)
+{
+    uint64_t m = ((uint64_t)a << 21) ^ (uint64_t)(b >> 11);
+    return (double)m * (1.0 / 9007199254740992.0);
+}
+
+/* Draw purposes (fourth counter word).  Reading: the RNG layout is not in the
+ * paper; every random number is keyed by (id, sub, step, purpose). */
+enum { ORA_ABSORB = 1, ORA_ROUND = 2, ORA_SAMPLE = 3, ORA_COLLIDE = 4 };
+
+typedef struct { uint32_t k0, k1; } ora_key;
+
+static void draw(ora_key key, uint32_t id, uint32_t sub, uint32_t step, uint32_t purpose,
+                 uint32_t w[4])
+{
+    uint32_t c[4] = { id, sub, step, purpose };
+    ora_philox(key.k0, key.k1, c, w);
+}
+
+/* Unbiased-enough integer pick in [0,n) by the multiply-shift map of a 32-bit word. */
+static uint32_t pick(uint32_t w, uint32_t n) { return (uint32_t)(((uint64_t)w * n) >> 32); }
+
+/* Pair of distinct indices in [0,N) (N >= 2): a uniform, b uniform over the others. */
+void ora_pick_pair(uint32_t w0, uint32_t w1, uint32_t N, uint32_t *a, uint32_t *b)
+{
+    uint32_t ia = pick(w0, N);
+    uint32_t ib = pick(w1, N - 1u);
+    if (ib >= ia) ib += 1u;
+    *a = ia; *b = ib;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Problem description (the paper's problem statement: gas and VHS constants, */
+/* mesh, Kn, time step, boundary states; Sec. 4 and Appendix A).              */
+/* ------------------------------------------------------------------------- */
+typedef struct { double rho, u, v, w, T; } ora_state;
+
+enum { ORA_BC_INOUT = 0, ORA_BC_SPECULAR = 1, ORA_BC_PERIODIC = 2, ORA_BC_VACUUM = 3 };
+enum { ORA_EPS1 = 0, ORA_EPS12 = 1, ORA_EPS0 = 2, ORA_EPS_AVG = 3 };
+enum { ORA_FLUX_GKS_EQ = 0, ORA_FLUX_KFVS = 1 };
+enum { ORA_NTC_PARTICLE = 0, ORA_NTC_TOTAL = 1 };
+
+typedef struct {
+    double gamma, Pr, R;
+    double omega, alpha;
+    double rho_ref, T_ref, Kn, L_ref;
+    double x_min, x_max;
+    int32_t n_cells;
+    double dt, cfl;
+    ora_state left, right;
+    double x_split;
+    int32_t bc_left, bc_right;
+    double ppc_ref;
+    int32_t fp32, eps_mode, flux_mode, ntc_rate;
+    uint64_t seed;
+    int32_t avg_start;
+} ora_params;
+
+typedef struct {
+    double dx, dt, dtdx, mp, dx_over_mp, mp_over_dx;
+    double beta, lambda_ref, mu_ref, p_ref, upsilon, c_ref, ntc_A;
+    float dtdx_f;
+} ora_consts;
+
+/* beta of the mean-free-path relation, Eq. (lambda), first form (Sec. 4.1). */
+double ora_beta(double omega, double alpha)
+{
+    return 5.0 * (alpha + 1.0) * (alpha + 2.0) / (4.0 * alpha * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
+}
+
+/* c_{r,ref} = sqrt(2 k T_ref / m_r) / Gamma(2.5 - omega)^{0.5/upsilon}, with k = mR and
+ * m_r = m/2, so 2kT_ref/m_r = 4 R T_ref (Appendix A).  HS (upsilon = 0) needs none. */
+double ora_c_ref(double omega, double R, double T_ref)
+{
+    double ups = omega - 0.5;
+    if (ups == 0.0) return sqrt(4.0 * R * T_ref);
+    return sqrt(4.0 * R * T_ref) / pow(tgamma(2.5 - omega), 0.5 / ups);
+}
+
+static double smax_of(const ora_state *s, double R)
+{
+    return fabs(s->u) + 3.0 * sqrt(2.0 * R * s->T);
+}
+
+static void derive(const ora_params *p, ora_consts *c)
+{
+    c->dx = (p->x_max - p->x_min) / (double)p->n_cells;
+    c->beta = ora_beta(p->omega, p->alpha);
+    c->lambda_ref = p->Kn * p->L_ref;
+    c->p_ref = p->rho_ref * p->R * p->T_ref;
+    /* Eq. (lambda) solved for mu at the reference state. */
+    c->mu_ref = c->beta * c->lambda_ref * c->p_ref * sqrt(2.0 * ORA_PI / (p->R * p->T_ref));
+    c->mp = p->rho_ref * c->dx / p->ppc_ref;
+    c->dx_over_mp = c->dx / c->mp;
+    c->mp_over_dx = c->mp / c->dx;
+    if (p->dt > 0.0) {
+        c->dt = p->dt;
+    } else {
+        /* reading: one global dt fixed at start from the CFL number and the
+         * fastest initial state (|U| + 3 sqrt(2RT)). */
+        double s = smax_of(&p->left, p->R);
+        double s2 = smax_of(&p->right, p->R);
+        if (s2 > s) s = s2;
+        c->dt = p->cfl * c->dx / s;
+    }
+    c->dtdx = c->dt / c->dx;
+    c->dtdx_f = (float)c->dtdx;
+    c->upsilon = p->omega - 0.5;
+    c->c_ref = ora_c_ref(p->omega, p->R, p->T_ref);
+    c->ntc_A = c->dt / (2.0 * sqrt(2.0) * c->lambda_ref);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Macroscopic quantities (Sec. 2): Psi = (rho, rho U, rho V, rho W, rho E),  */
+/* rho E = 1/2 rho |U|^2 + 3/2 rho R T for a monatomic gas (D = 0).            */
+/* ------------------------------------------------------------------------- */
+typedef struct { double rho, u, v, w, T; int valid; } ora_prim;
+
+static void cons_of_state(const ora_state *s, double R, double psi[5])
+{
+    psi[0] = s->rho;
+    psi[1] = s->rho * s->u;
+    psi[2] = s->rho * s->v;
+    psi[3] = s->rho * s->w;
+    psi[4] = 0.5 * s->rho * (s->u * s->u + s->v * s->v + s->w * s->w) + 1.5 * s->rho * R * s->T;
+}
+
+static ora_prim prim_of_cons(const double psi[5], double R)
+{
+    ora_prim q;
+    q.rho = psi[0];
+    q.valid = 0;
+    q.u = q.v = q.w = q.T = 0.0;
+    if (!(q.rho > 0.0)) return q;
+    q.u = psi[1] / q.rho;
+    q.v = psi[2] / q.rho;
+    q.w = psi[3] / q.rho;
+    double e = psi[4] / q.rho - 0.5 * (q.u * q.u + q.v * q.v + q.w * q.w);
+    q.T = e / (1.5 * R);
+    q.valid = (q.T > 0.0) && isfinite(q.T) && isfinite(q.u) && isfinite(q.v) && isfinite(q.w);
+    return q;
+}
+
+static double mu_of_T(const ora_params *p, const ora_consts *c, double T)
+{
+    return c->mu_ref * pow(T / p->T_ref, p->omega);
+}
+
+/* Absorption fraction, Eq. (p): P = 0 for dt <= tau, 1 - tau/dt otherwise; tau = mu/p. */
+static double pfrac(const ora_params *p, const ora_consts *c, const ora_prim *q)
+{
+    if (!q->valid) return 0.0;
+    double tau = mu_of_T(p, c, q->T) / (q->rho * p->R * q->T);
+    if (c->dt <= tau) return 0.0;
+    return 1.0 - tau / c->dt;
+}
+
+/* Viscosity correction factors of Sec. 3.3 as functions of x = dt/tau:
+ * eps1 (Eq. vp1) = 1 - x e^{-x}/(1-e^{-x}) = 1 - x/(e^x - 1); eps12 = x/(2+x); eps0 = 1;
+ * time-averaged eps (Eq. vp) = [-2(1-e^{-x}) + x(1+e^{-x})] / [x - (1-e^{-x})]. */
+double ora_eps(int mode, double x)
+{
+    if (mode == ORA_EPS0) return 1.0;
+    if (mode == ORA_EPS12) return x / (2.0 + x);
+    if (mode == ORA_EPS_AVG) {
+        double a = -expm1(-x);          /* 1 - e^{-x} */
+        double b = 1.0 + exp(-x);       /* 1 + e^{-x} */
+        return (-2.0 * a + x * b) / (x - a);
+    }
+    double d = expm1(x);                 /* e^x - 1, overflows to inf for large x: eps -> 1 */
+    return 1.0 - x / d;
+}
+
+/* Moments of the half-Maxwellian in the normal velocity u (unit density):
+ * Mp[n] = <u^n> over u > 0, Mm[n] over u < 0, with lam = 1/(2RT).
+ * <u^0> = erfc(-+sqrt(lam) U)/2, <u^1> = U<u^0> +- e^{-lam U^2}/(2 sqrt(pi lam)),
+ * <u^{n+1}> = U <u^n> + n/(2 lam) <u^{n-1}>. */
+void ora_half_moments(double U, double lam, double Mp[4], double Mm[4])
+{
+    double sl = sqrt(lam);
+    Mp[0] = 0.5 * erfc(-sl * U);
+    Mm[0] = 0.5 * erfc(sl * U);
+    double e = 0.5 * exp(-lam * U * U) / sqrt(ORA_PI * lam);
+    Mp[1] = U * Mp[0] + e;
+    Mm[1] = U * Mm[0] - e;
+    for (int n = 1; n <= 2; ++n) {
+        Mp[n + 1] = U * Mp[n] + (double)n * Mp[n - 1] / (2.0 * lam);
+        Mm[n + 1] = U * Mm[n] + (double)n * Mm[n - 1] / (2.0 * lam);
+    }
+}
+
+/* Wave flux across one interface (Step 3, "calculated by N-S solvers"; Sec. 3.3, Eq. ce2
+ * evaluated at t = dt with eps1 of Eq. vp1).  Reading: first-order states; the
+ * interface equilibrium W0 is built from the right-going half of the left
+ * Maxwellian and the left-going half of the right one (GKS_EQ), or the flux is the
+ * split kinetic flux of the two halves (KFVS); the NS viscous and heat-flux terms use
+ * mu_e = eps * mu(T0) and one-sided differences of the neighbouring cell states; the
+ * whole wave flux is weighted by P_f = max(0, 1 - tau_f/dt) at the interface state.
+ * Returns the flux per unit area (mass, x/y/z momentum, energy). */
+static void wave_flux(const ora_params *p, const ora_consts *c, const ora_prim *L, const ora_prim *Rr,
+                      int viscous_ok, double F[5])
+{
+    for (int k = 0; k < 5; ++k) F[k] = 0.0;
+    double MpL[4] = { 0, 0, 0, 0 }, MmL[4] = { 0, 0, 0, 0 };
+    double MpR[4] = { 0, 0, 0, 0 }, MmR[4] = { 0, 0, 0, 0 };
+    double lamL = 0.0, lamR = 0.0;
+    if (L->valid) { lamL = 1.0 / (2.0 * p->R * L->T); ora_half_moments(L->u, lamL, MpL, MmL); }
+    if (Rr->valid) { lamR = 1.0 / (2.0 * p->R * Rr->T); ora_half_moments(Rr->u, lamR, MpR, MmR); }
+    double rL = L->valid ? L->rho : 0.0, rR = Rr->valid ? Rr->rho : 0.0;
+    double tL = L->valid ? (L->v * L->v + L->w * L->w + 1.0 / lamL) : 0.0;
+    double tR = Rr->valid ? (Rr->v * Rr->v + Rr->w * Rr->w + 1.0 / lamR) : 0.0;
+
+    /* interface equilibrium state W0 (conservative) */
+    double rho0 = rL * MpL[0] + rR * MmR[0];
+    double m0 = rL * MpL[1] + rR * MmR[1];
+    double mv0 = rL * L->v * MpL[0] + rR * Rr->v * MmR[0];
+    double mw0 = rL * L->w * MpL[0] + rR * Rr->w * MmR[0];
+    double E0 = 0.5 * (rL * (MpL[2] + tL * MpL[0]) + rR * (MmR[2] + tR * MmR[0]));
+    if (!(rho0 > 0.0)) return;
+    double U0 = m0 / rho0, V0 = mv0 / rho0, W0 = mw0 / rho0;
+    double T0 = (E0 / rho0 - 0.5 * (U0 * U0 + V0 * V0 + W0 * W0)) / (1.5 * p->R);
+    if (!(T0 > 0.0)) return;
+    double p0 = rho0 * p->R * T0;
+    double mu0 = mu_of_T(p, c, T0);
+    double tauf = mu0 / p0;
+    if (c->dt <= tauf) return;                 /* P_f = 0: no wave flux (DSMC regime) */
+    double Pf = 1.0 - tauf / c->dt;
+
+    double Fe[5];
+    if (p->flux_mode == ORA_FLUX_KFVS) {
+        Fe[0] = rL * MpL[1] + rR * MmR[1];
+        Fe[1] = rL * MpL[2] + rR * MmR[2];
+        Fe[2] = rL * L->v * MpL[1] + rR * Rr->v * MmR[1];
+        Fe[3] = rL * L->w * MpL[1] + rR * Rr->w * MmR[1];
+        Fe[4] = 0.5 * (rL * (MpL[3] + tL * MpL[1]) + rR * (MmR[3] + tR * MmR[1]));
+    } else {
+        /* Euler flux of the interface equilibrium g0 */
+        Fe[0] = m0;
+        Fe[1] = m0 * U0 + p0;
+        Fe[2] = m0 * V0;
+        Fe[3] = m0 * W0;
+        Fe[4] = U0 * (E0 + p0);
+    }
+    if (viscous_ok && L->valid && Rr->valid) {
+        double x = c->dt / tauf;
+        double eps = ora_eps(p->eps_mode, x);
+        double mue = eps * mu0;
+        double kape = 2.5 * p->R * mue / p->Pr;
+        double dU = (Rr->u - L->u) / c->dx;
+        double dV = (Rr->v - L->v) / c->dx;
+        double dW = (Rr->w - L->w) / c->dx;
+        double dT = (Rr->T - L->T) / c->dx;
+        double txx = (4.0 / 3.0) * mue * dU;
+        double txy = mue * dV;
+        double txz = mue * dW;
+        Fe[1] -= txx;
+        Fe[2] -= txy;
+        Fe[3] -= txz;
+        Fe[4] -= U0 * txx + V0 * txy + W0 * txz + kape * dT;
+    }
+    for (int k = 0; k < 5; ++k) F[k] = Pf * Fe[k];
+}
+
+/* exported for the pin tests: flux of two primitive states */
+void ora_wave_flux(const ora_params *p, const double WL[5], const double WR[5], int viscous_ok, double F[5])
+{
+    ora_consts c;
+    derive(p, &c);
+    ora_prim L = { WL[0], WL[1], WL[2], WL[3], WL[4], 0 }, Rr = { WR[0], WR[1], WR[2], WR[3], WR[4], 0 };
+    L.valid = (L.rho > 0.0 && L.T > 0.0);
+    Rr.valid = (Rr.rho > 0.0 && Rr.T > 0.0);
+    wave_flux(p, &c, &L, &Rr, viscous_ok, F);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Particles                                                                   */
+/* ------------------------------------------------------------------------- */
+typedef struct { int32_t cell; double xl, u, v, w; } opart;
+
+static double st(const ora_params *p, double x) { return p->fp32 ? (double)(float)x : x; }
+
+/* The moments phi = (1, xi, |xi|^2/2) of one particle (Sec. 2), mass factor applied by caller. */
+static void add_phi(double acc[5], const opart *q)
+{
+    acc[0] += 1.0;
+    acc[1] += q->u;
+    acc[2] += q->v;
+    acc[3] += q->w;
+    acc[4] += 0.5 * (q->u * q->u + q->v * q->v + q->w * q->w);
+}
+
+/* Maxwellian sample at (U, V, W, T), Eq. (maxsample): xi = U + sqrt(2RT) cos(2 pi r1) sqrt(-ln r2)
+ * per component, r2 in (0,1]; position uniform in the cell (reading). */
+static void sample_particle(const ora_params *p, ora_key key, uint32_t id, uint32_t j, uint32_t step,
+                            const ora_prim *q, opart *out)
+{
+    uint32_t w[16];
+    for (uint32_t t = 0; t < 4; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE, w + 4 * t);
+    double u[8];
+    for (int k = 0; k < 8; ++k) u[k] = ora_u53(w[2 * k], w[2 * k + 1]);
+    double sq = sqrt(2.0 * p->R * q->T);
+    double mean[3] = { q->u, q->v, q->w };
+    double xi[3];
+    for (int d = 0; d < 3; ++d) {
+        double r1 = u[1 + 2 * d];
+        double r2 = 1.0 - u[2 + 2 * d];
+        xi[d] = mean[d] + (sq * cos(ORA_TWO_PI * r1)) * sqrt(-log(r2));
+    }
+    double xl = u[0];
+    if (p->fp32) {
+        float xf = (float)xl;
+        if (xf >= 1.0f) xf = 0x1.fffffep-1f;
+        xl = (double)xf;
+    }
+    out->xl = xl;
+    out->u = st(p, xi[0]);
+    out->v = st(p, xi[1]);
+    out->w = st(p, xi[2]);
+}
+
+/* Isotropic VHS post-collision velocities for equal masses (Appendix A):
+ * cos(theta) = 2 r1 - 1, phi = 2 pi r2, xi_r' = c_r (sin cos, sin sin, cos),
+ * xi_a' = xi_m + xi_r'/2, xi_b' = xi_m - xi_r'/2, xi_m = (xi_a + xi_b)/2
+ * (primes: post-collision values). */
+void ora_scatter(double r1, double r2, double a[3], double b[3])
+{
+    double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    double cr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double ct = 2.0 * r1 - 1.0;
+    double stt = sqrt(1.0 - ct * ct);
+    double ph = ORA_TWO_PI * r2;
+    double c0 = (cr * stt) * cos(ph), c1 = (cr * stt) * sin(ph), c2 = cr * ct;
+    double m0 = (a[0] + b[0]) * 0.5, m1 = (a[1] + b[1]) * 0.5, m2 = (a[2] + b[2]) * 0.5;
+    a[0] = m0 + c0 * 0.5; a[1] = m1 + c1 * 0.5; a[2] = m2 + c2 * 0.5;
+    b[0] = m0 - c0 * 0.5; b[1] = m1 - c1 * 0.5; b[2] = m2 - c2 * 0.5;
+}
+
+/* NTC candidate count before rounding, nondimensional form of Appendix A:
+ * (1/(2 sqrt2 lambda_ref)) (rho/rho_ref) (N-1) dt (c_max/c_ref)^{-2 upsilon} c_max. */
+static double ntc_nsel(const ora_consts *c, double rho_ratio, double N, double cmax)
+{
+    double f = (c->upsilon == 0.0) ? 1.0 : pow(cmax / c->c_ref, -2.0 * c->upsilon);
+    return c->ntc_A * rho_ratio * (N - 1.0) * f * cmax;
+}
+
+double ora_ntc_nsel(const ora_params *p, double rho_ratio, double N, double cmax)
+{
+    ora_consts c;
+    derive(p, &c);
+    return ntc_nsel(&c, rho_ratio, N, cmax);
+}
+
+/* Acceptance probability sigma_T c_r / (sigma_T c_r)_max = (c_r/c_max)^{1 - 2 upsilon}. */
+static double accept_prob(const ora_consts *c, double cr, double cmax)
+{
+    double x = cr / cmax;
+    if (c->upsilon == 0.0) return x;
+    return pow(x, 1.0 - 2.0 * c->upsilon);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Instance                                                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    ora_params p;
+    ora_consts c;
+    ora_key key;
+    int32_t C;
+    double *psi;      /* C x 5, total state Psi_t */
+    double *avg;      /* C x 5, time-averaged Psi_t */
+    int64_t navg;
+    double *cmax;     /* C, NTC majorant c_r,max per cell */
+    opart *parts;     /* sorted by cell, stable */
+    int64_t np, cap;
+    uint32_t step;
+    /* last-step diagnostics per cell */
+    int32_t *ncand, *nacc, *nabs, *nnew;
+    int64_t nfar;      /* particles that moved two or more cells (or wrapped) in the last step */
+    double *last_flux; /* (C+1) x 5 */
+    double *pre_m, *post_m; /* C x 5, particle moment sums of the last step (unscaled) */
+    opart *lastpre;   /* pre-transport array of the last step (source cell in .cell) */
+    int64_t *lastdest; /* destination cell of each entry, -1 = left the domain */
+    int64_t nlastpre;
+} ora_inst;
+
+static int grow(ora_inst *h, opart **arr, int64_t *cap, int64_t need)
+{
+    if (need <= *cap) return 0;
+    int64_t nc = *cap ? *cap : 1024;
+    while (nc < need) nc *= 2;
+    opart *na = (opart *)realloc(*arr, (size_t)nc * sizeof(opart));
+    if (!na) return -1;
+    *arr = na;
+    *cap = nc;
+    (void)h;
+    return 0;
+}
+
+static ora_prim ghost_prim(const ora_inst *h, int side, const ora_prim *inner)
+{
+    const ora_params *p = &h->p;
+    int bc = side ? p->bc_right : p->bc_left;
+    ora_prim g;
+    memset(&g, 0, sizeof g);
+    if (bc == ORA_BC_INOUT) {
+        const ora_state *s = side ? &p->right : &p->left;
+        g.rho = s->rho; g.u = s->u; g.v = s->v; g.w = s->w; g.T = s->T;
+        g.valid = (g.rho > 0.0 && g.T > 0.0);
+    } else if (bc == ORA_BC_SPECULAR) {
+        g = *inner;
+        g.u = -inner->u;
+    } else if (bc == ORA_BC_VACUUM) {
+        g.valid = 0;
+    }
+    return g;
+}
+
+void *ora_create(const ora_params *p)
+{
+    if (p->n_cells < 1 || !(p->x_max > p->x_min) || !(p->ppc_ref > 0.0) || !(p->Kn > 0.0)) return NULL;
+    if ((p->bc_left == ORA_BC_PERIODIC) != (p->bc_right == ORA_BC_PERIODIC)) return NULL;
+    ora_inst *h = (ora_inst *)calloc(1, sizeof(ora_inst));
+    if (!h) return NULL;
+    h->p = *p;
+    derive(p, &h->c);
+    h->key.k0 = (uint32_t)(p->seed & 0xffffffffu);
+    h->key.k1 = (uint32_t)(p->seed >> 32);
+    h->C = p->n_cells;
+    int32_t C = h->C;
+    h->psi = (double *)calloc((size_t)C * 5, sizeof(double));
+    h->avg = (double *)calloc((size_t)C * 5, sizeof(double));
+    h->cmax = (double *)calloc((size_t)C, sizeof(double));
+    h->ncand = (int32_t *)calloc((size_t)C, sizeof(int32_t));
+    h->nacc = (int32_t *)calloc((size_t)C, sizeof(int32_t));
+    h->nabs = (int32_t *)calloc((size_t)C, sizeof(int32_t));
+    h->nnew = (int32_t *)calloc((size_t)C, sizeof(int32_t));
+    h->last_flux = (double *)calloc((size_t)(C + 1) * 5, sizeof(double));
+    h->pre_m = (double *)calloc((size_t)C * 5, sizeof(double));
+    h->post_m = (double *)calloc((size_t)C * 5, sizeof(double));
+    /* Step 1 initial state: Psi_t from the two-state profile (cell centres), Psi_p = 0 (reading). */
+    for (int32_t i = 0; i < C; ++i) {
+        double xc = p->x_min + ((double)i + 0.5) * h->c.dx;
+        const ora_state *s = (xc < p->x_split) ? &p->left : &p->right;
+        cons_of_state(s, p->R, h->psi + 5 * i);
+        /* reading: the NTC majorant starts at 5 sqrt(2RT) of the initial cell state */
+        h->cmax[i] = 5.0 * sqrt(2.0 * p->R * s->T);
+    }
+    return h;
+}
+
+void ora_destroy(void *vh)
+{
+    ora_inst *h = (ora_inst *)vh;
+    if (!h) return;
+    free(h->psi); free(h->avg); free(h->cmax); free(h->parts);
+    free(h->ncand); free(h->nacc); free(h->nabs); free(h->nnew);
+    free(h->last_flux); free(h->pre_m); free(h->post_m);
+    free(h->lastpre); free(h->lastdest);
+    free(h);
+}
+
+/* Free transport of one particle over dt in cell units, with the boundary conditions.
+ * Returns the new cell in [0,C) or -1 if the particle left the domain.  The particle
+ * position is cell-local, xl in [0,1). */
+static int64_t transport(const ora_inst *h, int64_t cell, opart *q)
+{
+    const ora_params *p = &h->p;
+    int64_t C = h->C;
+    int64_t k;
+    double xl;
+    if (p->fp32) {
+        float s = fmaf((float)q->u, h->c.dtdx_f, (float)q->xl);
+        float fk = floorf(s);
+        float x = s - fk;
+        k = (int64_t)fk;
+        if (x >= 1.0f) { x = 0.0f; k += 1; }
+        xl = (double)x;
+    } else {
+        double s = fma(q->u, h->c.dtdx, q->xl);
+        double fk = floor(s);
+        double x = s - fk;
+        k = (int64_t)fk;
+        if (x >= 1.0) { x = 0.0; k += 1; }
+        xl = x;
+    }
+    int64_t dest = cell + k;
+    for (;;) {
+        if (dest < 0) {
+            if (p->bc_left == ORA_BC_SPECULAR) {
+                dest = -dest - 1;
+                xl = p->fp32 ? (double)(1.0f - (float)xl) : 1.0 - xl;
+                if (xl >= 1.0) { xl = 0.0; dest += 1; }
+                q->u = -q->u;
+                continue;
+            }
+            if (p->bc_left == ORA_BC_PERIODIC) { dest = ((dest % C) + C) % C; continue; }
+            return -1;
+        }
+        if (dest >= C) {
+            if (p->bc_right == ORA_BC_SPECULAR) {
+                dest = 2 * C - dest - 1;
+                xl = p->fp32 ? (double)(1.0f - (float)xl) : 1.0 - xl;
+                if (xl >= 1.0) { xl = 0.0; dest += 1; }
+                q->u = -q->u;
+                continue;
+            }
+            if (p->bc_right == ORA_BC_PERIODIC) { dest = dest % C; continue; }
+            return -1;
+        }
+        break;
+    }
+    q->xl = xl;
+    return dest;
+}
+
+/* exported for pin tests: transport one particle from `cell` and report the new cell */
+int64_t ora_transport(void *vh, int64_t cell, double *xl, double *u)
+{
+    ora_inst *h = (ora_inst *)vh;
+    opart q = { 0, *xl, *u, 0.0, 0.0 };
+    int64_t d = transport(h, cell, &q);
+    *xl = q.xl;
+    *u = q.u;
+    return d;
+}
+
+/* Collisions in one cell, NTC with VHS/HS (Appendix A).  `list` holds the N particles
+ * of the cell after absorption and re-sampling; c_max persists per cell (reading). */
+static void collide_cell(ora_inst *h, int32_t i, opart *list, int64_t N, double rho_t, int32_t *ncand,
+                         int32_t *nacc)
+{
+    const ora_params *p = &h->p;
+    const ora_consts *c = &h->c;
+    *ncand = 0;
+    *nacc = 0;
+    if (N < 2) return;
+    double rho_ratio;
+    if (p->ntc_rate == ORA_NTC_TOTAL) rho_ratio = rho_t / p->rho_ref;
+    else rho_ratio = ((double)N * c->mp / c->dx) / p->rho_ref;
+    double cmax = h->cmax[i];
+    double nsel = ntc_nsel(c, rho_ratio, (double)N, cmax);
+    uint32_t w[4];
+    draw(h->key, (uint32_t)(i + 1), 1u, h->step, ORA_ROUND, w);
+    /* reading: stochastic rounding of the candidate count */
+    double ncd = floor(nsel + ora_u53(w[0], w[1]));
+    int64_t Nc = (int64_t)ncd;
+    int32_t acc = 0;
+    for (int64_t k = 0; k < Nc; ++k) {
+        draw(h->key, (uint32_t)(i + 1), (uint32_t)(2 * k), h->step, ORA_COLLIDE, w);
+        uint32_t a, b;
+        ora_pick_pair(w[0], w[1], (uint32_t)N, &a, &b);
+        opart *A = list + a, *B = list + b;
+        double d0 = A->u - B->u, d1 = A->v - B->v, d2 = A->w - B->w;
+        double cr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        if (cr > cmax) cmax = cr;      /* reading: majorant raised before the test */
+        double ua = ora_u53(w[2], w[3]);
+        if (ua < accept_prob(c, cr, cmax)) {
+            uint32_t v[4];
+            draw(h->key, (uint32_t)(i + 1), (uint32_t)(2 * k + 1), h->step, ORA_COLLIDE, v);
+            double va[3] = { A->u, A->v, A->w }, vb[3] = { B->u, B->v, B->w };
+            ora_scatter(ora_u53(v[0], v[1]), ora_u53(v[2], v[3]), va, vb);
+            A->u = st(p, va[0]); A->v = st(p, va[1]); A->w = st(p, va[2]);
+            B->u = st(p, vb[0]); B->v = st(p, vb[1]); B->w = st(p, vb[2]);
+            ++acc;
+        }
+    }
+    h->cmax[i] = cmax;
+    *ncand = (int32_t)Nc;
+    *nacc = acc;
+}
+
+/* Number of particles re-sampled from the wave: stochastic rounding of
+ * (1-P) max(rho_w, 0) dx / m_p (reading of "1-P of wave part converted"). */
+static int64_t n_resample(const ora_inst *h, uint32_t id, double P, double rho_w)
+{
+    uint32_t w[4];
+    draw(h->key, id, 0u, h->step, ORA_ROUND, w);
+    double x = ((1.0 - P) * fmax(rho_w, 0.0)) * h->c.dx_over_mp;
+    return (int64_t)floor(x + ora_u53(w[0], w[1]));
+}
+
+typedef struct { opart q; int64_t dest; } moved;
+
+int ora_step(void *vh, int32_t nsteps)
+{
+    ora_inst *h = (ora_inst *)vh;
+    const ora_params *p = &h->p;
+    const ora_consts *c = &h->c;
+    int32_t C = h->C;
+    ora_prim *W = (ora_prim *)malloc((size_t)C * sizeof(ora_prim));
+    double *P = (double *)malloc((size_t)C * sizeof(double));
+    double *F = (double *)malloc((size_t)(C + 1) * 5 * sizeof(double));
+    int64_t *start = (int64_t *)malloc((size_t)(C + 1) * sizeof(int64_t));
+    if (!W || !P || !F || !start) { free(W); free(P); free(F); free(start); return -2; }
+    for (int32_t s = 0; s < nsteps; ++s) {
+        /* Step 1: total state and the split fraction of every cell */
+        for (int32_t i = 0; i < C; ++i) {
+            W[i] = prim_of_cons(h->psi + 5 * i, p->R);
+            P[i] = pfrac(p, c, &W[i]);
+        }
+        /* wave flux at the C+1 interfaces from the start-of-step states */
+        for (int32_t f = 0; f <= C; ++f) {
+            ora_prim L, Rr;
+            if (f == 0) {
+                Rr = W[0];
+                if (p->bc_left == ORA_BC_PERIODIC) L = W[C - 1];
+                else L = ghost_prim(h, 0, &W[0]);
+            } else if (f == C) {
+                L = W[C - 1];
+                if (p->bc_right == ORA_BC_PERIODIC) Rr = W[0];
+                else Rr = ghost_prim(h, 1, &W[C - 1]);
+            } else {
+                L = W[f - 1];
+                Rr = W[f];
+            }
+            wave_flux(p, c, &L, &Rr, 1, F + 5 * f);
+        }
+        if (p->bc_left == ORA_BC_PERIODIC) {
+            /* the two boundary interfaces are the same interface */
+            for (int k = 0; k < 5; ++k) F[5 * C + k] = F[k];
+        }
+        memcpy(h->last_flux, F, (size_t)(C + 1) * 5 * sizeof(double));
+
+        /* cell starts in the sorted particle array */
+        for (int32_t i = 0; i <= C; ++i) start[i] = 0;
+        for (int64_t q = 0; q < h->np; ++q) start[h->parts[q].cell + 1] += 1;
+        for (int32_t i = 0; i < C; ++i) start[i + 1] += start[i];
+
+        /* Step 2 per cell: absorb, re-sample, collide; build the pre-transport array,
+         * ordered left ghost, cells 0..C-1, right ghost */
+        opart *pre = NULL;
+        int64_t npre = 0, cpre = 0;
+        memset(h->pre_m, 0, (size_t)C * 5 * sizeof(double));
+        /* left ghost reservoir (inflow boundary) */
+        if (p->bc_left == ORA_BC_INOUT) {
+            ora_prim g = ghost_prim(h, 0, &W[0]);
+            double Pg = pfrac(p, c, &g);
+            int64_t ng = g.valid ? n_resample(h, 0u, Pg, g.rho) : 0;
+            if (grow(h, &pre, &cpre, npre + ng)) return -2;
+            for (int64_t j = 0; j < ng; ++j) {
+                opart *q = pre + npre++;
+                sample_particle(p, h->key, 0u, (uint32_t)j, h->step, &g, q);
+                q->cell = -1;
+            }
+        }
+        for (int32_t i = 0; i < C; ++i) {
+            int64_t n0 = start[i], n1 = start[i + 1];
+            int64_t base = npre;
+            if (grow(h, &pre, &cpre, npre + (n1 - n0))) return -2;
+            int32_t nab = 0;
+            for (int64_t k = n0; k < n1; ++k) {
+                int absorbed = 0;
+                if (P[i] > 0.0) {
+                    uint32_t w[4];
+                    draw(h->key, (uint32_t)(i + 1), (uint32_t)(k - n0), h->step, ORA_ABSORB, w);
+                    absorbed = ora_u53(w[0], w[1]) < P[i];
+                }
+                if (absorbed) { ++nab; continue; }
+                pre[npre++] = h->parts[k];
+            }
+            int64_t nsurv = npre - base;
+            double rho_w = h->psi[5 * i] - (double)nsurv * c->mp_over_dx;
+            int64_t nn = W[i].valid ? n_resample(h, (uint32_t)(i + 1), P[i], rho_w) : 0;
+            if (grow(h, &pre, &cpre, npre + nn)) return -2;
+            for (int64_t j = 0; j < nn; ++j) {
+                opart *q = pre + npre++;
+                sample_particle(p, h->key, (uint32_t)(i + 1), (uint32_t)j, h->step, &W[i], q);
+                q->cell = i;
+            }
+            collide_cell(h, i, pre + base, npre - base, h->psi[5 * i], &h->ncand[i], &h->nacc[i]);
+            h->nabs[i] = nab;
+            h->nnew[i] = (int32_t)nn;
+            for (int64_t q = base; q < npre; ++q) add_phi(h->pre_m + 5 * i, pre + q);
+        }
+        if (p->bc_right == ORA_BC_INOUT) {
+            ora_prim g = ghost_prim(h, 1, &W[C - 1]);
+            double Pg = pfrac(p, c, &g);
+            int64_t ng = g.valid ? n_resample(h, (uint32_t)(C + 1), Pg, g.rho) : 0;
+            if (grow(h, &pre, &cpre, npre + ng)) return -2;
+            for (int64_t j = 0; j < ng; ++j) {
+                opart *q = pre + npre++;
+                sample_particle(p, h->key, (uint32_t)(C + 1), (uint32_t)j, h->step, &g, q);
+                q->cell = C;
+            }
+        }
+
+        /* Step 3: free transport; particles leaving the domain are removed */
+        moved *mv = (moved *)malloc((size_t)(npre ? npre : 1) * sizeof(moved));
+        if (!mv) return -2;
+        int64_t nfar = 0;
+        for (int64_t q = 0; q < npre; ++q) {
+            mv[q].q = pre[q];
+            mv[q].dest = transport(h, pre[q].cell, &mv[q].q);
+            if (mv[q].dest >= 0) {
+                int64_t d = mv[q].dest - pre[q].cell;
+                if (d < -1 || d > 1) ++nfar;
+            }
+        }
+        h->nfar = nfar;
+        /* stable counting sort by the new cell: ties keep the pre-transport order */
+        int64_t *cnt = (int64_t *)calloc((size_t)C + 1, sizeof(int64_t));
+        for (int64_t q = 0; q < npre; ++q)
+            if (mv[q].dest >= 0) cnt[mv[q].dest + 1] += 1;
+        for (int32_t i = 0; i < C; ++i) cnt[i + 1] += cnt[i];
+        int64_t nkeep = cnt[C];
+        if (nkeep > h->cap) {
+            int64_t nc = h->cap ? h->cap : 1024;
+            while (nc < nkeep) nc *= 2;
+            opart *na = (opart *)realloc(h->parts, (size_t)nc * sizeof(opart));
+            if (!na) return -2;
+            h->parts = na;
+            h->cap = nc;
+        }
+        for (int64_t q = 0; q < npre; ++q) {
+            if (mv[q].dest < 0) continue;
+            int64_t pos = cnt[mv[q].dest]++;
+            h->parts[pos] = mv[q].q;
+            h->parts[pos].cell = (int32_t)mv[q].dest;
+        }
+        h->np = nkeep;
+        free(cnt);
+        free(h->lastpre);
+        free(h->lastdest);
+        h->lastpre = pre;
+        h->lastdest = (int64_t *)malloc((size_t)(npre ? npre : 1) * sizeof(int64_t));
+        if (!h->lastdest) return -2;
+        for (int64_t q = 0; q < npre; ++q) h->lastdest[q] = mv[q].dest;
+        h->nlastpre = npre;
+        free(mv);
+
+        /* particle flux Eq. (fp) = change of the per-cell particle moments over the
+         * transport; wave flux by the NS solver; conservative update Eq. (r1) */
+        memset(h->post_m, 0, (size_t)C * 5 * sizeof(double));
+        for (int64_t q = 0; q < h->np; ++q) add_phi(h->post_m + 5 * h->parts[q].cell, h->parts + q);
+        for (int32_t i = 0; i < C; ++i) {
+            for (int k = 0; k < 5; ++k) {
+                double fp = c->mp_over_dx * (h->post_m[5 * i + k] - h->pre_m[5 * i + k]);
+                double fw = c->dtdx * (F[5 * (i + 1) + k] - F[5 * i + k]);
+                h->psi[5 * i + k] = h->psi[5 * i + k] + fp - fw;
+            }
+        }
+        h->step += 1;
+        if ((int64_t)h->step > (int64_t)p->avg_start) {
+            for (int64_t k = 0; k < (int64_t)C * 5; ++k) h->avg[k] += h->psi[k];
+            h->navg += 1;
+        }
+    }
+    free(W); free(P); free(F); free(start);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Accessors                                                                   */
+/* ------------------------------------------------------------------------- */
+int64_t ora_num_particles(void *vh) { return ((ora_inst *)vh)->np; }
+int64_t ora_num_last_pre(void *vh) { return ((ora_inst *)vh)->nlastpre; }
+
+/* the last step's pre-transport array: source cell (-1 / C for the ghost reservoirs),
+ * destination cell (-1: removed), and the record before transport */
+void ora_get_last_pre(void *vh, int32_t *src, int64_t *dest, double *xl, double *u, double *v, double *w)
+{
+    ora_inst *h = (ora_inst *)vh;
+    for (int64_t q = 0; q < h->nlastpre; ++q) {
+        src[q] = h->lastpre[q].cell;
+        dest[q] = h->lastdest[q];
+        xl[q] = h->lastpre[q].xl;
+        u[q] = h->lastpre[q].u;
+        v[q] = h->lastpre[q].v;
+        w[q] = h->lastpre[q].w;
+    }
+}
+uint32_t ora_step_count(void *vh) { return ((ora_inst *)vh)->step; }
+int64_t ora_last_nfar(void *vh) { return ((ora_inst *)vh)->nfar; }
+
+void ora_get_particles(void *vh, int32_t *cell, double *xl, double *u, double *v, double *w)
+{
+    ora_inst *h = (ora_inst *)vh;
+    for (int64_t q = 0; q < h->np; ++q) {
+        cell[q] = h->parts[q].cell;
+        xl[q] = h->parts[q].xl;
+        u[q] = h->parts[q].u;
+        v[q] = h->parts[q].v;
+        w[q] = h->parts[q].w;
+    }
+}
+
+/* Replace the particle set (test hook: e.g. an anisotropic start for relaxation tests).
+ * The arrays must be sorted by cell. */
+int ora_set_particles(void *vh, int64_t n, const int32_t *cell, const double *xl, const double *u,
+                      const double *v, const double *w)
+{
+    ora_inst *h = (ora_inst *)vh;
+    if (n > h->cap) {
+        opart *na = (opart *)realloc(h->parts, (size_t)(n ? n : 1) * sizeof(opart));
+        if (!na) return -2;
+        h->parts = na;
+        h->cap = n;
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        if (cell[q] < 0 || cell[q] >= h->C) return -1;
+        if (q > 0 && cell[q] < cell[q - 1]) return -1;
+        h->parts[q].cell = cell[q];
+        h->parts[q].xl = st(&h->p, xl[q]);
+        h->parts[q].u = st(&h->p, u[q]);
+        h->parts[q].v = st(&h->p, v[q]);
+        h->parts[q].w = st(&h->p, w[q]);
+    }
+    h->np = n;
+    return 0;
+}
+
+void ora_get_psi(void *vh, double *out) { ora_inst *h = (ora_inst *)vh; memcpy(out, h->psi, (size_t)h->C * 5 * sizeof(double)); }
+void ora_set_psi(void *vh, const double *in) { ora_inst *h = (ora_inst *)vh; memcpy(h->psi, in, (size_t)h->C * 5 * sizeof(double)); }
+int64_t ora_get_avg(void *vh, double *out) { ora_inst *h = (ora_inst *)vh; memcpy(out, h->avg, (size_t)h->C * 5 * sizeof(double)); return h->navg; }
+void ora_get_cmax(void *vh, double *out) { ora_inst *h = (ora_inst *)vh; memcpy(out, h->cmax, (size_t)h->C * sizeof(double)); }
+void ora_get_last_flux(void *vh, double *out) { ora_inst *h = (ora_inst *)vh; memcpy(out, h->last_flux, (size_t)(h->C + 1) * 5 * sizeof(double)); }
+void ora_get_last_moments(void *vh, double *pre, double *post)
+{
+    ora_inst *h = (ora_inst *)vh;
+    memcpy(pre, h->pre_m, (size_t)h->C * 5 * sizeof(double));
+    memcpy(post, h->post_m, (size_t)h->C * 5 * sizeof(double));
+}
+
+void ora_get_counters(void *vh, int32_t *ncand, int32_t *nacc, int32_t *nabs, int32_t *nnew)
+{
+    ora_inst *h = (ora_inst *)vh;
+    memcpy(ncand, h->ncand, (size_t)h->C * sizeof(int32_t));
+    memcpy(nacc, h->nacc, (size_t)h->C * sizeof(int32_t));
+    memcpy(nabs, h->nabs, (size_t)h->C * sizeof(int32_t));
+    memcpy(nnew, h->nnew, (size_t)h->C * sizeof(int32_t));
+}
+
+/* derived constants: dx, dt, dtdx, mp, beta, lambda_ref, mu_ref, upsilon, c_ref, ntc_A */
+void ora_get_consts(void *vh, double out[10])
+{
+    ora_inst *h = (ora_inst *)vh;
+    const ora_consts *c = &h->c;
+    out[0] = c->dx; out[1] = c->dt; out[2] = c->dtdx; out[3] = c->mp; out[4] = c->beta;
+    out[5] = c->lambda_ref; out[6] = c->mu_ref; out[7] = c->upsilon; out[8] = c->c_ref; out[9] = c->ntc_A;
+}
+
+/* primitive state and P of every cell from the current Psi_t */
+void ora_get_prim(void *vh, double *rho, double *u, double *T, double *P, int32_t *valid)
+{
+    ora_inst *h = (ora_inst *)vh;
+    for (int32_t i = 0; i < h->C; ++i) {
+        ora_prim q = prim_of_cons(h->psi + 5 * i, h->p.R);
+        rho[i] = q.rho; u[i] = q.u; T[i] = q.T; valid[i] = q.valid;
+        P[i] = pfrac(&h->p, &h->c, &q);
+    }
+}

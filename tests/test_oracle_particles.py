@@ -1,0 +1,184 @@
+"""Pins of the oracle's particle operations: the isotropic VHS scatter (Appendix A),
+free transport with boundaries (Step 3), Maxwellian sampling (Eq. maxsample), the
+stable per-cell ordering, and the particle flux of Eq. (fp)."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2305_12071_gb300 import workloads as W
+
+
+def test_scatter_conserves_momentum_energy_and_relative_speed(oracle_mod):
+    g = np.random.default_rng(11)
+    for _ in range(2000):
+        a = g.normal(size=3) * 3.0 + 1.0
+        b = g.normal(size=3) * 0.5 - 2.0
+        r1, r2 = g.uniform(size=2)
+        A, B = oracle_mod.scatter(r1, r2, a, b)
+        assert np.allclose(A + B, a + b, rtol=0, atol=1e-13)
+        e0 = (a @ a + b @ b)
+        assert abs((A @ A + B @ B) - e0) <= 1e-13 * e0
+        assert np.linalg.norm(A - B) == pytest.approx(np.linalg.norm(a - b), rel=1e-13)
+
+
+def test_scatter_is_isotropic(oracle_mod):
+    g = np.random.default_rng(3)
+    a = np.array([1.0, 0.0, 0.0])
+    b = np.array([-1.0, 0.0, 0.0])
+    dirs = []
+    for _ in range(4000):
+        r1, r2 = g.uniform(size=2)
+        A, B = oracle_mod.scatter(r1, r2, a, b)
+        dirs.append((A - B) / np.linalg.norm(A - B))
+    dirs = np.array(dirs)
+    # each Cartesian component of a uniform unit vector is uniform on [-1, 1]
+    for k in range(3):
+        assert stats.kstest(dirs[:, k], "uniform", args=(-1, 2)).pvalue > 1e-3
+    assert np.abs(dirs.mean(0)).max() < 0.05
+
+
+def _exact(x):
+    return Fraction(x)
+
+
+def _round_f32(q: Fraction) -> float:
+    """Correctly rounded (nearest, ties to even) float32 of an exact rational."""
+    f = np.float32(float(q))
+    best = None
+    for c in (np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))):
+        d = abs(Fraction(float(c)) - q)
+        if best is None or d < best[0] or (d == best[0] and (np.float32(c).view(np.uint32) & 1) == 0):
+            best = (d, c)
+    return float(best[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_transport_interior_periodic_and_outflow(oracle_mod, precision):
+    C = 40
+    g = np.random.default_rng(5)
+    for bc in ("periodic", "inout"):
+        o = oracle_mod.Oracle(W.uniform(n_cells=C, bc=bc, precision=precision, dt=0.37, x_max=1.0))
+        dtdx = o.consts()["dtdx"]
+        for _ in range(3000):
+            cell = int(g.integers(0, C))
+            xl = float(g.uniform())
+            u = float(g.normal() * 8.0)
+            if precision == "fp32":
+                xl = float(np.float32(xl))
+                u = float(np.float32(u))
+                s = _round_f32(_exact(u) * _exact(float(np.float32(dtdx))) + _exact(xl))
+            else:
+                s = float(_exact(u) * _exact(dtdx) + _exact(xl))
+            xg = cell + s                                   # global coordinate in cell units
+            d, x2, u2 = o.transport(cell, xl, u)
+            # the local position is one rounding of s - floor(s) in the record precision
+            tol = 2.0**-23 if precision == "fp32" else 1e-12
+            assert 0.0 <= x2 < 1.0
+            assert u2 == u
+            if bc == "periodic":
+                assert 0 <= d < C
+                r = (d + x2 - xg) % C
+                assert min(r, C - r) < tol
+            else:
+                inside = 0.0 <= xg < C
+                if not inside:
+                    assert d == -1
+                else:
+                    assert d == math.floor(xg) or abs(xg - round(xg)) < tol
+                    assert d + x2 == pytest.approx(xg, abs=tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_transport_specular_mirror(oracle_mod, precision):
+    C = 10
+    g = np.random.default_rng(9)
+    o = oracle_mod.Oracle(W.uniform(n_cells=C, bc="specular", precision=precision, dt=0.9, x_max=1.0))
+    dtdx = o.consts()["dtdx"]
+    for _ in range(3000):
+        cell = int(g.integers(0, C))
+        xl = float(np.float32(g.uniform()))
+        u = float(np.float32(g.normal() * 6.0))
+        xg = cell + xl + u * dtdx
+        # unfold the mirror images of the segment [0, C]
+        period = 2 * C
+        y = xg % period
+        nref = math.floor(xg / C)          # number of wall reflections (either wall)
+        expect_x = y if y <= C else period - y
+        d, x2, u2 = o.transport(cell, xl, u)
+        tol = 1e-5 if precision == "fp32" else 1e-9
+        assert 0 <= d < C and 0 <= x2 < 1
+        assert d + x2 == pytest.approx(expect_x, abs=tol * max(1.0, abs(u)))
+        assert u2 == (u if nref % 2 == 0 else -u)
+
+
+def test_sampled_maxwellian_moments(oracle_mod):
+    # First step of an all-wave start with P = 0: every particle is drawn from Eq. (maxsample).
+    U, T = 0.4, 1.7
+    p = W.uniform(n_cells=8, Kn=1e3, ppc_ref=6000, state=(1.0, U, -0.2, 0.1, T))
+    o = oracle_mod.Oracle(p)
+    o.step(1)
+    c = o.counters()
+    assert c["ncand"].sum() < 5            # practically collisionless
+    q = o.pre_sample = o.last_pre()
+    inside = q["src"] >= 0
+    u, v, w = q["u"][inside], q["v"][inside], q["w"][inside]
+    n = len(u)
+    assert n == pytest.approx(8 * 6000, abs=8)
+    cu, cv, cw = u - U, v + 0.2, w - 0.1
+    se = math.sqrt(2 * T * T / n)
+    for comp in (cu, cv, cw):
+        assert abs(comp.mean()) < 5 * math.sqrt(T / n)
+        assert abs(np.mean(comp**2) - T) < 5 * se
+    c2 = cu**2 + cv**2 + cw**2
+    # <c^2> = 3RT and <c^4> = 15 (RT)^2 for a three-dimensional Maxwellian
+    assert np.mean(c2) / T == pytest.approx(3.0, rel=0.02)
+    assert np.mean(c2**2) / T**2 == pytest.approx(15.0, rel=0.04)
+    assert stats.kstest(cu / math.sqrt(T), "norm").pvalue > 1e-3
+    assert stats.kstest(q["xl"][inside], "uniform").pvalue > 1e-3
+
+
+def test_stable_sort_by_new_cell(oracle_mod):
+    o = oracle_mod.Oracle(W.config1())
+    o.step(3)
+    pre = o.last_pre()
+    keep = pre["dest"] >= 0
+    order = np.argsort(pre["dest"][keep], kind="stable")
+    post = o.particles()
+    # v and w are untouched by transport: the sorted array is the stable permutation
+    assert np.array_equal(post["v"], pre["v"][keep][order])
+    assert np.array_equal(post["w"], pre["w"][keep][order])
+    assert np.array_equal(post["cell"], pre["dest"][keep][order])
+    assert np.all(np.diff(post["cell"]) >= 0)
+
+
+def test_particle_flux_matches_interface_crossings(oracle_mod):
+    # Eq. (fp): the change of the particle moments of an interior cell is what
+    # crossed its interfaces (entering minus leaving), per particle.
+    o = oracle_mod.Oracle(W.config1())
+    o.step(4)
+    pre = o.last_pre()
+    pre_m, post_m = o.last_moments()
+    phi = np.stack([np.ones_like(pre["u"]), pre["u"], pre["v"], pre["w"],
+                    0.5 * (pre["u"]**2 + pre["v"]**2 + pre["w"]**2)], 1)
+    C = o.C
+    for i in range(3, C - 3):
+        enter = (pre["dest"] == i) & (pre["src"] != i)
+        leave = (pre["src"] == i) & (pre["dest"] != i)
+        fp = phi[enter].sum(0) - phi[leave].sum(0)
+        assert np.allclose(post_m[i] - pre_m[i], fp, rtol=0, atol=1e-9 * max(1.0, np.abs(pre_m[i]).max()))
+
+
+def test_absorption_fraction_is_P(oracle_mod):
+    # near-continuum uniform box: P = 1 - tau/dt; absorbed / arrived ~ Binomial(n, P)
+    p = W.uniform(n_cells=10, Kn=2e-4, ppc_ref=4000, state=(1.0, 0.0, 0.0, 0.0, 1.0), dt=2e-3, x_max=1.0)
+    o = oracle_mod.Oracle(p)
+    o.step(2)
+    n_before = o.num_particles()
+    P = o.prim()["P"].mean()
+    o.step(1)
+    nabs = o.counters()["nabs"].sum()
+    assert 0.3 < P < 0.95
+    assert abs(nabs - P * n_before) < 5 * math.sqrt(n_before * P * (1 - P))

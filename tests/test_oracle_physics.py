@@ -1,0 +1,176 @@
+"""Physics pins of the whole oracle step against what the paper and kinetic theory fix:
+Maxwell-molecule stress relaxation at rate p/mu, the VHS equilibrium collision rate,
+free-molecular expansion (erfc), the continuum limit against the exact Riemann solution
+of the Sod problem (Sec. 4.2), Rankine-Hugoniot far fields of the shock (Sec. 4.1),
+exact conservation in closed boxes, the wave/particle split fixed point, and the
+DSMC limit (dt < tau: no wave flux, no absorption; Sec. 4.1)."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erfc
+
+import riemann_exact as RE
+from paper_2305_12071_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rh_golden():
+    out = {}
+    with open(os.path.join(HERE, "golden", "rankine_hugoniot.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            m, r, p, t = map(float, line.split())
+            out[m] = (r, p, t)
+    return out
+
+
+@pytest.mark.parametrize("mach", [3.0, 8.0, 1.2])
+def test_workload_shock_states_are_rankine_hugoniot(mach):
+    r, p, t = W.rankine_hugoniot(mach)
+    gr, gp, gt = _rh_golden()[mach]
+    assert (r, p, t) == pytest.approx((gr, gp, gt), rel=1e-14)
+
+
+def test_maxwell_molecule_stress_relaxation_rate(oracle_mod):
+    # omega = 1: every NTC candidate is accepted and the traceless stress of a
+    # homogeneous gas decays exactly as exp(-t p/mu).
+    p = W.uniform(n_cells=4, Kn=1.0, ppc_ref=5000, state=(1, 0, 0, 0, 1), omega=1.0)
+    tau = oracle_mod.Oracle(p).consts()["mu_ref"]     # mu/p at rho = T = 1
+    p["dt"] = 0.02 * tau
+    o = oracle_mod.Oracle(p)
+    o.step(1)
+    q = o.particles()
+    u, v, w = q["u"] * math.sqrt(1.5), q["v"] * math.sqrt(0.75), q["w"] * math.sqrt(0.75)
+    o.set_particles(q["cell"], q["xl"], u, v, w)
+    c = o.consts()
+    mpdx = c["mp"] / c["dx"]
+    psi = np.zeros((4, 5))
+    for i in range(4):
+        m = q["cell"] == i
+        psi[i] = mpdx * np.array([m.sum(), u[m].sum(), v[m].sum(), w[m].sum(),
+                                  0.5 * (u[m]**2 + v[m]**2 + w[m]**2).sum()])
+    o.set_psi(psi)
+    ts, ss = [], []
+    for k in range(61):
+        q = o.particles()
+        uu, vv, ww = (q[a] - q[a].mean() for a in ("u", "v", "w"))
+        ts.append(k * p["dt"])
+        ss.append(np.mean(uu**2) - 0.5 * (np.mean(vv**2) + np.mean(ww**2)))
+        o.step(1)
+    rate = -np.polyfit(ts, np.log(ss), 1)[0]
+    assert rate * tau == pytest.approx(1.0, rel=0.04)
+
+
+@pytest.mark.parametrize("omega,T0", [(0.81, 1.0), (0.81, 2.0), (0.5, 1.0)])
+def test_vhs_equilibrium_collision_rate(oracle_mod, omega, T0):
+    # nu = n <sigma c_r> = (rho/rho_ref) <c_r>_ref / (sqrt2 lambda_ref) (T/T_ref)^{1-omega},
+    # <c_r>_ref = 4 sqrt(R T_ref / pi)
+    p = W.uniform(n_cells=4, Kn=1.0, ppc_ref=2000, state=(1, 0, 0, 0, T0), omega=omega)
+    o = oracle_mod.Oracle(p)
+    c = o.consts()
+    o.step(2)
+    tot, npart = 0, 0
+    for _ in range(40):
+        o.step(1)
+        tot += int(o.counters()["nacc"].sum())
+        npart += o.num_particles()
+    nu = 2 * tot / (npart * c["dt"])
+    nu_th = 4 * math.sqrt(1 / math.pi) / (math.sqrt(2) * c["lambda_ref"]) * T0 ** (1 - omega)
+    assert nu == pytest.approx(nu_th, rel=4.5 / math.sqrt(tot) + 0.005)
+
+
+def test_free_molecular_expansion_matches_erfc(oracle_mod):
+    nc, L = 100, 1.0
+    p = W.base(Kn=1e6, n_cells=nc, x_min=-L, x_max=L, left=(1, 0, 0, 0, 1), right=(0, 0, 0, 0, 1),
+               x_split=0.0, bc_left="specular", bc_right="vacuum", ppc_ref=2000, seed=3)
+    o = oracle_mod.Oracle(p)
+    c = o.consts()
+    n = 30
+    o.step(n)
+    assert o.counters()["ncand"].sum() == 0
+    s = math.sqrt(2.0) * n * c["dt"]
+    xf = np.linspace(-L, L, nc * 50 + 1)
+    xm = 0.5 * (xf[1:] + xf[:-1])
+    # gas initially on [-2L, 0] once the specular wall at -L is unfolded
+    ex = (0.5 * (erfc(xm / s) - erfc((xm + 2 * L) / s))).reshape(nc, 50).mean(1)
+    rho = o.prim()["rho"]
+    sig = np.sqrt(np.maximum(ex, 1e-12) * c["mp"] / c["dx"])
+    z = (rho - ex) / np.maximum(sig, 1e-9)
+    assert np.abs(z).max() < 5.0
+    assert np.mean(z**2) < 1.5
+
+
+def test_continuum_sod_converges_to_exact_riemann_solution(oracle_mod):
+    errs = []
+    for nc in (100, 400):
+        p = W.sod(n_cells=nc, Kn=1e-10, ppc_ref=200)
+        o = oracle_mod.Oracle(p)
+        c = o.consts()
+        nst = int(round(0.15 / c["dt"]))
+        o.step(nst)
+        pr = o.prim()
+        assert pr["P"].min() > 0.999          # the wave carries the flow
+        x = (np.arange(nc) + 0.5) / nc
+        ex = RE.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 5.0 / 3.0, (x - 0.5) / (nst * c["dt"]))
+        errs.append([np.mean(np.abs(pr["rho"] - ex[:, 0])), np.mean(np.abs(pr["u"] - ex[:, 1])),
+                     np.mean(np.abs(pr["rho"] * pr["T"] - ex[:, 2]))])
+    e100, e400 = np.array(errs)
+    assert np.all(e100 < [0.02, 0.035, 0.018])
+    assert np.all(e400 < 0.6 * e100)
+
+
+def test_shock_far_field_and_constant_mass_flux(oracle_mod):
+    p = W.config1()
+    o = oracle_mod.Oracle(p)
+    o.step(400)
+    a, na = o.avg()
+    assert na == 300
+    rho = a[:, 0] / na
+    mass_flux = a[:, 1] / na
+    r, _, t = W.rankine_hugoniot(3.0)
+    u1 = 3.0 * math.sqrt(5.0 / 3.0)
+    assert rho[:8].mean() == pytest.approx(1.0, rel=0.02)
+    assert rho[-8:].mean() == pytest.approx(r, rel=0.03)
+    assert mass_flux.mean() == pytest.approx(u1, rel=0.03)
+    T = (a[:, 4] / na - 0.5 * a[:, 1]**2 / a[:, 0] / na) / (1.5 * rho)
+    assert T[:8].mean() == pytest.approx(1.0, rel=0.03)
+    assert T[-8:].mean() == pytest.approx(t, rel=0.05)
+    # DSMC regime (dt < tau everywhere): the wave neither absorbs nor carries flux
+    assert np.all(o.last_flux() == 0.0)
+    assert o.counters()["nabs"].sum() == 0
+
+
+@pytest.mark.parametrize("Kn,bc", [(2e-4, "periodic"), (1.0, "periodic"), (3e-4, "specular")])
+def test_closed_box_conserves_totals(oracle_mod, Kn, bc):
+    p = W.uniform(n_cells=30, Kn=Kn, ppc_ref=300, state=(1.0, 0.3, 0.1, 0.0, 1.0), bc=bc, x_max=1.0,
+                  dt=2e-3)
+    if bc == "specular":
+        p["left"], p["right"] = (1.0, 0.0, 0.1, 0.0, 1.0), (0.4, 0.0, 0.0, -0.2, 0.7)
+    o = oracle_mod.Oracle(p)
+    tot0 = o.psi().sum(0)
+    o.step(60)
+    tot = o.psi().sum(0)
+    scale = np.abs(tot0).max()
+    keep = [0, 2, 3, 4] if bc == "specular" else [0, 1, 2, 3, 4]
+    assert np.allclose(tot[keep], tot0[keep], rtol=0, atol=1e-12 * scale)
+
+
+def test_wave_particle_split_fixed_point(oracle_mod):
+    # expected particle fraction f of a uniform gas with split fraction P:
+    # f' = (1-P) f + (1-P)(1 - (1-P) f)  =>  f* = (1-P) / (1 - P + P^2)
+    p = W.uniform(n_cells=10, Kn=2e-4, ppc_ref=4000, state=(1.0, 0.0, 0.0, 0.0, 1.0), dt=2e-3, x_max=1.0)
+    o = oracle_mod.Oracle(p)
+    c = o.consts()
+    o.step(5)
+    P = o.prim()["P"].mean()
+    fs = []
+    for _ in range(10):
+        o.step(1)
+        fs.append(o.num_particles() * c["mp"] / c["dx"] / o.psi()[:, 0].sum())
+    fstar = (1 - P) / (1 - P + P * P)
+    n = 10 * 4000
+    assert np.mean(fs) == pytest.approx(fstar, abs=6 * math.sqrt(fstar / n) + 2e-3)
