@@ -1,0 +1,268 @@
+/*
+ * duwp.h -- C ABI of the GB300 (sm_103a) library for the per-time-step hot path of the
+ * direct unified wave-particle (DUWP) method (Cao, Liu, Yang, Zhong, arXiv 2305.12071).
+ *
+ * One time step of one instance (Sec. 3.4, "Algorithm of DUWP", Steps 1-4):
+ *   - total state Psi_t = Psi_w + Psi_p per cell (Step 1);
+ *   - P of the particles of a cell absorbed into the wave, P from Eq. (p); (1-P) of the
+ *     wave re-sampled as Maxwellian particles at the total state, Eq. (maxsample);
+ *     NTC pair selection with VHS collisions on the particle part (Step 2, Appendix A);
+ *   - free transport x += xi dt with boundary handling, the particle flux of Eq. (fp),
+ *     an NS wave flux with the viscosity correction eps of Eq. (vp1), and the
+ *     conservative update of Eq. (r1) (Step 3).
+ * The problem is posed as in Sec. 4: gas and VHS constants, mesh, Knudsen number,
+ * time step and boundary states.
+ *
+ * Conventions for every function below:
+ *   - return value: DUWP_OK (0) or a negative DUWP_E* status; DUWP_PENDING (1) only
+ *     from duwp_poll;
+ *   - pointers named host_* or documented as host buffers are caller-owned host memory;
+ *     the library owns all device memory it allocates (through the caller's allocator
+ *     callbacks when given, cudaMallocAsync on the handle's stream otherwise);
+ *   - a handle is not thread-safe; a server is safe for concurrent submit/poll;
+ *   - work is enqueued on the CUDA stream given at creation; functions documented as
+ *     "synchronizing" wait for that stream and report any error recorded on the device
+ *     (a cell or buffer overflow inside a step) as their status.  After a failed step
+ *     the handle may only be destroyed.
+ */
+#ifndef DUWP_H
+#define DUWP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+    DUWP_OK = 0,
+    DUWP_EINVAL = -1,     /* invalid argument or problem description */
+    DUWP_ENOMEM = -2,     /* an allocation failed (host or device) */
+    DUWP_ECUDA = -3,      /* a CUDA call failed; see duwp_last_cuda_error() */
+    DUWP_ENUMERIC = -4,   /* non-finite or non-physical state uploaded or produced */
+    DUWP_ETIMEOUT = -5,   /* a bounded device wait ran out */
+    DUWP_EBUSY = -6,      /* server: request cannot be admitted now / queue full */
+    DUWP_EOVERFLOW = -7,  /* a cell, the particle buffers or the far-mover list overflowed */
+    DUWP_ENOTFOUND = -8,  /* server: unknown request id */
+    DUWP_PENDING = 1      /* server: request not finished yet */
+};
+
+/* ------------------------------------------------------------------ problem description */
+/* A macroscopic state (density, velocity components, temperature). */
+typedef struct { double rho, u, v, w, T; } duwp_state;
+
+enum {
+    DUWP_BC_INOUT = 0,     /* reservoir at the fixed boundary state: particles leaving are removed,
+                              inflow particles are sampled each step from the boundary state */
+    DUWP_BC_SPECULAR = 1,  /* specular wall: x and the normal velocity are mirrored */
+    DUWP_BC_PERIODIC = 2,  /* periodic (both ends must be periodic) */
+    DUWP_BC_VACUUM = 3     /* outflow into vacuum: particles leaving are removed, nothing enters */
+};
+enum { DUWP_FP64 = 0, DUWP_FP32 = 1 };                       /* particle record precision */
+enum { DUWP_EPS1 = 0, DUWP_EPS12 = 1, DUWP_EPS0 = 2, DUWP_EPS_AVG = 3 }; /* Sec. 3.3 */
+enum { DUWP_FLUX_GKS_EQ = 0, DUWP_FLUX_KFVS = 1 };           /* wave-flux form */
+enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the NTC count */
+
+/*
+ * Problem parameters of one instance (Sec. 4 and Appendix A; units nondimensional):
+ *   gamma, Pr, R        gas constants (5/3, 2/3, 1 for argon);
+ *   omega, alpha        VHS viscosity index and the alpha of beta in Eq. (lambda);
+ *   rho_ref, T_ref      reference state; Kn * L_ref is the reference mean free path,
+ *                       which fixes mu_ref through Eq. (lambda) (first form);
+ *   x_min, x_max, n_cells   uniform 1D mesh;
+ *   dt                  time step; if dt <= 0 it is cfl * dx / max(|u| + 3 sqrt(2 R T)) over
+ *                       the two initial states;
+ *   left, right, x_split   initial states left/right of x_split (cell centres decide);
+ *                       they are also the reservoir states of DUWP_BC_INOUT ends;
+ *   bc_left, bc_right   boundary kinds (DUWP_BC_*);
+ *   ppc_ref             simulated particles per cell at rho_ref: m_p = rho_ref dx / ppc_ref;
+ *   precision           DUWP_FP64 or DUWP_FP32 particle records (all cell quantities are FP64);
+ *   eps_mode, flux_mode, ntc_rate   options (DUWP_EPS*, DUWP_FLUX_*, DUWP_NTC_*);
+ *   seed                key of the counter-based generator of this instance;
+ *   capacity            particle slots per buffer (0: automatic);
+ *   cell_capacity       most particles one cell may hold within a step (0: automatic);
+ *   avg_start           time averages accumulate the states after step avg_start.
+ * In a batch all instances must use the same precision.
+ */
+typedef struct {
+    double gamma, Pr, R;
+    double omega, alpha;
+    double rho_ref, T_ref, Kn, L_ref;
+    double x_min, x_max;
+    int32_t n_cells;
+    double dt, cfl;
+    duwp_state left, right;
+    double x_split;
+    int32_t bc_left, bc_right;
+    double ppc_ref;
+    int32_t precision, eps_mode, flux_mode, ntc_rate;
+    uint64_t seed;
+    uint64_t capacity;
+    int32_t cell_capacity;
+    int32_t avg_start;
+} duwp_params;
+
+/* Device allocator callbacks: alloc returns device memory of `bytes` bytes usable on `stream`
+ * (NULL on failure); free releases it.  `ctx` is passed through unchanged. */
+typedef void *(*duwp_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*duwp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct duwp_handle duwp_handle;
+
+/* Derived constants of one instance (Sec. 4.1 Eq. lambda, Appendix A). */
+typedef struct {
+    double dx, dt, mp, beta, lambda_ref, mu_ref, c_ref;
+    int64_t capacity;        /* particle slots per buffer of the whole handle */
+    int32_t cell_capacity;   /* particles one cell may hold within a step */
+    int32_t n_instances;
+    int64_t steps_done;      /* steps taken by this instance */
+} duwp_info;
+
+/* ------------------------------------------------------------------ single instance and batch */
+
+/* Create one DUWP instance on the CUDA `stream` (cudaStream_t, NULL = legacy default).
+ * The initial state is all wave: Psi_t from the two-state profile and no particles; the
+ * first step samples the particle part (Step 1 of Sec. 3.4).  Allocates through
+ * alloc/free_fn when both are non-NULL.  Errors: DUWP_EINVAL (bad parameters), DUWP_ENOMEM,
+ * DUWP_ECUDA.  On success *out owns the device state until duwp_destroy. */
+int duwp_init(const duwp_params *params, void *stream, duwp_alloc_fn alloc, duwp_free_fn free_fn,
+              void *alloc_ctx, duwp_handle **out);
+
+/* Create `n` independent instances stepped together by one set of launches over a flattened
+ * cell index (batched form; instances never exchange data).  params[i] describes instance i;
+ * all share one precision.  Same errors and ownership as duwp_init. */
+int duwp_init_batch(const duwp_params *params, int32_t n, void *stream, duwp_alloc_fn alloc,
+                    duwp_free_fn free_fn, void *alloc_ctx, duwp_handle **out);
+
+/* Advance every instance of the handle by n_steps >= 0 DUWP steps (Steps 1-4 of Sec. 3.4).
+ * Asynchronous on the handle's stream: device-side overflows are reported by the next
+ * synchronizing call.  Errors: DUWP_EINVAL, DUWP_ECUDA. */
+int duwp_step(duwp_handle *h, int32_t n_steps);
+
+/* Synchronizing: wait for the handle's stream; returns the device error status. */
+int duwp_sync(duwp_handle *h);
+
+enum { DUWP_INSTANT = 0, DUWP_AVERAGED = 1 };
+
+/* Synchronizing.  Macroscopic profile of instance `inst` into caller-owned HOST arrays of
+ * n = n_cells doubles: density, x-velocity and temperature of the total state Psi_t
+ * (which = DUWP_INSTANT) or of its time average (DUWP_AVERAGED, over the states after step
+ * avg_start), and the wave fraction rho_w / rho_t of the current state (Fig. 5f).  Any of the
+ * output pointers may be NULL.  Errors: DUWP_EINVAL (inst or n), device errors. */
+int duwp_moments(duwp_handle *h, int32_t inst, int32_t which, double *host_rho, double *host_u,
+                 double *host_T, double *host_wave_frac, int32_t n);
+
+/* Synchronizing.  Conservative total state Psi_t = (rho, rho U, rho V, rho W, rho E) per cell of
+ * instance `inst` (which = DUWP_INSTANT) or its time average (DUWP_AVERAGED) into a caller-owned
+ * host array of n_cells * 5 doubles, cell-major.  *host_navg (may be NULL) receives the number of
+ * averaged states. */
+int duwp_fields(duwp_handle *h, int32_t inst, int32_t which, double *host_psi, int32_t n_cells,
+                int64_t *host_navg);
+
+/* Derived constants and sizes of instance `inst` (not synchronizing except steps_done). */
+int duwp_get_info(duwp_handle *h, int32_t inst, duwp_info *out);
+
+/* Release every device allocation of the handle (after waiting for its stream). */
+int duwp_destroy(duwp_handle *h);
+
+/* Static description of a status code. */
+const char *duwp_error_string(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread (static storage). */
+const char *duwp_last_cuda_error(void);
+
+/* ------------------------------------------------------------------ launch configuration */
+
+/* Launch shape of the particle kernel: threads per cell block (multiple of 32, 32..1024) and the
+ * shared-memory capacity in particles per cell (0 keeps the current one).  Used by the
+ * autotuner; results do not depend on it.  Errors: DUWP_EINVAL when the capacity is below the
+ * automatic minimum or over the shared-memory limit. */
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity);
+
+/* Capture the per-step launches in CUDA graphs (on = 1, default) or launch them one by one
+ * (on = 0, the plain loop). */
+int duwp_use_graphs(duwp_handle *h, int32_t on);
+
+/* ------------------------------------------------------------------ inspection (tests, checkpoints) */
+
+/* Synchronizing.  Number of particles of instance `inst` (all cells). */
+int duwp_num_particles(duwp_handle *h, int32_t inst, int64_t *out);
+
+/* Synchronizing.  Particles of instance `inst` in the stable per-cell order the method defines
+ * (sorted by cell; within a cell by their order before the last transport), into caller-owned
+ * host arrays of n entries (n = duwp_num_particles): cell index, cell-local position in [0,1),
+ * velocity.  Errors: DUWP_EINVAL if n differs. */
+int duwp_get_particles(duwp_handle *h, int32_t inst, int32_t *host_cell, double *host_xl,
+                       double *host_u, double *host_v, double *host_w, int64_t n);
+
+/* Synchronizing.  Per-cell counters of the last step of instance `inst` (host arrays of n_cells
+ * int32, any may be NULL): NTC candidates, accepted collisions, absorbed particles, re-sampled
+ * particles. */
+int duwp_get_counters(duwp_handle *h, int32_t inst, int32_t *host_ncand, int32_t *host_nacc,
+                      int32_t *host_nabs, int32_t *host_nnew, int32_t n_cells);
+
+/* Synchronizing.  Per-cell NTC majorant c_r,max of instance `inst` (host, n_cells doubles). */
+int duwp_get_cmax(duwp_handle *h, int32_t inst, double *host_cmax, int32_t n_cells);
+
+/* Checkpoint of the whole handle.  duwp_checkpoint_size gives the byte count; save copies the
+ * complete device state into a caller-owned host buffer (synchronizing); restore loads such a
+ * buffer into a handle created with identical parameters.  The generator is counter-based, so a
+ * restored run continues bit-identically.  Errors: DUWP_EINVAL on size or layout mismatch. */
+int duwp_checkpoint_size(duwp_handle *h, uint64_t *bytes);
+int duwp_checkpoint_save(duwp_handle *h, void *host_buf, uint64_t bytes);
+int duwp_checkpoint_restore(duwp_handle *h, const void *host_buf, uint64_t bytes);
+
+/* ------------------------------------------------------------------ serving (continuous batching) */
+
+typedef struct duwp_server duwp_server;
+
+/* hbm_budget_bytes: device memory the server may use for resident instances; max_slots: most
+ * instances resident at once; steps_per_launch: steps taken by all resident instances between
+ * admissions; precision: record precision of every request; stream: CUDA stream of the worker. */
+typedef struct {
+    uint64_t hbm_budget_bytes;
+    int32_t max_slots;
+    int32_t max_cells;
+    int32_t steps_per_launch;
+    int32_t precision;
+    void *stream;
+} duwp_server_cfg;
+
+/* Result of one request.  The arrays are owned by the server and stay valid until the request
+ * is released by a second duwp_poll of the same id after completion, or the server is destroyed. */
+typedef struct {
+    int32_t status;            /* DUWP_OK or the error that ended the request */
+    int32_t n_cells;
+    int64_t steps;
+    int64_t particle_updates;  /* particles streamed, summed over the request's steps */
+    double queue_ms;           /* submit -> admission */
+    double run_ms;             /* admission -> completion */
+    double step_p50_ms, step_p99_ms;  /* per-launch device time, per step */
+    const double *rho, *u, *T; /* final instantaneous profile (n_cells each) */
+} duwp_result;
+
+/* Create a server with its own worker thread (continuous batching: requests are admitted when
+ * a slot and enough of the HBM budget are free, are stepped together with every resident
+ * request, and leave as soon as their own step count is reached). */
+int duwp_server_create(const duwp_server_cfg *cfg, duwp_alloc_fn alloc, duwp_free_fn free_fn,
+                       void *alloc_ctx, duwp_server **out);
+
+/* Non-blocking: queue a request of n_steps steps; *req_id identifies it.  Errors: DUWP_EINVAL
+ * (bad parameters, precision mismatch, larger than the whole budget). */
+int duwp_submit(duwp_server *s, const duwp_params *params, int32_t n_steps, uint64_t *req_id);
+
+/* Non-blocking: DUWP_PENDING while queued or running; DUWP_OK with *out filled once finished
+ * (the request's own error is in out->status).  Polling a finished id a second time releases it
+ * (returns DUWP_ENOTFOUND afterwards). */
+int duwp_poll(duwp_server *s, uint64_t req_id, duwp_result *out);
+
+/* Stop the worker, drop queued requests and release all memory. */
+int duwp_server_destroy(duwp_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUWP_H */

@@ -533,7 +533,8 @@ void ora_destroy(void *vh)
 
 /* Free transport of one particle over dt in cell units, with the boundary conditions.
  * Returns the new cell in [0,C) or -1 if the particle left the domain.  The particle
- * position is cell-local, xl in [0,1). */
+ * position is cell-local, xl in [0,1).  Specular walls mirror the position (x -> 1 - x in
+ * the mirrored cell) and the normal velocity, once per wall met. */
 static int64_t transport(const ora_inst *h, int64_t cell, opart *q)
 {
     const ora_params *p = &h->p;
@@ -542,6 +543,7 @@ static int64_t transport(const ora_inst *h, int64_t cell, opart *q)
     double xl;
     if (p->fp32) {
         float s = fmaf((float)q->u, h->c.dtdx_f, (float)q->xl);
+        if (!(fabsf(s) < 1e15f)) return -1;   /* non-finite or absurd displacement: removed */
         float fk = floorf(s);
         float x = s - fk;
         k = (int64_t)fk;
@@ -549,6 +551,7 @@ static int64_t transport(const ora_inst *h, int64_t cell, opart *q)
         xl = (double)x;
     } else {
         double s = fma(q->u, h->c.dtdx, q->xl);
+        if (!(fabs(s) < 1e15)) return -1;
         double fk = floor(s);
         double x = s - fk;
         k = (int64_t)fk;
@@ -556,7 +559,9 @@ static int64_t transport(const ora_inst *h, int64_t cell, opart *q)
         xl = x;
     }
     int64_t dest = cell + k;
-    for (;;) {
+    /* reading: a particle needing more than 64 wall reflections in one step is removed */
+    for (int it = 0;; ++it) {
+        if (it == 64) return -1;
         if (dest < 0) {
             if (p->bc_left == ORA_BC_SPECULAR) {
                 dest = -dest - 1;

@@ -1,0 +1,735 @@
+// duwp_api.cu -- host side of the DUWP library: problem validation and derived constants
+// (Sec. 4.1 Eq. lambda, Appendix A), the engine (one HBM pool of cells and particle buffers
+// stepped by one set of launches per step, captured in CUDA graphs), inspection, checkpoints,
+// and the C ABI declared in include/duwp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "duwp_engine.h"
+#include "duwp_launch.h"
+
+namespace duwp {
+
+static thread_local std::string g_last_cuda;
+
+void set_cuda_error(cudaError_t e, const char *where)
+{
+    g_last_cuda = std::string(where) + ": " + cudaGetErrorString(e);
+}
+
+#define DUWP_CU(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) {                        \
+            set_cuda_error(e_, #call);                  \
+            return DUWP_ECUDA;                          \
+        }                                               \
+    } while (0)
+
+static bool finite_state(const duwp_state &s) { return std::isfinite(s.rho) && std::isfinite(s.u) && std::isfinite(s.v) && std::isfinite(s.w) && std::isfinite(s.T); }
+
+static void cons_of(const duwp_state &s, double R, double *c)
+{
+    c[0] = s.rho;
+    c[1] = s.rho * s.u;
+    c[2] = s.rho * s.v;
+    c[3] = s.rho * s.w;
+    c[4] = 0.5 * s.rho * (s.u * s.u + s.v * s.v + s.w * s.w) + 1.5 * s.rho * R * s.T;
+}
+
+int derive_instance(const duwp_params &p, HostInst &o)
+{
+    if (p.n_cells < 1 || p.n_cells > (1 << 26)) return DUWP_EINVAL;
+    if (!(p.x_max > p.x_min) || !(p.ppc_ref > 0.0) || !(p.Kn > 0.0) || !(p.L_ref > 0.0)) return DUWP_EINVAL;
+    if (!(p.R > 0.0) || !(p.Pr > 0.0) || !(p.rho_ref > 0.0) || !(p.T_ref > 0.0) || !(p.alpha > 0.0)) return DUWP_EINVAL;
+    if (!(p.omega >= 0.5 && p.omega <= 1.0)) return DUWP_EINVAL;
+    if (!finite_state(p.left) || !finite_state(p.right)) return DUWP_EINVAL;
+    if (p.left.rho < 0.0 || p.right.rho < 0.0 || !(p.left.T > 0.0) || !(p.right.T > 0.0)) return DUWP_EINVAL;
+    for (int32_t bc : {p.bc_left, p.bc_right})
+        if (bc < 0 || bc > 3) return DUWP_EINVAL;
+    if ((p.bc_left == DUWP_BC_PERIODIC) != (p.bc_right == DUWP_BC_PERIODIC)) return DUWP_EINVAL;
+    if (p.precision != DUWP_FP64 && p.precision != DUWP_FP32) return DUWP_EINVAL;
+    if (p.eps_mode < 0 || p.eps_mode > 3 || p.flux_mode < 0 || p.flux_mode > 1 || p.ntc_rate < 0 || p.ntc_rate > 1)
+        return DUWP_EINVAL;
+    if (!(p.dt > 0.0) && !(p.cfl > 0.0)) return DUWP_EINVAL;
+
+    o.p = p;
+    InstDev &d = o.d;
+    std::memset(&d, 0, sizeof d);
+    d.C = p.n_cells;
+    d.bc_left = p.bc_left;
+    d.bc_right = p.bc_right;
+    d.eps_mode = p.eps_mode;
+    d.flux_mode = p.flux_mode;
+    d.ntc_rate = p.ntc_rate;
+    d.active = 1;
+    d.key0 = static_cast<uint32_t>(p.seed & 0xffffffffu);
+    d.key1 = static_cast<uint32_t>(p.seed >> 32);
+    d.step = 0;
+    d.avg_start = p.avg_start;
+    d.navg = 0;
+    d.dx = (p.x_max - p.x_min) / static_cast<double>(p.n_cells);
+    // Eq. (lambda), first form, solved for the viscosity at the reference state
+    o.beta = 5.0 * (p.alpha + 1.0) * (p.alpha + 2.0) / (4.0 * p.alpha * (5.0 - 2.0 * p.omega) * (7.0 - 2.0 * p.omega));
+    o.lambda_ref = p.Kn * p.L_ref;
+    const double p_ref = p.rho_ref * p.R * p.T_ref;
+    d.mu_ref = o.beta * o.lambda_ref * p_ref * std::sqrt(2.0 * kPi / (p.R * p.T_ref));
+    d.mp = p.rho_ref * d.dx / p.ppc_ref;
+    d.dx_over_mp = d.dx / d.mp;
+    d.mp_over_dx = d.mp / d.dx;
+    if (p.dt > 0.0) {
+        d.dt = p.dt;
+    } else {
+        const double sl = std::fabs(p.left.u) + 3.0 * std::sqrt(2.0 * p.R * p.left.T);
+        const double sr = std::fabs(p.right.u) + 3.0 * std::sqrt(2.0 * p.R * p.right.T);
+        d.dt = p.cfl * d.dx / std::max(sl, sr);
+    }
+    if (!(d.dt > 0.0) || !std::isfinite(d.dt)) return DUWP_EINVAL;
+    d.dtdx = d.dt / d.dx;
+    d.dtdx_f = static_cast<float>(d.dtdx);
+    d.R = p.R;
+    d.Pr = p.Pr;
+    d.omega = p.omega;
+    d.T_ref = p.T_ref;
+    d.rho_ref = p.rho_ref;
+    d.upsilon = p.omega - 0.5;
+    // reference relative speed of the VHS cross-section: sqrt(2kT_ref/m_r) / Gamma(2.5-omega)^{0.5/upsilon},
+    // 2kT_ref/m_r = 4 R T_ref for equal masses (Appendix A)
+    if (d.upsilon == 0.0) d.c_ref = std::sqrt(4.0 * p.R * p.T_ref);
+    else d.c_ref = std::sqrt(4.0 * p.R * p.T_ref) / std::pow(std::tgamma(2.5 - p.omega), 0.5 / d.upsilon);
+    d.ntc_A = d.dt / (2.0 * std::sqrt(2.0) * o.lambda_ref);
+    const duwp_state *st[2] = {&p.left, &p.right};
+    for (int s = 0; s < 2; ++s) {
+        double *q = s ? d.right : d.left;
+        q[0] = st[s]->rho; q[1] = st[s]->u; q[2] = st[s]->v; q[3] = st[s]->w; q[4] = st[s]->T;
+    }
+    // particles expected from the initial mass
+    double mass = 0.0;
+    for (int32_t i = 0; i < p.n_cells; ++i) {
+        const double xc = p.x_min + (static_cast<double>(i) + 0.5) * d.dx;
+        mass += (xc < p.x_split ? p.left.rho : p.right.rho) * d.dx;
+    }
+    o.est_particles = static_cast<int64_t>(std::ceil(mass / d.mp));
+    o.active = true;
+    return DUWP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Engine
+// ------------------------------------------------------------------------------------------
+void *Engine::dalloc(size_t bytes)
+{
+    if (alloc && free_fn) return alloc(bytes, stream, alloc_ctx);
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaMallocAsync");
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Engine::dfree(void *p, size_t bytes)
+{
+    if (!p) return;
+    if (alloc && free_fn) free_fn(p, bytes, stream, alloc_ctx);
+    else cudaFreeAsync(p, stream);
+}
+
+void Engine::drop_graphs()
+{
+    for (auto &gx : graph) {
+        if (gx) cudaGraphExecDestroy(gx);
+        gx = nullptr;
+    }
+}
+
+Engine::~Engine()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    drop_graphs();
+    dfree(slab, slab_bytes);
+    if (stream) cudaStreamSynchronize(stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+namespace {
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count)
+    {
+        off = (off + 255) & ~static_cast<size_t>(255);
+        const size_t o = off;
+        off += count * sizeof(T);
+        return o;
+    }
+};
+}  // namespace
+
+int Engine::configure_launch(int threads_, int cell_cap_)
+{
+    if (threads_ < 32 || threads_ > 512 || (threads_ & 31)) return DUWP_EINVAL;
+    if (cell_cap_ < 64 || cell_cap_ > max_cell_capacity(fp32)) return DUWP_EINVAL;
+    const size_t sm = particles_smem_bytes(fp32, cell_cap_);
+    const int occ = particles_occupancy(fp32, threads_, sm);
+    if (occ <= 0) return DUWP_EINVAL;
+    int nsm = 0;
+    DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    threads = threads_;
+    cell_cap = cell_cap_;
+    dev.cell_cap = cell_cap_;
+    smem = sm;
+    grid = std::max(1, std::min(occ * nsm, G));
+    drop_graphs();
+    return DUWP_OK;
+}
+
+int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t cap_override,
+                   void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx)
+{
+    alloc = a;
+    free_fn = f;
+    alloc_ctx = ctx;
+    DUWP_CU(cudaGetDevice(&device));
+    if (stream_in) {
+        stream = static_cast<cudaStream_t>(stream_in);
+    } else {
+        DUWP_CU(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+        own_stream = true;
+    }
+    std::vector<HostInst> hs(static_cast<size_t>(n));
+    int64_t est = 0;
+    int64_t cells = 0;
+    double max_ppc = 0.0;
+    for (int32_t b = 0; b < n; ++b) {
+        const int rc = derive_instance(params[b], hs[b]);
+        if (rc != DUWP_OK) return rc;
+        if (params[b].precision != params[0].precision) return DUWP_EINVAL;
+        est += hs[b].est_particles;
+        cells += params[b].n_cells + 2;
+        const double rmax = std::max(params[b].left.rho, params[b].right.rho) / params[b].rho_ref;
+        max_ppc = std::max(max_ppc, rmax * params[b].ppc_ref);
+    }
+    fp32 = (n > 0 && params[0].precision == DUWP_FP32) ? 1 : 0;
+    if (pool_cells > 0) cells = std::max<int64_t>(cells, pool_cells);
+    if (cells > (int64_t(1) << 30)) return DUWP_EINVAL;
+    G = static_cast<int32_t>(cells);
+    max_inst = std::max<int32_t>(n, pool_slots);
+    if (max_inst < 1) return DUWP_EINVAL;
+    // particle slots: the slot bound of a cell is at most twice its mass in particles (plus 2),
+    // so twice the expected particles covers the re-sampling regimes
+    int64_t cap = 2 * est + 4 * static_cast<int64_t>(G) + 4096;
+    uint64_t cap_user = 0;
+    for (int32_t b = 0; b < n; ++b) cap_user = std::max<uint64_t>(cap_user, params[b].capacity);
+    if (cap_override > 0) cap = cap_override;
+    else if (cap_user > 0) cap = static_cast<int64_t>(cap_user);
+    if (cap >= (int64_t(1) << 40)) return DUWP_EINVAL;
+    capacity = cap;
+    int32_t cc = 0;
+    for (int32_t b = 0; b < n; ++b) cc = std::max(cc, params[b].cell_capacity);
+    if (cc <= 0) cc = static_cast<int32_t>(std::ceil(2.5 * max_ppc)) + 64;
+    cc = std::max(cc, 256);
+    cc = std::min(cc, max_cell_capacity(fp32));
+    far_cap = 1 << 16;
+
+    const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
+    const size_t far_item = fp32 ? sizeof(FarItem<RecF>) : sizeof(FarItem<RecD>);
+    const int32_t nblocks = (G + kCellBlock - 1) / kCellBlock;
+    Carver c;
+    const size_t o_inst = c.take<InstDev>(max_inst);
+    const size_t o_cinst = c.take<int32_t>(G);
+    const size_t o_psi = c.take<double>(5 * size_t(G));
+    const size_t o_prim = c.take<double>(5 * size_t(G));
+    const size_t o_valid = c.take<int32_t>(G);
+    const size_t o_P = c.take<double>(G);
+    const size_t o_cmax = c.take<double>(G);
+    const size_t o_flux = c.take<double>(5 * size_t(G));
+    const size_t o_avg = c.take<double>(5 * size_t(G));
+    const size_t o_AL = c.take<double>(4 * size_t(G));
+    const size_t o_AR = c.take<double>(4 * size_t(G));
+    const size_t o_As = c.take<double>(5 * size_t(G));
+    const size_t o_slots = c.take<int32_t>(G);
+    const size_t o_cnt = c.take<int32_t>(G);
+    size_t o_nL[2], o_nS[2], o_nR[2], o_off[2];
+    for (int p = 0; p < 2; ++p) {
+        o_nL[p] = c.take<int32_t>(G);
+        o_nS[p] = c.take<int32_t>(G);
+        o_nR[p] = c.take<int32_t>(G);
+        o_off[p] = c.take<int64_t>(G);
+    }
+    const size_t o_bs = c.take<int64_t>(nblocks);
+    const size_t o_nnew = c.take<int32_t>(G), o_nabs = c.take<int32_t>(G), o_ncand = c.take<int32_t>(G),
+                 o_nacc = c.take<int32_t>(G);
+    const size_t o_fc = c.take<int32_t>(4);
+    const size_t o_err = c.take<int32_t>(4);
+    const size_t o_ticket = c.take<int32_t>(4);
+    const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
+    const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
+    const size_t o_buf0 = c.take<unsigned char>(rec * size_t(capacity));
+    const size_t o_buf1 = c.take<unsigned char>(rec * size_t(capacity));
+    slab_bytes = (c.off + 255) & ~static_cast<size_t>(255);
+    slab = dalloc(slab_bytes);
+    if (!slab) return DUWP_ENOMEM;
+    unsigned char *base = static_cast<unsigned char *>(slab);
+    // zero everything except the particle buffers, then mark all cells unused
+    DUWP_CU(cudaMemsetAsync(base, 0, o_buf0, stream));
+    dev.G = G;
+    dev.n_inst = max_inst;
+    dev.capacity = capacity;
+    dev.cell_cap = cc;
+    dev.far_cap = far_cap;
+    dev.inst = reinterpret_cast<InstDev *>(base + o_inst);
+    dev.cell_inst = reinterpret_cast<int32_t *>(base + o_cinst);
+    dev.psi = reinterpret_cast<double *>(base + o_psi);
+    dev.prim = reinterpret_cast<double *>(base + o_prim);
+    dev.valid = reinterpret_cast<int32_t *>(base + o_valid);
+    dev.P = reinterpret_cast<double *>(base + o_P);
+    dev.cmax = reinterpret_cast<double *>(base + o_cmax);
+    dev.flux = reinterpret_cast<double *>(base + o_flux);
+    dev.avg = reinterpret_cast<double *>(base + o_avg);
+    dev.AL = reinterpret_cast<double *>(base + o_AL);
+    dev.AR = reinterpret_cast<double *>(base + o_AR);
+    dev.Aself = reinterpret_cast<double *>(base + o_As);
+    dev.slots = reinterpret_cast<int32_t *>(base + o_slots);
+    dev.cnt = reinterpret_cast<int32_t *>(base + o_cnt);
+    for (int p = 0; p < 2; ++p) {
+        dev.nL[p] = reinterpret_cast<int32_t *>(base + o_nL[p]);
+        dev.nS[p] = reinterpret_cast<int32_t *>(base + o_nS[p]);
+        dev.nR[p] = reinterpret_cast<int32_t *>(base + o_nR[p]);
+        dev.off[p] = reinterpret_cast<int64_t *>(base + o_off[p]);
+    }
+    dev.blocksum = reinterpret_cast<int64_t *>(base + o_bs);
+    dev.nnew = reinterpret_cast<int32_t *>(base + o_nnew);
+    dev.nabs = reinterpret_cast<int32_t *>(base + o_nabs);
+    dev.ncand = reinterpret_cast<int32_t *>(base + o_ncand);
+    dev.nacc = reinterpret_cast<int32_t *>(base + o_nacc);
+    dev.far_count = reinterpret_cast<int32_t *>(base + o_fc);
+    dev.err = reinterpret_cast<int32_t *>(base + o_err);
+    dev.ticket = reinterpret_cast<int32_t *>(base + o_ticket);
+    dev.far_app = base + o_fa;
+    dev.far_sorted = base + o_fs;
+    dev.buf[0] = base + o_buf0;
+    dev.buf[1] = base + o_buf1;
+    DUWP_CU(cudaMemsetAsync(dev.cell_inst, 0xff, sizeof(int32_t) * size_t(G), stream));
+
+    int rc = configure_launch(threads, cc);
+    if (rc != DUWP_OK) return rc;
+
+    inst.assign(static_cast<size_t>(max_inst), HostInst{});
+    for (auto &h : inst) h.active = false;
+    int32_t gb = 0;
+    for (int32_t b = 0; b < n; ++b) {
+        rc = add_instance(b, params[b], gb);
+        if (rc != DUWP_OK) return rc;
+        gb += params[b].n_cells + 2;
+    }
+    rc = enqueue_prepare();
+    if (rc != DUWP_OK) return rc;
+    return sync();
+}
+
+int Engine::add_instance(int slot, const duwp_params &p, int32_t cell_base)
+{
+    if (slot < 0 || slot >= max_inst) return DUWP_EINVAL;
+    HostInst h;
+    int rc = derive_instance(p, h);
+    if (rc != DUWP_OK) return rc;
+    if ((p.precision == DUWP_FP32) != (fp32 == 1)) return DUWP_EINVAL;
+    if (cell_base < 0 || int64_t(cell_base) + p.n_cells + 2 > G) return DUWP_EINVAL;
+    h.cell_base = cell_base;
+    h.d.cell_base = cell_base;
+    inst[slot] = h;
+    DUWP_CU(cudaMemcpyAsync(dev.inst + slot, &inst[slot].d, sizeof(InstDev), cudaMemcpyHostToDevice, stream));
+    double lc[5], rc5[5];
+    cons_of(p.left, p.R, lc);
+    cons_of(p.right, p.R, rc5);
+    DUWP_CU(launch_init_cells(dev, slot, cell_base, p.n_cells + 2, lc, rc5, p.x_min, p.x_split, stream));
+    return DUWP_OK;
+}
+
+int Engine::remove_instance(int slot)
+{
+    if (slot < 0 || slot >= max_inst || !inst[slot].active) return DUWP_EINVAL;
+    const HostInst &h = inst[slot];
+    DUWP_CU(cudaMemsetAsync(dev.cell_inst + h.cell_base, 0xff, sizeof(int32_t) * size_t(h.p.n_cells + 2), stream));
+    DUWP_CU(cudaMemsetAsync(dev.slots + h.cell_base, 0, sizeof(int32_t) * size_t(h.p.n_cells + 2), stream));
+    inst[slot].active = false;
+    return DUWP_OK;
+}
+
+int Engine::enqueue_prepare()
+{
+    DUWP_CU(launch_cells(dev, fp32, 0, 0, stream));
+    DUWP_CU(launch_offsets_flux(dev, 1 - parity, 0, stream));
+    return DUWP_OK;
+}
+
+int Engine::enqueue_step()
+{
+    const int rp = parity;
+    DUWP_CU(launch_particles(dev, fp32, rp, grid, threads, smem, stream));
+    DUWP_CU(launch_far_sort(dev, fp32, stream));
+    DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
+    DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+    parity = 1 - rp;
+    return DUWP_OK;
+}
+
+int Engine::step(int32_t n)
+{
+    if (n < 0) return DUWP_EINVAL;
+    int32_t left = n;
+    if (use_graphs) {
+        while (left >= 2) {
+            cudaGraphExec_t &gx = graph[parity];
+            if (!gx) {
+                cudaGraph_t gr = nullptr;
+                DUWP_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+                const int p0 = parity;
+                int rc = enqueue_step();
+                if (rc == DUWP_OK) rc = enqueue_step();
+                cudaError_t e = cudaStreamEndCapture(stream, &gr);
+                parity = p0;
+                if (rc != DUWP_OK) return rc;
+                if (e != cudaSuccess) { set_cuda_error(e, "cudaStreamEndCapture"); return DUWP_ECUDA; }
+                e = cudaGraphInstantiate(&gx, gr, 0);
+                cudaGraphDestroy(gr);
+                if (e != cudaSuccess) { set_cuda_error(e, "cudaGraphInstantiate"); gx = nullptr; return DUWP_ECUDA; }
+            }
+            DUWP_CU(cudaGraphLaunch(gx, stream));
+            left -= 2;
+            steps_done += 2;
+        }
+    }
+    while (left > 0) {
+        const int rc = enqueue_step();
+        if (rc != DUWP_OK) return rc;
+        --left;
+        ++steps_done;
+    }
+    return DUWP_OK;
+}
+
+int Engine::sync()
+{
+    DUWP_CU(cudaStreamSynchronize(stream));
+    int32_t e = 0;
+    DUWP_CU(cudaMemcpy(&e, dev.err, sizeof e, cudaMemcpyDeviceToHost));
+    return e;
+}
+
+int Engine::read_inst(int b, InstDev &out)
+{
+    DUWP_CU(cudaMemcpyAsync(&out, dev.inst + b, sizeof(InstDev), cudaMemcpyDeviceToHost, stream));
+    DUWP_CU(cudaStreamSynchronize(stream));
+    return DUWP_OK;
+}
+
+}  // namespace duwp
+
+using namespace duwp;
+
+struct duwp_handle {
+    Engine eng;
+};
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *duwp_error_string(int s)
+{
+    switch (s) {
+    case DUWP_OK: return "ok";
+    case DUWP_EINVAL: return "invalid argument or problem description";
+    case DUWP_ENOMEM: return "allocation failed";
+    case DUWP_ECUDA: return "CUDA error";
+    case DUWP_ENUMERIC: return "non-finite or non-physical state";
+    case DUWP_ETIMEOUT: return "bounded device wait ran out";
+    case DUWP_EBUSY: return "busy: cannot admit now";
+    case DUWP_EOVERFLOW: return "cell, particle-buffer or far-mover overflow";
+    case DUWP_ENOTFOUND: return "unknown request id";
+    case DUWP_PENDING: return "pending";
+    default: return "unknown status";
+    }
+}
+
+const char *duwp_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+int duwp_init_batch(const duwp_params *params, int32_t n, void *stream, duwp_alloc_fn alloc, duwp_free_fn free_fn,
+                    void *alloc_ctx, duwp_handle **out)
+{
+    if (!params || n < 1 || !out) return DUWP_EINVAL;
+    *out = nullptr;
+    duwp_handle *h = new (std::nothrow) duwp_handle;
+    if (!h) return DUWP_ENOMEM;
+    const int rc = h->eng.create(params, n, 0, 0, 0, stream, alloc, free_fn, alloc_ctx);
+    if (rc != DUWP_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DUWP_OK;
+}
+
+int duwp_init(const duwp_params *params, void *stream, duwp_alloc_fn alloc, duwp_free_fn free_fn, void *alloc_ctx,
+              duwp_handle **out)
+{
+    return duwp_init_batch(params, 1, stream, alloc, free_fn, alloc_ctx, out);
+}
+
+int duwp_step(duwp_handle *h, int32_t n_steps)
+{
+    if (!h) return DUWP_EINVAL;
+    return h->eng.step(n_steps);
+}
+
+int duwp_sync(duwp_handle *h)
+{
+    if (!h) return DUWP_EINVAL;
+    return h->eng.sync();
+}
+
+int duwp_destroy(duwp_handle *h)
+{
+    if (!h) return DUWP_EINVAL;
+    delete h;
+    return DUWP_OK;
+}
+
+static int check_inst(duwp_handle *h, int32_t b)
+{
+    if (!h || b < 0 || b >= h->eng.max_inst || !h->eng.inst[b].active) return DUWP_EINVAL;
+    return DUWP_OK;
+}
+
+int duwp_fields(duwp_handle *h, int32_t b, int32_t which, double *host_psi, int32_t n, int64_t *host_navg)
+{
+    int rc = check_inst(h, b);
+    if (rc) return rc;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    if (n != hi.p.n_cells || !host_psi || (which != DUWP_INSTANT && which != DUWP_AVERAGED)) return DUWP_EINVAL;
+    rc = E.sync();
+    if (rc) return rc;
+    const double *src = (which == DUWP_INSTANT ? E.dev.psi : E.dev.avg) + 5 * size_t(hi.cell_base + 1);
+    DUWP_CU(cudaMemcpy(host_psi, src, sizeof(double) * 5 * size_t(n), cudaMemcpyDeviceToHost));
+    InstDev d;
+    rc = E.read_inst(b, d);
+    if (rc) return rc;
+    if (host_navg) *host_navg = d.navg;
+    return DUWP_OK;
+}
+
+int duwp_moments(duwp_handle *h, int32_t b, int32_t which, double *rho, double *u, double *T, double *wave_frac,
+                 int32_t n)
+{
+    int rc = check_inst(h, b);
+    if (rc) return rc;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    if (n != hi.p.n_cells) return DUWP_EINVAL;
+    std::vector<double> psi(5 * static_cast<size_t>(n));
+    int64_t navg = 0;
+    rc = duwp_fields(h, b, which, psi.data(), n, &navg);
+    if (rc) return rc;
+    std::vector<int32_t> cnt(static_cast<size_t>(n), 0);
+    DUWP_CU(cudaMemcpy(cnt.data(), E.dev.cnt + hi.cell_base + 1, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost));
+    std::vector<double> cur(5 * static_cast<size_t>(n));
+    if (wave_frac) DUWP_CU(cudaMemcpy(cur.data(), E.dev.psi + 5 * size_t(hi.cell_base + 1), sizeof(double) * 5 * size_t(n), cudaMemcpyDeviceToHost));
+    const double scale = (which == DUWP_AVERAGED) ? (navg > 0 ? 1.0 / static_cast<double>(navg) : 0.0) : 1.0;
+    for (int32_t i = 0; i < n; ++i) {
+        const double *c = psi.data() + 5 * size_t(i);
+        const double r = c[0] * scale;
+        const double mx = c[1] * scale, my = c[2] * scale, mz = c[3] * scale, E5 = c[4] * scale;
+        const double ux = r > 0 ? mx / r : 0.0, uy = r > 0 ? my / r : 0.0, uz = r > 0 ? mz / r : 0.0;
+        const double tt = r > 0 ? (E5 / r - 0.5 * (ux * ux + uy * uy + uz * uz)) / (1.5 * hi.p.R) : 0.0;
+        if (rho) rho[i] = r;
+        if (u) u[i] = ux;
+        if (T) T[i] = tt;
+        if (wave_frac) {
+            const double rt = cur[5 * size_t(i)];
+            wave_frac[i] = rt > 0 ? (rt - static_cast<double>(cnt[i]) * hi.d.mp_over_dx) / rt : 0.0;
+        }
+    }
+    return DUWP_OK;
+}
+
+int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
+{
+    int rc = check_inst(h, b);
+    if (rc || !out) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    out->dx = hi.d.dx;
+    out->dt = hi.d.dt;
+    out->mp = hi.d.mp;
+    out->beta = hi.beta;
+    out->lambda_ref = hi.lambda_ref;
+    out->mu_ref = hi.d.mu_ref;
+    out->c_ref = hi.d.c_ref;
+    out->capacity = E.capacity;
+    out->cell_capacity = E.cell_cap;
+    int ni = 0;
+    for (const auto &x : E.inst) ni += x.active ? 1 : 0;
+    out->n_instances = ni;
+    InstDev d;
+    rc = E.read_inst(b, d);
+    if (rc) return rc;
+    out->steps_done = d.step;
+    return DUWP_OK;
+}
+
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity)
+{
+    if (!h) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    const int cc = cell_capacity > 0 ? cell_capacity : E.cell_cap;
+    const int rc = E.sync();
+    if (rc) return rc;
+    return E.configure_launch(threads, cc);
+}
+
+int duwp_use_graphs(duwp_handle *h, int32_t on)
+{
+    if (!h) return DUWP_EINVAL;
+    h->eng.use_graphs = on != 0;
+    return DUWP_OK;
+}
+
+int duwp_num_particles(duwp_handle *h, int32_t b, int64_t *out)
+{
+    int rc = check_inst(h, b);
+    if (rc || !out) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    rc = E.sync();
+    if (rc) return rc;
+    const HostInst &hi = E.inst[b];
+    std::vector<int32_t> cnt(static_cast<size_t>(hi.p.n_cells));
+    DUWP_CU(cudaMemcpy(cnt.data(), E.dev.cnt + hi.cell_base + 1, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+    int64_t s = 0;
+    for (int32_t c : cnt) s += c;
+    *out = s;
+    return DUWP_OK;
+}
+
+int duwp_get_particles(duwp_handle *h, int32_t b, int32_t *cell, double *xl, double *u, double *v, double *w, int64_t n)
+{
+    int64_t np = 0;
+    int rc = duwp_num_particles(h, b, &np);
+    if (rc) return rc;
+    if (n != np || !cell || !xl || !u || !v || !w) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    const int32_t C = hi.p.n_cells;
+    std::vector<int32_t> cnt(static_cast<size_t>(C));
+    DUWP_CU(cudaMemcpy(cnt.data(), E.dev.cnt + hi.cell_base + 1, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> start(static_cast<size_t>(C));
+    int64_t s = 0;
+    for (int32_t i = 0; i < C; ++i) { start[i] = s; s += cnt[i]; }
+    const size_t nb = std::max<int64_t>(np, 1);
+    const size_t bytes = sizeof(int64_t) * size_t(C) + nb * (sizeof(int32_t) + 4 * sizeof(double)) + 1024;
+    unsigned char *tmp = static_cast<unsigned char *>(E.dalloc(bytes));
+    if (!tmp) return DUWP_ENOMEM;
+    int64_t *d_start = reinterpret_cast<int64_t *>(tmp);
+    double *d_xl = reinterpret_cast<double *>(tmp + ((sizeof(int64_t) * size_t(C) + 255) & ~size_t(255)));
+    double *d_u = d_xl + nb, *d_v = d_u + nb, *d_w = d_v + nb;
+    int32_t *d_cell = reinterpret_cast<int32_t *>(d_w + nb);
+    cudaError_t e = cudaMemcpyAsync(d_start, start.data(), sizeof(int64_t) * size_t(C), cudaMemcpyHostToDevice, E.stream);
+    if (e == cudaSuccess) e = launch_gather(E.dev, E.fp32, E.parity, b, hi.cell_base + 1, C, d_start, np, d_cell, d_xl, d_u, d_v, d_w, E.stream);
+    if (e == cudaSuccess && np > 0) {
+        e = cudaMemcpyAsync(cell, d_cell, sizeof(int32_t) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(xl, d_xl, sizeof(double) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, d_u, sizeof(double) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(v, d_v, sizeof(double) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w, d_w, sizeof(double) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    E.dfree(tmp, bytes);
+    if (e != cudaSuccess) { set_cuda_error(e, "duwp_get_particles"); return DUWP_ECUDA; }
+    return E.sync();
+}
+
+int duwp_get_counters(duwp_handle *h, int32_t b, int32_t *ncand, int32_t *nacc, int32_t *nabs, int32_t *nnew, int32_t n)
+{
+    int rc = check_inst(h, b);
+    if (rc) return rc;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    if (n != hi.p.n_cells) return DUWP_EINVAL;
+    rc = E.sync();
+    if (rc) return rc;
+    const size_t o = size_t(hi.cell_base + 1), by = sizeof(int32_t) * size_t(n);
+    if (ncand) DUWP_CU(cudaMemcpy(ncand, E.dev.ncand + o, by, cudaMemcpyDeviceToHost));
+    if (nacc) DUWP_CU(cudaMemcpy(nacc, E.dev.nacc + o, by, cudaMemcpyDeviceToHost));
+    if (nabs) DUWP_CU(cudaMemcpy(nabs, E.dev.nabs + o, by, cudaMemcpyDeviceToHost));
+    if (nnew) DUWP_CU(cudaMemcpy(nnew, E.dev.nnew + o, by, cudaMemcpyDeviceToHost));
+    return DUWP_OK;
+}
+
+int duwp_get_cmax(duwp_handle *h, int32_t b, double *cmax, int32_t n)
+{
+    int rc = check_inst(h, b);
+    if (rc) return rc;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    if (n != hi.p.n_cells || !cmax) return DUWP_EINVAL;
+    rc = E.sync();
+    if (rc) return rc;
+    DUWP_CU(cudaMemcpy(cmax, E.dev.cmax + hi.cell_base + 1, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost));
+    return DUWP_OK;
+}
+
+struct CkptHeader {
+    uint64_t magic, slab_bytes, capacity;
+    int32_t G, max_inst, fp32, parity;
+    int64_t steps_done;
+};
+static const uint64_t kCkptMagic = 0x4455575043503031ull;
+
+int duwp_checkpoint_size(duwp_handle *h, uint64_t *bytes)
+{
+    if (!h || !bytes) return DUWP_EINVAL;
+    *bytes = sizeof(CkptHeader) + h->eng.slab_bytes;
+    return DUWP_OK;
+}
+
+int duwp_checkpoint_save(duwp_handle *h, void *buf, uint64_t bytes)
+{
+    if (!h || !buf) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    if (bytes != sizeof(CkptHeader) + E.slab_bytes) return DUWP_EINVAL;
+    const int rc = E.sync();
+    if (rc) return rc;
+    CkptHeader hd{kCkptMagic, E.slab_bytes, static_cast<uint64_t>(E.capacity), E.G, E.max_inst, E.fp32, E.parity, E.steps_done};
+    std::memcpy(buf, &hd, sizeof hd);
+    DUWP_CU(cudaMemcpy(static_cast<unsigned char *>(buf) + sizeof hd, E.slab, E.slab_bytes, cudaMemcpyDeviceToHost));
+    return DUWP_OK;
+}
+
+int duwp_checkpoint_restore(duwp_handle *h, const void *buf, uint64_t bytes)
+{
+    if (!h || !buf) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    if (bytes != sizeof(CkptHeader) + E.slab_bytes) return DUWP_EINVAL;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kCkptMagic || hd.slab_bytes != E.slab_bytes || hd.G != E.G || hd.max_inst != E.max_inst ||
+        hd.fp32 != E.fp32 || hd.capacity != static_cast<uint64_t>(E.capacity))
+        return DUWP_EINVAL;
+    DUWP_CU(cudaStreamSynchronize(E.stream));
+    DUWP_CU(cudaMemcpy(E.slab, static_cast<const unsigned char *>(buf) + sizeof hd, E.slab_bytes, cudaMemcpyHostToDevice));
+    E.parity = hd.parity;
+    E.steps_done = hd.steps_done;
+    return E.sync();
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// duwp_engine.h -- host-side engine: one pool of flattened cells and two particle buffers in
+// HBM shared by the resident DUWP instances, stepped by one set of launches per step.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "duwp.h"
+#include "duwp_internal.cuh"
+
+namespace duwp {
+
+void set_cuda_error(cudaError_t e, const char *where);
+
+struct HostInst {
+    duwp_params p;
+    InstDev d;          // constants as uploaded (step counters live on the device)
+    int32_t cell_base;  // flattened index of the left reservoir cell
+    double beta, lambda_ref;
+    int64_t est_particles;
+    bool active;
+};
+
+// Derive the constants of one instance (Sec. 4.1 Eq. lambda, Appendix A) and validate the
+// description.  Returns DUWP_OK or DUWP_EINVAL.
+int derive_instance(const duwp_params &p, HostInst &out);
+
+struct Engine {
+    int device = 0;
+    int fp32 = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    duwp_alloc_fn alloc = nullptr;
+    duwp_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
+
+    // sizes
+    int32_t G = 0;              // flattened cells
+    int32_t max_inst = 0;
+    int64_t capacity = 0;       // particle slots per buffer
+    int32_t cell_cap = 0;
+    int32_t far_cap = 0;
+    int32_t threads = 128;
+    int32_t grid = 0;
+    size_t smem = 0;
+
+    // device memory: one slab
+    void *slab = nullptr;
+    size_t slab_bytes = 0;
+    EngineDev dev{};
+    std::vector<HostInst> inst;
+
+    // stepping
+    int parity = 0;             // parity of the buffer holding the arrived lists of the next step
+    int64_t steps_done = 0;
+    bool use_graphs = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // two steps starting at parity 0 / 1
+
+    ~Engine();
+    int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
+               void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);
+    int configure_launch(int threads_, int cell_cap_);
+    int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
+    int remove_instance(int slot);
+    int enqueue_step();                // launches of one step on the stream
+    int enqueue_prepare();             // cell + offset kernels of the initial state
+    int step(int32_t n);
+    int sync();                        // wait + read the device error word
+    int read_inst(int b, InstDev &out);
+    void *dalloc(size_t bytes);
+    void dfree(void *p, size_t bytes);
+    void drop_graphs();
+};
+
+}  // namespace duwp

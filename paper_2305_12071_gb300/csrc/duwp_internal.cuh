@@ -1,0 +1,286 @@
+// duwp_internal.cuh -- device data layout and per-particle / per-cell arithmetic of the DUWP step
+// (Cao, Liu, Yang, Zhong, arXiv 2305.12071, Sec. 3.4 and Appendix A) for sm_103a.
+//
+// Layout in HBM (one engine = a pool of G flattened cells shared by all resident instances):
+//   instance b owns cells [cell_base, cell_base + C + 2): left reservoir (ghost), cells 0..C-1,
+//   right reservoir.  Particles are 16-byte (FP32: xl, u, v, w) or 32-byte (FP64) records in two
+//   buffers used alternately.  After a step every cell s owns one output block in the write
+//   buffer, holding its particles that moved one cell left (L), stayed (S), and moved one cell
+//   right (R), each run in the order the particles had before transport.  The stable sorted list
+//   of a cell g for the next step is then  [far movers from cells < g-1] R(g-1) S(g) L(g+1)
+//   [far movers from cells > g+1]  -- exactly the stable counting-sort order by new cell, without
+//   a global sort pass.  Particles that moved two or more cells (or wrapped around a periodic
+//   domain) go to a small list sorted separately.
+//
+// Every decision-bearing operation (transport, index picks, acceptance, counts) follows one fixed
+// operation order, and the library is compiled with -fmad=false; fused multiply-adds appear only
+// where written explicitly.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace duwp {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.283185307179586;
+
+// Device error codes (mirrors of the public status values).
+constexpr int kErrOverflow = -7;
+constexpr int kErrTimeout = -5;
+
+enum Purpose : uint32_t { kAbsorb = 1, kRound = 2, kSample = 3, kCollide = 4 };
+
+struct alignas(16) RecF { float xl, u, v, w; };
+struct alignas(16) RecD { double xl, u, v, w; };
+
+// Per-instance constants and state kept on the device.
+struct InstDev {
+    int32_t C;              // interior cells
+    int32_t cell_base;      // flattened index of the left reservoir cell
+    int32_t bc_left, bc_right;
+    int32_t eps_mode, flux_mode, ntc_rate, active;
+    uint32_t key0, key1;    // generator key (seed)
+    uint32_t step;          // steps completed (advanced once per step, after the cell update)
+    int32_t avg_start;
+    int64_t navg;           // states accumulated into the time average
+    double dx, dt, dtdx, mp, dx_over_mp, mp_over_dx;
+    double R, Pr, omega, T_ref, rho_ref, mu_ref, upsilon, c_ref, ntc_A;
+    float dtdx_f;
+    float pad0;
+    double left[5], right[5];   // reservoir primitive states (rho, u, v, w, T)
+};
+
+// Sorted list entry of a particle that moved two or more cells (or wrapped): new cell, source
+// cell and its position in the source cell's list before transport (the stable-order key).
+template <typename Rec>
+struct FarItem {
+    int32_t dest, src, q, pad;
+    Rec rec;
+};
+
+// Pointers of one engine, passed by value to every kernel.
+struct EngineDev {
+    int32_t G;                 // flattened cells in the pool
+    int32_t n_inst;
+    int64_t capacity;          // particle slots per buffer
+    int32_t cell_cap;          // particles one cell may hold within a step (shared memory)
+    int32_t far_cap;
+    InstDev *inst;
+    int32_t *cell_inst;        // instance of each flattened cell, -1 = unused
+    double *psi;               // G x 5 total state Psi_t (reservoirs: unused)
+    double *prim;              // G x 5 primitive state (rho, u, v, w, T)
+    int32_t *valid;            // G: primitive state usable (rho > 0, T > 0)
+    double *P;                 // G: absorption fraction, Eq. (p)
+    double *cmax;              // G: NTC majorant
+    double *flux;              // G x 5: wave flux at the interface between g and g+1
+    double *avg;               // G x 5: time-average accumulator of Psi_t
+    double *AL, *AR;           // G x 4: sums (u, v, w, |xi|^2/2) of the L / R runs (post-transport)
+    double *Aself;             // G x 5: change of the cell's own particle moments (leavers, reflections)
+    int32_t *slots;            // G: upper bound of the cell's list after re-sampling (this step)
+    int32_t *cnt;              // G: particles arriving in the cell (list length this step)
+    int32_t *nL[2], *nS[2], *nR[2];
+    int64_t *off[2];           // G: first slot of each cell's output block, per buffer
+    int64_t *blocksum;         // per 256-cell block sums of slots
+    int32_t *nnew, *nabs, *ncand, *nacc;
+    void *buf[2];
+    void *far_app;             // far movers appended during a step (unsorted)
+    void *far_sorted;          // the same, sorted by (dest, src, q)
+    int32_t *far_count;        // [0]: appended, [1]: sorted
+    int32_t *err;              // first device error
+    int32_t *ticket;           // work counter of the particle kernel
+};
+
+constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels
+
+// ------------------------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round multiplies words 0
+// and 2 by the two round constants (full 64-bit products), swaps the halves across the lanes with
+// the key XORed in, and the key is bumped by the Weyl increments after each round.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                                         uint32_t c3, uint32_t out[4])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Counter layout: (id, sub, step, purpose); id = local cell index + 1 (reservoirs 0 and C+1).
+__device__ __forceinline__ void draw(const InstDev &I, uint32_t id, uint32_t sub, uint32_t step, uint32_t purpose,
+                                     uint32_t w[4])
+{
+    philox10(I.key0, I.key1, id, sub, step, purpose, w);
+}
+
+// Uniform in [0,1) with 53 random bits: 32 from the first word, 21 from the second.
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
+{
+    const uint64_t m = (static_cast<uint64_t>(a) << 21) ^ static_cast<uint64_t>(b >> 11);
+    return static_cast<double>(m) * 0x1p-53;
+}
+
+// Index in [0, n) from a 32-bit word: the high half of the 64-bit product.
+__device__ __forceinline__ uint32_t idx32(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+
+// ------------------------------------------------------------------------------------------
+// Cell-level quantities (FP64)
+// ------------------------------------------------------------------------------------------
+
+// Primitive state from the conservative one (rho, rho U, rho V, rho W, rho E); monatomic gas:
+// rho E = rho |U|^2 / 2 + 3/2 rho R T.  Returns whether the state is usable.
+__device__ inline bool prim_from_cons(const double *psi, double R, double *q)
+{
+    const double rho = psi[0];
+    q[0] = rho;
+    q[1] = q[2] = q[3] = q[4] = 0.0;
+    if (!(rho > 0.0)) return false;
+    const double u = psi[1] / rho, v = psi[2] / rho, w = psi[3] / rho;
+    const double e = psi[4] / rho - 0.5 * (u * u + v * v + w * w);
+    const double T = e / (1.5 * R);
+    q[1] = u; q[2] = v; q[3] = w; q[4] = T;
+    return (T > 0.0) && isfinite(T) && isfinite(u) && isfinite(v) && isfinite(w);
+}
+
+__device__ inline double viscosity(const InstDev &I, double T) { return I.mu_ref * pow(T / I.T_ref, I.omega); }
+
+// Eq. (p): P = 0 if dt <= tau, else 1 - tau/dt, with tau = mu / p.
+__device__ inline double split_fraction(const InstDev &I, const double *q, bool ok)
+{
+    if (!ok) return 0.0;
+    const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
+    if (I.dt <= tau) return 0.0;
+    return 1.0 - tau / I.dt;
+}
+
+// Number of particles drawn from the wave: stochastic rounding of (1-P) max(rho_w,0) dx / m_p.
+__device__ inline int64_t resample_count(const InstDev &I, uint32_t id, uint32_t step, double P, double rho_w)
+{
+    uint32_t w[4];
+    draw(I, id, 0u, step, kRound, w);
+    const double x = ((1.0 - P) * fmax(rho_w, 0.0)) * I.dx_over_mp;
+    return static_cast<int64_t>(floor(x + u53(w[0], w[1])));
+}
+
+// Reservoir (ghost) primitive state beyond the left (side 0) or right (side 1) end.
+__device__ inline bool ghost_prim(const InstDev &I, int side, const double *inner, bool inner_ok, double *q)
+{
+    const int bc = side ? I.bc_right : I.bc_left;
+    if (bc == 0) {  // inflow/outflow reservoir at the boundary state
+        const double *s = side ? I.right : I.left;
+        for (int k = 0; k < 5; ++k) q[k] = s[k];
+        return s[0] > 0.0 && s[4] > 0.0;
+    }
+    if (bc == 1) {  // specular wall: mirror state
+        for (int k = 0; k < 5; ++k) q[k] = inner[k];
+        q[1] = -inner[1];
+        return inner_ok;
+    }
+    for (int k = 0; k < 5; ++k) q[k] = 0.0;   // vacuum (periodic is handled by the caller)
+    return false;
+}
+
+// Viscosity correction of the NS flux as a function of x = dt/tau (Sec. 3.3):
+// eps1 = 1 - x/(e^x - 1) (Eq. vp1), eps12 = x/(2+x), eps0 = 1, time-averaged eps (Eq. vp).
+__device__ inline double eps_factor(int mode, double x)
+{
+    if (mode == 2) return 1.0;
+    if (mode == 1) return x / (2.0 + x);
+    if (mode == 3) {
+        const double a = -expm1(-x), b = 1.0 + exp(-x);
+        return (-2.0 * a + x * b) / (x - a);
+    }
+    return 1.0 - x / expm1(x);
+}
+
+// <u^n> of a unit-density Maxwellian over u > 0 (pos) and u < 0 (neg), n = 0..3, lam = 1/(2RT).
+__device__ inline void half_moments(double U, double lam, double *pos, double *neg)
+{
+    const double s = sqrt(lam);
+    pos[0] = 0.5 * erfc(-s * U);
+    neg[0] = 0.5 * erfc(s * U);
+    const double tail = 0.5 * exp(-lam * U * U) / sqrt(kPi * lam);
+    pos[1] = U * pos[0] + tail;
+    neg[1] = U * neg[0] - tail;
+    const double h = 1.0 / (2.0 * lam);
+    pos[2] = U * pos[1] + h * pos[0];
+    neg[2] = U * neg[1] + h * neg[0];
+    pos[3] = U * pos[2] + 2.0 * h * pos[1];
+    neg[3] = U * neg[2] + 2.0 * h * neg[1];
+}
+
+// Wave flux through the interface between a left state a and a right state b (per unit area):
+// interface equilibrium from the colliding half-Maxwellians, Euler flux of it (or the split
+// kinetic flux), NS stress and heat flux with mu_e = eps mu(T0), weighted by
+// P_f = max(0, 1 - tau_f/dt) (Sec. 3.3, Eq. ce2 at t = dt; Step 3).
+__device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, const double *b, bool bok,
+                                 double *F)
+{
+    for (int k = 0; k < 5; ++k) F[k] = 0.0;
+    double ap[4] = {0, 0, 0, 0}, an[4] = {0, 0, 0, 0}, bp[4] = {0, 0, 0, 0}, bn[4] = {0, 0, 0, 0};
+    double la = 0.0, lb = 0.0, ra = 0.0, rb = 0.0, ta = 0.0, tb = 0.0;
+    if (aok) {
+        la = 1.0 / (2.0 * I.R * a[4]);
+        half_moments(a[1], la, ap, an);
+        ra = a[0];
+        ta = a[2] * a[2] + a[3] * a[3] + 1.0 / la;
+    }
+    if (bok) {
+        lb = 1.0 / (2.0 * I.R * b[4]);
+        half_moments(b[1], lb, bp, bn);
+        rb = b[0];
+        tb = b[2] * b[2] + b[3] * b[3] + 1.0 / lb;
+    }
+    const double av = aok ? a[2] : 0.0, aw = aok ? a[3] : 0.0;
+    const double bv = bok ? b[2] : 0.0, bw = bok ? b[3] : 0.0;
+    const double rho0 = ra * ap[0] + rb * bn[0];
+    const double mx0 = ra * ap[1] + rb * bn[1];
+    const double my0 = ra * av * ap[0] + rb * bv * bn[0];
+    const double mz0 = ra * aw * ap[0] + rb * bw * bn[0];
+    const double E0 = 0.5 * (ra * (ap[2] + ta * ap[0]) + rb * (bn[2] + tb * bn[0]));
+    if (!(rho0 > 0.0)) return;
+    const double U0 = mx0 / rho0, V0 = my0 / rho0, W0 = mz0 / rho0;
+    const double T0 = (E0 / rho0 - 0.5 * (U0 * U0 + V0 * V0 + W0 * W0)) / (1.5 * I.R);
+    if (!(T0 > 0.0)) return;
+    const double p0 = rho0 * I.R * T0;
+    const double mu0 = viscosity(I, T0);
+    const double tauf = mu0 / p0;
+    if (I.dt <= tauf) return;
+    const double Pf = 1.0 - tauf / I.dt;
+    double G[5];
+    if (I.flux_mode == 1) {
+        G[0] = ra * ap[1] + rb * bn[1];
+        G[1] = ra * ap[2] + rb * bn[2];
+        G[2] = ra * av * ap[1] + rb * bv * bn[1];
+        G[3] = ra * aw * ap[1] + rb * bw * bn[1];
+        G[4] = 0.5 * (ra * (ap[3] + ta * ap[1]) + rb * (bn[3] + tb * bn[1]));
+    } else {
+        G[0] = mx0;
+        G[1] = mx0 * U0 + p0;
+        G[2] = mx0 * V0;
+        G[3] = mx0 * W0;
+        G[4] = U0 * (E0 + p0);
+    }
+    if (aok && bok) {
+        const double mue = eps_factor(I.eps_mode, I.dt / tauf) * mu0;
+        const double kap = 2.5 * I.R * mue / I.Pr;
+        const double inv = 1.0 / I.dx;
+        const double sxx = (4.0 / 3.0) * mue * ((b[1] - a[1]) * inv);
+        const double sxy = mue * ((b[2] - a[2]) * inv);
+        const double sxz = mue * ((b[3] - a[3]) * inv);
+        G[1] -= sxx;
+        G[2] -= sxy;
+        G[3] -= sxz;
+        G[4] -= U0 * sxx + V0 * sxy + W0 * sxz + kap * ((b[4] - a[4]) * inv);
+    }
+    for (int k = 0; k < 5; ++k) F[k] = Pf * G[k];
+}
+
+}  // namespace duwp

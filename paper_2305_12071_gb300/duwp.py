@@ -1,0 +1,370 @@
+"""Python binding of the DUWP CUDA library (libduwp.so, C ABI in include/duwp.h).
+
+Argument marshalling only: every step of the method runs in the library's kernels.  PyTorch
+provides device memory (the caching allocator is handed to the library as its allocator
+callbacks) and the CUDA stream.  There is no CPU fallback: without the compiled library or a
+CUDA device every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libduwp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EBUSY, EOVERFLOW, ENOTFOUND, PENDING = 0, -1, -2, -3, -4, -5, -6, -7, -8, 1
+INSTANT, AVERAGED = 0, 1
+BC = {"inout": 0, "specular": 1, "periodic": 2, "vacuum": 3}
+PRECISION = {"fp64": 0, "fp32": 1}
+EPS = {"eps1": 0, "eps12": 1, "eps0": 2, "eps_avg": 3}
+FLUX = {"gks_eq": 0, "kfvs": 1}
+NTC = {"particle": 0, "total": 1}
+
+# Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
+EXPORTS = (
+    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_moments", "duwp_fields", "duwp_get_info",
+    "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
+    "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
+    "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
+    "duwp_server_destroy",
+)
+
+
+class DuwpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {_error_string(status)} ({status})"
+        if status == ECUDA and _lib is not None:
+            msg += ": " + _lib.duwp_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class State(C.Structure):
+    _fields_ = [("rho", C.c_double), ("u", C.c_double), ("v", C.c_double), ("w", C.c_double), ("T", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double), ("Pr", C.c_double), ("R", C.c_double),
+        ("omega", C.c_double), ("alpha", C.c_double),
+        ("rho_ref", C.c_double), ("T_ref", C.c_double), ("Kn", C.c_double), ("L_ref", C.c_double),
+        ("x_min", C.c_double), ("x_max", C.c_double),
+        ("n_cells", C.c_int32),
+        ("dt", C.c_double), ("cfl", C.c_double),
+        ("left", State), ("right", State),
+        ("x_split", C.c_double),
+        ("bc_left", C.c_int32), ("bc_right", C.c_int32),
+        ("ppc_ref", C.c_double),
+        ("precision", C.c_int32), ("eps_mode", C.c_int32), ("flux_mode", C.c_int32), ("ntc_rate", C.c_int32),
+        ("seed", C.c_uint64),
+        ("capacity", C.c_uint64),
+        ("cell_capacity", C.c_int32),
+        ("avg_start", C.c_int32),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [("dx", C.c_double), ("dt", C.c_double), ("mp", C.c_double), ("beta", C.c_double),
+                ("lambda_ref", C.c_double), ("mu_ref", C.c_double), ("c_ref", C.c_double),
+                ("capacity", C.c_int64), ("cell_capacity", C.c_int32), ("n_instances", C.c_int32),
+                ("steps_done", C.c_int64)]
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("max_cells", C.c_int32),
+                ("steps_per_launch", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_cells", C.c_int32), ("steps", C.c_int64),
+                ("particle_updates", C.c_int64), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("step_p50_ms", C.c_double), ("step_p99_ms", C.c_double),
+                ("rho", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _error_string(status: int) -> str:
+    if _lib is None:
+        return "status"
+    return _lib.duwp_error_string(status).decode()
+
+
+def load(path: str = LIB_PATH):
+    """Load libduwp.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"DUWP CUDA library not built ({path}); run paper_2305_12071_gb300.build.build()")
+        L = C.CDLL(path)
+        i32, i64, u64, vp, dp = C.c_int32, C.c_int64, C.c_uint64, C.c_void_p, C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        L.duwp_error_string.restype = C.c_char_p
+        L.duwp_error_string.argtypes = [C.c_int]
+        L.duwp_last_cuda_error.restype = C.c_char_p
+        L.duwp_init.argtypes = [C.POINTER(Params), vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]
+        L.duwp_init_batch.argtypes = [C.POINTER(Params), i32, vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]
+        L.duwp_step.argtypes = [vp, i32]
+        L.duwp_sync.argtypes = [vp]
+        L.duwp_moments.argtypes = [vp, i32, i32, dp, dp, dp, dp, i32]
+        L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
+        L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
+        L.duwp_destroy.argtypes = [vp]
+        L.duwp_set_launch.argtypes = [vp, i32, i32]
+        L.duwp_use_graphs.argtypes = [vp, i32]
+        L.duwp_num_particles.argtypes = [vp, i32, C.POINTER(i64)]
+        L.duwp_get_particles.argtypes = [vp, i32, ip, dp, dp, dp, dp, i64]
+        L.duwp_get_counters.argtypes = [vp, i32, ip, ip, ip, ip, i32]
+        L.duwp_get_cmax.argtypes = [vp, i32, dp, i32]
+        L.duwp_checkpoint_size.argtypes = [vp, C.POINTER(u64)]
+        L.duwp_checkpoint_save.argtypes = [vp, vp, u64]
+        L.duwp_checkpoint_restore.argtypes = [vp, vp, u64]
+        L.duwp_server_create.argtypes = [C.POINTER(ServerCfg), ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]
+        L.duwp_submit.argtypes = [vp, C.POINTER(Params), i32, C.POINTER(u64)]
+        L.duwp_poll.argtypes = [vp, u64, C.POINTER(Result)]
+        L.duwp_server_destroy.argtypes = [vp]
+        _lib = L
+        return L
+
+
+def make_params(p: dict) -> Params:
+    """Marshal a problem dict (see paper_2305_12071_gb300.workloads) into duwp_params."""
+    s = Params()
+    s.gamma = p.get("gamma", 5.0 / 3.0)
+    s.Pr = p.get("Pr", 2.0 / 3.0)
+    s.R = p.get("R", 1.0)
+    s.omega = p["omega"]
+    s.alpha = p.get("alpha", 1.0)
+    s.rho_ref = p.get("rho_ref", 1.0)
+    s.T_ref = p.get("T_ref", 1.0)
+    s.Kn = p["Kn"]
+    s.L_ref = p.get("L_ref", 1.0)
+    s.x_min, s.x_max = p["x_min"], p["x_max"]
+    s.n_cells = int(p["n_cells"])
+    s.dt = p.get("dt", 0.0)
+    s.cfl = p.get("cfl", 0.5)
+    s.left = State(*p["left"])
+    s.right = State(*p["right"])
+    s.x_split = p.get("x_split", 0.5 * (p["x_min"] + p["x_max"]))
+    s.bc_left = BC[p.get("bc_left", "inout")]
+    s.bc_right = BC[p.get("bc_right", "inout")]
+    s.ppc_ref = p["ppc_ref"]
+    s.precision = PRECISION[p.get("precision", "fp64")]
+    s.eps_mode = EPS[p.get("eps_mode", "eps1")]
+    s.flux_mode = FLUX[p.get("flux_mode", "gks_eq")]
+    s.ntc_rate = NTC[p.get("ntc_rate", "particle")]
+    s.seed = int(p.get("seed", 1)) & 0xFFFFFFFFFFFFFFFF
+    s.capacity = int(p.get("capacity", 0))
+    s.cell_capacity = int(p.get("cell_capacity", 0))
+    s.avg_start = int(p.get("avg_start", 0))
+    return s
+
+
+class _TorchAllocator:
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, ctx):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        if ptr:
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _chk(rc: int, where: str):
+    if rc != OK:
+        raise DuwpError(rc, where)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class Solver:
+    """One handle of the library: a single instance or a batch stepped together.
+
+    params: a problem dict or a list of them (one precision for all).  The handle owns its own
+    CUDA stream (a torch stream) so its steps can be captured in CUDA graphs."""
+
+    def __init__(self, params, device: int = 0, torch_alloc: bool = True, graphs: bool = True):
+        import torch
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DUWP library needs a CUDA device")
+        plist = [params] if isinstance(params, dict) else list(params)
+        self.params = plist
+        self.n = len(plist)
+        torch.cuda.set_device(device)
+        self.stream = torch.cuda.Stream(device=device)
+        arr = (Params * self.n)(*[make_params(p) for p in plist])
+        self._alloc = _TorchAllocator(device) if torch_alloc else None
+        h = C.c_void_p()
+        a = self._alloc.alloc if self._alloc else ALLOC_FN()
+        f = self._alloc.free if self._alloc else FREE_FN()
+        _chk(L.duwp_init_batch(arr, self.n, C.c_void_p(self.stream.cuda_stream), a, f, None, C.byref(h)),
+             "duwp_init_batch")
+        self.h = h
+        self.L = L
+        if not graphs:
+            _chk(L.duwp_use_graphs(self.h, 0), "duwp_use_graphs")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.duwp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _chk(self.L.duwp_step(self.h, int(n)), "duwp_step")
+
+    def sync(self):
+        _chk(self.L.duwp_sync(self.h), "duwp_sync")
+
+    def use_graphs(self, on: bool):
+        _chk(self.L.duwp_use_graphs(self.h, 1 if on else 0), "duwp_use_graphs")
+
+    def set_launch(self, threads: int, cell_capacity: int = 0):
+        _chk(self.L.duwp_set_launch(self.h, int(threads), int(cell_capacity)), "duwp_set_launch")
+
+    def n_cells(self, inst: int = 0) -> int:
+        return int(self.params[inst]["n_cells"])
+
+    def info(self, inst: int = 0) -> dict:
+        o = Info()
+        _chk(self.L.duwp_get_info(self.h, inst, C.byref(o)), "duwp_get_info")
+        return {k: getattr(o, k) for k, _ in Info._fields_}
+
+    def fields(self, inst: int = 0, which: int = INSTANT):
+        n = self.n_cells(inst)
+        out = np.empty((n, 5), np.float64)
+        navg = C.c_int64()
+        _chk(self.L.duwp_fields(self.h, inst, which, _dptr(out), n, C.byref(navg)), "duwp_fields")
+        return out, int(navg.value)
+
+    def moments(self, inst: int = 0, which: int = INSTANT) -> dict:
+        n = self.n_cells(inst)
+        r, u, T, wf = (np.empty(n, np.float64) for _ in range(4))
+        _chk(self.L.duwp_moments(self.h, inst, which, _dptr(r), _dptr(u), _dptr(T), _dptr(wf), n), "duwp_moments")
+        return {"rho": r, "u": u, "T": T, "wave_frac": wf}
+
+    def num_particles(self, inst: int = 0) -> int:
+        o = C.c_int64()
+        _chk(self.L.duwp_num_particles(self.h, inst, C.byref(o)), "duwp_num_particles")
+        return int(o.value)
+
+    def particles(self, inst: int = 0) -> dict:
+        n = self.num_particles(inst)
+        cell = np.empty(n, np.int32)
+        xl, u, v, w = (np.empty(n, np.float64) for _ in range(4))
+        _chk(self.L.duwp_get_particles(self.h, inst, _iptr(cell), _dptr(xl), _dptr(u), _dptr(v), _dptr(w), n),
+             "duwp_get_particles")
+        return {"cell": cell, "xl": xl, "u": u, "v": v, "w": w}
+
+    def counters(self, inst: int = 0) -> dict:
+        n = self.n_cells(inst)
+        out = {k: np.empty(n, np.int32) for k in ("ncand", "nacc", "nabs", "nnew")}
+        _chk(self.L.duwp_get_counters(self.h, inst, *[_iptr(out[k]) for k in ("ncand", "nacc", "nabs", "nnew")], n),
+             "duwp_get_counters")
+        return out
+
+    def cmax(self, inst: int = 0) -> np.ndarray:
+        n = self.n_cells(inst)
+        out = np.empty(n, np.float64)
+        _chk(self.L.duwp_get_cmax(self.h, inst, _dptr(out), n), "duwp_get_cmax")
+        return out
+
+    def checkpoint(self) -> bytes:
+        nb = C.c_uint64()
+        _chk(self.L.duwp_checkpoint_size(self.h, C.byref(nb)), "duwp_checkpoint_size")
+        buf = (C.c_ubyte * nb.value)()
+        _chk(self.L.duwp_checkpoint_save(self.h, buf, nb.value), "duwp_checkpoint_save")
+        return bytes(buf)
+
+    def restore(self, blob: bytes):
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        _chk(self.L.duwp_checkpoint_restore(self.h, buf, len(blob)), "duwp_checkpoint_restore")
+
+
+class Server:
+    """Continuous-batching server (duwp_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, max_cells: int = 0, steps_per_launch: int = 10,
+                 precision: str = "fp32", device: int = 0, torch_alloc: bool = True):
+        import torch
+        L = load()
+        torch.cuda.set_device(device)
+        self.stream = torch.cuda.Stream(device=device)
+        cfg = ServerCfg(int(hbm_budget_bytes), int(max_slots), int(max_cells), int(steps_per_launch),
+                        PRECISION[precision], C.c_void_p(self.stream.cuda_stream))
+        self._alloc = _TorchAllocator(device) if torch_alloc else None
+        a = self._alloc.alloc if self._alloc else ALLOC_FN()
+        f = self._alloc.free if self._alloc else FREE_FN()
+        s = C.c_void_p()
+        _chk(L.duwp_server_create(C.byref(cfg), a, f, None, C.byref(s)), "duwp_server_create")
+        self.s = s
+        self.L = L
+
+    def submit(self, params: dict, n_steps: int) -> int:
+        rid = C.c_uint64()
+        p = make_params(params)
+        _chk(self.L.duwp_submit(self.s, C.byref(p), int(n_steps), C.byref(rid)), "duwp_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int):
+        """None while pending; a dict once finished (the request is released by this call's
+        successor, so the arrays are copied here)."""
+        r = Result()
+        rc = self.L.duwp_poll(self.s, C.c_uint64(rid), C.byref(r))
+        if rc == PENDING:
+            return None
+        _chk(rc, "duwp_poll")
+        n = r.n_cells
+        out = {"status": r.status, "n_cells": n, "steps": r.steps, "particle_updates": r.particle_updates,
+               "queue_ms": r.queue_ms, "run_ms": r.run_ms, "step_p50_ms": r.step_p50_ms,
+               "step_p99_ms": r.step_p99_ms}
+        for k in ("rho", "u", "T"):
+            ptr = getattr(r, k)
+            out[k] = np.ctypeslib.as_array(ptr, shape=(n,)).copy() if (n > 0 and ptr) else np.zeros(0)
+        self.L.duwp_poll(self.s, C.c_uint64(rid), C.byref(r))   # release
+        return out
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.L.duwp_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

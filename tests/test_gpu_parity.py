@@ -1,0 +1,148 @@
+"""Parity of the CUDA library with the FP64 oracle on the same seeded problems.
+
+FP64 particle records: cell indices, the stable per-cell order (the sort permutation) and the
+per-cell NTC candidate / accepted-pair, absorption and re-sampling counts bit-exact over 20
+steps; particle state and the total state Psi_t within 1e-9 relative (the two sides differ only
+in the rounding order of sums and in last-bit differences of library transcendentals).
+FP32 particle records: the oracle stores the particle state in single precision at the same
+points and takes the transport decision in single precision (one fused multiply-add), so the
+same decisions are taken; per-particle state within 1e-5 relative over 5 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_12071_gb300 import workloads as W
+from parity_util import compare_counters, compare_fields, compare_particles, solver
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-9
+REL32 = 1e-5
+
+
+def _run_pair(params, checkpoints, rel_p, rel_f, counters=True):
+    g = solver(params)
+    o = O.Oracle(params)
+    done = 0
+    for n in checkpoints:
+        g.step(n - done)
+        o.step(n - done)
+        done = n
+        what = f"step {n}"
+        compare_particles(g.particles(), o.particles(), rel_p, what)
+        compare_fields(g.fields()[0], o.psi(), rel_f, what)
+        if counters:
+            compare_counters(g.counters(), o.counters(), what)
+        assert np.allclose(g.cmax(), o.cmax(), rtol=1e-12, atol=0), what
+    g.close()
+
+
+def test_shock_mach3_fp64_20_steps():
+    _run_pair(W.config1("fp64"), [1, 2, 5, 20], REL64, REL64)
+
+
+def test_shock_mach3_fp32_5_steps():
+    _run_pair(W.config1("fp32"), [1, 2, 5], REL32, REL64)
+
+
+@pytest.mark.parametrize("Kn", [1e-4, 1e-3])
+def test_sod_wave_regime_fp64(Kn):
+    # P > 0: absorption, re-sampling and the NS wave flux are all active
+    p = W.sod(n_cells=120, Kn=Kn, ppc_ref=150, precision="fp64", seed=7)
+    _run_pair(p, [1, 3, 20], REL64, REL64)
+
+
+def test_sod_wave_regime_fp32():
+    p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision="fp32", seed=8)
+    _run_pair(p, [1, 5], REL32, REL64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_periodic_far_movers(precision):
+    # a time step of ~1.6 cells at the thermal speed: many particles move two or more cells,
+    # and the periodic wrap sends particles across the whole domain
+    p = W.uniform(n_cells=37, Kn=0.05, ppc_ref=80, state=(1.0, 0.7, 0.0, 0.0, 1.0), bc="periodic",
+                  x_max=1.0, dt=0.02, precision=precision, seed=11)
+    o = O.Oracle(p)
+    o.step(2)
+    assert o.last_nfar() > 50
+    _run_pair(p, [1, 2, 8], REL64 if precision == "fp64" else REL32, REL64)
+
+
+def test_free_expansion_walls_and_vacuum():
+    p = W.base(Kn=0.2, n_cells=64, x_min=-1.0, x_max=1.0, left=(1, 0.2, 0, 0, 1), right=(0, 0, 0, 0, 1),
+               x_split=0.0, bc_left="specular", bc_right="vacuum", ppc_ref=120, seed=3, precision="fp64")
+    _run_pair(p, [1, 4, 20], REL64, REL64)
+
+
+def test_ragged_small_cases():
+    # one cell; two cells; cells with fewer than two particles (no collisions possible)
+    for C, ppc in ((1, 50), (2, 3), (5, 1.5)):
+        p = W.uniform(n_cells=C, Kn=0.3, ppc_ref=ppc, state=(1.0, 0.1, 0.0, 0.0, 1.0), bc="specular",
+                      x_max=1.0, dt=0.05, seed=5)
+        _run_pair(p, [1, 6], REL64, REL64)
+
+
+def test_hard_sphere_and_total_rate_options():
+    p = W.config1("fp64")
+    p.update(omega=0.5, ntc_rate="total", eps_mode="eps12", n_cells=40, ppc_ref=60)
+    _run_pair(p, [1, 10], REL64, REL64)
+    p = W.sod(n_cells=80, Kn=2e-4, ppc_ref=60, precision="fp64", flux_mode="kfvs", eps_mode="eps_avg", seed=4)
+    _run_pair(p, [1, 10], REL64, REL64)
+
+
+def test_batch_equals_alone():
+    ps = [W.config1("fp64"), W.sod(n_cells=90, Kn=1e-3, ppc_ref=100, seed=9),
+          W.uniform(n_cells=17, bc="periodic", dt=0.02, x_max=1.0, ppc_ref=60, seed=2)]
+    b = solver(ps)
+    b.step(7)
+    for i, p in enumerate(ps):
+        a = solver(p)
+        a.step(7)
+        pa, pb = a.particles(), b.particles(i)
+        for k in pa:
+            assert np.array_equal(pa[k], pb[k]), f"instance {i} field {k}"
+        assert np.array_equal(a.fields()[0], b.fields(i)[0])
+        a.close()
+    b.close()
+
+
+def test_graphs_and_plain_launches_agree():
+    p = W.sod(n_cells=100, Kn=1e-3, ppc_ref=100, precision="fp32", seed=12)
+    a = solver(p, graphs=True)
+    b = solver(p, graphs=False)
+    a.step(9)
+    b.step(9)
+    pa, pb = a.particles(), b.particles()
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k])
+    assert np.array_equal(a.fields()[0], b.fields()[0])
+
+
+def test_checkpoint_resume_bit_exact():
+    p = W.config1("fp32")
+    a = solver(p)
+    a.step(10)
+    blob = a.checkpoint()
+    a.step(10)
+    b = solver(p)
+    b.restore(blob)
+    b.step(10)
+    pa, pb = a.particles(), b.particles()
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k])
+    assert np.array_equal(a.fields()[0], b.fields()[0])
+
+
+def test_time_average_matches_oracle():
+    p = W.config1("fp64")
+    p["avg_start"] = 5
+    g = solver(p)
+    o = O.Oracle(p)
+    g.step(12)
+    o.step(12)
+    ga, gn = g.fields(which=1)
+    oa, on = o.avg()
+    assert gn == on == 7
+    compare_fields(ga, oa, REL64)
