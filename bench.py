@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the DUWP per-time-step hot path on GB300: particle-updates/s and the fraction of
+the measured HBM bandwidth the particle kernel reaches, plus step-latency percentiles, the
+graph-replayed step, the plain one-instance-at-a-time FP64 loop, an end-to-end number through
+the C ABI with host buffers, and the CPU oracle as a reported baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch64|mach8|sod] [--impl reference]
+
+A step is one DUWP time step (Sec. 3.4 of the paper) of every instance of the workload.  A
+particle-update is one particle streamed through one step (counted after absorption and
+re-sampling).  Algorithmic bytes per particle-update: one read and one write of the particle
+record, 32 B for FP32 records (64 B for FP64).  Default workload: 64 uneven Mach 1.2-8 argon
+shock instances (100-4000 cells, 100-1000 particles per cell, FP32 particles, FP64 cells) in one
+batch; about 1.4e8 particles, so the 2.2 GB of particle records per buffer exceed the 129 MB L2
+and every step streams them from HBM.  Under torchrun each rank runs its own copy of the batch
+(independent seeds): weak scaling with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DUWP particle-updates/s"
+UNIT = "particle-updates/s"
+
+
+# ---------------------------------------------------------------------------- workloads
+def workload(name: str, rank: int = 0):
+    from paper_2305_12071_gb300 import workloads as W
+    if name == "batch64":
+        ps = W.config3_batch(64, precision="fp32")
+        for i, p in enumerate(ps):
+            p["seed"] = 1000 + i + 100_000 * rank
+        return ps, {"workload": "batch64_shock_fp32", "instances": 64, "mach": "U[1.2,8]",
+                    "cells": "U[100,4000]", "ppc_ref": "U[100,1000]", "omega": 0.81, "records": "fp32",
+                    "cell_state": "fp64"}
+    if name == "mach8":
+        p = W.config4("fp32")
+        p["seed"] = 4 + 100_000 * rank
+        return [p], {"workload": "mach8_shock_1e5cells_fp32", "instances": 1, "cells": 100_000, "Kn": 0.1,
+                     "ppc_ref": 415, "omega": 0.68, "records": "fp32", "cell_state": "fp64"}
+    if name == "sod":
+        p = W.config2(Kn=1e-4, precision="fp32")
+        p["seed"] = 1 + 100_000 * rank
+        return [p], {"workload": "sod_1000cells_kn1e-4_fp32", "instances": 1, "cells": 1000, "ppc_ref": 500,
+                     "records": "fp32", "cell_state": "fp64"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def shard(n_items: int, rank: int, world: int):
+    """Items of one rank when a batch is split across ranks (round robin)."""
+    return list(range(rank, n_items, world))
+
+
+def aggregate(updates_per_rank, seconds_per_rank):
+    """Whole-job throughput: all updates over the slowest rank's time."""
+    t = max(seconds_per_rank)
+    return (sum(updates_per_rank) / t) if t > 0 else 0.0
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("duwp_kernels.cu", "duwp_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2305_12071_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name: str, updates_per_launch: float):
+    """DRAM bytes per launch of the particle kernel from the committed ncu summary, when it was
+    taken on the current kernel source; scaled by the particle-updates of a launch."""
+    path = os.path.join(ROOT, "profiles", "k_particles_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", txt)
+    b = re.search(r"dram bytes per particle-update:\s*([0-9.]+)", txt)
+    if not m or not b or m.group(1) != kernel_source_hash():
+        return None, None
+    per = float(b.group(1))
+    return per * updates_per_launch, per
+
+
+def oracle_sample(params_list, sample_idx, steps: int, warm: int = 1):
+    """Time the CPU oracle (single thread) on a sample of the instances."""
+    import oracle as O
+    inst = [O.Oracle(params_list[i]) for i in sample_idx]
+    for o in inst:
+        o.step(warm)
+    updates = 0
+    t0 = time.perf_counter()
+    for o in inst:
+        for _ in range(steps):
+            before = o.num_particles()
+            o.step(1)
+            c = o.counters()
+            # particles streamed = arrived - absorbed + re-sampled (interior cells)
+            updates += before - int(c["nabs"].sum()) + int(c["nnew"].sum())
+    dt = time.perf_counter() - t0
+    return updates, dt
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    plist, cfg = workload(args.workload, 0)
+    n = len(plist)
+    sample = list(range(0, n, max(1, n // 4)))[:4] if n > 1 else [0]
+    import oracle as O
+    inst = [O.Oracle(plist[i]) for i in sample]
+    if args.workload == "mach8":
+        # one instance of 1e8 particles: the oracle takes a bounded piece of it per step
+        raise SystemExit(json.dumps({"impl": "reference", "unavailable": "oracle sample of the 1e8-particle "
+                                     "instance exceeds the few-minute bound of the reference arm"}))
+    for _ in range(args.warmup):
+        for o in inst:
+            o.step(1)
+    times, ups = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for o in inst:
+            before = o.num_particles()
+            o.step(1)
+            c = o.counters()
+            ups += before - int(c["nabs"].sum()) + int(c["nnew"].sum())
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ups / tot
+    cfg = dict(cfg)
+    cfg["sample"] = f"instances {sample} of the batch (oracle, one thread)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": cfg["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="particle-kernel threads per cell (0: default)")
+    ap.add_argument("--instances", type=int, default=0, help="use only the first N instances of the batch")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2305_12071_gb300 import build as B
+    B.build()
+    from paper_2305_12071_gb300 import duwp
+
+    torch.cuda.set_device(local)
+    plist, cfg = workload(args.workload, rank)
+    if args.instances:
+        plist = plist[:args.instances]
+        cfg = dict(cfg, instances=len(plist), workload=cfg["workload"] + f"_first{len(plist)}")
+    fp32 = plist[0].get("precision", "fp64") == "fp32"
+    rec_bytes = 16 if fp32 else 32
+
+    sol = duwp.Solver(plist, device=local)
+    if args.threads:
+        sol.set_launch(args.threads)
+    sol.step(args.warmup)
+    sol.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ------------------------------------------------ timed region: K steps, events around each kernel
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    u0 = sol.particle_updates()
+    kms, step_ms = sol.step_timed(args.steps)
+    u1 = sol.particle_updates()
+    barrier()
+    clocks = clk.stop()
+    span_s = kms[4] / 1e3
+    updates = u1 - u0
+    if dist is not None:
+        t = torch.tensor([span_s, float(updates)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        span_all, updates_all = float(tmax[0]), float(t[1])
+    else:
+        span_all, updates_all = span_s, float(updates)
+    value = updates_all / span_all
+
+    # ------------------------------------------------ graph-replayed steps (same work, one graph per step)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(sol.stream):
+        g0.record()
+    sol.step(args.steps)
+    with torch.cuda.stream(sol.stream):
+        g1.record()
+    sol.sync()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+
+    out = None
+    if rank == 0:
+        steps_sorted = sorted(step_ms)
+        p50 = steps_sorted[len(steps_sorted) // 2]
+        p99 = steps_sorted[min(len(steps_sorted) - 1, int(math.ceil(0.99 * len(steps_sorted))) - 1)]
+        upl = updates / args.steps                     # particle-updates per launch of the particle kernel
+        k_ms = kms[0] / args.steps
+        peak, peak_kind = measured_peaks()
+        achieved = rec_bytes * 2 * upl / (k_ms * 1e-3) / 1e9
+        traffic, per_upd = profiled_traffic(args.workload, upl)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_particles",
+                "algorithmic_bytes_per_update": rec_bytes * 2, "updates_per_launch": upl,
+                "launch_ms": k_ms, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        kernel_share = {n: float(v / max(kms[:4].sum(), 1e-30)) for n, v in
+                        zip(("k_particles", "k_far_sort", "k_cells", "k_offsets_flux"), kms[:4])}
+        cfg = dict(cfg)
+        info0 = sol.info(0)
+        cfg.update({"particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
+                    "cells_total": int(sum(p["n_cells"] for p in plist)),
+                    "capacity_per_buffer": int(info0["capacity"]), "cell_capacity": int(info0["cell_capacity"]),
+                    "l2": "inputs larger than L2 (particle records exceed 129 MB)", "graphs": "one graph per step"})
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * span_all / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+               "data": "synthetic (seeded shock/Sod problems shaped like the paper's test cases)",
+               "config": cfg, "clocks": clocks, "gpu_launches": 4 * args.steps,
+               "step_ms_p50": p50, "step_ms_p99": p99, "graph_ms_per_step": graph_ms,
+               "kernel_ms_per_step": {n: float(v / args.steps) for n, v in
+                                      zip(("k_particles", "k_far_sort", "k_cells", "k_offsets_flux"), kms[:4])},
+               "kernel_share": kernel_share, "roofline": roof}
+    sol.close()
+    del sol
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ plain FP64 loop: one instance at a time, no graphs
+    if rank == 0 and not args.no_plain and world == 1:
+        pl_updates, pl_ms = 0, 0.0
+        kplain = max(3, min(args.steps, 10))
+        for p in plist:
+            q = dict(p)
+            q["precision"] = "fp64"
+            s = duwp.Solver(q, device=local, graphs=False)
+            s.step(3)
+            s.sync()
+            a = s.particle_updates()
+            k, _ = s.step_timed(kplain)
+            pl_updates += s.particle_updates() - a
+            pl_ms += k[4]
+            s.close()
+            del s
+        torch.cuda.empty_cache()
+        plain = pl_updates / (pl_ms / 1e3)
+        out["plain_fp64_loop"] = {"value": plain, "unit": UNIT, "steps": kplain,
+                                  "note": "same instances, FP64 records, one instance per launch sequence, no graphs"}
+        out["speedup_vs_plain_fp64_loop"] = value / plain
+
+    # ------------------------------------------------ end to end through the C ABI with host buffers
+    import numpy as np
+    if rank == 0:
+        t0 = time.perf_counter()
+        s = duwp.Solver(plist, device=local)           # host params -> device (init)
+        u_start = 0
+        d2h = 0
+        for _ in range(args.steps):
+            s.step(1)
+            for i in range(s.n):
+                m = s.moments(i)                          # host result arrays every step (synchronizing)
+                d2h += sum(a.nbytes for a in m.values())
+        u_e2e = s.particle_updates() - u_start
+        e2e_s = time.perf_counter() - t0
+        import ctypes
+        h2d = ctypes.sizeof(duwp.Params) * len(plist)
+        out["e2e"] = {"value": u_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                      "d2h_bytes_per_step": d2h / args.steps,
+                      "note": "duwp_init_batch from host parameters, then per step duwp_step + duwp_moments "
+                              "of every instance into host arrays; includes the first (all-sampling) step"}
+        s.close()
+        del s
+
+    # ------------------------------------------------ CPU oracle on a bounded sample
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = len(plist)
+        if n > 1:
+            idx = list(range(0, n, 8))
+            ups, secs = oracle_sample(plist, idx, steps=2)
+            sample = f"instances {idx} of the batch, 1 untimed + 2 timed steps each"
+        else:
+            ups, secs = None, None
+            sample = "not run: a single instance too large for a bounded oracle sample"
+        if ups is not None:
+            out["cpu_baseline"] = {"value": ups / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": sample, "seconds": secs}
+        else:
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -118,6 +118,7 @@ typedef struct {
     int32_t cell_capacity;   /* particles one cell may hold within a step */
     int32_t n_instances;
     int64_t steps_done;      /* steps taken by this instance */
+    int64_t particle_updates;/* particles streamed through a step by this instance, all steps so far */
 } duwp_info;
 
 /* ------------------------------------------------------------------ single instance and batch */
@@ -143,6 +144,14 @@ int duwp_step(duwp_handle *h, int32_t n_steps);
 
 /* Synchronizing: wait for the handle's stream; returns the device error status. */
 int duwp_sync(duwp_handle *h);
+
+/* Synchronizing.  Advance by n_steps >= 1 steps as individual launches with CUDA events recorded
+ * on the handle's stream around every kernel.  host_kernel_ms[5] (caller-owned) receives the summed
+ * device time of the particle kernel, the far-mover sort, the cell update and the offset/flux
+ * kernel, and in [4] the device time from the first launch to the end of the last;
+ * host_step_ms (n_steps entries, may be NULL) the device time of each step.  Results are
+ * identical to duwp_step.  Errors: as duwp_step and duwp_sync. */
+int duwp_step_timed(duwp_handle *h, int32_t n_steps, double *host_kernel_ms, double *host_step_ms);
 
 enum { DUWP_INSTANT = 0, DUWP_AVERAGED = 1 };
 

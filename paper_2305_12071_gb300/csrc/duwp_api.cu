@@ -371,13 +371,18 @@ int Engine::enqueue_prepare()
     return DUWP_OK;
 }
 
-int Engine::enqueue_step()
+int Engine::enqueue_step(cudaEvent_t *ev)
 {
     const int rp = parity;
+    if (ev) DUWP_CU(cudaEventRecord(ev[0], stream));
     DUWP_CU(launch_particles(dev, fp32, rp, grid, threads, smem, stream));
+    if (ev) DUWP_CU(cudaEventRecord(ev[1], stream));
     DUWP_CU(launch_far_sort(dev, fp32, stream));
+    if (ev) DUWP_CU(cudaEventRecord(ev[2], stream));
     DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
+    if (ev) DUWP_CU(cudaEventRecord(ev[3], stream));
     DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+    if (ev) DUWP_CU(cudaEventRecord(ev[4], stream));
     parity = 1 - rp;
     return DUWP_OK;
 }
@@ -498,6 +503,44 @@ int duwp_sync(duwp_handle *h)
     return h->eng.sync();
 }
 
+int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_ms)
+{
+    if (!h || n < 1 || !kernel_ms) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    std::vector<cudaEvent_t> ev(5 * static_cast<size_t>(n), nullptr);
+    int rc = DUWP_OK;
+    for (auto &e : ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) { rc = DUWP_ECUDA; break; }
+    }
+    for (int32_t s = 0; s < n && rc == DUWP_OK; ++s) {
+        rc = E.enqueue_step(ev.data() + 5 * static_cast<size_t>(s));
+        if (rc == DUWP_OK) ++E.steps_done;
+    }
+    if (rc == DUWP_OK) rc = E.sync();
+    for (int k = 0; k < 5; ++k) kernel_ms[k] = 0.0;
+    if (rc == DUWP_OK) {
+        float span = 0.f;
+        cudaEventElapsedTime(&span, ev[0], ev[5 * static_cast<size_t>(n) - 1]);
+        kernel_ms[4] = span;
+        for (int32_t s = 0; s < n; ++s) {
+            cudaEvent_t *e = ev.data() + 5 * static_cast<size_t>(s);
+            for (int k = 0; k < 4; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e[k], e[k + 1]);
+                kernel_ms[k] += ms;
+            }
+            if (step_ms) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e[0], e[4]);
+                step_ms[s] = ms;
+            }
+        }
+    }
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    return rc;
+}
+
 int duwp_destroy(duwp_handle *h)
 {
     if (!h) return DUWP_EINVAL;
@@ -585,6 +628,7 @@ int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
     rc = E.read_inst(b, d);
     if (rc) return rc;
     out->steps_done = d.step;
+    out->particle_updates = static_cast<int64_t>(d.updates);
     return DUWP_OK;
 }
 

@@ -65,7 +65,7 @@ struct Engine {
     int configure_launch(int threads_, int cell_cap_);
     int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
     int remove_instance(int slot);
-    int enqueue_step();                // launches of one step on the stream
+    int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[5]: events around kernels
     int enqueue_prepare();             // cell + offset kernels of the initial state
     int step(int32_t n);
     int sync();                        // wait + read the device error word

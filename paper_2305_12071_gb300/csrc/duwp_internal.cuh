@@ -44,6 +44,7 @@ struct InstDev {
     uint32_t step;          // steps completed (advanced once per step, after the cell update)
     int32_t avg_start;
     int64_t navg;           // states accumulated into the time average
+    unsigned long long updates;   // particles streamed by this instance (interior cells), all steps
     double dx, dt, dtdx, mp, dx_over_mp, mp_over_dx;
     double R, Pr, omega, T_ref, rho_ref, mu_ref, upsilon, c_ref, ntc_A;
     float dtdx_f;

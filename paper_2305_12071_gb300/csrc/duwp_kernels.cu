@@ -550,6 +550,7 @@ __global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
             __syncthreads();
         }
         if (tid == 0) {
+            if (!H.ghost) atomicAdd(&E.inst[H.b].updates, static_cast<unsigned long long>(n_tot));
             E.nL[wp][g] = H.cntL;
             E.nS[wp][g] = H.cntS;
             E.nR[wp][g] = H.cntR;

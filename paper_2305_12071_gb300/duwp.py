@@ -26,7 +26,7 @@ NTC = {"particle": 0, "total": 1}
 
 # Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
 EXPORTS = (
-    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_moments", "duwp_fields", "duwp_get_info",
+    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_step_timed", "duwp_moments", "duwp_fields", "duwp_get_info",
     "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
@@ -71,7 +71,7 @@ class Info(C.Structure):
     _fields_ = [("dx", C.c_double), ("dt", C.c_double), ("mp", C.c_double), ("beta", C.c_double),
                 ("lambda_ref", C.c_double), ("mu_ref", C.c_double), ("c_ref", C.c_double),
                 ("capacity", C.c_int64), ("cell_capacity", C.c_int32), ("n_instances", C.c_int32),
-                ("steps_done", C.c_int64)]
+                ("steps_done", C.c_int64), ("particle_updates", C.c_int64)]
 
 
 class ServerCfg(C.Structure):
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
         L.duwp_init_batch.argtypes = [C.POINTER(Params), i32, vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]
         L.duwp_step.argtypes = [vp, i32]
         L.duwp_sync.argtypes = [vp]
+        L.duwp_step_timed.argtypes = [vp, i32, dp, dp]
         L.duwp_moments.argtypes = [vp, i32, i32, dp, dp, dp, dp, i32]
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
@@ -249,6 +250,18 @@ class Solver:
 
     def sync(self):
         _chk(self.L.duwp_sync(self.h), "duwp_sync")
+
+    def step_timed(self, n: int):
+        """n steps as plain launches with CUDA events around each kernel: returns (kernel_ms[5]: summed
+        over the steps for particles, far sort, cells, offsets+flux, then the span of all n steps;
+        per-step ms)."""
+        k = np.zeros(5, np.float64)
+        st = np.zeros(int(n), np.float64)
+        _chk(self.L.duwp_step_timed(self.h, int(n), _dptr(k), _dptr(st)), "duwp_step_timed")
+        return k, st
+
+    def particle_updates(self) -> int:
+        return int(sum(self.info(i)["particle_updates"] for i in range(self.n)))
 
     def use_graphs(self, on: bool):
         _chk(self.L.duwp_use_graphs(self.h, 1 if on else 0), "duwp_use_graphs")
