@@ -18,7 +18,6 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libduwp.so")
-SOURCES = ["duwp_kernels.cu", "duwp_api.cu", "duwp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -52,7 +51,8 @@ def build(force: bool = False, verbose_ptx: bool = False, quiet: bool = True) ->
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "duwp.h"))
     objs, procs = [], []
-    for s in SOURCES:
+    sources = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    for s in sources:
         src = os.path.join(CSRC, s)
         obj = os.path.join(OUT_DIR, s.replace(".cu", ".o"))
         objs.append(obj)

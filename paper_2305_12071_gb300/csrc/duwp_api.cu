@@ -204,6 +204,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
         DUWP_CU(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
         own_stream = true;
     }
+    if (!params || n < 0) return DUWP_EINVAL;
     std::vector<HostInst> hs(static_cast<size_t>(n));
     int64_t est = 0;
     int64_t cells = 0;
@@ -217,7 +218,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
         const double rmax = std::max(params[b].left.rho, params[b].right.rho) / params[b].rho_ref;
         max_ppc = std::max(max_ppc, rmax * params[b].ppc_ref);
     }
-    fp32 = (n > 0 && params[0].precision == DUWP_FP32) ? 1 : 0;
+    fp32 = (params[0].precision == DUWP_FP32) ? 1 : 0;
     if (pool_cells > 0) cells = std::max<int64_t>(cells, pool_cells);
     if (cells > (int64_t(1) << 30)) return DUWP_EINVAL;
     G = static_cast<int32_t>(cells);
@@ -366,7 +367,10 @@ int Engine::remove_instance(int slot)
 
 int Engine::enqueue_prepare()
 {
-    DUWP_CU(launch_cells(dev, fp32, 0, 0, stream));
+    // Recompute the primitive state, P, slot bounds, offsets and flux of every cell from the
+    // current state without advancing: idempotent for instances already running (same inputs and
+    // draws), and the start of a newly added one.
+    DUWP_CU(launch_cells(dev, fp32, parity, 0, stream));
     DUWP_CU(launch_offsets_flux(dev, 1 - parity, 0, stream));
     return DUWP_OK;
 }
@@ -440,10 +444,6 @@ int Engine::read_inst(int b, InstDev &out)
 }  // namespace duwp
 
 using namespace duwp;
-
-struct duwp_handle {
-    Engine eng;
-};
 
 // ------------------------------------------------------------------------------------------
 // C ABI

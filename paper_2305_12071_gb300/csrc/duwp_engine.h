@@ -66,7 +66,7 @@ struct Engine {
     int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
     int remove_instance(int slot);
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[5]: events around kernels
-    int enqueue_prepare();             // cell + offset kernels of the initial state
+    int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
     int step(int32_t n);
     int sync();                        // wait + read the device error word
     int read_inst(int b, InstDev &out);
@@ -76,3 +76,8 @@ struct Engine {
 };
 
 }  // namespace duwp
+
+// The public handle: one engine.
+struct duwp_handle {
+    duwp::Engine eng;
+};

@@ -1,0 +1,83 @@
+"""Continuous-batching server: requests of different sizes, Mach and Kn arrive while others are on
+the GPU, are admitted by HBM footprint as slots free up, and each result equals the same problem
+solved alone (bit-identical: every request draws only from its own generator key and the per-cell
+arithmetic does not depend on what else is resident)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2305_12071_gb300 import workloads as W
+from parity_util import solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    reqs = []
+    for i, (mach, cells, ppc) in enumerate([(1.5, 120, 80), (3.0, 200, 60), (6.0, 90, 120), (2.2, 300, 40)]):
+        p = W.shock(mach, n_cells=cells, ppc_ref=ppc, precision="fp32", seed=500 + i)
+        reqs.append((p, 12 + 3 * i))
+    for i, (kn, cells) in enumerate([(1e-3, 150), (3e-4, 110), (0.05, 250)]):
+        p = W.sod(n_cells=cells, Kn=kn, ppc_ref=70, precision="fp32", seed=600 + i)
+        reqs.append((p, 9 + 4 * i))
+    return reqs
+
+
+def _alone(p, n):
+    s = solver(p)
+    s.step(n)
+    m = s.moments()
+    s.close()
+    return m
+
+
+def test_served_results_equal_alone():
+    from paper_2305_12071_gb300 import build as B
+    from paper_2305_12071_gb300 import duwp
+    B.build()
+    srv = duwp.Server(hbm_budget_bytes=2 << 30, max_slots=3, max_cells=2048, steps_per_launch=4,
+                      precision="fp32")
+    reqs = _mix()
+    ids = []
+    # first wave, then more requests while the first ones are running
+    for p, n in reqs[:3]:
+        ids.append(srv.submit(p, n))
+    time.sleep(0.05)
+    for p, n in reqs[3:]:
+        ids.append(srv.submit(p, n))
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids) and time.time() - t0 < 120:
+        for rid in ids:
+            if rid not in results:
+                r = srv.poll(rid)
+                if r is not None:
+                    results[rid] = r
+        time.sleep(0.002)
+    assert len(results) == len(ids)
+    srv.close()
+    for (p, n), rid in zip(reqs, ids):
+        r = results[rid]
+        assert r["status"] == 0
+        assert r["steps"] == n
+        assert r["particle_updates"] > 0
+        assert r["step_p99_ms"] >= r["step_p50_ms"] > 0
+        a = _alone(p, n)
+        for k in ("rho", "u", "T"):
+            assert np.array_equal(r[k], a[k]), f"request {rid} field {k} differs from the solve alone"
+
+
+def test_server_rejects_oversized_and_unknown():
+    from paper_2305_12071_gb300 import duwp
+    srv = duwp.Server(hbm_budget_bytes=256 << 20, max_slots=2, max_cells=1024, steps_per_launch=2,
+                      precision="fp32")
+    big = W.shock(3.0, n_cells=5000, ppc_ref=100, precision="fp32")
+    with pytest.raises(duwp.DuwpError):
+        srv.submit(big, 5)
+    wrong = W.shock(3.0, n_cells=50, ppc_ref=50, precision="fp64")
+    with pytest.raises(duwp.DuwpError):
+        srv.submit(wrong, 5)
+    with pytest.raises(duwp.DuwpError):
+        srv.poll(987654)
+    srv.close()
