@@ -223,6 +223,27 @@ int duwp_checkpoint_size(duwp_handle *h, uint64_t *bytes);
 int duwp_checkpoint_save(duwp_handle *h, void *host_buf, uint64_t bytes);
 int duwp_checkpoint_restore(duwp_handle *h, const void *host_buf, uint64_t bytes);
 
+/* ------------------------------------------------------------------ allocation-free inspection */
+
+/* The paper has no counterpart: this is a library facility.  Callers that cannot allocate device
+ * memory when they inspect the particles -- code running inside CUDA stream capture, where an
+ * allocation would break the capture, and hosts that hand the library a fixed memory arena at
+ * set-up and forbid allocations afterwards -- use this instead of duwp_get_particles.
+ * Writes the particles of instance `inst`, in the same stable per-cell order and values as
+ * duwp_get_particles, into caller-owned DEVICE arrays of n entries (n = duwp_num_particles):
+ * cell index, cell-local position, velocity.  Asynchronous on the handle's stream; a count that
+ * differs from n is recorded on the device and reported by the next synchronizing call
+ * (DUWP_EOVERFLOW), and nothing is written then.  Allocates nothing, on the device or the host:
+ * the per-cell start table it needs is a static device array of DUWP_NOALLOC_MAX_CELLS entries
+ * (2 MiB, held by every device that loads the library until the process exits); an instance with
+ * more cells is rejected with DUWP_EINVAL.  The first call on a device looks that array's address
+ * up and keeps it (make that first call before any stream capture).  All calls share the array
+ * and each call overwrites it, so calls that overlap on the GPU (from other streams or handles)
+ * race on it.  Errors: DUWP_EINVAL, DUWP_ECUDA. */
+#define DUWP_NOALLOC_MAX_CELLS 262144
+int duwp_get_particles_noalloc(duwp_handle *h, int32_t inst, int32_t *dev_cell, double *dev_xl,
+                               double *dev_u, double *dev_v, double *dev_w, int64_t n);
+
 /* ------------------------------------------------------------------ serving (continuous batching) */
 
 typedef struct duwp_server duwp_server;

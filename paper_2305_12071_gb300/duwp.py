@@ -30,7 +30,7 @@ EXPORTS = (
     "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
-    "duwp_server_destroy",
+    "duwp_server_destroy", "duwp_get_particles_noalloc",
 )
 
 
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
         L.duwp_num_particles.argtypes = [vp, i32, C.POINTER(i64)]
         L.duwp_get_particles.argtypes = [vp, i32, ip, dp, dp, dp, dp, i64]
         L.duwp_get_counters.argtypes = [vp, i32, ip, ip, ip, ip, i32]
+        L.duwp_get_particles_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp, i64]
         L.duwp_get_cmax.argtypes = [vp, i32, dp, i32]
         L.duwp_checkpoint_size.argtypes = [vp, C.POINTER(u64)]
         L.duwp_checkpoint_save.argtypes = [vp, vp, u64]
@@ -302,6 +303,14 @@ class Solver:
         _chk(self.L.duwp_get_particles(self.h, inst, _iptr(cell), _dptr(xl), _dptr(u), _dptr(v), _dptr(w), n),
              "duwp_get_particles")
         return {"cell": cell, "xl": xl, "u": u, "v": v, "w": w}
+
+    def particles_noalloc(self, out: dict, inst: int = 0):
+        """Write the particles into caller-owned CUDA tensors (keys cell (int32), xl, u, v, w (float64),
+        each of num_particles entries) without any allocation inside the library; asynchronous on the
+        handle's stream (call sync() before reading them)."""
+        n = int(out["cell"].numel())
+        ptr = [C.c_void_p(out[k].data_ptr()) for k in ("cell", "xl", "u", "v", "w")]
+        _chk(self.L.duwp_get_particles_noalloc(self.h, inst, *ptr, n), "duwp_get_particles_noalloc")
 
     def counters(self, inst: int = 0) -> dict:
         n = self.n_cells(inst)
