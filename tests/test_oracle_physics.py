@@ -174,3 +174,38 @@ def test_wave_particle_split_fixed_point(oracle_mod):
     fstar = (1 - P) / (1 - P + P * P)
     n = 10 * 4000
     assert np.mean(fs) == pytest.approx(fstar, abs=6 * math.sqrt(fstar / n) + 2e-3)
+
+
+def test_collision_rate_with_too_small_initial_majorant(oracle_mod):
+    # The gas is heated 16x after the start, so the initial c_max = 5 sqrt(2RT_init) is far below
+    # typical relative speeds.  Raising c_max to c_r whenever a candidate exceeds it (Appendix A
+    # leaves the majorant to be estimated during the run) restores the equilibrium collision rate
+    # at the new temperature; without it the NTC count would stay tied to the stale majorant.
+    omega = 0.81
+    p = W.uniform(n_cells=4, Kn=1.0, ppc_ref=2000, state=(1, 0, 0, 0, 1.0), omega=omega, dt=0.01, x_max=1.0)
+    o = oracle_mod.Oracle(p)
+    o.step(1)
+    q = o.particles()
+    s = 4.0                                          # velocities x4: temperature x16
+    u, v, w = q["u"] * s, q["v"] * s, q["w"] * s
+    o.set_particles(q["cell"], q["xl"], u, v, w)
+    c = o.consts()
+    mpdx = c["mp"] / c["dx"]
+    psi = np.zeros((4, 5))
+    for i in range(4):
+        m = q["cell"] == i
+        psi[i] = mpdx * np.array([m.sum(), u[m].sum(), v[m].sum(), w[m].sum(),
+                                  0.5 * (u[m]**2 + v[m]**2 + w[m]**2).sum()])
+    o.set_psi(psi)
+    cm0 = o.cmax().copy()
+    o.step(3)
+    assert np.all(o.cmax() > 2.0 * cm0)              # the majorant was raised
+    tot, npart = 0, 0
+    for _ in range(30):
+        o.step(1)
+        tot += int(o.counters()["nacc"].sum())
+        npart += o.num_particles()
+    T = float(np.mean(u**2 + v**2 + w**2) / 3)
+    nu = 2 * tot / (npart * c["dt"])
+    nu_th = 4 * math.sqrt(1 / math.pi) / (math.sqrt(2) * c["lambda_ref"]) * T ** (1 - omega)
+    assert nu == pytest.approx(nu_th, rel=5.0 / math.sqrt(tot) + 0.01)
