@@ -1,0 +1,79 @@
+"""Autotuner of the particle kernel's launch shape.
+
+Two knobs: threads per cell block (the block works on one cell list at a time) and the number of
+particles a cell list may hold in shared memory (particles per thread x threads; larger lists are
+staged in a per-block slice of global memory).  Together they fix the blocks resident per SM.  The
+tuner times a few steps of the caller's own workload for every candidate with CUDA events
+(duwp_step_timed) and keeps the fastest.  Results do not depend on the launch shape (the per-cell
+moment sums are exact fixed-point integers and the partition order is defined by the method), so
+tuning changes speed only.  Choices are cached in a JSON file keyed by device, precision and
+workload size buckets.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
+
+CANDIDATES_FP32 = [(t, c) for t in (64, 128, 256) for c in (512, 1024, 2048, 3072)]
+CANDIDATES_FP64 = [(t, c) for t in (64, 128, 256) for c in (256, 512, 1024, 1536)]
+
+
+def _key(solver) -> str:
+    import torch
+    name = torch.cuda.get_device_name()
+    prec = solver.params[0].get("precision", "fp64")
+    cells = sum(int(p["n_cells"]) for p in solver.params)
+    parts = sum(solver.num_particles(i) for i in range(solver.n))
+    ppc = parts / max(cells, 1)
+    return f"{name}|{prec}|cells2^{int(math.log2(max(cells, 1)))}|ppc2^{int(math.log2(max(ppc, 1)))}"
+
+
+def _load():
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(d):
+    os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+    tmp = _CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1)
+    os.replace(tmp, _CACHE)
+
+
+def tune(solver, steps: int = 3, use_cache: bool = True, candidates=None):
+    """Pick and apply the fastest (threads, cell_capacity) for this solver's workload.  The solver
+    advances by len(candidates) * steps steps.  Returns (choice, timings)."""
+    key = _key(solver)
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        t, c = cache[key]["threads"], cache[key]["cell_capacity"]
+        solver.set_launch(t, c)
+        return (t, c), cache[key].get("timings", {})
+    fp32 = solver.params[0].get("precision", "fp64") == "fp32"
+    cands = candidates or (CANDIDATES_FP32 if fp32 else CANDIDATES_FP64)
+    timings = {}
+    best = None
+    for t, c in cands:
+        try:
+            solver.set_launch(t, c)
+        except Exception:
+            continue
+        solver.step_timed(1)                     # first launch of a shape: not timed
+        k, _ = solver.step_timed(steps)
+        ms = float(k[0]) / steps
+        timings[f"{t}x{c}"] = ms
+        if best is None or ms < best[0]:
+            best = (ms, t, c)
+    if best is None:
+        raise RuntimeError("no launch shape could be configured")
+    solver.set_launch(best[1], best[2])
+    cache[key] = {"threads": best[1], "cell_capacity": best[2], "ms": best[0], "timings": timings}
+    _save(cache)
+    return (best[1], best[2]), timings

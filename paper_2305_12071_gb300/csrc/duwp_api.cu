@@ -154,6 +154,7 @@ Engine::~Engine()
 {
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    dfree(stage, stage_bytes);
     dfree(slab, slab_bytes);
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -182,11 +183,34 @@ int Engine::configure_launch(int threads_, int cell_cap_)
     if (occ <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    const int grid_ = std::max(1, std::min(occ * nsm, G));
+    // global staging for cells whose list exceeds the shared-memory capacity
+    if (stage_cap > cell_cap_) {
+        const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
+        const size_t per = (static_cast<size_t>(stage_cap) * rec + 255) & ~static_cast<size_t>(255);
+        const size_t need = static_cast<size_t>(grid_) * (per + ((static_cast<size_t>(stage_cap) + 255) & ~static_cast<size_t>(255)));
+        if (need > stage_bytes) {
+            DUWP_CU(cudaStreamSynchronize(stream));
+            dfree(stage, stage_bytes);
+            stage = nullptr;
+            stage_bytes = 0;
+            stage = dalloc(need);
+            if (!stage) return DUWP_ENOMEM;
+            stage_bytes = need;
+        }
+        dev.stage = stage;
+        dev.stage_cls = static_cast<uint8_t *>(stage) + static_cast<size_t>(grid_) * per;
+        dev.stage_cap = stage_cap;
+    } else {
+        dev.stage = nullptr;
+        dev.stage_cls = nullptr;
+        dev.stage_cap = 0;
+    }
     threads = threads_;
     cell_cap = cell_cap_;
     dev.cell_cap = cell_cap_;
     smem = sm;
-    grid = std::max(1, std::min(occ * nsm, G));
+    grid = grid_;
     drop_graphs();
     return DUWP_OK;
 }
@@ -233,10 +257,14 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     else if (cap_user > 0) cap = static_cast<int64_t>(cap_user);
     if (cap >= (int64_t(1) << 40)) return DUWP_EINVAL;
     capacity = cap;
+    // largest cell list within a step (the slot bound is at most twice the cell's mass in
+    // particles), and the shared-memory share of it
     int32_t cc = 0;
     for (int32_t b = 0; b < n; ++b) cc = std::max(cc, params[b].cell_capacity);
     if (cc <= 0) cc = static_cast<int32_t>(std::ceil(2.5 * max_ppc)) + 64;
     cc = std::max(cc, 256);
+    stage_cap = cc;
+    cc = std::min(cc, fp32 ? 2048 : 1024);
     cc = std::min(cc, max_cell_capacity(fp32));
     far_cap = 1 << 16;
 

@@ -41,8 +41,11 @@ struct Engine {
     int32_t G = 0;              // flattened cells
     int32_t max_inst = 0;
     int64_t capacity = 0;       // particle slots per buffer
-    int32_t cell_cap = 0;
+    int32_t cell_cap = 0;       // shared-memory list capacity of the particle kernel
+    int32_t stage_cap = 0;      // largest cell list within a step (global staging above cell_cap)
     int32_t far_cap = 0;
+    void *stage = nullptr;      // grid x stage_cap records + class bytes
+    size_t stage_bytes = 0;
     int32_t threads = 128;
     int32_t grid = 0;
     size_t smem = 0;

@@ -65,7 +65,7 @@ struct EngineDev {
     int32_t G;                 // flattened cells in the pool
     int32_t n_inst;
     int64_t capacity;          // particle slots per buffer
-    int32_t cell_cap;          // particles one cell may hold within a step (shared memory)
+    int32_t cell_cap;          // cell lists up to this size are staged in shared memory
     int32_t far_cap;
     InstDev *inst;
     int32_t *cell_inst;        // instance of each flattened cell, -1 = unused
@@ -90,6 +90,9 @@ struct EngineDev {
     int32_t *far_count;        // [0]: appended, [1]: sorted
     int32_t *err;              // first device error
     int32_t *ticket;           // work counter of the particle kernel
+    void *stage;               // per-CTA global staging of cell lists above cell_cap (stage_cap records each)
+    uint8_t *stage_cls;        // per-CTA class bytes of the same
+    int32_t stage_cap;         // particles one cell may hold within a step (global staging)
 };
 
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels
@@ -152,10 +155,23 @@ __device__ inline bool prim_from_cons(const double *psi, double R, double *q)
 
 __device__ inline double viscosity(const InstDev &I, double T) { return I.mu_ref * pow(T / I.T_ref, I.omega); }
 
-// Eq. (p): P = 0 if dt <= tau, else 1 - tau/dt, with tau = mu / p.
+// Single-precision estimate of tau = mu(T)/(rho R T); used only where an error far below 1% cannot
+// change the decision dt <= tau.  Returns 0 when the estimate is not usable (over/underflow).
+__device__ __forceinline__ float tau_estimate(const InstDev &I, float rho, float T)
+{
+    const float mu = static_cast<float>(I.mu_ref) * powf(T / static_cast<float>(I.T_ref), static_cast<float>(I.omega));
+    const float tau = mu / (rho * static_cast<float>(I.R) * T);
+    return (tau > 0.0f && tau < 1e30f) ? tau : 0.0f;
+}
+
+// Eq. (p): P = 0 if dt <= tau, else 1 - tau/dt, with tau = mu / p.  When the single-precision
+// estimate of tau exceeds dt by more than 1% (its error is below 1e-5 relative), P = 0 without the
+// double-precision power.
 __device__ inline double split_fraction(const InstDev &I, const double *q, bool ok)
 {
     if (!ok) return 0.0;
+    const float t32 = tau_estimate(I, static_cast<float>(q[0]), static_cast<float>(q[4]));
+    if (t32 > 1.01f * static_cast<float>(I.dt) && q[0] > 1e-30 && q[4] > 1e-30 && q[4] < 1e30) return 0.0;
     const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
     if (I.dt <= tau) return 0.0;
     return 1.0 - tau / I.dt;
@@ -221,10 +237,47 @@ __device__ inline void half_moments(double U, double lam, double *pos, double *n
 // interface equilibrium from the colliding half-Maxwellians, Euler flux of it (or the split
 // kinetic flux), NS stress and heat flux with mu_e = eps mu(T0), weighted by
 // P_f = max(0, 1 - tau_f/dt) (Sec. 3.3, Eq. ce2 at t = dt; Step 3).
+// Single-precision interface state (rho0, T0) of the colliding half-Maxwellians and a bound on
+// the cancellation in T0; returns false when the estimate cannot decide P_f = 0.
+__device__ inline bool flux_is_zero_estimate(const InstDev &I, const double *a, bool aok, const double *b, bool bok)
+{
+    float r0 = 0.f, m0 = 0.f, my = 0.f, mz = 0.f, e0 = 0.f;
+    const float R = static_cast<float>(I.R);
+    for (int side = 0; side < 2; ++side) {
+        const double *s = side ? b : a;
+        if (!(side ? bok : aok)) continue;
+        const float rho = static_cast<float>(s[0]), U = static_cast<float>(s[1]), V = static_cast<float>(s[2]),
+                    W = static_cast<float>(s[3]), T = static_cast<float>(s[4]);
+        const float lam = 1.0f / (2.0f * R * T);
+        const float sl = sqrtf(lam);
+        const float sg = side ? 1.0f : -1.0f;            // left: u > 0 half; right: u < 0 half
+        const float M0 = 0.5f * erfcf(sg * sl * U);
+        const float tail = -sg * 0.5f * expf(-lam * U * U) / sqrtf(3.14159265f * lam);
+        const float M1 = U * M0 + tail;
+        const float M2 = U * M1 + M0 / (2.0f * lam);
+        r0 += rho * M0;
+        m0 += rho * M1;
+        my += rho * V * M0;
+        mz += rho * W * M0;
+        e0 += 0.5f * rho * (M2 + (V * V + W * W + 1.0f / lam) * M0);
+    }
+    if (!(r0 > 1e-30f)) return false;
+    const float U0 = m0 / r0, V0 = my / r0, W0 = mz / r0;
+    const float kin = 0.5f * (U0 * U0 + V0 * V0 + W0 * W0);
+    const float th = e0 / r0 - kin;
+    // cancellation: the relative error of th is about 1e-6 (e0/r0)/th; require it below 1e-3
+    if (!(th > 1e-3f * (e0 / r0))) return false;
+    const float T0 = th / (1.5f * R);
+    const float t32 = tau_estimate(I, r0, T0);
+    return t32 > 1.05f * static_cast<float>(I.dt);
+}
+
 __device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, const double *b, bool bok,
                                  double *F)
 {
     for (int k = 0; k < 5; ++k) F[k] = 0.0;
+    // P_f = 0 (no wave flux) is decided in single precision when tau_f exceeds dt by over 5%
+    if (flux_is_zero_estimate(I, a, aok, b, bok)) return;
     double ap[4] = {0, 0, 0, 0}, an[4] = {0, 0, 0, 0}, bp[4] = {0, 0, 0, 0}, bn[4] = {0, 0, 0, 0};
     double la = 0.0, lb = 0.0, ra = 0.0, rb = 0.0, ta = 0.0, tb = 0.0;
     if (aok) {

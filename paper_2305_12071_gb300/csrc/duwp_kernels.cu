@@ -145,61 +145,6 @@ __device__ inline Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j,
 }
 
 // ------------------------------------------------------------------------------------------
-// NTC collisions of one cell (Appendix A), one thread, candidates in order.
-// ------------------------------------------------------------------------------------------
-template <typename Rec>
-__device__ void collide_cell(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, double rho_t,
-                             double &cmax, int &ncand, int &nacc)
-{
-    using T = decltype(list[0].xl);
-    ncand = 0;
-    nacc = 0;
-    if (N < 2) return;
-    const double rr = (I.ntc_rate == 1) ? rho_t / I.rho_ref : ((static_cast<double>(N) * I.mp) / I.dx) / I.rho_ref;
-    const double f = (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
-    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * f * cmax;
-    uint32_t w[4];
-    draw(I, id, 1u, step, kRound, w);
-    int64_t nc = static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
-    if (!(nsel < 1e8)) nc = -1;   // reported by the caller as an overflow; no candidates run
-    const double expo = 1.0 - 2.0 * I.upsilon;
-    int acc = 0;
-    for (int64_t k = 0; k < nc; ++k) {
-        draw(I, id, static_cast<uint32_t>(2 * k), step, kCollide, w);
-        const uint32_t a = idx32(w[0], static_cast<uint32_t>(N));
-        uint32_t b = idx32(w[1], static_cast<uint32_t>(N - 1));
-        if (b >= a) ++b;
-        Rec A = list[a], B = list[b];
-        const double au = A.u, av = A.v, aw = A.w, bu = B.u, bv = B.v, bw = B.w;
-        const double d0 = au - bu, d1 = av - bv, d2 = aw - bw;
-        const double cr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-        if (cr > cmax) cmax = cr;
-        const double x = cr / cmax;
-        const double prob = (I.upsilon == 0.0) ? x : pow(x, expo);
-        if (u53(w[2], w[3]) < prob) {
-            uint32_t v[4];
-            draw(I, id, static_cast<uint32_t>(2 * k + 1), step, kCollide, v);
-            const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
-            const double st = sqrt(1.0 - ct * ct);
-            const double ph = kTwoPi * u53(v[2], v[3]);
-            const double c0 = (cr * st) * cos(ph), c1 = (cr * st) * sin(ph), c2 = cr * ct;
-            const double m0 = (au + bu) * 0.5, m1 = (av + bv) * 0.5, m2 = (aw + bw) * 0.5;
-            A.u = store_val(m0 + c0 * 0.5, T());
-            A.v = store_val(m1 + c1 * 0.5, T());
-            A.w = store_val(m2 + c2 * 0.5, T());
-            B.u = store_val(m0 - c0 * 0.5, T());
-            B.v = store_val(m1 - c1 * 0.5, T());
-            B.w = store_val(m2 - c2 * 0.5, T());
-            list[a] = A;
-            list[b] = B;
-            ++acc;
-        }
-    }
-    ncand = static_cast<int>(nc);
-    nacc = acc;
-}
-
-// ------------------------------------------------------------------------------------------
 // Block-wide helpers
 // ------------------------------------------------------------------------------------------
 
@@ -252,45 +197,396 @@ __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
 }
 
 // ------------------------------------------------------------------------------------------
+// NTC collisions of one cell (Appendix A), one warp.  Candidates are taken in order in batches of
+// up to 32: the batch is cut before the first candidate that shares a particle with an earlier
+// one in the batch, and after the first whose c_r raises c_max; inside such a prefix the
+// candidates touch disjoint particles and see the same c_max, so doing them at once gives exactly
+// the sequential result.  The acceptance test (c_r/c_max)^{1-2 upsilon} > u is first decided in
+// FP32 with a margin far above its error; only draws within the margin take the FP64 pow.
+// ------------------------------------------------------------------------------------------
+template <typename Rec>
+__device__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, double rho_t,
+                             double &cmax, int &ncand, int &nacc, int *s_ab)
+{
+    using T = decltype(list[0].xl);
+    const int lane = threadIdx.x & 31;
+    ncand = 0;
+    nacc = 0;
+    if (N < 2) return;
+    const double rr = (I.ntc_rate == 1) ? rho_t / I.rho_ref : ((static_cast<double>(N) * I.mp) / I.dx) / I.rho_ref;
+    const double f = (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
+    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * f * cmax;
+    uint32_t w[4];
+    draw(I, id, 1u, step, kRound, w);
+    int64_t nc = static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
+    if (!(nsel < 1e8)) { ncand = -1; return; }
+    const double expo = 1.0 - 2.0 * I.upsilon;
+    const float expo_f = static_cast<float>(expo);
+    int acc = 0;
+    double cm = cmax;
+    for (int64_t k0 = 0; k0 < nc;) {
+        const int64_t k = k0 + lane;
+        const bool act = k < nc;
+        uint32_t a = 0, b = 0;
+        double ua = 0.0;
+        if (act) {
+            draw(I, id, static_cast<uint32_t>(2 * k), step, kCollide, w);
+            a = idx32(w[0], static_cast<uint32_t>(N));
+            b = idx32(w[1], static_cast<uint32_t>(N - 1));
+            if (b >= a) ++b;
+            ua = u53(w[2], w[3]);
+        }
+        s_ab[lane] = act ? static_cast<int>(a) : -1;
+        s_ab[32 + lane] = act ? static_cast<int>(b) : -2;
+        __syncwarp();
+        bool conf = false;
+        for (int j = 0; j < lane; ++j) {
+            const int aj = s_ab[j], bj = s_ab[32 + j];
+            conf |= (static_cast<int>(a) == aj) | (static_cast<int>(a) == bj) | (static_cast<int>(b) == aj) |
+                    (static_cast<int>(b) == bj);
+        }
+        const unsigned cmask = __ballot_sync(0xffffffffu, act && conf);
+        const int navail = static_cast<int>(min(static_cast<int64_t>(32), nc - k0));
+        const int m1 = cmask ? min(navail, __ffs(cmask) - 1) : navail;
+        Rec A, B;
+        double cr = 0.0;
+        if (lane < m1) {
+            A = list[a];
+            B = list[b];
+            const double d0 = static_cast<double>(A.u) - static_cast<double>(B.u);
+            const double d1 = static_cast<double>(A.v) - static_cast<double>(B.v);
+            const double d2 = static_cast<double>(A.w) - static_cast<double>(B.w);
+            cr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        const unsigned rmask = __ballot_sync(0xffffffffu, lane < m1 && cr > cm);
+        const int fr = rmask ? __ffs(rmask) - 1 : 32;
+        const int m = min(m1, fr + 1);
+        const double cr_r = __shfl_sync(0xffffffffu, cr, fr < 32 ? fr : 0);
+        bool accd = false;
+        if (lane < m) {
+            const double cml = (lane == fr) ? cr : cm;
+            const double x = cr / cml;
+            if (I.upsilon == 0.0) {
+                accd = ua < x;
+            } else if (expo == 0.0) {
+                accd = ua < 1.0;
+            } else {
+                const float pf = exp2f(expo_f * log2f(static_cast<float>(x)));
+                const double p = static_cast<double>(pf);
+                const double margin = 2e-5 * p;
+                if (ua < p - margin) accd = true;
+                else if (ua > p + margin) accd = false;
+                else accd = ua < pow(x, expo);
+            }
+            if (accd) {
+                uint32_t v[4];
+                draw(I, id, static_cast<uint32_t>(2 * k + 1), step, kCollide, v);
+                const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
+                const double st = sqrt(1.0 - ct * ct);
+                double sp, cp;
+                sincos(kTwoPi * u53(v[2], v[3]), &sp, &cp);
+                const double c0 = (cr * st) * cp, c1 = (cr * st) * sp, c2 = cr * ct;
+                const double au = A.u, av = A.v, aw = A.w, bu = B.u, bv = B.v, bw = B.w;
+                const double m0 = (au + bu) * 0.5, mm1 = (av + bv) * 0.5, m2 = (aw + bw) * 0.5;
+                A.u = store_val(m0 + c0 * 0.5, T());
+                A.v = store_val(mm1 + c1 * 0.5, T());
+                A.w = store_val(m2 + c2 * 0.5, T());
+                B.u = store_val(m0 - c0 * 0.5, T());
+                B.v = store_val(mm1 - c1 * 0.5, T());
+                B.w = store_val(m2 - c2 * 0.5, T());
+                list[a] = A;
+                list[b] = B;
+            }
+        }
+        acc += __popc(__ballot_sync(0xffffffffu, accd));
+        if (fr < m) cm = cr_r;
+        __syncwarp();
+        k0 += m;
+    }
+    cmax = cm;
+    ncand = static_cast<int>(nc);
+    nacc = acc;
+}
+
+// ------------------------------------------------------------------------------------------
+// Exact fixed-point sums of particle moments: velocities at 2^-40, |xi|^2/2 at 2^-32.  Integer
+// sums do not depend on the order of accumulation, so the per-cell flux sums are identical for
+// every launch shape, and the global particle-flux ledger telescopes exactly.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ long long fx_vel(float x) { return __float2ll_rn(x * 1099511627776.0f); }
+__device__ __forceinline__ long long fx_vel(double x) { return __double2ll_rn(x * 1099511627776.0); }
+
+// |xi|^2/2 * 2^32: squares split exactly into float pairs (TwoProd by fma), summed error-free.
+__device__ __forceinline__ long long fx_energy(float u, float v, float w)
+{
+    const float pu = u * u, pv = v * v, pw = w * w;
+    const float qu = __fmaf_rn(u, u, -pu), qv = __fmaf_rn(v, v, -pv), qw = __fmaf_rn(w, w, -pw);
+    float s = pu + pv;
+    float bb = s - pu;
+    float e = (pu - (s - bb)) + (pv - bb);
+    const float s2 = s + pw;
+    bb = s2 - s;
+    e += (s - (s2 - bb)) + (pw - bb);
+    const float lo = ((qu + qv) + qw) + e;
+    return __float2ll_rn(s2 * 2147483648.0f) + __float2ll_rn(lo * 2147483648.0f);
+}
+__device__ __forceinline__ long long fx_energy(double u, double v, double w)
+{
+    return __double2ll_rn((u * u + v * v + w * w) * 2147483648.0);
+}
+
+// ------------------------------------------------------------------------------------------
 // Particle kernel
 // ------------------------------------------------------------------------------------------
 struct CellHdr {
-    int b, i, C, ghost, skip;
+    int b, i, ghost, skip;
     int n_in, slots, n_surv, n_new, n_tot;
     int nfb, nfa, fb, fa;
-    int64_t Ra, Sa, La, off_out;
+    long long Ra, Sa, La, off_out;
     int Rn, Sn, Ln;
     double P, rho_t, cmax;
     double q[5];
     int valid;
     int ncand, nacc;
-    int cntL, cntS, cntR;
+    int nL, nS, nR;
 };
 
+constexpr int kMaxWarps = 16;
+
+struct PartShared {
+    CellHdr H;
+    int g;
+    int wcnt[kMaxWarps][3];
+    long long red[kMaxWarps][13];
+    uint64_t scan[32];
+    uint64_t run;
+    int ab[64];
+};
+
+// Stages of one cell after the header: list = the cell's staging area (shared memory or a
+// global slice), cls = one byte per particle.
 template <typename Rec>
-__global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
+__device__ __forceinline__ void process_cell(const EngineDev &E, int rp, int g, PartShared &S, Rec *__restrict__ list,
+                                             uint8_t *__restrict__ cls)
 {
     using T = decltype(Rec().xl);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Rec *sm = reinterpret_cast<Rec *>(smraw);
-    uint8_t *cls = smraw + static_cast<size_t>(E.cell_cap) * sizeof(Rec);
-    __shared__ CellHdr H;
-    __shared__ int s_g;
-    __shared__ uint64_t s_scan[32];
-    __shared__ double s_red[32][13];
-    __shared__ uint64_t s_run;
-
+    CellHdr &H = S.H;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int wp = 1 - rp;
     const Rec *in = static_cast<const Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[wp]);
     const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
     FarItem<Rec> *fa = static_cast<FarItem<Rec> *>(E.far_app);
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const InstDev &I = E.inst[H.b];
+    const uint32_t step = I.step;
+    const uint32_t id = static_cast<uint32_t>(H.i + 1);
+
+    // ---------------- gather the arrived list (sorted order) into the staging area
+    const int n_in = H.n_in;
+    for (int k = tid; k < n_in; k += nt) {
+        int r = k;
+        Rec v;
+        if (r < H.nfb) { v = fs[H.fb + r].rec; }
+        else if ((r -= H.nfb) < H.Rn) { v = ld_rec(in + H.Ra + r); }
+        else if ((r -= H.Rn) < H.Sn) { v = ld_rec(in + H.Sa + r); }
+        else if ((r -= H.Sn) < H.Ln) { v = ld_rec(in + H.La + r); }
+        else { r -= H.Ln; v = fs[H.fa + r].rec; }
+        list[k] = v;
+    }
+    __syncthreads();
+
+    // ---------------- absorption into the wave with probability P (Eq. p), stable compaction
+    int n_surv = n_in;
+    if (!H.ghost && H.P > 0.0) {
+        const double P = H.P;
+        if (tid == 0) S.run = 0;
+        __syncthreads();
+        for (int base = 0; base < n_in; base += nt) {
+            const int k = base + tid;
+            Rec v;
+            int keep = 0;
+            if (k < n_in) {
+                v = list[k];
+                uint32_t w[4];
+                draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
+                keep = !(u53(w[0], w[1]) < P);
+            }
+            uint64_t tot;
+            const uint64_t pos = block_scan_u64(static_cast<uint64_t>(keep), S.scan, &tot);
+            const uint64_t run = S.run;
+            __syncthreads();
+            if (keep) list[run + pos] = v;
+            __syncthreads();
+            if (tid == 0) S.run = run + tot;
+            __syncthreads();
+        }
+        n_surv = static_cast<int>(S.run);
+    }
+
+    // ---------------- re-sampling of (1-P) of the wave (Step 2)
+    if (tid == 0) {
+        H.n_surv = n_surv;
+        if (!H.ghost) {
+            const double rho_w = H.rho_t - static_cast<double>(n_surv) * I.mp_over_dx;
+            H.n_new = H.valid ? static_cast<int>(resample_count(I, id, step, H.P, rho_w)) : 0;
+        }
+        H.n_tot = n_surv + H.n_new;
+        if (H.n_tot > H.slots || H.off_out + H.n_tot > E.capacity) {
+            set_err(E.err, kErrOverflow);
+            H.skip = 1;
+        }
+    }
+    __syncthreads();
+    if (H.skip) return;
+    const int n_tot = H.n_tot;
+    for (int j = tid; j < H.n_new; j += nt) list[n_surv + j] = sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, H.q);
+    __syncthreads();
+
+    // ---------------- collisions (Appendix A), one warp
+    if (!H.ghost && warp == 0) {
+        double cmax = H.cmax;
+        int nc = 0, na = 0;
+        collide_warp<Rec>(I, id, step, list, n_tot, H.rho_t, cmax, nc, na, S.ab);
+        if (lane == 0) {
+            if (nc < 0) { set_err(E.err, kErrOverflow); nc = 0; }
+            H.ncand = nc;
+            H.nacc = na;
+            E.cmax[g] = cmax;
+        }
+    }
+    __syncthreads();
+
+    // ---------------- transport, classification and flux sums (pass A, one chunk per warp)
+    const int chunk = (((n_tot + nw - 1) / nw) + 31) & ~31;
+    const int c0 = min(warp * chunk, n_tot), c1 = min(c0 + chunk, n_tot);
+    long long sL[4] = {0, 0, 0, 0}, sR[4] = {0, 0, 0, 0}, sS[4] = {0, 0, 0, 0};
+    int nlv = 0, cntL = 0, cntS = 0, cntR = 0;
+    const int cell_base = I.cell_base;
+    for (int base = c0; base < c1; base += 32) {
+        const int k = base + lane;
+        int c = 5;
+        if (k < c1) {
+            Rec v = list[k];
+            const T u0 = v.u;
+            T xl = v.xl, uu = v.u;
+            bool refl = false;
+            const int64_t d = transport(I, H.i, xl, uu, refl);
+            v.xl = xl;
+            v.u = uu;
+            if (d < 0) c = 4;
+            else if (d == H.i - 1) c = 0;
+            else if (d == H.i) c = 1;
+            else if (d == H.i + 1) c = 2;
+            else c = 3;
+            if (c == 1) {
+                if (refl) sS[0] += fx_vel(uu) - fx_vel(u0);
+            } else {
+                const long long qv = fx_vel(v.v), qw = fx_vel(v.w), qe = fx_energy(u0, v.v, v.w);
+                ++nlv;
+                sS[0] -= fx_vel(u0); sS[1] -= qv; sS[2] -= qw; sS[3] -= qe;
+                if (c == 0) { sL[0] += fx_vel(uu); sL[1] += qv; sL[2] += qw; sL[3] += qe; }
+                else if (c == 2) { sR[0] += fx_vel(uu); sR[1] += qv; sR[2] += qw; sR[3] += qe; }
+                else if (c == 3) {
+                    const int slot = atomicAdd(&E.far_count[0], 1);
+                    if (slot < E.far_cap) {
+                        FarItem<Rec> it;
+                        it.dest = cell_base + 1 + static_cast<int>(d);
+                        it.src = g;
+                        it.q = k;
+                        it.pad = 0;
+                        it.rec = v;
+                        fa[slot] = it;
+                    } else {
+                        set_err(E.err, kErrOverflow);
+                    }
+                }
+            }
+            list[k] = v;
+            cls[k] = static_cast<uint8_t>(c);
+        }
+        cntL += __popc(__ballot_sync(0xffffffffu, c == 0));
+        cntS += __popc(__ballot_sync(0xffffffffu, c == 1));
+        cntR += __popc(__ballot_sync(0xffffffffu, c == 2));
+    }
+    // per-warp class counts and moment sums
+    {
+        long long vals[13] = {sL[0], sL[1], sL[2], sL[3], sR[0], sR[1], sR[2], sR[3],
+                              sS[0], sS[1], sS[2], sS[3], static_cast<long long>(nlv)};
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < 13; ++j) S.red[warp][j] = vals[j];
+            S.wcnt[warp][0] = cntL;
+            S.wcnt[warp][1] = cntS;
+            S.wcnt[warp][2] = cntR;
+        }
+    }
+    __syncthreads();
+    if (tid < 13) {
+        long long s = 0;
+        for (int w2 = 0; w2 < nw; ++w2) s += S.red[w2][tid];
+        if (tid < 4) E.AL[4 * g + tid] = static_cast<double>(s) * (tid < 3 ? 0x1p-40 : 0x1p-32);
+        else if (tid < 8) E.AR[4 * g + tid - 4] = static_cast<double>(s) * (tid < 7 ? 0x1p-40 : 0x1p-32);
+        else if (tid < 12) E.Aself[5 * g + tid - 7] = static_cast<double>(s) * (tid < 11 ? 0x1p-40 : 0x1p-32);
+        else E.Aself[5 * g] = -static_cast<double>(s);
+    }
+    // warp bases of the three runs
+    int wb[3] = {0, 0, 0}, tot3[3] = {0, 0, 0};
+    for (int w2 = 0; w2 < nw; ++w2) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (w2 < warp) wb[c] += S.wcnt[w2][c];
+            tot3[c] += S.wcnt[w2][c];
+        }
+    }
+    // ---------------- stable partition into the output block [L | S | R] (pass B, no barriers)
+    const long long cbase[3] = {H.off_out, H.off_out + tot3[0], H.off_out + tot3[0] + tot3[1]};
+    int runc[3] = {0, 0, 0};
+    const unsigned lt = (1u << lane) - 1u;
+    for (int base = c0; base < c1; base += 32) {
+        const int k = base + lane;
+        const int c = (k < c1) ? cls[k] : 5;
+        const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
+        const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
+        const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
+        if (c <= 2) {
+            const unsigned mm = (c == 0) ? mL : (c == 1) ? mS : mR;
+            const long long pos = cbase[c] + wb[c] + runc[c] + __popc(mm & lt);
+            st_rec(out + pos, list[k]);
+        }
+        runc[0] += __popc(mL);
+        runc[1] += __popc(mS);
+        runc[2] += __popc(mR);
+    }
+    if (tid == 0) {
+        H.nL = tot3[0];
+        H.nS = tot3[1];
+        H.nR = tot3[2];
+    }
+}
+
+template <typename Rec>
+__global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Rec *sm = reinterpret_cast<Rec *>(smraw);
+    uint8_t *smcls = smraw + static_cast<size_t>(E.cell_cap) * sizeof(Rec);
+    __shared__ PartShared S;
+    CellHdr &H = S.H;
+    const int wp = 1 - rp;
+    const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
+    const int tid = threadIdx.x;
+    Rec *gstage = static_cast<Rec *>(E.stage) + static_cast<size_t>(blockIdx.x) * E.stage_cap;
+    uint8_t *gcls = E.stage_cls + static_cast<size_t>(blockIdx.x) * E.stage_cap;
 
     for (;;) {
-        if (tid == 0) s_g = atomicAdd(E.ticket, 1);
+        if (tid == 0) S.g = atomicAdd(E.ticket, 1);
         __syncthreads();
-        const int g = s_g;
+        const int g = S.g;
         if (g >= E.G) break;
 
         // ---------------- header (one thread)
@@ -298,7 +594,7 @@ __global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
             H.skip = 0;
             H.b = E.cell_inst[g];
             H.ncand = H.nacc = 0;
-            H.cntL = H.cntS = H.cntR = 0;
+            H.nL = H.nS = H.nR = 0;
             H.n_in = H.n_surv = H.n_new = H.n_tot = 0;
             H.nfb = H.nfa = 0;
             H.Rn = H.Sn = H.Ln = 0;
@@ -306,7 +602,6 @@ __global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
                 H.skip = 1;
             } else {
                 const InstDev &I = E.inst[H.b];
-                H.C = I.C;
                 H.i = g - I.cell_base - 1;
                 H.ghost = (H.i < 0) ? 1 : (H.i >= I.C ? 2 : 0);
                 H.slots = E.slots[g];
@@ -322,6 +617,8 @@ __global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
                         for (int k = 0; k < 5; ++k) H.q[k] = q[k];
                         H.valid = ok;
                         H.P = split_fraction(I, q, ok);
+                        H.rho_t = 0.0;
+                        H.cmax = 0.0;
                         H.n_new = ok ? static_cast<int>(resample_count(I, static_cast<uint32_t>(H.i + 1), I.step, H.P, q[0])) : 0;
                     }
                 } else {
@@ -348,216 +645,37 @@ __global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
                     H.fa = mid;
                     H.nfa = hi - mid;
                     H.n_in = H.nfb + H.Rn + H.Sn + H.Ln + H.nfa;
-                    if (H.n_in != E.cnt[g] || H.n_in > E.cell_cap) {
+                    if (H.n_in != E.cnt[g] || H.n_in > H.slots) {
                         set_err(E.err, kErrOverflow);
                         H.skip = 1;
                     }
                 }
-            }
-        }
-        __syncthreads();
-        if (H.skip) {
-            if (tid == 0) {
-                E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0;
-                for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
-                for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
-                E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0;
-            }
-            __syncthreads();
-            continue;
-        }
-        const InstDev &I = E.inst[H.b];
-        const uint32_t step = I.step;
-        const uint32_t id = static_cast<uint32_t>(H.i + 1);
-
-        // ---------------- gather the arrived list into shared memory
-        const int n_in = H.n_in;
-        for (int k = tid; k < n_in; k += nt) {
-            int r = k;
-            Rec v;
-            if (r < H.nfb) { v = fs[H.fb + r].rec; }
-            else if ((r -= H.nfb) < H.Rn) { v = ld_rec(in + H.Ra + r); }
-            else if ((r -= H.Rn) < H.Sn) { v = ld_rec(in + H.Sa + r); }
-            else if ((r -= H.Sn) < H.Ln) { v = ld_rec(in + H.La + r); }
-            else { r -= H.Ln; v = fs[H.fa + r].rec; }
-            sm[k] = v;
-        }
-        __syncthreads();
-
-        // ---------------- absorption into the wave with probability P (Eq. p), stable compaction
-        int n_surv = n_in;
-        if (!H.ghost && H.P > 0.0) {
-            const double P = H.P;
-            if (tid == 0) s_run = 0;
-            __syncthreads();
-            for (int base = 0; base < n_in; base += nt) {
-                const int k = base + tid;
-                Rec v;
-                int keep = 0;
-                if (k < n_in) {
-                    v = sm[k];
-                    uint32_t w[4];
-                    draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
-                    keep = !(u53(w[0], w[1]) < P);
+                if (!H.skip && H.slots > E.cell_cap && H.slots > E.stage_cap) {
+                    set_err(E.err, kErrOverflow);
+                    H.skip = 1;
                 }
-                uint64_t tot;
-                const uint64_t pos = block_scan_u64(static_cast<uint64_t>(keep), s_scan, &tot);
-                const uint64_t run = s_run;
-                __syncthreads();
-                if (keep) sm[run + pos] = v;
-                __syncthreads();
-                if (tid == 0) s_run = run + tot;
-                __syncthreads();
-            }
-            n_surv = static_cast<int>(s_run);
-        }
-
-        // ---------------- re-sampling of (1-P) of the wave (Step 2), then collisions (Appendix A)
-        if (tid == 0) {
-            H.n_surv = n_surv;
-            if (!H.ghost) {
-                const double rho_w = H.rho_t - static_cast<double>(n_surv) * I.mp_over_dx;
-                H.n_new = H.valid ? static_cast<int>(resample_count(I, id, step, H.P, rho_w)) : 0;
-            }
-            H.n_tot = n_surv + H.n_new;
-            if (H.n_tot > H.slots || H.n_tot > E.cell_cap || H.off_out + H.n_tot > E.capacity) {
-                set_err(E.err, kErrOverflow);
-                H.skip = 1;
             }
         }
         __syncthreads();
-        if (H.skip) {
-            if (tid == 0) {
-                E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0;
+        if (!H.skip) {
+            if (H.slots <= E.cell_cap) process_cell<Rec>(E, rp, g, S, sm, smcls);
+            else process_cell<Rec>(E, rp, g, S, gstage, gcls);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int done = !H.skip;
+            if (done && !H.ghost) atomicAdd(&E.inst[H.b].updates, static_cast<unsigned long long>(H.n_tot));
+            E.nL[wp][g] = done ? H.nL : 0;
+            E.nS[wp][g] = done ? H.nS : 0;
+            E.nR[wp][g] = done ? H.nR : 0;
+            E.ncand[g] = done ? H.ncand : 0;
+            E.nacc[g] = done ? H.nacc : 0;
+            E.nabs[g] = done ? H.n_in - H.n_surv : 0;
+            E.nnew[g] = done ? H.n_new : 0;
+            if (!done) {
                 for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
                 for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
             }
-            __syncthreads();
-            continue;
-        }
-        const int n_tot = H.n_tot;
-        for (int j = tid; j < H.n_new; j += nt) sm[n_surv + j] = sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, H.q);
-        __syncthreads();
-        if (!H.ghost && tid == 0) {
-            double cmax = H.cmax;
-            int nc = 0, na = 0;
-            collide_cell<Rec>(I, id, step, sm, n_tot, H.rho_t, cmax, nc, na);
-            if (nc < 0) { set_err(E.err, kErrOverflow); nc = 0; }
-            H.ncand = nc;
-            H.nacc = na;
-            E.cmax[g] = cmax;
-        }
-        __syncthreads();
-
-        // ---------------- transport and classification (pass A)
-        double aL[4] = {0, 0, 0, 0}, aR[4] = {0, 0, 0, 0}, aS[5] = {0, 0, 0, 0, 0};
-        int cL = 0, cS = 0, cR = 0;
-        const int cell_base = I.cell_base;
-        for (int k = tid; k < n_tot; k += nt) {
-            Rec v = sm[k];
-            const double u0 = v.u;
-            T xl = v.xl, uu = v.u;
-            bool refl = false;
-            const int64_t d = transport(I, H.i, xl, uu, refl);
-            v.xl = xl;
-            v.u = uu;
-            const double u1 = uu, vv = v.v, ww = v.w;
-            const double e_pre = 0.5 * (u0 * u0 + vv * vv + ww * ww);
-            const double e_post = 0.5 * (u1 * u1 + vv * vv + ww * ww);
-            int c;
-            if (d < 0) c = 4;
-            else if (d == H.i - 1) c = 0;
-            else if (d == H.i) c = 1;
-            else if (d == H.i + 1) c = 2;
-            else c = 3;
-            if (c == 1) {
-                ++cS;
-                if (refl) aS[1] += u1 - u0;
-            } else {
-                aS[0] -= 1.0; aS[1] -= u0; aS[2] -= vv; aS[3] -= ww; aS[4] -= e_pre;
-                if (c == 0) { ++cL; aL[0] += u1; aL[1] += vv; aL[2] += ww; aL[3] += e_post; }
-                else if (c == 2) { ++cR; aR[0] += u1; aR[1] += vv; aR[2] += ww; aR[3] += e_post; }
-                else if (c == 3) {
-                    const int slot = atomicAdd(&E.far_count[0], 1);
-                    if (slot < E.far_cap) {
-                        FarItem<Rec> it;
-                        it.dest = cell_base + 1 + static_cast<int>(d);
-                        it.src = g;
-                        it.q = k;
-                        it.pad = 0;
-                        it.rec = v;
-                        fa[slot] = it;
-                    } else {
-                        set_err(E.err, kErrOverflow);
-                    }
-                }
-            }
-            sm[k] = v;
-            cls[k] = static_cast<uint8_t>(c);
-        }
-        // reductions of the class counts and moment sums
-        {
-            const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-            double vals[13] = {aL[0], aL[1], aL[2], aL[3], aR[0], aR[1], aR[2], aR[3], aS[0], aS[1], aS[2], aS[3], aS[4]};
-#pragma unroll
-            for (int k = 0; k < 13; ++k) vals[k] = warp_sum(vals[k]);
-            int c3[3] = {cL, cS, cR};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) c3[k] += __shfl_down_sync(0xffffffffu, c3[k], o);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < 13; ++k) s_red[warp][k] = vals[k];
-                atomicAdd(&H.cntL, c3[0]);
-                atomicAdd(&H.cntS, c3[1]);
-                atomicAdd(&H.cntR, c3[2]);
-            }
-            __syncthreads();
-            if (tid < 13) {
-                double s = 0.0;
-                for (int w = 0; w < nw; ++w) s += s_red[w][tid];
-                if (tid < 4) E.AL[4 * g + tid] = s;
-                else if (tid < 8) E.AR[4 * g + tid - 4] = s;
-                else E.Aself[5 * g + tid - 8] = s;
-            }
-        }
-        __syncthreads();
-
-        // ---------------- stable partition into the cell's output block [L | S | R] (pass B)
-        const int nL = H.cntL, nS = H.cntS;
-        if (tid == 0) s_run = 0;
-        __syncthreads();
-        for (int base = 0; base < n_tot; base += nt) {
-            const int k = base + tid;
-            int c = 5;
-            Rec v;
-            if (k < n_tot) { c = cls[k]; v = sm[k]; }
-            const uint64_t f = (c == 0) ? 1ull : (c == 1) ? (1ull << 21) : (c == 2) ? (1ull << 42) : 0ull;
-            uint64_t tot;
-            const uint64_t pre = block_scan_u64(f, s_scan, &tot);
-            const uint64_t run = s_run;
-            if (c <= 2) {
-                const uint64_t msk = (1ull << 21) - 1;
-                const int sh = 21 * c;
-                const int64_t rank = static_cast<int64_t>(((run >> sh) & msk) + ((pre >> sh) & msk));
-                const int64_t basec = (c == 0) ? 0 : (c == 1) ? nL : nL + nS;
-                st_rec(out + H.off_out + basec + rank, v);
-            }
-            __syncthreads();
-            if (tid == 0) s_run = run + tot;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            if (!H.ghost) atomicAdd(&E.inst[H.b].updates, static_cast<unsigned long long>(n_tot));
-            E.nL[wp][g] = H.cntL;
-            E.nS[wp][g] = H.cntS;
-            E.nR[wp][g] = H.cntR;
-            E.ncand[g] = H.ncand;
-            E.nacc[g] = H.nacc;
-            E.nabs[g] = H.n_in - H.n_surv;
-            E.nnew[g] = H.n_new;
         }
         __syncthreads();
     }
@@ -842,7 +960,7 @@ size_t particles_smem_bytes(int fp32, int cell_cap)
 
 static size_t static_smem_particles()
 {
-    return sizeof(CellHdr) + 4 + 32 * 8 + 32 * 13 * 8 + 8 + 64;
+    return sizeof(PartShared) + 64;
 }
 
 int max_cell_capacity(int fp32)

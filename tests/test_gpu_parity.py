@@ -146,3 +146,24 @@ def test_time_average_matches_oracle():
     oa, on = o.avg()
     assert gn == on == 7
     compare_fields(ga, oa, REL64)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_launch_shape_does_not_change_results(precision):
+    # threads per block and the shared-memory list capacity (64 forces the global staging path)
+    p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=8)
+    ref = None
+    for t, c in ((128, 2048), (64, 256), (256, 512), (512, 64)):
+        s = solver(p)
+        s.set_launch(t, c)
+        s.step(6)
+        got = (s.particles(), s.fields()[0], s.counters())
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for k in ref[0]:
+            assert np.array_equal(ref[0][k], got[0][k]), f"{t}x{c}: particles {k}"
+        assert np.array_equal(ref[1], got[1]), f"{t}x{c}: fields"
+        for k in ref[2]:
+            assert np.array_equal(ref[2][k], got[2][k]), f"{t}x{c}: counter {k}"
