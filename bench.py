@@ -226,7 +226,8 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--threads", type=int, default=0, help="particle-kernel threads per cell (0: default)")
+    ap.add_argument("--launch", default="", help="particle-kernel launch shape threads,cell_capacity,reg_capped "
+                                                 "(skips the autotuner)")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances of the batch")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     args = ap.parse_args()
@@ -262,12 +263,14 @@ def main():
     sol.step(args.warmup)
     sol.sync()
     tuned = None
-    if args.threads:
-        sol.set_launch(args.threads)
+    if args.launch:
+        t_l, c_l, r_l = (int(x) for x in args.launch.split(","))
+        sol.set_launch(t_l, c_l, r_l)
+        tuned = {"threads": t_l, "cell_capacity": c_l, "reg_capped": r_l, "candidates_ms": None}
     elif not args.no_tune:
         from paper_2305_12071_gb300 import autotune
-        (t_best, c_best), tune_ms = autotune.tune(sol)
-        tuned = {"threads": t_best, "cell_capacity": c_best, "candidates_ms": tune_ms}
+        (t_best, c_best, r_best), tune_ms = autotune.tune(sol)
+        tuned = {"threads": t_best, "cell_capacity": c_best, "reg_capped": r_best, "candidates_ms": tune_ms}
 
     def barrier():
         if dist is not None:

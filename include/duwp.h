@@ -184,11 +184,13 @@ const char *duwp_last_cuda_error(void);
 
 /* ------------------------------------------------------------------ launch configuration */
 
-/* Launch shape of the particle kernel: threads per cell block (multiple of 32, 32..1024) and the
- * shared-memory capacity in particles per cell (0 keeps the current one).  Used by the
- * autotuner; results do not depend on it.  Errors: DUWP_EINVAL when the capacity is below the
- * automatic minimum or over the shared-memory limit. */
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity);
+/* Launch shape of the particle kernel: threads per cell block (multiple of 32, 32..512), the
+ * number of particles a cell list may hold in shared memory (0 keeps the current one; larger
+ * lists are staged in global memory), and the register budget (reg_capped = 0: unconstrained;
+ * 1: capped so that six 128-thread blocks fit on an SM, threads <= 128).  Used by the
+ * autotuner; results do not depend on it.  Synchronizing.  Errors: DUWP_EINVAL for shapes the
+ * device cannot launch (capacity below 64 or over the shared-memory limit). */
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity, int32_t reg_capped);
 
 /* Capture the per-step launches in CUDA graphs (on = 1, default) or launch them one by one
  * (on = 0, the plain loop). */

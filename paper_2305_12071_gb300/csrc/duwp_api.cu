@@ -174,12 +174,13 @@ struct Carver {
 };
 }  // namespace
 
-int Engine::configure_launch(int threads_, int cell_cap_)
+int Engine::configure_launch(int threads_, int cell_cap_, int variant_)
 {
     if (threads_ < 32 || threads_ > 512 || (threads_ & 31)) return DUWP_EINVAL;
     if (cell_cap_ < 64 || cell_cap_ > max_cell_capacity(fp32)) return DUWP_EINVAL;
+    if (variant_ < 0 || variant_ > 1) return DUWP_EINVAL;
     const size_t sm = particles_smem_bytes(fp32, cell_cap_);
-    const int occ = particles_occupancy(fp32, threads_, sm);
+    const int occ = particles_occupancy(fp32, variant_, threads_, sm);
     if (occ <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
@@ -207,6 +208,7 @@ int Engine::configure_launch(int threads_, int cell_cap_)
         dev.stage_cap = 0;
     }
     threads = threads_;
+    variant = variant_;
     cell_cap = cell_cap_;
     dev.cell_cap = cell_cap_;
     smem = sm;
@@ -407,7 +409,7 @@ int Engine::enqueue_step(cudaEvent_t *ev)
 {
     const int rp = parity;
     if (ev) DUWP_CU(cudaEventRecord(ev[0], stream));
-    DUWP_CU(launch_particles(dev, fp32, rp, grid, threads, smem, stream));
+    DUWP_CU(launch_particles(dev, fp32, variant, rp, grid, threads, smem, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[1], stream));
     DUWP_CU(launch_far_sort(dev, fp32, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[2], stream));
@@ -660,14 +662,14 @@ int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
     return DUWP_OK;
 }
 
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity)
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity, int32_t reg_capped)
 {
     if (!h) return DUWP_EINVAL;
     Engine &E = h->eng;
     const int cc = cell_capacity > 0 ? cell_capacity : E.cell_cap;
     const int rc = E.sync();
     if (rc) return rc;
-    return E.configure_launch(threads, cc);
+    return E.configure_launch(threads, cc, reg_capped ? 1 : 0);
 }
 
 int duwp_use_graphs(duwp_handle *h, int32_t on)

@@ -92,7 +92,9 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, flo
     if (!(fabsf(s) < 1e15f)) return -1;
     const float fk = floorf(s);
     float x = __fsub_rn(s, fk);
-    int64_t k = static_cast<int64_t>(fk);
+    // the integral value fk converts exactly; a 32-bit conversion covers every displacement
+    // below 2^30 cells (the 64-bit one is reserved for larger ones)
+    int64_t k = (fabsf(fk) < 1073741824.0f) ? static_cast<int64_t>(__float2int_rz(fk)) : static_cast<int64_t>(fk);
     if (x >= 1.0f) { x = 0.0f; k += 1; }
     xl = x;
     return apply_walls<float>(I, cell + k, xl, u, refl);
@@ -313,8 +315,27 @@ __device__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *
 // sums do not depend on the order of accumulation, so the per-cell flux sums are identical for
 // every launch shape, and the global particle-flux ledger telescopes exactly.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ long long fx_vel(float x) { return __float2ll_rn(x * 1099511627776.0f); }
+// x * 2^S rounded to the nearest integer (halves away from zero), from the bits of the float with
+// integer arithmetic only; |x| must stay below 2^(62-S) (guarded by the caller's range check).
+template <int S>
+__device__ __forceinline__ long long fx_bits(float x)
+{
+    const unsigned bits = __float_as_uint(x);
+    const unsigned be = (bits >> 23) & 0xffu;
+    const unsigned long long mant = (bits & 0x7fffffu) | (be ? 0x800000u : 0u);
+    const int e = static_cast<int>(be ? be : 1u) - 150 + S;   // |x| 2^S = mant 2^e
+    long long v;
+    if (e >= 0) v = static_cast<long long>(mant << e);
+    else if (e > -32) v = static_cast<long long>((mant + (1ull << (-e - 1))) >> (-e));
+    else v = 0;
+    return (bits >> 31) ? -v : v;
+}
+__device__ __forceinline__ long long fx_vel(float x) { return fx_bits<40>(x); }
 __device__ __forceinline__ long long fx_vel(double x) { return __double2ll_rn(x * 1099511627776.0); }
+// largest velocity component accepted in the exact sums (2^14; |xi|^2 then stays below 2^30):
+// faster particles are reported as overflow
+__device__ __forceinline__ bool fx_in_range(float x) { return fabsf(x) < 16384.0f; }
+__device__ __forceinline__ bool fx_in_range(double x) { return fabs(x) < 16384.0; }
 
 // |xi|^2/2 * 2^32: squares split exactly into float pairs (TwoProd by fma), summed error-free.
 __device__ __forceinline__ long long fx_energy(float u, float v, float w)
@@ -328,7 +349,7 @@ __device__ __forceinline__ long long fx_energy(float u, float v, float w)
     bb = s2 - s;
     e += (s - (s2 - bb)) + (pw - bb);
     const float lo = ((qu + qv) + qw) + e;
-    return __float2ll_rn(s2 * 2147483648.0f) + __float2ll_rn(lo * 2147483648.0f);
+    return fx_bits<31>(s2) + fx_bits<31>(lo);
 }
 __device__ __forceinline__ long long fx_energy(double u, double v, double w)
 {
@@ -478,6 +499,7 @@ __device__ __forceinline__ void process_cell(const EngineDev &E, int rp, int g, 
             else if (d == H.i) c = 1;
             else if (d == H.i + 1) c = 2;
             else c = 3;
+            if (!(fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w))) set_err(E.err, kErrOverflow);
             if (c == 1) {
                 if (refl) sS[0] += fx_vel(uu) - fx_vel(u0);
             } else {
@@ -535,17 +557,14 @@ __device__ __forceinline__ void process_cell(const EngineDev &E, int rp, int g, 
         else E.Aself[5 * g] = -static_cast<double>(s);
     }
     // warp bases of the three runs
-    int wb[3] = {0, 0, 0}, tot3[3] = {0, 0, 0};
+    int wbL = 0, wbS = 0, wbR = 0, tL = 0, tS = 0, tR = 0;
     for (int w2 = 0; w2 < nw; ++w2) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (w2 < warp) wb[c] += S.wcnt[w2][c];
-            tot3[c] += S.wcnt[w2][c];
-        }
+        const int a0 = S.wcnt[w2][0], a1 = S.wcnt[w2][1], a2 = S.wcnt[w2][2];
+        if (w2 < warp) { wbL += a0; wbS += a1; wbR += a2; }
+        tL += a0; tS += a1; tR += a2;
     }
     // ---------------- stable partition into the output block [L | S | R] (pass B, no barriers)
-    const long long cbase[3] = {H.off_out, H.off_out + tot3[0], H.off_out + tot3[0] + tot3[1]};
-    int runc[3] = {0, 0, 0};
+    long long pL = H.off_out + wbL, pS = H.off_out + tL + wbS, pR = H.off_out + tL + tS + wbR;
     const unsigned lt = (1u << lane) - 1u;
     for (int base = c0; base < c1; base += 32) {
         const int k = base + lane;
@@ -555,22 +574,24 @@ __device__ __forceinline__ void process_cell(const EngineDev &E, int rp, int g, 
         const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
         if (c <= 2) {
             const unsigned mm = (c == 0) ? mL : (c == 1) ? mS : mR;
-            const long long pos = cbase[c] + wb[c] + runc[c] + __popc(mm & lt);
-            st_rec(out + pos, list[k]);
+            const long long pb = (c == 0) ? pL : (c == 1) ? pS : pR;
+            st_rec(out + pb + __popc(mm & lt), list[k]);
         }
-        runc[0] += __popc(mL);
-        runc[1] += __popc(mS);
-        runc[2] += __popc(mR);
+        pL += __popc(mL);
+        pS += __popc(mS);
+        pR += __popc(mR);
     }
     if (tid == 0) {
-        H.nL = tot3[0];
-        H.nS = tot3[1];
-        H.nR = tot3[2];
+        H.nL = tL;
+        H.nS = tS;
+        H.nR = tR;
     }
 }
 
-template <typename Rec>
-__global__ void __launch_bounds__(512) k_particles(EngineDev E, int rp)
+// kMinBlocks = 1: registers unconstrained (up to 512 threads per block); kMinBlocks = 6: at most
+// 128 threads and about 80 registers per thread, so that six blocks fit on one SM.
+template <typename Rec, int kMinBlocks>
+__global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_particles(EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     Rec *sm = reinterpret_cast<Rec *>(smraw);
@@ -970,25 +991,35 @@ int max_cell_capacity(int fp32)
     return static_cast<int>((limit - 16) / per);
 }
 
-int particles_occupancy(int fp32, int threads, size_t smem)
+template <typename K>
+static int occupancy_of(K kern, int threads, size_t smem)
 {
     int n = 0;
-    cudaError_t e;
-    if (fp32) {
-        cudaFuncSetAttribute(k_particles<RecF>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_particles<RecF>, threads, smem);
-    } else {
-        cudaFuncSetAttribute(k_particles<RecD>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_particles<RecD>, threads, smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
-    if (e != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_particles(const EngineDev &E, int fp32, int rp, int grid, int threads, size_t smem, cudaStream_t s)
+int particles_occupancy(int fp32, int variant, int threads, size_t smem)
 {
-    if (fp32) k_particles<RecF><<<grid, threads, smem, s>>>(E, rp);
-    else k_particles<RecD><<<grid, threads, smem, s>>>(E, rp);
+    if (variant && threads > 128) return 0;
+    if (fp32) return variant ? occupancy_of(k_particles<RecF, 6>, threads, smem) : occupancy_of(k_particles<RecF, 1>, threads, smem);
+    return variant ? occupancy_of(k_particles<RecD, 6>, threads, smem) : occupancy_of(k_particles<RecD, 1>, threads, smem);
+}
+
+cudaError_t launch_particles(const EngineDev &E, int fp32, int variant, int rp, int grid, int threads, size_t smem,
+                             cudaStream_t s)
+{
+    if (fp32) {
+        if (variant) k_particles<RecF, 6><<<grid, threads, smem, s>>>(E, rp);
+        else k_particles<RecF, 1><<<grid, threads, smem, s>>>(E, rp);
+    } else {
+        if (variant) k_particles<RecD, 6><<<grid, threads, smem, s>>>(E, rp);
+        else k_particles<RecD, 1><<<grid, threads, smem, s>>>(E, rp);
+    }
     return cudaGetLastError();
 }
 

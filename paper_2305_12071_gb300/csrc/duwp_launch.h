@@ -9,7 +9,7 @@ namespace duwp {
 
 // Particle kernel of one step: absorb, re-sample, collide, transport, write the L/S/R runs.
 // rp = parity of the buffer holding the arrived lists.  grid: persistent CTAs.
-cudaError_t launch_particles(const EngineDev &E, int fp32, int rp, int grid, int threads, size_t smem,
+cudaError_t launch_particles(const EngineDev &E, int fp32, int variant, int rp, int grid, int threads, size_t smem,
                              cudaStream_t s);
 // Sort of the particles that moved two or more cells.
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
@@ -27,7 +27,8 @@ cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const do
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
                           int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s);
 // Kernel attributes (dynamic shared memory) of the particle kernel; returns blocks per SM.
-int particles_occupancy(int fp32, int threads, size_t smem);
+// variant 0: registers unconstrained; 1: capped (<= 128 threads, six blocks per SM)
+int particles_occupancy(int fp32, int variant, int threads, size_t smem);
 size_t particles_smem_bytes(int fp32, int cell_cap);
 int max_cell_capacity(int fp32);
 

@@ -271,7 +271,7 @@ int duwp_server_create(const duwp_server_cfg *cfg, duwp_alloc_fn alloc, duwp_fre
     if (rc != DUWP_OK) { delete s; return rc; }
     // shared-memory list capacity for the largest requests of the mix
     const int cc = std::min(max_cell_capacity(s->eng.fp32), cfg->precision == DUWP_FP32 ? 8192 : 4096);
-    const int rc2 = s->eng.configure_launch(s->eng.threads, cc);
+    const int rc2 = s->eng.configure_launch(s->eng.threads, cc, 0);
     if (rc2 != DUWP_OK) { delete s; return rc2; }
     s->resident.assign(static_cast<size_t>(s->eng.max_inst), nullptr);
     s->cells.init(s->eng.G);

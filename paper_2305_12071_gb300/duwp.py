@@ -122,7 +122,7 @@ def load(path: str = LIB_PATH):
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
-        L.duwp_set_launch.argtypes = [vp, i32, i32]
+        L.duwp_set_launch.argtypes = [vp, i32, i32, i32]
         L.duwp_use_graphs.argtypes = [vp, i32]
         L.duwp_num_particles.argtypes = [vp, i32, C.POINTER(i64)]
         L.duwp_get_particles.argtypes = [vp, i32, ip, dp, dp, dp, dp, i64]
@@ -267,8 +267,8 @@ class Solver:
     def use_graphs(self, on: bool):
         _chk(self.L.duwp_use_graphs(self.h, 1 if on else 0), "duwp_use_graphs")
 
-    def set_launch(self, threads: int, cell_capacity: int = 0):
-        _chk(self.L.duwp_set_launch(self.h, int(threads), int(cell_capacity)), "duwp_set_launch")
+    def set_launch(self, threads: int, cell_capacity: int = 0, reg_capped: int = 0):
+        _chk(self.L.duwp_set_launch(self.h, int(threads), int(cell_capacity), int(reg_capped)), "duwp_set_launch")
 
     def n_cells(self, inst: int = 0) -> int:
         return int(self.params[inst]["n_cells"])

@@ -153,9 +153,9 @@ def test_launch_shape_does_not_change_results(precision):
     # threads per block and the shared-memory list capacity (64 forces the global staging path)
     p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=8)
     ref = None
-    for t, c in ((128, 2048), (64, 256), (256, 512), (512, 64)):
+    for t, c, r in ((128, 2048, 0), (64, 256, 0), (256, 512, 0), (512, 64, 0), (128, 1024, 1), (64, 64, 1)):
         s = solver(p)
-        s.set_launch(t, c)
+        s.set_launch(t, c, r)
         s.step(6)
         got = (s.particles(), s.fields()[0], s.counters())
         s.close()
