@@ -226,7 +226,7 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--launch", default="", help="particle-kernel launch shape threads,cell_capacity,reg_capped "
+    ap.add_argument("--launch", default="", help="particle-kernel launch shape threads,reg_capped "
                                                  "(skips the autotuner)")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances of the batch")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
@@ -264,13 +264,13 @@ def main():
     sol.sync()
     tuned = None
     if args.launch:
-        t_l, c_l, r_l = (int(x) for x in args.launch.split(","))
-        sol.set_launch(t_l, c_l, r_l)
-        tuned = {"threads": t_l, "cell_capacity": c_l, "reg_capped": r_l, "candidates_ms": None}
+        t_l, r_l = (int(x) for x in args.launch.split(","))
+        sol.set_launch(t_l, r_l)
+        tuned = {"threads": t_l, "reg_capped": r_l, "candidates_ms": None}
     elif not args.no_tune:
         from paper_2305_12071_gb300 import autotune
-        (t_best, c_best, r_best), tune_ms = autotune.tune(sol)
-        tuned = {"threads": t_best, "cell_capacity": c_best, "reg_capped": r_best, "candidates_ms": tune_ms}
+        (t_best, r_best), tune_ms = autotune.tune(sol)
+        tuned = {"threads": t_best, "reg_capped": r_best, "candidates_ms": tune_ms}
 
     def barrier():
         if dist is not None:
@@ -330,7 +330,7 @@ def main():
         info0 = sol.info(0)
         cfg.update({"particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
                     "cells_total": int(sum(p["n_cells"] for p in plist)),
-                    "capacity_per_buffer": int(info0["capacity"]), "cell_capacity": int(info0["cell_capacity"]),
+                    "capacity_per_buffer": int(info0["capacity"]),
                     "l2": "inputs larger than L2 (particle records exceed 129 MB)", "graphs": "one graph per step",
                     "launch": tuned})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

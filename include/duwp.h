@@ -81,8 +81,8 @@ enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the N
  *   precision           DUWP_FP64 or DUWP_FP32 particle records (all cell quantities are FP64);
  *   eps_mode, flux_mode, ntc_rate   options (DUWP_EPS*, DUWP_FLUX_*, DUWP_NTC_*);
  *   seed                key of the counter-based generator of this instance;
- *   capacity            particle slots per buffer (0: automatic);
- *   cell_capacity       most particles one cell may hold within a step (0: automatic);
+ *   capacity            particle slots per buffer (0: automatic; each cell's output block takes
+ *                       twice the bound on its list after re-sampling);
  *   avg_start           time averages accumulate the states after step avg_start.
  * In a batch all instances must use the same precision.
  */
@@ -100,7 +100,6 @@ typedef struct {
     int32_t precision, eps_mode, flux_mode, ntc_rate;
     uint64_t seed;
     uint64_t capacity;
-    int32_t cell_capacity;
     int32_t avg_start;
 } duwp_params;
 
@@ -115,7 +114,6 @@ typedef struct duwp_handle duwp_handle;
 typedef struct {
     double dx, dt, mp, beta, lambda_ref, mu_ref, c_ref;
     int64_t capacity;        /* particle slots per buffer of the whole handle */
-    int32_t cell_capacity;   /* particles one cell may hold within a step */
     int32_t n_instances;
     int64_t steps_done;      /* steps taken by this instance */
     int64_t particle_updates;/* particles streamed through a step by this instance, all steps so far */
@@ -184,13 +182,11 @@ const char *duwp_last_cuda_error(void);
 
 /* ------------------------------------------------------------------ launch configuration */
 
-/* Launch shape of the particle kernel: threads per cell block (multiple of 32, 32..512), the
- * number of particles a cell list may hold in shared memory (0 keeps the current one; larger
- * lists are staged in global memory), and the register budget (reg_capped = 0: unconstrained;
- * 1: capped so that six 128-thread blocks fit on an SM, threads <= 128).  Used by the
- * autotuner; results do not depend on it.  Synchronizing.  Errors: DUWP_EINVAL for shapes the
- * device cannot launch (capacity below 64 or over the shared-memory limit). */
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity, int32_t reg_capped);
+/* Launch shape of the particle kernel (one warp per cell): threads per block (multiple of 32,
+ * 32..512) and the register budget (reg_capped = 0: unconstrained; 1: capped so that six
+ * 128-thread blocks fit on an SM, threads <= 128).  Used by the autotuner; results do not depend
+ * on it.  Synchronizing.  Errors: DUWP_EINVAL for shapes the device cannot launch. */
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped);
 
 /* Capture the per-step launches in CUDA graphs (on = 1, default) or launch them one by one
  * (on = 0, the plain loop). */

@@ -1,9 +1,8 @@
 """Autotuner of the particle kernel's launch shape.
 
-Three knobs: threads per cell block (the block works on one cell list at a time), the number of
-particles a cell list may hold in shared memory (particles per thread x threads; larger lists are
-staged in a per-block slice of global memory), and the register budget (unconstrained, or capped
-so that six 128-thread blocks fit on an SM).  Together they fix the blocks resident per SM.  The
+Two knobs: threads per block (each warp of the block works through its own cells) and the
+register budget (unconstrained, or capped so that six 128-thread blocks fit on an SM).  Together
+they fix the warps resident per SM.  The
 tuner times a few steps of the caller's own workload for every candidate with CUDA events
 (duwp_step_timed) and keeps the fastest.  Results do not depend on the launch shape (the per-cell
 moment sums are exact fixed-point integers and the partition order is defined by the method), so
@@ -18,10 +17,8 @@ import os
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
 
-CANDIDATES_FP32 = ([(t, c, 0) for t in (64, 128, 256) for c in (512, 1024, 2048, 3072)]
-                   + [(t, c, 1) for t in (64, 128) for c in (512, 1024, 2048)])
-CANDIDATES_FP64 = ([(t, c, 0) for t in (64, 128, 256) for c in (256, 512, 1024, 1536)]
-                   + [(t, c, 1) for t in (64, 128) for c in (256, 512, 1024)])
+CANDIDATES_FP32 = [(t, 0) for t in (32, 64, 128, 256, 512)] + [(t, 1) for t in (32, 64, 128)]
+CANDIDATES_FP64 = CANDIDATES_FP32
 
 
 def _key(solver) -> str:
@@ -51,33 +48,32 @@ def _save(d):
 
 
 def tune(solver, steps: int = 3, use_cache: bool = True, candidates=None):
-    """Pick and apply the fastest (threads, cell_capacity) for this solver's workload.  The solver
+    """Pick and apply the fastest (threads, reg_capped) for this solver's workload.  The solver
     advances by len(candidates) * steps steps.  Returns (choice, timings)."""
     key = _key(solver)
     cache = _load() if use_cache else {}
-    if use_cache and key in cache:
-        t, c, r = cache[key]["threads"], cache[key]["cell_capacity"], cache[key].get("reg_capped", 0)
-        solver.set_launch(t, c, r)
-        return (t, c, r), cache[key].get("timings", {})
+    if use_cache and key in cache and "cell_capacity" not in cache[key]:
+        t, r = cache[key]["threads"], cache[key].get("reg_capped", 0)
+        solver.set_launch(t, r)
+        return (t, r), cache[key].get("timings", {})
     fp32 = solver.params[0].get("precision", "fp64") == "fp32"
     cands = candidates or (CANDIDATES_FP32 if fp32 else CANDIDATES_FP64)
     timings = {}
     best = None
-    for t, c, r in cands:
+    for t, r in cands:
         try:
-            solver.set_launch(t, c, r)
+            solver.set_launch(t, r)
         except Exception:
             continue
         solver.step_timed(1)                     # first launch of a shape: not timed
         k, _ = solver.step_timed(steps)
         ms = float(k[0]) / steps
-        timings[f"{t}x{c}{'r' if r else ''}"] = ms
+        timings[f"{t}{'r' if r else ''}"] = ms
         if best is None or ms < best[0]:
-            best = (ms, t, c, r)
+            best = (ms, t, r)
     if best is None:
         raise RuntimeError("no launch shape could be configured")
-    solver.set_launch(best[1], best[2], best[3])
-    cache[key] = {"threads": best[1], "cell_capacity": best[2], "reg_capped": best[3], "ms": best[0],
-                  "timings": timings}
+    solver.set_launch(best[1], best[2])
+    cache[key] = {"threads": best[1], "reg_capped": best[2], "ms": best[0], "timings": timings}
     _save(cache)
-    return (best[1], best[2], best[3]), timings
+    return (best[1], best[2]), timings

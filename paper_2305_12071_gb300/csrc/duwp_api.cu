@@ -154,7 +154,6 @@ Engine::~Engine()
 {
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
-    dfree(stage, stage_bytes);
     dfree(slab, slab_bytes);
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -174,45 +173,21 @@ struct Carver {
 };
 }  // namespace
 
-int Engine::configure_launch(int threads_, int cell_cap_, int variant_)
+int Engine::configure_launch(int threads_, int variant_)
 {
     if (threads_ < 32 || threads_ > 512 || (threads_ & 31)) return DUWP_EINVAL;
-    if (cell_cap_ < 64 || cell_cap_ > max_cell_capacity(fp32)) return DUWP_EINVAL;
     if (variant_ < 0 || variant_ > 1) return DUWP_EINVAL;
-    const size_t sm = particles_smem_bytes(fp32, cell_cap_);
+    const size_t sm = particles_smem_bytes(fp32, threads_);
     const int occ = particles_occupancy(fp32, variant_, threads_, sm);
     if (occ <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-    const int grid_ = std::max(1, std::min(occ * nsm, G));
-    // global staging for cells whose list exceeds the shared-memory capacity
-    if (stage_cap > cell_cap_) {
-        const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
-        const size_t per = (static_cast<size_t>(stage_cap) * rec + 255) & ~static_cast<size_t>(255);
-        const size_t need = static_cast<size_t>(grid_) * (per + ((static_cast<size_t>(stage_cap) + 255) & ~static_cast<size_t>(255)));
-        if (need > stage_bytes) {
-            DUWP_CU(cudaStreamSynchronize(stream));
-            dfree(stage, stage_bytes);
-            stage = nullptr;
-            stage_bytes = 0;
-            stage = dalloc(need);
-            if (!stage) return DUWP_ENOMEM;
-            stage_bytes = need;
-        }
-        dev.stage = stage;
-        dev.stage_cls = static_cast<uint8_t *>(stage) + static_cast<size_t>(grid_) * per;
-        dev.stage_cap = stage_cap;
-    } else {
-        dev.stage = nullptr;
-        dev.stage_cls = nullptr;
-        dev.stage_cap = 0;
-    }
     threads = threads_;
     variant = variant_;
-    cell_cap = cell_cap_;
-    dev.cell_cap = cell_cap_;
     smem = sm;
-    grid = grid_;
+    // persistent blocks: as many as fit, but no more warps than cells
+    const int warps = threads_ / 32;
+    grid = std::max(1, std::min(occ * nsm, (G + warps - 1) / warps));
     drop_graphs();
     return DUWP_OK;
 }
@@ -250,24 +225,16 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     G = static_cast<int32_t>(cells);
     max_inst = std::max<int32_t>(n, pool_slots);
     if (max_inst < 1) return DUWP_EINVAL;
-    // particle slots: the slot bound of a cell is at most twice its mass in particles (plus 2),
-    // so twice the expected particles covers the re-sampling regimes
-    int64_t cap = 2 * est + 4 * static_cast<int64_t>(G) + 4096;
+    // particle slots: every cell's output block is twice its slot bound, and the slot bound is at
+    // most twice the cell's mass in particles (plus 2) in the re-sampling regimes
+    int64_t cap = 4 * est + 8 * static_cast<int64_t>(G) + 8192;
     uint64_t cap_user = 0;
     for (int32_t b = 0; b < n; ++b) cap_user = std::max<uint64_t>(cap_user, params[b].capacity);
     if (cap_override > 0) cap = cap_override;
     else if (cap_user > 0) cap = static_cast<int64_t>(cap_user);
     if (cap >= (int64_t(1) << 40)) return DUWP_EINVAL;
     capacity = cap;
-    // largest cell list within a step (the slot bound is at most twice the cell's mass in
-    // particles), and the shared-memory share of it
-    int32_t cc = 0;
-    for (int32_t b = 0; b < n; ++b) cc = std::max(cc, params[b].cell_capacity);
-    if (cc <= 0) cc = static_cast<int32_t>(std::ceil(2.5 * max_ppc)) + 64;
-    cc = std::max(cc, 256);
-    stage_cap = cc;
-    cc = std::min(cc, fp32 ? 2048 : 1024);
-    cc = std::min(cc, max_cell_capacity(fp32));
+    (void)max_ppc;
     far_cap = 1 << 16;
 
     const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
@@ -289,7 +256,9 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_slots = c.take<int32_t>(G);
     const size_t o_cnt = c.take<int32_t>(G);
     size_t o_nL[2], o_nS[2], o_nR[2], o_off[2];
+    size_t o_sb[2];
     for (int p = 0; p < 2; ++p) {
+        o_sb[p] = c.take<int32_t>(G);
         o_nL[p] = c.take<int32_t>(G);
         o_nS[p] = c.take<int32_t>(G);
         o_nR[p] = c.take<int32_t>(G);
@@ -314,7 +283,6 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.G = G;
     dev.n_inst = max_inst;
     dev.capacity = capacity;
-    dev.cell_cap = cc;
     dev.far_cap = far_cap;
     dev.inst = reinterpret_cast<InstDev *>(base + o_inst);
     dev.cell_inst = reinterpret_cast<int32_t *>(base + o_cinst);
@@ -331,6 +299,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.slots = reinterpret_cast<int32_t *>(base + o_slots);
     dev.cnt = reinterpret_cast<int32_t *>(base + o_cnt);
     for (int p = 0; p < 2; ++p) {
+        dev.slotsb[p] = reinterpret_cast<int32_t *>(base + o_sb[p]);
         dev.nL[p] = reinterpret_cast<int32_t *>(base + o_nL[p]);
         dev.nS[p] = reinterpret_cast<int32_t *>(base + o_nS[p]);
         dev.nR[p] = reinterpret_cast<int32_t *>(base + o_nR[p]);
@@ -350,7 +319,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.buf[1] = base + o_buf1;
     DUWP_CU(cudaMemsetAsync(dev.cell_inst, 0xff, sizeof(int32_t) * size_t(G), stream));
 
-    int rc = configure_launch(threads, cc);
+    int rc = configure_launch(threads, variant);
     if (rc != DUWP_OK) return rc;
 
     inst.assign(static_cast<size_t>(max_inst), HostInst{});
@@ -650,7 +619,6 @@ int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
     out->mu_ref = hi.d.mu_ref;
     out->c_ref = hi.d.c_ref;
     out->capacity = E.capacity;
-    out->cell_capacity = E.cell_cap;
     int ni = 0;
     for (const auto &x : E.inst) ni += x.active ? 1 : 0;
     out->n_instances = ni;
@@ -662,14 +630,13 @@ int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
     return DUWP_OK;
 }
 
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t cell_capacity, int32_t reg_capped)
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped)
 {
     if (!h) return DUWP_EINVAL;
     Engine &E = h->eng;
-    const int cc = cell_capacity > 0 ? cell_capacity : E.cell_cap;
     const int rc = E.sync();
     if (rc) return rc;
-    return E.configure_launch(threads, cc, reg_capped ? 1 : 0);
+    return E.configure_launch(threads, reg_capped ? 1 : 0);
 }
 
 int duwp_use_graphs(duwp_handle *h, int32_t on)

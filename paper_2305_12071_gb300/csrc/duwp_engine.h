@@ -41,11 +41,7 @@ struct Engine {
     int32_t G = 0;              // flattened cells
     int32_t max_inst = 0;
     int64_t capacity = 0;       // particle slots per buffer
-    int32_t cell_cap = 0;       // shared-memory list capacity of the particle kernel
-    int32_t stage_cap = 0;      // largest cell list within a step (global staging above cell_cap)
     int32_t far_cap = 0;
-    void *stage = nullptr;      // grid x stage_cap records + class bytes
-    size_t stage_bytes = 0;
     int32_t threads = 128;
     int32_t variant = 0;        // particle-kernel register budget (0: unconstrained, 1: occupancy-capped)
     int32_t grid = 0;
@@ -66,7 +62,7 @@ struct Engine {
     ~Engine();
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
                void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);
-    int configure_launch(int threads_, int cell_cap_, int variant_ = 0);
+    int configure_launch(int threads_, int variant_ = 0);
     int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
     int remove_instance(int slot);
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[5]: events around kernels

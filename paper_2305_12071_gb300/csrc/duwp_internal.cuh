@@ -4,9 +4,10 @@
 // Layout in HBM (one engine = a pool of G flattened cells shared by all resident instances):
 //   instance b owns cells [cell_base, cell_base + C + 2): left reservoir (ghost), cells 0..C-1,
 //   right reservoir.  Particles are 16-byte (FP32: xl, u, v, w) or 32-byte (FP64) records in two
-//   buffers used alternately.  After a step every cell s owns one output block in the write
-//   buffer, holding its particles that moved one cell left (L), stayed (S), and moved one cell
-//   right (R), each run in the order the particles had before transport.  The stable sorted list
+//   buffers used alternately.  After a step every cell s owns one output block (twice its slot
+//   bound) in the write buffer, holding its particles that stayed (S, forward from the start),
+//   moved one cell left (L, forward from the middle) and moved one cell right (R, backward from
+//   the end), each run in the order the particles had before transport.  The stable sorted list
 //   of a cell g for the next step is then  [far movers from cells < g-1] R(g-1) S(g) L(g+1)
 //   [far movers from cells > g+1]  -- exactly the stable counting-sort order by new cell, without
 //   a global sort pass.  Particles that moved two or more cells (or wrapped around a periodic
@@ -65,7 +66,6 @@ struct EngineDev {
     int32_t G;                 // flattened cells in the pool
     int32_t n_inst;
     int64_t capacity;          // particle slots per buffer
-    int32_t cell_cap;          // cell lists up to this size are staged in shared memory
     int32_t far_cap;
     InstDev *inst;
     int32_t *cell_inst;        // instance of each flattened cell, -1 = unused
@@ -79,6 +79,7 @@ struct EngineDev {
     double *AL, *AR;           // G x 4: sums (u, v, w, |xi|^2/2) of the L / R runs (post-transport)
     double *Aself;             // G x 5: change of the cell's own particle moments (leavers, reflections)
     int32_t *slots;            // G: upper bound of the cell's list after re-sampling (this step)
+    int32_t *slotsb[2];        // G: the bound each output block was written with, per buffer (block = 2 x bound)
     int32_t *cnt;              // G: particles arriving in the cell (list length this step)
     int32_t *nL[2], *nS[2], *nR[2];
     int64_t *off[2];           // G: first slot of each cell's output block, per buffer
@@ -90,9 +91,6 @@ struct EngineDev {
     int32_t *far_count;        // [0]: appended, [1]: sorted
     int32_t *err;              // first device error
     int32_t *ticket;           // work counter of the particle kernel
-    void *stage;               // per-CTA global staging of cell lists above cell_cap (stage_cap records each)
-    uint8_t *stage_cls;        // per-CTA class bytes of the same
-    int32_t stage_cap;         // particles one cell may hold within a step (global staging)
 };
 
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels

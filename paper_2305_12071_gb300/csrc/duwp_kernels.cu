@@ -119,7 +119,7 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, dou
 // (1,2) -> x, (3,4) -> y, (5,6) -> z.
 // ------------------------------------------------------------------------------------------
 template <typename Rec>
-__device__ inline Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const double *q)
+__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const double *q)
 {
     uint32_t w[16];
 #pragma unroll
@@ -206,22 +206,34 @@ __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
 // the sequential result.  The acceptance test (c_r/c_max)^{1-2 upsilon} > u is first decided in
 // FP32 with a margin far above its error; only draws within the margin take the FP64 pow.
 // ------------------------------------------------------------------------------------------
+// NTC candidate count of a cell with N particles (Appendix A, nondimensional form), rounded with the
+// cell's ROUND draw 1; -1 when the count is absurd (over 1e8).
+__device__ inline int64_t ntc_candidates(const InstDev &I, uint32_t id, uint32_t step, int N, double rho_t, double cmax)
+{
+    if (N < 2) return 0;
+    const double rr = (I.ntc_rate == 1) ? rho_t / I.rho_ref : ((static_cast<double>(N) * I.mp) / I.dx) / I.rho_ref;
+    const double f = (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
+    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * f * cmax;
+    if (!(nsel < 1e8)) return -1;
+    uint32_t w[4];
+    draw(I, id, 1u, step, kRound, w);
+    return static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
+}
+
+// tidx (optional): sorted list indices of the records held in `list` (the touched particles);
+// without it `list` is the whole cell list.
 template <typename Rec>
-__device__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, double rho_t,
-                             double &cmax, int &ncand, int &nacc, int *s_ab)
+__device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, double rho_t,
+                             double &cmax, int &ncand, int &nacc, int *s_ab, const int *tidx, int ntouch)
 {
     using T = decltype(list[0].xl);
     const int lane = threadIdx.x & 31;
     ncand = 0;
     nacc = 0;
     if (N < 2) return;
-    const double rr = (I.ntc_rate == 1) ? rho_t / I.rho_ref : ((static_cast<double>(N) * I.mp) / I.dx) / I.rho_ref;
-    const double f = (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
-    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * f * cmax;
     uint32_t w[4];
-    draw(I, id, 1u, step, kRound, w);
-    int64_t nc = static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
-    if (!(nsel < 1e8)) { ncand = -1; return; }
+    const int64_t nc = ntc_candidates(I, id, step, N, rho_t, cmax);
+    if (nc < 0) { ncand = -1; return; }
     const double expo = 1.0 - 2.0 * I.upsilon;
     const float expo_f = static_cast<float>(expo);
     int acc = 0;
@@ -252,9 +264,18 @@ __device__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *
         const int m1 = cmask ? min(navail, __ffs(cmask) - 1) : navail;
         Rec A, B;
         double cr = 0.0;
+        uint32_t sa = a, sb = b;
+        if (tidx && lane < m1) {
+            int lo = 0, hi = ntouch;
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (tidx[mid] < static_cast<int>(a)) lo = mid + 1; else hi = mid; }
+            sa = static_cast<uint32_t>(lo);
+            lo = 0; hi = ntouch;
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (tidx[mid] < static_cast<int>(b)) lo = mid + 1; else hi = mid; }
+            sb = static_cast<uint32_t>(lo);
+        }
         if (lane < m1) {
-            A = list[a];
-            B = list[b];
+            A = list[sa];
+            B = list[sb];
             const double d0 = static_cast<double>(A.u) - static_cast<double>(B.u);
             const double d1 = static_cast<double>(A.v) - static_cast<double>(B.v);
             const double d2 = static_cast<double>(A.w) - static_cast<double>(B.w);
@@ -296,8 +317,8 @@ __device__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *
                 B.u = store_val(m0 - c0 * 0.5, T());
                 B.v = store_val(mm1 - c1 * 0.5, T());
                 B.w = store_val(m2 - c2 * 0.5, T());
-                list[a] = A;
-                list[b] = B;
+                list[sa] = A;
+                list[sb] = B;
             }
         }
         acc += __popc(__ballot_sync(0xffffffffu, accd));
@@ -357,348 +378,465 @@ __device__ __forceinline__ long long fx_energy(double u, double v, double w)
 }
 
 // ------------------------------------------------------------------------------------------
-// Particle kernel
+// Particle kernel: one warp per cell, no block-wide barriers.
+//
+// Output block of a cell s (2 x slots records, slots = the bound on its list after re-sampling):
+// particles that stay (S) are written forward from the block start, those moving one cell left
+// (L) forward from the middle, those moving one cell right (R) backward from the end; each run
+// keeps the order the particles had before transport.  The sorted list of cell g for the next
+// step reads R(g-1) from its end backwards, then S(g), then L(g+1).
+//
+// Two ways through a cell:
+//   direct  (P = 0 and at most 32 NTC candidates): the candidate pairs are drawn first (they depend
+//           only on counters), the touched particles are copied to shared memory and collided
+//           there, then one streaming pass reads the arrived runs (and samples the re-sampled
+//           particles), substitutes the touched ones, transports and writes;
+//   staged  (P > 0, or more candidates): survivors of the absorption draw and the re-sampled
+//           particles are written to the first half of the cell's own output block, collided
+//           there, then streamed from there (stayers are written back in place, never ahead of
+//           the read position).
 // ------------------------------------------------------------------------------------------
-struct CellHdr {
-    int b, i, ghost, skip;
-    int n_in, slots, n_surv, n_new, n_tot;
-    int nfb, nfa, fb, fa;
-    long long Ra, Sa, La, off_out;
-    int Rn, Sn, Ln;
+constexpr int kTouchCap = 64;
+constexpr int kMaxCand = 32;
+
+template <typename Rec>
+struct WarpShared {
+    int b, i, ghost, skip, staged;
+    int n_in, n_surv, n_new, n_tot, slots;
+    int nfb, fb, Rn, Sn, Ln, nfa, fa;
+    long long Rend, Sa, La, off_out;
     double P, rho_t, cmax;
     double q[5];
-    int valid;
-    int ncand, nacc;
+    int valid, ncand, nacc, ntouch;
     int nL, nS, nR;
-};
-
-constexpr int kMaxWarps = 16;
-
-struct PartShared {
-    CellHdr H;
-    int g;
-    int wcnt[kMaxWarps][3];
-    long long red[kMaxWarps][13];
-    uint64_t scan[32];
-    uint64_t run;
     int ab[64];
+    int tidx[kTouchCap];
+    Rec trec[kTouchCap];
+    long long acc[12][32];   // lane-private fixed-point sums: L (u, v, w, e), R (...), self (...)
 };
 
-// Stages of one cell after the header: list = the cell's staging area (shared memory or a
-// global slice), cls = one byte per particle.
+// Record of position k of the cell's arrived (sorted) list.
 template <typename Rec>
-__device__ __forceinline__ void process_cell(const EngineDev &E, int rp, int g, PartShared &S, Rec *__restrict__ list,
-                                             uint8_t *__restrict__ cls)
+__device__ __forceinline__ Rec fetch_arrived(int k, int nfb, int fb, int Rn, long long Rend, int Sn, long long Sa,
+                                             int Ln, long long La, int fa, const Rec *in, const FarItem<Rec> *fs)
+{
+    int r = k;
+    if (r < nfb) return fs[fb + r].rec;
+    r -= nfb;
+    if (r < Rn) return ld_rec(in + (Rend - 1 - r));
+    r -= Rn;
+    if (r < Sn) return ld_rec(in + (Sa + r));
+    r -= Sn;
+    if (r < Ln) return ld_rec(in + (La + r));
+    r -= Ln;
+    return fs[fa + r].rec;
+}
+
+// Plain (coherent) loads for records written earlier in the same kernel.
+__device__ __forceinline__ RecF ld_rec_rw(const RecF *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return RecF{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ RecD ld_rec_rw(const RecD *p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return RecD{a.x, a.y, b.x, b.y};
+}
+
+template <typename Rec>
+__device__ __forceinline__ int touched_slot(const WarpShared<Rec> &S, int x)
+{
+    int lo = 0, hi = S.ntouch;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (S.tidx[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Header of cell g (lane 0).
+template <typename Rec>
+__device__ __noinline__ void cell_header(const EngineDev &E, int rp, int g, WarpShared<Rec> &S)
+{
+    const int wp = 1 - rp;
+    S.skip = 0;
+    S.staged = 0;
+    S.ncand = S.nacc = 0;
+    S.nL = S.nS = S.nR = 0;
+    S.n_in = S.n_surv = S.n_new = S.n_tot = 0;
+    S.nfb = S.nfa = S.fb = S.fa = 0;
+    S.Rn = S.Sn = S.Ln = 0;
+    S.ntouch = 0;
+    S.b = E.cell_inst[g];
+    if (S.b < 0) { S.skip = 1; return; }
+    const InstDev &I = E.inst[S.b];
+    S.i = g - I.cell_base - 1;
+    S.ghost = (S.i < 0) ? 1 : (S.i >= I.C ? 2 : 0);
+    S.slots = E.slots[g];
+    S.off_out = E.off[wp][g];
+    if (S.off_out + 2 * static_cast<long long>(S.slots) > E.capacity) {
+        set_err(E.err, kErrOverflow);
+        S.skip = 1;
+        return;
+    }
+    const uint32_t step = I.step;
+    if (S.ghost) {
+        const int side = S.ghost - 1;
+        const int bc = side ? I.bc_right : I.bc_left;
+        if (bc != 0) { S.skip = 1; return; }
+        double q[5];
+        const bool ok = ghost_prim(I, side, q, false, q);
+        for (int k = 0; k < 5; ++k) S.q[k] = q[k];
+        S.valid = ok;
+        S.P = split_fraction(I, q, ok);
+        S.rho_t = 0.0;
+        S.cmax = 0.0;
+        S.n_new = ok ? static_cast<int>(resample_count(I, static_cast<uint32_t>(S.i + 1), step, S.P, q[0])) : 0;
+        S.n_tot = S.n_new;
+        if (S.n_tot > S.slots) { set_err(E.err, kErrOverflow); S.skip = 1; }
+        return;
+    }
+    for (int k = 0; k < 5; ++k) S.q[k] = E.prim[5 * g + k];
+    S.valid = E.valid[g];
+    S.P = E.P[g];
+    S.rho_t = E.psi[5 * g];
+    S.cmax = E.cmax[g];
+    S.Rend = E.off[rp][g - 1] + 2 * static_cast<long long>(E.slotsb[rp][g - 1]);
+    S.Rn = E.nR[rp][g - 1];
+    S.Sa = E.off[rp][g];
+    S.Sn = E.nS[rp][g];
+    S.La = E.off[rp][g + 1] + E.slotsb[rp][g + 1];
+    S.Ln = E.nL[rp][g + 1];
+    const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
+    const int nf = E.far_count[1];
+    if (nf > 0) {
+        const int lo = far_lower(fs, nf, g, INT32_MIN);
+        const int mid = far_lower(fs, nf, g, g + 2);
+        const int hi = far_lower(fs, nf, g + 1, INT32_MIN);
+        S.fb = lo;
+        S.nfb = mid - lo;
+        S.fa = mid;
+        S.nfa = hi - mid;
+    }
+    S.n_in = S.nfb + S.Rn + S.Sn + S.Ln + S.nfa;
+    if (S.n_in != E.cnt[g] || S.n_in > S.slots) {
+        set_err(E.err, kErrOverflow);
+        S.skip = 1;
+        return;
+    }
+    if (S.P > 0.0) { S.staged = 1; return; }
+    // P = 0: nothing is absorbed; the re-sampled count and the NTC candidate count are known now
+    const uint32_t id = static_cast<uint32_t>(S.i + 1);
+    S.n_surv = S.n_in;
+    const double rho_w = S.rho_t - static_cast<double>(S.n_in) * I.mp_over_dx;
+    S.n_new = S.valid ? static_cast<int>(resample_count(I, id, step, 0.0, rho_w)) : 0;
+    S.n_tot = S.n_in + S.n_new;
+    if (S.n_tot > S.slots) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
+    const int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, S.cmax);
+    if (nc < 0) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
+    S.ncand = static_cast<int>(nc);
+    if (nc > kMaxCand) S.staged = 1;
+}
+
+struct StreamState {
+    long long pS, pL, pR;                 // next write position of the S, L (forward) and R (backward) runs
+    long long *acc;                       // this lane's column of the warp's fixed-point sums (stride 32)
+    int nlv = 0;
+    bool range_ok = true;
+};
+
+struct StreamCtx {
+    const InstDev *I;
+    const EngineDev *E;
+    int ci, cell_base, g;
+};
+
+// One group of 32 consecutive list positions (lanes in list order): transport, classification,
+// stable writes to the three runs, and the fixed-point sums of what leaves / enters.
+template <typename Rec>
+__device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool valid, int k, Rec *out,
+                                             FarItem<Rec> *fa, StreamState &st)
 {
     using T = decltype(Rec().xl);
-    CellHdr &H = S.H;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int c = 5;
+    if (valid) {
+        const T u0 = v.u;
+        T xl = v.xl, uu = v.u;
+        bool refl = false;
+        const int64_t d = transport(*cx.I, cx.ci, xl, uu, refl);
+        v.xl = xl;
+        v.u = uu;
+        if (d < 0) c = 4;
+        else if (d == cx.ci - 1) c = 0;
+        else if (d == cx.ci) c = 1;
+        else if (d == cx.ci + 1) c = 2;
+        else c = 3;
+        st.range_ok = st.range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
+        long long *a = st.acc;
+        if (c == 1) {
+            if (refl) a[8 * 32] += fx_vel(uu) - fx_vel(u0);
+        } else {
+            const long long qv = fx_vel(v.v), qw = fx_vel(v.w), qe = fx_energy(u0, v.v, v.w);
+            ++st.nlv;
+            a[8 * 32] -= fx_vel(u0); a[9 * 32] -= qv; a[10 * 32] -= qw; a[11 * 32] -= qe;
+            if (c == 0 || c == 2) {
+                long long *b = a + (c == 0 ? 0 : 4 * 32);
+                b[0] += fx_vel(uu); b[32] += qv; b[64] += qw; b[96] += qe;
+            } else if (c == 3) {
+                const EngineDev &E = *cx.E;
+                const int slot = atomicAdd(&E.far_count[0], 1);
+                if (slot < E.far_cap) {
+                    FarItem<Rec> it;
+                    it.dest = cx.cell_base + 1 + static_cast<int>(d);
+                    it.src = cx.g;
+                    it.q = k;
+                    it.pad = 0;
+                    it.rec = v;
+                    fa[slot] = it;
+                } else {
+                    set_err(E.err, kErrOverflow);
+                }
+            }
+        }
+    }
+    const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
+    const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
+    const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
+    if (c == 1) st_rec(out + st.pS + __popc(mS & lt), v);
+    else if (c == 0) st_rec(out + st.pL + __popc(mL & lt), v);
+    else if (c == 2) st_rec(out + st.pR - __popc(mR & lt), v);
+    st.pS += __popc(mS);
+    st.pL += __popc(mL);
+    st.pR -= __popc(mR);
+}
+
+template <typename Rec, int kMinBlocks>
+__global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_particles(EngineDev E, int rp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    WarpShared<Rec> &S = reinterpret_cast<WarpShared<Rec> *>(smraw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int wp = 1 - rp;
     const Rec *in = static_cast<const Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[wp]);
     const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
     FarItem<Rec> *fa = static_cast<FarItem<Rec> *>(E.far_app);
-    const InstDev &I = E.inst[H.b];
-    const uint32_t step = I.step;
-    const uint32_t id = static_cast<uint32_t>(H.i + 1);
-
-    // ---------------- gather the arrived list (sorted order) into the staging area
-    const int n_in = H.n_in;
-    for (int k = tid; k < n_in; k += nt) {
-        int r = k;
-        Rec v;
-        if (r < H.nfb) { v = fs[H.fb + r].rec; }
-        else if ((r -= H.nfb) < H.Rn) { v = ld_rec(in + H.Ra + r); }
-        else if ((r -= H.Rn) < H.Sn) { v = ld_rec(in + H.Sa + r); }
-        else if ((r -= H.Sn) < H.Ln) { v = ld_rec(in + H.La + r); }
-        else { r -= H.Ln; v = fs[H.fa + r].rec; }
-        list[k] = v;
-    }
-    __syncthreads();
-
-    // ---------------- absorption into the wave with probability P (Eq. p), stable compaction
-    int n_surv = n_in;
-    if (!H.ghost && H.P > 0.0) {
-        const double P = H.P;
-        if (tid == 0) S.run = 0;
-        __syncthreads();
-        for (int base = 0; base < n_in; base += nt) {
-            const int k = base + tid;
-            Rec v;
-            int keep = 0;
-            if (k < n_in) {
-                v = list[k];
-                uint32_t w[4];
-                draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
-                keep = !(u53(w[0], w[1]) < P);
-            }
-            uint64_t tot;
-            const uint64_t pos = block_scan_u64(static_cast<uint64_t>(keep), S.scan, &tot);
-            const uint64_t run = S.run;
-            __syncthreads();
-            if (keep) list[run + pos] = v;
-            __syncthreads();
-            if (tid == 0) S.run = run + tot;
-            __syncthreads();
-        }
-        n_surv = static_cast<int>(S.run);
-    }
-
-    // ---------------- re-sampling of (1-P) of the wave (Step 2)
-    if (tid == 0) {
-        H.n_surv = n_surv;
-        if (!H.ghost) {
-            const double rho_w = H.rho_t - static_cast<double>(n_surv) * I.mp_over_dx;
-            H.n_new = H.valid ? static_cast<int>(resample_count(I, id, step, H.P, rho_w)) : 0;
-        }
-        H.n_tot = n_surv + H.n_new;
-        if (H.n_tot > H.slots || H.off_out + H.n_tot > E.capacity) {
-            set_err(E.err, kErrOverflow);
-            H.skip = 1;
-        }
-    }
-    __syncthreads();
-    if (H.skip) return;
-    const int n_tot = H.n_tot;
-    for (int j = tid; j < H.n_new; j += nt) list[n_surv + j] = sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, H.q);
-    __syncthreads();
-
-    // ---------------- collisions (Appendix A), one warp
-    if (!H.ghost && warp == 0) {
-        double cmax = H.cmax;
-        int nc = 0, na = 0;
-        collide_warp<Rec>(I, id, step, list, n_tot, H.rho_t, cmax, nc, na, S.ab);
-        if (lane == 0) {
-            if (nc < 0) { set_err(E.err, kErrOverflow); nc = 0; }
-            H.ncand = nc;
-            H.nacc = na;
-            E.cmax[g] = cmax;
-        }
-    }
-    __syncthreads();
-
-    // ---------------- transport, classification and flux sums (pass A, one chunk per warp)
-    const int chunk = (((n_tot + nw - 1) / nw) + 31) & ~31;
-    const int c0 = min(warp * chunk, n_tot), c1 = min(c0 + chunk, n_tot);
-    long long sL[4] = {0, 0, 0, 0}, sR[4] = {0, 0, 0, 0}, sS[4] = {0, 0, 0, 0};
-    int nlv = 0, cntL = 0, cntS = 0, cntR = 0;
-    const int cell_base = I.cell_base;
-    for (int base = c0; base < c1; base += 32) {
-        const int k = base + lane;
-        int c = 5;
-        if (k < c1) {
-            Rec v = list[k];
-            const T u0 = v.u;
-            T xl = v.xl, uu = v.u;
-            bool refl = false;
-            const int64_t d = transport(I, H.i, xl, uu, refl);
-            v.xl = xl;
-            v.u = uu;
-            if (d < 0) c = 4;
-            else if (d == H.i - 1) c = 0;
-            else if (d == H.i) c = 1;
-            else if (d == H.i + 1) c = 2;
-            else c = 3;
-            if (!(fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w))) set_err(E.err, kErrOverflow);
-            if (c == 1) {
-                if (refl) sS[0] += fx_vel(uu) - fx_vel(u0);
-            } else {
-                const long long qv = fx_vel(v.v), qw = fx_vel(v.w), qe = fx_energy(u0, v.v, v.w);
-                ++nlv;
-                sS[0] -= fx_vel(u0); sS[1] -= qv; sS[2] -= qw; sS[3] -= qe;
-                if (c == 0) { sL[0] += fx_vel(uu); sL[1] += qv; sL[2] += qw; sL[3] += qe; }
-                else if (c == 2) { sR[0] += fx_vel(uu); sR[1] += qv; sR[2] += qw; sR[3] += qe; }
-                else if (c == 3) {
-                    const int slot = atomicAdd(&E.far_count[0], 1);
-                    if (slot < E.far_cap) {
-                        FarItem<Rec> it;
-                        it.dest = cell_base + 1 + static_cast<int>(d);
-                        it.src = g;
-                        it.q = k;
-                        it.pad = 0;
-                        it.rec = v;
-                        fa[slot] = it;
-                    } else {
-                        set_err(E.err, kErrOverflow);
-                    }
-                }
-            }
-            list[k] = v;
-            cls[k] = static_cast<uint8_t>(c);
-        }
-        cntL += __popc(__ballot_sync(0xffffffffu, c == 0));
-        cntS += __popc(__ballot_sync(0xffffffffu, c == 1));
-        cntR += __popc(__ballot_sync(0xffffffffu, c == 2));
-    }
-    // per-warp class counts and moment sums
-    {
-        long long vals[13] = {sL[0], sL[1], sL[2], sL[3], sR[0], sR[1], sR[2], sR[3],
-                              sS[0], sS[1], sS[2], sS[3], static_cast<long long>(nlv)};
-#pragma unroll
-        for (int j = 0; j < 13; ++j) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < 13; ++j) S.red[warp][j] = vals[j];
-            S.wcnt[warp][0] = cntL;
-            S.wcnt[warp][1] = cntS;
-            S.wcnt[warp][2] = cntR;
-        }
-    }
-    __syncthreads();
-    if (tid < 13) {
-        long long s = 0;
-        for (int w2 = 0; w2 < nw; ++w2) s += S.red[w2][tid];
-        if (tid < 4) E.AL[4 * g + tid] = static_cast<double>(s) * (tid < 3 ? 0x1p-40 : 0x1p-32);
-        else if (tid < 8) E.AR[4 * g + tid - 4] = static_cast<double>(s) * (tid < 7 ? 0x1p-40 : 0x1p-32);
-        else if (tid < 12) E.Aself[5 * g + tid - 7] = static_cast<double>(s) * (tid < 11 ? 0x1p-40 : 0x1p-32);
-        else E.Aself[5 * g] = -static_cast<double>(s);
-    }
-    // warp bases of the three runs
-    int wbL = 0, wbS = 0, wbR = 0, tL = 0, tS = 0, tR = 0;
-    for (int w2 = 0; w2 < nw; ++w2) {
-        const int a0 = S.wcnt[w2][0], a1 = S.wcnt[w2][1], a2 = S.wcnt[w2][2];
-        if (w2 < warp) { wbL += a0; wbS += a1; wbR += a2; }
-        tL += a0; tS += a1; tR += a2;
-    }
-    // ---------------- stable partition into the output block [L | S | R] (pass B, no barriers)
-    long long pL = H.off_out + wbL, pS = H.off_out + tL + wbS, pR = H.off_out + tL + tS + wbR;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int base = c0; base < c1; base += 32) {
-        const int k = base + lane;
-        const int c = (k < c1) ? cls[k] : 5;
-        const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
-        const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
-        const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
-        if (c <= 2) {
-            const unsigned mm = (c == 0) ? mL : (c == 1) ? mS : mR;
-            const long long pb = (c == 0) ? pL : (c == 1) ? pS : pR;
-            st_rec(out + pb + __popc(mm & lt), list[k]);
-        }
-        pL += __popc(mL);
-        pS += __popc(mS);
-        pR += __popc(mR);
-    }
-    if (tid == 0) {
-        H.nL = tL;
-        H.nS = tS;
-        H.nR = tR;
-    }
-}
-
-// kMinBlocks = 1: registers unconstrained (up to 512 threads per block); kMinBlocks = 6: at most
-// 128 threads and about 80 registers per thread, so that six blocks fit on one SM.
-template <typename Rec, int kMinBlocks>
-__global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_particles(EngineDev E, int rp)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Rec *sm = reinterpret_cast<Rec *>(smraw);
-    uint8_t *smcls = smraw + static_cast<size_t>(E.cell_cap) * sizeof(Rec);
-    __shared__ PartShared S;
-    CellHdr &H = S.H;
-    const int wp = 1 - rp;
-    const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-    const int tid = threadIdx.x;
-    Rec *gstage = static_cast<Rec *>(E.stage) + static_cast<size_t>(blockIdx.x) * E.stage_cap;
-    uint8_t *gcls = E.stage_cls + static_cast<size_t>(blockIdx.x) * E.stage_cap;
 
     for (;;) {
-        if (tid == 0) S.g = atomicAdd(E.ticket, 1);
-        __syncthreads();
-        const int g = S.g;
+        int g = 0;
+        if (lane == 0) g = atomicAdd(E.ticket, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= E.G) break;
+        if (lane == 0) cell_header<Rec>(E, rp, g, S);
+        __syncwarp();
+        if (!S.skip) {
+            const InstDev &I = E.inst[S.b];
+            const uint32_t step = I.step;
+            const uint32_t id = static_cast<uint32_t>(S.i + 1);
+            const int ci = S.i, cell_base = I.cell_base;
+            const int nfb = S.nfb, fb = S.fb, Rn = S.Rn, Sn = S.Sn, Ln = S.Ln, fa_ = S.fa;
+            const long long Rend = S.Rend, Sa = S.Sa, La = S.La, off = S.off_out;
+            const int slots = S.slots;
+            const int n_in = S.n_in;
+            Rec *stage = out + off;
+            bool ok = true;
 
-        // ---------------- header (one thread)
-        if (tid == 0) {
-            H.skip = 0;
-            H.b = E.cell_inst[g];
-            H.ncand = H.nacc = 0;
-            H.nL = H.nS = H.nR = 0;
-            H.n_in = H.n_surv = H.n_new = H.n_tot = 0;
-            H.nfb = H.nfa = 0;
-            H.Rn = H.Sn = H.Ln = 0;
-            if (H.b < 0) {
-                H.skip = 1;
-            } else {
-                const InstDev &I = E.inst[H.b];
-                H.i = g - I.cell_base - 1;
-                H.ghost = (H.i < 0) ? 1 : (H.i >= I.C ? 2 : 0);
-                H.slots = E.slots[g];
-                H.off_out = E.off[wp][g];
-                if (H.ghost) {
-                    const int side = H.ghost - 1;
-                    const int bc = side ? I.bc_right : I.bc_left;
-                    if (bc != 0) {
-                        H.skip = 1;
-                    } else {
-                        double q[5];
-                        const bool ok = ghost_prim(I, side, q, false, q);
-                        for (int k = 0; k < 5; ++k) H.q[k] = q[k];
-                        H.valid = ok;
-                        H.P = split_fraction(I, q, ok);
-                        H.rho_t = 0.0;
-                        H.cmax = 0.0;
-                        H.n_new = ok ? static_cast<int>(resample_count(I, static_cast<uint32_t>(H.i + 1), I.step, H.P, q[0])) : 0;
+            if (S.staged) {
+                // ---- survivors of the absorption draw (Eq. p) into the first half, in order
+                const double P = S.P;
+                int run = 0;
+                for (int base = 0; base < n_in; base += 32) {
+                    const int k = base + lane;
+                    Rec v;
+                    bool keep = false;
+                    if (k < n_in) {
+                        v = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
+                        keep = true;
+                        if (P > 0.0) {
+                            uint32_t w[4];
+                            draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
+                            keep = !(u53(w[0], w[1]) < P);
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) st_rec(stage + run + __popc(m & lt), v);
+                    run += __popc(m);
+                }
+                if (lane == 0) {
+                    S.n_surv = run;
+                    const double rho_w = S.rho_t - static_cast<double>(run) * I.mp_over_dx;
+                    S.n_new = S.valid ? static_cast<int>(resample_count(I, id, step, P, rho_w)) : 0;
+                    S.n_tot = run + S.n_new;
+                    if (S.n_tot > slots) { set_err(E.err, kErrOverflow); S.skip = 1; }
+                }
+                __syncwarp();
+                if (S.skip) {
+                    ok = false;
+                } else {
+                    // ---- re-sampled particles (Eq. maxsample) after the survivors, then collisions
+                    const int n_surv = S.n_surv;
+                    for (int j = lane; j < S.n_new; j += 32)
+                        st_rec(stage + n_surv + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, S.q));
+                    __syncwarp();
+                    double cmax = S.cmax;
+                    int nc = 0, na = 0;
+                    collide_warp<Rec>(I, id, step, stage, S.n_tot, S.rho_t, cmax, nc, na, S.ab, nullptr, 0);
+                    if (lane == 0) {
+                        if (nc < 0) { set_err(E.err, kErrOverflow); nc = 0; }
+                        S.ncand = nc;
+                        S.nacc = na;
+                        E.cmax[g] = cmax;
+                    }
+                    __syncwarp();
+                }
+            } else if (S.ncand > 0) {
+                // ---- direct way: stage only the particles the candidates touch
+                const int nc = S.ncand, N = S.n_tot;
+                int a = 0x7fffffff, b = 0x7fffffff;
+                if (lane < nc) {
+                    uint32_t w[4];
+                    draw(I, id, static_cast<uint32_t>(2 * lane), step, kCollide, w);
+                    a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
+                    b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
+                    if (b >= a) ++b;
+                }
+                S.ab[lane] = a;
+                S.ab[32 + lane] = b;
+                __syncwarp();
+                // rank sort of the 64 picks, then drop repeats
+                int ra = 0, rb = 0;
+                for (int j = 0; j < 64; ++j) {
+                    const int x = S.ab[j];
+                    ra += (x < a) || (x == a && j < lane);
+                    rb += (x < b) || (x == b && j < 32 + lane);
+                }
+                __syncwarp();
+                S.tidx[ra] = a;
+                S.tidx[rb] = b;
+                __syncwarp();
+                const int v0 = S.tidx[2 * lane], v1 = S.tidx[2 * lane + 1];
+                const int p0 = (2 * lane == 0) ? 0x7ffffffe : S.tidx[2 * lane - 1];
+                const bool k0 = v0 != 0x7fffffff && v0 != p0;
+                const bool k1 = v1 != 0x7fffffff && v1 != v0;
+                const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+                const int before = __popc(m0 & lt) + __popc(m1 & lt);
+                __syncwarp();
+                if (k0) S.tidx[before] = v0;
+                if (k1) S.tidx[before + (k0 ? 1 : 0)] = v1;
+                const int nt = __popc(m0) + __popc(m1);
+                if (lane == 0) S.ntouch = nt;
+                __syncwarp();
+                for (int t = lane; t < nt; t += 32) {
+                    const int x = S.tidx[t];
+                    S.trec[t] = (x < n_in) ? fetch_arrived<Rec>(x, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs)
+                                           : sample_particle<Rec>(I, id, static_cast<uint32_t>(x - n_in), step, S.q);
+                }
+                __syncwarp();
+                double cmax = S.cmax;
+                int ncc = 0, na = 0;
+                collide_warp<Rec>(I, id, step, S.trec, N, S.rho_t, cmax, ncc, na, S.ab, S.tidx, nt);
+                if (lane == 0) {
+                    S.nacc = na;
+                    E.cmax[g] = cmax;
+                }
+                __syncwarp();
+            }
+
+            if (ok) {
+                // ---- streaming pass: transport (Step 3), classification, runs, flux sums
+                const int n_tot = S.n_tot;
+                const int ntouch = S.ntouch;
+                StreamState st;
+                st.pS = off;
+                st.pL = off + slots;
+                st.pR = off + 2 * static_cast<long long>(slots) - 1;
+                st.acc = &S.acc[0][lane];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) S.acc[j][lane] = 0;
+                const StreamCtx ctx{&I, &E, ci, cell_base, g};
+                if (S.staged) {
+                    for (int base = 0; base < n_tot; base += 32) {
+                        const int k = base + lane;
+                        Rec v;
+                        if (k < n_tot) v = ld_rec_rw(stage + k);
+                        stream_group<Rec>(ctx, v, k < n_tot, k, out, fa, st);
                     }
                 } else {
-                    for (int k = 0; k < 5; ++k) H.q[k] = E.prim[5 * g + k];
-                    H.valid = E.valid[g];
-                    H.P = E.P[g];
-                    H.rho_t = E.psi[5 * g];
-                    H.cmax = E.cmax[g];
-                    H.Ra = E.off[rp][g - 1] + E.nL[rp][g - 1] + E.nS[rp][g - 1];
-                    H.Rn = E.nR[rp][g - 1];
-                    H.Sa = E.off[rp][g] + E.nL[rp][g];
-                    H.Sn = E.nS[rp][g];
-                    H.La = E.off[rp][g + 1];
-                    H.Ln = E.nL[rp][g + 1];
-                    const int nf = E.far_count[1];
-                    int lo = 0, mid = 0, hi = 0;
-                    if (nf > 0) {
-                        lo = far_lower(fs, nf, g, INT32_MIN);
-                        mid = far_lower(fs, nf, g, g + 2);
-                        hi = far_lower(fs, nf, g + 1, INT32_MIN);
+                    int tp = 0;   // first touched index not below the current group
+                    for (int base = 0; base < n_in; base += 32) {
+                        const int k = base + lane;
+                        Rec v;
+                        if (k < n_in) {
+                            v = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
+                            for (int t = tp; t < ntouch && S.tidx[t] < base + 32; ++t)
+                                if (S.tidx[t] == k) v = S.trec[t];
+                        }
+                        stream_group<Rec>(ctx, v, k < n_in, k, out, fa, st);
+                        const int hi = min(base + 32, n_in);   // touched re-sampled particles stay for the next loop
+                        while (tp < ntouch && S.tidx[tp] < hi) ++tp;
                     }
-                    H.fb = lo;
-                    H.nfb = mid - lo;
-                    H.fa = mid;
-                    H.nfa = hi - mid;
-                    H.n_in = H.nfb + H.Rn + H.Sn + H.Ln + H.nfa;
-                    if (H.n_in != E.cnt[g] || H.n_in > H.slots) {
-                        set_err(E.err, kErrOverflow);
-                        H.skip = 1;
+                    for (int base = n_in; base < n_tot; base += 32) {
+                        const int k = base + lane;
+                        Rec v;
+                        if (k < n_tot) {
+                            bool hit = false;
+                            for (int t = tp; t < ntouch && S.tidx[t] < base + 32; ++t)
+                                if (S.tidx[t] == k) { v = S.trec[t]; hit = true; }
+                            if (!hit) v = sample_particle<Rec>(I, id, static_cast<uint32_t>(k - n_in), step, S.q);
+                        }
+                        stream_group<Rec>(ctx, v, k < n_tot, k, out, fa, st);
+                        while (tp < ntouch && S.tidx[tp] < base + 32) ++tp;
                     }
                 }
-                if (!H.skip && H.slots > E.cell_cap && H.slots > E.stage_cap) {
-                    set_err(E.err, kErrOverflow);
-                    H.skip = 1;
+                if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
+                int nlv = st.nlv;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) nlv += __shfl_down_sync(0xffffffffu, nlv, o);
+                __syncwarp();
+                if (lane < 12) {
+                    // lane j sums row j over the 32 lane columns (exact integer sum, any order)
+                    long long t = 0;
+                    for (int l = 0; l < 32; ++l) t += S.acc[lane][l];
+                    const double sc = ((lane & 3) == 3) ? 0x1p-32 : 0x1p-40;
+                    const double val = static_cast<double>(t) * sc;
+                    if (lane < 4) E.AL[4 * g + lane] = val;
+                    else if (lane < 8) E.AR[4 * g + lane - 4] = val;
+                    else E.Aself[5 * g + 1 + (lane - 8)] = val;
                 }
-            }
-        }
-        __syncthreads();
-        if (!H.skip) {
-            if (H.slots <= E.cell_cap) process_cell<Rec>(E, rp, g, S, sm, smcls);
-            else process_cell<Rec>(E, rp, g, S, gstage, gcls);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const int done = !H.skip;
-            if (done && !H.ghost) atomicAdd(&E.inst[H.b].updates, static_cast<unsigned long long>(H.n_tot));
-            E.nL[wp][g] = done ? H.nL : 0;
-            E.nS[wp][g] = done ? H.nS : 0;
-            E.nR[wp][g] = done ? H.nR : 0;
-            E.ncand[g] = done ? H.ncand : 0;
-            E.nacc[g] = done ? H.nacc : 0;
-            E.nabs[g] = done ? H.n_in - H.n_surv : 0;
-            E.nnew[g] = done ? H.n_new : 0;
-            if (!done) {
+                if (lane == 0) {
+                    E.Aself[5 * g] = -static_cast<double>(nlv);
+                    S.nS = static_cast<int>(st.pS - off);
+                    S.nL = static_cast<int>(st.pL - (off + slots));
+                    S.nR = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
+                }
+            } else if (lane == 0) {
                 for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
                 for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
+                S.skip = 1;
             }
+        } else if (lane == 0) {
+            for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
+            for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) {
+            const int done = !S.skip;
+            if (done && !S.ghost) atomicAdd(&E.inst[S.b].updates, static_cast<unsigned long long>(S.n_tot));
+            E.nL[wp][g] = done ? S.nL : 0;
+            E.nS[wp][g] = done ? S.nS : 0;
+            E.nR[wp][g] = done ? S.nR : 0;
+            E.slotsb[wp][g] = done ? S.slots : 0;
+            E.ncand[g] = done ? S.ncand : 0;
+            E.nacc[g] = done ? S.nacc : 0;
+            E.nabs[g] = done ? S.n_in - S.n_surv : 0;
+            E.nnew[g] = done ? S.n_new : 0;
+        }
+        __syncwarp();
     }
 }
 
@@ -813,7 +951,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     if (threadIdx.x == 0) {
         int64_t s = 0;
         for (int w = 0; w < kCellBlock / 32; ++w) s += s_w[w];
-        E.blocksum[blockIdx.x] = s;
+        E.blocksum[blockIdx.x] = 2 * s;
     }
 }
 
@@ -840,7 +978,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     }
     __syncthreads();
     // exclusive scan of the slots inside the block
-    const int64_t v = (g < E.G) ? E.slots[g] : 0;
+    const int64_t v = (g < E.G) ? 2 * static_cast<int64_t>(E.slots[g]) : 0;
     int64_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -907,7 +1045,7 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     const InstDev &I = E.inst[b];
     E.cell_inst[g] = b;
     const int i = g - I.cell_base - 1;
-    for (int p = 0; p < 2; ++p) { E.nL[p][g] = 0; E.nS[p][g] = 0; E.nR[p][g] = 0; E.off[p][g] = 0; }
+    for (int p = 0; p < 2; ++p) { E.nL[p][g] = 0; E.nS[p][g] = 0; E.nR[p][g] = 0; E.off[p][g] = 0; E.slotsb[p][g] = 0; }
     for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
     for (int k = 0; k < 5; ++k) { E.Aself[5 * g + k] = 0.0; E.avg[5 * g + k] = 0.0; E.flux[5 * g + k] = 0.0; E.psi[5 * g + k] = 0.0; E.prim[5 * g + k] = 0.0; }
     E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0; E.cnt[g] = 0; E.slots[g] = 0; E.valid[g] = 0; E.P[g] = 0.0; E.cmax[g] = 0.0;
@@ -939,11 +1077,11 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
         mid = far_lower(fs, nf, g, g + 2);
         hi = far_lower(fs, nf, g + 1, INT32_MIN);
     }
-    const int64_t Ra = E.off[rp][g - 1] + E.nL[rp][g - 1] + E.nS[rp][g - 1];
+    const int64_t Rend = E.off[rp][g - 1] + 2 * static_cast<int64_t>(E.slotsb[rp][g - 1]);
     const int Rn = E.nR[rp][g - 1];
-    const int64_t Sa = E.off[rp][g] + E.nL[rp][g];
+    const int64_t Sa = E.off[rp][g];
     const int Sn = E.nS[rp][g];
-    const int64_t La = E.off[rp][g + 1];
+    const int64_t La = E.off[rp][g + 1] + E.slotsb[rp][g + 1];
     const int Ln = E.nL[rp][g + 1];
     const int nfb = mid - lo, nfa = hi - mid;
     const int n = nfb + Rn + Sn + Ln + nfa;
@@ -957,7 +1095,7 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
         int r = k;
         Rec x;
         if (r < nfb) x = fs[lo + r].rec;
-        else if ((r -= nfb) < Rn) x = in[Ra + r];
+        else if ((r -= nfb) < Rn) x = in[Rend - 1 - r];
         else if ((r -= Rn) < Sn) x = in[Sa + r];
         else if ((r -= Sn) < Ln) x = in[La + r];
         else { r -= Ln; x = fs[mid + r].rec; }
@@ -972,23 +1110,10 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 // ------------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------------
-size_t particles_smem_bytes(int fp32, int cell_cap)
+size_t particles_smem_bytes(int fp32, int threads)
 {
-    const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
-    size_t b = static_cast<size_t>(cell_cap) * rec + static_cast<size_t>(cell_cap);
-    return (b + 15) & ~static_cast<size_t>(15);
-}
-
-static size_t static_smem_particles()
-{
-    return sizeof(PartShared) + 64;
-}
-
-int max_cell_capacity(int fp32)
-{
-    const size_t limit = 227 * 1024 - static_smem_particles();
-    const size_t per = (fp32 ? sizeof(RecF) : sizeof(RecD)) + 1;
-    return static_cast<int>((limit - 16) / per);
+    const size_t per = fp32 ? sizeof(WarpShared<RecF>) : sizeof(WarpShared<RecD>);
+    return per * static_cast<size_t>(threads / 32);
 }
 
 template <typename K>

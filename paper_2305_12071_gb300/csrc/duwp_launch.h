@@ -29,7 +29,7 @@ cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, i
 // Kernel attributes (dynamic shared memory) of the particle kernel; returns blocks per SM.
 // variant 0: registers unconstrained; 1: capped (<= 128 threads, six blocks per SM)
 int particles_occupancy(int fp32, int variant, int threads, size_t smem);
-size_t particles_smem_bytes(int fp32, int cell_cap);
-int max_cell_capacity(int fp32);
+// dynamic shared memory of a particle-kernel block (one slice per warp)
+size_t particles_smem_bytes(int fp32, int threads);
 
 }  // namespace duwp

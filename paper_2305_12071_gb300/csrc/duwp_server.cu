@@ -105,12 +105,7 @@ struct duwp_server {
 
     int64_t footprint(const HostInst &h) const
     {
-        return 2 * h.est_particles + 4 * static_cast<int64_t>(h.p.n_cells + 2) + 64;
-    }
-    int32_t cell_need(const duwp_params &p) const
-    {
-        const double rmax = std::max(p.left.rho, p.right.rho) / p.rho_ref;
-        return static_cast<int32_t>(std::ceil(2.0 * rmax * p.ppc_ref)) + 64;
+        return 4 * h.est_particles + 8 * static_cast<int64_t>(h.p.n_cells + 2) + 64;
     }
 
     void run();
@@ -269,10 +264,6 @@ int duwp_server_create(const duwp_server_cfg *cfg, duwp_alloc_fn alloc, duwp_fre
     const int rc = s->eng.create(&dummy, 0, static_cast<int32_t>(cells), cfg->max_slots, cap, cfg->stream, alloc,
                                  free_fn, alloc_ctx);
     if (rc != DUWP_OK) { delete s; return rc; }
-    // shared-memory list capacity for the largest requests of the mix
-    const int cc = std::min(max_cell_capacity(s->eng.fp32), cfg->precision == DUWP_FP32 ? 8192 : 4096);
-    const int rc2 = s->eng.configure_launch(s->eng.threads, cc, 0);
-    if (rc2 != DUWP_OK) { delete s; return rc2; }
     s->resident.assign(static_cast<size_t>(s->eng.max_inst), nullptr);
     s->cells.init(s->eng.G);
     s->worker = std::thread([s] { s->run(); });
@@ -293,7 +284,7 @@ int duwp_submit(duwp_server *s, const duwp_params *params, int32_t n_steps, uint
     r->n_steps = n_steps;
     r->reserve = s->footprint(h);
     r->t_submit = Clock::now();
-    if (r->reserve > s->eng.capacity || params->n_cells + 2 > s->eng.G || s->cell_need(*params) > s->eng.cell_cap) {
+    if (r->reserve > s->eng.capacity || params->n_cells + 2 > s->eng.G) {
         delete r;
         return DUWP_EINVAL;
     }

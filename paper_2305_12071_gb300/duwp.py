@@ -62,7 +62,6 @@ class Params(C.Structure):
         ("precision", C.c_int32), ("eps_mode", C.c_int32), ("flux_mode", C.c_int32), ("ntc_rate", C.c_int32),
         ("seed", C.c_uint64),
         ("capacity", C.c_uint64),
-        ("cell_capacity", C.c_int32),
         ("avg_start", C.c_int32),
     ]
 
@@ -70,7 +69,7 @@ class Params(C.Structure):
 class Info(C.Structure):
     _fields_ = [("dx", C.c_double), ("dt", C.c_double), ("mp", C.c_double), ("beta", C.c_double),
                 ("lambda_ref", C.c_double), ("mu_ref", C.c_double), ("c_ref", C.c_double),
-                ("capacity", C.c_int64), ("cell_capacity", C.c_int32), ("n_instances", C.c_int32),
+                ("capacity", C.c_int64), ("n_instances", C.c_int32),
                 ("steps_done", C.c_int64), ("particle_updates", C.c_int64)]
 
 
@@ -122,7 +121,7 @@ def load(path: str = LIB_PATH):
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
-        L.duwp_set_launch.argtypes = [vp, i32, i32, i32]
+        L.duwp_set_launch.argtypes = [vp, i32, i32]
         L.duwp_use_graphs.argtypes = [vp, i32]
         L.duwp_num_particles.argtypes = [vp, i32, C.POINTER(i64)]
         L.duwp_get_particles.argtypes = [vp, i32, ip, dp, dp, dp, dp, i64]
@@ -168,7 +167,6 @@ def make_params(p: dict) -> Params:
     s.ntc_rate = NTC[p.get("ntc_rate", "particle")]
     s.seed = int(p.get("seed", 1)) & 0xFFFFFFFFFFFFFFFF
     s.capacity = int(p.get("capacity", 0))
-    s.cell_capacity = int(p.get("cell_capacity", 0))
     s.avg_start = int(p.get("avg_start", 0))
     return s
 
@@ -267,8 +265,8 @@ class Solver:
     def use_graphs(self, on: bool):
         _chk(self.L.duwp_use_graphs(self.h, 1 if on else 0), "duwp_use_graphs")
 
-    def set_launch(self, threads: int, cell_capacity: int = 0, reg_capped: int = 0):
-        _chk(self.L.duwp_set_launch(self.h, int(threads), int(cell_capacity), int(reg_capped)), "duwp_set_launch")
+    def set_launch(self, threads: int, reg_capped: int = 0):
+        _chk(self.L.duwp_set_launch(self.h, int(threads), int(reg_capped)), "duwp_set_launch")
 
     def n_cells(self, inst: int = 0) -> int:
         return int(self.params[inst]["n_cells"])
