@@ -103,6 +103,8 @@ int derive_instance(const duwp_params &p, HostInst &o)
     if (d.upsilon == 0.0) d.c_ref = std::sqrt(4.0 * p.R * p.T_ref);
     else d.c_ref = std::sqrt(4.0 * p.R * p.T_ref) / std::pow(std::tgamma(2.5 - p.omega), 0.5 / d.upsilon);
     d.ntc_A = d.dt / (2.0 * std::sqrt(2.0) * o.lambda_ref);
+    d.ntc_rr = (d.mp / d.dx) / p.rho_ref;
+    d.inv_rho_ref = 1.0 / p.rho_ref;
     const duwp_state *st[2] = {&p.left, &p.right};
     for (int s = 0; s < 2; ++s) {
         double *q = s ? d.right : d.left;
@@ -248,6 +250,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_valid = c.take<int32_t>(G);
     const size_t o_P = c.take<double>(G);
     const size_t o_cmax = c.take<double>(G);
+    const size_t o_fmaj = c.take<double>(G);
     const size_t o_flux = c.take<double>(5 * size_t(G));
     const size_t o_avg = c.take<double>(5 * size_t(G));
     const size_t o_AL = c.take<double>(4 * size_t(G));
@@ -291,6 +294,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.valid = reinterpret_cast<int32_t *>(base + o_valid);
     dev.P = reinterpret_cast<double *>(base + o_P);
     dev.cmax = reinterpret_cast<double *>(base + o_cmax);
+    dev.fmaj = reinterpret_cast<double *>(base + o_fmaj);
     dev.flux = reinterpret_cast<double *>(base + o_flux);
     dev.avg = reinterpret_cast<double *>(base + o_avg);
     dev.AL = reinterpret_cast<double *>(base + o_AL);

@@ -48,6 +48,8 @@ struct InstDev {
     unsigned long long updates;   // particles streamed by this instance (interior cells), all steps
     double dx, dt, dtdx, mp, dx_over_mp, mp_over_dx;
     double R, Pr, omega, T_ref, rho_ref, mu_ref, upsilon, c_ref, ntc_A;
+    double ntc_rr;          // m_p / (dx rho_ref): particle density ratio per particle
+    double inv_rho_ref;
     float dtdx_f;
     float pad0;
     double left[5], right[5];   // reservoir primitive states (rho, u, v, w, T)
@@ -74,6 +76,7 @@ struct EngineDev {
     int32_t *valid;            // G: primitive state usable (rho > 0, T > 0)
     double *P;                 // G: absorption fraction, Eq. (p)
     double *cmax;              // G: NTC majorant
+    double *fmaj;              // G: (c_max / c_ref)^{-2 upsilon} of the current c_max
     double *flux;              // G x 5: wave flux at the interface between g and g+1
     double *avg;               // G x 5: time-average accumulator of Psi_t
     double *AL, *AR;           // G x 4: sums (u, v, w, |xi|^2/2) of the L / R runs (post-transport)

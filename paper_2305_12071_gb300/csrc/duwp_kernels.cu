@@ -206,34 +206,64 @@ __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
 // the sequential result.  The acceptance test (c_r/c_max)^{1-2 upsilon} > u is first decided in
 // FP32 with a margin far above its error; only draws within the margin take the FP64 pow.
 // ------------------------------------------------------------------------------------------
+// Majorant factor (c_max/c_ref)^{-2 upsilon} of the NTC count; kept per cell and recomputed only when
+// c_max is raised.
+__device__ inline double majorant_factor(const InstDev &I, double cmax)
+{
+    return (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
+}
+
 // NTC candidate count of a cell with N particles (Appendix A, nondimensional form), rounded with the
-// cell's ROUND draw 1; -1 when the count is absurd (over 1e8).
-__device__ inline int64_t ntc_candidates(const InstDev &I, uint32_t id, uint32_t step, int N, double rho_t, double cmax)
+// cell's ROUND draw 1; -1 when the count is absurd (over 1e8).  The density ratio uses the
+// precomputed m_p/(dx rho_ref) and the majorant factor comes from the per-cell cache, so the product
+// may differ from the plain left-to-right evaluation by a few ulps; the rounded count differs only
+// when N_sel + u lies within those ulps of an integer.
+__device__ inline int64_t ntc_candidates(const InstDev &I, uint32_t id, uint32_t step, int N, double rho_t, double cmax,
+                                         double fmaj)
 {
     if (N < 2) return 0;
-    const double rr = (I.ntc_rate == 1) ? rho_t / I.rho_ref : ((static_cast<double>(N) * I.mp) / I.dx) / I.rho_ref;
-    const double f = (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
-    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * f * cmax;
+    const double rr = (I.ntc_rate == 1) ? rho_t * I.inv_rho_ref : static_cast<double>(N) * I.ntc_rr;
+    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * fmaj * cmax;
     if (!(nsel < 1e8)) return -1;
     uint32_t w[4];
     draw(I, id, 1u, step, kRound, w);
     return static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
 }
 
-// tidx (optional): sorted list indices of the records held in `list` (the touched particles);
-// without it `list` is the whole cell list.
+// Relative speed of two records, single precision (relative error below 1e-6).
+__device__ __forceinline__ float rel_speed_f32(const RecF &A, const RecF &B)
+{
+    const float d0 = A.u - B.u, d1 = A.v - B.v, d2 = A.w - B.w;
+    return sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+}
+__device__ __forceinline__ float rel_speed_f32(const RecD &A, const RecD &B)
+{
+    const float d0 = static_cast<float>(A.u - B.u), d1 = static_cast<float>(A.v - B.v), d2 = static_cast<float>(A.w - B.w);
+    return sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+}
 template <typename Rec>
-__device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, double rho_t,
-                             double &cmax, int &ncand, int &nacc, int *s_ab, const int *tidx, int ntouch)
+__device__ __forceinline__ double rel_speed(const Rec &A, const Rec &B)
+{
+    const double d0 = static_cast<double>(A.u) - static_cast<double>(B.u);
+    const double d1 = static_cast<double>(A.v) - static_cast<double>(B.v);
+    const double d2 = static_cast<double>(A.w) - static_cast<double>(B.w);
+    return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// The nc candidates of a cell in order (nc from ntc_candidates).  tidx (optional): sorted list
+// indices of the records held in `list` (the touched particles); without it `list` is the whole
+// cell list.  Both the test c_r > c_max and the acceptance u < (c_r/c_max)^{1-2 upsilon} are first
+// decided in single precision with margins far above its error; exact double-precision values are
+// computed for draws inside the margins and for every accepted pair (its scattering).
+template <typename Rec>
+__device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, int64_t nc,
+                                          double &cmax, int &nacc, int *s_ab, const int *tidx, int ntouch)
 {
     using T = decltype(list[0].xl);
     const int lane = threadIdx.x & 31;
-    ncand = 0;
     nacc = 0;
-    if (N < 2) return;
+    if (N < 2 || nc <= 0) return;
     uint32_t w[4];
-    const int64_t nc = ntc_candidates(I, id, step, N, rho_t, cmax);
-    if (nc < 0) { ncand = -1; return; }
     const double expo = 1.0 - 2.0 * I.upsilon;
     const float expo_f = static_cast<float>(expo);
     int acc = 0;
@@ -263,7 +293,9 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
         const int navail = static_cast<int>(min(static_cast<int64_t>(32), nc - k0));
         const int m1 = cmask ? min(navail, __ffs(cmask) - 1) : navail;
         Rec A, B;
+        float cr32 = 0.f;
         double cr = 0.0;
+        bool exact = false;
         uint32_t sa = a, sb = b;
         if (tidx && lane < m1) {
             int lo = 0, hi = ntouch;
@@ -273,35 +305,41 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
             while (lo < hi) { const int mid = (lo + hi) >> 1; if (tidx[mid] < static_cast<int>(b)) lo = mid + 1; else hi = mid; }
             sb = static_cast<uint32_t>(lo);
         }
+        const float cm32 = static_cast<float>(cm);
         if (lane < m1) {
             A = list[sa];
             B = list[sb];
-            const double d0 = static_cast<double>(A.u) - static_cast<double>(B.u);
-            const double d1 = static_cast<double>(A.v) - static_cast<double>(B.v);
-            const double d2 = static_cast<double>(A.w) - static_cast<double>(B.w);
-            cr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            cr32 = rel_speed_f32(A, B);
+            if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
+                cr = rel_speed(A, B);
+                exact = true;
+            }
         }
-        const unsigned rmask = __ballot_sync(0xffffffffu, lane < m1 && cr > cm);
+        const unsigned rmask = __ballot_sync(0xffffffffu, lane < m1 && exact && cr > cm);
         const int fr = rmask ? __ffs(rmask) - 1 : 32;
         const int m = min(m1, fr + 1);
         const double cr_r = __shfl_sync(0xffffffffu, cr, fr < 32 ? fr : 0);
         bool accd = false;
         if (lane < m) {
-            const double cml = (lane == fr) ? cr : cm;
-            const double x = cr / cml;
-            if (I.upsilon == 0.0) {
-                accd = ua < x;
+            if (lane == fr) {
+                accd = true;                    // c_max = c_r: acceptance probability 1
             } else if (expo == 0.0) {
                 accd = ua < 1.0;
             } else {
-                const float pf = exp2f(expo_f * log2f(static_cast<float>(x)));
-                const double p = static_cast<double>(pf);
-                const double margin = 2e-5 * p;
+                const float x32 = cr32 / cm32;
+                const float p32 = (I.upsilon == 0.0) ? x32 : exp2f(expo_f * log2f(x32));
+                const double p = static_cast<double>(p32);
+                const double margin = 1e-4 * p + 1e-7;
                 if (ua < p - margin) accd = true;
                 else if (ua > p + margin) accd = false;
-                else accd = ua < pow(x, expo);
+                else {
+                    if (!exact) { cr = rel_speed(A, B); exact = true; }
+                    const double x = cr / cm;
+                    accd = ua < ((I.upsilon == 0.0) ? x : pow(x, expo));
+                }
             }
             if (accd) {
+                if (!exact) cr = rel_speed(A, B);
                 uint32_t v[4];
                 draw(I, id, static_cast<uint32_t>(2 * k + 1), step, kCollide, v);
                 const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
@@ -327,7 +365,6 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
         k0 += m;
     }
     cmax = cm;
-    ncand = static_cast<int>(nc);
     nacc = acc;
 }
 
@@ -534,7 +571,7 @@ __device__ __noinline__ void cell_header(const EngineDev &E, int rp, int g, Warp
     S.n_new = S.valid ? static_cast<int>(resample_count(I, id, step, 0.0, rho_w)) : 0;
     S.n_tot = S.n_in + S.n_new;
     if (S.n_tot > S.slots) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
-    const int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, S.cmax);
+    const int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, S.cmax, E.fmaj[g]);
     if (nc < 0) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
     S.ncand = static_cast<int>(nc);
     if (nc > kMaxCand) S.staged = 1;
@@ -684,13 +721,20 @@ __global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_par
                         st_rec(stage + n_surv + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, S.q));
                     __syncwarp();
                     double cmax = S.cmax;
-                    int nc = 0, na = 0;
-                    collide_warp<Rec>(I, id, step, stage, S.n_tot, S.rho_t, cmax, nc, na, S.ab, nullptr, 0);
+                    int na = 0;
+                    int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, cmax, E.fmaj[g]);
+                    if (nc < 0) {
+                        if (lane == 0) set_err(E.err, kErrOverflow);
+                        nc = 0;
+                    }
+                    collide_warp<Rec>(I, id, step, stage, S.n_tot, nc, cmax, na, S.ab, nullptr, 0);
                     if (lane == 0) {
-                        if (nc < 0) { set_err(E.err, kErrOverflow); nc = 0; }
-                        S.ncand = nc;
+                        S.ncand = static_cast<int>(nc);
                         S.nacc = na;
-                        E.cmax[g] = cmax;
+                        if (cmax != S.cmax) {
+                            E.cmax[g] = cmax;
+                            E.fmaj[g] = majorant_factor(I, cmax);
+                        }
                     }
                     __syncwarp();
                 }
@@ -738,11 +782,14 @@ __global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_par
                 }
                 __syncwarp();
                 double cmax = S.cmax;
-                int ncc = 0, na = 0;
-                collide_warp<Rec>(I, id, step, S.trec, N, S.rho_t, cmax, ncc, na, S.ab, S.tidx, nt);
+                int na = 0;
+                collide_warp<Rec>(I, id, step, S.trec, N, nc, cmax, na, S.ab, S.tidx, nt);
                 if (lane == 0) {
                     S.nacc = na;
-                    E.cmax[g] = cmax;
+                    if (cmax != S.cmax) {
+                        E.cmax[g] = cmax;
+                        E.fmaj[g] = majorant_factor(I, cmax);
+                    }
                 }
                 __syncwarp();
             }
@@ -1048,7 +1095,7 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     for (int p = 0; p < 2; ++p) { E.nL[p][g] = 0; E.nS[p][g] = 0; E.nR[p][g] = 0; E.off[p][g] = 0; E.slotsb[p][g] = 0; }
     for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
     for (int k = 0; k < 5; ++k) { E.Aself[5 * g + k] = 0.0; E.avg[5 * g + k] = 0.0; E.flux[5 * g + k] = 0.0; E.psi[5 * g + k] = 0.0; E.prim[5 * g + k] = 0.0; }
-    E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0; E.cnt[g] = 0; E.slots[g] = 0; E.valid[g] = 0; E.P[g] = 0.0; E.cmax[g] = 0.0;
+    E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0; E.cnt[g] = 0; E.slots[g] = 0; E.valid[g] = 0; E.P[g] = 0.0; E.cmax[g] = 0.0; E.fmaj[g] = 1.0;
     if (i < 0 || i >= I.C) return;
     const double xc = x_min + (static_cast<double>(i) + 0.5) * I.dx;
     const bool left = xc < x_split;
@@ -1056,6 +1103,7 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     for (int k = 0; k < 5; ++k) E.psi[5 * g + k] = c[k];
     const double T = left ? I.left[4] : I.right[4];
     E.cmax[g] = 5.0 * sqrt(2.0 * I.R * T);
+    E.fmaj[g] = majorant_factor(I, E.cmax[g]);
 }
 
 // ------------------------------------------------------------------------------------------
