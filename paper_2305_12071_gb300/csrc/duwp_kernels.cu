@@ -449,7 +449,7 @@ struct WarpShared {
     int ab[64];
     int tidx[kTouchCap];
     Rec trec[kTouchCap];
-    long long acc[12][32];   // lane-private fixed-point sums: L (u, v, w, e), R (...), self (...)
+    long long acc[4][32];    // lane-private fixed-point sums of the rare cases (u, v, w, e)
 };
 
 // Record of position k of the cell's arrived (sorted) list.
@@ -579,8 +579,8 @@ __device__ __noinline__ void cell_header(const EngineDev &E, int rp, int g, Warp
 
 struct StreamState {
     long long pS, pL, pR;                 // next write position of the S, L (forward) and R (backward) runs
-    long long *acc;                       // this lane's column of the warp's fixed-point sums (stride 32)
-    int nlv = 0;
+    long long *acc;                       // this lane's column of the warp's rare-path sums (stride 32)
+    int ngone = 0;                        // far movers and removed particles of this lane
     bool range_ok = true;
 };
 
@@ -590,8 +590,11 @@ struct StreamCtx {
     int ci, cell_base, g;
 };
 
-// One group of 32 consecutive list positions (lanes in list order): transport, classification,
-// stable writes to the three runs, and the fixed-point sums of what leaves / enters.
+// One group of 32 consecutive list positions (lanes in list order): transport, classification and
+// stable writes to the three runs.  The moments of the L and R runs are summed afterwards from the
+// runs themselves; only the rare cases are summed here: particles that move two or more cells or
+// leave the domain (their pre-transport moments leave the cell), and wall reflections (the normal
+// momentum a reflected particle carries changes sign: +2 u after the reflection).
 template <typename Rec>
 __device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool valid, int k, Rec *out,
                                              FarItem<Rec> *fa, StreamState &st)
@@ -612,18 +615,19 @@ __device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool va
         else if (d == cx.ci) c = 1;
         else if (d == cx.ci + 1) c = 2;
         else c = 3;
-        st.range_ok = st.range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
-        long long *a = st.acc;
-        if (c == 1) {
-            if (refl) a[8 * 32] += fx_vel(uu) - fx_vel(u0);
-        } else {
-            const long long qv = fx_vel(v.v), qw = fx_vel(v.w), qe = fx_energy(u0, v.v, v.w);
-            ++st.nlv;
-            a[8 * 32] -= fx_vel(u0); a[9 * 32] -= qv; a[10 * 32] -= qw; a[11 * 32] -= qe;
-            if (c == 0 || c == 2) {
-                long long *b = a + (c == 0 ? 0 : 4 * 32);
-                b[0] += fx_vel(uu); b[32] += qv; b[64] += qw; b[96] += qe;
-            } else if (c == 3) {
+        if (refl || c >= 3) {
+            long long *a = st.acc;
+            st.range_ok = st.range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
+            if (c >= 3) {
+                ++st.ngone;
+                a[0] -= fx_vel(u0);
+                a[32] -= fx_vel(v.v);
+                a[64] -= fx_vel(v.w);
+                a[96] -= fx_energy(u0, v.v, v.w);
+            } else {
+                a[0] += fx_vel(uu) - fx_vel(u0);
+            }
+            if (c == 3) {
                 const EngineDev &E = *cx.E;
                 const int slot = atomicAdd(&E.far_count[0], 1);
                 if (slot < E.far_cap) {
@@ -649,6 +653,20 @@ __device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool va
     st.pS += __popc(mS);
     st.pL += __popc(mL);
     st.pR -= __popc(mR);
+}
+
+// Fixed-point sums (u, v, w, |xi|^2/2) of n contiguous records, each lane a strided share.
+template <typename Rec>
+__device__ __forceinline__ void run_sums(const Rec *p, int n, long long s[4], bool &ok)
+{
+    for (int j = threadIdx.x & 31; j < n; j += 32) {
+        const Rec v = ld_rec_rw(p + j);
+        ok = ok && fx_in_range(v.u) && fx_in_range(v.v) && fx_in_range(v.w);
+        s[0] += fx_vel(v.u);
+        s[1] += fx_vel(v.v);
+        s[2] += fx_vel(v.w);
+        s[3] += fx_energy(v.u, v.v, v.w);
+    }
 }
 
 template <typename Rec, int kMinBlocks>
@@ -804,28 +822,49 @@ __global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_par
                 st.pR = off + 2 * static_cast<long long>(slots) - 1;
                 st.acc = &S.acc[0][lane];
 #pragma unroll
-                for (int j = 0; j < 12; ++j) S.acc[j][lane] = 0;
+                for (int j = 0; j < 4; ++j) S.acc[j][lane] = 0;
                 const StreamCtx ctx{&I, &E, ci, cell_base, g};
                 if (S.staged) {
-                    for (int base = 0; base < n_tot; base += 32) {
-                        const int k = base + lane;
-                        Rec v;
-                        if (k < n_tot) v = ld_rec_rw(stage + k);
-                        stream_group<Rec>(ctx, v, k < n_tot, k, out, fa, st);
+                    for (int base = 0; base < n_tot; base += 128) {
+                        Rec v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = base + 32 * u + lane;
+                            if (k < n_tot) v[u] = ld_rec_rw(stage + k);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = base + 32 * u + lane;
+                            if (base + 32 * u < n_tot) stream_group<Rec>(ctx, v[u], k < n_tot, k, out, fa, st);
+                        }
                     }
                 } else {
                     int tp = 0;   // first touched index not below the current group
-                    for (int base = 0; base < n_in; base += 32) {
-                        const int k = base + lane;
-                        Rec v;
-                        if (k < n_in) {
-                            v = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
-                            for (int t = tp; t < ntouch && S.tidx[t] < base + 32; ++t)
-                                if (S.tidx[t] == k) v = S.trec[t];
+                    for (int base = 0; base < n_in; base += 128) {
+                        Rec v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = base + 32 * u + lane;
+                            if (k < n_in) v[u] = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
                         }
-                        stream_group<Rec>(ctx, v, k < n_in, k, out, fa, st);
-                        const int hi = min(base + 32, n_in);   // touched re-sampled particles stay for the next loop
-                        while (tp < ntouch && S.tidx[tp] < hi) ++tp;
+                        if (ntouch > 0) {
+                            const int hi = min(base + 128, n_in);
+                            for (int t = tp; t < ntouch && S.tidx[t] < hi; ++t) {
+                                const int x = S.tidx[t];
+                                const int u = (x - base) >> 5;
+                                if (x >= base && (x & 31) == lane) {
+#pragma unroll
+                                    for (int uu = 0; uu < 4; ++uu)
+                                        if (uu == u) v[uu] = S.trec[t];
+                                }
+                            }
+                            while (tp < ntouch && S.tidx[tp] < hi) ++tp;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = base + 32 * u + lane;
+                            if (base + 32 * u < n_in) stream_group<Rec>(ctx, v[u], k < n_in, k, out, fa, st);
+                        }
                     }
                     for (int base = n_in; base < n_tot; base += 32) {
                         const int k = base + lane;
@@ -840,23 +879,43 @@ __global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_par
                         while (tp < ntouch && S.tidx[tp] < base + 32) ++tp;
                     }
                 }
-                if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
-                int nlv = st.nlv;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) nlv += __shfl_down_sync(0xffffffffu, nlv, o);
                 __syncwarp();
-                if (lane < 12) {
-                    // lane j sums row j over the 32 lane columns (exact integer sum, any order)
-                    long long t = 0;
-                    for (int l = 0; l < 32; ++l) t += S.acc[lane][l];
-                    const double sc = ((lane & 3) == 3) ? 0x1p-32 : 0x1p-40;
-                    const double val = static_cast<double>(t) * sc;
-                    if (lane < 4) E.AL[4 * g + lane] = val;
-                    else if (lane < 8) E.AR[4 * g + lane - 4] = val;
-                    else E.Aself[5 * g + 1 + (lane - 8)] = val;
+                // moments of the L and R runs, read back with every lane busy
+                const int nLr = static_cast<int>(st.pL - (off + slots));
+                const int nRr = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
+                long long sLv[4] = {0, 0, 0, 0}, sRv[4] = {0, 0, 0, 0};
+                run_sums<Rec>(out + off + slots, nLr, sLv, st.range_ok);
+                run_sums<Rec>(out + st.pR + 1, nRr, sRv, st.range_ok);
+                if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
+                long long rv[8] = {sLv[0], sLv[1], sLv[2], sLv[3], sRv[0], sRv[1], sRv[2], sRv[3]};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) rv[j] += __shfl_down_sync(0xffffffffu, rv[j], o);
+                }
+                int ngone = st.ngone;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ngone += __shfl_down_sync(0xffffffffu, ngone, o);
+                long long gone = 0;
+                if (lane < 4) {
+                    for (int l = 0; l < 32; ++l) gone += S.acc[lane][l];
+                }
+                // lane j < 4 needs rv[j] and rv[4 + j] from lane 0
+                long long lj = 0, rj = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long a0 = __shfl_sync(0xffffffffu, rv[j], 0);
+                    const long long b0 = __shfl_sync(0xffffffffu, rv[4 + j], 0);
+                    if (lane == j) { lj = a0; rj = b0; }
+                }
+                if (lane < 4) {
+                    const double sc = (lane == 3) ? 0x1p-32 : 0x1p-40;
+                    E.AL[4 * g + lane] = static_cast<double>(lj) * sc;
+                    E.AR[4 * g + lane] = static_cast<double>(rj) * sc;
+                    E.Aself[5 * g + 1 + lane] = static_cast<double>(gone - lj - rj) * sc;
                 }
                 if (lane == 0) {
-                    E.Aself[5 * g] = -static_cast<double>(nlv);
+                    E.Aself[5 * g] = -static_cast<double>(ngone + nLr + nRr);
                     S.nS = static_cast<int>(st.pS - off);
                     S.nL = static_cast<int>(st.pL - (off + slots));
                     S.nR = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
