@@ -1,6 +1,6 @@
 #!/usr/bin/env python
 """Benchmark of the DUWP per-time-step hot path on GB300: particle-updates/s and the fraction of
-the measured HBM bandwidth the particle kernel reaches, plus step-latency percentiles, the
+the measured HBM bandwidth the streaming kernel reaches, plus step-latency percentiles, the
 graph-replayed step, the plain one-instance-at-a-time FP64 loop, an end-to-end number through
 the C ABI with host buffers, and the CPU oracle as a reported baseline.
 
@@ -143,9 +143,9 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(workload_name: str, updates_per_launch: float):
-    """DRAM bytes per launch of the particle kernel from the committed ncu summary, when it was
+    """DRAM bytes per launch of the streaming kernel from the committed ncu summary, when it was
     taken on the current kernel source; scaled by the particle-updates of a launch."""
-    path = os.path.join(ROOT, "profiles", "k_particles_ncu.md")
+    path = os.path.join(ROOT, "profiles", "k_stream_ncu.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -226,7 +226,7 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--launch", default="", help="particle-kernel launch shape threads,reg_capped "
+    ap.add_argument("--launch", default="", help="streaming-kernel launch shape threads,reg_capped "
                                                  "(skips the autotuner)")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances of the batch")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
@@ -287,7 +287,7 @@ def main():
     u1 = sol.particle_updates()
     barrier()
     clocks = clk.stop()
-    span_s = kms[4] / 1e3
+    span_s = kms[5] / 1e3
     updates = u1 - u0
     if dist is not None:
         t = torch.tensor([span_s, float(updates)], dtype=torch.float64, device="cuda")
@@ -315,17 +315,16 @@ def main():
         steps_sorted = sorted(step_ms)
         p50 = steps_sorted[len(steps_sorted) // 2]
         p99 = steps_sorted[min(len(steps_sorted) - 1, int(math.ceil(0.99 * len(steps_sorted))) - 1)]
-        upl = updates / args.steps                     # particle-updates per launch of the particle kernel
-        k_ms = kms[0] / args.steps
+        upl = updates / args.steps                     # particle-updates per launch of the streaming kernel
+        k_ms = kms[1] / args.steps
         peak, peak_kind = measured_peaks()
         achieved = rec_bytes * 2 * upl / (k_ms * 1e-3) / 1e9
         traffic, per_upd = profiled_traffic(args.workload, upl)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_particles",
+                "traffic": traffic, "kernel": "k_stream",
                 "algorithmic_bytes_per_update": rec_bytes * 2, "updates_per_launch": upl,
                 "launch_ms": k_ms, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
-        kernel_share = {n: float(v / max(kms[:4].sum(), 1e-30)) for n, v in
-                        zip(("k_particles", "k_far_sort", "k_cells", "k_offsets_flux"), kms[:4])}
+        kernel_share = {n: float(v / max(kms[:5].sum(), 1e-30)) for n, v in zip(duwp.Solver.KERNELS, kms[:5])}
         cfg = dict(cfg)
         info0 = sol.info(0)
         cfg.update({"particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
@@ -337,10 +336,9 @@ def main():
                "warmup": args.warmup, "ms_per_step": 1e3 * span_all / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
                "data": "synthetic (seeded shock/Sod problems shaped like the paper's test cases)",
-               "config": cfg, "clocks": clocks, "gpu_launches": 4 * args.steps,
+               "config": cfg, "clocks": clocks, "gpu_launches": 5 * args.steps,
                "step_ms_p50": p50, "step_ms_p99": p99, "graph_ms_per_step": graph_ms,
-               "kernel_ms_per_step": {n: float(v / args.steps) for n, v in
-                                      zip(("k_particles", "k_far_sort", "k_cells", "k_offsets_flux"), kms[:4])},
+               "kernel_ms_per_step": {n: float(v / args.steps) for n, v in zip(duwp.Solver.KERNELS, kms[:5])},
                "kernel_share": kernel_share, "roofline": roof}
     sol.close()
     del sol
@@ -359,7 +357,7 @@ def main():
             a = s.particle_updates()
             k, _ = s.step_timed(kplain)
             pl_updates += s.particle_updates() - a
-            pl_ms += k[4]
+            pl_ms += k[5]
             s.close()
             del s
         torch.cuda.empty_cache()

@@ -144,11 +144,14 @@ int duwp_step(duwp_handle *h, int32_t n_steps);
 int duwp_sync(duwp_handle *h);
 
 /* Synchronizing.  Advance by n_steps >= 1 steps as individual launches with CUDA events recorded
- * on the handle's stream around every kernel.  host_kernel_ms[5] (caller-owned) receives the summed
- * device time of the particle kernel, the far-mover sort, the cell update and the offset/flux
- * kernel, and in [4] the device time from the first launch to the end of the last;
- * host_step_ms (n_steps entries, may be NULL) the device time of each step.  Results are
- * identical to duwp_step.  Errors: as duwp_step and duwp_sync. */
+ * on the handle's stream around every kernel.  host_kernel_ms[DUWP_TIMED_SLOTS] (caller-owned)
+ * receives the summed device time of [0] the collision kernel (collisions, absorption and
+ * re-sampling of the cells that need them), [1] the streaming kernel (transport and sorted runs of
+ * every particle), [2] the far-mover sort, [3] the cell update and [4] the offset/flux kernel, and
+ * in [5] the device time from the first launch to the end of the last; host_step_ms (n_steps
+ * entries, may be NULL) the device time of each step.  Results are identical to duwp_step.
+ * Errors: as duwp_step and duwp_sync. */
+enum { DUWP_TIMED_SLOTS = 6 };
 int duwp_step_timed(duwp_handle *h, int32_t n_steps, double *host_kernel_ms, double *host_step_ms);
 
 enum { DUWP_INSTANT = 0, DUWP_AVERAGED = 1 };
@@ -182,10 +185,11 @@ const char *duwp_last_cuda_error(void);
 
 /* ------------------------------------------------------------------ launch configuration */
 
-/* Launch shape of the particle kernel (one warp per cell): threads per block (multiple of 32,
- * 32..512) and the register budget (reg_capped = 0: unconstrained; 1: capped so that six
- * 128-thread blocks fit on an SM, threads <= 128).  Used by the autotuner; results do not depend
- * on it.  Synchronizing.  Errors: DUWP_EINVAL for shapes the device cannot launch. */
+/* Launch shape of the streaming kernel (one warp per cell): threads per block (multiple of 32,
+ * 32..512) and the register budget (reg_capped = 0: up to 128 registers per thread; 1: up to 64,
+ * two 512-thread blocks per SM; 2: up to 40, three).  Used by the autotuner; results do not depend
+ * on it.
+ * Synchronizing.  Errors: DUWP_EINVAL for shapes the device cannot launch. */
 int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped);
 
 /* Capture the per-step launches in CUDA graphs (on = 1, default) or launch them one by one

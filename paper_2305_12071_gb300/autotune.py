@@ -1,10 +1,9 @@
-"""Autotuner of the particle kernel's launch shape.
+"""Autotuner of the streaming kernel's launch shape.
 
-Two knobs: threads per block (each warp of the block works through its own cells) and the
-register budget (unconstrained, or capped so that six 128-thread blocks fit on an SM).  Together
-they fix the warps resident per SM.  The
+Two knobs of the streaming kernel: threads per block (one warp per cell) and the register budget
+(up to 128, 64 or 40 registers per thread).  Together they fix the warps resident per SM.  The
 tuner times a few steps of the caller's own workload for every candidate with CUDA events
-(duwp_step_timed) and keeps the fastest.  Results do not depend on the launch shape (the per-cell
+(duwp_step_timed: collision + streaming kernels) and keeps the fastest.  Results do not depend on the launch shape (the per-cell
 moment sums are exact fixed-point integers and the partition order is defined by the method), so
 tuning changes speed only.  Choices are cached in a JSON file keyed by device, precision and
 workload size buckets.
@@ -15,9 +14,10 @@ import json
 import math
 import os
 
+_VERSION = 2          # layout of the launch knobs (entries of other versions are re-tuned)
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
 
-CANDIDATES_FP32 = [(t, 0) for t in (32, 64, 128, 256, 512)] + [(t, 1) for t in (32, 64, 128)]
+CANDIDATES_FP32 = [(t, r) for r in (0, 1, 2) for t in (64, 128, 256, 512)]
 CANDIDATES_FP64 = CANDIDATES_FP32
 
 
@@ -52,7 +52,7 @@ def tune(solver, steps: int = 3, use_cache: bool = True, candidates=None):
     advances by len(candidates) * steps steps.  Returns (choice, timings)."""
     key = _key(solver)
     cache = _load() if use_cache else {}
-    if use_cache and key in cache and "cell_capacity" not in cache[key]:
+    if use_cache and key in cache and cache[key].get("version") == _VERSION:
         t, r = cache[key]["threads"], cache[key].get("reg_capped", 0)
         solver.set_launch(t, r)
         return (t, r), cache[key].get("timings", {})
@@ -67,13 +67,13 @@ def tune(solver, steps: int = 3, use_cache: bool = True, candidates=None):
             continue
         solver.step_timed(1)                     # first launch of a shape: not timed
         k, _ = solver.step_timed(steps)
-        ms = float(k[0]) / steps
-        timings[f"{t}{'r' if r else ''}"] = ms
+        ms = float(k[0] + k[1]) / steps
+        timings[f"{t}r{r}"] = ms
         if best is None or ms < best[0]:
             best = (ms, t, r)
     if best is None:
         raise RuntimeError("no launch shape could be configured")
     solver.set_launch(best[1], best[2])
-    cache[key] = {"threads": best[1], "reg_capped": best[2], "ms": best[0], "timings": timings}
+    cache[key] = {"threads": best[1], "reg_capped": best[2], "ms": best[0], "timings": timings, "version": _VERSION}
     _save(cache)
     return (best[1], best[2]), timings

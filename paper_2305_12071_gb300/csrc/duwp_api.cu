@@ -178,18 +178,18 @@ struct Carver {
 int Engine::configure_launch(int threads_, int variant_)
 {
     if (threads_ < 32 || threads_ > 512 || (threads_ & 31)) return DUWP_EINVAL;
-    if (variant_ < 0 || variant_ > 1) return DUWP_EINVAL;
-    const size_t sm = particles_smem_bytes(fp32, threads_);
-    const int occ = particles_occupancy(fp32, variant_, threads_, sm);
+    if (variant_ < 0 || variant_ > 2) return DUWP_EINVAL;
+    const int occ = stream_occupancy(fp32, variant_, threads_);
     if (occ <= 0) return DUWP_EINVAL;
+    const int occ_c = collide_occupancy(fp32);
+    if (occ_c <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
     threads = threads_;
     variant = variant_;
-    smem = sm;
-    // persistent blocks: as many as fit, but no more warps than cells
-    const int warps = threads_ / 32;
-    grid = std::max(1, std::min(occ * nsm, (G + warps - 1) / warps));
+    // collision kernel: persistent blocks, as many as fit, but no more warps than cells
+    const int cw = collide_threads() / 32;
+    grid_collide = std::max(1, std::min(occ_c * nsm, (G + cw - 1) / cw));
     drop_graphs();
     return DUWP_OK;
 }
@@ -273,6 +273,8 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_fc = c.take<int32_t>(4);
     const size_t o_err = c.take<int32_t>(4);
     const size_t o_ticket = c.take<int32_t>(4);
+    const size_t o_hdr = c.take<CellHdr>(G);
+    const size_t o_wl = c.take<int32_t>(G);
     const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
     const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
     const size_t o_buf0 = c.take<unsigned char>(rec * size_t(capacity));
@@ -317,6 +319,8 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.far_count = reinterpret_cast<int32_t *>(base + o_fc);
     dev.err = reinterpret_cast<int32_t *>(base + o_err);
     dev.ticket = reinterpret_cast<int32_t *>(base + o_ticket);
+    dev.hdr = reinterpret_cast<CellHdr *>(base + o_hdr);
+    dev.wl = reinterpret_cast<int32_t *>(base + o_wl);
     dev.far_app = base + o_fa;
     dev.far_sorted = base + o_fs;
     dev.buf[0] = base + o_buf0;
@@ -364,6 +368,8 @@ int Engine::remove_instance(int slot)
     const HostInst &h = inst[slot];
     DUWP_CU(cudaMemsetAsync(dev.cell_inst + h.cell_base, 0xff, sizeof(int32_t) * size_t(h.p.n_cells + 2), stream));
     DUWP_CU(cudaMemsetAsync(dev.slots + h.cell_base, 0, sizeof(int32_t) * size_t(h.p.n_cells + 2), stream));
+    // class kClsSkip (0) until the next cell kernel rebuilds the plans
+    DUWP_CU(cudaMemsetAsync(dev.hdr + h.cell_base, 0, sizeof(CellHdr) * size_t(h.p.n_cells + 2), stream));
     inst[slot].active = false;
     return DUWP_OK;
 }
@@ -382,14 +388,16 @@ int Engine::enqueue_step(cudaEvent_t *ev)
 {
     const int rp = parity;
     if (ev) DUWP_CU(cudaEventRecord(ev[0], stream));
-    DUWP_CU(launch_particles(dev, fp32, variant, rp, grid, threads, smem, stream));
+    DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[1], stream));
-    DUWP_CU(launch_far_sort(dev, fp32, stream));
+    DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[2], stream));
-    DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
+    DUWP_CU(launch_far_sort(dev, fp32, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[3], stream));
-    DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+    DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[4], stream));
+    DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+    if (ev) DUWP_CU(cudaEventRecord(ev[5], stream));
     parity = 1 - rp;
     return DUWP_OK;
 }
@@ -510,31 +518,32 @@ int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_m
 {
     if (!h || n < 1 || !kernel_ms) return DUWP_EINVAL;
     Engine &E = h->eng;
-    std::vector<cudaEvent_t> ev(5 * static_cast<size_t>(n), nullptr);
+    constexpr int kEv = kStepEvents;
+    std::vector<cudaEvent_t> ev(kEv * static_cast<size_t>(n), nullptr);
     int rc = DUWP_OK;
     for (auto &e : ev) {
         if (cudaEventCreate(&e) != cudaSuccess) { rc = DUWP_ECUDA; break; }
     }
     for (int32_t s = 0; s < n && rc == DUWP_OK; ++s) {
-        rc = E.enqueue_step(ev.data() + 5 * static_cast<size_t>(s));
+        rc = E.enqueue_step(ev.data() + kEv * static_cast<size_t>(s));
         if (rc == DUWP_OK) ++E.steps_done;
     }
     if (rc == DUWP_OK) rc = E.sync();
-    for (int k = 0; k < 5; ++k) kernel_ms[k] = 0.0;
+    for (int k = 0; k < kEv; ++k) kernel_ms[k] = 0.0;
     if (rc == DUWP_OK) {
         float span = 0.f;
-        cudaEventElapsedTime(&span, ev[0], ev[5 * static_cast<size_t>(n) - 1]);
-        kernel_ms[4] = span;
+        cudaEventElapsedTime(&span, ev[0], ev[kEv * static_cast<size_t>(n) - 1]);
+        kernel_ms[kEv - 1] = span;
         for (int32_t s = 0; s < n; ++s) {
-            cudaEvent_t *e = ev.data() + 5 * static_cast<size_t>(s);
-            for (int k = 0; k < 4; ++k) {
+            cudaEvent_t *e = ev.data() + kEv * static_cast<size_t>(s);
+            for (int k = 0; k < kEv - 1; ++k) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e[k], e[k + 1]);
                 kernel_ms[k] += ms;
             }
             if (step_ms) {
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, e[0], e[4]);
+                cudaEventElapsedTime(&ms, e[0], e[kEv - 1]);
                 step_ms[s] = ms;
             }
         }
@@ -640,7 +649,7 @@ int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped)
     Engine &E = h->eng;
     const int rc = E.sync();
     if (rc) return rc;
-    return E.configure_launch(threads, reg_capped ? 1 : 0);
+    return E.configure_launch(threads, reg_capped);
 }
 
 int duwp_use_graphs(duwp_handle *h, int32_t on)

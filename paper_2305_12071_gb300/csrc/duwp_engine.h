@@ -15,6 +15,9 @@ namespace duwp {
 
 void set_cuda_error(cudaError_t e, const char *where);
 
+// Events recorded by a timed step: before the collision kernel and after each of the five kernels.
+constexpr int kStepEvents = 6;
+
 struct HostInst {
     duwp_params p;
     InstDev d;          // constants as uploaded (step counters live on the device)
@@ -42,10 +45,9 @@ struct Engine {
     int32_t max_inst = 0;
     int64_t capacity = 0;       // particle slots per buffer
     int32_t far_cap = 0;
-    int32_t threads = 128;
-    int32_t variant = 0;        // particle-kernel register budget (0: unconstrained, 1: occupancy-capped)
-    int32_t grid = 0;
-    size_t smem = 0;
+    int32_t threads = 128;      // streaming kernel: threads per block (one warp per cell)
+    int32_t variant = 0;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers)
+    int32_t grid_collide = 0;   // collision kernel: persistent blocks
 
     // device memory: one slab
     void *slab = nullptr;
@@ -65,7 +67,7 @@ struct Engine {
     int configure_launch(int threads_, int variant_ = 0);
     int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
     int remove_instance(int slot);
-    int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[5]: events around kernels
+    int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[kStepEvents]: events around kernels
     int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
     int step(int32_t n);
     int sync();                        // wait + read the device error word

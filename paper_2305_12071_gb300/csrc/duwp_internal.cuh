@@ -63,6 +63,37 @@ struct FarItem {
     Rec rec;
 };
 
+// Plan of one cell's particle work in the next step, written by the cell kernels at the end of a
+// step (k_cells: lists, counts, class; k_offsets_flux: output block): where the cell's arrived list
+// lies in the read buffer, where its output block starts, and the counts that are known before any
+// particle is touched (re-sampled count and NTC candidate count when P = 0).
+enum CellClass : int32_t {
+    kClsSkip = 0,       // unused cell, a reservoir that samples nothing, or a cell in error
+    kClsStream = 1,     // P = 0 and no collision candidates: stream the arrived + re-sampled particles
+    kClsDirect = 2,     // P = 0, 1..kMaxDirect candidates, nothing re-sampled: collide in place, stream
+    kClsStaged = 3,     // P > 0, more candidates, or re-sampled particles with candidates
+    kClsReservoir = 4   // inflow/outflow reservoir: stream the particles sampled at its state
+};
+constexpr int kMaxDirect = 32;
+
+struct alignas(16) CellHdr {
+    int64_t Rend;       // one past the last record of the left neighbour's R run (read backwards)
+    int64_t Sa;         // first record of the cell's own S run
+    int64_t La;         // first record of the right neighbour's L run
+    int64_t off;        // first slot of the cell's output block in the write buffer
+    int32_t Rn, Sn, Ln;
+    int32_t slots;      // slot bound (the output block holds 2 x slots)
+    int32_t fb, nfb, nfa;   // far movers: first sorted index, counts from the left / from the right
+    int32_t n_in;       // arrived particles (the list length before absorption)
+    int32_t n_new;      // re-sampled particles (classes 1, 2, 4)
+    int32_t nc;         // NTC candidates (classes 1, 2)
+    int32_t cls;        // CellClass
+    int32_t b;          // instance
+    int32_t i;          // local cell index (-1 and C: reservoirs)
+    int32_t pad[3];
+};
+static_assert(sizeof(CellHdr) == 96, "cell header layout");
+
 // Pointers of one engine, passed by value to every kernel.
 struct EngineDev {
     int32_t G;                 // flattened cells in the pool
@@ -93,7 +124,9 @@ struct EngineDev {
     void *far_sorted;          // the same, sorted by (dest, src, q)
     int32_t *far_count;        // [0]: appended, [1]: sorted
     int32_t *err;              // first device error
-    int32_t *ticket;           // work counter of the particle kernel
+    int32_t *ticket;           // [0]: work counter of the collision kernel, [1]: its work-list length
+    CellHdr *hdr;              // G: plan of each cell's particle work in the next step
+    int32_t *wl;               // work list of the collision kernel (cells of class 2 and 3)
 };
 
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels

@@ -1,16 +1,17 @@
 // duwp_kernels.cu -- the per-step kernels of the DUWP method (arXiv 2305.12071, Sec. 3.4) on sm_103a.
 //
-//   k_particles   (per cell, persistent CTAs): gather the cell's stable list (far movers, R(g-1),
-//                 S(g), L(g+1)) into shared memory; absorb each particle with probability P
-//                 (Eq. p); re-sample (1-P) of the wave as Maxwellian particles (Eq. maxsample);
-//                 NTC/VHS collisions (Appendix A); free transport with boundaries (Step 3); write
-//                 the L/S/R runs of the cell to its output block; sums of the moments that left or
-//                 entered the cell (Eq. fp).
+//   k_collide     (persistent, one warp per listed cell): NTC/VHS collisions (Appendix A) of the
+//                 cells that have candidates, and absorption with probability P (Eq. p) plus
+//                 re-sampling of (1-P) of the wave (Eq. maxsample) in the cells where P > 0.
+//   k_stream      (one warp per cell): read the cell's stable list (far movers, R(g-1), S(g),
+//                 L(g+1), or the staged list), sample the re-sampled particles of cells without
+//                 collisions, free transport with boundaries (Step 3), write the L/S/R runs of the
+//                 cell's output block, exact sums of the moments that left or entered (Eq. fp).
 //   k_far_sort    stable order of the rare particles that moved two or more cells.
-//   k_cells       (per cell): conservative update Eq. (r1), time average, primitive state, P and
-//                 the slot bound of the next step.
-//   k_offsets     (per cell): output block offsets of the next step (scan of the slot bounds) and
-//                 the wave flux at every interface.
+//   k_cells       (per cell): conservative update Eq. (r1), time average, primitive state, P, the
+//                 slot bound and the plan (counts, class) of the next step.
+//   k_offsets     (per cell): output block offsets of the next step (scan of the slot bounds), the
+//                 work list of the collision kernel, and the wave flux at every interface.
 #include <cstdio>
 
 #include "duwp_launch.h"
@@ -86,18 +87,28 @@ __device__ __forceinline__ int64_t apply_walls(const InstDev &I, int64_t dest, T
     return -1;   // more than 64 wall reflections within one step: removed
 }
 
-__device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, float &xl, float &u, bool &refl)
+// Single-precision records: the displacement is converted with a 32-bit conversion when below
+// 2^30 cells (the integral value fk converts exactly) and the new cell index stays in 32 bits;
+// a particle that ends inside the domain needs no wall logic.
+__device__ __forceinline__ int move_particle(const InstDev &I, float dtdx, int C, int cell, float &xl, float &u,
+                                             bool &refl)
 {
-    const float s = __fmaf_rn(u, I.dtdx_f, xl);
+    const float s = __fmaf_rn(u, dtdx, xl);
     if (!(fabsf(s) < 1e15f)) return -1;
     const float fk = floorf(s);
     float x = __fsub_rn(s, fk);
-    // the integral value fk converts exactly; a 32-bit conversion covers every displacement
-    // below 2^30 cells (the 64-bit one is reserved for larger ones)
-    int64_t k = (fabsf(fk) < 1073741824.0f) ? static_cast<int64_t>(__float2int_rz(fk)) : static_cast<int64_t>(fk);
+    if (fabsf(fk) < 1073741824.0f) {
+        int k = __float2int_rz(fk);
+        if (x >= 1.0f) { x = 0.0f; k += 1; }
+        xl = x;
+        const int d = cell + k;   // |cell| < 2^30 and |k| <= 2^30: no overflow
+        if (static_cast<unsigned>(d) < static_cast<unsigned>(C)) return d;
+        return static_cast<int>(apply_walls<float>(I, d, xl, u, refl));
+    }
+    int64_t k = static_cast<int64_t>(fk);
     if (x >= 1.0f) { x = 0.0f; k += 1; }
     xl = x;
-    return apply_walls<float>(I, cell + k, xl, u, refl);
+    return static_cast<int>(apply_walls<float>(I, static_cast<int64_t>(cell) + k, xl, u, refl));
 }
 
 __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, double &xl, double &u, bool &refl)
@@ -110,6 +121,11 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, dou
     if (x >= 1.0) { x = 0.0; k += 1; }
     xl = x;
     return apply_walls<double>(I, cell + k, xl, u, refl);
+}
+
+__device__ __forceinline__ int move_particle(const InstDev &I, double, int, int cell, double &xl, double &u, bool &refl)
+{
+    return static_cast<int>(transport(I, cell, xl, u, refl));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -146,45 +162,6 @@ __device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint3
     return r;
 }
 
-// ------------------------------------------------------------------------------------------
-// Block-wide helpers
-// ------------------------------------------------------------------------------------------
-
-// Exclusive scan of a 64-bit value over the CTA (in thread order); total returned via *tot.
-__device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *s_w, uint64_t *tot)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint64_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint64_t t = (lane < nw) ? s_w[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < nw) s_w[lane] = t;
-    }
-    __syncthreads();
-    const uint64_t pre = (warp > 0) ? s_w[warp - 1] : 0;
-    *tot = s_w[nw - 1];
-    __syncthreads();
-    return pre + x - v;
-}
-
-__device__ __forceinline__ double warp_sum(double x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // Lower bound of `key` in the far list ordered by (dest, src, q): first index with (dest, src) >= key.
 template <typename Rec>
 __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
@@ -198,14 +175,7 @@ __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
     return lo;
 }
 
-// ------------------------------------------------------------------------------------------
-// NTC collisions of one cell (Appendix A), one warp.  Candidates are taken in order in batches of
-// up to 32: the batch is cut before the first candidate that shares a particle with an earlier
-// one in the batch, and after the first whose c_r raises c_max; inside such a prefix the
-// candidates touch disjoint particles and see the same c_max, so doing them at once gives exactly
-// the sequential result.  The acceptance test (c_r/c_max)^{1-2 upsilon} > u is first decided in
-// FP32 with a margin far above its error; only draws within the margin take the FP64 pow.
-// ------------------------------------------------------------------------------------------
+
 // Majorant factor (c_max/c_ref)^{-2 upsilon} of the NTC count; kept per cell and recomputed only when
 // c_max is raised.
 __device__ inline double majorant_factor(const InstDev &I, double cmax)
@@ -250,20 +220,71 @@ __device__ __forceinline__ double rel_speed(const Rec &A, const Rec &B)
     return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
 }
 
-// The nc candidates of a cell in order (nc from ntc_candidates).  tidx (optional): sorted list
-// indices of the records held in `list` (the touched particles); without it `list` is the whole
-// cell list.  Both the test c_r > c_max and the acceptance u < (c_r/c_max)^{1-2 upsilon} are first
-// decided in single precision with margins far above its error; exact double-precision values are
-// computed for draws inside the margins and for every accepted pair (its scattering).
+// ------------------------------------------------------------------------------------------
+// NTC collisions (Appendix A).  Candidates are taken in order in batches: a batch is cut before the
+// first candidate that shares a particle with an earlier one in the batch, and after the first whose
+// c_r raises c_max; inside such a prefix the candidates touch disjoint particles and see the same
+// c_max, so doing them at once gives exactly the sequential result.
+// ------------------------------------------------------------------------------------------
+
+// Acceptance of a candidate: u < (c_r/c_max)^{1-2 upsilon} with u = u53(w2, w3).  Decided in single
+// precision first: u lies in [uf, uf + 2^-24) with uf from the top 24 bits of w2, and for a ratio
+// x32 = c_r/c_max above 1e-30 (relative speed above 1e-12) the single-precision power has a relative
+// error below 1e-5; outside the margin 2e-4 p + 2.5e-7 around the threshold the decision is the exact
+// one.  Inside it (and for tiny ratios) c_r and the power are evaluated in double precision.
+// cr / exact: the exact relative speed, computed here when needed.
 template <typename Rec>
-__device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, int64_t nc,
-                                          double &cmax, int &nacc, int *s_ab, const int *tidx, int ntouch)
+__device__ __forceinline__ bool accept_pair(const InstDev &I, double expo, float expo_f, const Rec &A, const Rec &B,
+                                            float cr32, float cm32, double cm, uint32_t w2, uint32_t w3, double &cr,
+                                            bool &exact)
 {
-    using T = decltype(list[0].xl);
+    if (expo == 0.0) return true;                    // Maxwell molecules: every candidate collides
+    const float x32 = cr32 / cm32;
+    if (cr32 > 1e-12f && x32 > 1e-30f) {
+        const float p32 = (I.upsilon == 0.0) ? x32 : exp2f(expo_f * log2f(x32));
+        const float m32 = 2e-4f * p32 + 2.5e-7f;
+        const float uf = static_cast<float>(w2 >> 8) * 0x1p-24f;
+        if (uf < p32 - m32) return true;
+        if (uf > p32 + m32) return false;
+    }
+    if (!exact) { cr = rel_speed(A, B); exact = true; }
+    const double x = cr / cm;
+    return u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo));
+}
+
+// Isotropic VHS scattering of an accepted pair k (Appendix A): the relative velocity keeps its
+// magnitude c_r and takes the direction (theta, phi) with cos(theta) = 2 u1 - 1, phi = 2 pi u2.
+template <typename Rec>
+__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, Rec &A, Rec &B,
+                                             double cr)
+{
+    using T = decltype(A.xl);
+    uint32_t v[4];
+    draw(I, id, 2u * k + 1u, step, kCollide, v);
+    const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
+    const double st = sqrt(1.0 - ct * ct);
+    double sp, cp;
+    sincos(kTwoPi * u53(v[2], v[3]), &sp, &cp);
+    const double c0 = (cr * st) * cp, c1 = (cr * st) * sp, c2 = cr * ct;
+    const double au = A.u, av = A.v, aw = A.w, bu = B.u, bv = B.v, bw = B.w;
+    const double m0 = (au + bu) * 0.5, m1 = (av + bv) * 0.5, m2 = (aw + bw) * 0.5;
+    A.u = store_val(m0 + c0 * 0.5, T());
+    A.v = store_val(m1 + c1 * 0.5, T());
+    A.w = store_val(m2 + c2 * 0.5, T());
+    B.u = store_val(m0 - c0 * 0.5, T());
+    B.v = store_val(m1 - c1 * 0.5, T());
+    B.w = store_val(m2 - c2 * 0.5, T());
+}
+
+// The nc candidates of a staged cell list (nc from ntc_candidates), in order; candidate k is drawn
+// in the batch that reaches it.
+template <typename Rec>
+__device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, int64_t nc,
+                                          double &cmax, int &nacc, int *s_ab)
+{
     const int lane = threadIdx.x & 31;
     nacc = 0;
     if (N < 2 || nc <= 0) return;
-    uint32_t w[4];
     const double expo = 1.0 - 2.0 * I.upsilon;
     const float expo_f = static_cast<float>(expo);
     int acc = 0;
@@ -271,14 +292,15 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
     for (int64_t k0 = 0; k0 < nc;) {
         const int64_t k = k0 + lane;
         const bool act = k < nc;
-        uint32_t a = 0, b = 0;
-        double ua = 0.0;
+        uint32_t a = 0, b = 0, w2 = 0, w3 = 0;
         if (act) {
+            uint32_t w[4];
             draw(I, id, static_cast<uint32_t>(2 * k), step, kCollide, w);
             a = idx32(w[0], static_cast<uint32_t>(N));
             b = idx32(w[1], static_cast<uint32_t>(N - 1));
             if (b >= a) ++b;
-            ua = u53(w[2], w[3]);
+            w2 = w[2];
+            w3 = w[3];
         }
         s_ab[lane] = act ? static_cast<int>(a) : -1;
         s_ab[32 + lane] = act ? static_cast<int>(b) : -2;
@@ -296,19 +318,10 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
         float cr32 = 0.f;
         double cr = 0.0;
         bool exact = false;
-        uint32_t sa = a, sb = b;
-        if (tidx && lane < m1) {
-            int lo = 0, hi = ntouch;
-            while (lo < hi) { const int mid = (lo + hi) >> 1; if (tidx[mid] < static_cast<int>(a)) lo = mid + 1; else hi = mid; }
-            sa = static_cast<uint32_t>(lo);
-            lo = 0; hi = ntouch;
-            while (lo < hi) { const int mid = (lo + hi) >> 1; if (tidx[mid] < static_cast<int>(b)) lo = mid + 1; else hi = mid; }
-            sb = static_cast<uint32_t>(lo);
-        }
         const float cm32 = static_cast<float>(cm);
         if (lane < m1) {
-            A = list[sa];
-            B = list[sb];
+            A = list[a];
+            B = list[b];
             cr32 = rel_speed_f32(A, B);
             if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
                 cr = rel_speed(A, B);
@@ -321,42 +334,12 @@ __device__ __noinline__ void collide_warp(const InstDev &I, uint32_t id, uint32_
         const double cr_r = __shfl_sync(0xffffffffu, cr, fr < 32 ? fr : 0);
         bool accd = false;
         if (lane < m) {
-            if (lane == fr) {
-                accd = true;                    // c_max = c_r: acceptance probability 1
-            } else if (expo == 0.0) {
-                accd = ua < 1.0;
-            } else {
-                const float x32 = cr32 / cm32;
-                const float p32 = (I.upsilon == 0.0) ? x32 : exp2f(expo_f * log2f(x32));
-                const double p = static_cast<double>(p32);
-                const double margin = 1e-4 * p + 1e-7;
-                if (ua < p - margin) accd = true;
-                else if (ua > p + margin) accd = false;
-                else {
-                    if (!exact) { cr = rel_speed(A, B); exact = true; }
-                    const double x = cr / cm;
-                    accd = ua < ((I.upsilon == 0.0) ? x : pow(x, expo));
-                }
-            }
+            accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
                 if (!exact) cr = rel_speed(A, B);
-                uint32_t v[4];
-                draw(I, id, static_cast<uint32_t>(2 * k + 1), step, kCollide, v);
-                const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
-                const double st = sqrt(1.0 - ct * ct);
-                double sp, cp;
-                sincos(kTwoPi * u53(v[2], v[3]), &sp, &cp);
-                const double c0 = (cr * st) * cp, c1 = (cr * st) * sp, c2 = cr * ct;
-                const double au = A.u, av = A.v, aw = A.w, bu = B.u, bv = B.v, bw = B.w;
-                const double m0 = (au + bu) * 0.5, mm1 = (av + bv) * 0.5, m2 = (aw + bw) * 0.5;
-                A.u = store_val(m0 + c0 * 0.5, T());
-                A.v = store_val(mm1 + c1 * 0.5, T());
-                A.w = store_val(m2 + c2 * 0.5, T());
-                B.u = store_val(m0 - c0 * 0.5, T());
-                B.v = store_val(mm1 - c1 * 0.5, T());
-                B.w = store_val(m2 - c2 * 0.5, T());
-                list[sa] = A;
-                list[sb] = B;
+                scatter_pair<Rec>(I, id, static_cast<uint32_t>(k), step, A, B, cr);
+                list[a] = A;
+                list[b] = B;
             }
         }
         acc += __popc(__ballot_sync(0xffffffffu, accd));
@@ -414,61 +397,6 @@ __device__ __forceinline__ long long fx_energy(double u, double v, double w)
     return __double2ll_rn((u * u + v * v + w * w) * 2147483648.0);
 }
 
-// ------------------------------------------------------------------------------------------
-// Particle kernel: one warp per cell, no block-wide barriers.
-//
-// Output block of a cell s (2 x slots records, slots = the bound on its list after re-sampling):
-// particles that stay (S) are written forward from the block start, those moving one cell left
-// (L) forward from the middle, those moving one cell right (R) backward from the end; each run
-// keeps the order the particles had before transport.  The sorted list of cell g for the next
-// step reads R(g-1) from its end backwards, then S(g), then L(g+1).
-//
-// Two ways through a cell:
-//   direct  (P = 0 and at most 32 NTC candidates): the candidate pairs are drawn first (they depend
-//           only on counters), the touched particles are copied to shared memory and collided
-//           there, then one streaming pass reads the arrived runs (and samples the re-sampled
-//           particles), substitutes the touched ones, transports and writes;
-//   staged  (P > 0, or more candidates): survivors of the absorption draw and the re-sampled
-//           particles are written to the first half of the cell's own output block, collided
-//           there, then streamed from there (stayers are written back in place, never ahead of
-//           the read position).
-// ------------------------------------------------------------------------------------------
-constexpr int kTouchCap = 64;
-constexpr int kMaxCand = 32;
-
-template <typename Rec>
-struct WarpShared {
-    int b, i, ghost, skip, staged;
-    int n_in, n_surv, n_new, n_tot, slots;
-    int nfb, fb, Rn, Sn, Ln, nfa, fa;
-    long long Rend, Sa, La, off_out;
-    double P, rho_t, cmax;
-    double q[5];
-    int valid, ncand, nacc, ntouch;
-    int nL, nS, nR;
-    int ab[64];
-    int tidx[kTouchCap];
-    Rec trec[kTouchCap];
-    long long acc[4][32];    // lane-private fixed-point sums of the rare cases (u, v, w, e)
-};
-
-// Record of position k of the cell's arrived (sorted) list.
-template <typename Rec>
-__device__ __forceinline__ Rec fetch_arrived(int k, int nfb, int fb, int Rn, long long Rend, int Sn, long long Sa,
-                                             int Ln, long long La, int fa, const Rec *in, const FarItem<Rec> *fs)
-{
-    int r = k;
-    if (r < nfb) return fs[fb + r].rec;
-    r -= nfb;
-    if (r < Rn) return ld_rec(in + (Rend - 1 - r));
-    r -= Rn;
-    if (r < Sn) return ld_rec(in + (Sa + r));
-    r -= Sn;
-    if (r < Ln) return ld_rec(in + (La + r));
-    r -= Ln;
-    return fs[fa + r].rec;
-}
-
 // Plain (coherent) loads for records written earlier in the same kernel.
 __device__ __forceinline__ RecF ld_rec_rw(const RecF *p)
 {
@@ -482,100 +410,271 @@ __device__ __forceinline__ RecD ld_rec_rw(const RecD *p)
     return RecD{a.x, a.y, b.x, b.y};
 }
 
-template <typename Rec>
-__device__ __forceinline__ int touched_slot(const WarpShared<Rec> &S, int x)
+// Address of position x of a cell's arrived (sorted) list: far movers from the left, the left
+// neighbour's R run (stored backwards), the cell's S run, the right neighbour's L run, far movers
+// from the right.
+template <typename Rec, typename FR>
+__device__ __forceinline__ Rec *arrived_ptr(int x, const CellHdr &h, Rec *in, FR *fs)
 {
-    int lo = 0, hi = S.ntouch;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (S.tidx[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+    int r = x;
+    if (r < h.nfb) return &fs[h.fb + r].rec;
+    r -= h.nfb;
+    if (r < h.Rn) return in + (h.Rend - 1 - r);
+    r -= h.Rn;
+    if (r < h.Sn) return in + (h.Sa + r);
+    r -= h.Sn;
+    if (r < h.Ln) return in + (h.La + r);
+    r -= h.Ln;
+    return &fs[h.fb + h.nfb + r].rec;
 }
 
-// Header of cell g (lane 0).
+// ------------------------------------------------------------------------------------------
+// Collision kernel.  Runs before the streaming kernel on the cells of class kClsDirect and
+// kClsStaged (work list built by k_offsets_flux):
+//   direct: the candidate pairs depend only on counters, so all of them (at most 32) are drawn at
+//           once; the touched particles (at most 64) are loaded into a shared-memory table keyed by
+//           list position, collided there in candidate order, and the changed ones written back in
+//           place, into the arrived runs or the far-mover list, where the streaming kernel reads them;
+//   staged: the survivors of the absorption draw (Eq. p) and the re-sampled particles (Eq.
+//           maxsample) are written to the first half of the cell's output block and collided there;
+//           the streaming kernel reads this list instead of the arrived runs.
+// ------------------------------------------------------------------------------------------
+constexpr int kHash = 128;             // slots of the touched-particle table (at most 2 x kMaxDirect keys)
+constexpr int kCollideThreads = 128;
+
 template <typename Rec>
-__device__ __noinline__ void cell_header(const EngineDev &E, int rp, int g, WarpShared<Rec> &S)
+struct CollideShared {
+    int key[kHash];     // list position of the particle held in the slot, -1 = empty
+    int own[kHash];     // lowest lane of the current batch whose candidate touches the slot (32 = none)
+    int mod[kHash];     // changed by an accepted collision
+    int ab[64];         // picks of a batch (staged cells)
+    Rec rec[kHash];
+};
+
+// Slot of list position x in the table (inserted if absent).  At most 64 keys share 128 slots, so
+// a free slot or the key itself is always found within the probe limit.
+__device__ __forceinline__ int hash_insert(int *key, int x, int32_t *err)
 {
-    const int wp = 1 - rp;
-    S.skip = 0;
-    S.staged = 0;
-    S.ncand = S.nacc = 0;
-    S.nL = S.nS = S.nR = 0;
-    S.n_in = S.n_surv = S.n_new = S.n_tot = 0;
-    S.nfb = S.nfa = S.fb = S.fa = 0;
-    S.Rn = S.Sn = S.Ln = 0;
-    S.ntouch = 0;
-    S.b = E.cell_inst[g];
-    if (S.b < 0) { S.skip = 1; return; }
-    const InstDev &I = E.inst[S.b];
-    S.i = g - I.cell_base - 1;
-    S.ghost = (S.i < 0) ? 1 : (S.i >= I.C ? 2 : 0);
-    S.slots = E.slots[g];
-    S.off_out = E.off[wp][g];
-    if (S.off_out + 2 * static_cast<long long>(S.slots) > E.capacity) {
-        set_err(E.err, kErrOverflow);
-        S.skip = 1;
-        return;
+    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> 25;
+    for (int it = 0; it < kHash; ++it) {
+        const int old = atomicCAS(&key[h], -1, x);
+        if (old == -1 || old == x) return static_cast<int>(h);
+        h = (h + 1u) & (kHash - 1);
     }
-    const uint32_t step = I.step;
-    if (S.ghost) {
-        const int side = S.ghost - 1;
-        const int bc = side ? I.bc_right : I.bc_left;
-        if (bc != 0) { S.skip = 1; return; }
-        double q[5];
-        const bool ok = ghost_prim(I, side, q, false, q);
-        for (int k = 0; k < 5; ++k) S.q[k] = q[k];
-        S.valid = ok;
-        S.P = split_fraction(I, q, ok);
-        S.rho_t = 0.0;
-        S.cmax = 0.0;
-        S.n_new = ok ? static_cast<int>(resample_count(I, static_cast<uint32_t>(S.i + 1), step, S.P, q[0])) : 0;
-        S.n_tot = S.n_new;
-        if (S.n_tot > S.slots) { set_err(E.err, kErrOverflow); S.skip = 1; }
-        return;
-    }
-    for (int k = 0; k < 5; ++k) S.q[k] = E.prim[5 * g + k];
-    S.valid = E.valid[g];
-    S.P = E.P[g];
-    S.rho_t = E.psi[5 * g];
-    S.cmax = E.cmax[g];
-    S.Rend = E.off[rp][g - 1] + 2 * static_cast<long long>(E.slotsb[rp][g - 1]);
-    S.Rn = E.nR[rp][g - 1];
-    S.Sa = E.off[rp][g];
-    S.Sn = E.nS[rp][g];
-    S.La = E.off[rp][g + 1] + E.slotsb[rp][g + 1];
-    S.Ln = E.nL[rp][g + 1];
-    const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-    const int nf = E.far_count[1];
-    if (nf > 0) {
-        const int lo = far_lower(fs, nf, g, INT32_MIN);
-        const int mid = far_lower(fs, nf, g, g + 2);
-        const int hi = far_lower(fs, nf, g + 1, INT32_MIN);
-        S.fb = lo;
-        S.nfb = mid - lo;
-        S.fa = mid;
-        S.nfa = hi - mid;
-    }
-    S.n_in = S.nfb + S.Rn + S.Sn + S.Ln + S.nfa;
-    if (S.n_in != E.cnt[g] || S.n_in > S.slots) {
-        set_err(E.err, kErrOverflow);
-        S.skip = 1;
-        return;
-    }
-    if (S.P > 0.0) { S.staged = 1; return; }
-    // P = 0: nothing is absorbed; the re-sampled count and the NTC candidate count are known now
-    const uint32_t id = static_cast<uint32_t>(S.i + 1);
-    S.n_surv = S.n_in;
-    const double rho_w = S.rho_t - static_cast<double>(S.n_in) * I.mp_over_dx;
-    S.n_new = S.valid ? static_cast<int>(resample_count(I, id, step, 0.0, rho_w)) : 0;
-    S.n_tot = S.n_in + S.n_new;
-    if (S.n_tot > S.slots) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
-    const int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, S.cmax, E.fmaj[g]);
-    if (nc < 0) { set_err(E.err, kErrOverflow); S.skip = 1; return; }
-    S.ncand = static_cast<int>(nc);
-    if (nc > kMaxCand) S.staged = 1;
+    set_err(err, kErrOverflow);
+    return 0;
 }
+
+template <typename Rec>
+__device__ void collide_direct(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, CollideShared<Rec> &S,
+                               Rec *in, FarItem<Rec> *fs)
+{
+    const int lane = threadIdx.x & 31;
+    const int N = h.n_in, nc = h.nc;
+    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
+    for (int t = lane; t < kHash; t += 32) { S.key[t] = -1; S.own[t] = 32; S.mod[t] = 0; }
+    __syncwarp();
+    const bool act = lane < nc;
+    int sa = 0, sb = 0;
+    uint32_t w2 = 0, w3 = 0;
+    if (act) {
+        uint32_t w[4];
+        draw(I, id, 2u * static_cast<uint32_t>(lane), step, kCollide, w);
+        const int a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
+        int b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
+        if (b >= a) ++b;
+        w2 = w[2];
+        w3 = w[3];
+        sa = hash_insert(S.key, a, E.err);
+        sb = hash_insert(S.key, b, E.err);
+    }
+    __syncwarp();
+    for (int t = lane; t < kHash; t += 32) {
+        const int x = S.key[t];
+        if (x >= 0) S.rec[t] = ld_rec_rw(arrived_ptr<Rec>(x, h, in, fs));
+    }
+    __syncwarp();
+    const double expo = 1.0 - 2.0 * I.upsilon;
+    const float expo_f = static_cast<float>(expo);
+    const double cm0 = E.cmax[g];
+    double cm = cm0;
+    int acc = 0;
+    for (int k0 = 0; k0 < nc;) {
+        const bool live = act && lane >= k0;
+        if (live) { atomicMin(&S.own[sa], lane); atomicMin(&S.own[sb], lane); }
+        __syncwarp();
+        const bool conf = live && (S.own[sa] < lane || S.own[sb] < lane);
+        const unsigned cmask = __ballot_sync(0xffffffffu, conf);
+        const int end1 = cmask ? __ffs(cmask) - 1 : nc;      // first candidate that shares a particle
+        const bool inb = live && lane < end1;
+        Rec A, B;
+        float cr32 = 0.f;
+        double cr = 0.0;
+        bool exact = false;
+        const float cm32 = static_cast<float>(cm);
+        if (inb) {
+            A = S.rec[sa];
+            B = S.rec[sb];
+            cr32 = rel_speed_f32(A, B);
+            if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
+                cr = rel_speed(A, B);
+                exact = true;
+            }
+        }
+        const unsigned rmask = __ballot_sync(0xffffffffu, inb && exact && cr > cm);
+        const int fr = rmask ? __ffs(rmask) - 1 : 32;
+        const int end = min(end1, fr + 1);
+        const double cr_r = __shfl_sync(0xffffffffu, cr, fr < 32 ? fr : 0);
+        bool accd = false;
+        if (live && lane < end) {
+            accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
+            if (accd) {
+                if (!exact) cr = rel_speed(A, B);
+                scatter_pair<Rec>(I, id, static_cast<uint32_t>(lane), step, A, B, cr);
+                S.rec[sa] = A;
+                S.rec[sb] = B;
+                S.mod[sa] = 1;
+                S.mod[sb] = 1;
+            }
+        }
+        acc += __popc(__ballot_sync(0xffffffffu, accd));
+        if (fr < end) cm = cr_r;
+        __syncwarp();
+        if (live) { S.own[sa] = 32; S.own[sb] = 32; }
+        __syncwarp();
+        k0 = end;
+    }
+    for (int t = lane; t < kHash; t += 32) {
+        const int x = S.key[t];
+        if (x >= 0 && S.mod[t]) st_rec(arrived_ptr<Rec>(x, h, in, fs), S.rec[t]);
+    }
+    if (lane == 0) {
+        E.ncand[g] = nc;
+        E.nacc[g] = acc;
+        if (cm != cm0) {
+            E.cmax[g] = cm;
+            E.fmaj[g] = majorant_factor(I, cm);
+        }
+    }
+}
+
+// Absorption draw u53(w0, w1) < P decided on the first word: with T = floor(P 2^32), w0 < T means
+// u < P and w0 > T means u >= P; only w0 = T needs the 53-bit value.
+__device__ __forceinline__ bool absorbed(uint32_t w0, uint32_t w1, double P, uint32_t T, bool all)
+{
+    if (all) return true;
+    if (w0 != T) return w0 < T;
+    return u53(w0, w1) < P;
+}
+
+template <typename Rec>
+__device__ void collide_staged(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, CollideShared<Rec> &S,
+                               Rec *in, Rec *out, FarItem<Rec> *fs)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
+    const double P = E.P[g];
+    const bool all = !(P < 1.0);                       // u53 < 1 always
+    const uint32_t T = all ? 0u : static_cast<uint32_t>(floor(P * 4294967296.0));
+    Rec *stage = out + h.off;
+    int run = 0;
+    for (int base = 0; base < h.n_in; base += 32) {
+        const int k = base + lane;
+        Rec v;
+        bool keep = false;
+        if (k < h.n_in) {
+            v = ld_rec_rw(arrived_ptr<Rec>(k, h, in, fs));
+            keep = true;
+            if (P > 0.0) {
+                uint32_t w[4];
+                draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
+                keep = !absorbed(w[0], w[1], P, T, all);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) st_rec(stage + run + __popc(m & lt), v);
+        run += __popc(m);
+    }
+    const double rho_t = E.psi[5 * g];
+    const double rho_w = rho_t - static_cast<double>(run) * I.mp_over_dx;
+    const int64_t nn = E.valid[g] ? resample_count(I, id, step, P, rho_w) : 0;
+    const int64_t n_tot = run + nn;
+    if (n_tot > h.slots) {
+        if (lane == 0) {
+            set_err(E.err, kErrOverflow);
+            E.hdr[g].cls = kClsSkip;
+        }
+        return;
+    }
+    double q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = E.prim[5 * g + k];
+    for (int j = lane; j < nn; j += 32)
+        st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, q));
+    __syncwarp();
+    const double cm0 = E.cmax[g];
+    double cmax = cm0;
+    int64_t nc = ntc_candidates(I, id, step, static_cast<int>(n_tot), rho_t, cmax, E.fmaj[g]);
+    if (nc < 0) {
+        if (lane == 0) set_err(E.err, kErrOverflow);
+        nc = 0;
+    }
+    int na = 0;
+    collide_list<Rec>(I, id, step, stage, static_cast<int>(n_tot), nc, cmax, na, S.ab);
+    if (lane == 0) {
+        E.ncand[g] = static_cast<int32_t>(nc);
+        E.nacc[g] = na;
+        E.nabs[g] = h.n_in - run;
+        E.nnew[g] = static_cast<int32_t>(nn);
+        if (cmax != cm0) {
+            E.cmax[g] = cmax;
+            E.fmaj[g] = majorant_factor(I, cmax);
+        }
+    }
+}
+
+template <typename Rec>
+__global__ void __launch_bounds__(kCollideThreads) k_collide(EngineDev E, int rp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CollideShared<Rec> &S = reinterpret_cast<CollideShared<Rec> *>(smraw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    Rec *in = static_cast<Rec *>(E.buf[rp]);
+    Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
+    FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
+    const int n_items = E.ticket[1];
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&E.ticket[0], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_items) break;
+        const int g = E.wl[t];
+        const CellHdr h = E.hdr[g];
+        const InstDev &I = E.inst[h.b];
+        if (h.cls == kClsDirect) collide_direct<Rec>(E, I, h, g, S, in, fs);
+        else if (h.cls == kClsStaged) collide_staged<Rec>(E, I, h, g, S, in, out, fs);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Streaming kernel: one warp per cell.
+//
+// Output block of a cell s (2 x slots records, slots = the bound on its list after re-sampling):
+// particles that stay (S) are written forward from the block start, those moving one cell left
+// (L) forward from the middle, those moving one cell right (R) backward from the end; each run
+// keeps the order the particles had before transport.  The sorted list of cell g for the next
+// step reads R(g-1) from its end backwards, then S(g), then L(g+1).  A staged cell's list lies
+// in the first half of its own block; its stayers are written back in place, never ahead of the
+// read position.
+// ------------------------------------------------------------------------------------------
+template <typename Rec>
+struct StreamCell {
+    const InstDev *I;
+    decltype(Rec().xl) dtdx;
+    int C, ci, dest_base, g;
+};
 
 struct StreamState {
     long long pS, pL, pR;                 // next write position of the S, L (forward) and R (backward) runs
@@ -584,20 +683,45 @@ struct StreamState {
     bool range_ok = true;
 };
 
-struct StreamCtx {
-    const InstDev *I;
-    const EngineDev *E;
-    int ci, cell_base, g;
-};
-
-// One group of 32 consecutive list positions (lanes in list order): transport, classification and
-// stable writes to the three runs.  The moments of the L and R runs are summed afterwards from the
-// runs themselves; only the rare cases are summed here: particles that move two or more cells or
-// leave the domain (their pre-transport moments leave the cell), and wall reflections (the normal
-// momentum a reflected particle carries changes sign: +2 u after the reflection).
+// Rare cases of one particle: it moved two or more cells or left the domain (its pre-transport
+// moments leave the cell; a far mover is appended to the far list), or it was reflected by a wall
+// (the normal momentum it carries changes sign: +2 u after the reflection).
 template <typename Rec>
-__device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool valid, int k, Rec *out,
-                                             FarItem<Rec> *fa, StreamState &st)
+__device__ __noinline__ void stream_rare(const EngineDev &E, int c, int dest, int src, int k, Rec v,
+                                         decltype(Rec().xl) u0, long long *a, int &ngone, bool &range_ok)
+{
+    range_ok = range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
+    if (c >= 3) {
+        ++ngone;
+        a[0] -= fx_vel(u0);
+        a[32] -= fx_vel(v.v);
+        a[64] -= fx_vel(v.w);
+        a[96] -= fx_energy(u0, v.v, v.w);
+    } else {
+        a[0] += fx_vel(v.u) - fx_vel(u0);
+    }
+    if (c == 3) {
+        const int slot = atomicAdd(&E.far_count[0], 1);
+        if (slot < E.far_cap) {
+            FarItem<Rec> it;
+            it.dest = dest;
+            it.src = src;
+            it.q = k;
+            it.pad = 0;
+            it.rec = v;
+            static_cast<FarItem<Rec> *>(E.far_app)[slot] = it;
+        } else {
+            set_err(E.err, kErrOverflow);
+        }
+    }
+}
+
+// One group of up to 32 consecutive list positions (lanes in list order): transport,
+// classification and stable writes to the three runs.  The moments of the L and R runs are summed
+// afterwards from the runs themselves; only the rare cases are summed here.
+template <typename Rec>
+__device__ __forceinline__ void stream_group(const StreamCell<Rec> &cx, const EngineDev &E, Rec v, bool valid, int k,
+                                             Rec *out, StreamState &st)
 {
     using T = decltype(Rec().xl);
     const int lane = threadIdx.x & 31;
@@ -607,42 +731,15 @@ __device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool va
         const T u0 = v.u;
         T xl = v.xl, uu = v.u;
         bool refl = false;
-        const int64_t d = transport(*cx.I, cx.ci, xl, uu, refl);
+        const int d = move_particle(*cx.I, cx.dtdx, cx.C, cx.ci, xl, uu, refl);
         v.xl = xl;
         v.u = uu;
         if (d < 0) c = 4;
-        else if (d == cx.ci - 1) c = 0;
         else if (d == cx.ci) c = 1;
+        else if (d == cx.ci - 1) c = 0;
         else if (d == cx.ci + 1) c = 2;
         else c = 3;
-        if (refl || c >= 3) {
-            long long *a = st.acc;
-            st.range_ok = st.range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
-            if (c >= 3) {
-                ++st.ngone;
-                a[0] -= fx_vel(u0);
-                a[32] -= fx_vel(v.v);
-                a[64] -= fx_vel(v.w);
-                a[96] -= fx_energy(u0, v.v, v.w);
-            } else {
-                a[0] += fx_vel(uu) - fx_vel(u0);
-            }
-            if (c == 3) {
-                const EngineDev &E = *cx.E;
-                const int slot = atomicAdd(&E.far_count[0], 1);
-                if (slot < E.far_cap) {
-                    FarItem<Rec> it;
-                    it.dest = cx.cell_base + 1 + static_cast<int>(d);
-                    it.src = cx.g;
-                    it.q = k;
-                    it.pad = 0;
-                    it.rec = v;
-                    fa[slot] = it;
-                } else {
-                    set_err(E.err, kErrOverflow);
-                }
-            }
-        }
+        if (refl || c >= 3) stream_rare<Rec>(E, c, cx.dest_base + d, cx.g, k, v, u0, st.acc, st.ngone, st.range_ok);
     }
     const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
     const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
@@ -653,6 +750,25 @@ __device__ __forceinline__ void stream_group(const StreamCtx &cx, Rec v, bool va
     st.pS += __popc(mS);
     st.pL += __popc(mL);
     st.pR -= __popc(mR);
+}
+
+// List positions [k0, k0 + n) whose records lie at p[dir * r], r = 0..n-1 (dir = -1: a run stored
+// backwards).  Any split of the list into consecutive groups gives the same stable order, so every
+// run is streamed in its own groups.  kCoherent: plain loads (records written earlier in this
+// kernel); otherwise read-only loads.
+template <typename Rec, bool kCoherent>
+__device__ __forceinline__ void stream_run(const StreamCell<Rec> &cx, const EngineDev &E, const Rec *p, int dir,
+                                           int n, int k0, Rec *out, StreamState &st)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < n; base += 64) {
+        const int r0 = base + lane, r1 = base + 32 + lane;
+        Rec v0, v1;
+        if (r0 < n) v0 = kCoherent ? ld_rec_rw(p + static_cast<long long>(dir) * r0) : ld_rec(p + static_cast<long long>(dir) * r0);
+        if (r1 < n) v1 = kCoherent ? ld_rec_rw(p + static_cast<long long>(dir) * r1) : ld_rec(p + static_cast<long long>(dir) * r1);
+        stream_group<Rec>(cx, E, v0, r0 < n, k0 + r0, out, st);
+        if (base + 32 < n) stream_group<Rec>(cx, E, v1, r1 < n, k0 + r1, out, st);
+    }
 }
 
 // Fixed-point sums (u, v, w, |xi|^2/2) of n contiguous records, each lane a strided share.
@@ -669,280 +785,137 @@ __device__ __forceinline__ void run_sums(const Rec *p, int n, long long s[4], bo
     }
 }
 
-template <typename Rec, int kMinBlocks>
-__global__ void __launch_bounds__(kMinBlocks == 1 ? 512 : 128, kMinBlocks) k_particles(EngineDev E, int rp)
+__device__ __forceinline__ long long warp_sum_ll(long long x)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    WarpShared<Rec> &S = reinterpret_cast<WarpShared<Rec> *>(smraw)[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <typename Rec, int kMinBlocks>
+__global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
+{
+    extern __shared__ __align__(16) long long s_acc[];   // per warp: 4 x 32 lane-private sums
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= E.G) return;
     const int wp = 1 - rp;
+    const CellHdr h = E.hdr[g];
+    int n_tot = 0;
+    if (h.cls == kClsStaged) n_tot = h.n_in - E.nabs[g] + E.nnew[g];
+    else if (h.cls != kClsSkip) n_tot = h.n_in + h.n_new;
+    if (h.cls == kClsSkip || n_tot > h.slots) {
+        if (h.cls != kClsSkip && lane == 0) set_err(E.err, kErrOverflow);
+        if (lane < 4) { E.AL[4 * g + lane] = 0.0; E.AR[4 * g + lane] = 0.0; }
+        if (lane < 5) E.Aself[5 * g + lane] = 0.0;
+        if (lane == 0) {
+            E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0; E.slotsb[wp][g] = 0;
+            E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0;
+        }
+        return;
+    }
+    const InstDev &I = E.inst[h.b];
+    const uint32_t step = I.step;
+    const uint32_t id = static_cast<uint32_t>(h.i + 1);
     const Rec *in = static_cast<const Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[wp]);
-    const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-    FarItem<Rec> *fa = static_cast<FarItem<Rec> *>(E.far_app);
-
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(E.ticket, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= E.G) break;
-        if (lane == 0) cell_header<Rec>(E, rp, g, S);
-        __syncwarp();
-        if (!S.skip) {
-            const InstDev &I = E.inst[S.b];
-            const uint32_t step = I.step;
-            const uint32_t id = static_cast<uint32_t>(S.i + 1);
-            const int ci = S.i, cell_base = I.cell_base;
-            const int nfb = S.nfb, fb = S.fb, Rn = S.Rn, Sn = S.Sn, Ln = S.Ln, fa_ = S.fa;
-            const long long Rend = S.Rend, Sa = S.Sa, La = S.La, off = S.off_out;
-            const int slots = S.slots;
-            const int n_in = S.n_in;
-            Rec *stage = out + off;
-            bool ok = true;
-
-            if (S.staged) {
-                // ---- survivors of the absorption draw (Eq. p) into the first half, in order
-                const double P = S.P;
-                int run = 0;
-                for (int base = 0; base < n_in; base += 32) {
-                    const int k = base + lane;
-                    Rec v;
-                    bool keep = false;
-                    if (k < n_in) {
-                        v = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
-                        keep = true;
-                        if (P > 0.0) {
-                            uint32_t w[4];
-                            draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
-                            keep = !(u53(w[0], w[1]) < P);
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if (keep) st_rec(stage + run + __popc(m & lt), v);
-                    run += __popc(m);
-                }
-                if (lane == 0) {
-                    S.n_surv = run;
-                    const double rho_w = S.rho_t - static_cast<double>(run) * I.mp_over_dx;
-                    S.n_new = S.valid ? static_cast<int>(resample_count(I, id, step, P, rho_w)) : 0;
-                    S.n_tot = run + S.n_new;
-                    if (S.n_tot > slots) { set_err(E.err, kErrOverflow); S.skip = 1; }
-                }
-                __syncwarp();
-                if (S.skip) {
-                    ok = false;
-                } else {
-                    // ---- re-sampled particles (Eq. maxsample) after the survivors, then collisions
-                    const int n_surv = S.n_surv;
-                    for (int j = lane; j < S.n_new; j += 32)
-                        st_rec(stage + n_surv + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, S.q));
-                    __syncwarp();
-                    double cmax = S.cmax;
-                    int na = 0;
-                    int64_t nc = ntc_candidates(I, id, step, S.n_tot, S.rho_t, cmax, E.fmaj[g]);
-                    if (nc < 0) {
-                        if (lane == 0) set_err(E.err, kErrOverflow);
-                        nc = 0;
-                    }
-                    collide_warp<Rec>(I, id, step, stage, S.n_tot, nc, cmax, na, S.ab, nullptr, 0);
-                    if (lane == 0) {
-                        S.ncand = static_cast<int>(nc);
-                        S.nacc = na;
-                        if (cmax != S.cmax) {
-                            E.cmax[g] = cmax;
-                            E.fmaj[g] = majorant_factor(I, cmax);
-                        }
-                    }
-                    __syncwarp();
-                }
-            } else if (S.ncand > 0) {
-                // ---- direct way: stage only the particles the candidates touch
-                const int nc = S.ncand, N = S.n_tot;
-                int a = 0x7fffffff, b = 0x7fffffff;
-                if (lane < nc) {
-                    uint32_t w[4];
-                    draw(I, id, static_cast<uint32_t>(2 * lane), step, kCollide, w);
-                    a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
-                    b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
-                    if (b >= a) ++b;
-                }
-                S.ab[lane] = a;
-                S.ab[32 + lane] = b;
-                __syncwarp();
-                // rank sort of the 64 picks, then drop repeats
-                int ra = 0, rb = 0;
-                for (int j = 0; j < 64; ++j) {
-                    const int x = S.ab[j];
-                    ra += (x < a) || (x == a && j < lane);
-                    rb += (x < b) || (x == b && j < 32 + lane);
-                }
-                __syncwarp();
-                S.tidx[ra] = a;
-                S.tidx[rb] = b;
-                __syncwarp();
-                const int v0 = S.tidx[2 * lane], v1 = S.tidx[2 * lane + 1];
-                const int p0 = (2 * lane == 0) ? 0x7ffffffe : S.tidx[2 * lane - 1];
-                const bool k0 = v0 != 0x7fffffff && v0 != p0;
-                const bool k1 = v1 != 0x7fffffff && v1 != v0;
-                const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-                const int before = __popc(m0 & lt) + __popc(m1 & lt);
-                __syncwarp();
-                if (k0) S.tidx[before] = v0;
-                if (k1) S.tidx[before + (k0 ? 1 : 0)] = v1;
-                const int nt = __popc(m0) + __popc(m1);
-                if (lane == 0) S.ntouch = nt;
-                __syncwarp();
-                for (int t = lane; t < nt; t += 32) {
-                    const int x = S.tidx[t];
-                    S.trec[t] = (x < n_in) ? fetch_arrived<Rec>(x, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs)
-                                           : sample_particle<Rec>(I, id, static_cast<uint32_t>(x - n_in), step, S.q);
-                }
-                __syncwarp();
-                double cmax = S.cmax;
-                int na = 0;
-                collide_warp<Rec>(I, id, step, S.trec, N, nc, cmax, na, S.ab, S.tidx, nt);
-                if (lane == 0) {
-                    S.nacc = na;
-                    if (cmax != S.cmax) {
-                        E.cmax[g] = cmax;
-                        E.fmaj[g] = majorant_factor(I, cmax);
-                    }
-                }
-                __syncwarp();
-            }
-
-            if (ok) {
-                // ---- streaming pass: transport (Step 3), classification, runs, flux sums
-                const int n_tot = S.n_tot;
-                const int ntouch = S.ntouch;
-                StreamState st;
-                st.pS = off;
-                st.pL = off + slots;
-                st.pR = off + 2 * static_cast<long long>(slots) - 1;
-                st.acc = &S.acc[0][lane];
+    const long long off = h.off;
+    const int slots = h.slots;
+    StreamCell<Rec> cx;
+    cx.I = &I;
+    if constexpr (sizeof(decltype(Rec().xl)) == 4) cx.dtdx = I.dtdx_f; else cx.dtdx = I.dtdx;
+    cx.C = I.C;
+    cx.ci = h.i;
+    cx.dest_base = I.cell_base + 1;
+    cx.g = g;
+    StreamState st;
+    st.pS = off;
+    st.pL = off + slots;
+    st.pR = off + 2 * static_cast<long long>(slots) - 1;
+    long long *accw = s_acc + 128 * warp;
+    st.acc = accw + lane;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) S.acc[j][lane] = 0;
-                const StreamCtx ctx{&I, &E, ci, cell_base, g};
-                if (S.staged) {
-                    for (int base = 0; base < n_tot; base += 128) {
-                        Rec v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = base + 32 * u + lane;
-                            if (k < n_tot) v[u] = ld_rec_rw(stage + k);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = base + 32 * u + lane;
-                            if (base + 32 * u < n_tot) stream_group<Rec>(ctx, v[u], k < n_tot, k, out, fa, st);
-                        }
-                    }
-                } else {
-                    int tp = 0;   // first touched index not below the current group
-                    for (int base = 0; base < n_in; base += 128) {
-                        Rec v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = base + 32 * u + lane;
-                            if (k < n_in) v[u] = fetch_arrived<Rec>(k, nfb, fb, Rn, Rend, Sn, Sa, Ln, La, fa_, in, fs);
-                        }
-                        if (ntouch > 0) {
-                            const int hi = min(base + 128, n_in);
-                            for (int t = tp; t < ntouch && S.tidx[t] < hi; ++t) {
-                                const int x = S.tidx[t];
-                                const int u = (x - base) >> 5;
-                                if (x >= base && (x & 31) == lane) {
-#pragma unroll
-                                    for (int uu = 0; uu < 4; ++uu)
-                                        if (uu == u) v[uu] = S.trec[t];
-                                }
-                            }
-                            while (tp < ntouch && S.tidx[tp] < hi) ++tp;
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = base + 32 * u + lane;
-                            if (base + 32 * u < n_in) stream_group<Rec>(ctx, v[u], k < n_in, k, out, fa, st);
-                        }
-                    }
-                    for (int base = n_in; base < n_tot; base += 32) {
-                        const int k = base + lane;
-                        Rec v;
-                        if (k < n_tot) {
-                            bool hit = false;
-                            for (int t = tp; t < ntouch && S.tidx[t] < base + 32; ++t)
-                                if (S.tidx[t] == k) { v = S.trec[t]; hit = true; }
-                            if (!hit) v = sample_particle<Rec>(I, id, static_cast<uint32_t>(k - n_in), step, S.q);
-                        }
-                        stream_group<Rec>(ctx, v, k < n_tot, k, out, fa, st);
-                        while (tp < ntouch && S.tidx[tp] < base + 32) ++tp;
-                    }
-                }
-                __syncwarp();
-                // moments of the L and R runs, read back with every lane busy
-                const int nLr = static_cast<int>(st.pL - (off + slots));
-                const int nRr = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
-                long long sLv[4] = {0, 0, 0, 0}, sRv[4] = {0, 0, 0, 0};
-                run_sums<Rec>(out + off + slots, nLr, sLv, st.range_ok);
-                run_sums<Rec>(out + st.pR + 1, nRr, sRv, st.range_ok);
-                if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
-                long long rv[8] = {sLv[0], sLv[1], sLv[2], sLv[3], sRv[0], sRv[1], sRv[2], sRv[3]};
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) rv[j] += __shfl_down_sync(0xffffffffu, rv[j], o);
-                }
-                int ngone = st.ngone;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ngone += __shfl_down_sync(0xffffffffu, ngone, o);
-                long long gone = 0;
-                if (lane < 4) {
-                    for (int l = 0; l < 32; ++l) gone += S.acc[lane][l];
-                }
-                // lane j < 4 needs rv[j] and rv[4 + j] from lane 0
-                long long lj = 0, rj = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const long long a0 = __shfl_sync(0xffffffffu, rv[j], 0);
-                    const long long b0 = __shfl_sync(0xffffffffu, rv[4 + j], 0);
-                    if (lane == j) { lj = a0; rj = b0; }
-                }
-                if (lane < 4) {
-                    const double sc = (lane == 3) ? 0x1p-32 : 0x1p-40;
-                    E.AL[4 * g + lane] = static_cast<double>(lj) * sc;
-                    E.AR[4 * g + lane] = static_cast<double>(rj) * sc;
-                    E.Aself[5 * g + 1 + lane] = static_cast<double>(gone - lj - rj) * sc;
-                }
-                if (lane == 0) {
-                    E.Aself[5 * g] = -static_cast<double>(ngone + nLr + nRr);
-                    S.nS = static_cast<int>(st.pS - off);
-                    S.nL = static_cast<int>(st.pL - (off + slots));
-                    S.nR = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
-                }
-            } else if (lane == 0) {
-                for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
-                for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
-                S.skip = 1;
-            }
-        } else if (lane == 0) {
-            for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
-            for (int k = 0; k < 5; ++k) E.Aself[5 * g + k] = 0.0;
+    for (int j = 0; j < 4; ++j) accw[32 * j + lane] = 0;
+    if (h.cls == kClsStaged) {
+        stream_run<Rec, true>(cx, E, out + off, 1, n_tot, 0, out, st);
+    } else {
+        // arrived list: far movers from the left, R(g-1) backwards, S(g), L(g+1), far movers from the right
+        const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
+        int k = 0;
+        for (int base = 0; base < h.nfb; base += 32) {
+            const int r = base + lane;
+            const bool ok = r < h.nfb;
+            Rec v;
+            if (ok) v = fs[h.fb + r].rec;
+            stream_group<Rec>(cx, E, v, ok, k + r, out, st);
         }
-        __syncwarp();
-        if (lane == 0) {
-            const int done = !S.skip;
-            if (done && !S.ghost) atomicAdd(&E.inst[S.b].updates, static_cast<unsigned long long>(S.n_tot));
-            E.nL[wp][g] = done ? S.nL : 0;
-            E.nS[wp][g] = done ? S.nS : 0;
-            E.nR[wp][g] = done ? S.nR : 0;
-            E.slotsb[wp][g] = done ? S.slots : 0;
-            E.ncand[g] = done ? S.ncand : 0;
-            E.nacc[g] = done ? S.nacc : 0;
-            E.nabs[g] = done ? S.n_in - S.n_surv : 0;
-            E.nnew[g] = done ? S.n_new : 0;
+        k += h.nfb;
+        stream_run<Rec, false>(cx, E, in + (h.Rend - 1), -1, h.Rn, k, out, st);
+        k += h.Rn;
+        stream_run<Rec, false>(cx, E, in + h.Sa, 1, h.Sn, k, out, st);
+        k += h.Sn;
+        stream_run<Rec, false>(cx, E, in + h.La, 1, h.Ln, k, out, st);
+        k += h.Ln;
+        for (int base = 0; base < h.nfa; base += 32) {
+            const int r = base + lane;
+            const bool ok = r < h.nfa;
+            Rec v;
+            if (ok) v = fs[h.fb + h.nfb + r].rec;
+            stream_group<Rec>(cx, E, v, ok, k + r, out, st);
         }
-        __syncwarp();
+        k += h.nfa;
+        if (h.n_new > 0) {
+            double q[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) q[j] = E.prim[5 * g + j];
+            for (int base = 0; base < h.n_new; base += 32) {
+                const int r = base + lane;
+                const bool ok = r < h.n_new;
+                Rec v;
+                if (ok) v = sample_particle<Rec>(I, id, static_cast<uint32_t>(r), step, q);
+                stream_group<Rec>(cx, E, v, ok, k + r, out, st);
+            }
+        }
+    }
+    __syncwarp();
+    // moments of the L and R runs, read back with every lane busy
+    const int nLr = static_cast<int>(st.pL - (off + slots));
+    const int nRr = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
+    long long sL[4] = {0, 0, 0, 0}, sR[4] = {0, 0, 0, 0};
+    run_sums<Rec>(out + off + slots, nLr, sL, st.range_ok);
+    run_sums<Rec>(out + st.pR + 1, nRr, sR, st.range_ok);
+    if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
+    long long gone[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        sL[j] = warp_sum_ll(sL[j]);
+        sR[j] = warp_sum_ll(sR[j]);
+        gone[j] = warp_sum_ll(accw[32 * j + lane]);
+    }
+    const int ngone = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(st.ngone));
+    // lane j < 4 writes component j
+    long long lj = 0, rj = 0, gj = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lane == j) { lj = sL[j]; rj = sR[j]; gj = gone[j]; }
+    if (lane < 4) {
+        const double sc = (lane == 3) ? 0x1p-32 : 0x1p-40;
+        E.AL[4 * g + lane] = static_cast<double>(lj) * sc;
+        E.AR[4 * g + lane] = static_cast<double>(rj) * sc;
+        E.Aself[5 * g + 1 + lane] = static_cast<double>(gj - lj - rj) * sc;
+    }
+    if (lane == 0) {
+        E.Aself[5 * g] = -static_cast<double>(ngone + nLr + nRr);
+        E.nS[wp][g] = static_cast<int>(st.pS - off);
+        E.nL[wp][g] = nLr;
+        E.nR[wp][g] = nRr;
+        E.slotsb[wp][g] = slots;
+        if (h.cls != kClsStaged) {
+            if (h.cls != kClsDirect) { E.ncand[g] = 0; E.nacc[g] = 0; }
+            E.nabs[g] = 0;
+            E.nnew[g] = h.n_new;
+        }
+        if (h.cls != kClsReservoir) atomicAdd(&E.inst[h.b].updates, static_cast<unsigned long long>(n_tot));
     }
 }
 
@@ -970,7 +943,9 @@ __global__ void k_far_sort(EngineDev E)
 }
 
 // ------------------------------------------------------------------------------------------
-// Cell kernel: Eq. (r1) update, time average, primitive state, P, slot bound of the next step.
+// Cell kernel: Eq. (r1) update, time average, primitive state, P, slot bound and plan of the next
+// step.  For P = 0 the re-sampled count and the NTC candidate count depend only on cell data and
+// counters, so they are decided here, one thread per cell, instead of inside the particle kernels.
 // ------------------------------------------------------------------------------------------
 template <typename Rec>
 __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int update)
@@ -978,13 +953,27 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     __shared__ int64_t s_w[kCellBlock / 32];
     const int g = blockIdx.x * kCellBlock + threadIdx.x;
     int64_t myslots = 0;
-    if (threadIdx.x == 0 && blockIdx.x == 0 && update) E.far_count[0] = 0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (update) E.far_count[0] = 0;
+        E.ticket[1] = 0;
+    }
     if (g < E.G) {
+        CellHdr hd;
+        hd.Rend = hd.Sa = hd.La = hd.off = 0;
+        hd.Rn = hd.Sn = hd.Ln = hd.slots = 0;
+        hd.fb = hd.nfb = hd.nfa = 0;
+        hd.n_in = hd.n_new = hd.nc = 0;
+        hd.cls = kClsSkip;
+        hd.b = -1;
+        hd.i = 0;
+        hd.pad[0] = hd.pad[1] = hd.pad[2] = 0;
         const int b = E.cell_inst[g];
         if (b >= 0) {
             const InstDev &I = E.inst[b];
             const int i = g - I.cell_base - 1;
             const uint32_t step_next = I.step + (update ? 1u : 0u);
+            hd.b = b;
+            hd.i = i;
             if (i < 0 || i >= I.C) {
                 const int side = (i < 0) ? 0 : 1;
                 const int bc = side ? I.bc_right : I.bc_left;
@@ -993,29 +982,44 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                     const bool ok = ghost_prim(I, side, qg, false, qg);
                     const double Pg = split_fraction(I, qg, ok);
                     myslots = ok ? resample_count(I, static_cast<uint32_t>(i + 1), step_next, Pg, qg[0]) : 0;
+                    for (int k = 0; k < 5; ++k) E.prim[5 * g + k] = qg[k];
+                    E.valid[g] = ok ? 1 : 0;
+                    E.P[g] = Pg;
+                    hd.cls = kClsReservoir;
+                    hd.n_new = static_cast<int32_t>(myslots);
                 }
                 E.cnt[g] = 0;
             } else {
                 // particles arriving in g and the sums of what they carry
-                int farn = 0;
+                int farn = 0, lo = 0, mid = 0;
                 double fsum[4] = {0, 0, 0, 0};
                 const int nf = E.far_count[1];
                 if (nf > 0) {
                     const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-                    int lo = far_lower(fs, nf, g, INT32_MIN);
-                    int hi = far_lower(fs, nf, g + 1, INT32_MIN);
+                    lo = far_lower(fs, nf, g, INT32_MIN);
+                    mid = far_lower(fs, nf, g, g + 2);
+                    const int hi = far_lower(fs, nf, g + 1, INT32_MIN);
                     farn = hi - lo;
                     for (int k = lo; k < hi; ++k) {
                         const double u = fs[k].rec.u, v = fs[k].rec.v, w = fs[k].rec.w;
                         fsum[0] += u; fsum[1] += v; fsum[2] += w; fsum[3] += 0.5 * (u * u + v * v + w * w);
                     }
+                    hd.fb = lo;
+                    hd.nfb = mid - lo;
+                    hd.nfa = hi - mid;
                 }
-                const int arrivals = E.nR[q][g - 1] + E.nS[q][g] + E.nL[q][g + 1] + farn;
+                hd.Rend = E.off[q][g - 1] + 2 * static_cast<int64_t>(E.slotsb[q][g - 1]);
+                hd.Rn = E.nR[q][g - 1];
+                hd.Sa = E.off[q][g];
+                hd.Sn = E.nS[q][g];
+                hd.La = E.off[q][g + 1] + E.slotsb[q][g + 1];
+                hd.Ln = E.nL[q][g + 1];
+                const int arrivals = hd.Rn + hd.Sn + hd.Ln + farn;
                 double *psi = E.psi + 5 * g;
                 if (update) {
                     const double *aR = E.AR + 4 * (g - 1), *aL = E.AL + 4 * (g + 1), *aS = E.Aself + 5 * g;
                     double dp[5];
-                    dp[0] = static_cast<double>(E.nR[q][g - 1] + E.nL[q][g + 1] + farn) + aS[0];
+                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + aS[0];
                     for (int k = 0; k < 4; ++k) dp[k + 1] = aR[k] + aL[k] + fsum[k] + aS[k + 1];
                     const double *Fl = E.flux + 5 * (g - 1), *Fr = E.flux + 5 * g;
                     for (int k = 0; k < 5; ++k) {
@@ -1044,9 +1048,34 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                 }
                 E.cnt[g] = arrivals;
                 myslots = arrivals + extra;
+                hd.n_in = arrivals;
+                if (P > 0.0) {
+                    hd.cls = kClsStaged;
+                } else {
+                    const int64_t n_tot = arrivals + extra;
+                    const int64_t nc = ntc_candidates(I, static_cast<uint32_t>(i + 1), step_next,
+                                                      static_cast<int>(n_tot), psi[0], E.cmax[g], E.fmaj[g]);
+                    hd.n_new = static_cast<int32_t>(extra);
+                    if (nc < 0 || n_tot > INT32_MAX) {
+                        set_err(E.err, kErrOverflow);
+                        hd.cls = kClsSkip;
+                    } else {
+                        hd.nc = static_cast<int32_t>(nc);
+                        if (nc == 0) hd.cls = kClsStream;
+                        else if (nc <= kMaxDirect && extra == 0) hd.cls = kClsDirect;
+                        else hd.cls = kClsStaged;
+                    }
+                }
             }
         }
+        if (myslots > INT32_MAX / 2) {
+            set_err(E.err, kErrOverflow);
+            myslots = 0;
+            hd.cls = kClsSkip;
+        }
+        hd.slots = static_cast<int32_t>(myslots);
         E.slots[g] = static_cast<int32_t>(myslots);
+        E.hdr[g] = hd;
     }
     // block sum of the slot bounds
     int64_t x = myslots;
@@ -1062,7 +1091,8 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
 }
 
 // ------------------------------------------------------------------------------------------
-// Offsets of the next step's output blocks and the wave flux of every interface.
+// Offsets of the next step's output blocks, the collision kernel's work list, and the wave flux of
+// every interface.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp, int advance)
 {
@@ -1095,12 +1125,28 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     __syncthreads();
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
+    bool listed = false;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
         E.off[wp][g] = o;
-        if (o + v > E.capacity) set_err(E.err, kErrOverflow);
+        E.hdr[g].off = o;
+        if (o + v > E.capacity) {
+            set_err(E.err, kErrOverflow);
+            E.hdr[g].cls = kClsSkip;
+        } else {
+            const int cls = E.hdr[g].cls;
+            listed = (cls == kClsDirect) || (cls == kClsStaged);
+        }
     }
-    if (g == 0) *E.ticket = 0;
+    // work list of the collision kernel (one atomic per warp)
+    const unsigned lm = __ballot_sync(0xffffffffu, listed);
+    if (lm) {
+        int base = 0;
+        if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[1], __popc(lm));
+        base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
+        if (listed) E.wl[base + __popc(lm & ((1u << lane) - 1u))] = g;
+    }
+    if (g == 0) E.ticket[0] = 0;
     if (g >= E.G) return;
     const int b = E.cell_inst[g];
     if (b < 0) return;
@@ -1217,11 +1263,12 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 // ------------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------------
-size_t particles_smem_bytes(int fp32, int threads)
+size_t stream_smem_bytes(int threads) { return static_cast<size_t>(threads / 32) * 128 * sizeof(long long); }
+size_t collide_smem_bytes(int fp32)
 {
-    const size_t per = fp32 ? sizeof(WarpShared<RecF>) : sizeof(WarpShared<RecD>);
-    return per * static_cast<size_t>(threads / 32);
+    return (fp32 ? sizeof(CollideShared<RecF>) : sizeof(CollideShared<RecD>)) * (kCollideThreads / 32);
 }
+int collide_threads() { return kCollideThreads; }
 
 template <typename K>
 static int occupancy_of(K kern, int threads, size_t smem)
@@ -1235,22 +1282,46 @@ static int occupancy_of(K kern, int threads, size_t smem)
     return n;
 }
 
-int particles_occupancy(int fp32, int variant, int threads, size_t smem)
+int stream_occupancy(int fp32, int variant, int threads)
 {
-    if (variant && threads > 128) return 0;
-    if (fp32) return variant ? occupancy_of(k_particles<RecF, 6>, threads, smem) : occupancy_of(k_particles<RecF, 1>, threads, smem);
-    return variant ? occupancy_of(k_particles<RecD, 6>, threads, smem) : occupancy_of(k_particles<RecD, 1>, threads, smem);
+    const size_t smem = stream_smem_bytes(threads);
+    if (fp32) {
+        if (variant == 2) return occupancy_of(k_stream<RecF, 3>, threads, smem);
+        if (variant == 1) return occupancy_of(k_stream<RecF, 2>, threads, smem);
+        return occupancy_of(k_stream<RecF, 1>, threads, smem);
+    }
+    if (variant == 2) return occupancy_of(k_stream<RecD, 3>, threads, smem);
+    if (variant == 1) return occupancy_of(k_stream<RecD, 2>, threads, smem);
+    return occupancy_of(k_stream<RecD, 1>, threads, smem);
 }
 
-cudaError_t launch_particles(const EngineDev &E, int fp32, int variant, int rp, int grid, int threads, size_t smem,
-                             cudaStream_t s)
+int collide_occupancy(int fp32)
 {
+    const size_t smem = collide_smem_bytes(fp32);
+    return fp32 ? occupancy_of(k_collide<RecF>, kCollideThreads, smem) : occupancy_of(k_collide<RecD>, kCollideThreads, smem);
+}
+
+cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s)
+{
+    const size_t smem = collide_smem_bytes(fp32);
+    if (fp32) k_collide<RecF><<<grid, kCollideThreads, smem, s>>>(E, rp);
+    else k_collide<RecD><<<grid, kCollideThreads, smem, s>>>(E, rp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s)
+{
+    const int wpb = threads / 32;
+    const int grid = (E.G + wpb - 1) / wpb;
+    const size_t smem = stream_smem_bytes(threads);
     if (fp32) {
-        if (variant) k_particles<RecF, 6><<<grid, threads, smem, s>>>(E, rp);
-        else k_particles<RecF, 1><<<grid, threads, smem, s>>>(E, rp);
+        if (variant == 2) k_stream<RecF, 3><<<grid, threads, smem, s>>>(E, rp);
+        else if (variant == 1) k_stream<RecF, 2><<<grid, threads, smem, s>>>(E, rp);
+        else k_stream<RecF, 1><<<grid, threads, smem, s>>>(E, rp);
     } else {
-        if (variant) k_particles<RecD, 6><<<grid, threads, smem, s>>>(E, rp);
-        else k_particles<RecD, 1><<<grid, threads, smem, s>>>(E, rp);
+        if (variant == 2) k_stream<RecD, 3><<<grid, threads, smem, s>>>(E, rp);
+        else if (variant == 1) k_stream<RecD, 2><<<grid, threads, smem, s>>>(E, rp);
+        else k_stream<RecD, 1><<<grid, threads, smem, s>>>(E, rp);
     }
     return cudaGetLastError();
 }

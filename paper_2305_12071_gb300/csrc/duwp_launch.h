@@ -7,10 +7,12 @@
 
 namespace duwp {
 
-// Particle kernel of one step: absorb, re-sample, collide, transport, write the L/S/R runs.
-// rp = parity of the buffer holding the arrived lists.  grid: persistent CTAs.
-cudaError_t launch_particles(const EngineDev &E, int fp32, int variant, int rp, int grid, int threads, size_t smem,
-                             cudaStream_t s);
+// Collision kernel of one step (cells of the work list): NTC collisions in place, or absorption,
+// re-sampling and collisions into the staged list.  rp = parity of the buffer holding the arrived
+// lists.  grid: persistent CTAs of collide_threads() threads.
+cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s);
+// Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s);
 // Sort of the particles that moved two or more cells.
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
 // Cell kernel: update Psi_t from the step's particle runs and wave flux (update = 1), then the
@@ -26,10 +28,14 @@ cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const do
 // Gather the stable sorted particle list of instance b into device arrays (debug/inspection).
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
                           int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s);
-// Kernel attributes (dynamic shared memory) of the particle kernel; returns blocks per SM.
-// variant 0: registers unconstrained; 1: capped (<= 128 threads, six blocks per SM)
-int particles_occupancy(int fp32, int variant, int threads, size_t smem);
-// dynamic shared memory of a particle-kernel block (one slice per warp)
-size_t particles_smem_bytes(int fp32, int threads);
+// Kernel attributes (dynamic shared memory) and blocks per SM of the streaming kernel.
+// variant 0: registers unconstrained (<= 128); 1: two 512-thread blocks per SM (<= 64 registers);
+// 2: three (<= 40 registers)
+int stream_occupancy(int fp32, int variant, int threads);
+size_t stream_smem_bytes(int threads);
+// The same for the collision kernel (fixed block size).
+int collide_occupancy(int fp32);
+size_t collide_smem_bytes(int fp32);
+int collide_threads();
 
 }  // namespace duwp

@@ -250,11 +250,12 @@ class Solver:
     def sync(self):
         _chk(self.L.duwp_sync(self.h), "duwp_sync")
 
+    KERNELS = ("k_collide", "k_stream", "k_far_sort", "k_cells", "k_offsets_flux")
+
     def step_timed(self, n: int):
-        """n steps as plain launches with CUDA events around each kernel: returns (kernel_ms[5]: summed
-        over the steps for particles, far sort, cells, offsets+flux, then the span of all n steps;
-        per-step ms)."""
-        k = np.zeros(5, np.float64)
+        """n steps as plain launches with CUDA events around each kernel: returns (kernel_ms[6]: summed
+        over the steps for the kernels named in KERNELS, then the span of all n steps; per-step ms)."""
+        k = np.zeros(6, np.float64)
         st = np.zeros(int(n), np.float64)
         _chk(self.L.duwp_step_timed(self.h, int(n), _dptr(k), _dptr(st)), "duwp_step_timed")
         return k, st

@@ -153,7 +153,7 @@ def test_launch_shape_does_not_change_results(precision):
     # threads per block (warps per block) and the register budget
     p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=8)
     ref = None
-    for t, r in ((128, 0), (32, 0), (256, 0), (512, 0), (128, 1), (64, 1)):
+    for t, r in ((128, 0), (32, 0), (256, 0), (512, 0), (128, 1), (512, 1), (64, 2), (512, 2)):
         s = solver(p)
         s.set_launch(t, r)
         s.step(6)
