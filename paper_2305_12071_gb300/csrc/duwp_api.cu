@@ -275,6 +275,11 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_ticket = c.take<int32_t>(4);
     const size_t o_hdr = c.take<CellHdr>(G);
     const size_t o_wl = c.take<int32_t>(G);
+    // chunks of re-sampled particles: at most one partial chunk per cell plus the re-sampled
+    // particles (at most half the slots of a buffer) in full chunks
+    const int64_t wls_cap = int64_t(G) + capacity / (2 * kSampleChunk) + 64;
+    if (wls_cap > INT32_MAX) return DUWP_EINVAL;
+    const size_t o_wls = c.take<int2>(size_t(wls_cap));
     const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
     const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
     const size_t o_buf0 = c.take<unsigned char>(rec * size_t(capacity));
@@ -321,6 +326,8 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.ticket = reinterpret_cast<int32_t *>(base + o_ticket);
     dev.hdr = reinterpret_cast<CellHdr *>(base + o_hdr);
     dev.wl = reinterpret_cast<int32_t *>(base + o_wl);
+    dev.wls = reinterpret_cast<int2 *>(base + o_wls);
+    dev.wls_cap = static_cast<int32_t>(wls_cap);
     dev.far_app = base + o_fa;
     dev.far_sorted = base + o_fs;
     dev.buf[0] = base + o_buf0;

@@ -124,10 +124,16 @@ struct EngineDev {
     void *far_sorted;          // the same, sorted by (dest, src, q)
     int32_t *far_count;        // [0]: appended, [1]: sorted
     int32_t *err;              // first device error
-    int32_t *ticket;           // [0]: work counter of the collision kernel, [1]: its work-list length
+    int32_t *ticket;           // collision kernel: [0]/[1] counter/length of the cell list, [2]/[3] of the sample list
     CellHdr *hdr;              // G: plan of each cell's particle work in the next step
     int32_t *wl;               // work list of the collision kernel (cells of class 2 and 3)
+    int2 *wls;                 // sample list: (cell, first index) of chunks of kSampleChunk re-sampled particles
+    int32_t wls_cap;           // entries of wls
 };
+
+// Re-sampled particles of classes 1 and 4 are drawn by the collision kernel in chunks of this many,
+// spread over all its warps, and written after the arrived positions of the cell's output block.
+constexpr int kSampleChunk = 64;
 
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels
 

@@ -656,6 +656,28 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(EngineDev E, int rp
         else if (h.cls == kClsStaged) collide_staged<Rec>(E, I, h, g, S, in, out, fs);
         __syncwarp();
     }
+    // re-sampled particles of cells without collisions (Eq. maxsample), chunk by chunk, into the
+    // positions after the cell's arrived list in its output block
+    const int n_chunks = min(E.ticket[2], E.wls_cap);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&E.ticket[3], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_chunks) break;
+        const int2 it = E.wls[t];
+        const int g = it.x, j0 = it.y;
+        const CellHdr &h = E.hdr[g];
+        const int b = h.b, n_in = h.n_in, n_new = h.n_new, cls = h.cls, i = h.i;
+        const long long off = h.off;
+        if (cls != kClsStream && cls != kClsReservoir) continue;
+        const InstDev &I = E.inst[b];
+        double q[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = E.prim[5 * g + k];
+        const int j1 = min(j0 + kSampleChunk, n_new);
+        for (int j = j0 + lane; j < j1; j += 32)
+            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, q));
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -864,18 +886,9 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
             stream_group<Rec>(cx, E, v, ok, k + r, out, st);
         }
         k += h.nfa;
-        if (h.n_new > 0) {
-            double q[5];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) q[j] = E.prim[5 * g + j];
-            for (int base = 0; base < h.n_new; base += 32) {
-                const int r = base + lane;
-                const bool ok = r < h.n_new;
-                Rec v;
-                if (ok) v = sample_particle<Rec>(I, id, static_cast<uint32_t>(r), step, q);
-                stream_group<Rec>(cx, E, v, ok, k + r, out, st);
-            }
-        }
+        // re-sampled particles, drawn by the collision kernel after the arrived positions (the
+        // stayers written so far lie below the read position)
+        stream_run<Rec, true>(cx, E, out + off + k, 1, h.n_new, k, out, st);
     }
     __syncwarp();
     // moments of the L and R runs, read back with every lane busy
@@ -956,6 +969,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (update) E.far_count[0] = 0;
         E.ticket[1] = 0;
+        E.ticket[2] = 0;
     }
     if (g < E.G) {
         CellHdr hd;
@@ -1126,6 +1140,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
+    int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
         E.off[wp][g] = o;
@@ -1136,6 +1151,27 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         } else {
             const int cls = E.hdr[g].cls;
             listed = (cls == kClsDirect) || (cls == kClsStaged);
+            if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
+        }
+    }
+    // sample list (one atomic per warp): chunk c of cell g starts at particle c * kSampleChunk
+    {
+        int incl = chunks;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total > 0) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&E.ticket[2], total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int first = base + incl - chunks;
+            for (int c = 0; c < chunks; ++c) {
+                if (first + c < E.wls_cap) E.wls[first + c] = make_int2(g, c * kSampleChunk);
+                else set_err(E.err, kErrOverflow);
+            }
         }
     }
     // work list of the collision kernel (one atomic per warp)
@@ -1146,7 +1182,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
         if (listed) E.wl[base + __popc(lm & ((1u << lane) - 1u))] = g;
     }
-    if (g == 0) E.ticket[0] = 0;
+    if (g == 0) { E.ticket[0] = 0; E.ticket[3] = 0; }
     if (g >= E.G) return;
     const int b = E.cell_inst[g];
     if (b < 0) return;
