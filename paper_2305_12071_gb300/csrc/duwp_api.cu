@@ -333,6 +333,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.buf[0] = base + o_buf0;
     dev.buf[1] = base + o_buf1;
     DUWP_CU(cudaMemsetAsync(dev.cell_inst, 0xff, sizeof(int32_t) * size_t(G), stream));
+    DUWP_CU(launch_init_turn(stream));
 
     int rc = configure_launch(threads, variant);
     if (rc != DUWP_OK) return rc;

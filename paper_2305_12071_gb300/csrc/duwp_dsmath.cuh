@@ -1,0 +1,180 @@
+// duwp_dsmath.cuh -- double-single (float-pair) arithmetic for the isotropic scattering of
+// single-precision particle records (Appendix A), so that the post-collision velocities are
+// computed on the single-precision pipes instead of the (slow) double-precision pipe.
+//
+// A value is an unevaluated sum hi + lo of two floats (about 48 significant bits).  Products use
+// the exact product error of a fused multiply-add; sums use the exact error of a rounded sum
+// (Knuth's TwoSum, Dekker's FastTwoSum); square roots take one Newton correction.  Written for
+// host and device so that the arithmetic can be checked on the CPU against double precision.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+namespace duwp {
+
+struct ds {
+    float hi, lo;
+};
+
+__host__ __device__ __forceinline__ uint32_t f_bits(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float bits_f(uint32_t u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+// s + e = a + b exactly (TwoSum)
+__host__ __device__ __forceinline__ ds ds_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+// s + e = a + b exactly, given |a| >= |b| or a = 0 (FastTwoSum)
+__host__ __device__ __forceinline__ ds ds_fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float e = b - (s - a);
+    return {s, e};
+}
+// p + e = a b exactly
+__host__ __device__ __forceinline__ ds ds_two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+// a + b; the error is below 2^-47 of |a| + |b|
+__host__ __device__ __forceinline__ ds ds_add(ds a, ds b)
+{
+    ds s = ds_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return ds_fast_two_sum(s.hi, s.lo);
+}
+__host__ __device__ __forceinline__ ds ds_neg(ds a) { return {-a.hi, -a.lo}; }
+// a b; relative error below 2^-46
+__host__ __device__ __forceinline__ ds ds_mul(ds a, ds b)
+{
+    ds p = ds_two_prod(a.hi, b.hi);
+    p.lo = fmaf(a.hi, b.lo, p.lo);
+    p.lo = fmaf(a.lo, b.hi, p.lo);
+    return ds_fast_two_sum(p.hi, p.lo);
+}
+// sqrt(a) for a > 0 (0 otherwise): y = sqrt(hi) corrected by (a - y^2) / (2 y)
+__host__ __device__ __forceinline__ ds ds_sqrt(ds a)
+{
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    const float y = sqrtf(a.hi);
+    const ds y2 = ds_two_prod(y, y);
+    const float r = (((a.hi - y2.hi) - y2.lo) + a.lo) / (2.0f * y);
+    return ds_fast_two_sum(y, r);
+}
+// double-single value of a double constant (hi the nearest float, lo the nearest float to the rest)
+__host__ __device__ constexpr ds ds_const(double x)
+{
+    return {static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x)))};
+}
+
+// Whether the single-precision rounding of every value within err of v.hi + v.lo is v.hi, i.e.
+// whether v.hi is the correct single-precision result even if the exact value differs from the
+// computed one by up to err.  v must be normalized (|lo| at most half an ulp of hi).
+__host__ __device__ __forceinline__ bool ds_rounds_to_hi(ds v, float err)
+{
+    const float a = fabsf(v.hi);
+    if (!(a >= 1e-30f && a < 1e30f)) return false;
+    const uint32_t b = f_bits(a);
+    const float ulp = bits_f(b & 0x7f800000u) * 0x1p-23f;
+    const float up = 0.5f * ulp;                                     // half ulp away from zero
+    const float dn = (b & 0x7fffffu) ? 0.5f * ulp : 0.25f * ulp;     // toward zero (below a power of 2)
+    const float l = (v.hi < 0.0f) ? -v.lo : v.lo;                    // low part in the direction of |hi|
+    const float e = 1.25f * err;
+    return (l + e < up) && (l - e > -dn);
+}
+
+// Turn table: cos and sin of 2 pi k / 64, k = 0..63, as double-single pairs (cos hi, cos lo,
+// sin hi, sin lo).
+constexpr int kTurnTable = 64;
+
+// Post-collision velocities of an accepted pair of single-precision records (isotropic VHS
+// scattering, Appendix A): the relative velocity keeps its magnitude c_r and takes the direction
+// with cos(theta) = 2 u1 - 1, phi = 2 pi u2, where u1 = u53(v0, v1) and u2 = u53(v2, v3) (53-bit
+// uniforms u53(a, b) = a 2^-32 + (b >> 11) 2^-53).  out = (u, v, w) of A then of B, each the
+// single-precision rounding of the exact value.  Returns false (out unusable) when that cannot be
+// guaranteed: when a computed value lies within 2^-40 (c_r + |(a+b)/2|) of a rounding boundary --
+// the double-single error is below 2^-43 of that and a double-precision evaluation of the same
+// formula deviates by less than 2^-42 -- or when sin(theta) < 2^-10, where the double-precision
+// form sqrt(1 - cos^2) itself loses accuracy.  The caller then evaluates in double precision.
+__host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au, float av, float aw, float bu,
+                                                    float bv, float bw, uint32_t v0, uint32_t v1, uint32_t v2,
+                                                    uint32_t v3, float out[6])
+{
+    constexpr ds kTwoPiDs = ds_const(6.283185307179586476925286766559);
+    constexpr ds kMinusSixth = ds_const(-1.0 / 6.0);
+    // relative speed c_r of the pair (the differences of two floats are exact pairs)
+    const ds du = ds_two_sum(au, -bu), dv = ds_two_sum(av, -bv), dw = ds_two_sum(aw, -bw);
+    const ds cr = ds_sqrt(ds_add(ds_add(ds_mul(du, du), ds_mul(dv, dv)), ds_mul(dw, dw)));
+    // cos(theta) = 2 u1 - 1 = (v0 - 2^31) 2^-31 + (v1 >> 11) 2^-52, split exactly into two floats
+    const int32_t c_int = static_cast<int32_t>(v0 - 0x80000000u);
+    const int32_t c_hi = c_int & ~0xff;
+    const uint32_t c_lo = (static_cast<uint32_t>(c_int & 0xff) << 21) | (v1 >> 11);
+    const ds ct = ds_two_sum(static_cast<float>(c_hi) * 0x1p-31f, static_cast<float>(c_lo) * 0x1p-52f);
+    // sin(theta) = sqrt((1 - ct)(1 + ct))
+    const ds st = ds_sqrt(ds_mul(ds_add({1.0f, 0.0f}, ds_neg(ct)), ds_add({1.0f, 0.0f}, ct)));
+    if (!(st.hi >= 0x1p-10f)) return false;
+    // phi = 2 pi u2 = 2 pi (K/64 + r), K = round(64 u2), |r| <= 1/128; r exact from the bits:
+    // r 2^32 = d + (v3 >> 11) 2^-21 with d = v2 - K 2^26 (32-bit wrap-around gives the sign)
+    const uint32_t K = (v2 >> 26) + ((v2 >> 25) & 1u);
+    const int32_t d = static_cast<int32_t>(v2 - (K << 26));
+    const int32_t d_hi = d & ~3;
+    const uint32_t r_lo = (static_cast<uint32_t>(d & 3) << 21) | (v3 >> 11);
+    const ds r = ds_two_sum(static_cast<float>(d_hi) * 0x1p-32f, static_cast<float>(r_lo) * 0x1p-53f);
+    const ds x = ds_mul(kTwoPiDs, r);                                 // |x| <= pi/64
+    const ds x2 = ds_mul(x, x);
+    // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040), cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720);
+    // the omitted terms are below 2^-49 for |x| <= pi/64
+    const float ts = x2.hi * (1.0f / 120.0f - x2.hi * (1.0f / 5040.0f));
+    const ds sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
+    const float tc = x2.hi * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
+    const ds cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
+    const float4 T = turn[K & (kTurnTable - 1)];
+    const ds C = {T.x, T.y}, S = {T.z, T.w};
+    const ds cp = ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
+    const ds sp = ds_add(ds_mul(S, cx), ds_mul(C, sx));
+    // relative velocity after the collision and the two velocities (a + b)/2 +- c/2
+    const ds crst = ds_mul(cr, st);
+    const ds c[3] = {ds_mul(crst, cp), ds_mul(crst, sp), ds_mul(cr, ct)};
+    const float a3[3] = {au, av, aw}, b3[3] = {bu, bv, bw};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ds m = ds_two_sum(a3[k], b3[k]);
+        const ds half_m = {0.5f * m.hi, 0.5f * m.lo};
+        const ds half_c = {0.5f * c[k].hi, 0.5f * c[k].lo};
+        const ds pa = ds_add(half_m, half_c), pb = ds_add(half_m, ds_neg(half_c));
+        const float err = 0x1p-40f * (cr.hi + fabsf(half_m.hi));
+        ok = ok && ds_rounds_to_hi(pa, err) && ds_rounds_to_hi(pb, err);
+        out[k] = pa.hi;
+        out[3 + k] = pb.hi;
+    }
+    return ok;
+}
+
+}  // namespace duwp

@@ -14,9 +14,24 @@
 //                 work list of the collision kernel, and the wave flux at every interface.
 #include <cstdio>
 
+#include "duwp_dsmath.cuh"
 #include "duwp_launch.h"
 
 namespace duwp {
+
+// cos and sin of 2 pi k / kTurnTable as double-single pairs (scattering of single-precision records)
+__device__ float4 g_turn[kTurnTable];
+
+__global__ void k_init_turn()
+{
+    const int k = threadIdx.x;
+    if (k >= kTurnTable) return;
+    double s, c;
+    sincospi(static_cast<double>(k) / (0.5 * kTurnTable), &s, &c);
+    const float ch = __double2float_rn(c), sh = __double2float_rn(s);
+    g_turn[k] = make_float4(ch, __double2float_rn(c - static_cast<double>(ch)), sh,
+                            __double2float_rn(s - static_cast<double>(sh)));
+}
 
 __device__ __forceinline__ void set_err(int32_t *err, int code) { atomicCAS(err, 0, code); }
 
@@ -252,15 +267,13 @@ __device__ __forceinline__ bool accept_pair(const InstDev &I, double expo, float
     return u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo));
 }
 
-// Isotropic VHS scattering of an accepted pair k (Appendix A): the relative velocity keeps its
-// magnitude c_r and takes the direction (theta, phi) with cos(theta) = 2 u1 - 1, phi = 2 pi u2.
+// Isotropic VHS scattering of an accepted pair (Appendix A) in double precision: the relative
+// velocity keeps its magnitude c_r and takes the direction (theta, phi) with cos(theta) = 2 u1 - 1,
+// phi = 2 pi u2 (u1, u2 from the draw v).
 template <typename Rec>
-__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, Rec &A, Rec &B,
-                                             double cr)
+__device__ __noinline__ void scatter_fp64(const uint32_t *v, Rec &A, Rec &B, double cr)
 {
     using T = decltype(A.xl);
-    uint32_t v[4];
-    draw(I, id, 2u * k + 1u, step, kCollide, v);
     const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
     const double st = sqrt(1.0 - ct * ct);
     double sp, cp;
@@ -274,6 +287,31 @@ __device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint
     B.u = store_val(m0 - c0 * 0.5, T());
     B.v = store_val(m1 - c1 * 0.5, T());
     B.w = store_val(m2 - c2 * 0.5, T());
+}
+
+// Scattering of accepted candidate k.  cr / exact: the double-precision relative speed when the
+// caller already has it.  Single-precision records are scattered in double-single arithmetic, which
+// yields the single-precision rounding of the same values as the double-precision evaluation; the
+// few pairs where that cannot be guaranteed take the double-precision path.
+__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecD &A, RecD &B,
+                                             double cr, bool exact)
+{
+    uint32_t v[4];
+    draw(I, id, 2u * k + 1u, step, kCollide, v);
+    scatter_fp64<RecD>(v, A, B, exact ? cr : rel_speed(A, B));
+}
+__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecF &A, RecF &B,
+                                             double cr, bool exact)
+{
+    uint32_t v[4];
+    draw(I, id, 2u * k + 1u, step, kCollide, v);
+    float o[6];
+    if (ds_scatter(g_turn, A.u, A.v, A.w, B.u, B.v, B.w, v[0], v[1], v[2], v[3], o)) {
+        A.u = o[0]; A.v = o[1]; A.w = o[2];
+        B.u = o[3]; B.v = o[4]; B.w = o[5];
+    } else {
+        scatter_fp64<RecF>(v, A, B, exact ? cr : rel_speed(A, B));
+    }
 }
 
 // The nc candidates of a staged cell list (nc from ntc_candidates), in order; candidate k is drawn
@@ -336,8 +374,7 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
         if (lane < m) {
             accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
-                if (!exact) cr = rel_speed(A, B);
-                scatter_pair<Rec>(I, id, static_cast<uint32_t>(k), step, A, B, cr);
+                scatter_pair(I, id, static_cast<uint32_t>(k), step, A, B, cr, exact);
                 list[a] = A;
                 list[b] = B;
             }
@@ -529,8 +566,7 @@ __device__ void collide_direct(const EngineDev &E, const InstDev &I, const CellH
         if (live && lane < end) {
             accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
-                if (!exact) cr = rel_speed(A, B);
-                scatter_pair<Rec>(I, id, static_cast<uint32_t>(lane), step, A, B, cr);
+                scatter_pair(I, id, static_cast<uint32_t>(lane), step, A, B, cr, exact);
                 S.rec[sa] = A;
                 S.rec[sb] = B;
                 S.mod[sa] = 1;
@@ -1382,6 +1418,12 @@ cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStr
 {
     const int grid = (E.G + kCellBlock - 1) / kCellBlock;
     k_offsets_flux<<<grid, kCellBlock, 0, s>>>(E, wp, advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_turn(cudaStream_t s)
+{
+    k_init_turn<<<1, kTurnTable, 0, s>>>();
     return cudaGetLastError();
 }
 

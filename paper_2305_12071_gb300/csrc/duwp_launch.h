@@ -22,6 +22,8 @@ cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaSt
 // Offsets of the next step's output blocks (write parity wp) and the wave flux at every
 // interface; advance = 1 also advances the per-instance step counters.
 cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStream_t s);
+// Turn table of the double-single scattering (idempotent; once per engine).
+cudaError_t launch_init_turn(cudaStream_t s);
 // Initial state of the cells [g0, g0 + n) of instance b (all wave, no particles).
 cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const double *left_cons,
                               const double *right_cons, double x_min, double x_split, cudaStream_t s);
