@@ -90,7 +90,9 @@ struct alignas(16) CellHdr {
     int32_t cls;        // CellClass
     int32_t b;          // instance
     int32_t i;          // local cell index (-1 and C: reservoirs)
-    int32_t pad[3];
+    int32_t C;          // cells of the instance
+    float dtdx_f;       // dt/dx of the instance in single precision (transport of FP32 records)
+    int32_t pad;
 };
 static_assert(sizeof(CellHdr) == 96, "cell header layout");
 

@@ -102,30 +102,6 @@ __device__ __forceinline__ int64_t apply_walls(const InstDev &I, int64_t dest, T
     return -1;   // more than 64 wall reflections within one step: removed
 }
 
-// Single-precision records: the displacement is converted with a 32-bit conversion when below
-// 2^30 cells (the integral value fk converts exactly) and the new cell index stays in 32 bits;
-// a particle that ends inside the domain needs no wall logic.
-__device__ __forceinline__ int move_particle(const InstDev &I, float dtdx, int C, int cell, float &xl, float &u,
-                                             bool &refl)
-{
-    const float s = __fmaf_rn(u, dtdx, xl);
-    if (!(fabsf(s) < 1e15f)) return -1;
-    const float fk = floorf(s);
-    float x = __fsub_rn(s, fk);
-    if (fabsf(fk) < 1073741824.0f) {
-        int k = __float2int_rz(fk);
-        if (x >= 1.0f) { x = 0.0f; k += 1; }
-        xl = x;
-        const int d = cell + k;   // |cell| < 2^30 and |k| <= 2^30: no overflow
-        if (static_cast<unsigned>(d) < static_cast<unsigned>(C)) return d;
-        return static_cast<int>(apply_walls<float>(I, d, xl, u, refl));
-    }
-    int64_t k = static_cast<int64_t>(fk);
-    if (x >= 1.0f) { x = 0.0f; k += 1; }
-    xl = x;
-    return static_cast<int>(apply_walls<float>(I, static_cast<int64_t>(cell) + k, xl, u, refl));
-}
-
 __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, double &xl, double &u, bool &refl)
 {
     const double s = __fma_rn(u, I.dtdx, xl);
@@ -136,11 +112,6 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, dou
     if (x >= 1.0) { x = 0.0; k += 1; }
     xl = x;
     return apply_walls<double>(I, cell + k, xl, u, refl);
-}
-
-__device__ __forceinline__ int move_particle(const InstDev &I, double, int, int cell, double &xl, double &u, bool &refl)
-{
-    return static_cast<int>(transport(I, cell, xl, u, refl));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -725,108 +696,130 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(EngineDev E, int rp
 // keeps the order the particles had before transport.  The sorted list of cell g for the next
 // step reads R(g-1) from its end backwards, then S(g), then L(g+1).  A staged cell's list lies
 // in the first half of its own block; its stayers are written back in place, never ahead of the
-// read position.
+// read position.  Any split of the list into consecutive groups gives the same stable order, so
+// every piece of the list is streamed in its own groups of 32.
+//
+// Register use decides the bandwidth of this kernel (it needs about 48 resident warps per SM to
+// keep HBM busy), so the loop state is small: the piece descriptors live in shared memory and the
+// rare cases (walls, wraps, leavers, moves of two or more cells) share one code path.
 // ------------------------------------------------------------------------------------------
+// One piece of a cell's list: list positions [k0, k0 + n); kind 0: records at p[dir * r], read-only
+// loads (arrived runs); 1: records at p[r], plain loads (records written by the collision kernel
+// into the output block); 2: the records of the sorted far-list items p[r].
 template <typename Rec>
-struct StreamCell {
-    const InstDev *I;
-    decltype(Rec().xl) dtdx;
-    int C, ci, dest_base, g;
+struct Piece {
+    const void *p;
+    int n, k0, dir, kind;
+};
+
+template <typename Rec>
+struct StreamShared {
+    long long acc[4][32];     // lane-private rare-path sums (u, v, w, |xi|^2/2)
+    Piece<Rec> piece[6];
 };
 
 struct StreamState {
-    long long pS, pL, pR;                 // next write position of the S, L (forward) and R (backward) runs
-    long long *acc;                       // this lane's column of the warp's rare-path sums (stride 32)
-    int ngone = 0;                        // far movers and removed particles of this lane
-    bool range_ok = true;
+    int oS, oL, oR;                       // next write offsets in the block: S, L (forward), R (backward)
+    int ngone;                            // far movers and removed particles of this lane
+    bool range_ok;
 };
 
-// Rare cases of one particle: it moved two or more cells or left the domain (its pre-transport
-// moments leave the cell; a far mover is appended to the far list), or it was reflected by a wall
-// (the normal momentum it carries changes sign: +2 u after the reflection).
-template <typename Rec>
-__device__ __noinline__ void stream_rare(const EngineDev &E, int c, int dest, int src, int k, Rec v,
-                                         decltype(Rec().xl) u0, long long *a, int &ngone, bool &range_ok)
+// Full transport of one particle (Step 3) with 64-bit cell arithmetic and the boundary conditions.
+__device__ __forceinline__ int64_t transport_full(const InstDev &I, int64_t cell, float &xl, float &u, bool &refl)
 {
-    range_ok = range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
-    if (c >= 3) {
-        ++ngone;
-        a[0] -= fx_vel(u0);
-        a[32] -= fx_vel(v.v);
-        a[64] -= fx_vel(v.w);
-        a[96] -= fx_energy(u0, v.v, v.w);
-    } else {
-        a[0] += fx_vel(v.u) - fx_vel(u0);
-    }
-    if (c == 3) {
-        const int slot = atomicAdd(&E.far_count[0], 1);
-        if (slot < E.far_cap) {
-            FarItem<Rec> it;
-            it.dest = dest;
-            it.src = src;
-            it.q = k;
-            it.pad = 0;
-            it.rec = v;
-            static_cast<FarItem<Rec> *>(E.far_app)[slot] = it;
-        } else {
-            set_err(E.err, kErrOverflow);
-        }
-    }
+    const float s = __fmaf_rn(u, I.dtdx_f, xl);
+    if (!(fabsf(s) < 1e15f)) return -1;
+    const float fk = floorf(s);
+    float x = __fsub_rn(s, fk);
+    int64_t k = static_cast<int64_t>(fk);
+    if (x >= 1.0f) { x = 0.0f; k += 1; }
+    xl = x;
+    return apply_walls<float>(I, cell + k, xl, u, refl);
+}
+__device__ __forceinline__ int64_t transport_full(const InstDev &I, int64_t cell, double &xl, double &u, bool &refl)
+{
+    return transport(I, cell, xl, u, refl);
 }
 
-// One group of up to 32 consecutive list positions (lanes in list order): transport,
-// classification and stable writes to the three runs.  The moments of the L and R runs are summed
-// afterwards from the runs themselves; only the rare cases are summed here.
+// Everything but a move to the same or a neighbouring cell inside the domain: wall reflections,
+// periodic wraps, particles that leave the domain or move two or more cells.  The particle is
+// transported from its original state with the boundary conditions; particles that move two or
+// more cells or leave take their pre-transport moments out of the cell (a far mover is appended to
+// the far list), a reflected particle's normal momentum changes sign (+2 u after the reflection).
+// Returns the class: 0 one cell left, 1 stays, 2 one cell right, 3 farther, 4 left the domain.
 template <typename Rec>
-__device__ __forceinline__ void stream_group(const StreamCell<Rec> &cx, const EngineDev &E, Rec v, bool valid, int k,
-                                             Rec *out, StreamState &st)
+__device__ __forceinline__ int stream_rare(const EngineDev &E, int g, int k, Rec &v, long long *a, StreamState &st)
 {
     using T = decltype(Rec().xl);
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int c = 5;
-    if (valid) {
-        const T u0 = v.u;
-        T xl = v.xl, uu = v.u;
-        bool refl = false;
-        const int d = move_particle(*cx.I, cx.dtdx, cx.C, cx.ci, xl, uu, refl);
-        v.xl = xl;
-        v.u = uu;
-        if (d < 0) c = 4;
-        else if (d == cx.ci) c = 1;
-        else if (d == cx.ci - 1) c = 0;
-        else if (d == cx.ci + 1) c = 2;
-        else c = 3;
-        if (refl || c >= 3) stream_rare<Rec>(E, c, cx.dest_base + d, cx.g, k, v, u0, st.acc, st.ngone, st.range_ok);
+    const CellHdr &h = E.hdr[g];
+    const InstDev &I = E.inst[h.b];
+    const int ci = h.i;
+    const T u0 = v.u;
+    bool refl = false;
+    const int64_t d = transport_full(I, ci, v.xl, v.u, refl);
+    int c;
+    if (d < 0) c = 4;
+    else if (d == ci) c = 1;
+    else if (d == ci - 1) c = 0;
+    else if (d == ci + 1) c = 2;
+    else c = 3;
+    if (refl || c >= 3) {
+        st.range_ok = st.range_ok && fx_in_range(u0) && fx_in_range(v.v) && fx_in_range(v.w);
+        if (c >= 3) {
+            ++st.ngone;
+            a[0] -= fx_vel(u0);
+            a[32] -= fx_vel(v.v);
+            a[64] -= fx_vel(v.w);
+            a[96] -= fx_energy(u0, v.v, v.w);
+        } else {
+            a[0] += fx_vel(v.u) - fx_vel(u0);
+        }
+        if (c == 3) {
+            const int slot = atomicAdd(&E.far_count[0], 1);
+            if (slot < E.far_cap) {
+                FarItem<Rec> it;
+                it.dest = I.cell_base + 1 + static_cast<int>(d);
+                it.src = g;
+                it.q = k;
+                it.pad = 0;
+                it.rec = v;
+                static_cast<FarItem<Rec> *>(E.far_app)[slot] = it;
+            } else {
+                set_err(E.err, kErrOverflow);
+            }
+        }
     }
-    const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
-    const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
-    const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
-    if (c == 1) st_rec(out + st.pS + __popc(mS & lt), v);
-    else if (c == 0) st_rec(out + st.pL + __popc(mL & lt), v);
-    else if (c == 2) st_rec(out + st.pR - __popc(mR & lt), v);
-    st.pS += __popc(mS);
-    st.pL += __popc(mL);
-    st.pR -= __popc(mR);
+    return c;
 }
 
-// List positions [k0, k0 + n) whose records lie at p[dir * r], r = 0..n-1 (dir = -1: a run stored
-// backwards).  Any split of the list into consecutive groups gives the same stable order, so every
-// run is streamed in its own groups.  kCoherent: plain loads (records written earlier in this
-// kernel); otherwise read-only loads.
-template <typename Rec, bool kCoherent>
-__device__ __forceinline__ void stream_run(const StreamCell<Rec> &cx, const EngineDev &E, const Rec *p, int dir,
-                                           int n, int k0, Rec *out, StreamState &st)
+// Same or neighbouring cell inside the domain, decided on the common path: c in {0, 1, 2}, or -1.
+__device__ __forceinline__ int move_near(float dtdx, int C, int ci, float &xl, float u)
 {
-    const int lane = threadIdx.x & 31;
-    for (int base = 0; base < n; base += 64) {
-        const int r0 = base + lane, r1 = base + 32 + lane;
-        Rec v0, v1;
-        if (r0 < n) v0 = kCoherent ? ld_rec_rw(p + static_cast<long long>(dir) * r0) : ld_rec(p + static_cast<long long>(dir) * r0);
-        if (r1 < n) v1 = kCoherent ? ld_rec_rw(p + static_cast<long long>(dir) * r1) : ld_rec(p + static_cast<long long>(dir) * r1);
-        stream_group<Rec>(cx, E, v0, r0 < n, k0 + r0, out, st);
-        if (base + 32 < n) stream_group<Rec>(cx, E, v1, r1 < n, k0 + r1, out, st);
-    }
+    const float s = __fmaf_rn(u, dtdx, xl);
+    if (!(fabsf(s) < 1073741824.0f)) return -1;
+    const float fk = floorf(s);
+    float x = __fsub_rn(s, fk);
+    int k = __float2int_rz(fk);                  // |fk| <= 2^30: exact
+    if (x >= 1.0f) { x = 0.0f; k += 1; }
+    const unsigned dd = static_cast<unsigned>(k + 1);
+    const int d = ci + k;                        // |ci| < 2^30, |k| <= 2^30: no overflow
+    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) return -1;
+    xl = x;
+    return static_cast<int>(dd);
+}
+__device__ __forceinline__ int move_near(double dtdx, int C, int ci, double &xl, double u)
+{
+    const double s = __fma_rn(u, dtdx, xl);
+    if (!(fabs(s) < 1073741824.0)) return -1;
+    const double fk = floor(s);
+    double x = __dsub_rn(s, fk);
+    int k = __double2int_rz(fk);
+    if (x >= 1.0) { x = 0.0; k += 1; }
+    const unsigned dd = static_cast<unsigned>(k + 1);
+    const int d = ci + k;
+    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) return -1;
+    xl = x;
+    return static_cast<int>(dd);
 }
 
 // Fixed-point sums (u, v, w, |xi|^2/2) of n contiguous records, each lane a strided share.
@@ -843,110 +836,144 @@ __device__ __forceinline__ void run_sums(const Rec *p, int n, long long s[4], bo
     }
 }
 
+// Warp sum of a 64-bit integer whose lane values stay below 2^62 in magnitude: three 32-bit
+// reductions of its 21-bit limbs (the limb sums of 32 lanes fit in 32 bits).
 __device__ __forceinline__ long long warp_sum_ll(long long x)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+    const unsigned a0 = static_cast<unsigned>(x) & 0x1fffffu;
+    const unsigned a1 = static_cast<unsigned>(x >> 21) & 0x1fffffu;
+    const int a2 = static_cast<int>(x >> 42);
+    const unsigned s0 = __reduce_add_sync(0xffffffffu, a0);
+    const unsigned s1 = __reduce_add_sync(0xffffffffu, a1);
+    const int s2 = __reduce_add_sync(0xffffffffu, a2);
+    return static_cast<long long>(s2) * (1LL << 42) + static_cast<long long>(s1) * (1LL << 21) + static_cast<long long>(s0);
+}
+
+// Outputs of a cell that streams nothing (skipped, or in error).
+__device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int wp)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < 4) { E.AL[4 * g + lane] = 0.0; E.AR[4 * g + lane] = 0.0; }
+    if (lane < 5) E.Aself[5 * g + lane] = 0.0;
+    if (lane == 0) {
+        E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0; E.slotsb[wp][g] = 0;
+        E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0;
+    }
 }
 
 template <typename Rec, int kMinBlocks>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
 {
-    extern __shared__ __align__(16) long long s_acc[];   // per warp: 4 x 32 lane-private sums
+    using T = decltype(Rec().xl);
+    extern __shared__ __align__(16) unsigned char s_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * (blockDim.x >> 5) + warp;
     if (g >= E.G) return;
+    StreamShared<Rec> &SS = reinterpret_cast<StreamShared<Rec> *>(s_raw)[warp];
     const int wp = 1 - rp;
-    const CellHdr h = E.hdr[g];
+    const CellHdr *hp = E.hdr + g;
+    const int cls = hp->cls;
     int n_tot = 0;
-    if (h.cls == kClsStaged) n_tot = h.n_in - E.nabs[g] + E.nnew[g];
-    else if (h.cls != kClsSkip) n_tot = h.n_in + h.n_new;
-    if (h.cls == kClsSkip || n_tot > h.slots) {
-        if (h.cls != kClsSkip && lane == 0) set_err(E.err, kErrOverflow);
-        if (lane < 4) { E.AL[4 * g + lane] = 0.0; E.AR[4 * g + lane] = 0.0; }
-        if (lane < 5) E.Aself[5 * g + lane] = 0.0;
-        if (lane == 0) {
-            E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0; E.slotsb[wp][g] = 0;
-            E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0;
-        }
+    if (cls == kClsStaged) n_tot = hp->n_in - E.nabs[g] + E.nnew[g];
+    else if (cls != kClsSkip) n_tot = hp->n_in + hp->n_new;
+    const int slots = hp->slots;
+    if (cls == kClsSkip || n_tot > slots) {
+        if (cls != kClsSkip && lane == 0) set_err(E.err, kErrOverflow);
+        stream_cell_empty(E, g, wp);
         return;
     }
-    const InstDev &I = E.inst[h.b];
-    const uint32_t step = I.step;
-    const uint32_t id = static_cast<uint32_t>(h.i + 1);
-    const Rec *in = static_cast<const Rec *>(E.buf[rp]);
-    Rec *out = static_cast<Rec *>(E.buf[wp]);
-    const long long off = h.off;
-    const int slots = h.slots;
-    StreamCell<Rec> cx;
-    cx.I = &I;
-    if constexpr (sizeof(decltype(Rec().xl)) == 4) cx.dtdx = I.dtdx_f; else cx.dtdx = I.dtdx;
-    cx.C = I.C;
-    cx.ci = h.i;
-    cx.dest_base = I.cell_base + 1;
-    cx.g = g;
-    StreamState st;
-    st.pS = off;
-    st.pL = off + slots;
-    st.pR = off + 2 * static_cast<long long>(slots) - 1;
-    long long *accw = s_acc + 128 * warp;
-    st.acc = accw + lane;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) accw[32 * j + lane] = 0;
-    if (h.cls == kClsStaged) {
-        stream_run<Rec, true>(cx, E, out + off, 1, n_tot, 0, out, st);
-    } else {
-        // arrived list: far movers from the left, R(g-1) backwards, S(g), L(g+1), far movers from the right
+    Rec *blk = static_cast<Rec *>(E.buf[wp]) + hp->off;
+    // pieces of the list, in list order
+    if (lane == 0) {
+        const Rec *in = static_cast<const Rec *>(E.buf[rp]);
         const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-        int k = 0;
-        for (int base = 0; base < h.nfb; base += 32) {
-            const int r = base + lane;
-            const bool ok = r < h.nfb;
-            Rec v;
-            if (ok) v = fs[h.fb + r].rec;
-            stream_group<Rec>(cx, E, v, ok, k + r, out, st);
+        if (cls == kClsStaged) {
+            for (int q = 0; q < 5; ++q) SS.piece[q] = Piece<Rec>{blk, 0, 0, 1, 1};
+            SS.piece[5] = Piece<Rec>{blk, n_tot, 0, 1, 1};
+        } else {
+            int k = 0;
+            SS.piece[0] = Piece<Rec>{fs + hp->fb, hp->nfb, k, 1, 2};
+            k += hp->nfb;
+            SS.piece[1] = Piece<Rec>{in + (hp->Rend - 1), hp->Rn, k, -1, 0};
+            k += hp->Rn;
+            SS.piece[2] = Piece<Rec>{in + hp->Sa, hp->Sn, k, 1, 0};
+            k += hp->Sn;
+            SS.piece[3] = Piece<Rec>{in + hp->La, hp->Ln, k, 1, 0};
+            k += hp->Ln;
+            SS.piece[4] = Piece<Rec>{fs + hp->fb + hp->nfb, hp->nfa, k, 1, 2};
+            k += hp->nfa;
+            // re-sampled particles, drawn by the collision kernel after the arrived positions (the
+            // stayers written so far lie below the read position)
+            SS.piece[5] = Piece<Rec>{blk + k, n_tot - k, k, 1, 1};
         }
-        k += h.nfb;
-        stream_run<Rec, false>(cx, E, in + (h.Rend - 1), -1, h.Rn, k, out, st);
-        k += h.Rn;
-        stream_run<Rec, false>(cx, E, in + h.Sa, 1, h.Sn, k, out, st);
-        k += h.Sn;
-        stream_run<Rec, false>(cx, E, in + h.La, 1, h.Ln, k, out, st);
-        k += h.Ln;
-        for (int base = 0; base < h.nfa; base += 32) {
-            const int r = base + lane;
-            const bool ok = r < h.nfa;
-            Rec v;
-            if (ok) v = fs[h.fb + h.nfb + r].rec;
-            stream_group<Rec>(cx, E, v, ok, k + r, out, st);
+    }
+    long long *acc = &SS.acc[0][lane];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[32 * j] = 0;
+    __syncwarp();
+    T dtdx;
+    if constexpr (sizeof(T) == 4) dtdx = hp->dtdx_f;
+    else dtdx = E.inst[hp->b].dtdx;
+    const int C = hp->C, ci = hp->i;
+    const unsigned lt = (1u << lane) - 1u;
+    StreamState st;
+    st.oS = 0;
+    st.oL = slots;
+    st.oR = 2 * slots - 1;
+    st.ngone = 0;
+    st.range_ok = true;
+    for (int q = 0; q < 6; ++q) {
+        const void *p = SS.piece[q].p;
+        const int n = SS.piece[q].n, k0 = SS.piece[q].k0, dir = SS.piece[q].dir, kind = SS.piece[q].kind;
+        for (int base = 0; base < n; base += 64) {
+            Rec v[2];
+#pragma unroll
+            for (int u2 = 0; u2 < 2; ++u2) {
+                const int r = base + 32 * u2 + lane;
+                if (r < n) {
+                    if (kind == 0) v[u2] = ld_rec(static_cast<const Rec *>(p) + dir * r);
+                    else if (kind == 1) v[u2] = ld_rec_rw(static_cast<const Rec *>(p) + r);
+                    else v[u2] = static_cast<const FarItem<Rec> *>(p)[r].rec;
+                }
+            }
+#pragma unroll
+            for (int u2 = 0; u2 < 2; ++u2) {
+                const int r = base + 32 * u2 + lane;
+                if (base + 32 * u2 >= n) break;
+                int c = 5;
+                if (r < n) {
+                    c = move_near(dtdx, C, ci, v[u2].xl, v[u2].u);
+                    if (c < 0) c = stream_rare<Rec>(E, g, k0 + r, v[u2], acc, st);
+                }
+                const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
+                const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
+                const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
+                const unsigned m = (c == 0) ? mL : ((c == 1) ? mS : mR);
+                const int rk = __popc(m & lt);
+                const int o = (c == 0) ? st.oL + rk : ((c == 1) ? st.oS + rk : st.oR - rk);
+                if (c < 3) st_rec(blk + o, v[u2]);
+                st.oS += __popc(mS);
+                st.oL += __popc(mL);
+                st.oR -= __popc(mR);
+            }
         }
-        k += h.nfa;
-        // re-sampled particles, drawn by the collision kernel after the arrived positions (the
-        // stayers written so far lie below the read position)
-        stream_run<Rec, true>(cx, E, out + off + k, 1, h.n_new, k, out, st);
     }
     __syncwarp();
     // moments of the L and R runs, read back with every lane busy
-    const int nLr = static_cast<int>(st.pL - (off + slots));
-    const int nRr = static_cast<int>(off + 2 * static_cast<long long>(slots) - 1 - st.pR);
+    const int nLr = st.oL - slots;
+    const int nRr = 2 * slots - 1 - st.oR;
     long long sL[4] = {0, 0, 0, 0}, sR[4] = {0, 0, 0, 0};
-    run_sums<Rec>(out + off + slots, nLr, sL, st.range_ok);
-    run_sums<Rec>(out + st.pR + 1, nRr, sR, st.range_ok);
-    if (!__all_sync(0xffffffffu, st.range_ok) && lane == 0) set_err(E.err, kErrOverflow);
-    long long gone[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        sL[j] = warp_sum_ll(sL[j]);
-        sR[j] = warp_sum_ll(sR[j]);
-        gone[j] = warp_sum_ll(accw[32 * j + lane]);
-    }
-    const int ngone = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(st.ngone));
-    // lane j < 4 writes component j
+    bool ok = st.range_ok;
+    run_sums<Rec>(blk + slots, nLr, sL, ok);
+    run_sums<Rec>(blk + st.oR + 1, nRr, sR, ok);
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) set_err(E.err, kErrOverflow);
     long long lj = 0, rj = 0, gj = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (lane == j) { lj = sL[j]; rj = sR[j]; gj = gone[j]; }
+    for (int j = 0; j < 4; ++j) {
+        const long long a = warp_sum_ll(sL[j]), b = warp_sum_ll(sR[j]), c = warp_sum_ll(acc[32 * j]);
+        if (lane == j) { lj = a; rj = b; gj = c; }
+    }
+    const int ngone = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(st.ngone));
     if (lane < 4) {
         const double sc = (lane == 3) ? 0x1p-32 : 0x1p-40;
         E.AL[4 * g + lane] = static_cast<double>(lj) * sc;
@@ -955,16 +982,16 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
     }
     if (lane == 0) {
         E.Aself[5 * g] = -static_cast<double>(ngone + nLr + nRr);
-        E.nS[wp][g] = static_cast<int>(st.pS - off);
+        E.nS[wp][g] = st.oS;
         E.nL[wp][g] = nLr;
         E.nR[wp][g] = nRr;
         E.slotsb[wp][g] = slots;
-        if (h.cls != kClsStaged) {
-            if (h.cls != kClsDirect) { E.ncand[g] = 0; E.nacc[g] = 0; }
+        if (cls != kClsStaged) {
+            if (cls != kClsDirect) { E.ncand[g] = 0; E.nacc[g] = 0; }
             E.nabs[g] = 0;
-            E.nnew[g] = h.n_new;
+            E.nnew[g] = hp->n_new;
         }
-        if (h.cls != kClsReservoir) atomicAdd(&E.inst[h.b].updates, static_cast<unsigned long long>(n_tot));
+        if (cls != kClsReservoir) atomicAdd(&E.inst[hp->b].updates, static_cast<unsigned long long>(n_tot));
     }
 }
 
@@ -1016,7 +1043,9 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
         hd.cls = kClsSkip;
         hd.b = -1;
         hd.i = 0;
-        hd.pad[0] = hd.pad[1] = hd.pad[2] = 0;
+        hd.C = 0;
+        hd.dtdx_f = 0.0f;
+        hd.pad = 0;
         const int b = E.cell_inst[g];
         if (b >= 0) {
             const InstDev &I = E.inst[b];
@@ -1024,6 +1053,8 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
             const uint32_t step_next = I.step + (update ? 1u : 0u);
             hd.b = b;
             hd.i = i;
+            hd.C = I.C;
+            hd.dtdx_f = I.dtdx_f;
             if (i < 0 || i >= I.C) {
                 const int side = (i < 0) ? 0 : 1;
                 const int bc = side ? I.bc_right : I.bc_left;
@@ -1335,18 +1366,23 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 // ------------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------------
-size_t stream_smem_bytes(int threads) { return static_cast<size_t>(threads / 32) * 128 * sizeof(long long); }
+size_t stream_smem_bytes(int fp32, int threads)
+{
+    return static_cast<size_t>(threads / 32) * (fp32 ? sizeof(StreamShared<RecF>) : sizeof(StreamShared<RecD>));
+}
 size_t collide_smem_bytes(int fp32)
 {
     return (fp32 ? sizeof(CollideShared<RecF>) : sizeof(CollideShared<RecD>)) * (kCollideThreads / 32);
 }
 int collide_threads() { return kCollideThreads; }
 
+// Sets the kernel's dynamic shared-memory limit to smem_max (the largest any launch shape uses, so
+// that engines with different shapes can coexist) and returns blocks per SM at `threads`, `smem`.
 template <typename K>
-static int occupancy_of(K kern, int threads, size_t smem)
+static int occupancy_of(K kern, int threads, size_t smem, size_t smem_max)
 {
     int n = 0;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -1356,21 +1392,22 @@ static int occupancy_of(K kern, int threads, size_t smem)
 
 int stream_occupancy(int fp32, int variant, int threads)
 {
-    const size_t smem = stream_smem_bytes(threads);
+    const size_t smem = stream_smem_bytes(fp32, threads), mx = stream_smem_bytes(fp32, 512);
     if (fp32) {
-        if (variant == 2) return occupancy_of(k_stream<RecF, 3>, threads, smem);
-        if (variant == 1) return occupancy_of(k_stream<RecF, 2>, threads, smem);
-        return occupancy_of(k_stream<RecF, 1>, threads, smem);
+        if (variant == 2) return occupancy_of(k_stream<RecF, 3>, threads, smem, mx);
+        if (variant == 1) return occupancy_of(k_stream<RecF, 2>, threads, smem, mx);
+        return occupancy_of(k_stream<RecF, 1>, threads, smem, mx);
     }
-    if (variant == 2) return occupancy_of(k_stream<RecD, 3>, threads, smem);
-    if (variant == 1) return occupancy_of(k_stream<RecD, 2>, threads, smem);
-    return occupancy_of(k_stream<RecD, 1>, threads, smem);
+    if (variant == 2) return occupancy_of(k_stream<RecD, 3>, threads, smem, mx);
+    if (variant == 1) return occupancy_of(k_stream<RecD, 2>, threads, smem, mx);
+    return occupancy_of(k_stream<RecD, 1>, threads, smem, mx);
 }
 
 int collide_occupancy(int fp32)
 {
     const size_t smem = collide_smem_bytes(fp32);
-    return fp32 ? occupancy_of(k_collide<RecF>, kCollideThreads, smem) : occupancy_of(k_collide<RecD>, kCollideThreads, smem);
+    return fp32 ? occupancy_of(k_collide<RecF>, kCollideThreads, smem, smem)
+                : occupancy_of(k_collide<RecD>, kCollideThreads, smem, smem);
 }
 
 cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s)
@@ -1385,7 +1422,7 @@ cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int
 {
     const int wpb = threads / 32;
     const int grid = (E.G + wpb - 1) / wpb;
-    const size_t smem = stream_smem_bytes(threads);
+    const size_t smem = stream_smem_bytes(fp32, threads);
     if (fp32) {
         if (variant == 2) k_stream<RecF, 3><<<grid, threads, smem, s>>>(E, rp);
         else if (variant == 1) k_stream<RecF, 2><<<grid, threads, smem, s>>>(E, rp);
