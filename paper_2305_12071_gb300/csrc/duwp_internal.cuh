@@ -126,12 +126,20 @@ struct EngineDev {
     void *far_sorted;          // the same, sorted by (dest, src, q)
     int32_t *far_count;        // [0]: appended, [1]: sorted
     int32_t *err;              // first device error
-    int32_t *ticket;           // collision kernel: [0]/[1] counter/length of the cell list, [2]/[3] of the sample list
+    int32_t *ticket;           // collision kernel work counters and list lengths (kTickets, see below)
     CellHdr *hdr;              // G: plan of each cell's particle work in the next step
-    int32_t *wl;               // work list of the collision kernel (cells of class 2 and 3)
+    int32_t *wl;               // 4 x G: work lists of the collision kernel (direct cells with up to 8, 16,
+                               // 32 candidates; staged cells)
     int2 *wls;                 // sample list: (cell, first index) of chunks of kSampleChunk re-sampled particles
     int32_t wls_cap;           // entries of wls
 };
+
+// ticket[q] (q < 4): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
+// and ticket[kSampleCtr]: length of and next item of the sample list.
+constexpr int kListLen = 4;
+constexpr int kSampleLen = 8;
+constexpr int kSampleCtr = 9;
+constexpr int kTickets = 16;
 
 // Re-sampled particles of classes 1 and 4 are drawn by the collision kernel in chunks of this many,
 // spread over all its warps, and written after the arrived positions of the cell's output block.

@@ -459,108 +459,130 @@ struct CollideShared {
     Rec rec[kHash];
 };
 
-// Slot of list position x in the table (inserted if absent).  At most 64 keys share 128 slots, so
-// a free slot or the key itself is always found within the probe limit.
+// Slot of list position x in a table of NS slots (inserted if absent).  At most NS/2 keys share
+// the NS slots, so a free slot or the key itself is always found within the probe limit.
+template <int NS>
 __device__ __forceinline__ int hash_insert(int *key, int x, int32_t *err)
 {
-    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> 25;
-    for (int it = 0; it < kHash; ++it) {
+    constexpr int kShift = (NS == 32) ? 27 : ((NS == 64) ? 26 : 25);
+    static_assert(NS == 32 || NS == 64 || NS == 128, "table size");
+    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> kShift;
+    for (int it = 0; it < NS; ++it) {
         const int old = atomicCAS(&key[h], -1, x);
         if (old == -1 || old == x) return static_cast<int>(h);
-        h = (h + 1u) & (kHash - 1);
+        h = (h + 1u) & (NS - 1);
     }
     set_err(err, kErrOverflow);
     return 0;
 }
 
-template <typename Rec>
-__device__ void collide_direct(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, CollideShared<Rec> &S,
-                               Rec *in, FarItem<Rec> *fs)
+// Direct cells, 32/Z per warp: lanes [s Z, (s+1) Z) handle the cell g of segment s (g < 0: none),
+// lane l of the segment candidate l (at most Z candidates), with the segment's own 4Z-slot table.
+// Every ballot is taken by the whole warp and masked to the segment, so each segment follows
+// exactly the batches of a one-cell warp.
+template <typename Rec, int Z>
+__device__ __noinline__ void collide_direct(const EngineDev &E, int g, CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
 {
+    constexpr int NS = 4 * Z;
     const int lane = threadIdx.x & 31;
-    const int N = h.n_in, nc = h.nc;
-    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
-    for (int t = lane; t < kHash; t += 32) { S.key[t] = -1; S.own[t] = 32; S.mod[t] = 0; }
+    const int sb0 = (lane / Z) * Z, l = lane - sb0;
+    const unsigned segmask = (Z == 32) ? 0xffffffffu : (((1u << Z) - 1u) << sb0);
+    int *key = S.key + (lane / Z) * NS;
+    int *own = S.own + (lane / Z) * NS;
+    int *mod = S.mod + (lane / Z) * NS;
+    Rec *rec = S.rec + (lane / Z) * NS;
+    const CellHdr *hp = E.hdr + (g >= 0 ? g : 0);
+    const InstDev &I = E.inst[g >= 0 ? hp->b : 0];
+    const int N = (g >= 0) ? hp->n_in : 0, nc = (g >= 0) ? hp->nc : 0;
+    const uint32_t id = static_cast<uint32_t>(hp->i + 1), step = I.step;
+    for (int t = l; t < NS; t += Z) { key[t] = -1; own[t] = 32; mod[t] = 0; }
     __syncwarp();
-    const bool act = lane < nc;
+    const bool act = l < nc;
     int sa = 0, sb = 0;
     uint32_t w2 = 0, w3 = 0;
     if (act) {
         uint32_t w[4];
-        draw(I, id, 2u * static_cast<uint32_t>(lane), step, kCollide, w);
+        draw(I, id, 2u * static_cast<uint32_t>(l), step, kCollide, w);
         const int a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
         int b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
         if (b >= a) ++b;
         w2 = w[2];
         w3 = w[3];
-        sa = hash_insert(S.key, a, E.err);
-        sb = hash_insert(S.key, b, E.err);
+        sa = hash_insert<NS>(key, a, E.err);
+        sb = hash_insert<NS>(key, b, E.err);
     }
     __syncwarp();
-    for (int t = lane; t < kHash; t += 32) {
-        const int x = S.key[t];
-        if (x >= 0) S.rec[t] = ld_rec_rw(arrived_ptr<Rec>(x, h, in, fs));
+    if (g >= 0) {
+        const CellHdr h = *hp;
+        for (int t = l; t < NS; t += Z) {
+            const int x = key[t];
+            if (x >= 0) rec[t] = ld_rec_rw(arrived_ptr<Rec>(x, h, in, fs));
+        }
     }
     __syncwarp();
     const double expo = 1.0 - 2.0 * I.upsilon;
     const float expo_f = static_cast<float>(expo);
-    const double cm0 = E.cmax[g];
+    const double cm0 = (g >= 0) ? E.cmax[g] : 0.0;
     double cm = cm0;
     int acc = 0;
-    for (int k0 = 0; k0 < nc;) {
-        const bool live = act && lane >= k0;
-        if (live) { atomicMin(&S.own[sa], lane); atomicMin(&S.own[sb], lane); }
+    int k0 = 0;
+    while (__any_sync(0xffffffffu, k0 < nc)) {
+        const bool live = act && l >= k0;
+        if (live) { atomicMin(&own[sa], l); atomicMin(&own[sb], l); }
         __syncwarp();
-        const bool conf = live && (S.own[sa] < lane || S.own[sb] < lane);
-        const unsigned cmask = __ballot_sync(0xffffffffu, conf);
+        const bool conf = live && (own[sa] < l || own[sb] < l);
+        const unsigned cmask = (__ballot_sync(0xffffffffu, conf) & segmask) >> sb0;
         const int end1 = cmask ? __ffs(cmask) - 1 : nc;      // first candidate that shares a particle
-        const bool inb = live && lane < end1;
+        const bool inb = live && l < end1;
         Rec A, B;
         float cr32 = 0.f;
         double cr = 0.0;
         bool exact = false;
         const float cm32 = static_cast<float>(cm);
         if (inb) {
-            A = S.rec[sa];
-            B = S.rec[sb];
+            A = rec[sa];
+            B = rec[sb];
             cr32 = rel_speed_f32(A, B);
             if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
                 cr = rel_speed(A, B);
                 exact = true;
             }
         }
-        const unsigned rmask = __ballot_sync(0xffffffffu, inb && exact && cr > cm);
+        const unsigned rmask = (__ballot_sync(0xffffffffu, inb && exact && cr > cm) & segmask) >> sb0;
         const int fr = rmask ? __ffs(rmask) - 1 : 32;
         const int end = min(end1, fr + 1);
-        const double cr_r = __shfl_sync(0xffffffffu, cr, fr < 32 ? fr : 0);
+        const double cr_r = __shfl_sync(0xffffffffu, cr, sb0 + (fr < 32 ? fr : 0));
         bool accd = false;
-        if (live && lane < end) {
-            accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
+        if (live && l < end) {
+            accd = (l == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
-                scatter_pair(I, id, static_cast<uint32_t>(lane), step, A, B, cr, exact);
-                S.rec[sa] = A;
-                S.rec[sb] = B;
-                S.mod[sa] = 1;
-                S.mod[sb] = 1;
+                scatter_pair(I, id, static_cast<uint32_t>(l), step, A, B, cr, exact);
+                rec[sa] = A;
+                rec[sb] = B;
+                mod[sa] = 1;
+                mod[sb] = 1;
             }
         }
-        acc += __popc(__ballot_sync(0xffffffffu, accd));
+        acc += __popc(__ballot_sync(0xffffffffu, accd) & segmask);
         if (fr < end) cm = cr_r;
         __syncwarp();
-        if (live) { S.own[sa] = 32; S.own[sb] = 32; }
+        if (live) { own[sa] = 32; own[sb] = 32; }
         __syncwarp();
-        k0 = end;
+        if (k0 < nc) k0 = end;
     }
-    for (int t = lane; t < kHash; t += 32) {
-        const int x = S.key[t];
-        if (x >= 0 && S.mod[t]) st_rec(arrived_ptr<Rec>(x, h, in, fs), S.rec[t]);
-    }
-    if (lane == 0) {
-        E.ncand[g] = nc;
-        E.nacc[g] = acc;
-        if (cm != cm0) {
-            E.cmax[g] = cm;
-            E.fmaj[g] = majorant_factor(I, cm);
+    if (g >= 0) {
+        const CellHdr h = *hp;
+        for (int t = l; t < NS; t += Z) {
+            const int x = key[t];
+            if (x >= 0 && mod[t]) st_rec(arrived_ptr<Rec>(x, h, in, fs), rec[t]);
+        }
+        if (l == 0) {
+            E.ncand[g] = nc;
+            E.nacc[g] = acc;
+            if (cm != cm0) {
+                E.cmax[g] = cm;
+                E.fmaj[g] = majorant_factor(I, cm);
+            }
         }
     }
 }
@@ -575,7 +597,7 @@ __device__ __forceinline__ bool absorbed(uint32_t w0, uint32_t w1, double P, uin
 }
 
 template <typename Rec>
-__device__ void collide_staged(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, CollideShared<Rec> &S,
+__device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, CollideShared<Rec> &S,
                                Rec *in, Rec *out, FarItem<Rec> *fs)
 {
     const int lane = threadIdx.x & 31;
@@ -642,7 +664,7 @@ __device__ void collide_staged(const EngineDev &E, const InstDev &I, const CellH
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kCollideThreads) k_collide(EngineDev E, int rp)
+__global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     CollideShared<Rec> &S = reinterpret_cast<CollideShared<Rec> *>(smraw)[threadIdx.x >> 5];
@@ -650,25 +672,40 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(EngineDev E, int rp
     Rec *in = static_cast<Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
-    const int n_items = E.ticket[1];
-    for (;;) {
+    // staged cells (one per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and
+    // four per warp); the next ticket of a list is fetched while the current item runs
+    for (int q = 3; q >= 0; --q) {
+        const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
+        const int n_items = E.ticket[kListLen + q];
+        const int32_t *list = E.wl + static_cast<size_t>(q) * E.G;
         int t = 0;
-        if (lane == 0) t = atomicAdd(&E.ticket[0], 1);
+        if (lane == 0) t = atomicAdd(&E.ticket[q], per);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= n_items) break;
-        const int g = E.wl[t];
-        const CellHdr h = E.hdr[g];
-        const InstDev &I = E.inst[h.b];
-        if (h.cls == kClsDirect) collide_direct<Rec>(E, I, h, g, S, in, fs);
-        else if (h.cls == kClsStaged) collide_staged<Rec>(E, I, h, g, S, in, out, fs);
-        __syncwarp();
+        while (t < n_items) {
+            int tn = 0;
+            if (lane == 0) tn = atomicAdd(&E.ticket[q], per);
+            if (q == 3) {
+                const int g = list[t];
+                const CellHdr h = E.hdr[g];
+                if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
+            } else {
+                const int me = t + lane / (32 / per);
+                int g = (me < n_items) ? list[me] : -1;
+                if (g >= 0 && E.hdr[g].cls != kClsDirect) g = -1;
+                if (q == 2) collide_direct<Rec, 32>(E, g, S, in, fs);
+                else if (q == 1) collide_direct<Rec, 16>(E, g, S, in, fs);
+                else collide_direct<Rec, 8>(E, g, S, in, fs);
+            }
+            __syncwarp();
+            t = __shfl_sync(0xffffffffu, tn, 0);
+        }
     }
     // re-sampled particles of cells without collisions (Eq. maxsample), chunk by chunk, into the
     // positions after the cell's arrived list in its output block
-    const int n_chunks = min(E.ticket[2], E.wls_cap);
+    const int n_chunks = min(E.ticket[kSampleLen], E.wls_cap);
     for (;;) {
         int t = 0;
-        if (lane == 0) t = atomicAdd(&E.ticket[3], 1);
+        if (lane == 0) t = atomicAdd(&E.ticket[kSampleCtr], 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= n_chunks) break;
         const int2 it = E.wls[t];
@@ -1031,8 +1068,8 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     int64_t myslots = 0;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (update) E.far_count[0] = 0;
-        E.ticket[1] = 0;
-        E.ticket[2] = 0;
+        for (int q = 0; q < 4; ++q) E.ticket[kListLen + q] = 0;
+        E.ticket[kSampleLen] = 0;
     }
     if (g < E.G) {
         CellHdr hd;
@@ -1207,6 +1244,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
+    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates, 3 staged cells
     int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1218,6 +1256,10 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         } else {
             const int cls = E.hdr[g].cls;
             listed = (cls == kClsDirect) || (cls == kClsStaged);
+            if (cls == kClsDirect) {
+                const int nc = E.hdr[g].nc;
+                lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : 2);
+            }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
     }
@@ -1232,7 +1274,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total > 0) {
             int base = 0;
-            if (lane == 0) base = atomicAdd(&E.ticket[2], total);
+            if (lane == 0) base = atomicAdd(&E.ticket[kSampleLen], total);
             base = __shfl_sync(0xffffffffu, base, 0);
             const int first = base + incl - chunks;
             for (int c = 0; c < chunks; ++c) {
@@ -1241,15 +1283,22 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             }
         }
     }
-    // work list of the collision kernel (one atomic per warp)
-    const unsigned lm = __ballot_sync(0xffffffffu, listed);
-    if (lm) {
-        int base = 0;
-        if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[1], __popc(lm));
-        base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
-        if (listed) E.wl[base + __popc(lm & ((1u << lane) - 1u))] = g;
+    // work lists of the collision kernel (one atomic per warp and list)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool mine = listed && lq == q;
+        const unsigned lm = __ballot_sync(0xffffffffu, mine);
+        if (lm) {
+            int base = 0;
+            if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[kListLen + q], __popc(lm));
+            base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
+            if (mine) E.wl[static_cast<size_t>(q) * E.G + base + __popc(lm & ((1u << lane) - 1u))] = g;
+        }
     }
-    if (g == 0) { E.ticket[0] = 0; E.ticket[3] = 0; }
+    if (g == 0) {
+        for (int q = 0; q < 4; ++q) E.ticket[q] = 0;
+        E.ticket[kSampleCtr] = 0;
+    }
     if (g >= E.G) return;
     const int b = E.cell_inst[g];
     if (b < 0) return;
