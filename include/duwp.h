@@ -164,6 +164,15 @@ enum { DUWP_INSTANT = 0, DUWP_AVERAGED = 1 };
 int duwp_moments(duwp_handle *h, int32_t inst, int32_t which, double *host_rho, double *host_u,
                  double *host_T, double *host_wave_frac, int32_t n);
 
+/* Synchronizing.  duwp_moments for every active instance of the handle at once: one device pass
+ * and one copy per output array.  The caller-owned HOST arrays hold total_cells doubles each (the
+ * sum of n_cells over the active instances); instance b's cells follow those of the active
+ * instances with smaller index.  Any of the output pointers may be NULL.  The values are those of
+ * duwp_moments bit for bit.  Errors: DUWP_EINVAL (which, or total_cells not the sum), DUWP_ENOMEM
+ * (its device scratch, 32 B per cell, kept by the handle), device errors. */
+int duwp_moments_all(duwp_handle *h, int32_t which, double *host_rho, double *host_u, double *host_T,
+                     double *host_wave_frac, int64_t total_cells);
+
 /* Synchronizing.  Conservative total state Psi_t = (rho, rho U, rho V, rho W, rho E) per cell of
  * instance `inst` (which = DUWP_INSTANT) or its time average (DUWP_AVERAGED) into a caller-owned
  * host array of n_cells * 5 doubles, cell-major.  *host_navg (may be NULL) receives the number of

@@ -156,6 +156,7 @@ Engine::~Engine()
 {
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    if (mom) dfree(mom, mom_bytes);
     dfree(slab, slab_bytes);
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -624,6 +625,46 @@ int duwp_moments(duwp_handle *h, int32_t b, int32_t which, double *rho, double *
         }
     }
     return DUWP_OK;
+}
+
+int duwp_moments_all(duwp_handle *h, int32_t which, double *rho, double *u, double *T, double *wave_frac,
+                     int64_t total_cells)
+{
+    if (!h || (which != DUWP_INSTANT && which != DUWP_AVERAGED)) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    std::vector<int64_t> base(static_cast<size_t>(E.max_inst), -1);
+    int64_t total = 0;
+    for (int32_t b = 0; b < E.max_inst; ++b) {
+        if (!E.inst[b].active) continue;
+        base[b] = total;
+        total += E.inst[b].p.n_cells;
+    }
+    if (total != total_cells) return DUWP_EINVAL;
+    if (total == 0) return E.sync();
+    const size_t need = sizeof(int64_t) * base.size() + sizeof(double) * 4 * static_cast<size_t>(total) + 256;
+    if (E.mom_bytes < need) {
+        if (E.mom) {
+            const int rc = E.sync();
+            if (rc) return rc;
+            E.dfree(E.mom, E.mom_bytes);
+            E.mom = nullptr;
+            E.mom_bytes = 0;
+        }
+        E.mom = E.dalloc(need);
+        if (!E.mom) return DUWP_ENOMEM;
+        E.mom_bytes = need;
+    }
+    int64_t *d_base = static_cast<int64_t *>(E.mom);
+    double *d_out = reinterpret_cast<double *>(static_cast<unsigned char *>(E.mom) +
+                                               ((sizeof(int64_t) * base.size() + 255) & ~static_cast<size_t>(255)));
+    DUWP_CU(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice, E.stream));
+    DUWP_CU(launch_moments(E.dev, which, d_base, total, d_out, E.stream));
+    double *dst[4] = {rho, u, T, wave_frac};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k])
+            DUWP_CU(cudaMemcpyAsync(dst[k], d_out + static_cast<size_t>(k) * total, sizeof(double) * total,
+                                    cudaMemcpyDeviceToHost, E.stream));
+    return E.sync();
 }
 
 int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)

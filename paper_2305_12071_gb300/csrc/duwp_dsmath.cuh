@@ -113,6 +113,33 @@ __host__ __device__ __forceinline__ bool ds_rounds_to_hi(ds v, float err)
 // sin hi, sin lo).
 constexpr int kTurnTable = 64;
 
+// cos and sin of phi = 2 pi u for the 53-bit uniform u = v2 2^-32 + (v3 >> 11) 2^-53: phi = 2 pi (K/64
+// + r) with K = round(64 u), |r| <= 1/128 taken exactly from the bits; cos and sin of 2 pi r from
+// their Taylor series (the omitted terms are below 2^-49 for |2 pi r| <= pi/64) combined with the
+// turn table by the angle-addition formulas.  Absolute error below 2^-45.
+__host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2, uint32_t v3, ds &cp, ds &sp)
+{
+    constexpr ds kTwoPiDs = ds_const(6.283185307179586476925286766559);
+    constexpr ds kMinusSixth = ds_const(-1.0 / 6.0);
+    // r 2^32 = d + (v3 >> 11) 2^-21 with d = v2 - K 2^26 (32-bit wrap-around gives the sign)
+    const uint32_t K = (v2 >> 26) + ((v2 >> 25) & 1u);
+    const int32_t d = static_cast<int32_t>(v2 - (K << 26));
+    const int32_t d_hi = d & ~3;
+    const uint32_t r_lo = (static_cast<uint32_t>(d & 3) << 21) | (v3 >> 11);
+    const ds r = ds_two_sum(static_cast<float>(d_hi) * 0x1p-32f, static_cast<float>(r_lo) * 0x1p-53f);
+    const ds x = ds_mul(kTwoPiDs, r);                                 // |x| <= pi/64
+    const ds x2 = ds_mul(x, x);
+    // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040), cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
+    const float ts = x2.hi * (1.0f / 120.0f - x2.hi * (1.0f / 5040.0f));
+    const ds sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
+    const float tc = x2.hi * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
+    const ds cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
+    const float4 T = turn[K & (kTurnTable - 1)];
+    const ds C = {T.x, T.y}, S = {T.z, T.w};
+    cp = ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
+    sp = ds_add(ds_mul(S, cx), ds_mul(C, sx));
+}
+
 // Post-collision velocities of an accepted pair of single-precision records (isotropic VHS
 // scattering, Appendix A): the relative velocity keeps its magnitude c_r and takes the direction
 // with cos(theta) = 2 u1 - 1, phi = 2 pi u2, where u1 = u53(v0, v1) and u2 = u53(v2, v3) (53-bit
@@ -126,8 +153,6 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
                                                     float bv, float bw, uint32_t v0, uint32_t v1, uint32_t v2,
                                                     uint32_t v3, float out[6])
 {
-    constexpr ds kTwoPiDs = ds_const(6.283185307179586476925286766559);
-    constexpr ds kMinusSixth = ds_const(-1.0 / 6.0);
     // relative speed c_r of the pair (the differences of two floats are exact pairs)
     const ds du = ds_two_sum(au, -bu), dv = ds_two_sum(av, -bv), dw = ds_two_sum(aw, -bw);
     const ds cr = ds_sqrt(ds_add(ds_add(ds_mul(du, du), ds_mul(dv, dv)), ds_mul(dw, dw)));
@@ -139,25 +164,9 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
     // sin(theta) = sqrt((1 - ct)(1 + ct))
     const ds st = ds_sqrt(ds_mul(ds_add({1.0f, 0.0f}, ds_neg(ct)), ds_add({1.0f, 0.0f}, ct)));
     if (!(st.hi >= 0x1p-10f)) return false;
-    // phi = 2 pi u2 = 2 pi (K/64 + r), K = round(64 u2), |r| <= 1/128; r exact from the bits:
-    // r 2^32 = d + (v3 >> 11) 2^-21 with d = v2 - K 2^26 (32-bit wrap-around gives the sign)
-    const uint32_t K = (v2 >> 26) + ((v2 >> 25) & 1u);
-    const int32_t d = static_cast<int32_t>(v2 - (K << 26));
-    const int32_t d_hi = d & ~3;
-    const uint32_t r_lo = (static_cast<uint32_t>(d & 3) << 21) | (v3 >> 11);
-    const ds r = ds_two_sum(static_cast<float>(d_hi) * 0x1p-32f, static_cast<float>(r_lo) * 0x1p-53f);
-    const ds x = ds_mul(kTwoPiDs, r);                                 // |x| <= pi/64
-    const ds x2 = ds_mul(x, x);
-    // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040), cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720);
-    // the omitted terms are below 2^-49 for |x| <= pi/64
-    const float ts = x2.hi * (1.0f / 120.0f - x2.hi * (1.0f / 5040.0f));
-    const ds sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
-    const float tc = x2.hi * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
-    const ds cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
-    const float4 T = turn[K & (kTurnTable - 1)];
-    const ds C = {T.x, T.y}, S = {T.z, T.w};
-    const ds cp = ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
-    const ds sp = ds_add(ds_mul(S, cx), ds_mul(C, sx));
+    // phi = 2 pi u2
+    ds cp, sp;
+    ds_turn(turn, v2, v3, cp, sp);
     // relative velocity after the collision and the two velocities (a + b)/2 +- c/2
     const ds crst = ds_mul(cr, st);
     const ds c[3] = {ds_mul(crst, cp), ds_mul(crst, sp), ds_mul(cr, ct)};
@@ -173,6 +182,101 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
         ok = ok && ds_rounds_to_hi(pa, err) && ds_rounds_to_hi(pb, err);
         out[k] = pa.hi;
         out[3 + k] = pb.hi;
+    }
+    return ok;
+}
+
+// Exact double-single value of a 53-bit integer m = (a << 21) | (b >> 11) scaled by 2^-53 (three
+// exact 24-bit pieces summed; relative error below 2^-47).
+__host__ __device__ __forceinline__ ds ds_u53(uint32_t a, uint32_t b)
+{
+    const uint32_t m0 = ((a & 7u) << 21) | (b >> 11), m1 = (a >> 3) & 0xffffffu, m2 = a >> 27;
+    return ds_add(ds_two_sum(static_cast<float>(m2) * 0x1p-5f, static_cast<float>(m1) * 0x1p-29f),
+                  {static_cast<float>(m0) * 0x1p-53f, 0.0f});
+}
+
+// a / b for b > 0: one correction of the single-precision quotient; relative error below 2^-46.
+__host__ __device__ __forceinline__ ds ds_div(ds a, ds b)
+{
+    const float q0 = a.hi / b.hi;
+    const ds p = ds_mul({q0, 0.0f}, b);
+    const ds r = ds_add(a, ds_neg(p));
+    const float q1 = r.hi / b.hi;
+    return ds_fast_two_sum(q0, q1);
+}
+
+// atanh(t) = t (1 + t^2/3 + t^4/5 + ...) for |t| <= 0.18: the terms through t^10/11 in double-single,
+// the rest (below 3e-9 of the sum) in single precision, truncated after t^22/23; relative error below
+// 2^-45.
+__host__ __device__ __forceinline__ ds ds_atanh_small(ds t)
+{
+    const ds y = ds_mul(t, t);
+    const float yf = y.hi;
+    const float tail = 1.0f / 13.0f + yf * (1.0f / 15.0f + yf * (1.0f / 17.0f + yf * (1.0f / 19.0f + yf * (1.0f / 21.0f + yf * (1.0f / 23.0f)))));
+    ds p = ds_add(ds_const(1.0 / 11.0), {yf * tail, 0.0f});
+    p = ds_add(ds_const(1.0 / 9.0), ds_mul(y, p));
+    p = ds_add(ds_const(1.0 / 7.0), ds_mul(y, p));
+    p = ds_add(ds_const(1.0 / 5.0), ds_mul(y, p));
+    p = ds_add(ds_const(1.0 / 3.0), ds_mul(y, p));
+    p = ds_add({1.0f, 0.0f}, ds_mul(y, p));
+    return ds_mul(t, p);
+}
+
+// -log(1 - u) for the 53-bit uniform u = u53(a, b) in [0, 1); relative error below 2^-44.
+// u < 1/4: 2 atanh(u / (2 - u)) (exact u, no cancellation for small u; the argument is below 1/7);
+// u >= 1/4: with r = 1 - u = n 2^-53 (n exact), r = 2^e f, f in [sqrt(1/2), sqrt(2)):
+// (53 - e) ln 2 - 2 atanh((f - 1)/(f + 1)).
+__host__ __device__ __forceinline__ ds ds_neg_log1m(uint32_t a, uint32_t b)
+{
+    constexpr ds kLn2 = ds_const(0.69314718055994530941723212145818);
+    if (a < 0x40000000u) {                                  // u < 1/4
+        const ds u = ds_u53(a, b);
+        const ds t = ds_div(u, ds_add({2.0f, 0.0f}, ds_neg(u)));
+        const ds at = ds_atanh_small(t);
+        return {2.0f * at.hi, 2.0f * at.lo};
+    }
+    // n = 2^53 - m, m = (a << 21) | (b >> 11), 1 <= n <= 3 2^51
+    const uint64_t m = (static_cast<uint64_t>(a) << 21) | static_cast<uint64_t>(b >> 11);
+    const uint64_t n = (1ull << 53) - m;
+#ifdef __CUDA_ARCH__
+    int e = 63 - __clzll(static_cast<long long>(n));        // n = 2^e f, f in [1, 2)
+#else
+    int e = 63 - __builtin_clzll(n);
+#endif
+    // f as an exact double-single (n has at most 53 bits: pieces of 24 and 29 bits)
+    const uint64_t top = n >> (e >= 24 ? e - 23 : 0);       // 24 leading bits
+    const uint64_t rest = (e >= 24) ? (n & ((1ull << (e - 23)) - 1ull)) : 0ull;
+    const float fh = static_cast<float>(static_cast<uint32_t>(top)) * ((e >= 23) ? 0x1p-23f : 1.0f / static_cast<float>(1u << e));
+    const float fl = (e >= 24) ? static_cast<float>(rest) * ldexpf(1.0f, -e) : 0.0f;
+    ds f = ds_two_sum(fh, fl);
+    if (f.hi > 1.41421356f) { f = {0.5f * f.hi, 0.5f * f.lo}; ++e; }
+    const ds t = ds_div(ds_add(f, {-1.0f, 0.0f}), ds_add(f, {1.0f, 0.0f}));
+    const ds at = ds_atanh_small(t);
+    const ds l2 = ds_mul(kLn2, {static_cast<float>(53 - e), 0.0f});
+    return ds_add(l2, {-2.0f * at.hi, -2.0f * at.lo});
+}
+
+// Velocity components of a Maxwellian sample (Eq. maxsample) for single-precision records:
+// xi_d = U_d + (s cos(2 pi r1)) sqrt(-log(1 - r2)), d = 0, 1, 2, with s = sqrt(2 R T), U and s as
+// double-single values, (r1, r2) the 53-bit uniforms of words w[4d+2..4d+5] (w = the 14 words after
+// the position's two).  out = the single-precision roundings; returns false when one of them cannot
+// be guaranteed (a value within 2^-40 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary), then the
+// caller evaluates in double precision.
+__host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const ds U[3], ds s, const uint32_t *w,
+                                                   float out[3])
+{
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ds cp, sp;
+        ds_turn(turn, w[4 * k], w[4 * k + 1], cp, sp);
+        const ds L = ds_neg_log1m(w[4 * k + 2], w[4 * k + 3]);
+        const ds rl = ds_sqrt(L);
+        const ds mag = ds_mul(s, rl);
+        const ds xi = ds_add(U[k], ds_mul(mag, cp));
+        const float err = 0x1p-40f * (fabsf(U[k].hi) + mag.hi);
+        ok = ok && ds_rounds_to_hi(xi, err);
+        out[k] = xi.hi;
     }
     return ok;
 }

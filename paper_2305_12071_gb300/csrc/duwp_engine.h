@@ -61,6 +61,10 @@ struct Engine {
     bool use_graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // two steps starting at parity 0 / 1
 
+    // device scratch of duwp_moments_all (allocated on first use)
+    void *mom = nullptr;
+    size_t mom_bytes = 0;
+
     ~Engine();
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
                void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);

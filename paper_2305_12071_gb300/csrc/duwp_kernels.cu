@@ -120,31 +120,71 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, dou
 // Particle j of a cell uses counters (id, 4j..4j+3, step, SAMPLE): uniforms 0 -> position,
 // (1,2) -> x, (3,4) -> y, (5,6) -> z.
 // ------------------------------------------------------------------------------------------
+// Per-cell part of the sample: the state and sqrt(2RT), also as double-single values.
+struct MaxwellCell {
+    double q[5];
+    double sq;
+    ds U[3];
+    ds s;
+};
+
+__device__ inline MaxwellCell maxwell_cell(const InstDev &I, const double *q)
+{
+    MaxwellCell m;
+    for (int k = 0; k < 5; ++k) m.q[k] = q[k];
+    m.sq = sqrt(2.0 * I.R * q[4]);
+    for (int d = 0; d < 3; ++d) {
+        const float h = __double2float_rn(q[1 + d]);
+        m.U[d] = {h, __double2float_rn(q[1 + d] - static_cast<double>(h))};
+    }
+    const float h = __double2float_rn(m.sq);
+    m.s = {h, __double2float_rn(m.sq - static_cast<double>(h))};
+    return m;
+}
+
+// Velocities in double precision from the 14 draw words after the position's (w).
+template <typename T>
+__device__ __noinline__ void maxwell_fp64(const MaxwellCell &mc, const uint32_t *w, T out[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double r1 = u53(w[4 * d], w[4 * d + 1]);
+        const double r2 = 1.0 - u53(w[4 * d + 2], w[4 * d + 3]);
+        out[d] = store_val(mc.q[1 + d] + (mc.sq * cos(kTwoPi * r1)) * sqrt(-log(r2)), T());
+    }
+}
+
+// Single-precision rounding of the 53-bit uniform u53(a, b) (exact integer conversion, then a power
+// of two): the same value as rounding the double u53(a, b).
+__device__ __forceinline__ float u53_float(uint32_t a, uint32_t b)
+{
+    const unsigned long long m = (static_cast<unsigned long long>(a) << 21) | static_cast<unsigned long long>(b >> 11);
+    return __ull2float_rn(m) * 0x1p-53f;
+}
+
 template <typename Rec>
-__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const double *q)
+__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc)
 {
     uint32_t w[16];
 #pragma unroll
     for (uint32_t t = 0; t < 4; ++t) draw(I, id, 4u * j + t, step, kSample, w + 4 * t);
-    double un[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) un[k] = u53(w[2 * k], w[2 * k + 1]);
-    const double sq = sqrt(2.0 * I.R * q[4]);
-    double xi[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double r1 = un[1 + 2 * d];
-        const double r2 = 1.0 - un[2 + 2 * d];
-        xi[d] = q[1 + d] + (sq * cos(kTwoPi * r1)) * sqrt(-log(r2));
-    }
     Rec r;
     using T = decltype(r.xl);
-    T x = store_val(un[0], T());
-    if (x >= T(1)) x = sizeof(T) == 4 ? T(0x1.fffffep-1f) : T(un[0]);
+    T x, xi[3];
+    if constexpr (sizeof(T) == 4) {
+        // single-precision records: double-single evaluation, double precision only where the
+        // rounding of a component cannot be guaranteed
+        x = u53_float(w[0], w[1]);
+        if (!ds_maxwell(g_turn, mc.U, mc.s, w + 2, xi)) maxwell_fp64<T>(mc, w + 2, xi);
+    } else {
+        x = u53(w[0], w[1]);
+        maxwell_fp64<T>(mc, w + 2, xi);
+    }
+    if (x >= T(1)) x = sizeof(T) == 4 ? T(0x1.fffffep-1f) : x;
     r.xl = x;
-    r.u = store_val(xi[0], T());
-    r.v = store_val(xi[1], T());
-    r.w = store_val(xi[2], T());
+    r.u = xi[0];
+    r.v = xi[1];
+    r.w = xi[2];
     return r;
 }
 
@@ -636,11 +676,11 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
         }
         return;
     }
-    double q[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = E.prim[5 * g + k];
-    for (int j = lane; j < nn; j += 32)
-        st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, q));
+    if (nn > 0) {
+        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+        for (int j = lane; j < nn; j += 32)
+            st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc));
+    }
     __syncwarp();
     const double cm0 = E.cmax[g];
     double cmax = cm0;
@@ -715,12 +755,10 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
         const long long off = h.off;
         if (cls != kClsStream && cls != kClsReservoir) continue;
         const InstDev &I = E.inst[b];
-        double q[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = E.prim[5 * g + k];
+        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
         const int j1 = min(j0 + kSampleChunk, n_new);
         for (int j = j0 + lane; j < j1; j += 32)
-            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, q));
+            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, mc));
     }
 }
 
@@ -1413,6 +1451,35 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 }
 
 // ------------------------------------------------------------------------------------------
+// Macroscopic profiles of all instances in one pass (inspection): out = [rho | u | T | wave
+// fraction] x total, instance b's interior cell i at base[b] + i (base[b] < 0: not reported).
+// ------------------------------------------------------------------------------------------
+__global__ void k_moments(EngineDev E, int which, const int64_t *base, int64_t total, double *out)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= E.G) return;
+    const int b = E.cell_inst[g];
+    if (b < 0 || base[b] < 0) return;
+    const InstDev &I = E.inst[b];
+    const int i = g - I.cell_base - 1;
+    if (i < 0 || i >= I.C) return;
+    const int64_t o = base[b] + i;
+    if (o >= total) return;
+    const double *c = (which == 1 ? E.avg : E.psi) + 5 * static_cast<int64_t>(g);
+    const int64_t navg = I.navg;
+    const double scale = (which == 1) ? (navg > 0 ? 1.0 / static_cast<double>(navg) : 0.0) : 1.0;
+    const double r = c[0] * scale;
+    const double mx = c[1] * scale, my = c[2] * scale, mz = c[3] * scale, e5 = c[4] * scale;
+    const double ux = r > 0 ? mx / r : 0.0, uy = r > 0 ? my / r : 0.0, uz = r > 0 ? mz / r : 0.0;
+    const double tt = r > 0 ? (e5 / r - 0.5 * (ux * ux + uy * uy + uz * uz)) / (1.5 * I.R) : 0.0;
+    const double rt = E.psi[5 * static_cast<int64_t>(g)];
+    out[o] = r;
+    out[total + o] = ux;
+    out[2 * total + o] = tt;
+    out[3 * total + o] = rt > 0 ? (rt - static_cast<double>(E.cnt[g]) * I.mp_over_dx) / rt : 0.0;
+}
+
+// ------------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------------
 size_t stream_smem_bytes(int fp32, int threads)
@@ -1519,6 +1586,13 @@ cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const do
     const int grid = (n + 255) / 256;
     k_init_cells<<<grid, 256, 0, s>>>(E, b, g0, n, lc[0], lc[1], lc[2], lc[3], lc[4], rc[0], rc[1], rc[2], rc[3], rc[4],
                                       x_min, x_split);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const EngineDev &E, int which, const int64_t *d_base, int64_t total, double *d_out,
+                           cudaStream_t s)
+{
+    k_moments<<<(E.G + 255) / 256, 256, 0, s>>>(E, which, d_base, total, d_out);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,10 @@ cudaError_t launch_init_turn(cudaStream_t s);
 // Initial state of the cells [g0, g0 + n) of instance b (all wave, no particles).
 cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const double *left_cons,
                               const double *right_cons, double x_min, double x_split, cudaStream_t s);
+// Profiles (rho, u, T, wave fraction) of every instance into d_out = [4 x total], instance b at
+// d_base[b] (device array of n_inst entries, < 0: skip).
+cudaError_t launch_moments(const EngineDev &E, int which, const int64_t *d_base, int64_t total, double *d_out,
+                           cudaStream_t s);
 // Gather the stable sorted particle list of instance b into device arrays (debug/inspection).
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
                           int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s);

@@ -26,7 +26,7 @@ NTC = {"particle": 0, "total": 1}
 
 # Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
 EXPORTS = (
-    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_step_timed", "duwp_moments", "duwp_fields", "duwp_get_info",
+    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_step_timed", "duwp_moments", "duwp_moments_all", "duwp_fields", "duwp_get_info",
     "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         L.duwp_sync.argtypes = [vp]
         L.duwp_step_timed.argtypes = [vp, i32, dp, dp]
         L.duwp_moments.argtypes = [vp, i32, i32, dp, dp, dp, dp, i32]
+        L.duwp_moments_all.argtypes = [vp, i32, dp, dp, dp, dp, i64]
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
@@ -289,6 +290,16 @@ class Solver:
         r, u, T, wf = (np.empty(n, np.float64) for _ in range(4))
         _chk(self.L.duwp_moments(self.h, inst, which, _dptr(r), _dptr(u), _dptr(T), _dptr(wf), n), "duwp_moments")
         return {"rho": r, "u": u, "T": T, "wave_frac": wf}
+
+    def moments_all(self, which: int = INSTANT, out: dict | None = None) -> dict:
+        """Profiles of every instance at once (concatenated in instance order): one call, one copy.
+        `out` (optional) supplies the host arrays to fill (e.g. pinned ones) and is returned."""
+        total = sum(self.n_cells(i) for i in range(self.n))
+        if out is None:
+            out = {k: np.empty(total, np.float64) for k in ("rho", "u", "T", "wave_frac")}
+        _chk(self.L.duwp_moments_all(self.h, which, _dptr(out["rho"]), _dptr(out["u"]), _dptr(out["T"]),
+                                     _dptr(out["wave_frac"]), total), "duwp_moments_all")
+        return out
 
     def num_particles(self, inst: int = 0) -> int:
         o = C.c_int64()

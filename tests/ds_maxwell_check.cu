@@ -1,0 +1,80 @@
+// Host-side check of the double-single Maxwellian sampling of single-precision records: for random
+// draws and cell states, whenever ds_maxwell reports success its floats must equal the
+// single-precision rounding of the double-precision evaluation of Eq. (maxsample),
+// xi = U + (sqrt(2RT) cos(2 pi r1)) sqrt(-log(1 - r2)), with r1, r2 the 53-bit uniforms of the draw
+// words; the fallback must stay rare.  Also checks -log(1 - u) against long double.
+// Usage: ds_maxwell_check N  -> prints "n fallbacks mismatches max_log_rel_err"; exit 1 on a mismatch.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+
+#include "duwp_dsmath.cuh"
+
+using namespace duwp;
+
+static double u53_host(uint32_t a, uint32_t b)
+{
+    const uint64_t m = (static_cast<uint64_t>(a) << 21) ^ static_cast<uint64_t>(b >> 11);
+    return static_cast<double>(m) * 0x1p-53;
+}
+
+int main(int argc, char **argv)
+{
+    float4 turn[kTurnTable];
+    for (int k = 0; k < kTurnTable; ++k) {
+        const long double ang = 2.0L * 3.14159265358979323846264338327950288L * k / kTurnTable;
+        const double c = static_cast<double>(cosl(ang)), s = static_cast<double>(sinl(ang));
+        const float ch = static_cast<float>(c), sh = static_cast<float>(s);
+        turn[k] = make_float4(ch, static_cast<float>(c - ch), sh, static_cast<float>(s - sh));
+    }
+    std::mt19937_64 rng(2306);
+    std::uniform_real_distribution<double> ud(0.0, 1.0);
+    const long n = argc > 1 ? atol(argv[1]) : 100000;
+    long nfail = 0, nbad = 0;
+    double max_rel = 0.0;
+    for (long t = 0; t < n; ++t) {
+        const double R = 1.0, T = 0.05 + 8.0 * ud(rng);
+        const double Uc[3] = {(ud(rng) - 0.5) * 20.0, (t % 3 == 0) ? 0.0 : ud(rng) - 0.5, 0.0};
+        uint32_t w[12];
+        for (int k = 0; k < 12; ++k) w[k] = static_cast<uint32_t>(rng());
+        if (t % 7 == 0) w[2] = 0u;                              // u close to 0 (small -log(1 - u))
+        if (t % 11 == 0) w[6] = 0xffffffffu;                    // u close to 1
+        if (t % 13 == 0) { w[10] = 0u; w[11] = static_cast<uint32_t>(t) << 11; }   // tiny u
+        // -log(1 - u) against long double
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t a = w[4 * k + 2], b = w[4 * k + 3];
+            const ds L = ds_neg_log1m(a, b);
+            const long double u = static_cast<long double>(u53_host(a, b));
+            const long double ex = -log1pl(-u);
+            if (ex > 0) {
+                const double rel = static_cast<double>(fabsl((static_cast<long double>(L.hi) + L.lo - ex) / ex));
+                if (rel > max_rel) max_rel = rel;
+            }
+        }
+        const double sq = sqrt(2.0 * R * T);
+        ds U[3];
+        for (int k = 0; k < 3; ++k) {
+            const float h = static_cast<float>(Uc[k]);
+            U[k] = {h, static_cast<float>(Uc[k] - h)};
+        }
+        const float sh = static_cast<float>(sq);
+        const ds s = {sh, static_cast<float>(sq - sh)};
+        float out[3];
+        if (!ds_maxwell(turn, U, s, w, out)) {
+            ++nfail;
+            continue;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double r1 = u53_host(w[4 * k], w[4 * k + 1]);
+            const double r2 = 1.0 - u53_host(w[4 * k + 2], w[4 * k + 3]);
+            const double xi = Uc[k] + (sq * cos(6.283185307179586 * r1)) * sqrt(-log(r2));
+            if (out[k] != static_cast<float>(xi)) {
+                if (nbad < 5) printf("mismatch at %ld component %d: %.9g vs %.9g\n", t, k, out[k], static_cast<float>(xi));
+                ++nbad;
+            }
+        }
+    }
+    printf("%ld %ld %ld %.3e\n", n, nfail, nbad, max_rel);
+    return nbad ? 1 : 0;
+}

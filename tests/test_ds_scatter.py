@@ -1,7 +1,7 @@
-"""The double-single scattering of single-precision records (host build of the device header):
-whenever it reports success, the stored floats are exactly the single-precision rounding of the
-double-precision evaluation of the scattering formula (Appendix A), and the double-precision
-fallback stays rare."""
+"""The double-single arithmetic of single-precision records (host builds of the device header):
+whenever the scattering (Appendix A) or the Maxwellian sampling (Eq. maxsample) reports success,
+the stored floats are exactly the single-precision rounding of the double-precision evaluation of
+the same formula, and the double-precision fallback stays rare."""
 import os
 import shutil
 import subprocess
@@ -29,3 +29,17 @@ def test_ds_scatter_matches_double_precision(tmp_path):
     assert r.returncode == 0 and nbad == 0, r.stdout
     assert nfail_generic < 0.01 * n, r.stdout
     assert nfail >= n // 17 - 1, r.stdout       # the near-pole cases always take the fallback
+
+
+def test_ds_maxwell_matches_double_precision(tmp_path):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "ds_maxwell_check")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-Xcompiler", "-ffp-contract=off", "-I", CSRC,
+                    os.path.join(HERE, "ds_maxwell_check.cu"), "-o", exe], check=True, capture_output=True)
+    r = subprocess.run([exe, "300000"], capture_output=True, text=True)
+    n, nfail, nbad, log_rel = r.stdout.split()[-4:]
+    assert r.returncode == 0 and int(nbad) == 0, r.stdout
+    assert int(nfail) < 0.005 * int(n), r.stdout
+    assert float(log_rel) < 2.0 ** -44, r.stdout      # -log(1 - u) against long double

@@ -167,3 +167,22 @@ def test_launch_shape_does_not_change_results(precision):
         assert np.array_equal(ref[1], got[1]), f"{t}/{r}: fields"
         for k in ref[2]:
             assert np.array_equal(ref[2][k], got[2][k]), f"{t}/{r}: counter {k}"
+
+
+def test_moments_all_equals_per_instance():
+    ps = [W.config1("fp32"), W.sod(n_cells=90, Kn=1e-3, ppc_ref=100, precision="fp32", seed=9),
+          W.uniform(n_cells=17, bc="periodic", dt=0.02, x_max=1.0, ppc_ref=60, seed=2, precision="fp32")]
+    for p in ps:
+        p["avg_start"] = 2
+    g = solver(ps)
+    g.step(6)
+    for which in (0, 1):
+        allm = g.moments_all(which)
+        o = 0
+        for i in range(g.n):
+            m = g.moments(i, which)
+            n = g.n_cells(i)
+            for k in m:
+                assert np.array_equal(allm[k][o:o + n], m[k]), f"instance {i} {k} which {which}"
+            o += n
+    g.close()
