@@ -416,14 +416,14 @@ int Engine::step(int32_t n)
     if (n < 0) return DUWP_EINVAL;
     int32_t left = n;
     if (use_graphs) {
-        while (left >= 2) {
-            cudaGraphExec_t &gx = graph[parity];
+        while (left >= 1) {
+            // one graph per read parity, each holding the launches of one step
+            const int p0 = parity;
+            cudaGraphExec_t &gx = graph[p0];
             if (!gx) {
                 cudaGraph_t gr = nullptr;
                 DUWP_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-                const int p0 = parity;
-                int rc = enqueue_step();
-                if (rc == DUWP_OK) rc = enqueue_step();
+                const int rc = enqueue_step();
                 cudaError_t e = cudaStreamEndCapture(stream, &gr);
                 parity = p0;
                 if (rc != DUWP_OK) return rc;
@@ -433,8 +433,9 @@ int Engine::step(int32_t n)
                 if (e != cudaSuccess) { set_cuda_error(e, "cudaGraphInstantiate"); gx = nullptr; return DUWP_ECUDA; }
             }
             DUWP_CU(cudaGraphLaunch(gx, stream));
-            left -= 2;
-            steps_done += 2;
+            parity = 1 - p0;
+            left -= 1;
+            steps_done += 1;
         }
     }
     while (left > 0) {

@@ -59,7 +59,7 @@ struct Engine {
     int parity = 0;             // parity of the buffer holding the arrived lists of the next step
     int64_t steps_done = 0;
     bool use_graphs = true;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // two steps starting at parity 0 / 1
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step starting at read parity 0 / 1
 
     // device scratch of duwp_moments_all (allocated on first use)
     void *mom = nullptr;

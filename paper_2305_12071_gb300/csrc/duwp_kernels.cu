@@ -867,7 +867,10 @@ __device__ __forceinline__ int stream_rare(const EngineDev &E, int g, int k, Rec
     return c;
 }
 
-// Same or neighbouring cell inside the domain, decided on the common path: c in {0, 1, 2}, or -1.
+// Common path of the transport: c in {0, 1, 2} for the same or a neighbouring cell inside the
+// domain; 4 for a particle of an inflow/outflow reservoir (ci = -1 or C) that stays outside the
+// domain on the reservoir's side (discarded: a reservoir keeps only what enters, and its own
+// moment sums are not used); -1 for everything else (general path).
 __device__ __forceinline__ int move_near(float dtdx, int C, int ci, float &xl, float u)
 {
     const float s = __fmaf_rn(u, dtdx, xl);
@@ -877,8 +880,11 @@ __device__ __forceinline__ int move_near(float dtdx, int C, int ci, float &xl, f
     int k = __float2int_rz(fk);                  // |fk| <= 2^30: exact
     if (x >= 1.0f) { x = 0.0f; k += 1; }
     const unsigned dd = static_cast<unsigned>(k + 1);
-    const int d = ci + k;                        // |ci| < 2^30, |k| <= 2^30: no overflow
-    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) return -1;
+    const int d = ci + k;                        // |ci| <= 2^30, |k| <= 2^30: no overflow
+    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) {
+        if ((d < 0 && ci < 0) || (d >= C && ci >= C)) return 4;
+        return -1;
+    }
     xl = x;
     return static_cast<int>(dd);
 }
@@ -892,7 +898,10 @@ __device__ __forceinline__ int move_near(double dtdx, int C, int ci, double &xl,
     if (x >= 1.0) { x = 0.0; k += 1; }
     const unsigned dd = static_cast<unsigned>(k + 1);
     const int d = ci + k;
-    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) return -1;
+    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) {
+        if ((d < 0 && ci < 0) || (d >= C && ci >= C)) return 4;
+        return -1;
+    }
     xl = x;
     return static_cast<int>(dd);
 }
