@@ -30,6 +30,7 @@ BC = {"inout": 0, "specular": 1, "periodic": 2, "vacuum": 3}
 EPS = {"eps1": 0, "eps12": 1, "eps0": 2, "eps_avg": 3}
 FLUX = {"gks_eq": 0, "kfvs": 1}
 NTC = {"particle": 0, "total": 1}
+RESAMPLE = {"maxwell": 0, "ce": 1}
 
 
 class _State(C.Structure):
@@ -51,6 +52,7 @@ class _Params(C.Structure):
         ("fp32", C.c_int32), ("eps_mode", C.c_int32), ("flux_mode", C.c_int32), ("ntc_rate", C.c_int32),
         ("seed", C.c_uint64),
         ("avg_start", C.c_int32),
+        ("resample_mode", C.c_int32),
     ]
 
 
@@ -107,6 +109,7 @@ def lib():
         L.ora_get_consts.argtypes = [vp, P(d)]
         L.ora_get_prim.argtypes = [vp, P(d), P(d), P(d), P(d), P(i32)]
         L.ora_transport.argtypes = [vp, i64, P(d), P(d)]; L.ora_transport.restype = i64
+        L.ora_ce_sample.argtypes = [P(_Params), P(d), P(d), P(d), u32, u32, u32, u32, i64, P(d), P(d)]
         _lib = L
     return _lib
 
@@ -143,6 +146,7 @@ def make_params(p: dict) -> _Params:
     s.ntc_rate = NTC[p.get("ntc_rate", "particle")]
     s.seed = int(p.get("seed", 1)) & 0xFFFFFFFFFFFFFFFF
     s.avg_start = int(p.get("avg_start", 0))
+    s.resample_mode = RESAMPLE[p.get("resample_mode", "maxwell")]
     return s
 
 
@@ -153,6 +157,18 @@ def philox(key0: int, key1: int, ctr) -> tuple:
     o = (C.c_uint32 * 4)()
     lib().ora_philox(key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, c, o)
     return tuple(int(x) for x in o)
+
+
+def ce_sample(params: dict, Wm, W0, Wp, key=(7, 11), cell_id: int = 1, step: int = 0, n: int = 1000):
+    """Chapman-Enskog coefficients (on, sigma_xx, sigma_yy, sigma_xy, sigma_xz, q_x, A) of a cell with
+    neighbouring states Wm | W0 | Wp ((rho, u, v, w, T) each) and n velocity samples of that cell."""
+    pr = make_params(params)
+    arr = lambda x: (C.c_double * 5)(*[float(v) for v in x])
+    xi = np.zeros(3 * n, np.float64)
+    coef = (C.c_double * 7)()
+    lib().ora_ce_sample(C.byref(pr), arr(Wm), arr(W0), arr(Wp), key[0], key[1], cell_id, step, n,
+                        xi.ctypes.data_as(C.POINTER(C.c_double)), coef)
+    return list(coef), xi.reshape(n, 3)
 
 
 def u53(a: int, b: int) -> float:

@@ -111,6 +111,7 @@ enum { ORA_BC_INOUT = 0, ORA_BC_SPECULAR = 1, ORA_BC_PERIODIC = 2, ORA_BC_VACUUM
 enum { ORA_EPS1 = 0, ORA_EPS12 = 1, ORA_EPS0 = 2, ORA_EPS_AVG = 3 };
 enum { ORA_FLUX_GKS_EQ = 0, ORA_FLUX_KFVS = 1 };
 enum { ORA_NTC_PARTICLE = 0, ORA_NTC_TOTAL = 1 };
+enum { ORA_RESAMPLE_MAXWELL = 0, ORA_RESAMPLE_CE = 1 };
 
 typedef struct {
     double gamma, Pr, R;
@@ -126,6 +127,7 @@ typedef struct {
     int32_t fp32, eps_mode, flux_mode, ntc_rate;
     uint64_t seed;
     int32_t avg_start;
+    int32_t resample_mode;
 } ora_params;
 
 typedef struct {
@@ -361,24 +363,104 @@ static void add_phi(double acc[5], const opart *q)
     acc[4] += 0.5 * (q->u * q->u + q->v * q->v + q->w * q->w);
 }
 
-/* Maxwellian sample at (U, V, W, T), Eq. (maxsample): xi = U + sqrt(2RT) cos(2 pi r1) sqrt(-ln r2)
- * per component, r2 in (0,1]; position uniform in the cell (reading). */
+/* Chapman-Enskog correction of the re-sampled particles (resample_mode = CE; reading of "the
+ * local equilibrium with its NS correction"): the density f_M (1 + Gamma_1) whose pressure tensor
+ * is p delta_ij + sigma_ij and whose heat flux is q, to first order in the gradients:
+ *   Gamma = 1 + sigma_ij c_i c_j / (2 p R T) + (q . c / (p R T)) (c^2 / (5 R T) - 1),
+ * c = xi - U.  With the 1D NS stress and heat flux of the wave (mu_e = eps mu, as in its flux):
+ *   sigma_xx = -(4/3) mu_e dU/dx, sigma_yy = sigma_zz = (2/3) mu_e dU/dx, sigma_xy = -mu_e dV/dx,
+ *   sigma_xz = -mu_e dW/dx, q_x = -kappa_e dT/dx, kappa_e = (5/2) R mu_e / Pr,
+ * gradients by central differences of the neighbouring cell states.  Sampled by acceptance-
+ * rejection against the Maxwellian (Garcia and Alder, J. Comput. Phys. 140, 1998): accept with
+ * probability Gamma / A, A = 1 + 30 B, B the largest of |sigma_ij| / p and 2 |q_x| / (p sqrt(2RT)).
+ * Where B > 1/4 the first-order expansion is out of its range and the Maxwellian is kept. */
+#define ORA_CE_ATTEMPTS 64
+#define ORA_CE_BMAX 0.25
+
+typedef struct {
+    int on;
+    double U[3], RT, prt, A;
+    double sxx, syy, sxy, sxz, qx;
+} ora_ce;
+
+static ora_ce ce_factor(const ora_params *p, const ora_consts *c, const ora_prim *Wm, const ora_prim *W0,
+                        const ora_prim *Wp)
+{
+    ora_ce f;
+    memset(&f, 0, sizeof f);
+    if (!W0->valid) return f;
+    const ora_prim *a = Wm->valid ? Wm : W0, *b = Wp->valid ? Wp : W0;   /* missing neighbour: own state */
+    double inv = 1.0 / (2.0 * c->dx);
+    double dU = (b->u - a->u) * inv, dV = (b->v - a->v) * inv, dW = (b->w - a->w) * inv, dT = (b->T - a->T) * inv;
+    double RT = p->R * W0->T;
+    double p0 = W0->rho * RT;
+    double mu = mu_of_T(p, c, W0->T);
+    double mue = ora_eps(p->eps_mode, c->dt / (mu / p0)) * mu;
+    double kap = 2.5 * p->R * mue / p->Pr;
+    f.sxx = -(4.0 / 3.0) * mue * dU;
+    f.syy = (2.0 / 3.0) * mue * dU;
+    f.sxy = -mue * dV;
+    f.sxz = -mue * dW;
+    f.qx = -kap * dT;
+    double B = fmax(fmax(fabs(f.sxx), fabs(f.syy)), fmax(fabs(f.sxy), fabs(f.sxz))) / p0;
+    B = fmax(B, 2.0 * fabs(f.qx) / (p0 * sqrt(2.0 * RT)));
+    if (!(B <= ORA_CE_BMAX)) return f;
+    f.on = 1;
+    f.U[0] = W0->u; f.U[1] = W0->v; f.U[2] = W0->w;
+    f.RT = RT;
+    f.prt = p0 * RT;
+    f.A = 1.0 + 30.0 * B;
+    return f;
+}
+
+static double ce_gamma(const ora_ce *f, const double xi[3])
+{
+    double cx = xi[0] - f->U[0], cy = xi[1] - f->U[1], cz = xi[2] - f->U[2];
+    double c2 = cx * cx + cy * cy + cz * cz;
+    double s = f->sxx * cx * cx + f->syy * (cy * cy + cz * cz) + 2.0 * (f->sxy * cx * cy + f->sxz * cx * cz);
+    return 1.0 + s / (2.0 * f->prt) + (f->qx * cx / f->prt) * (c2 / (5.0 * f->RT) - 1.0);
+}
+
+/* Maxwellian velocities at (U, V, W, T) from words w[0..11], Eq. (maxsample): per component
+ * xi = U + sqrt(2RT) cos(2 pi r1) sqrt(-ln r2), r1 = u53(w[4d], w[4d+1]), r2 = 1 - u53(w[4d+2], w[4d+3]). */
+static void maxwell_xi(const ora_params *p, const ora_prim *q, const uint32_t *w, double xi[3])
+{
+    double sq = sqrt(2.0 * p->R * q->T);
+    double mean[3] = { q->u, q->v, q->w };
+    for (int d = 0; d < 3; ++d) {
+        double r1 = ora_u53(w[4 * d], w[4 * d + 1]);
+        double r2 = 1.0 - ora_u53(w[4 * d + 2], w[4 * d + 3]);
+        xi[d] = mean[d] + (sq * cos(ORA_TWO_PI * r1)) * sqrt(-log(r2));
+    }
+}
+
+/* Sample j of a cell at state q, Eq. (maxsample); position uniform in the cell (reading).  Words of
+ * the counters (id, 4j..4j+3, step, SAMPLE): 0-1 position, 2-13 velocities, 14-15 the acceptance
+ * draw of the Chapman-Enskog correction (ce != NULL and on); its attempt a > 0 draws the counters
+ * (id, 4j..4j+3, step, SAMPLE + 8a).  After ORA_CE_ATTEMPTS rejections the first Maxwellian
+ * candidate is kept. */
 static void sample_particle(const ora_params *p, ora_key key, uint32_t id, uint32_t j, uint32_t step,
-                            const ora_prim *q, opart *out)
+                            const ora_prim *q, const ora_ce *ce, opart *out)
 {
     uint32_t w[16];
     for (uint32_t t = 0; t < 4; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE, w + 4 * t);
-    double u[8];
-    for (int k = 0; k < 8; ++k) u[k] = ora_u53(w[2 * k], w[2 * k + 1]);
-    double sq = sqrt(2.0 * p->R * q->T);
-    double mean[3] = { q->u, q->v, q->w };
     double xi[3];
-    for (int d = 0; d < 3; ++d) {
-        double r1 = u[1 + 2 * d];
-        double r2 = 1.0 - u[2 + 2 * d];
-        xi[d] = mean[d] + (sq * cos(ORA_TWO_PI * r1)) * sqrt(-log(r2));
+    maxwell_xi(p, q, w + 2, xi);
+    if (ce && ce->on) {
+        double xi0[3] = { xi[0], xi[1], xi[2] };
+        int accepted = 0;
+        for (uint32_t a = 0; a < ORA_CE_ATTEMPTS; ++a) {
+            if (a > 0) {
+                for (uint32_t t = 0; t < 4; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE + 8u * a, w + 4 * t);
+                maxwell_xi(p, q, w + 2, xi);
+            }
+            if (ora_u53(w[14], w[15]) * ce->A < ce_gamma(ce, xi)) { accepted = 1; break; }
+        }
+        if (!accepted) { xi[0] = xi0[0]; xi[1] = xi0[1]; xi[2] = xi0[2]; }
+        /* the position always comes from the first attempt's words */
+        for (uint32_t t = 0; t < 1; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE, w + 4 * t);
     }
-    double xl = u[0];
+    double xl = ora_u53(w[0], w[1]);
     if (p->fp32) {
         float xf = (float)xl;
         if (xf >= 1.0f) xf = 0x1.fffffep-1f;
@@ -428,6 +510,26 @@ static double accept_prob(const ora_consts *c, double cr, double cmax)
     double x = cr / cmax;
     if (c->upsilon == 0.0) return x;
     return pow(x, 1.0 - 2.0 * c->upsilon);
+}
+
+/* Test hook: the Chapman-Enskog coefficients of a cell with states Wm | W0 | Wp (rho, u, v, w, T
+ * each; all valid) and n samples j = 0..n-1 of that cell (counters (id, 4j.., step, ...) of the key
+ * (k0, k1)), velocities into xi (n x 3).  coef = (on, sigma_xx, sigma_yy, sigma_xy, sigma_xz, q_x, A). */
+void ora_ce_sample(const ora_params *p, const double Wm5[5], const double W05[5], const double Wp5[5],
+                   uint32_t k0, uint32_t k1, uint32_t id, uint32_t step, int64_t n, double *xi, double coef[7])
+{
+    ora_consts c;
+    derive(p, &c);
+    ora_prim Wm = { Wm5[0], Wm5[1], Wm5[2], Wm5[3], Wm5[4], 1 }, W0 = { W05[0], W05[1], W05[2], W05[3], W05[4], 1 },
+             Wp = { Wp5[0], Wp5[1], Wp5[2], Wp5[3], Wp5[4], 1 };
+    ora_ce ce = ce_factor(p, &c, &Wm, &W0, &Wp);
+    coef[0] = ce.on; coef[1] = ce.sxx; coef[2] = ce.syy; coef[3] = ce.sxy; coef[4] = ce.sxz; coef[5] = ce.qx; coef[6] = ce.A;
+    ora_key key = { k0, k1 };
+    for (int64_t j = 0; j < n; ++j) {
+        opart q;
+        sample_particle(p, key, id, (uint32_t)j, step, &W0, &ce, &q);
+        xi[3 * j] = q.u; xi[3 * j + 1] = q.v; xi[3 * j + 2] = q.w;
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -716,7 +818,7 @@ int ora_step(void *vh, int32_t nsteps)
             if (grow(h, &pre, &cpre, npre + ng)) return -2;
             for (int64_t j = 0; j < ng; ++j) {
                 opart *q = pre + npre++;
-                sample_particle(p, h->key, 0u, (uint32_t)j, h->step, &g, q);
+                sample_particle(p, h->key, 0u, (uint32_t)j, h->step, &g, NULL, q);
                 q->cell = -1;
             }
         }
@@ -739,9 +841,22 @@ int ora_step(void *vh, int32_t nsteps)
             double rho_w = h->psi[5 * i] - (double)nsurv * c->mp_over_dx;
             int64_t nn = W[i].valid ? n_resample(h, (uint32_t)(i + 1), P[i], rho_w) : 0;
             if (grow(h, &pre, &cpre, npre + nn)) return -2;
+            ora_ce ce;
+            memset(&ce, 0, sizeof ce);
+            if (p->resample_mode == ORA_RESAMPLE_CE && nn > 0) {
+                /* neighbouring states as the wave flux sees them */
+                ora_prim Wm, Wp;
+                if (i > 0) Wm = W[i - 1];
+                else if (p->bc_left == ORA_BC_PERIODIC) Wm = W[C - 1];
+                else Wm = ghost_prim(h, 0, &W[0]);
+                if (i < C - 1) Wp = W[i + 1];
+                else if (p->bc_right == ORA_BC_PERIODIC) Wp = W[0];
+                else Wp = ghost_prim(h, 1, &W[C - 1]);
+                ce = ce_factor(p, c, &Wm, &W[i], &Wp);
+            }
             for (int64_t j = 0; j < nn; ++j) {
                 opart *q = pre + npre++;
-                sample_particle(p, h->key, (uint32_t)(i + 1), (uint32_t)j, h->step, &W[i], q);
+                sample_particle(p, h->key, (uint32_t)(i + 1), (uint32_t)j, h->step, &W[i], &ce, q);
                 q->cell = i;
             }
             collide_cell(h, i, pre + base, npre - base, h->psi[5 * i], &h->ncand[i], &h->nacc[i]);
@@ -756,7 +871,7 @@ int ora_step(void *vh, int32_t nsteps)
             if (grow(h, &pre, &cpre, npre + ng)) return -2;
             for (int64_t j = 0; j < ng; ++j) {
                 opart *q = pre + npre++;
-                sample_particle(p, h->key, (uint32_t)(C + 1), (uint32_t)j, h->step, &g, q);
+                sample_particle(p, h->key, (uint32_t)(C + 1), (uint32_t)j, h->step, &g, NULL, q);
                 q->cell = C;
             }
         }

@@ -182,3 +182,49 @@ def test_absorption_fraction_is_P(oracle_mod):
     nabs = o.counters()["nabs"].sum()
     assert 0.3 < P < 0.95
     assert abs(nabs - P * n_before) < 5 * math.sqrt(n_before * P * (1 - P))
+
+
+# ------------------------------------------------------------------ Chapman-Enskog re-sampling
+def _ce_params(**kw):
+    # wave regime (dt >> tau): eps ~ 1, so the correction carries the full NS stress and heat flux
+    p = W.uniform(n_cells=50, Kn=0.01, ppc_ref=100, state=(1.0, 0.0, 0.0, 0.0, 1.0), x_max=1.0, dt=0.1,
+                  resample_mode="ce")
+    p.update(kw)
+    return p
+
+
+@pytest.mark.parametrize("grad", [(0.075, 0.0, 0.05), (-0.06, 0.1, -0.04)])
+def test_ce_samples_carry_the_ns_stress_and_heat_flux(oracle_mod, grad):
+    # The Chapman-Enskog density f_M (1 + Gamma_1) must reproduce the pressure tensor p delta + sigma
+    # and the heat flux q it is built from, while keeping density, velocity and temperature: the
+    # sample moments are compared with the coefficients within 5 standard errors.
+    dU, dV, dT = grad                      # differences across the cell, so gradients ~ 1/dx larger
+    Wm, W0, Wp = (1.0, -dU, -dV, 0.0, 1.0 - dT), (1.0, 0.0, 0.0, 0.0, 1.0), (1.0, dU, dV, 0.0, 1.0 + dT)
+    n = 400_000
+    coef, xi = oracle_mod.ce_sample(_ce_params(), Wm, W0, Wp, n=n)
+    on, sxx, syy, sxy, sxz, qx, A = coef
+    assert on == 1 and 1.0 < A < 8.6
+    assert max(abs(sxx), abs(sxy), abs(qx)) > 0.02     # a correction far above the sampling noise
+    c = xi                                              # U = 0
+    se2 = np.sqrt(2.0 / n)                              # standard error of <c_x^2> (RT = 1)
+    assert abs(c[:, 0].mean()) < 5 * np.sqrt(1.0 / n)
+    assert (c[:, 0] ** 2).mean() - 1.0 == pytest.approx(sxx, abs=5 * se2)
+    assert (c[:, 1] ** 2).mean() - 1.0 == pytest.approx(syy, abs=5 * se2)
+    assert (c[:, 2] ** 2).mean() - 1.0 == pytest.approx(syy, abs=5 * se2)
+    assert (c[:, 0] * c[:, 1]).mean() == pytest.approx(sxy, abs=5 * np.sqrt(1.0 / n))
+    assert (c ** 2).sum(1).mean() == pytest.approx(3.0, abs=5 * np.sqrt(6.0 / n))
+    q_sample = 0.5 * (c[:, 0] * (c ** 2).sum(1)).mean()
+    assert q_sample == pytest.approx(qx, abs=5 * 0.5 * np.sqrt(35.0 / n))
+
+
+def test_ce_without_gradients_or_out_of_range_is_the_maxwellian(oracle_mod):
+    W0 = (1.0, 0.2, 0.0, 0.0, 1.3)
+    _, ref = oracle_mod.ce_sample(_ce_params(resample_mode="maxwell"), W0, W0, W0, n=2000)
+    coef, xi = oracle_mod.ce_sample(_ce_params(), W0, W0, W0, n=2000)
+    assert coef[0] == 1 and coef[6] == 1.0              # no gradient: Gamma = 1, every first draw accepted
+    assert np.array_equal(xi, ref)
+    steep = ((1.0, -0.5, 0.0, 0.0, 0.5), W0, (1.0, 0.9, 0.0, 0.0, 2.0))
+    coef, xi = oracle_mod.ce_sample(_ce_params(), *steep, n=2000)
+    assert coef[0] == 0                                 # beyond the first-order range: Maxwellian
+    _, ref = oracle_mod.ce_sample(_ce_params(resample_mode="maxwell"), *steep, n=2000)
+    assert np.array_equal(xi, ref)
