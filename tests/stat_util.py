@@ -1,0 +1,97 @@
+"""Long-run statistics of time-averaged profiles (stochastic results that cannot agree run by run).
+
+The Mach-3 argon shock (100 cells, ~200 particles per upstream cell, 500 steps, averages over the
+states after step 100) wanders: a single correct run differs from the ensemble mean by 1-4% in L2, concentrated at
+the shock.  So two implementations (or precisions) are compared through ensembles of runs with
+distinct seeds: with means m_a, m_b and single-run standard deviations s_a, s_b over K_a, K_b runs,
+per quantity (density, velocity, temperature of the averaged state) and cell,
+  d = m_a - m_b,  sigma_d = sqrt(s_a^2 / K_a + s_b^2 / K_b);
+they agree when at most 5 of the 100 cells have |d| > 3 sigma_d (a chance failure of a correct
+pair has probability below 1e-3 per quantity for K >= 16) and, where the ensembles are large
+enough that the noise in d is well below 1% (K = 128 each: ~0.5% for the temperature), the
+relative L2 distance |d| / |m_b| is at most 1%.
+"""
+import os
+
+import numpy as np
+
+from paper_2305_12071_gb300 import workloads as W
+
+STEPS = 500
+AVG_START = 100
+MAX_EXCEED = 5
+REL_L2 = 0.01
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shock_mach3_average.txt")
+QUANTITIES = ("rho", "u", "T")
+
+
+def problem(precision: str, seed: int, **kw) -> dict:
+    p = W.config1(precision)
+    p.update(seed=seed, avg_start=AVG_START, **kw)
+    return p
+
+
+def profiles(psi_sum: np.ndarray, n: int, R: float = 1.0) -> dict:
+    """rho, u, T of the time-averaged conservative state (sums over n states)."""
+    m = psi_sum / float(n)
+    rho = m[:, 0]
+    u = m[:, 1] / rho
+    e = m[:, 4] / rho - 0.5 * (m[:, 1] ** 2 + m[:, 2] ** 2 + m[:, 3] ** 2) / rho ** 2
+    return {"rho": rho, "u": u, "T": e / (1.5 * R)}
+
+
+def oracle_profiles(oracle_mod, p: dict) -> dict:
+    o = oracle_mod.Oracle(p)
+    o.step(STEPS)
+    a, n = o.avg()
+    assert n == STEPS - p["avg_start"]
+    return profiles(a, n, p.get("R", 1.0))
+
+
+def summarize(runs: list) -> dict:
+    """{quantity: (mean, single-run sd, K)} of a list of profile dicts."""
+    out = {}
+    for k in QUANTITIES:
+        x = np.stack([r[k] for r in runs])
+        out[k] = (x.mean(axis=0), x.std(axis=0, ddof=1), x.shape[0])
+    return out
+
+
+def load_golden() -> dict:
+    t = np.loadtxt(GOLDEN)
+    with open(GOLDEN) as f:
+        head = f.read(2000)
+    K = int(head.split("K = ")[1].split()[0])
+    return {k: (t[:, 2 * j], t[:, 2 * j + 1], K) for j, k in enumerate(QUANTITIES)}
+
+
+def verdict(a: dict, b: dict) -> dict:
+    """Per quantity: (relative L2 distance of the means, cells beyond 3 sigma_d)."""
+    res = {}
+    for k in QUANTITIES:
+        ma, sa, Ka = a[k]
+        mb, sb, Kb = b[k]
+        d = ma - mb
+        sd = np.sqrt(sa ** 2 / Ka + sb ** 2 / Kb)
+        res[k] = (float(np.linalg.norm(d) / np.linalg.norm(mb)), int(np.sum(np.abs(d) > 3.0 * sd)))
+    return res
+
+
+def agrees(v: dict, with_l2: bool) -> bool:
+    return all((rel <= REL_L2 or not with_l2) and ex <= MAX_EXCEED for rel, ex in v.values())
+
+
+def _oracle_run(args):
+    import oracle
+    precision, seed, kw = args
+    return oracle_profiles(oracle, problem(precision, seed, **kw))
+
+
+def oracle_ensemble(precision: str, seeds, **kw) -> dict:
+    """summarize() of oracle runs with the given seeds, in a pool of spawned processes."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+        runs = pool.map(_oracle_run, [(precision, s, kw) for s in seeds])
+    return summarize(runs)
