@@ -64,6 +64,7 @@ enum { DUWP_FP64 = 0, DUWP_FP32 = 1 };                       /* particle record 
 enum { DUWP_EPS1 = 0, DUWP_EPS12 = 1, DUWP_EPS0 = 2, DUWP_EPS_AVG = 3 }; /* Sec. 3.3 */
 enum { DUWP_FLUX_GKS_EQ = 0, DUWP_FLUX_KFVS = 1 };           /* wave-flux form */
 enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the NTC count */
+enum { DUWP_RESAMPLE_MAXWELL = 0, DUWP_RESAMPLE_CE = 1 };    /* velocity law of re-sampled particles */
 
 /*
  * Problem parameters of one instance (Sec. 4 and Appendix A; units nondimensional):
@@ -83,7 +84,15 @@ enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the N
  *   seed                key of the counter-based generator of this instance;
  *   capacity            particle slots per buffer (0: automatic; each cell's output block takes
  *                       twice the bound on its list after re-sampling);
- *   avg_start           time averages accumulate the states after step avg_start.
+ *   avg_start           time averages accumulate the states after step avg_start;
+ *   resample_mode       velocities of the particles drawn from the wave (Sec. 3.4, Step 2):
+ *                       DUWP_RESAMPLE_MAXWELL (default, Eq. maxsample: the local Maxwellian) or
+ *                       DUWP_RESAMPLE_CE (the local Maxwellian times its first-order
+ *                       Chapman-Enskog factor, Eq. ce2, with the NS stress and heat flux of the
+ *                       wave from central differences of the neighbouring cells and the viscosity
+ *                       eps mu of the flux; drawn by acceptance-rejection against 1 + 30 B, B the
+ *                       largest normalised stress or heat flux; Maxwellian where B > 1/4 and in the
+ *                       inflow reservoirs).
  * In a batch all instances must use the same precision.
  */
 typedef struct {
@@ -101,6 +110,7 @@ typedef struct {
     uint64_t seed;
     uint64_t capacity;
     int32_t avg_start;
+    int32_t resample_mode;
 } duwp_params;
 
 /* Device allocator callbacks: alloc returns device memory of `bytes` bytes usable on `stream`
@@ -169,9 +179,26 @@ int duwp_moments(duwp_handle *h, int32_t inst, int32_t which, double *host_rho, 
  * sum of n_cells over the active instances); instance b's cells follow those of the active
  * instances with smaller index.  Any of the output pointers may be NULL.  The values are those of
  * duwp_moments bit for bit.  Errors: DUWP_EINVAL (which, or total_cells not the sum), DUWP_ENOMEM
- * (its device scratch, 32 B per cell, kept by the handle), device errors. */
+ * (its device scratch, 64 B per cell, kept by the handle), device errors. */
 int duwp_moments_all(duwp_handle *h, int32_t which, double *host_rho, double *host_u, double *host_T,
                      double *host_wave_frac, int64_t total_cells);
+
+/* Non-blocking.  duwp_moments_all of the state reached by the steps enqueued so far: the profile
+ * pass is enqueued behind them and the copies into the caller's HOST arrays run on a separate
+ * stream, so the caller may enqueue the next steps at once and they overlap with the copies (the
+ * arrays must be pinned for that; with pageable arrays the call blocks until its copies are done).
+ * The arrays (same layout as duwp_moments_all) must stay valid, and are not to be read, until
+ * duwp_moments_wait (or any synchronizing call) returns.  Reads complete in call order; at most two
+ * are in flight (a third waits on the device, not the host, for the first one's copies).  Values
+ * equal those of duwp_moments_all bit for bit.  Errors: DUWP_EINVAL (which, or total_cells not the
+ * sum), DUWP_ENOMEM (scratch, 64 B per cell); device errors are reported by the next synchronizing
+ * call. */
+int duwp_moments_all_async(duwp_handle *h, int32_t which, double *host_rho, double *host_u, double *host_T,
+                           double *host_wave_frac, int64_t total_cells);
+
+/* Blocks until every read enqueued by duwp_moments_all_async has landed in its host arrays (the steps
+ * enqueued after them may still run).  Errors: DUWP_EINVAL (h), device errors. */
+int duwp_moments_wait(duwp_handle *h);
 
 /* Synchronizing.  Conservative total state Psi_t = (rho, rho U, rho V, rho W, rho E) per cell of
  * instance `inst` (which = DUWP_INSTANT) or its time average (DUWP_AVERAGED) into a caller-owned

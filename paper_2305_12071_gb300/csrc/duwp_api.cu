@@ -56,6 +56,7 @@ int derive_instance(const duwp_params &p, HostInst &o)
     if (p.precision != DUWP_FP64 && p.precision != DUWP_FP32) return DUWP_EINVAL;
     if (p.eps_mode < 0 || p.eps_mode > 3 || p.flux_mode < 0 || p.flux_mode > 1 || p.ntc_rate < 0 || p.ntc_rate > 1)
         return DUWP_EINVAL;
+    if (p.resample_mode != DUWP_RESAMPLE_MAXWELL && p.resample_mode != DUWP_RESAMPLE_CE) return DUWP_EINVAL;
     if (!(p.dt > 0.0) && !(p.cfl > 0.0)) return DUWP_EINVAL;
 
     o.p = p;
@@ -67,6 +68,7 @@ int derive_instance(const duwp_params &p, HostInst &o)
     d.eps_mode = p.eps_mode;
     d.flux_mode = p.flux_mode;
     d.ntc_rate = p.ntc_rate;
+    d.resample_mode = p.resample_mode;
     d.active = 1;
     d.key0 = static_cast<uint32_t>(p.seed & 0xffffffffu);
     d.key1 = static_cast<uint32_t>(p.seed >> 32);
@@ -154,8 +156,14 @@ void Engine::drop_graphs()
 
 Engine::~Engine()
 {
+    if (cstream) cudaStreamSynchronize(cstream);
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    for (int k = 0; k < 2; ++k) {
+        if (mom_ready[k]) cudaEventDestroy(mom_ready[k]);
+        if (copy_done[k]) cudaEventDestroy(copy_done[k]);
+    }
+    if (cstream) cudaStreamDestroy(cstream);
     if (mom) dfree(mom, mom_bytes);
     dfree(slab, slab_bytes);
     if (stream) cudaStreamSynchronize(stream);
@@ -449,6 +457,7 @@ int Engine::step(int32_t n)
 
 int Engine::sync()
 {
+    if (cstream) DUWP_CU(cudaStreamSynchronize(cstream));
     DUWP_CU(cudaStreamSynchronize(stream));
     int32_t e = 0;
     DUWP_CU(cudaMemcpy(&e, dev.err, sizeof e, cudaMemcpyDeviceToHost));
@@ -628,44 +637,117 @@ int duwp_moments(duwp_handle *h, int32_t b, int32_t which, double *rho, double *
     return DUWP_OK;
 }
 
-int duwp_moments_all(duwp_handle *h, int32_t which, double *rho, double *u, double *T, double *wave_frac,
-                     int64_t total_cells)
+namespace duwp {
+
+int Engine::moments_scratch(const std::vector<int64_t> &base, int64_t total)
 {
-    if (!h || (which != DUWP_INSTANT && which != DUWP_AVERAGED)) return DUWP_EINVAL;
-    Engine &E = h->eng;
-    std::vector<int64_t> base(static_cast<size_t>(E.max_inst), -1);
+    const size_t head = (sizeof(int64_t) * base.size() + 255) & ~static_cast<size_t>(255);
+    const size_t area = (sizeof(double) * 4 * static_cast<size_t>(total) + 255) & ~static_cast<size_t>(255);
+    const size_t need = head + 2 * area;
+    if (mom_bytes >= need && base == mom_base && mom_area == area) return DUWP_OK;
+    // the scratch may still be read by pending copies: wait for them first
+    int rc = sync();
+    if (rc) return rc;
+    if (mom_bytes < need) {
+        if (mom) dfree(mom, mom_bytes);
+        mom = nullptr;
+        mom_bytes = 0;
+        mom = dalloc(need);
+        if (!mom) return DUWP_ENOMEM;
+        mom_bytes = need;
+    }
+    mom_head = head;
+    mom_area = area;
+    DUWP_CU(cudaMemcpyAsync(mom, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice, stream));
+    DUWP_CU(cudaStreamSynchronize(stream));
+    mom_base = base;
+    return DUWP_OK;
+}
+
+double *Engine::mom_out(int area) const
+{
+    return reinterpret_cast<double *>(static_cast<unsigned char *>(mom) + mom_head + static_cast<size_t>(area) * mom_area);
+}
+
+}  // namespace duwp
+
+// Bases of the active instances' cells in the output arrays of the profile reads; returns the total.
+static int64_t moment_bases(const Engine &E, std::vector<int64_t> &base)
+{
+    base.assign(static_cast<size_t>(E.max_inst), -1);
     int64_t total = 0;
     for (int32_t b = 0; b < E.max_inst; ++b) {
         if (!E.inst[b].active) continue;
         base[b] = total;
         total += E.inst[b].p.n_cells;
     }
+    return total;
+}
+
+int duwp_moments_all(duwp_handle *h, int32_t which, double *rho, double *u, double *T, double *wave_frac,
+                     int64_t total_cells)
+{
+    if (!h || (which != DUWP_INSTANT && which != DUWP_AVERAGED)) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    std::vector<int64_t> base;
+    const int64_t total = moment_bases(E, base);
     if (total != total_cells) return DUWP_EINVAL;
     if (total == 0) return E.sync();
-    const size_t need = sizeof(int64_t) * base.size() + sizeof(double) * 4 * static_cast<size_t>(total) + 256;
-    if (E.mom_bytes < need) {
-        if (E.mom) {
-            const int rc = E.sync();
-            if (rc) return rc;
-            E.dfree(E.mom, E.mom_bytes);
-            E.mom = nullptr;
-            E.mom_bytes = 0;
-        }
-        E.mom = E.dalloc(need);
-        if (!E.mom) return DUWP_ENOMEM;
-        E.mom_bytes = need;
-    }
-    int64_t *d_base = static_cast<int64_t *>(E.mom);
-    double *d_out = reinterpret_cast<double *>(static_cast<unsigned char *>(E.mom) +
-                                               ((sizeof(int64_t) * base.size() + 255) & ~static_cast<size_t>(255)));
-    DUWP_CU(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice, E.stream));
-    DUWP_CU(launch_moments(E.dev, which, d_base, total, d_out, E.stream));
+    int rc = E.moments_scratch(base, total);
+    if (rc) return rc;
+    // area 0 may be the target of a pending non-blocking read
+    if (E.cstream) DUWP_CU(cudaStreamSynchronize(E.cstream));
+    double *d_out = E.mom_out(0);
+    DUWP_CU(launch_moments(E.dev, which, static_cast<const int64_t *>(E.mom), total, d_out, E.stream));
     double *dst[4] = {rho, u, T, wave_frac};
     for (int k = 0; k < 4; ++k)
         if (dst[k])
             DUWP_CU(cudaMemcpyAsync(dst[k], d_out + static_cast<size_t>(k) * total, sizeof(double) * total,
                                     cudaMemcpyDeviceToHost, E.stream));
     return E.sync();
+}
+
+int duwp_moments_all_async(duwp_handle *h, int32_t which, double *rho, double *u, double *T, double *wave_frac,
+                           int64_t total_cells)
+{
+    if (!h || (which != DUWP_INSTANT && which != DUWP_AVERAGED)) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    std::vector<int64_t> base;
+    const int64_t total = moment_bases(E, base);
+    if (total != total_cells) return DUWP_EINVAL;
+    if (total == 0) return DUWP_OK;
+    int rc = E.moments_scratch(base, total);
+    if (rc) return rc;
+    if (!E.cstream) {
+        DUWP_CU(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            DUWP_CU(cudaEventCreateWithFlags(&E.mom_ready[k], cudaEventDisableTiming));
+            DUWP_CU(cudaEventCreateWithFlags(&E.copy_done[k], cudaEventDisableTiming));
+        }
+    }
+    const int a = static_cast<int>(E.n_async & 1);
+    // area a is free once the copies of the read two calls back have finished
+    if (E.n_async >= 2) DUWP_CU(cudaStreamWaitEvent(E.stream, E.copy_done[a], 0));
+    double *d_out = E.mom_out(a);
+    DUWP_CU(launch_moments(E.dev, which, static_cast<const int64_t *>(E.mom), total, d_out, E.stream));
+    DUWP_CU(cudaEventRecord(E.mom_ready[a], E.stream));
+    DUWP_CU(cudaStreamWaitEvent(E.cstream, E.mom_ready[a], 0));
+    double *dst[4] = {rho, u, T, wave_frac};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k])
+            DUWP_CU(cudaMemcpyAsync(dst[k], d_out + static_cast<size_t>(k) * total, sizeof(double) * total,
+                                    cudaMemcpyDeviceToHost, E.cstream));
+    DUWP_CU(cudaEventRecord(E.copy_done[a], E.cstream));
+    E.n_async += 1;
+    return DUWP_OK;
+}
+
+int duwp_moments_wait(duwp_handle *h)
+{
+    if (!h) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    if (E.cstream) DUWP_CU(cudaStreamSynchronize(E.cstream));
+    return DUWP_OK;
 }
 
 int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)

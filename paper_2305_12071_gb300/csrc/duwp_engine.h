@@ -61,9 +61,17 @@ struct Engine {
     bool use_graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step starting at read parity 0 / 1
 
-    // device scratch of duwp_moments_all (allocated on first use)
+    // device scratch of the profile reads (allocated on first use): the table of instance bases
+    // (uploaded when the set of instances changes) and two output areas of 4 x total doubles; the
+    // non-blocking reads copy out on their own stream, area n_async % 2, ordered by events
     void *mom = nullptr;
     size_t mom_bytes = 0;
+    size_t mom_head = 0, mom_area = 0;
+    std::vector<int64_t> mom_base;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t mom_ready[2] = {nullptr, nullptr};
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+    int64_t n_async = 0;
 
     ~Engine();
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
@@ -74,7 +82,9 @@ struct Engine {
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[kStepEvents]: events around kernels
     int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
     int step(int32_t n);
-    int sync();                        // wait + read the device error word
+    int sync();                        // wait (steps and profile copies) + read the device error word
+    int moments_scratch(const std::vector<int64_t> &base, int64_t total);   // size + base table
+    double *mom_out(int area) const;
     int read_inst(int b, InstDev &out);
     void *dalloc(size_t bytes);
     void dfree(void *p, size_t bytes);

@@ -51,7 +51,7 @@ struct InstDev {
     double ntc_rr;          // m_p / (dx rho_ref): particle density ratio per particle
     double inv_rho_ref;
     float dtdx_f;
-    float pad0;
+    int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
     double left[5], right[5];   // reservoir primitive states (rho, u, v, w, T)
 };
 

@@ -128,6 +128,11 @@ struct MaxwellCell {
     ds s;
 };
 
+// Chapman-Enskog factor of a cell's samples under the NS-corrected option (below).
+struct CeCell {
+    double A, sxx, syy, sxy, sxz, qx, prt, RT;
+};
+
 __device__ inline MaxwellCell maxwell_cell(const InstDev &I, const double *q)
 {
     MaxwellCell m;
@@ -143,14 +148,103 @@ __device__ inline MaxwellCell maxwell_cell(const InstDev &I, const double *q)
 }
 
 // Velocities in double precision from the 14 draw words after the position's (w).
-template <typename T>
-__device__ __noinline__ void maxwell_fp64(const MaxwellCell &mc, const uint32_t *w, T out[3])
+__device__ __forceinline__ void maxwell_xi(const MaxwellCell &mc, const uint32_t *w, double out[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double r1 = u53(w[4 * d], w[4 * d + 1]);
         const double r2 = 1.0 - u53(w[4 * d + 2], w[4 * d + 3]);
-        out[d] = store_val(mc.q[1 + d] + (mc.sq * cos(kTwoPi * r1)) * sqrt(-log(r2)), T());
+        out[d] = mc.q[1 + d] + (mc.sq * cos(kTwoPi * r1)) * sqrt(-log(r2));
+    }
+}
+
+template <typename T>
+__device__ __noinline__ void maxwell_fp64(const MaxwellCell &mc, const uint32_t *w, T out[3])
+{
+    double xi[3];
+    maxwell_xi(mc, w, xi);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d] = store_val(xi[d], T());
+}
+
+// NS-corrected sampling (resample_mode CE; the first-order Chapman-Enskog form of the equilibrium,
+// Eq. ce2): the density f_M (1 + sigma_ij c_i c_j / (2 p R T) + (q . c / (p R T)) (c^2 / (5 R T) - 1)),
+// c = xi - U, with the 1D NS stress and heat flux of the wave at the viscosity eps mu of its flux
+// (Eq. vp1, Sec. 3.3):
+//   sigma_xx = -(4/3) mu_e dU/dx, sigma_yy = sigma_zz = (2/3) mu_e dU/dx, sigma_xy = -mu_e dV/dx,
+//   sigma_xz = -mu_e dW/dx, q_x = -kappa_e dT/dx, kappa_e = (5/2) R mu_e / Pr,
+// the gradients by central differences of the neighbouring states (the periodic partner or the
+// reservoir/mirror state beyond an end; an unusable neighbour counts as the cell's own state).
+// Drawn by acceptance-rejection against A = 1 + 30 B, B the largest of |sigma_ij| / p and
+// 2 |q_x| / (p sqrt(2RT)) (Garcia and Alder, J. Comput. Phys. 140, 1998); for B > 1/4 the expansion
+// is out of range and the plain Maxwellian is drawn.  Every expression keeps the order of
+// operations of the double-precision checker, so decisions agree to the last bit of the inputs.
+constexpr int kCeAttempts = 64;
+
+// Returns false where the plain Maxwellian is drawn.
+__device__ __noinline__ bool ce_coefs(const InstDev &I, const double *prim, const int32_t *valid, int g, int i,
+                                      CeCell &m)
+{
+    if (!valid[g]) return false;
+    const double *W0 = prim + 5 * g;
+    double wm[5], wp[5];
+    bool okm, okp;
+    const bool periodic = (I.bc_left == 2);
+    if (i > 0) { for (int k = 0; k < 5; ++k) wm[k] = W0[k - 5]; okm = valid[g - 1] != 0; }
+    else if (periodic) { for (int k = 0; k < 5; ++k) wm[k] = prim[5 * (g + I.C - 1) + k]; okm = valid[g + I.C - 1] != 0; }
+    else okm = ghost_prim(I, 0, W0, true, wm);
+    if (i < I.C - 1) { for (int k = 0; k < 5; ++k) wp[k] = W0[k + 5]; okp = valid[g + 1] != 0; }
+    else if (periodic) { for (int k = 0; k < 5; ++k) wp[k] = prim[5 * (g - I.C + 1) + k]; okp = valid[g - I.C + 1] != 0; }
+    else okp = ghost_prim(I, 1, W0, true, wp);
+    const double *a = okm ? wm : W0, *b = okp ? wp : W0;
+    const double inv = 1.0 / (2.0 * I.dx);
+    const double dU = (b[1] - a[1]) * inv, dV = (b[2] - a[2]) * inv, dW = (b[3] - a[3]) * inv;
+    const double dT = (b[4] - a[4]) * inv;
+    const double RT = I.R * W0[4];
+    const double p0 = W0[0] * RT;
+    const double mu = viscosity(I, W0[4]);
+    const double mue = eps_factor(I.eps_mode, I.dt / (mu / p0)) * mu;
+    const double kap = 2.5 * I.R * mue / I.Pr;
+    m.sxx = -(4.0 / 3.0) * mue * dU;
+    m.syy = (2.0 / 3.0) * mue * dU;
+    m.sxy = -mue * dV;
+    m.sxz = -mue * dW;
+    m.qx = -kap * dT;
+    double B = fmax(fmax(fabs(m.sxx), fabs(m.syy)), fmax(fabs(m.sxy), fabs(m.sxz))) / p0;
+    B = fmax(B, 2.0 * fabs(m.qx) / (p0 * sqrt(2.0 * RT)));
+    if (!(B <= 0.25)) return false;
+    m.RT = RT;
+    m.prt = p0 * RT;
+    m.A = 1.0 + 30.0 * B;
+    return true;
+}
+
+__device__ __forceinline__ double ce_gamma(const MaxwellCell &mc, const CeCell &m, const double xi[3])
+{
+    const double cx = xi[0] - mc.q[1], cy = xi[1] - mc.q[2], cz = xi[2] - mc.q[3];
+    const double c2 = cx * cx + cy * cy + cz * cz;
+    const double s = m.sxx * cx * cx + m.syy * (cy * cy + cz * cz) + 2.0 * (m.sxy * cx * cy + m.sxz * cx * cz);
+    return 1.0 + s / (2.0 * m.prt) + (m.qx * cx / m.prt) * (c2 / (5.0 * m.RT) - 1.0);
+}
+
+// Velocities of an NS-corrected sample: attempt 0 uses the sample's own words w0 (velocities from
+// w0[2..13], acceptance from w0[14..15]); attempt a > 0 draws the counters (id, 4j..4j+3, step,
+// SAMPLE + 8a).  After kCeAttempts rejections the attempt-0 Maxwellian is kept.
+__device__ __noinline__ void ce_xi(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
+                                   const CeCell &ce, const uint32_t *w0, double xi[3])
+{
+    maxwell_xi(mc, w0 + 2, xi);
+    if (u53(w0[14], w0[15]) * ce.A < ce_gamma(mc, ce, xi)) return;
+    uint32_t w[16];
+    double t[3];
+    for (int a = 1; a < kCeAttempts; ++a) {
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) draw(I, id, 4u * j + k, step, kSample + 8u * static_cast<uint32_t>(a), w + 4 * k);
+        maxwell_xi(mc, w + 2, t);
+        if (u53(w[14], w[15]) * ce.A < ce_gamma(mc, ce, t)) {
+            xi[0] = t[0]; xi[1] = t[1]; xi[2] = t[2];
+            return;
+        }
     }
 }
 
@@ -163,7 +257,8 @@ __device__ __forceinline__ float u53_float(uint32_t a, uint32_t b)
 }
 
 template <typename Rec>
-__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc)
+__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
+                                           const CeCell *ce)
 {
     uint32_t w[16];
 #pragma unroll
@@ -171,7 +266,14 @@ __device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint3
     Rec r;
     using T = decltype(r.xl);
     T x, xi[3];
-    if constexpr (sizeof(T) == 4) {
+    if (ce) {
+        // NS-corrected option: the acceptance test needs the double-precision velocities
+        x = (sizeof(T) == 4) ? static_cast<T>(u53_float(w[0], w[1])) : static_cast<T>(u53(w[0], w[1]));
+        double xd[3];
+        ce_xi(I, id, j, step, mc, *ce, w, xd);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) xi[d] = store_val(xd[d], T());
+    } else if constexpr (sizeof(T) == 4) {
         // single-precision records: double-single evaluation, double precision only where the
         // rounding of a component cannot be guaranteed
         x = u53_float(w[0], w[1]);
@@ -186,6 +288,19 @@ __device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint3
     r.v = xi[1];
     r.w = xi[2];
     return r;
+}
+
+// Samples j0..j1-1 of interior cell g (local index i) under the NS-corrected option, one per lane,
+// into dst[j]: the per-cell factor once, then the samples (Maxwellian where the factor is off).
+template <typename Rec>
+__device__ __noinline__ void sample_run_ce(const InstDev &I, const double *prim, const int32_t *valid, int g, int i,
+                                           uint32_t step, Rec *dst, int j0, int j1, int lane)
+{
+    const MaxwellCell mc = maxwell_cell(I, prim + 5 * g);
+    CeCell ce;
+    const bool on = ce_coefs(I, prim, valid, g, i, ce);
+    for (int j = j0 + lane; j < j1; j += 32)
+        st_rec(dst + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), step, mc, on ? &ce : nullptr));
 }
 
 // Lower bound of `key` in the far list ordered by (dest, src, q): first index with (dest, src) >= key.
@@ -677,9 +792,13 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
         return;
     }
     if (nn > 0) {
-        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
-        for (int j = lane; j < nn; j += 32)
-            st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc));
+        if (I.resample_mode == 1) {
+            sample_run_ce<Rec>(I, E.prim, E.valid, g, h.i, step, stage + run, 0, static_cast<int>(nn), lane);
+        } else {
+            const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+            for (int j = lane; j < nn; j += 32)
+                st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc, nullptr));
+        }
     }
     __syncwarp();
     const double cm0 = E.cmax[g];
@@ -755,10 +874,15 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
         const long long off = h.off;
         if (cls != kClsStream && cls != kClsReservoir) continue;
         const InstDev &I = E.inst[b];
-        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
         const int j1 = min(j0 + kSampleChunk, n_new);
+        if (I.resample_mode == 1 && cls == kClsStream) {
+            sample_run_ce<Rec>(I, E.prim, E.valid, g, i, I.step, out + off + n_in, j0, j1, lane);
+            continue;
+        }
+        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
         for (int j = j0 + lane; j < j1; j += 32)
-            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, mc));
+            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, mc,
+                                                              nullptr));
     }
 }
 
@@ -945,6 +1069,9 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
     }
 }
 
+// Groups of 32 records each lane loads before any of them is processed (loads in flight per warp).
+constexpr int kStreamGroups = 2;
+
 template <typename Rec, int kMinBlocks>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
 {
@@ -1009,10 +1136,10 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
     for (int q = 0; q < 6; ++q) {
         const void *p = SS.piece[q].p;
         const int n = SS.piece[q].n, k0 = SS.piece[q].k0, dir = SS.piece[q].dir, kind = SS.piece[q].kind;
-        for (int base = 0; base < n; base += 64) {
-            Rec v[2];
+        for (int base = 0; base < n; base += 32 * kStreamGroups) {
+            Rec v[kStreamGroups];
 #pragma unroll
-            for (int u2 = 0; u2 < 2; ++u2) {
+            for (int u2 = 0; u2 < kStreamGroups; ++u2) {
                 const int r = base + 32 * u2 + lane;
                 if (r < n) {
                     if (kind == 0) v[u2] = ld_rec(static_cast<const Rec *>(p) + dir * r);
@@ -1021,7 +1148,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
                 }
             }
 #pragma unroll
-            for (int u2 = 0; u2 < 2; ++u2) {
+            for (int u2 = 0; u2 < kStreamGroups; ++u2) {
                 const int r = base + 32 * u2 + lane;
                 if (base + 32 * u2 >= n) break;
                 int c = 5;

@@ -23,10 +23,11 @@ PRECISION = {"fp64": 0, "fp32": 1}
 EPS = {"eps1": 0, "eps12": 1, "eps0": 2, "eps_avg": 3}
 FLUX = {"gks_eq": 0, "kfvs": 1}
 NTC = {"particle": 0, "total": 1}
+RESAMPLE = {"maxwell": 0, "ce": 1}
 
 # Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
 EXPORTS = (
-    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_step_timed", "duwp_moments", "duwp_moments_all", "duwp_fields", "duwp_get_info",
+    "duwp_init", "duwp_init_batch", "duwp_step", "duwp_sync", "duwp_step_timed", "duwp_moments", "duwp_moments_all", "duwp_moments_all_async", "duwp_moments_wait", "duwp_fields", "duwp_get_info",
     "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
@@ -63,6 +64,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("capacity", C.c_uint64),
         ("avg_start", C.c_int32),
+        ("resample_mode", C.c_int32),
     ]
 
 
@@ -119,6 +121,8 @@ def load(path: str = LIB_PATH):
         L.duwp_step_timed.argtypes = [vp, i32, dp, dp]
         L.duwp_moments.argtypes = [vp, i32, i32, dp, dp, dp, dp, i32]
         L.duwp_moments_all.argtypes = [vp, i32, dp, dp, dp, dp, i64]
+        L.duwp_moments_all_async.argtypes = [vp, i32, dp, dp, dp, dp, i64]
+        L.duwp_moments_wait.argtypes = [vp]
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
@@ -169,6 +173,7 @@ def make_params(p: dict) -> Params:
     s.seed = int(p.get("seed", 1)) & 0xFFFFFFFFFFFFFFFF
     s.capacity = int(p.get("capacity", 0))
     s.avg_start = int(p.get("avg_start", 0))
+    s.resample_mode = RESAMPLE[p.get("resample_mode", "maxwell")]
     return s
 
 
@@ -300,6 +305,21 @@ class Solver:
         _chk(self.L.duwp_moments_all(self.h, which, _dptr(out["rho"]), _dptr(out["u"]), _dptr(out["T"]),
                                      _dptr(out["wave_frac"]), total), "duwp_moments_all")
         return out
+
+    def moments_all_async(self, out: dict, which: int = INSTANT) -> dict:
+        """Enqueue moments_all into the host arrays of `out` (pinned, so that the copies overlap with
+        the next steps) and return at once; the arrays are valid after moments_wait()."""
+        total = sum(self.n_cells(i) for i in range(self.n))
+        for k in ("rho", "u", "T", "wave_frac"):
+            a = out[k]
+            if a.shape != (total,) or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError(f"moments_all_async: out[{k!r}] must hold {total} contiguous float64")
+        _chk(self.L.duwp_moments_all_async(self.h, which, _dptr(out["rho"]), _dptr(out["u"]), _dptr(out["T"]),
+                                           _dptr(out["wave_frac"]), total), "duwp_moments_all_async")
+        return out
+
+    def moments_wait(self):
+        _chk(self.L.duwp_moments_wait(self.h), "duwp_moments_wait")
 
     def num_particles(self, inst: int = 0) -> int:
         o = C.c_int64()

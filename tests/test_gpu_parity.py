@@ -59,6 +59,42 @@ def test_sod_wave_regime_fp32():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ns_corrected_resampling(precision):
+    # resample_mode CE: particles drawn from the wave follow the Maxwellian times its Chapman-Enskog
+    # factor (acceptance-rejection, up to 64 attempts); mirror walls give the end cells' neighbours
+    p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=9, resample_mode="ce")
+    if precision == "fp64":
+        _run_pair(p, [1, 3, 20], REL64, REL64)
+    else:
+        _run_pair(p, [1, 5], REL32, REL64)
+    # the option is in effect: the first step's samples differ from the plain Maxwellian's
+    a, b = solver(p), solver(dict(p, resample_mode="maxwell"))
+    a.step(1)
+    b.step(1)
+    pa, pb = a.particles(), b.particles()
+    assert len(pa["u"]) == len(pb["u"])
+    assert np.setdiff1d(pa["u"], pb["u"]).size > 20
+    a.close()
+    b.close()
+    # inflow reservoirs beside the end cells (their own samples stay Maxwellian)
+    q = dict(W.config1(precision), Kn=2e-3, n_cells=80, ppc_ref=60, resample_mode="ce")
+    _run_pair(q, [1, 10] if precision == "fp64" else [1, 4], REL64 if precision == "fp64" else REL32, REL64)
+
+
+def test_resample_mode_is_validated():
+    import ctypes as C
+    from paper_2305_12071_gb300 import build as B
+    from paper_2305_12071_gb300 import duwp
+    B.build()
+    L = duwp.load()
+    prm = duwp.make_params(dict(W.config1("fp64"), n_cells=20))
+    prm.resample_mode = 2
+    h = C.c_void_p()
+    assert L.duwp_init(C.byref(prm), None, duwp.ALLOC_FN(0), duwp.FREE_FN(0), None, C.byref(h)) == -1
+    assert not h.value
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_periodic_far_movers(precision):
     # a time step of ~1.6 cells at the thermal speed: many particles move two or more cells,
     # and the periodic wrap sends particles across the whole domain
@@ -186,3 +222,27 @@ def test_moments_all_equals_per_instance():
                 assert np.array_equal(allm[k][o:o + n], m[k]), f"instance {i} {k} which {which}"
             o += n
     g.close()
+
+
+def test_async_moments_equal_synchronous_reads():
+    # reads enqueued behind each step into pinned arrays, overlapping the next step's kernels, equal
+    # the synchronous reads of a twin run bit for bit (three or more reads in flight exercise the
+    # reuse of the two device areas)
+    import torch
+    plist = [W.shock(m, n_cells=n, ppc_ref=80, precision="fp32", seed=30 + k)
+             for k, (m, n) in enumerate(((2.0, 70), (5.0, 130), (3.0, 41)))]
+    a, b = solver(plist), solver(plist)
+    total = sum(int(p["n_cells"]) for p in plist)
+    bufs = [{k: torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for k in ("rho", "u", "T", "wave_frac")}
+            for _ in range(6)]
+    for j in range(6):
+        a.step(1)
+        a.moments_all_async(bufs[j])
+    a.moments_wait()
+    for j in range(6):
+        b.step(1)
+        ref = b.moments_all()
+        for k in ref:
+            assert np.array_equal(ref[k], bufs[j][k]), (j, k)
+    a.close()
+    b.close()

@@ -228,3 +228,18 @@ def test_ce_without_gradients_or_out_of_range_is_the_maxwellian(oracle_mod):
     assert coef[0] == 0                                 # beyond the first-order range: Maxwellian
     _, ref = oracle_mod.ce_sample(_ce_params(resample_mode="maxwell"), *steep, n=2000)
     assert np.array_equal(xi, ref)
+
+
+def test_ce_option_is_active_in_the_sod_parity_case(oracle_mod):
+    # the wave-regime Sod tube of the GPU parity test: the first step re-samples every cell, and
+    # near the discontinuity the Chapman-Enskog factor rejects some first attempts
+    from paper_2305_12071_gb300 import workloads as W
+    runs = {}
+    for m in ("maxwell", "ce"):
+        o = oracle_mod.Oracle(W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision="fp64", seed=9, resample_mode=m))
+        o.step(1)
+        runs[m] = o.particles()
+    a, b = runs["maxwell"], runs["ce"]
+    assert len(a["u"]) == len(b["u"])
+    n_diff = np.setdiff1d(b["u"], a["u"]).size      # velocities not drawn by the plain Maxwellian
+    assert 20 < n_diff < len(a["u"]) // 10
