@@ -442,8 +442,15 @@ __device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint
 
 // The nc candidates of a staged cell list (nc from ntc_candidates), in order; candidate k is drawn
 // in the batch that reaches it.
+// A cell's particle list as collide_list sees it: position x -> record address.
 template <typename Rec>
-__device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_t step, Rec *list, int N, int64_t nc,
+struct StagedList {
+    Rec *p;
+    __device__ __forceinline__ Rec *at(int x) const { return p + x; }
+};
+
+template <typename Rec, typename List>
+__device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_t step, List list, int N, int64_t nc,
                                           double &cmax, int &nacc, int *s_ab)
 {
     const int lane = threadIdx.x & 31;
@@ -484,8 +491,8 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
         bool exact = false;
         const float cm32 = static_cast<float>(cm);
         if (lane < m1) {
-            A = list[a];
-            B = list[b];
+            A = *list.at(static_cast<int>(a));
+            B = *list.at(static_cast<int>(b));
             cr32 = rel_speed_f32(A, B);
             if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
                 cr = rel_speed(A, B);
@@ -501,8 +508,8 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
             accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
                 scatter_pair(I, id, static_cast<uint32_t>(k), step, A, B, cr, exact);
-                list[a] = A;
-                list[b] = B;
+                *list.at(static_cast<int>(a)) = A;
+                *list.at(static_cast<int>(b)) = B;
             }
         }
         acc += __popc(__ballot_sync(0xffffffffu, accd));
@@ -594,10 +601,11 @@ __device__ __forceinline__ Rec *arrived_ptr(int x, const CellHdr &h, Rec *in, FR
 // ------------------------------------------------------------------------------------------
 // Collision kernel.  Runs before the streaming kernel on the cells of class kClsDirect and
 // kClsStaged (work list built by k_offsets_flux):
-//   direct: the candidate pairs depend only on counters, so all of them (at most 32) are drawn at
-//           once; the touched particles (at most 64) are loaded into a shared-memory table keyed by
-//           list position, collided there in candidate order, and the changed ones written back in
-//           place, into the arrived runs or the far-mover list, where the streaming kernel reads them;
+//   direct: the candidate pairs depend only on counters, so up to 32 of them are drawn at once;
+//           the touched particles (at most 64) are loaded into a shared-memory table keyed by list
+//           position, collided there in candidate order, and the changed ones written back in
+//           place, into the arrived runs or the far-mover list, where the streaming kernel reads
+//           them; cells with more candidates run them in batches on the arrived list in place;
 //   staged: the survivors of the absorption draw (Eq. p) and the re-sampled particles (Eq.
 //           maxsample) are written to the first half of the cell's output block and collided there;
 //           the streaming kernel reads this list instead of the arrived runs.
@@ -742,6 +750,38 @@ __device__ __noinline__ void collide_direct(const EngineDev &E, int g, CollideSh
     }
 }
 
+// The arrived list of a direct cell, read and updated in place.
+template <typename Rec>
+struct ArrivedList {
+    const CellHdr *h;
+    Rec *in;
+    FarItem<Rec> *fs;
+    __device__ __forceinline__ Rec *at(int x) const { return arrived_ptr<Rec>(x, *h, in, fs); }
+};
+
+// Direct cells with more than kMaxDirect candidates, one per warp: the candidates in batches of
+// up to 32 (cut at the first pair that shares a particle with an earlier one of the batch), the
+// records read and written in place in the arrived list, where the streaming kernel reads them.
+template <typename Rec>
+__device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
+{
+    const CellHdr *hp = E.hdr + g;
+    const InstDev &I = E.inst[hp->b];
+    const int nc = hp->nc;
+    const double cm0 = E.cmax[g];
+    double cmax = cm0;
+    int na = 0;
+    collide_list<Rec>(I, static_cast<uint32_t>(hp->i + 1), I.step, ArrivedList<Rec>{hp, in, fs}, hp->n_in, nc, cmax, na, S.ab);
+    if ((threadIdx.x & 31) == 0) {
+        E.ncand[g] = nc;
+        E.nacc[g] = na;
+        if (cmax != cm0) {
+            E.cmax[g] = cmax;
+            E.fmaj[g] = majorant_factor(I, cmax);
+        }
+    }
+}
+
 // Absorption draw u53(w0, w1) < P decided on the first word: with T = floor(P 2^32), w0 < T means
 // u < P and w0 > T means u >= P; only w0 = T needs the 53-bit value.
 __device__ __forceinline__ bool absorbed(uint32_t w0, uint32_t w1, double P, uint32_t T, bool all)
@@ -809,7 +849,7 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
         nc = 0;
     }
     int na = 0;
-    collide_list<Rec>(I, id, step, stage, static_cast<int>(n_tot), nc, cmax, na, S.ab);
+    collide_list<Rec>(I, id, step, StagedList<Rec>{stage}, static_cast<int>(n_tot), nc, cmax, na, S.ab);
     if (lane == 0) {
         E.ncand[g] = static_cast<int32_t>(nc);
         E.nacc[g] = na;
@@ -831,8 +871,9 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *in = static_cast<Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
-    // staged cells (one per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and
-    // four per warp); the next ticket of a list is fetched while the current item runs
+    // staged cells and direct cells with more than 32 candidates (one per warp), then direct cells
+    // with up to 32, 16 and 8 candidates (one, two and four per warp); the next ticket of a list is
+    // fetched while the current item runs
     for (int q = 3; q >= 0; --q) {
         const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
         const int n_items = E.ticket[kListLen + q];
@@ -847,6 +888,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
                 const int g = list[t];
                 const CellHdr h = E.hdr[g];
                 if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
+                else if (h.cls == kClsDirect) collide_big<Rec>(E, g, S, in, fs);
             } else {
                 const int me = t + lane / (32 / per);
                 int g = (me < n_items) ? list[me] : -1;
@@ -1070,7 +1112,7 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
 }
 
 // Groups of 32 records each lane loads before any of them is processed (loads in flight per warp).
-constexpr int kStreamGroups = 2;
+constexpr int kStreamGroups = 3;
 
 template <typename Rec, int kMinBlocks>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
@@ -1354,7 +1396,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                     } else {
                         hd.nc = static_cast<int32_t>(nc);
                         if (nc == 0) hd.cls = kClsStream;
-                        else if (nc <= kMaxDirect && extra == 0) hd.cls = kClsDirect;
+                        else if (extra == 0) hd.cls = kClsDirect;
                         else hd.cls = kClsStaged;
                     }
                 }
@@ -1418,7 +1460,8 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
-    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates, 3 staged cells
+    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates, 3 staged cells and
+                       // direct cells with more candidates
     int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1432,7 +1475,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             listed = (cls == kClsDirect) || (cls == kClsStaged);
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
-                lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : 2);
+                lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
