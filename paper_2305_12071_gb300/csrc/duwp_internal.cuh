@@ -70,8 +70,9 @@ struct FarItem {
 enum CellClass : int32_t {
     kClsSkip = 0,       // unused cell, a reservoir that samples nothing, or a cell in error
     kClsStream = 1,     // P = 0 and no collision candidates: stream the arrived + re-sampled particles
-    kClsDirect = 2,     // P = 0, candidates, nothing re-sampled: collide in place, stream
-    kClsStaged = 3,     // P > 0, or re-sampled particles with candidates
+    kClsDirect = 2,     // P = 0 and candidates: re-sample after the arrived positions, collide in
+                        // place, stream
+    kClsStaged = 3,     // P > 0: absorption, compaction and re-sampling into the output block
     kClsReservoir = 4   // inflow/outflow reservoir: stream the particles sampled at its state
 };
 constexpr int kMaxDirect = 32;

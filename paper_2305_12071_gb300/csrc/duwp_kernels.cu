@@ -605,7 +605,8 @@ __device__ __forceinline__ Rec *arrived_ptr(int x, const CellHdr &h, Rec *in, FR
 //           the touched particles (at most 64) are loaded into a shared-memory table keyed by list
 //           position, collided there in candidate order, and the changed ones written back in
 //           place, into the arrived runs or the far-mover list, where the streaming kernel reads
-//           them; cells with more candidates run them in batches on the arrived list in place;
+//           them; cells with more candidates or with re-sampled particles (drawn first, after the
+//           arrived positions) run the candidates in batches on that list in place;
 //   staged: the survivors of the absorption draw (Eq. p) and the re-sampled particles (Eq.
 //           maxsample) are written to the first half of the cell's output block and collided there;
 //           the streaming kernel reads this list instead of the arrived runs.
@@ -750,29 +751,47 @@ __device__ __noinline__ void collide_direct(const EngineDev &E, int g, CollideSh
     }
 }
 
-// The arrived list of a direct cell, read and updated in place.
+// The list of a direct cell, read and updated in place: the arrived positions, then the re-sampled
+// particles after them in the cell's output block.
 template <typename Rec>
 struct ArrivedList {
     const CellHdr *h;
     Rec *in;
     FarItem<Rec> *fs;
-    __device__ __forceinline__ Rec *at(int x) const { return arrived_ptr<Rec>(x, *h, in, fs); }
+    Rec *blk;
+    __device__ __forceinline__ Rec *at(int x) const { return x < h->n_in ? arrived_ptr<Rec>(x, *h, in, fs) : blk + x; }
 };
 
-// Direct cells with more than kMaxDirect candidates, one per warp: the candidates in batches of
-// up to 32 (cut at the first pair that shares a particle with an earlier one of the batch), the
-// records read and written in place in the arrived list, where the streaming kernel reads them.
+// Direct cells with more than kMaxDirect candidates or with re-sampled particles, one per warp: the
+// re-sampled particles first (sampling precedes the collisions), written after the arrived positions
+// in the output block; then the candidates in batches of up to 32 (cut at the first pair that shares
+// a particle with an earlier one of the batch), the records read and written in place, where the
+// streaming kernel reads them.
 template <typename Rec>
-__device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
+__device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShared<Rec> &S, Rec *in, Rec *out,
+                                         FarItem<Rec> *fs)
 {
+    const int lane = threadIdx.x & 31;
     const CellHdr *hp = E.hdr + g;
     const InstDev &I = E.inst[hp->b];
-    const int nc = hp->nc;
+    const int nc = hp->nc, n_in = hp->n_in, nn = hp->n_new, i = hp->i;
+    const uint32_t id = static_cast<uint32_t>(i + 1), step = I.step;
+    Rec *blk = out + hp->off;
+    if (nn > 0) {
+        if (I.resample_mode == 1) {
+            sample_run_ce<Rec>(I, E.prim, E.valid, g, i, step, blk + n_in, 0, nn, lane);
+        } else {
+            const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+            for (int j = lane; j < nn; j += 32)
+                st_rec(blk + n_in + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc, nullptr));
+        }
+        __syncwarp();
+    }
     const double cm0 = E.cmax[g];
     double cmax = cm0;
     int na = 0;
-    collide_list<Rec>(I, static_cast<uint32_t>(hp->i + 1), I.step, ArrivedList<Rec>{hp, in, fs}, hp->n_in, nc, cmax, na, S.ab);
-    if ((threadIdx.x & 31) == 0) {
+    collide_list<Rec>(I, id, step, ArrivedList<Rec>{hp, in, fs, blk}, n_in + nn, nc, cmax, na, S.ab);
+    if (lane == 0) {
         E.ncand[g] = nc;
         E.nacc[g] = na;
         if (cmax != cm0) {
@@ -871,9 +890,9 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *in = static_cast<Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
-    // staged cells and direct cells with more than 32 candidates (one per warp), then direct cells
-    // with up to 32, 16 and 8 candidates (one, two and four per warp); the next ticket of a list is
-    // fetched while the current item runs
+    // staged cells and direct cells with more than 32 candidates or with re-sampled particles (one
+    // per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and four per warp);
+    // the next ticket of a list is fetched while the current item runs
     for (int q = 3; q >= 0; --q) {
         const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
         const int n_items = E.ticket[kListLen + q];
@@ -888,7 +907,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
                 const int g = list[t];
                 const CellHdr h = E.hdr[g];
                 if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
-                else if (h.cls == kClsDirect) collide_big<Rec>(E, g, S, in, fs);
+                else if (h.cls == kClsDirect) collide_big<Rec>(E, g, S, in, out, fs);
             } else {
                 const int me = t + lane / (32 / per);
                 int g = (me < n_items) ? list[me] : -1;
@@ -1395,9 +1414,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                         hd.cls = kClsSkip;
                     } else {
                         hd.nc = static_cast<int32_t>(nc);
-                        if (nc == 0) hd.cls = kClsStream;
-                        else if (extra == 0) hd.cls = kClsDirect;
-                        else hd.cls = kClsStaged;
+                        hd.cls = (nc == 0) ? kClsStream : kClsDirect;
                     }
                 }
             }
@@ -1460,8 +1477,8 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
-    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates, 3 staged cells and
-                       // direct cells with more candidates
+    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
+                       // re-sampled, 3 the other direct cells and the staged cells
     int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1475,7 +1492,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             listed = (cls == kClsDirect) || (cls == kClsStaged);
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
-                lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
+                if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
