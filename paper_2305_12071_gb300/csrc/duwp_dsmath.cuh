@@ -109,6 +109,21 @@ __host__ __device__ __forceinline__ bool ds_rounds_to_hi(ds v, float err)
     return (l + e < up) && (l - e > -dn);
 }
 
+// Double-single value of an integer |n| < 2^53 (pieces of at most 24 bits, summed; relative error below
+// 2^-47).
+__host__ __device__ __forceinline__ ds ds_int53(int64_t n)
+{
+    const uint64_t a = static_cast<uint64_t>(n < 0 ? -n : n);
+    const float s = (n < 0) ? -1.0f : 1.0f;
+    const float p2 = s * static_cast<float>(static_cast<uint32_t>(a >> 48)) * 0x1p48f;
+    const float p1 = s * static_cast<float>(static_cast<uint32_t>((a >> 24) & 0xffffffu)) * 0x1p24f;
+    const float p0 = s * static_cast<float>(static_cast<uint32_t>(a & 0xffffffu));
+    return ds_add(ds_two_sum(p2, p1), {p0, 0.0f});
+}
+
+// x 2^k for a power of two f = 2^k (exact).
+__host__ __device__ __forceinline__ ds ds_scale(ds x, float f) { return {x.hi * f, x.lo * f}; }
+
 // Turn table: cos and sin of 2 pi k / 64, k = 0..63, as double-single pairs (cos hi, cos lo,
 // sin hi, sin lo).
 constexpr int kTurnTable = 64;
@@ -144,25 +159,29 @@ __host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2
 // scattering, Appendix A): the relative velocity keeps its magnitude c_r and takes the direction
 // with cos(theta) = 2 u1 - 1, phi = 2 pi u2, where u1 = u53(v0, v1) and u2 = u53(v2, v3) (53-bit
 // uniforms u53(a, b) = a 2^-32 + (b >> 11) 2^-53).  out = (u, v, w) of A then of B, each the
-// single-precision rounding of the exact value.  Returns false (out unusable) when that cannot be
-// guaranteed: when a computed value lies within 2^-40 (c_r + |(a+b)/2|) of a rounding boundary --
-// the double-single error is below 2^-43 of that and a double-precision evaluation of the same
-// formula deviates by less than 2^-42 -- or when sin(theta) < 2^-10, where the double-precision
-// form sqrt(1 - cos^2) itself loses accuracy.  The caller then evaluates in double precision.
+// single-precision rounding of the double-precision evaluation of the same formula.  Returns false
+// (out unusable) when that cannot be guaranteed: when a computed value lies within
+// 2^-44 (c_r + |m|) + 2^-51 c_r / sin(theta) of a rounding boundary (m = (a+b)/2) -- the double-single
+// error is below 2^-45.5 (c_r + |m|) (1 - cos and 1 + cos are formed exactly), and the
+// double-precision formula deviates from the exact value by less than 2^-52 |m| + c_r (2^-49 +
+// 2^-52 / sin(theta)), the last term from its sqrt(1 - cos^2) near the poles -- or when
+// sin(theta) < 2^-10.  The caller then evaluates in double precision.
 __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au, float av, float aw, float bu,
                                                     float bv, float bw, uint32_t v0, uint32_t v1, uint32_t v2,
-                                                    uint32_t v3, float out[6])
+                                                    uint32_t v3, float out[6], ds *unrounded = nullptr)
 {
     // relative speed c_r of the pair (the differences of two floats are exact pairs)
     const ds du = ds_two_sum(au, -bu), dv = ds_two_sum(av, -bv), dw = ds_two_sum(aw, -bw);
     const ds cr = ds_sqrt(ds_add(ds_add(ds_mul(du, du), ds_mul(dv, dv)), ds_mul(dw, dw)));
-    // cos(theta) = 2 u1 - 1 = (v0 - 2^31) 2^-31 + (v1 >> 11) 2^-52, split exactly into two floats
-    const int32_t c_int = static_cast<int32_t>(v0 - 0x80000000u);
-    const int32_t c_hi = c_int & ~0xff;
-    const uint32_t c_lo = (static_cast<uint32_t>(c_int & 0xff) << 21) | (v1 >> 11);
-    const ds ct = ds_two_sum(static_cast<float>(c_hi) * 0x1p-31f, static_cast<float>(c_lo) * 0x1p-52f);
+    // cos(theta) = 2 u1 - 1 = n 2^-52 with the integer n = m - 2^52, m = (v0 << 21) | (v1 >> 11); the
+    // factors 1 - cos(theta) = (2^52 - n) 2^-52 and 1 + cos(theta) = (2^52 + n) 2^-52 are formed exactly
+    // as integers, so sin(theta) carries no error amplified by 1 / sin(theta) near the poles
+    const uint64_t m53 = (static_cast<uint64_t>(v0) << 21) | static_cast<uint64_t>(v1 >> 11);
+    const int64_t n = static_cast<int64_t>(m53) - (1ll << 52);
+    const ds ct = ds_scale(ds_int53(n), 0x1p-52f);
+    const ds omc = ds_int53((1ll << 52) - n), opc = ds_int53((1ll << 52) + n);
     // sin(theta) = sqrt((1 - ct)(1 + ct))
-    const ds st = ds_sqrt(ds_mul(ds_add({1.0f, 0.0f}, ds_neg(ct)), ds_add({1.0f, 0.0f}, ct)));
+    const ds st = ds_scale(ds_sqrt(ds_mul(omc, opc)), 0x1p-52f);
     if (!(st.hi >= 0x1p-10f)) return false;
     // phi = 2 pi u2
     ds cp, sp;
@@ -178,10 +197,14 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
         const ds half_m = {0.5f * m.hi, 0.5f * m.lo};
         const ds half_c = {0.5f * c[k].hi, 0.5f * c[k].lo};
         const ds pa = ds_add(half_m, half_c), pb = ds_add(half_m, ds_neg(half_c));
-        const float err = 0x1p-40f * (cr.hi + fabsf(half_m.hi));
+        const float err = 0x1p-44f * (cr.hi + fabsf(half_m.hi)) + cr.hi * (0x1p-51f / st.hi);
         ok = ok && ds_rounds_to_hi(pa, err) && ds_rounds_to_hi(pb, err);
         out[k] = pa.hi;
         out[3 + k] = pb.hi;
+        if (unrounded) {
+            unrounded[k] = pa;
+            unrounded[3 + k] = pb;
+        }
     }
     return ok;
 }
@@ -260,10 +283,11 @@ __host__ __device__ __forceinline__ ds ds_neg_log1m(uint32_t a, uint32_t b)
 // xi_d = U_d + (s cos(2 pi r1)) sqrt(-log(1 - r2)), d = 0, 1, 2, with s = sqrt(2 R T), U and s as
 // double-single values, (r1, r2) the 53-bit uniforms of words w[4d+2..4d+5] (w = the 14 words after
 // the position's two).  out = the single-precision roundings; returns false when one of them cannot
-// be guaranteed (a value within 2^-40 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary), then the
-// caller evaluates in double precision.
+// be guaranteed (a value within 2^-43 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary: the
+// double-single error is below 2^-44 of that, the double-precision formula's deviation below
+// 2^-50), then the caller evaluates in double precision.
 __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const ds U[3], ds s, const uint32_t *w,
-                                                   float out[3])
+                                                   float out[3], ds *unrounded = nullptr)
 {
     bool ok = true;
 #pragma unroll
@@ -274,9 +298,10 @@ __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const ds
         const ds rl = ds_sqrt(L);
         const ds mag = ds_mul(s, rl);
         const ds xi = ds_add(U[k], ds_mul(mag, cp));
-        const float err = 0x1p-40f * (fabsf(U[k].hi) + mag.hi);
+        const float err = 0x1p-43f * (fabsf(U[k].hi) + mag.hi);
         ok = ok && ds_rounds_to_hi(xi, err);
         out[k] = xi.hi;
+        if (unrounded) unrounded[k] = xi;
     }
     return ok;
 }

@@ -33,6 +33,7 @@ int main(int argc, char **argv)
     const long n = argc > 1 ? atol(argv[1]) : 100000;
     long nfail = 0, nbad = 0;
     double max_rel = 0.0;
+    long double max_ds = 0.0L, max_fp = 0.0L;
     for (long t = 0; t < n; ++t) {
         const double R = 1.0, T = 0.05 + 8.0 * ud(rng);
         const double Uc[3] = {(ud(rng) - 0.5) * 20.0, (t % 3 == 0) ? 0.0 : ud(rng) - 0.5, 0.0};
@@ -61,7 +62,25 @@ int main(int argc, char **argv)
         const float sh = static_cast<float>(sq);
         const ds s = {sh, static_cast<float>(sq - sh)};
         float out[3];
-        if (!ds_maxwell(turn, U, s, w, out)) {
+        ds un[3];
+        const bool ok = ds_maxwell(turn, U, s, w, out, un);
+        for (int k = 0; k < 3; ++k) {
+            // errors against a long-double evaluation with the same double inputs: of the
+            // double-single value (relative to |U| + s sqrt(L)), and of the double-precision formula
+            const long double r1 = u53_host(w[4 * k], w[4 * k + 1]);
+            const long double L = -log1pl(-(long double)u53_host(w[4 * k + 2], w[4 * k + 3]));
+            const long double ex = (long double)Uc[k] + (long double)sq * cosl(6.283185307179586476925286766559L * r1) * sqrtl(L);
+            const long double S = fabsl((long double)Uc[k]) + (long double)sq * sqrtl(L);
+            if (S > 0) {
+                const long double e = fabsl((long double)un[k].hi + un[k].lo - ex) / S;
+                if (e > max_ds) max_ds = e;
+                const double r2 = 1.0 - u53_host(w[4 * k + 2], w[4 * k + 3]);
+                const double xi = Uc[k] + (sq * cos(6.283185307179586 * (double)r1)) * sqrt(-log(r2));
+                const long double f = fabsl((long double)xi - ex) / S;
+                if (f > max_fp) max_fp = f;
+            }
+        }
+        if (!ok) {
             ++nfail;
             continue;
         }
@@ -75,6 +94,7 @@ int main(int argc, char **argv)
             }
         }
     }
+    printf("ds-error/(|U|+s sqrt(L)) max 2^%.2f; fp64-error/(|U|+s sqrt(L)) max 2^%.2f\n", (double)log2l(max_ds), (double)log2l(max_fp));
     printf("%ld %ld %ld %.3e\n", n, nfail, nbad, max_rel);
     return nbad ? 1 : 0;
 }

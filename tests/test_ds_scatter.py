@@ -27,8 +27,14 @@ def test_ds_scatter_matches_double_precision(tmp_path):
     r = subprocess.run([exe, "400000"], capture_output=True, text=True)
     n, nfail, nfail_generic, nbad = map(int, r.stdout.split()[-4:])
     assert r.returncode == 0 and nbad == 0, r.stdout
-    assert nfail_generic < 0.01 * n, r.stdout
+    assert nfail_generic < 0.002 * n, r.stdout
     assert nfail >= n // 17 - 1, r.stdout       # the near-pole cases always take the fallback
+    # the error bounds the rounding window rests on: double-single error below 2^-45.5 (c_r + |m|),
+    # double-precision deviation within its stated bound
+    line = [x for x in r.stdout.splitlines() if x.startswith("ds-error")][0]
+    ds_exp = float(line.split("max 2^")[1].split(";")[0])
+    fp_ratio = float(line.split("bound max ")[1])
+    assert ds_exp < -45.5 and fp_ratio < 1.0, line
 
 
 def test_ds_maxwell_matches_double_precision(tmp_path):
@@ -41,5 +47,9 @@ def test_ds_maxwell_matches_double_precision(tmp_path):
     r = subprocess.run([exe, "300000"], capture_output=True, text=True)
     n, nfail, nbad, log_rel = r.stdout.split()[-4:]
     assert r.returncode == 0 and int(nbad) == 0, r.stdout
-    assert int(nfail) < 0.005 * int(n), r.stdout
+    assert int(nfail) < 0.001 * int(n), r.stdout
+    line = [x for x in r.stdout.splitlines() if x.startswith("ds-error")][0]
+    ds_exp = float(line.split("max 2^")[1].split(";")[0])
+    fp_exp = float(line.split("max 2^")[2])
+    assert ds_exp < -44.0 and fp_exp < -48.0, line
     assert float(log_rel) < 2.0 ** -44, r.stdout      # -log(1 - u) against long double
