@@ -567,6 +567,12 @@ __device__ __forceinline__ long long fx_energy(double u, double v, double w)
     return __double2ll_rn((u * u + v * v + w * w) * 2147483648.0);
 }
 
+// Prefetch of the 128-byte line holding p into L2 (a hint: no register, no fault on any address).
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
+
 // Plain (coherent) loads for records written earlier in the same kernel.
 __device__ __forceinline__ RecF ld_rec_rw(const RecF *p)
 {
@@ -1199,6 +1205,15 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
         const int n = SS.piece[q].n, k0 = SS.piece[q].k0, dir = SS.piece[q].dir, kind = SS.piece[q].kind;
         for (int base = 0; base < n; base += 32 * kStreamGroups) {
             Rec v[kStreamGroups];
+            if (kind == 0) {
+                // the records of the next iteration into L2 now: memory requests in flight without
+                // holding registers (the kernel is bound by requests in flight per SM)
+#pragma unroll
+                for (int u2 = 0; u2 < kStreamGroups; ++u2) {
+                    const int rp = base + 32 * kStreamGroups + 32 * u2 + lane;
+                    if (rp < n) prefetch_l2(static_cast<const Rec *>(p) + dir * rp);
+                }
+            }
 #pragma unroll
             for (int u2 = 0; u2 < kStreamGroups; ++u2) {
                 const int r = base + 32 * u2 + lane;
