@@ -131,8 +131,10 @@ constexpr int kTurnTable = 64;
 // cos and sin of phi = 2 pi u for the 53-bit uniform u = v2 2^-32 + (v3 >> 11) 2^-53: phi = 2 pi (K/64
 // + r) with K = round(64 u), |r| <= 1/128 taken exactly from the bits; cos and sin of 2 pi r from
 // their Taylor series (the omitted terms are below 2^-49 for |2 pi r| <= pi/64) combined with the
-// turn table by the angle-addition formulas.  Absolute error below 2^-45.
-__host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2, uint32_t v3, ds &cp, ds &sp)
+// turn table by the angle-addition formulas.  Absolute error below 2^-45.  ds_turn_parts gives the
+// table entry (C, S) = (cos, sin)(2 pi K/64) and (cx, sx) = (cos, sin)(2 pi r).
+__host__ __device__ __forceinline__ void ds_turn_parts(const float4 *turn, uint32_t v2, uint32_t v3, ds &C, ds &S,
+                                                       ds &cx, ds &sx)
 {
     constexpr ds kTwoPiDs = ds_const(6.283185307179586476925286766559);
     constexpr ds kMinusSixth = ds_const(-1.0 / 6.0);
@@ -146,13 +148,28 @@ __host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2
     const ds x2 = ds_mul(x, x);
     // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040), cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
     const float ts = x2.hi * (1.0f / 120.0f - x2.hi * (1.0f / 5040.0f));
-    const ds sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
+    sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
     const float tc = x2.hi * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
-    const ds cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
+    cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
     const float4 T = turn[K & (kTurnTable - 1)];
-    const ds C = {T.x, T.y}, S = {T.z, T.w};
+    C = {T.x, T.y};
+    S = {T.z, T.w};
+}
+
+__host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2, uint32_t v3, ds &cp, ds &sp)
+{
+    ds C, S, cx, sx;
+    ds_turn_parts(turn, v2, v3, C, S, cx, sx);
     cp = ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
     sp = ds_add(ds_mul(S, cx), ds_mul(C, sx));
+}
+
+// cos(2 pi u) alone (same evaluation as ds_turn's cp).
+__host__ __device__ __forceinline__ ds ds_turn_cos(const float4 *turn, uint32_t v2, uint32_t v3)
+{
+    ds C, S, cx, sx;
+    ds_turn_parts(turn, v2, v3, C, S, cx, sx);
+    return ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
 }
 
 // Post-collision velocities of an accepted pair of single-precision records (isotropic VHS
@@ -209,74 +226,49 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
     return ok;
 }
 
-// Exact double-single value of a 53-bit integer m = (a << 21) | (b >> 11) scaled by 2^-53 (three
-// exact 24-bit pieces summed; relative error below 2^-47).
-__host__ __device__ __forceinline__ ds ds_u53(uint32_t a, uint32_t b)
-{
-    const uint32_t m0 = ((a & 7u) << 21) | (b >> 11), m1 = (a >> 3) & 0xffffffu, m2 = a >> 27;
-    return ds_add(ds_two_sum(static_cast<float>(m2) * 0x1p-5f, static_cast<float>(m1) * 0x1p-29f),
-                  {static_cast<float>(m0) * 0x1p-53f, 0.0f});
-}
+// Log table: nodes F_j = 1 + (j - kLogCenter)/256, j = 0..kLogTable-1 (covering [sqrt(1/2), 1.416]),
+// entries (1/F_j hi, lo, log F_j hi, lo); entry kLogCenter is (1, 0, 0, 0).
+constexpr int kLogTable = 192;
+constexpr int kLogCenter = 75;
 
-// a / b for b > 0: one correction of the single-precision quotient; relative error below 2^-46.
-__host__ __device__ __forceinline__ ds ds_div(ds a, ds b)
-{
-    const float q0 = a.hi / b.hi;
-    const ds p = ds_mul({q0, 0.0f}, b);
-    const ds r = ds_add(a, ds_neg(p));
-    const float q1 = r.hi / b.hi;
-    return ds_fast_two_sum(q0, q1);
-}
-
-// atanh(t) = t (1 + t^2/3 + t^4/5 + ...) for |t| <= 0.18: the terms through t^10/11 in double-single,
-// the rest (below 3e-9 of the sum) in single precision, truncated after t^22/23; relative error below
-// 2^-45.
-__host__ __device__ __forceinline__ ds ds_atanh_small(ds t)
-{
-    const ds y = ds_mul(t, t);
-    const float yf = y.hi;
-    const float tail = 1.0f / 13.0f + yf * (1.0f / 15.0f + yf * (1.0f / 17.0f + yf * (1.0f / 19.0f + yf * (1.0f / 21.0f + yf * (1.0f / 23.0f)))));
-    ds p = ds_add(ds_const(1.0 / 11.0), {yf * tail, 0.0f});
-    p = ds_add(ds_const(1.0 / 9.0), ds_mul(y, p));
-    p = ds_add(ds_const(1.0 / 7.0), ds_mul(y, p));
-    p = ds_add(ds_const(1.0 / 5.0), ds_mul(y, p));
-    p = ds_add(ds_const(1.0 / 3.0), ds_mul(y, p));
-    p = ds_add({1.0f, 0.0f}, ds_mul(y, p));
-    return ds_mul(t, p);
-}
-
-// -log(1 - u) for the 53-bit uniform u = u53(a, b) in [0, 1); relative error below 2^-44.
-// u < 1/4: 2 atanh(u / (2 - u)) (exact u, no cancellation for small u; the argument is below 1/7);
-// u >= 1/4: with r = 1 - u = n 2^-53 (n exact), r = 2^e f, f in [sqrt(1/2), sqrt(2)):
-// (53 - e) ln 2 - 2 atanh((f - 1)/(f + 1)).
-__host__ __device__ __forceinline__ ds ds_neg_log1m(uint32_t a, uint32_t b)
+// -log(1 - u) for the 53-bit uniform u = u53(a, b) in [0, 1), relative error below 2^-46.
+// 1 - u = n 2^-53 with the integer n = 2^53 - m, m = (a << 21) | (b >> 11); n = 2^e f with f in
+// [0.708, 1.416), F the nearest table node (f - F formed exactly from the integers, |f - F| <= 2^-9),
+// d = (f - F)/F, |d| < 2^-8.5, and
+//   -log(1 - u) = (53 - e) ln 2 - log F - log(1 + d),  log(1 + d) = d - d^2/2 + d^3/3 + d^3 q(d),
+// the last term (below 2^-25 |d|) in single precision.  For u near 0 the node is F = 1 and d = -u
+// exactly, so small results keep their relative accuracy.
+__host__ __device__ __forceinline__ ds ds_neg_log1m(const float4 *logt, uint32_t a, uint32_t b)
 {
     constexpr ds kLn2 = ds_const(0.69314718055994530941723212145818);
-    if (a < 0x40000000u) {                                  // u < 1/4
-        const ds u = ds_u53(a, b);
-        const ds t = ds_div(u, ds_add({2.0f, 0.0f}, ds_neg(u)));
-        const ds at = ds_atanh_small(t);
-        return {2.0f * at.hi, 2.0f * at.lo};
-    }
-    // n = 2^53 - m, m = (a << 21) | (b >> 11), 1 <= n <= 3 2^51
+    constexpr ds kThird = ds_const(1.0 / 3.0);
     const uint64_t m = (static_cast<uint64_t>(a) << 21) | static_cast<uint64_t>(b >> 11);
-    const uint64_t n = (1ull << 53) - m;
+    const uint64_t n = (1ull << 53) - m;                   // 1 <= n <= 2^53
 #ifdef __CUDA_ARCH__
-    int e = 63 - __clzll(static_cast<long long>(n));        // n = 2^e f, f in [1, 2)
+    int e = 63 - __clzll(static_cast<long long>(n));        // n = 2^e f0, f0 in [1, 2)
 #else
     int e = 63 - __builtin_clzll(n);
 #endif
-    // f as an exact double-single (n has at most 53 bits: pieces of 24 and 29 bits)
-    const uint64_t top = n >> (e >= 24 ? e - 23 : 0);       // 24 leading bits
-    const uint64_t rest = (e >= 24) ? (n & ((1ull << (e - 23)) - 1ull)) : 0ull;
-    const float fh = static_cast<float>(static_cast<uint32_t>(top)) * ((e >= 23) ? 0x1p-23f : 1.0f / static_cast<float>(1u << e));
-    const float fl = (e >= 24) ? static_cast<float>(rest) * ldexpf(1.0f, -e) : 0.0f;
-    ds f = ds_two_sum(fh, fl);
-    if (f.hi > 1.41421356f) { f = {0.5f * f.hi, 0.5f * f.lo}; ++e; }
-    const ds t = ds_div(ds_add(f, {-1.0f, 0.0f}), ds_add(f, {1.0f, 0.0f}));
-    const ds at = ds_atanh_small(t);
-    const ds l2 = ds_mul(kLn2, {static_cast<float>(53 - e), 0.0f});
-    return ds_add(l2, {-2.0f * at.hi, -2.0f * at.lo});
+    const uint64_t r9 = (e >= 9) ? (n >> (e - 9)) : (n << (9 - e));    // floor(f0 512), in [512, 1023]
+    int k = static_cast<int>((r9 + 1) >> 1) - 256;          // round((f0 - 1) 256), in [0, 256]
+    if (k > 106) {                                          // f = f0 / 2
+        e += 1;
+        k = static_cast<int>(((r9 >> 1) + 1) >> 1) - 256;   // round((f - 1) 256), in [-75, 0]
+    }
+    // f - F = D 2^-e (e >= 8) or D 2^-8, F = (256 + k) 2^-8; |D| < 2^45
+    const int64_t Fn = 256 + k;
+    const int64_t D = (e >= 8) ? static_cast<int64_t>(n) - (Fn << (e - 8)) : (static_cast<int64_t>(n) << (8 - e)) - Fn;
+    const float scale = (e >= 8) ? ldexpf(1.0f, -e) : 0x1p-8f;
+    const float4 T = logt[k + kLogCenter];
+    const ds t = ds_scale(ds_int53(D), scale);
+    const ds d = ds_mul(t, {T.x, T.y});
+    const ds d2 = ds_mul(d, d);
+    const ds d3 = ds_mul(d2, d);
+    const float df = d.hi;
+    const float q = df * (-0.25f + df * (0.2f - df * (1.0f / 6.0f - df * (1.0f / 7.0f))));
+    const ds lp = ds_add(d, ds_add(ds_scale(d2, -0.5f), ds_add(ds_mul(d3, kThird), {d3.hi * q, 0.0f})));
+    const ds lf = ds_add({T.z, T.w}, lp);
+    return ds_add(ds_mul(kLn2, {static_cast<float>(53 - e), 0.0f}), ds_neg(lf));
 }
 
 // Velocity components of a Maxwellian sample (Eq. maxsample) for single-precision records:
@@ -286,15 +278,14 @@ __host__ __device__ __forceinline__ ds ds_neg_log1m(uint32_t a, uint32_t b)
 // be guaranteed (a value within 2^-43 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary: the
 // double-single error is below 2^-44 of that, the double-precision formula's deviation below
 // 2^-50), then the caller evaluates in double precision.
-__host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const ds U[3], ds s, const uint32_t *w,
-                                                   float out[3], ds *unrounded = nullptr)
+__host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const float4 *logt, const ds U[3], ds s,
+                                                   const uint32_t *w, float out[3], ds *unrounded = nullptr)
 {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        ds cp, sp;
-        ds_turn(turn, w[4 * k], w[4 * k + 1], cp, sp);
-        const ds L = ds_neg_log1m(w[4 * k + 2], w[4 * k + 3]);
+        const ds cp = ds_turn_cos(turn, w[4 * k], w[4 * k + 1]);
+        const ds L = ds_neg_log1m(logt, w[4 * k + 2], w[4 * k + 3]);
         const ds rl = ds_sqrt(L);
         const ds mag = ds_mul(s, rl);
         const ds xi = ds_add(U[k], ds_mul(mag, cp));

@@ -19,18 +19,31 @@
 
 namespace duwp {
 
-// cos and sin of 2 pi k / kTurnTable as double-single pairs (scattering of single-precision records)
+// cos and sin of 2 pi k / kTurnTable as double-single pairs (scattering and sampling of
+// single-precision records), and the log table of the sampling (1/F and log F at F = 1 + (j - kLogCenter)/256)
 __device__ float4 g_turn[kTurnTable];
+__device__ float4 g_logt[kLogTable];
+
+__device__ __forceinline__ float2 ds_split(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - static_cast<double>(h)));
+}
 
 __global__ void k_init_turn()
 {
     const int k = threadIdx.x;
-    if (k >= kTurnTable) return;
-    double s, c;
-    sincospi(static_cast<double>(k) / (0.5 * kTurnTable), &s, &c);
-    const float ch = __double2float_rn(c), sh = __double2float_rn(s);
-    g_turn[k] = make_float4(ch, __double2float_rn(c - static_cast<double>(ch)), sh,
-                            __double2float_rn(s - static_cast<double>(sh)));
+    if (k < kTurnTable) {
+        double s, c;
+        sincospi(static_cast<double>(k) / (0.5 * kTurnTable), &s, &c);
+        const float2 cc = ds_split(c), ss = ds_split(s);
+        g_turn[k] = make_float4(cc.x, cc.y, ss.x, ss.y);
+    }
+    if (k < kLogTable) {
+        const double F = static_cast<double>(256 + k - kLogCenter) * 0x1p-8;
+        const float2 inv = ds_split(1.0 / F), lg = ds_split(log(F));
+        g_logt[k] = make_float4(inv.x, inv.y, lg.x, lg.y);
+    }
 }
 
 __device__ __forceinline__ void set_err(int32_t *err, int code) { atomicCAS(err, 0, code); }
@@ -277,7 +290,7 @@ __device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint3
         // single-precision records: double-single evaluation, double precision only where the
         // rounding of a component cannot be guaranteed
         x = u53_float(w[0], w[1]);
-        if (!ds_maxwell(g_turn, mc.U, mc.s, w + 2, xi)) maxwell_fp64<T>(mc, w + 2, xi);
+        if (!ds_maxwell(g_turn, g_logt, mc.U, mc.s, w + 2, xi)) maxwell_fp64<T>(mc, w + 2, xi);
     } else {
         x = u53(w[0], w[1]);
         maxwell_fp64<T>(mc, w + 2, xi);
@@ -1137,7 +1150,7 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
 }
 
 // Groups of 32 records each lane loads before any of them is processed (loads in flight per warp).
-constexpr int kStreamGroups = 3;
+constexpr int kStreamGroups = 2;
 
 template <typename Rec, int kMinBlocks>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
@@ -1212,6 +1225,19 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
                 for (int u2 = 0; u2 < kStreamGroups; ++u2) {
                     const int rp = base + 32 * kStreamGroups + 32 * u2 + lane;
                     if (rp < n) prefetch_l2(static_cast<const Rec *>(p) + dir * rp);
+                }
+            }
+            if (base + 32 * kStreamGroups >= n && q < 5) {
+                // last iteration of this piece: the head of the next non-empty one
+                const int q2 = (q < 4 && SS.piece[q + 1].n == 0) ? q + 2 : q + 1;
+                if (SS.piece[q2].kind == 0) {
+                    const Rec *p2 = static_cast<const Rec *>(SS.piece[q2].p);
+                    const int n2 = SS.piece[q2].n, d2 = SS.piece[q2].dir;
+#pragma unroll
+                    for (int u2 = 0; u2 < kStreamGroups; ++u2) {
+                        const int rp = 32 * u2 + lane;
+                        if (rp < n2) prefetch_l2(p2 + d2 * rp);
+                    }
                 }
             }
 #pragma unroll
@@ -1787,7 +1813,7 @@ cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStr
 
 cudaError_t launch_init_turn(cudaStream_t s)
 {
-    k_init_turn<<<1, kTurnTable, 0, s>>>();
+    k_init_turn<<<1, (kTurnTable > kLogTable ? kTurnTable : kLogTable), 0, s>>>();
     return cudaGetLastError();
 }
 

@@ -28,6 +28,13 @@ int main(int argc, char **argv)
         const float ch = static_cast<float>(c), sh = static_cast<float>(s);
         turn[k] = make_float4(ch, static_cast<float>(c - ch), sh, static_cast<float>(s - sh));
     }
+    float4 logt[kLogTable];
+    for (int k = 0; k < kLogTable; ++k) {
+        const long double F = (long double)(256 + k - kLogCenter) / 256.0L;
+        const long double inv = 1.0L / F, lg = logl(F);
+        const float ih = static_cast<float>(inv), lh = static_cast<float>(lg);
+        logt[k] = make_float4(ih, static_cast<float>(inv - ih), lh, static_cast<float>(lg - lh));
+    }
     std::mt19937_64 rng(2306);
     std::uniform_real_distribution<double> ud(0.0, 1.0);
     const long n = argc > 1 ? atol(argv[1]) : 100000;
@@ -45,7 +52,7 @@ int main(int argc, char **argv)
         // -log(1 - u) against long double
         for (int k = 0; k < 3; ++k) {
             const uint32_t a = w[4 * k + 2], b = w[4 * k + 3];
-            const ds L = ds_neg_log1m(a, b);
+            const ds L = ds_neg_log1m(logt, a, b);
             const long double u = static_cast<long double>(u53_host(a, b));
             const long double ex = -log1pl(-u);
             if (ex > 0) {
@@ -63,7 +70,7 @@ int main(int argc, char **argv)
         const ds s = {sh, static_cast<float>(sq - sh)};
         float out[3];
         ds un[3];
-        const bool ok = ds_maxwell(turn, U, s, w, out, un);
+        const bool ok = ds_maxwell(turn, logt, U, s, w, out, un);
         for (int k = 0; k < 3; ++k) {
             // errors against a long-double evaluation with the same double inputs: of the
             // double-single value (relative to |U| + s sqrt(L)), and of the double-precision formula
