@@ -647,8 +647,8 @@ struct CollideShared {
 template <int NS>
 __device__ __forceinline__ int hash_insert(int *key, int x, int32_t *err)
 {
-    constexpr int kShift = (NS == 32) ? 27 : ((NS == 64) ? 26 : 25);
-    static_assert(NS == 32 || NS == 64 || NS == 128, "table size");
+    static_assert(NS == 8 || NS == 16 || NS == 32 || NS == 64 || NS == 128, "table size");
+    constexpr int kShift = (NS == 8) ? 29 : ((NS == 16) ? 28 : ((NS == 32) ? 27 : ((NS == 64) ? 26 : 25)));
     uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> kShift;
     for (int it = 0; it < NS; ++it) {
         const int old = atomicCAS(&key[h], -1, x);
@@ -910,10 +910,10 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
     // staged cells and direct cells with more than 32 candidates or with re-sampled particles (one
-    // per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and four per warp);
-    // the next ticket of a list is fetched while the current item runs
-    for (int q = 3; q >= 0; --q) {
-        const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
+    // per warp), then direct cells with up to 32, 16, 8, 4 and 2 candidates (1, 2, 4, 8 and 16 per
+    // warp); the next ticket of a list is fetched while the current item runs
+    for (int q = kNumLists - 1; q >= 0; --q) {
+        const int per = (q == kNumLists - 1) ? 1 : (16 >> q);
         const int n_items = E.ticket[kListLen + q];
         const int32_t *list = E.wl + static_cast<size_t>(q) * E.G;
         int t = 0;
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
         while (t < n_items) {
             int tn = 0;
             if (lane == 0) tn = atomicAdd(&E.ticket[q], per);
-            if (q == 3) {
+            if (q == kNumLists - 1) {
                 const int g = list[t];
                 const CellHdr h = E.hdr[g];
                 if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
@@ -931,9 +931,11 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
                 const int me = t + lane / (32 / per);
                 int g = (me < n_items) ? list[me] : -1;
                 if (g >= 0 && E.hdr[g].cls != kClsDirect) g = -1;
-                if (q == 2) collide_direct<Rec, 32>(E, g, S, in, fs);
-                else if (q == 1) collide_direct<Rec, 16>(E, g, S, in, fs);
-                else collide_direct<Rec, 8>(E, g, S, in, fs);
+                if (q == 4) collide_direct<Rec, 32>(E, g, S, in, fs);
+                else if (q == 3) collide_direct<Rec, 16>(E, g, S, in, fs);
+                else if (q == 2) collide_direct<Rec, 8>(E, g, S, in, fs);
+                else if (q == 1) collide_direct<Rec, 4>(E, g, S, in, fs);
+                else collide_direct<Rec, 2>(E, g, S, in, fs);
             }
             __syncwarp();
             t = __shfl_sync(0xffffffffu, tn, 0);
@@ -1110,17 +1112,36 @@ __device__ __forceinline__ int move_near(double dtdx, int C, int ci, double &xl,
     return static_cast<int>(dd);
 }
 
-// Fixed-point sums (u, v, w, |xi|^2/2) of n contiguous records, each lane a strided share.
+// Moment sums of the L run (pL, nL) and the R run (pR, nR) of a block, read back together: the runs
+// are taken as one list, two records per lane in flight per iteration.
 template <typename Rec>
-__device__ __forceinline__ void run_sums(const Rec *p, int n, long long s[4], bool &ok)
+__device__ __forceinline__ void run_sums_lr(const Rec *pL, int nL, const Rec *pR, int nR, long long sL[4],
+                                            long long sR[4], bool &ok)
 {
-    for (int j = threadIdx.x & 31; j < n; j += 32) {
-        const Rec v = ld_rec_rw(p + j);
-        ok = ok && fx_in_range(v.u) && fx_in_range(v.v) && fx_in_range(v.w);
-        s[0] += fx_vel(v.u);
-        s[1] += fx_vel(v.v);
-        s[2] += fx_vel(v.w);
-        s[3] += fx_energy(v.u, v.v, v.w);
+    const int n = nL + nR;
+    for (int j = threadIdx.x & 31; j < n; j += 64) {
+        const int j2 = j + 32;
+        const Rec a = ld_rec_rw(j < nL ? pL + j : pR + (j - nL));
+        Rec b = a;
+        if (j2 < n) b = ld_rec_rw(j2 < nL ? pL + j2 : pR + (j2 - nL));
+        const long long fa[4] = {fx_vel(a.u), fx_vel(a.v), fx_vel(a.w), fx_energy(a.u, a.v, a.w)};
+        ok = ok && fx_in_range(a.u) && fx_in_range(a.v) && fx_in_range(a.w);
+        const bool aL = j < nL;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sL[k] += aL ? fa[k] : 0;
+            sR[k] += aL ? 0 : fa[k];
+        }
+        if (j2 < n) {
+            const long long fb[4] = {fx_vel(b.u), fx_vel(b.v), fx_vel(b.w), fx_energy(b.u, b.v, b.w)};
+            ok = ok && fx_in_range(b.u) && fx_in_range(b.v) && fx_in_range(b.w);
+            const bool bL = j2 < nL;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                sL[k] += bL ? fb[k] : 0;
+                sR[k] += bL ? 0 : fb[k];
+            }
+        }
     }
 }
 
@@ -1277,8 +1298,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
     const int nRr = 2 * slots - 1 - st.oR;
     long long sL[4] = {0, 0, 0, 0}, sR[4] = {0, 0, 0, 0};
     bool ok = st.range_ok;
-    run_sums<Rec>(blk + slots, nLr, sL, ok);
-    run_sums<Rec>(blk + st.oR + 1, nRr, sR, ok);
+    run_sums_lr<Rec>(blk + slots, nLr, blk + st.oR + 1, nRr, sL, sR, ok);
     if (!__all_sync(0xffffffffu, ok) && lane == 0) set_err(E.err, kErrOverflow);
     long long lj = 0, rj = 0, gj = 0;
 #pragma unroll
@@ -1344,7 +1364,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     int64_t myslots = 0;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (update) E.far_count[0] = 0;
-        for (int q = 0; q < 4; ++q) E.ticket[kListLen + q] = 0;
+        for (int q = 0; q < kNumLists; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
     }
     if (g < E.G) {
@@ -1518,8 +1538,8 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
-    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
-                       // re-sampled, 3 the other direct cells and the staged cells
+    int lq = kNumLists - 1;   // work list: 0..4 direct cells with up to 2/4/8/16/32 candidates and
+                              // nothing re-sampled, 5 the other direct cells and the staged cells
     int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1533,7 +1553,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             listed = (cls == kClsDirect) || (cls == kClsStaged);
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
-                if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
+                if (E.hdr[g].n_new == 0 && nc <= kMaxDirect) lq = (nc <= 2) ? 0 : ((nc <= 4) ? 1 : ((nc <= 8) ? 2 : ((nc <= 16) ? 3 : 4)));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
@@ -1560,7 +1580,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     }
     // work lists of the collision kernel (one atomic per warp and list)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kNumLists; ++q) {
         const bool mine = listed && lq == q;
         const unsigned lm = __ballot_sync(0xffffffffu, mine);
         if (lm) {
@@ -1571,7 +1591,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         }
     }
     if (g == 0) {
-        for (int q = 0; q < 4; ++q) E.ticket[q] = 0;
+        for (int q = 0; q < kNumLists; ++q) E.ticket[q] = 0;
         E.ticket[kSampleCtr] = 0;
     }
     if (g >= E.G) return;
