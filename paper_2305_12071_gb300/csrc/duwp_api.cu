@@ -283,7 +283,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_err = c.take<int32_t>(4);
     const size_t o_ticket = c.take<int32_t>(kTickets);
     const size_t o_hdr = c.take<CellHdr>(G);
-    const size_t o_wl = c.take<int32_t>(kNumLists * size_t(G));
+    const size_t o_wl = c.take<int32_t>(4 * size_t(G));
     // chunks of re-sampled particles: at most one partial chunk per cell plus the re-sampled
     // particles (at most half the slots of a buffer) in full chunks
     const int64_t wls_cap = int64_t(G) + capacity / (2 * kSampleChunk) + 64;

@@ -135,14 +135,11 @@ struct EngineDev {
     int32_t wls_cap;           // entries of wls
 };
 
-// ticket[q] (q < kNumLists): next item of work list q; ticket[kListLen + q]: its length;
-// ticket[kSampleLen] and ticket[kSampleCtr]: length of and next item of the sample list.
-// Lists 0..4: direct cells with up to 2, 4, 8, 16, 32 candidates and nothing re-sampled (16, 8, 4, 2
-// and 1 cells per warp); list 5: the other direct cells and the staged cells (one per warp).
-constexpr int kNumLists = 6;
-constexpr int kListLen = 6;
-constexpr int kSampleLen = 12;
-constexpr int kSampleCtr = 13;
+// ticket[q] (q < 4): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
+// and ticket[kSampleCtr]: length of and next item of the sample list.
+constexpr int kListLen = 4;
+constexpr int kSampleLen = 8;
+constexpr int kSampleCtr = 9;
 constexpr int kTickets = 16;
 
 // Re-sampled particles of classes 1 and 4 are drawn by the collision kernel in chunks of this many,

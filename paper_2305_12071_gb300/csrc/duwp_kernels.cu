@@ -270,7 +270,7 @@ __device__ __forceinline__ float u53_float(uint32_t a, uint32_t b)
 }
 
 template <typename Rec>
-__device__ __noinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
+__device__ __forceinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
                                            const CeCell *ce)
 {
     uint32_t w[16];
@@ -647,8 +647,8 @@ struct CollideShared {
 template <int NS>
 __device__ __forceinline__ int hash_insert(int *key, int x, int32_t *err)
 {
-    static_assert(NS == 8 || NS == 16 || NS == 32 || NS == 64 || NS == 128, "table size");
-    constexpr int kShift = (NS == 8) ? 29 : ((NS == 16) ? 28 : ((NS == 32) ? 27 : ((NS == 64) ? 26 : 25)));
+    constexpr int kShift = (NS == 32) ? 27 : ((NS == 64) ? 26 : 25);
+    static_assert(NS == 32 || NS == 64 || NS == 128, "table size");
     uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> kShift;
     for (int it = 0; it < NS; ++it) {
         const int old = atomicCAS(&key[h], -1, x);
@@ -910,10 +910,10 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
     // staged cells and direct cells with more than 32 candidates or with re-sampled particles (one
-    // per warp), then direct cells with up to 32, 16, 8, 4 and 2 candidates (1, 2, 4, 8 and 16 per
-    // warp); the next ticket of a list is fetched while the current item runs
-    for (int q = kNumLists - 1; q >= 0; --q) {
-        const int per = (q == kNumLists - 1) ? 1 : (16 >> q);
+    // per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and four per warp);
+    // the next ticket of a list is fetched while the current item runs
+    for (int q = 3; q >= 0; --q) {
+        const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
         const int n_items = E.ticket[kListLen + q];
         const int32_t *list = E.wl + static_cast<size_t>(q) * E.G;
         int t = 0;
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
         while (t < n_items) {
             int tn = 0;
             if (lane == 0) tn = atomicAdd(&E.ticket[q], per);
-            if (q == kNumLists - 1) {
+            if (q == 3) {
                 const int g = list[t];
                 const CellHdr h = E.hdr[g];
                 if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
@@ -931,11 +931,9 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
                 const int me = t + lane / (32 / per);
                 int g = (me < n_items) ? list[me] : -1;
                 if (g >= 0 && E.hdr[g].cls != kClsDirect) g = -1;
-                if (q == 4) collide_direct<Rec, 32>(E, g, S, in, fs);
-                else if (q == 3) collide_direct<Rec, 16>(E, g, S, in, fs);
-                else if (q == 2) collide_direct<Rec, 8>(E, g, S, in, fs);
-                else if (q == 1) collide_direct<Rec, 4>(E, g, S, in, fs);
-                else collide_direct<Rec, 2>(E, g, S, in, fs);
+                if (q == 2) collide_direct<Rec, 32>(E, g, S, in, fs);
+                else if (q == 1) collide_direct<Rec, 16>(E, g, S, in, fs);
+                else collide_direct<Rec, 8>(E, g, S, in, fs);
             }
             __syncwarp();
             t = __shfl_sync(0xffffffffu, tn, 0);
@@ -1364,7 +1362,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     int64_t myslots = 0;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (update) E.far_count[0] = 0;
-        for (int q = 0; q < kNumLists; ++q) E.ticket[kListLen + q] = 0;
+        for (int q = 0; q < 4; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
     }
     if (g < E.G) {
@@ -1538,8 +1536,8 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int64_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
-    int lq = kNumLists - 1;   // work list: 0..4 direct cells with up to 2/4/8/16/32 candidates and
-                              // nothing re-sampled, 5 the other direct cells and the staged cells
+    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
+                       // re-sampled, 3 the other direct cells and the staged cells
     int chunks = 0;
     if (g < E.G) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1553,7 +1551,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             listed = (cls == kClsDirect) || (cls == kClsStaged);
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
-                if (E.hdr[g].n_new == 0 && nc <= kMaxDirect) lq = (nc <= 2) ? 0 : ((nc <= 4) ? 1 : ((nc <= 8) ? 2 : ((nc <= 16) ? 3 : 4)));
+                if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
@@ -1580,7 +1578,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     }
     // work lists of the collision kernel (one atomic per warp and list)
 #pragma unroll
-    for (int q = 0; q < kNumLists; ++q) {
+    for (int q = 0; q < 4; ++q) {
         const bool mine = listed && lq == q;
         const unsigned lm = __ballot_sync(0xffffffffu, mine);
         if (lm) {
@@ -1591,7 +1589,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         }
     }
     if (g == 0) {
-        for (int q = 0; q < kNumLists; ++q) E.ticket[q] = 0;
+        for (int q = 0; q < 4; ++q) E.ticket[q] = 0;
         E.ticket[kSampleCtr] = 0;
     }
     if (g >= E.G) return;
