@@ -258,7 +258,7 @@ __host__ __device__ __forceinline__ ds ds_neg_log1m(const float4 *logt, uint32_t
     // f - F = D 2^-e (e >= 8) or D 2^-8, F = (256 + k) 2^-8; |D| < 2^45
     const int64_t Fn = 256 + k;
     const int64_t D = (e >= 8) ? static_cast<int64_t>(n) - (Fn << (e - 8)) : (static_cast<int64_t>(n) << (8 - e)) - Fn;
-    const float scale = (e >= 8) ? ldexpf(1.0f, -e) : 0x1p-8f;
+    const float scale = bits_f(static_cast<uint32_t>(127 - (e >= 8 ? e : 8)) << 23);   // 2^-max(e, 8), e <= 54
     const float4 T = logt[k + kLogCenter];
     const ds t = ds_scale(ds_int53(D), scale);
     const ds d = ds_mul(t, {T.x, T.y});
