@@ -158,23 +158,26 @@ def profiled_traffic(workload_name: str, updates_per_launch: float):
     return per * updates_per_launch, per
 
 
-def oracle_sample(params_list, sample_idx, steps: int, warm: int = 1):
-    """Time the CPU oracle (single thread) on a sample of the instances."""
+def oracle_sample(params_list, sample_idx, min_steps: int = 2, budget_s: float = 10.0, warm: int = 1):
+    """Time the CPU oracle (single thread) on a sample of the instances: rounds of one step of every
+    sampled instance, at least min_steps rounds and until about budget_s seconds of oracle time.
+    Returns (particle-updates, seconds, rounds)."""
     import oracle as O
     inst = [O.Oracle(params_list[i]) for i in sample_idx]
     for o in inst:
         o.step(warm)
-    updates = 0
+    updates, rounds = 0, 0
     t0 = time.perf_counter()
-    for o in inst:
-        for _ in range(steps):
+    while rounds < min_steps or time.perf_counter() - t0 < budget_s:
+        for o in inst:
             before = o.num_particles()
             o.step(1)
             c = o.counters()
             # particles streamed = arrived - absorbed + re-sampled (interior cells)
             updates += before - int(c["nabs"].sum()) + int(c["nnew"].sum())
+        rounds += 1
     dt = time.perf_counter() - t0
-    return updates, dt
+    return updates, dt, rounds
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -410,8 +413,9 @@ def main():
         n = len(plist)
         if n > 1:
             idx = list(range(0, n, 8))
-            ups, secs = oracle_sample(plist, idx, steps=2)
-            sample = f"instances {idx} of the batch, 1 untimed + 2 timed steps each"
+            ups, secs, rounds = oracle_sample(plist, idx)
+            sample = (f"instances {idx} of the batch, 1 untimed + {rounds} timed steps each "
+                      f"(about 10 s of oracle time)")
         else:
             ups, secs = None, None
             sample = "not run: a single instance too large for a bounded oracle sample"
