@@ -157,8 +157,12 @@ void Engine::drop_graphs()
 Engine::~Engine()
 {
     if (cstream) cudaStreamSynchronize(cstream);
+    if (side) cudaStreamSynchronize(side);
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     for (int k = 0; k < 2; ++k) {
         if (mom_ready[k]) cudaEventDestroy(mom_ready[k]);
         if (copy_done[k]) cudaEventDestroy(copy_done[k]);
@@ -217,6 +221,10 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
         own_stream = true;
     }
     if (!params || n < 0) return DUWP_EINVAL;
+    DUWP_CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    DUWP_CU(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    DUWP_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    DUWP_CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     std::vector<HostInst> hs(static_cast<size_t>(n));
     int64_t est = 0;
     int64_t cells = 0;
@@ -404,11 +412,24 @@ int Engine::enqueue_prepare()
 int Engine::enqueue_step(cudaEvent_t *ev)
 {
     const int rp = parity;
-    if (ev) DUWP_CU(cudaEventRecord(ev[0], stream));
-    DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream));
-    if (ev) DUWP_CU(cudaEventRecord(ev[1], stream));
-    DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream));
-    if (ev) DUWP_CU(cudaEventRecord(ev[2], stream));
+    if (ev) {
+        // timed: one kernel after the other, events around each
+        DUWP_CU(cudaEventRecord(ev[0], stream));
+        DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
+        DUWP_CU(cudaEventRecord(ev[1], stream));
+        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 0, prio_hi));
+        DUWP_CU(cudaEventRecord(ev[2], stream));
+    } else {
+        // the free cells stream on the side stream while the collision kernel runs; the other cells
+        // after it; the side stream joins before the far movers are sorted
+        DUWP_CU(cudaEventRecord(ev_fork, stream));
+        DUWP_CU(cudaStreamWaitEvent(side, ev_fork, 0));
+        DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
+        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, side, 1, prio_lo));
+        DUWP_CU(cudaEventRecord(ev_join, side));
+        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 2, prio_hi));
+        DUWP_CU(cudaStreamWaitEvent(stream, ev_join, 0));
+    }
     DUWP_CU(launch_far_sort(dev, fp32, stream));
     if (ev) DUWP_CU(cudaEventRecord(ev[3], stream));
     DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
@@ -436,7 +457,7 @@ int Engine::step(int32_t n)
                 parity = p0;
                 if (rc != DUWP_OK) return rc;
                 if (e != cudaSuccess) { set_cuda_error(e, "cudaStreamEndCapture"); return DUWP_ECUDA; }
-                e = cudaGraphInstantiate(&gx, gr, 0);
+                e = cudaGraphInstantiate(&gx, gr, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(gr);
                 if (e != cudaSuccess) { set_cuda_error(e, "cudaGraphInstantiate"); gx = nullptr; return DUWP_ECUDA; }
             }

@@ -1171,8 +1171,10 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
 // Groups of 32 records each lane loads before any of them is processed (loads in flight per warp).
 constexpr int kStreamGroups = 2;
 
+// phase: 0 every cell; 1 only the free cells (stream class, nothing re-sampled: they read and write
+// nothing the collision kernel touches, so they may stream while it runs); 2 every other cell.
 template <typename Rec, int kMinBlocks>
-__global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
+__global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp, int phase)
 {
     using T = decltype(Rec().xl);
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -1183,6 +1185,10 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
     const int wp = 1 - rp;
     const CellHdr *hp = E.hdr + g;
     const int cls = hp->cls;
+    if (phase != 0) {
+        const bool free_cell = (cls == kClsStream) && hp->n_new == 0;
+        if (free_cell != (phase == 1)) return;
+    }
     int n_tot = 0;
     if (cls == kClsStaged) n_tot = hp->n_in - E.nabs[g] + E.nnew[g];
     else if (cls != kClsSkip) n_tot = hp->n_in + hp->n_new;
@@ -1781,29 +1787,51 @@ int collide_occupancy(int fp32)
                 : occupancy_of(k_collide<RecD>, kCollideThreads, smem, smem);
 }
 
-cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s)
+namespace {
+// Launch with a scheduling priority (blocks of higher-priority launches are dispatched first).
+template <typename... Args>
+cudaError_t launch_prio(void (*kernel)(Args...), int grid, int threads, size_t smem, cudaStream_t s, int prio,
+                        Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+}  // namespace
+
+cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
 {
     const size_t smem = collide_smem_bytes(fp32);
-    if (fp32) k_collide<RecF><<<grid, kCollideThreads, smem, s>>>(E, rp);
-    else k_collide<RecD><<<grid, kCollideThreads, smem, s>>>(E, rp);
-    return cudaGetLastError();
+    cudaError_t e = fp32 ? launch_prio(k_collide<RecF>, grid, kCollideThreads, smem, s, prio, E, rp)
+                         : launch_prio(k_collide<RecD>, grid, kCollideThreads, smem, s, prio, E, rp);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s)
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s, int phase,
+                          int prio)
 {
     const int wpb = threads / 32;
     const int grid = (E.G + wpb - 1) / wpb;
     const size_t smem = stream_smem_bytes(fp32, threads);
+    cudaError_t e;
     if (fp32) {
-        if (variant == 2) k_stream<RecF, 3><<<grid, threads, smem, s>>>(E, rp);
-        else if (variant == 1) k_stream<RecF, 2><<<grid, threads, smem, s>>>(E, rp);
-        else k_stream<RecF, 1><<<grid, threads, smem, s>>>(E, rp);
+        if (variant == 2) e = launch_prio(k_stream<RecF, 3>, grid, threads, smem, s, prio, E, rp, phase);
+        else if (variant == 1) e = launch_prio(k_stream<RecF, 2>, grid, threads, smem, s, prio, E, rp, phase);
+        else e = launch_prio(k_stream<RecF, 1>, grid, threads, smem, s, prio, E, rp, phase);
     } else {
-        if (variant == 2) k_stream<RecD, 3><<<grid, threads, smem, s>>>(E, rp);
-        else if (variant == 1) k_stream<RecD, 2><<<grid, threads, smem, s>>>(E, rp);
-        else k_stream<RecD, 1><<<grid, threads, smem, s>>>(E, rp);
+        if (variant == 2) e = launch_prio(k_stream<RecD, 3>, grid, threads, smem, s, prio, E, rp, phase);
+        else if (variant == 1) e = launch_prio(k_stream<RecD, 2>, grid, threads, smem, s, prio, E, rp, phase);
+        else e = launch_prio(k_stream<RecD, 1>, grid, threads, smem, s, prio, E, rp, phase);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s)

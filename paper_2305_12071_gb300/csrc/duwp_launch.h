@@ -9,10 +9,14 @@ namespace duwp {
 
 // Collision kernel of one step (cells of the work list): NTC collisions in place, or absorption,
 // re-sampling and collisions into the staged list.  rp = parity of the buffer holding the arrived
-// lists.  grid: persistent CTAs of collide_threads() threads.
-cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s);
-// Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).
-cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s);
+// lists.  grid: persistent CTAs of collide_threads() threads.  prio: scheduling priority of the
+// launch (cudaLaunchAttributePriority; a smaller number is a higher priority).
+cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
+// Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).  phase 0:
+// every cell; 1: only the cells that need nothing from the collision kernel (stream class, nothing
+// re-sampled); 2: the other cells.
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s, int phase,
+                          int prio);
 // Sort of the particles that moved two or more cells.
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
 // Cell kernel: update Psi_t from the step's particle runs and wave flux (update = 1), then the

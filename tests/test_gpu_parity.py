@@ -246,3 +246,21 @@ def test_async_moments_equal_synchronous_reads():
             assert np.array_equal(ref[k], bufs[j][k]), (j, k)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_overlapped_step_equals_serial_step(precision):
+    # duwp_step streams the cells that need nothing from the collision kernel on a side stream while
+    # it runs; duwp_step_timed runs the kernels one after the other: same particles and states
+    plist = [W.shock(m, n_cells=n, ppc_ref=70, precision=precision, seed=40 + k)
+             for k, (m, n) in enumerate(((1.5, 60), (6.0, 150), (3.0, 90)))]
+    a, b = solver(plist), solver(plist)
+    a.step(6)
+    b.step_timed(6)
+    for i in range(len(plist)):
+        pa, pb = a.particles(i), b.particles(i)
+        for k in pa:
+            assert np.array_equal(pa[k], pb[k]), (i, k)
+        assert np.array_equal(a.fields(i)[0], b.fields(i)[0]), i
+    a.close()
+    b.close()
