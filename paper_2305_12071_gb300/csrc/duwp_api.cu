@@ -359,16 +359,29 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     for (auto &h : inst) h.active = false;
     int32_t gb = 0;
     for (int32_t b = 0; b < n; ++b) {
-        rc = add_instance(b, params[b], gb);
+        rc = add_instance(b, params[b], gb, false);
         if (rc != DUWP_OK) return rc;
         gb += params[b].n_cells + 2;
+    }
+    // the instance table in one copy (a copy from pageable memory waits for the stream), then the
+    // cells of every instance
+    if (n > 0) {
+        std::vector<InstDev> table(static_cast<size_t>(n));
+        for (int32_t b = 0; b < n; ++b) table[b] = inst[b].d;
+        DUWP_CU(cudaMemcpyAsync(dev.inst, table.data(), sizeof(InstDev) * static_cast<size_t>(n), cudaMemcpyHostToDevice,
+                                stream));
+        DUWP_CU(cudaStreamSynchronize(stream));
+        for (int32_t b = 0; b < n; ++b) {
+            rc = init_instance_cells(b);
+            if (rc != DUWP_OK) return rc;
+        }
     }
     rc = enqueue_prepare();
     if (rc != DUWP_OK) return rc;
     return sync();
 }
 
-int Engine::add_instance(int slot, const duwp_params &p, int32_t cell_base)
+int Engine::add_instance(int slot, const duwp_params &p, int32_t cell_base, bool upload)
 {
     if (slot < 0 || slot >= max_inst) return DUWP_EINVAL;
     HostInst h;
@@ -379,11 +392,18 @@ int Engine::add_instance(int slot, const duwp_params &p, int32_t cell_base)
     h.cell_base = cell_base;
     h.d.cell_base = cell_base;
     inst[slot] = h;
+    if (!upload) return DUWP_OK;
     DUWP_CU(cudaMemcpyAsync(dev.inst + slot, &inst[slot].d, sizeof(InstDev), cudaMemcpyHostToDevice, stream));
+    return init_instance_cells(slot);
+}
+
+int Engine::init_instance_cells(int slot)
+{
+    const duwp_params &p = inst[slot].p;
     double lc[5], rc5[5];
     cons_of(p.left, p.R, lc);
     cons_of(p.right, p.R, rc5);
-    DUWP_CU(launch_init_cells(dev, slot, cell_base, p.n_cells + 2, lc, rc5, p.x_min, p.x_split, stream));
+    DUWP_CU(launch_init_cells(dev, slot, inst[slot].cell_base, p.n_cells + 2, lc, rc5, p.x_min, p.x_split, stream));
     return DUWP_OK;
 }
 

@@ -82,7 +82,10 @@ struct Engine {
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
                void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);
     int configure_launch(int threads_, int variant_ = 0);
-    int add_instance(int slot, const duwp_params &p, int32_t cell_base);   // used by create and the server
+    // used by create (upload = false: neither the table entry nor the cells yet; create copies the
+    // table once and then initialises the cells) and the server
+    int add_instance(int slot, const duwp_params &p, int32_t cell_base, bool upload = true);
+    int init_instance_cells(int slot);
     int remove_instance(int slot);
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[kStepEvents]: events around kernels
     int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
