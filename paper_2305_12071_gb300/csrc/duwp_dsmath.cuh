@@ -282,7 +282,7 @@ __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const fl
                                                    const uint32_t *w, float out[3], ds *unrounded = nullptr)
 {
     bool ok = true;
-#pragma unroll
+#pragma unroll 1   // one copy of the component code: the sampling loop is large for the instruction cache
     for (int k = 0; k < 3; ++k) {
         const ds cp = ds_turn_cos(turn, w[4 * k], w[4 * k + 1]);
         const ds L = ds_neg_log1m(logt, w[4 * k + 2], w[4 * k + 3]);
