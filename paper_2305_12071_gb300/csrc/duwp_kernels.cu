@@ -332,7 +332,7 @@ __device__ int far_lower(const FarItem<Rec> *f, int n, int dest, int src)
 
 // Majorant factor (c_max/c_ref)^{-2 upsilon} of the NTC count; kept per cell and recomputed only when
 // c_max is raised.
-__device__ inline double majorant_factor(const InstDev &I, double cmax)
+__device__ __noinline__ double majorant_factor(const InstDev &I, double cmax)   // rare: when c_max rises
 {
     return (I.upsilon == 0.0) ? 1.0 : pow(cmax / I.c_ref, -2.0 * I.upsilon);
 }
@@ -387,6 +387,17 @@ __device__ __forceinline__ double rel_speed(const Rec &A, const Rec &B)
 // error below 1e-5; outside the margin 2e-4 p + 2.5e-7 around the threshold the decision is the exact
 // one.  Inside it (and for tiny ratios) c_r and the power are evaluated in double precision.
 // cr / exact: the exact relative speed, computed here when needed.
+// The acceptance decided in double precision (the single-precision test was within its margin): out
+// of line, as it is rare.
+template <typename Rec>
+__device__ __noinline__ bool accept_exact(const InstDev &I, double expo, const Rec &A, const Rec &B, double cm,
+                                          uint32_t w2, uint32_t w3, double &cr, bool &exact)
+{
+    if (!exact) { cr = rel_speed(A, B); exact = true; }
+    const double x = cr / cm;
+    return u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo));
+}
+
 template <typename Rec>
 __device__ __forceinline__ bool accept_pair(const InstDev &I, double expo, float expo_f, const Rec &A, const Rec &B,
                                             float cr32, float cm32, double cm, uint32_t w2, uint32_t w3, double &cr,
@@ -401,9 +412,7 @@ __device__ __forceinline__ bool accept_pair(const InstDev &I, double expo, float
         if (uf < p32 - m32) return true;
         if (uf > p32 + m32) return false;
     }
-    if (!exact) { cr = rel_speed(A, B); exact = true; }
-    const double x = cr / cm;
-    return u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo));
+    return accept_exact<Rec>(I, expo, A, B, cm, w2, w3, cr, exact);
 }
 
 // Isotropic VHS scattering of an accepted pair (Appendix A) in double precision: the relative
@@ -439,7 +448,8 @@ __device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint
     draw(I, id, 2u * k + 1u, step, kCollide, v);
     scatter_fp64<RecD>(v, A, B, exact ? cr : rel_speed(A, B));
 }
-__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecF &A, RecF &B,
+// (one copy, called from every collision loop: inlined five times it crowded the instruction cache)
+__device__ __noinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecF &A, RecF &B,
                                              double cr, bool exact)
 {
     uint32_t v[4];
