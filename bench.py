@@ -180,6 +180,61 @@ def oracle_sample(params_list, sample_idx, min_steps: int = 2, budget_s: float =
     return updates, dt, rounds
 
 
+# ---------------------------------------------------------------------------- serving
+def run_serving(args, rank: int, world: int):
+    """Continuous batching under Poisson arrivals (50 requests/s of shock and Sod problems, cells
+    log-uniform in [100, 1e4], 100-1000 particles per cell, Kn log-uniform in [1e-4, 1]): arrivals
+    are replayed in real time for --serve-seconds, then the server drains; one JSON line with the
+    p50/p99 solve latency (arrival -> result) and the aggregate particle-updates/s."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2305_12071_gb300 import build as B
+    from paper_2305_12071_gb300 import duwp
+    from paper_2305_12071_gb300 import workloads as W
+    B.build()
+    reqs = W.serving_mix(duration_s=args.serve_seconds, rate_hz=50.0, precision="fp32")
+    srv = duwp.Server(hbm_budget_bytes=96 << 30, max_slots=128, max_cells=1_000_000, steps_per_launch=10,
+                      precision="fp32", device=int(os.environ.get("LOCAL_RANK", 0)))
+    pending, lat, queue_ms, run_ms = {}, [], [], []
+    updates, i, failed = 0, 0, 0
+    t0 = time.perf_counter()
+    limit = 20.0 * args.serve_seconds + 60.0
+    while (i < len(reqs) or pending) and time.perf_counter() - t0 < limit:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            pending[srv.submit(reqs[i][1], reqs[i][2])] = reqs[i][0]
+            i += 1
+        for rid in list(pending):
+            r = srv.poll(rid)
+            if r is None:
+                continue
+            lat.append(time.perf_counter() - t0 - pending.pop(rid))
+            updates += int(r["particle_updates"])
+            queue_ms.append(r["queue_ms"])
+            run_ms.append(r["run_ms"])
+            failed += int(r["status"] != 0)
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat_s = sorted(lat)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)] if v else None
+
+    print(json.dumps({"metric": "serving solve latency (arrival -> result)", "value": pct(lat_s, 0.5), "unit": "s",
+                      "p50_s": pct(lat_s, 0.5), "p99_s": pct(lat_s, 0.99), "higher_is_better": False,
+                      "requests": len(reqs), "completed": len(lat), "failed": failed,
+                      "unfinished": len(pending), "wall_s": wall,
+                      "particle_updates_per_s": updates / wall if wall > 0 else None,
+                      "queue_ms_p50": pct(sorted(queue_ms), 0.5), "run_ms_p50": pct(sorted(run_ms), 0.5),
+                      "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "serving_poisson50_mixed_fp32", "arrivals_s": args.serve_seconds,
+                                 "rate_hz": 50, "cells": "log-U[100,1e4]", "ppc_ref": "U[100,1000]",
+                                 "Kn": "log-U[1e-4,1]", "shock_steps": 500, "sod_steps": "to t = 0.15 at CFL 0.5",
+                                 "steps_per_launch": 10, "max_slots": 128}}), flush=True)
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank: int, world: int):
     if rank != 0:
@@ -226,7 +281,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod"])
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of --workload serve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--launch", default="", help="streaming-kernel launch shape threads,reg_capped "
@@ -241,6 +297,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.workload == "serve" and args.impl != "reference":
+        run_serving(args, rank, world)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
