@@ -308,6 +308,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     // zero everything except the particle buffers, then mark all cells unused
     DUWP_CU(cudaMemsetAsync(base, 0, o_buf0, stream));
     dev.G = G;
+    dev.G_run = G;
     dev.n_inst = max_inst;
     dev.capacity = capacity;
     dev.far_cap = far_cap;
@@ -416,6 +417,16 @@ int Engine::remove_instance(int slot)
     // class kClsSkip (0) until the next cell kernel rebuilds the plans
     DUWP_CU(cudaMemsetAsync(dev.hdr + h.cell_base, 0, sizeof(CellHdr) * size_t(h.p.n_cells + 2), stream));
     inst[slot].active = false;
+    return DUWP_OK;
+}
+
+int Engine::set_run_extent(int32_t cells)
+{
+    const int32_t n = std::max<int32_t>(1, std::min(cells, G));
+    if (n == dev.G_run) return DUWP_OK;
+    // the grids of the captured step graphs follow the extent
+    dev.G_run = n;
+    drop_graphs();
     return DUWP_OK;
 }
 

@@ -89,6 +89,10 @@ struct Engine {
     int remove_instance(int slot);
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[kStepEvents]: events around kernels
     int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
+    // Cells the step kernels cover, [0, cells) clamped to [1, G]: every active instance must lie
+    // below it and the cells above it must be unused (as remove_instance leaves them).  Drops the
+    // step graphs when it changes.
+    int set_run_extent(int32_t cells);
     int step(int32_t n);
     int sync();                        // wait (steps and profile copies) + read the device error word
     int moments_scratch(const std::vector<int64_t> &base, int64_t total);   // size + base table

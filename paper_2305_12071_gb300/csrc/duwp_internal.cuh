@@ -103,6 +103,8 @@ struct EngineDev {
     int32_t n_inst;
     int64_t capacity;          // particle slots per buffer
     int32_t far_cap;
+    int32_t G_run;             // the step kernels cover cells [0, G_run) (<= G): every resident
+                               // instance lies below it, the cells above are unused and clean
     InstDev *inst;
     int32_t *cell_inst;        // instance of each flattened cell, -1 = unused
     double *psi;               // G x 5 total state Psi_t (reservoirs: unused)

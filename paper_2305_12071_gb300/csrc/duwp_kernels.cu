@@ -1190,7 +1190,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (g >= E.G) return;
+    if (g >= E.G_run) return;
     StreamShared<Rec> &SS = reinterpret_cast<StreamShared<Rec> *>(s_raw)[warp];
     const int wp = 1 - rp;
     const CellHdr *hp = E.hdr + g;
@@ -1381,7 +1381,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
         for (int q = 0; q < 4; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
     }
-    if (g < E.G) {
+    if (g < E.G_run) {
         CellHdr hd;
         hd.Rend = hd.Sa = hd.La = hd.off = 0;
         hd.Rn = hd.Sn = hd.Ln = hd.slots = 0;
@@ -1540,7 +1540,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     }
     __syncthreads();
     // exclusive scan of the slots inside the block
-    const int64_t v = (g < E.G) ? 2 * static_cast<int64_t>(E.slots[g]) : 0;
+    const int64_t v = (g < E.G_run) ? 2 * static_cast<int64_t>(E.slots[g]) : 0;
     int64_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1555,7 +1555,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
                        // re-sampled, 3 the other direct cells and the staged cells
     int chunks = 0;
-    if (g < E.G) {
+    if (g < E.G_run) {
         const int64_t o = s_pre + wpre + x - v;
         E.off[wp][g] = o;
         E.hdr[g].off = o;
@@ -1608,7 +1608,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         for (int q = 0; q < 4; ++q) E.ticket[q] = 0;
         E.ticket[kSampleCtr] = 0;
     }
-    if (g >= E.G) return;
+    if (g >= E.G_run) return;
     const int b = E.cell_inst[g];
     if (b < 0) return;
     InstDev &I = E.inst[b];
@@ -1829,7 +1829,7 @@ cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int
                           int prio)
 {
     const int wpb = threads / 32;
-    const int grid = (E.G + wpb - 1) / wpb;
+    const int grid = (E.G_run + wpb - 1) / wpb;
     const size_t smem = stream_smem_bytes(fp32, threads);
     cudaError_t e;
     if (fp32) {
@@ -1854,7 +1854,7 @@ cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s)
 
 cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaStream_t s)
 {
-    const int grid = (E.G + kCellBlock - 1) / kCellBlock;
+    const int grid = (E.G_run + kCellBlock - 1) / kCellBlock;
     if (fp32) k_cells<RecF><<<grid, kCellBlock, 0, s>>>(E, q, update);
     else k_cells<RecD><<<grid, kCellBlock, 0, s>>>(E, q, update);
     return cudaGetLastError();
@@ -1862,7 +1862,7 @@ cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaSt
 
 cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStream_t s)
 {
-    const int grid = (E.G + kCellBlock - 1) / kCellBlock;
+    const int grid = (E.G_run + kCellBlock - 1) / kCellBlock;
     k_offsets_flux<<<grid, kCellBlock, 0, s>>>(E, wp, advance);
     return cudaGetLastError();
 }

@@ -3,8 +3,8 @@
 // Requests (a problem description and a step count) queue on the host.  A worker thread owns the
 // engine: between launches it admits queued requests while an instance slot, a contiguous range
 // of pool cells and enough of the particle-slot budget are free (admission by HBM footprint),
-// steps every resident request together (one set of launches over the whole cell pool, replayed
-// from CUDA graphs, so requests admitted meanwhile join the next launch), and retires each request
+// steps every resident request together (one set of launches over the occupied part of the cell
+// pool, replayed from CUDA graphs, so requests admitted meanwhile join the next launch), and retires each request
 // as soon as its own step count is reached: its profile is copied out, its cells and slots freed.
 // Each request draws only from its own generator key, so its result does not depend on what else
 // is resident.
@@ -111,7 +111,20 @@ struct duwp_server {
     void run();
     bool admit_locked();
     void retire(Request *r);
+    int32_t run_extent() const;
 };
+
+// Cells the step kernels cover: up to the end of the highest resident range, rounded up to a
+// granule so that small changes keep the captured graphs (first-fit keeps the ranges low, and an
+// empty pool's cells cost block launches every step).
+int32_t duwp_server::run_extent() const
+{
+    constexpr int32_t kGranule = 4096;
+    int32_t hi = 0;
+    for (const Request *r : resident)
+        if (r) hi = std::max(hi, r->cell_base + r->p.n_cells + 2);
+    return ((hi + kGranule - 1) / kGranule) * kGranule;
+}
 
 void duwp_server::retire(Request *r)
 {
@@ -194,9 +207,13 @@ void duwp_server::run()
             cv.wait(lk, [&] { return stop || !queue.empty(); });
             continue;
         }
+        const int32_t extent = run_extent();
         lk.unlock();
         int rc = DUWP_OK;
-        if (admitted) rc = eng.enqueue_prepare();
+        if (admitted) {
+            rc = eng.set_run_extent(extent);
+            if (rc == DUWP_OK) rc = eng.enqueue_prepare();
+        }
         const int32_t k = static_cast<int32_t>(std::min<int64_t>(std::max(1, cfg.steps_per_launch), min_left));
         float ms = 0.f;
         if (rc == DUWP_OK && k > 0) {
@@ -227,6 +244,7 @@ void duwp_server::run()
             }
         }
         if (retired) {
+            eng.set_run_extent(run_extent());
             lk.unlock();
             const int rc2 = eng.enqueue_prepare();
             lk.lock();

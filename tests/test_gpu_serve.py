@@ -32,19 +32,18 @@ def _alone(p, n):
     return m
 
 
-def test_served_results_equal_alone():
+def _serve_and_compare(reqs, max_slots, max_cells, first_wave):
     from paper_2305_12071_gb300 import build as B
     from paper_2305_12071_gb300 import duwp
     B.build()
-    srv = duwp.Server(hbm_budget_bytes=2 << 30, max_slots=3, max_cells=2048, steps_per_launch=4,
+    srv = duwp.Server(hbm_budget_bytes=2 << 30, max_slots=max_slots, max_cells=max_cells, steps_per_launch=4,
                       precision="fp32")
-    reqs = _mix()
     ids = []
     # first wave, then more requests while the first ones are running
-    for p, n in reqs[:3]:
+    for p, n in reqs[:first_wave]:
         ids.append(srv.submit(p, n))
     time.sleep(0.05)
-    for p, n in reqs[3:]:
+    for p, n in reqs[first_wave:]:
         ids.append(srv.submit(p, n))
     results = {}
     t0 = time.time()
@@ -66,6 +65,21 @@ def test_served_results_equal_alone():
         a = _alone(p, n)
         for k in ("rho", "u", "T"):
             assert np.array_equal(r[k], a[k]), f"request {rid} field {k} differs from the solve alone"
+
+
+def test_served_results_equal_alone():
+    _serve_and_compare(_mix(), max_slots=3, max_cells=2048, first_wave=3)
+
+
+def test_served_results_equal_alone_sparse_pool():
+    """A pool far larger than what is resident: the step kernels cover only the cells below the
+    highest resident range (in granules of 4096 cells), which grows and shrinks as requests of a few
+    thousand cells are admitted into, and retired from, ranges above and below one another."""
+    reqs = []
+    for i, (mach, cells, ppc, n) in enumerate([(2.0, 3000, 12, 14), (4.0, 2500, 16, 6), (1.4, 4500, 10, 10),
+                                               (5.0, 800, 30, 5), (3.0, 5200, 8, 9), (2.6, 1200, 20, 7)]):
+        reqs.append((W.shock(mach, n_cells=cells, ppc_ref=ppc, precision="fp32", seed=700 + i), n))
+    _serve_and_compare(reqs, max_slots=3, max_cells=200_000, first_wave=3)
 
 
 def test_server_rejects_oversized_and_unknown():
