@@ -108,6 +108,7 @@ def lib():
         L.ora_get_counters.argtypes = [vp, P(i32), P(i32), P(i32), P(i32)]
         L.ora_get_consts.argtypes = [vp, P(d)]
         L.ora_get_prim.argtypes = [vp, P(d), P(d), P(d), P(d), P(i32)]
+        L.ora_stress_heat.argtypes = [vp, P(d), P(d)]
         L.ora_transport.argtypes = [vp, i64, P(d), P(d)]; L.ora_transport.restype = i64
         L.ora_ce_sample.argtypes = [P(_Params), P(d), P(d), P(d), u32, u32, u32, u32, i64, P(d), P(d)]
         _lib = L
@@ -326,6 +327,13 @@ class Oracle:
         lib().ora_get_prim(self.h, _ptr(rho, C.c_double), _ptr(u, C.c_double), _ptr(T, C.c_double),
                            _ptr(P, C.c_double), _ptr(valid, C.c_int32))
         return {"rho": rho, "u": u, "T": T, "P": P, "valid": valid.astype(bool)}
+
+    def stress_heat(self) -> dict:
+        """Normal stress Pi = S_xx and heat flux Q = Q_x per cell (Eq. gkt_moment1) of the current
+        state: particle central moments about U_t plus the wave's NS values weighted by rho_w/rho_t."""
+        Pi, Q = np.empty(self.C, np.float64), np.empty(self.C, np.float64)
+        lib().ora_stress_heat(self.h, _ptr(Pi, C.c_double), _ptr(Q, C.c_double))
+        return {"Pi": Pi, "Q": Q}
 
     def transport(self, cell: int, xl: float, u: float):
         x, uu = C.c_double(xl), C.c_double(u)

@@ -1031,6 +1031,62 @@ void ora_get_consts(void *vh, double out[10])
     out[5] = c->lambda_ref; out[6] = c->mu_ref; out[7] = c->upsilon; out[8] = c->c_ref; out[9] = c->ntc_A;
 }
 
+/* Normal stress Pi = S_xx and heat flux Q = Q_x of every cell (Eq. gkt_moment1: S is the second
+ * central moment of f - g, Q the third of f) from the current state.  The distribution is the
+ * particles plus the wave (Step 1):
+ *   particles: central moments about the total velocity U_t of the cell,
+ *     S_p = (m_p/dx) sum (xi_x - U)^2 - rho_p R T_t,  Q_p = (m_p/dx) sum (xi_x - U) |xi - U|^2 / 2,
+ *     rho_p = n m_p / dx (the Maxwellian g at the total state takes rho_t R T_t; the wave's
+ *     Maxwellian part takes rho_w R T_t of it back, leaving rho_p R T_t);
+ *   wave (reading): its NS stress and heat flux, the values the Chapman-Enskog re-sampling uses
+ *     (neighbour states as the wave flux sees them, mu_e = eps mu), weighted by rho_w / rho_t.
+ * A cell whose total state is not usable (rho_t <= 0 or T_t <= 0) reports 0 for both. */
+void ora_stress_heat(void *vh, double *Pi, double *Q)
+{
+    ora_inst *h = (ora_inst *)vh;
+    const ora_params *p = &h->p;
+    const ora_consts *c = &h->c;
+    const int32_t C = h->C;
+    ora_prim *W = (ora_prim *)malloc((size_t)C * sizeof(ora_prim));
+    double *s2 = (double *)calloc((size_t)C, sizeof(double));
+    double *s3 = (double *)calloc((size_t)C, sizeof(double));
+    int64_t *n = (int64_t *)calloc((size_t)C, sizeof(int64_t));
+    if (!W || !s2 || !s3 || !n) {
+        free(W); free(s2); free(s3); free(n);
+        for (int32_t i = 0; i < C; ++i) Pi[i] = Q[i] = NAN;
+        return;
+    }
+    for (int32_t i = 0; i < C; ++i) W[i] = prim_of_cons(h->psi + 5 * i, p->R);
+    for (int64_t k = 0; k < h->np; ++k) {
+        const opart *q = h->parts + k;
+        const int32_t i = q->cell;
+        const double cx = q->u - W[i].u, cy = q->v - W[i].v, cz = q->w - W[i].w;
+        s2[i] += cx * cx;
+        s3[i] += cx * (0.5 * (cx * cx + cy * cy + cz * cz));
+        n[i] += 1;
+    }
+    for (int32_t i = 0; i < C; ++i) {
+        Pi[i] = Q[i] = 0.0;
+        if (!W[i].valid) continue;
+        const double rho_p = (double)n[i] * c->mp_over_dx;
+        Pi[i] = c->mp_over_dx * s2[i] - rho_p * p->R * W[i].T;
+        Q[i] = c->mp_over_dx * s3[i];
+        ora_prim Wm, Wp;
+        if (i > 0) Wm = W[i - 1];
+        else if (p->bc_left == ORA_BC_PERIODIC) Wm = W[C - 1];
+        else Wm = ghost_prim(h, 0, &W[0]);
+        if (i < C - 1) Wp = W[i + 1];
+        else if (p->bc_right == ORA_BC_PERIODIC) Wp = W[0];
+        else Wp = ghost_prim(h, 1, &W[C - 1]);
+        const ora_ce f = ce_factor(p, c, &Wm, &W[i], &Wp);
+        const double rho_t = h->psi[5 * i];
+        const double wgt = (rho_t - rho_p) / rho_t;
+        Pi[i] += wgt * f.sxx;
+        Q[i] += wgt * f.qx;
+    }
+    free(W); free(s2); free(s3); free(n);
+}
+
 /* primitive state and P of every cell from the current Psi_t */
 void ora_get_prim(void *vh, double *rho, double *u, double *T, double *P, int32_t *valid)
 {
