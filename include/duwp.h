@@ -207,6 +207,27 @@ int duwp_moments_wait(duwp_handle *h);
 int duwp_fields(duwp_handle *h, int32_t inst, int32_t which, double *host_psi, int32_t n_cells,
                 int64_t *host_navg);
 
+/* Synchronizing.  Normal stress Pi = S_xx and heat flux Q = Q_x (Sec. 2, Eq. gkt_moment1: S the
+ * second central moment of f - g, Q the third of f) per cell of instance `inst` into caller-owned
+ * HOST arrays of n = n_cells doubles.  f is the particles plus the wave: the particle part from the
+ * central moments of the cell's particles about the total velocity U_t,
+ *   (m_p/dx) sum (xi_x - U)^2 - rho_p R T_t   and   (m_p/dx) sum (xi_x - U) |xi - U|^2 / 2,
+ * the wave part its Navier-Stokes stress -(4/3) mu_e dU/dx and heat flux -(5/2) R mu_e / Pr dT/dx
+ * (mu_e = eps mu at the cell's state, central differences over the neighbouring states as the wave
+ * flux sees them) weighted by rho_w / rho_t.  A cell whose total state is not usable reports 0.
+ * which = DUWP_INSTANT: of the current state (one device pass over the instance's particles);
+ * DUWP_AVERAGED: the mean of the values taken by duwp_stress_heat_accumulate so far (0 before the
+ * first).  Errors: DUWP_EINVAL (inst, which, n, NULL arrays), DUWP_ENOMEM (its device scratch,
+ * 32 B per cell, kept by the handle), device errors. */
+int duwp_stress_heat(duwp_handle *h, int32_t inst, int32_t which, double *host_Pi, double *host_Q, int32_t n);
+
+/* Non-blocking.  Adds the current Pi and Q of every cell of every instance (as duwp_stress_heat
+ * DUWP_INSTANT computes them) to the handle's running sums: enqueued behind the steps enqueued so
+ * far, one call per state to be averaged (for the time-averaged profiles of Sec. 4.1, after each
+ * step from the first averaged one).  The sums are not part of a checkpoint.  Errors: DUWP_EINVAL
+ * (h), DUWP_ENOMEM (scratch); device errors are reported by the next synchronizing call. */
+int duwp_stress_heat_accumulate(duwp_handle *h);
+
 /* Derived constants and sizes of instance `inst` (not synchronizing except steps_done). */
 int duwp_get_info(duwp_handle *h, int32_t inst, duwp_info *out);
 

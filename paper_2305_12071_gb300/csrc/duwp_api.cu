@@ -169,6 +169,7 @@ Engine::~Engine()
     }
     if (cstream) cudaStreamDestroy(cstream);
     if (mom) dfree(mom, mom_bytes);
+    if (sh) dfree(sh, sh_bytes);
     dfree(slab, slab_bytes);
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -691,6 +692,18 @@ int duwp_moments(duwp_handle *h, int32_t b, int32_t which, double *rho, double *
 
 namespace duwp {
 
+int Engine::stress_scratch()
+{
+    if (sh) return DUWP_OK;
+    const size_t bytes = 4 * sizeof(double) * size_t(G);
+    sh = static_cast<double *>(dalloc(bytes));
+    if (!sh) return DUWP_ENOMEM;
+    sh_bytes = bytes;
+    sh_count = 0;
+    DUWP_CU(cudaMemsetAsync(sh, 0, bytes, stream));
+    return DUWP_OK;
+}
+
 int Engine::moments_scratch(const std::vector<int64_t> &base, int64_t total)
 {
     const size_t head = (sizeof(int64_t) * base.size() + 255) & ~static_cast<size_t>(255);
@@ -894,6 +907,44 @@ int duwp_get_particles(duwp_handle *h, int32_t b, int32_t *cell, double *xl, dou
     E.dfree(tmp, bytes);
     if (e != cudaSuccess) { set_cuda_error(e, "duwp_get_particles"); return DUWP_ECUDA; }
     return E.sync();
+}
+
+int duwp_stress_heat(duwp_handle *h, int32_t b, int32_t which, double *Pi, double *Q, int32_t n)
+{
+    int rc = check_inst(h, b);
+    if (rc) return rc;
+    if (which != DUWP_INSTANT && which != DUWP_AVERAGED) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    const HostInst &hi = E.inst[b];
+    if (n != hi.p.n_cells || !Pi || !Q) return DUWP_EINVAL;
+    rc = E.stress_scratch();
+    if (rc) return rc;
+    const int32_t g0 = hi.cell_base + 1;
+    const double *src = E.sh + (which == DUWP_INSTANT ? 0 : 2 * size_t(E.G));
+    cudaError_t e = cudaSuccess;
+    if (which == DUWP_INSTANT) e = launch_stress_heat(E.dev, E.fp32, E.parity, g0, n, 0, E.sh, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Pi, src + g0, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q, src + E.G + g0, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) { set_cuda_error(e, "duwp_stress_heat"); return DUWP_ECUDA; }
+    rc = E.sync();
+    if (rc) return rc;
+    if (which == DUWP_AVERAGED) {
+        const double scale = E.sh_count > 0 ? 1.0 / static_cast<double>(E.sh_count) : 0.0;
+        for (int32_t i = 0; i < n; ++i) { Pi[i] *= scale; Q[i] *= scale; }
+    }
+    return DUWP_OK;
+}
+
+int duwp_stress_heat_accumulate(duwp_handle *h)
+{
+    if (!h) return DUWP_EINVAL;
+    Engine &E = h->eng;
+    const int rc = E.stress_scratch();
+    if (rc) return rc;
+    DUWP_CU(launch_stress_heat(E.dev, E.fp32, E.parity, 0, E.dev.G_run, 1, E.sh + 2 * size_t(E.G), E.stream));
+    E.sh_count += 1;
+    return DUWP_OK;
 }
 
 int duwp_get_counters(duwp_handle *h, int32_t b, int32_t *ncand, int32_t *nacc, int32_t *nabs, int32_t *nnew, int32_t n)

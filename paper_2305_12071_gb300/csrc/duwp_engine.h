@@ -78,6 +78,12 @@ struct Engine {
     cudaEvent_t copy_done[2] = {nullptr, nullptr};
     int64_t n_async = 0;
 
+    // device scratch of the stress / heat-flux read-out (allocated on first use): [Pi | Q] of the
+    // last instantaneous read and [Pi | Q] running sums, G doubles each; sums taken so far
+    double *sh = nullptr;
+    size_t sh_bytes = 0;
+    int64_t sh_count = 0;
+
     ~Engine();
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
                void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);
@@ -97,6 +103,7 @@ struct Engine {
     int sync();                        // wait (steps and profile copies) + read the device error word
     int moments_scratch(const std::vector<int64_t> &base, int64_t total);   // size + base table
     double *mom_out(int area) const;
+    int stress_scratch();              // allocates and zeroes sh on first use
     int read_inst(int b, InstDev &out);
     void *dalloc(size_t bytes);
     void dfree(void *p, size_t bytes);

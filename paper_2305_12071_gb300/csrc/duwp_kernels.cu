@@ -1722,6 +1722,90 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 }
 
 // ------------------------------------------------------------------------------------------
+// Normal stress Pi = S_xx and heat flux Q = Q_x of interior cells (Eq. gkt_moment1), one warp per
+// cell (inspection, not part of the step): the particle part from the central moments of the
+// arrived particles about the total velocity U_t,
+//   S_p = (m_p/dx) sum (xi_x - U)^2 - rho_p R T_t,   Q_p = (m_p/dx) sum (xi_x - U) |xi - U|^2 / 2,
+// rho_p = n m_p / dx; the wave part its NS stress and heat flux (the values of the Chapman-Enskog
+// re-sampling: neighbour states as the wave flux sees them, mu_e = eps mu) weighted by
+// rho_w / rho_t.  A cell whose total state is not usable reports 0.  Cells g0 .. g0 + ncell - 1;
+// out: [Pi | Q] of G entries each, written (accumulate = 0) or added to (accumulate = 1).
+// ------------------------------------------------------------------------------------------
+template <typename Rec>
+__global__ void k_stress_heat(EngineDev E, int rp, int g0, int ncell, int accumulate, double *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= ncell) return;
+    const int g = g0 + t;
+    const int b = E.cell_inst[g];
+    if (b < 0) return;
+    const InstDev &I = E.inst[b];
+    const int i = g - I.cell_base - 1;
+    if (i < 0 || i >= I.C) return;
+    double pi = 0.0, q = 0.0;
+    if (E.valid[g]) {
+        const double *W0 = E.prim + 5 * static_cast<int64_t>(g);
+        const double U = W0[1], V = W0[2], Wz = W0[3], T = W0[4];
+        // the arrived runs of the cell, as the particle read-out finds them
+        const Rec *in = static_cast<const Rec *>(E.buf[rp]);
+        const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
+        const int nf = E.far_count[1];
+        int lo = 0, mid = 0, hi = 0;
+        if (nf > 0) {
+            lo = far_lower(fs, nf, g, INT32_MIN);
+            mid = far_lower(fs, nf, g, g + 2);
+            hi = far_lower(fs, nf, g + 1, INT32_MIN);
+        }
+        const int64_t Rend = E.off[rp][g - 1] + 2 * static_cast<int64_t>(E.slotsb[rp][g - 1]);
+        const int Rn = E.nR[rp][g - 1];
+        const int64_t Sa = E.off[rp][g];
+        const int Sn = E.nS[rp][g];
+        const int64_t La = E.off[rp][g + 1] + E.slotsb[rp][g + 1];
+        const int Ln = E.nL[rp][g + 1];
+        const int nfb = mid - lo, nfa = hi - mid;
+        const int n = nfb + Rn + Sn + Ln + nfa;
+        double s2 = 0.0, s3 = 0.0;
+        for (int k = lane; k < n; k += 32) {
+            int r = k;
+            Rec x;
+            if (r < nfb) x = fs[lo + r].rec;
+            else if ((r -= nfb) < Rn) x = in[Rend - 1 - r];
+            else if ((r -= Rn) < Sn) x = in[Sa + r];
+            else if ((r -= Sn) < Ln) x = in[La + r];
+            else { r -= Ln; x = fs[mid + r].rec; }
+            const double cx = static_cast<double>(x.u) - U, cy = static_cast<double>(x.v) - V,
+                         cz = static_cast<double>(x.w) - Wz;
+            s2 += cx * cx;
+            s3 += cx * (0.5 * (cx * cx + cy * cy + cz * cz));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        }
+        const double rho_p = static_cast<double>(n) * I.mp_over_dx;
+        pi = I.mp_over_dx * s2 - rho_p * I.R * T;
+        q = I.mp_over_dx * s3;
+        CeCell m;
+        ce_coefs(I, E.prim, E.valid, g, i, m);   // sets the stress and heat flux of a usable cell
+        const double rho_t = E.psi[5 * static_cast<int64_t>(g)];
+        const double wgt = (rho_t - rho_p) / rho_t;
+        pi += wgt * m.sxx;
+        q += wgt * m.qx;
+    }
+    if (lane == 0) {
+        if (accumulate) {
+            out[g] += pi;
+            out[E.G + g] += q;
+        } else {
+            out[g] = pi;
+            out[E.G + g] = q;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Macroscopic profiles of all instances in one pass (inspection): out = [rho | u | T | wave
 // fraction] x total, instance b's interior cell i at base[b] + i (base[b] < 0: not reported).
 // ------------------------------------------------------------------------------------------
@@ -1864,6 +1948,16 @@ cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStr
 {
     const int grid = (E.G_run + kCellBlock - 1) / kCellBlock;
     k_offsets_flux<<<grid, kCellBlock, 0, s>>>(E, wp, advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stress_heat(const EngineDev &E, int fp32, int rp, int g0, int ncell, int accumulate, double *out,
+                               cudaStream_t s)
+{
+    if (ncell <= 0) return cudaSuccess;
+    const int grid = (ncell + 3) / 4;
+    if (fp32) k_stress_heat<RecF><<<grid, 128, 0, s>>>(E, rp, g0, ncell, accumulate, out);
+    else k_stress_heat<RecD><<<grid, 128, 0, s>>>(E, rp, g0, ncell, accumulate, out);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "duwp_destroy", "duwp_error_string", "duwp_last_cuda_error", "duwp_set_launch", "duwp_use_graphs",
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
-    "duwp_server_destroy", "duwp_get_particles_noalloc",
+    "duwp_server_destroy", "duwp_get_particles_noalloc", "duwp_stress_heat", "duwp_stress_heat_accumulate",
 )
 
 
@@ -123,6 +123,8 @@ def load(path: str = LIB_PATH):
         L.duwp_moments_all.argtypes = [vp, i32, dp, dp, dp, dp, i64]
         L.duwp_moments_all_async.argtypes = [vp, i32, dp, dp, dp, dp, i64]
         L.duwp_moments_wait.argtypes = [vp]
+        L.duwp_stress_heat.argtypes = [vp, i32, i32, dp, dp, i32]
+        L.duwp_stress_heat_accumulate.argtypes = [vp]
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
@@ -296,6 +298,18 @@ class Solver:
         _chk(self.L.duwp_moments(self.h, inst, which, _dptr(r), _dptr(u), _dptr(T), _dptr(wf), n), "duwp_moments")
         return {"rho": r, "u": u, "T": T, "wave_frac": wf}
 
+    def stress_heat(self, inst: int = 0, which: int = INSTANT) -> dict:
+        """Normal stress Pi = S_xx and heat flux Q = Q_x per cell (Eq. gkt_moment1) of the current
+        state, or (AVERAGED) the mean of the states taken by stress_heat_accumulate."""
+        n = self.n_cells(inst)
+        Pi, Q = np.empty(n, np.float64), np.empty(n, np.float64)
+        _chk(self.L.duwp_stress_heat(self.h, inst, which, _dptr(Pi), _dptr(Q), n), "duwp_stress_heat")
+        return {"Pi": Pi, "Q": Q}
+
+    def stress_heat_accumulate(self):
+        """Adds the current Pi and Q of every cell to the running sums (enqueued, non-blocking)."""
+        _chk(self.L.duwp_stress_heat_accumulate(self.h), "duwp_stress_heat_accumulate")
+
     def moments_all(self, which: int = INSTANT, out: dict | None = None) -> dict:
         """Profiles of every instance at once (concatenated in instance order): one call, one copy.
         `out` (optional) supplies the host arrays to fill (e.g. pinned ones) and is returned."""
@@ -420,3 +434,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def shock_normalised(kind: str, x, rho, T, Pi, Q, up, down, lam_up: float, beta: float = 1.0,
+                     R: float = 1.0) -> dict:
+    """Shock-structure profiles in the paper's normalisation (Sec. 4.1).  up, down: (rho, T) of the
+    inflow and outflow states; lam_up: the inflow mean free path of Eq. (lambda); beta its factor.
+      'ma3' (Eq. ma3): rho/rho_up, T/T_up, Pi/p_up, Q/(p_up sqrt(2 R T_up)), x/(sqrt(pi) lam_up / 2);
+      'ma8' (Eq. ma8): (rho - rho_up)/(rho_down - rho_up), (T - T_up)/(T_down - T_up),
+                       Pi/(rho_up 2 R T_up), Q/(rho_up (2 R T_up)^1.5), x/(beta pi lam_up)."""
+    x, rho, T, Pi, Q = (np.asarray(a, np.float64) for a in (x, rho, T, Pi, Q))
+    (r1, T1), (r2, T2) = up, down
+    if kind == "ma3":
+        p1 = r1 * R * T1
+        return {"x": x / (0.5 * np.sqrt(np.pi) * lam_up), "rho": rho / r1, "T": T / T1, "Pi": Pi / p1,
+                "Q": Q / (p1 * np.sqrt(2.0 * R * T1))}
+    if kind == "ma8":
+        s = 2.0 * R * T1
+        return {"x": x / (beta * np.pi * lam_up), "rho": (rho - r1) / (r2 - r1), "T": (T - T1) / (T2 - T1),
+                "Pi": Pi / (r1 * s), "Q": Q / (r1 * s ** 1.5)}
+    raise ValueError(f"unknown normalisation {kind!r} (ma3 | ma8)")
