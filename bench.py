@@ -378,6 +378,21 @@ def main():
     upd_timed = sol.particle_updates() - u2
     serial_ms = kms[5] / args.steps
 
+    # ------------------------------------------------ the stress / heat-flux read-out (Eq. gkt_moment1; not
+    # part of the step): one pass over every particle record of the batch, events around 3 passes
+    n_part = int(sum(sol.num_particles(i) for i in range(sol.n)))
+    sol.stress_heat_accumulate()                      # the first call allocates its scratch
+    sol.sync()
+    ro_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(sol.stream):
+        ro_ev[0].record()
+    for _ in range(3):
+        sol.stress_heat_accumulate()
+    with torch.cuda.stream(sol.stream):
+        ro_ev[1].record()
+    sol.sync()
+    ro_ms = ro_ev[0].elapsed_time(ro_ev[1]) / 3
+
     out = None
     if rank == 0:
         steps_sorted = sorted(step_ms)
@@ -409,7 +424,11 @@ def main():
                "step_ms_p50": p50, "step_ms_p99": p99, "serial_ms_per_step": serial_ms,
                "kernel_ms_per_step": {n: float(v / args.steps) for n, v in zip(duwp.Solver.KERNELS, kms[:5])},
                "kernel_times": "from the same number of steps run kernel by kernel with events around each",
-               "kernel_share": kernel_share, "roofline": roof}
+               "kernel_share": kernel_share, "roofline": roof,
+               "readout": {"kernel": "k_sh_split + k_sh_sums + k_sh_finish", "what": "normal stress and heat flux of every cell",
+                           "ms": ro_ms, "particles": n_part, "bytes_per_particle": rec_bytes,
+                           "achieved_gbs": n_part * rec_bytes / (ro_ms * 1e-3) / 1e9,
+                           "frac": n_part * rec_bytes / (ro_ms * 1e-3) / 1e9 / peak}}
     sol.close()
     del sol
     torch.cuda.empty_cache()

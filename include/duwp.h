@@ -218,7 +218,7 @@ int duwp_fields(duwp_handle *h, int32_t inst, int32_t which, double *host_psi, i
  * which = DUWP_INSTANT: of the current state (one device pass over the instance's particles);
  * DUWP_AVERAGED: the mean of the values taken by duwp_stress_heat_accumulate so far (0 before the
  * first).  Errors: DUWP_EINVAL (inst, which, n, NULL arrays), DUWP_ENOMEM (its device scratch,
- * 32 B per cell, kept by the handle), device errors. */
+ * 72 B per cell, kept by the handle), device errors. */
 int duwp_stress_heat(duwp_handle *h, int32_t inst, int32_t which, double *host_Pi, double *host_Q, int32_t n);
 
 /* Non-blocking.  Adds the current Pi and Q of every cell of every instance (as duwp_stress_heat

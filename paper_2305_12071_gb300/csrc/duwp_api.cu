@@ -695,12 +695,12 @@ namespace duwp {
 int Engine::stress_scratch()
 {
     if (sh) return DUWP_OK;
-    const size_t bytes = 4 * sizeof(double) * size_t(G);
+    const size_t bytes = (4 * sizeof(double) + stress_tmp_bytes()) * size_t(G);
     sh = static_cast<double *>(dalloc(bytes));
     if (!sh) return DUWP_ENOMEM;
     sh_bytes = bytes;
     sh_count = 0;
-    DUWP_CU(cudaMemsetAsync(sh, 0, bytes, stream));
+    DUWP_CU(cudaMemsetAsync(sh, 0, 4 * sizeof(double) * size_t(G), stream));
     return DUWP_OK;
 }
 
@@ -922,7 +922,7 @@ int duwp_stress_heat(duwp_handle *h, int32_t b, int32_t which, double *Pi, doubl
     const int32_t g0 = hi.cell_base + 1;
     const double *src = E.sh + (which == DUWP_INSTANT ? 0 : 2 * size_t(E.G));
     cudaError_t e = cudaSuccess;
-    if (which == DUWP_INSTANT) e = launch_stress_heat(E.dev, E.fp32, E.parity, g0, n, 0, E.sh, E.stream);
+    if (which == DUWP_INSTANT) e = launch_stress_heat(E.dev, E.fp32, E.parity, g0, n, 0, E.sh, E.sh + 4 * size_t(E.G), E.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Pi, src + g0, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, E.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Q, src + E.G + g0, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost, E.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
@@ -942,7 +942,7 @@ int duwp_stress_heat_accumulate(duwp_handle *h)
     Engine &E = h->eng;
     const int rc = E.stress_scratch();
     if (rc) return rc;
-    DUWP_CU(launch_stress_heat(E.dev, E.fp32, E.parity, 0, E.dev.G_run, 1, E.sh + 2 * size_t(E.G), E.stream));
+    DUWP_CU(launch_stress_heat(E.dev, E.fp32, E.parity, 0, E.dev.G_run, 1, E.sh + 2 * size_t(E.G), E.sh + 4 * size_t(E.G), E.stream));
     E.sh_count += 1;
     return DUWP_OK;
 }

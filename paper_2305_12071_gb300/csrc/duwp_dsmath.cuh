@@ -87,6 +87,12 @@ __host__ __device__ __forceinline__ ds ds_sqrt(ds a)
     const float r = (((a.hi - y2.hi) - y2.lo) + a.lo) / (2.0f * y);
     return ds_fast_two_sum(y, r);
 }
+// double-single value of a double (hi the nearest float, lo the nearest float to the rest)
+__host__ __device__ __forceinline__ ds ds_of_double(double x)
+{
+    const float h = static_cast<float>(x);
+    return {h, static_cast<float>(x - static_cast<double>(h))};
+}
 // double-single value of a double constant (hi the nearest float, lo the nearest float to the rest)
 __host__ __device__ constexpr ds ds_const(double x)
 {

@@ -79,7 +79,8 @@ struct Engine {
     int64_t n_async = 0;
 
     // device scratch of the stress / heat-flux read-out (allocated on first use): [Pi | Q] of the
-    // last instantaneous read and [Pi | Q] running sums, G doubles each; sums taken so far
+    // last instantaneous read and [Pi | Q] running sums, G doubles each, then the per-cell
+    // temporaries of the read-out passes; sums taken so far
     double *sh = nullptr;
     size_t sh_bytes = 0;
     int64_t sh_count = 0;

@@ -1722,70 +1722,139 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
 }
 
 // ------------------------------------------------------------------------------------------
-// Normal stress Pi = S_xx and heat flux Q = Q_x of interior cells (Eq. gkt_moment1), one warp per
-// cell (inspection, not part of the step): the particle part from the central moments of the
-// arrived particles about the total velocity U_t,
+// Normal stress Pi = S_xx and heat flux Q = Q_x of interior cells (Eq. gkt_moment1; inspection,
+// not part of the step): the particle part from the central moments of the arrived particles about
+// the total velocity U_t,
 //   S_p = (m_p/dx) sum (xi_x - U)^2 - rho_p R T_t,   Q_p = (m_p/dx) sum (xi_x - U) |xi - U|^2 / 2,
 // rho_p = n m_p / dx; the wave part its NS stress and heat flux (the values of the Chapman-Enskog
 // re-sampling: neighbour states as the wave flux sees them, mu_e = eps mu) weighted by
-// rho_w / rho_t.  A cell whose total state is not usable reports 0.  Cells g0 .. g0 + ncell - 1;
-// out: [Pi | Q] of G entries each, written (accumulate = 0) or added to (accumulate = 1).
+// rho_w / rho_t.  A cell whose total state is not usable reports 0.
+// Three passes: one thread per cell splits -U into float pairs; one warp per cell sums its particles
+// (single-precision records in double-single arithmetic: the double-precision units are a small
+// fraction of the single-precision ones); one thread per cell finishes in double precision.
 // ------------------------------------------------------------------------------------------
+struct ShCell {
+    float nu[6];      // -U, -V, -W as double-single pairs
+    double s[2];      // sum (xi_x - U)^2, sum (xi_x - U) |xi - U|^2 / 2 (as (hi, lo) floats for FP32 records)
+};
+
+__device__ __forceinline__ bool sh_interior(const EngineDev &E, int g, int &b, int &i)
+{
+    b = E.cell_inst[g];
+    if (b < 0) return false;
+    i = g - E.inst[b].cell_base - 1;
+    return i >= 0 && i < E.inst[b].C;
+}
+
+__global__ void k_sh_split(EngineDev E, int g0, int ncell, ShCell *tmp)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncell) return;
+    const int g = g0 + t;
+    int b, i;
+    if (!sh_interior(E, g, b, i) || !E.valid[g]) return;
+    for (int d = 0; d < 3; ++d) {
+        const ds x = ds_neg(ds_of_double(E.prim[5 * static_cast<int64_t>(g) + 1 + d]));
+        tmp[g].nu[2 * d] = x.hi;
+        tmp[g].nu[2 * d + 1] = x.lo;
+    }
+}
+
 template <typename Rec>
-__global__ void k_stress_heat(EngineDev E, int rp, int g0, int ncell, int accumulate, double *out)
+__global__ void k_sh_sums(EngineDev E, int rp, int g0, int ncell, ShCell *tmp)
 {
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (t >= ncell) return;
     const int g = g0 + t;
-    const int b = E.cell_inst[g];
-    if (b < 0) return;
-    const InstDev &I = E.inst[b];
-    const int i = g - I.cell_base - 1;
-    if (i < 0 || i >= I.C) return;
-    double pi = 0.0, q = 0.0;
-    if (E.valid[g]) {
-        const double *W0 = E.prim + 5 * static_cast<int64_t>(g);
-        const double U = W0[1], V = W0[2], Wz = W0[3], T = W0[4];
-        // the arrived runs of the cell, as the particle read-out finds them
-        const Rec *in = static_cast<const Rec *>(E.buf[rp]);
-        const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
-        const int nf = E.far_count[1];
-        int lo = 0, mid = 0, hi = 0;
-        if (nf > 0) {
-            lo = far_lower(fs, nf, g, INT32_MIN);
-            mid = far_lower(fs, nf, g, g + 2);
-            hi = far_lower(fs, nf, g + 1, INT32_MIN);
+    int b, i;
+    if (!sh_interior(E, g, b, i) || !E.valid[g]) return;
+    Rec *in = static_cast<Rec *>(E.buf[rp]);
+    FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
+    const CellHdr h = E.hdr[g];
+    const int n = h.n_in;
+    constexpr int kIn = 4;   // records per lane in flight
+    if constexpr (sizeof(Rec().u) == 4) {
+        const ds V[3] = {{tmp[g].nu[0], tmp[g].nu[1]}, {tmp[g].nu[2], tmp[g].nu[3]}, {tmp[g].nu[4], tmp[g].nu[5]}};
+        ds f2 = {0.0f, 0.0f}, f3 = {0.0f, 0.0f};
+        for (int k0 = lane; k0 < n; k0 += 32 * kIn) {
+            Rec x[kIn];
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                const int r = k0 + 32 * u;
+                if (r >= n) break;
+                x[u] = ld_rec(arrived_ptr<Rec>(r, h, in, fs));
+            }
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                if (k0 + 32 * u >= n) break;
+                const ds cx = ds_add({x[u].u, 0.0f}, V[0]), cy = ds_add({x[u].v, 0.0f}, V[1]),
+                         cz = ds_add({x[u].w, 0.0f}, V[2]);
+                const ds xx = ds_mul(cx, cx);
+                const ds c2 = ds_add(ds_add(xx, ds_mul(cy, cy)), ds_mul(cz, cz));
+                f2 = ds_add(f2, xx);
+                f3 = ds_add(f3, ds_mul(cx, ds_scale(c2, 0.5f)));
+            }
         }
-        const int64_t Rend = E.off[rp][g - 1] + 2 * static_cast<int64_t>(E.slotsb[rp][g - 1]);
-        const int Rn = E.nR[rp][g - 1];
-        const int64_t Sa = E.off[rp][g];
-        const int Sn = E.nS[rp][g];
-        const int64_t La = E.off[rp][g + 1] + E.slotsb[rp][g + 1];
-        const int Ln = E.nL[rp][g + 1];
-        const int nfb = mid - lo, nfa = hi - mid;
-        const int n = nfb + Rn + Sn + Ln + nfa;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f2 = ds_add(f2, {__shfl_xor_sync(0xffffffffu, f2.hi, o), __shfl_xor_sync(0xffffffffu, f2.lo, o)});
+            f3 = ds_add(f3, {__shfl_xor_sync(0xffffffffu, f3.hi, o), __shfl_xor_sync(0xffffffffu, f3.lo, o)});
+        }
+        if (lane == 0) {
+            float *o = reinterpret_cast<float *>(tmp[g].s);
+            o[0] = f2.hi; o[1] = f2.lo; o[2] = f3.hi; o[3] = f3.lo;
+        }
+    } else {
+        const double *W0 = E.prim + 5 * static_cast<int64_t>(g);
+        const double U = W0[1], V = W0[2], Wz = W0[3];
         double s2 = 0.0, s3 = 0.0;
-        for (int k = lane; k < n; k += 32) {
-            int r = k;
-            Rec x;
-            if (r < nfb) x = fs[lo + r].rec;
-            else if ((r -= nfb) < Rn) x = in[Rend - 1 - r];
-            else if ((r -= Rn) < Sn) x = in[Sa + r];
-            else if ((r -= Sn) < Ln) x = in[La + r];
-            else { r -= Ln; x = fs[mid + r].rec; }
-            const double cx = static_cast<double>(x.u) - U, cy = static_cast<double>(x.v) - V,
-                         cz = static_cast<double>(x.w) - Wz;
-            s2 += cx * cx;
-            s3 += cx * (0.5 * (cx * cx + cy * cy + cz * cz));
+        for (int k0 = lane; k0 < n; k0 += 32 * kIn) {
+            Rec x[kIn];
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                const int r = k0 + 32 * u;
+                if (r >= n) break;
+                x[u] = ld_rec(arrived_ptr<Rec>(r, h, in, fs));
+            }
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                if (k0 + 32 * u >= n) break;
+                const double cx = x[u].u - U, cy = x[u].v - V, cz = x[u].w - Wz;
+                s2 += cx * cx;
+                s3 += cx * (0.5 * (cx * cx + cy * cy + cz * cz));
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             s3 += __shfl_xor_sync(0xffffffffu, s3, o);
         }
-        const double rho_p = static_cast<double>(n) * I.mp_over_dx;
-        pi = I.mp_over_dx * s2 - rho_p * I.R * T;
+        if (lane == 0) { tmp[g].s[0] = s2; tmp[g].s[1] = s3; }
+    }
+}
+
+__global__ void k_sh_finish(EngineDev E, int fp32, int g0, int ncell, const ShCell *tmp, int accumulate, double *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncell) return;
+    const int g = g0 + t;
+    int b, i;
+    if (!sh_interior(E, g, b, i)) return;
+    double pi = 0.0, q = 0.0;
+    if (E.valid[g]) {
+        const InstDev &I = E.inst[b];
+        double s2, s3;
+        if (fp32) {
+            const float *o = reinterpret_cast<const float *>(tmp[g].s);
+            s2 = static_cast<double>(o[0]) + static_cast<double>(o[1]);
+            s3 = static_cast<double>(o[2]) + static_cast<double>(o[3]);
+        } else {
+            s2 = tmp[g].s[0];
+            s3 = tmp[g].s[1];
+        }
+        const double rho_p = static_cast<double>(E.hdr[g].n_in) * I.mp_over_dx;
+        pi = I.mp_over_dx * s2 - rho_p * I.R * E.prim[5 * static_cast<int64_t>(g) + 4];
         q = I.mp_over_dx * s3;
         CeCell m;
         ce_coefs(I, E.prim, E.valid, g, i, m);   // sets the stress and heat flux of a usable cell
@@ -1794,14 +1863,12 @@ __global__ void k_stress_heat(EngineDev E, int rp, int g0, int ncell, int accumu
         pi += wgt * m.sxx;
         q += wgt * m.qx;
     }
-    if (lane == 0) {
-        if (accumulate) {
-            out[g] += pi;
-            out[E.G + g] += q;
-        } else {
-            out[g] = pi;
-            out[E.G + g] = q;
-        }
+    if (accumulate) {
+        out[g] += pi;
+        out[E.G + g] += q;
+    } else {
+        out[g] = pi;
+        out[E.G + g] = q;
     }
 }
 
@@ -1841,6 +1908,7 @@ size_t stream_smem_bytes(int fp32, int threads)
 {
     return static_cast<size_t>(threads / 32) * (fp32 ? sizeof(StreamShared<RecF>) : sizeof(StreamShared<RecD>));
 }
+size_t stress_tmp_bytes() { return sizeof(ShCell); }
 size_t collide_smem_bytes(int fp32)
 {
     return (fp32 ? sizeof(CollideShared<RecF>) : sizeof(CollideShared<RecD>)) * (kCollideThreads / 32);
@@ -1952,12 +2020,16 @@ cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStr
 }
 
 cudaError_t launch_stress_heat(const EngineDev &E, int fp32, int rp, int g0, int ncell, int accumulate, double *out,
-                               cudaStream_t s)
+                               void *tmp, cudaStream_t s)
 {
     if (ncell <= 0) return cudaSuccess;
-    const int grid = (ncell + 3) / 4;
-    if (fp32) k_stress_heat<RecF><<<grid, 128, 0, s>>>(E, rp, g0, ncell, accumulate, out);
-    else k_stress_heat<RecD><<<grid, 128, 0, s>>>(E, rp, g0, ncell, accumulate, out);
+    ShCell *t = static_cast<ShCell *>(tmp);
+    const int gt = (ncell + 255) / 256;
+    if (fp32) k_sh_split<<<gt, 256, 0, s>>>(E, g0, ncell, t);
+    const int gw = (ncell + 3) / 4;   // one warp per cell
+    if (fp32) k_sh_sums<RecF><<<gw, 128, 0, s>>>(E, rp, g0, ncell, t);
+    else k_sh_sums<RecD><<<gw, 128, 0, s>>>(E, rp, g0, ncell, t);
+    k_sh_finish<<<gt, 256, 0, s>>>(E, fp32, g0, ncell, t, accumulate, out);
     return cudaGetLastError();
 }
 

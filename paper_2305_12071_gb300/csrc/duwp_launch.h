@@ -36,9 +36,11 @@ cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const do
 cudaError_t launch_moments(const EngineDev &E, int which, const int64_t *d_base, int64_t total, double *d_out,
                            cudaStream_t s);
 // Normal stress and heat flux (Eq. gkt_moment1) of the interior cells among g0 .. g0 + ncell - 1:
-// out[g] and out[G + g] written (accumulate = 0) or added to (accumulate = 1).
+// out[g] and out[G + g] written (accumulate = 0) or added to (accumulate = 1).  tmp: device scratch
+// of stress_tmp_bytes() per flattened cell (G of them).
 cudaError_t launch_stress_heat(const EngineDev &E, int fp32, int rp, int g0, int ncell, int accumulate, double *out,
-                               cudaStream_t s);
+                               void *tmp, cudaStream_t s);
+size_t stress_tmp_bytes();
 // Gather the stable sorted particle list of instance b into device arrays (debug/inspection).
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
                           int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s);
