@@ -271,9 +271,9 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_fmaj = c.take<double>(G);
     const size_t o_flux = c.take<double>(5 * size_t(G));
     const size_t o_avg = c.take<double>(5 * size_t(G));
-    const size_t o_AL = c.take<double>(4 * size_t(G));
-    const size_t o_AR = c.take<double>(4 * size_t(G));
-    const size_t o_As = c.take<double>(5 * size_t(G));
+    const size_t o_AL = c.take<int64_t>(4 * size_t(G));
+    const size_t o_AR = c.take<int64_t>(4 * size_t(G));
+    const size_t o_As = c.take<int64_t>(5 * size_t(G));
     const size_t o_slots = c.take<int32_t>(G);
     const size_t o_cnt = c.take<int32_t>(G);
     size_t o_nL[2], o_nS[2], o_nR[2], o_off[2];
@@ -323,9 +323,9 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.fmaj = reinterpret_cast<double *>(base + o_fmaj);
     dev.flux = reinterpret_cast<double *>(base + o_flux);
     dev.avg = reinterpret_cast<double *>(base + o_avg);
-    dev.AL = reinterpret_cast<double *>(base + o_AL);
-    dev.AR = reinterpret_cast<double *>(base + o_AR);
-    dev.Aself = reinterpret_cast<double *>(base + o_As);
+    dev.AL = reinterpret_cast<int64_t *>(base + o_AL);
+    dev.AR = reinterpret_cast<int64_t *>(base + o_AR);
+    dev.Aself = reinterpret_cast<int64_t *>(base + o_As);
     dev.slots = reinterpret_cast<int32_t *>(base + o_slots);
     dev.cnt = reinterpret_cast<int32_t *>(base + o_cnt);
     for (int p = 0; p < 2; ++p) {

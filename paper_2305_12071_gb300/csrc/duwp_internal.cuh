@@ -115,8 +115,11 @@ struct EngineDev {
     double *fmaj;              // G: (c_max / c_ref)^{-2 upsilon} of the current c_max
     double *flux;              // G x 5: wave flux at the interface between g and g+1
     double *avg;               // G x 5: time-average accumulator of Psi_t
-    double *AL, *AR;           // G x 4: sums (u, v, w, |xi|^2/2) of the L / R runs (post-transport)
-    double *Aself;             // G x 5: change of the cell's own particle moments (leavers, reflections)
+    // exact fixed-point sums written by the streaming kernel (velocities x 2^40, |xi|^2/2 x 2^32),
+    // converted to double by the cell kernel
+    int64_t *AL, *AR;          // G x 4: sums (u, v, w, |xi|^2/2) of the L / R runs (post-transport)
+    int64_t *Aself;            // G x 5: change of the cell's own particle moments (leavers,
+                               // reflections); [0] the count
     int32_t *slots;            // G: upper bound of the cell's list after re-sampling (this step)
     int32_t *slotsb[2];        // G: the bound each output block was written with, per buffer (block = 2 x bound)
     int32_t *cnt;              // G: particles arriving in the cell (list length this step)

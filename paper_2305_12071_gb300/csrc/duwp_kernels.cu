@@ -1170,8 +1170,8 @@ __device__ __forceinline__ long long warp_sum_ll(long long x)
 __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int wp)
 {
     const int lane = threadIdx.x & 31;
-    if (lane < 4) { E.AL[4 * g + lane] = 0.0; E.AR[4 * g + lane] = 0.0; }
-    if (lane < 5) E.Aself[5 * g + lane] = 0.0;
+    if (lane < 4) { E.AL[4 * g + lane] = 0; E.AR[4 * g + lane] = 0; }
+    if (lane < 5) E.Aself[5 * g + lane] = 0;
     if (lane == 0) {
         E.nL[wp][g] = 0; E.nS[wp][g] = 0; E.nR[wp][g] = 0; E.slotsb[wp][g] = 0;
         E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0;
@@ -1322,13 +1322,12 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
     }
     const int ngone = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(st.ngone));
     if (lane < 4) {
-        const double sc = (lane == 3) ? 0x1p-32 : 0x1p-40;
-        E.AL[4 * g + lane] = static_cast<double>(lj) * sc;
-        E.AR[4 * g + lane] = static_cast<double>(rj) * sc;
-        E.Aself[5 * g + 1 + lane] = static_cast<double>(gj - lj - rj) * sc;
+        E.AL[4 * g + lane] = lj;
+        E.AR[4 * g + lane] = rj;
+        E.Aself[5 * g + 1 + lane] = gj - lj - rj;
     }
     if (lane == 0) {
-        E.Aself[5 * g] = -static_cast<double>(ngone + nLr + nRr);
+        E.Aself[5 * g] = -static_cast<int64_t>(ngone + nLr + nRr);
         E.nS[wp][g] = st.oS;
         E.nL[wp][g] = nLr;
         E.nR[wp][g] = nRr;
@@ -1445,10 +1444,14 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                 const int arrivals = hd.Rn + hd.Sn + hd.Ln + farn;
                 double *psi = E.psi + 5 * g;
                 if (update) {
-                    const double *aR = E.AR + 4 * (g - 1), *aL = E.AL + 4 * (g + 1), *aS = E.Aself + 5 * g;
+                    const int64_t *aR = E.AR + 4 * (g - 1), *aL = E.AL + 4 * (g + 1), *aS = E.Aself + 5 * g;
                     double dp[5];
-                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + aS[0];
-                    for (int k = 0; k < 4; ++k) dp[k + 1] = aR[k] + aL[k] + fsum[k] + aS[k + 1];
+                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + static_cast<double>(aS[0]);
+                    for (int k = 0; k < 4; ++k) {
+                        const double sc = (k == 3) ? 0x1p-32 : 0x1p-40;
+                        dp[k + 1] = static_cast<double>(aR[k]) * sc + static_cast<double>(aL[k]) * sc + fsum[k] +
+                                    static_cast<double>(aS[k + 1]) * sc;
+                    }
                     const double *Fl = E.flux + 5 * (g - 1), *Fr = E.flux + 5 * g;
                     for (int k = 0; k < 5; ++k) {
                         const double fp = I.mp_over_dx * dp[k];
@@ -1659,8 +1662,8 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     E.cell_inst[g] = b;
     const int i = g - I.cell_base - 1;
     for (int p = 0; p < 2; ++p) { E.nL[p][g] = 0; E.nS[p][g] = 0; E.nR[p][g] = 0; E.off[p][g] = 0; E.slotsb[p][g] = 0; }
-    for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0.0; E.AR[4 * g + k] = 0.0; }
-    for (int k = 0; k < 5; ++k) { E.Aself[5 * g + k] = 0.0; E.avg[5 * g + k] = 0.0; E.flux[5 * g + k] = 0.0; E.psi[5 * g + k] = 0.0; E.prim[5 * g + k] = 0.0; }
+    for (int k = 0; k < 4; ++k) { E.AL[4 * g + k] = 0; E.AR[4 * g + k] = 0; }
+    for (int k = 0; k < 5; ++k) { E.Aself[5 * g + k] = 0; E.avg[5 * g + k] = 0.0; E.flux[5 * g + k] = 0.0; E.psi[5 * g + k] = 0.0; E.prim[5 * g + k] = 0.0; }
     E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0; E.cnt[g] = 0; E.slots[g] = 0; E.valid[g] = 0; E.P[g] = 0.0; E.cmax[g] = 0.0; E.fmaj[g] = 1.0;
     if (i < 0 || i >= I.C) return;
     const double xc = x_min + (static_cast<double>(i) + 0.5) * I.dx;
