@@ -112,6 +112,7 @@ enum { ORA_EPS1 = 0, ORA_EPS12 = 1, ORA_EPS0 = 2, ORA_EPS_AVG = 3 };
 enum { ORA_FLUX_GKS_EQ = 0, ORA_FLUX_KFVS = 1 };
 enum { ORA_NTC_PARTICLE = 0, ORA_NTC_TOTAL = 1 };
 enum { ORA_RESAMPLE_MAXWELL = 0, ORA_RESAMPLE_CE = 1 };
+enum { ORA_SPLIT_P = 0, ORA_SPLIT_QMC = 1 };
 
 typedef struct {
     double gamma, Pr, R;
@@ -128,6 +129,7 @@ typedef struct {
     uint64_t seed;
     int32_t avg_start;
     int32_t resample_mode;
+    int32_t split_mode;
 } ora_params;
 
 typedef struct {
@@ -220,11 +222,15 @@ static double mu_of_T(const ora_params *p, const ora_consts *c, double T)
     return c->mu_ref * pow(T / p->T_ref, p->omega);
 }
 
-/* Absorption fraction, Eq. (p): P = 0 for dt <= tau, 1 - tau/dt otherwise; tau = mu/p. */
+/* Absorption fraction, Eq. (p): P = 0 for dt <= tau, 1 - tau/dt otherwise; tau = mu/p.
+ * split_mode QMC (Sec. 3.2, the multi-scale Boltzmann equation solved by quantified model
+ * competition): a particle collides during dt, and joins the wave, with probability
+ * 1 - exp(-dt/tau). */
 static double pfrac(const ora_params *p, const ora_consts *c, const ora_prim *q)
 {
     if (!q->valid) return 0.0;
     double tau = mu_of_T(p, c, q->T) / (q->rho * p->R * q->T);
+    if (p->split_mode == ORA_SPLIT_QMC) return -expm1(-(c->dt / tau));
     if (c->dt <= tau) return 0.0;
     return 1.0 - tau / c->dt;
 }
@@ -269,7 +275,8 @@ void ora_half_moments(double U, double lam, double Mp[4], double Mm[4])
  * Maxwellian and the left-going half of the right one (GKS_EQ), or the flux is the
  * split kinetic flux of the two halves (KFVS); the NS viscous and heat-flux terms use
  * mu_e = eps * mu(T0) and one-sided differences of the neighbouring cell states; the
- * whole wave flux is weighted by P_f = max(0, 1 - tau_f/dt) at the interface state.
+ * whole wave flux is weighted by P_f = max(0, 1 - tau_f/dt) at the interface state
+ * (split_mode QMC: by 1 - exp(-dt/tau_f), the weight of Sec. 3.3's flux at t = dt).
  * Returns the flux per unit area (mass, x/y/z momentum, energy). */
 static void wave_flux(const ora_params *p, const ora_consts *c, const ora_prim *L, const ora_prim *Rr,
                       int viscous_ok, double F[5])
@@ -297,8 +304,13 @@ static void wave_flux(const ora_params *p, const ora_consts *c, const ora_prim *
     double p0 = rho0 * p->R * T0;
     double mu0 = mu_of_T(p, c, T0);
     double tauf = mu0 / p0;
-    if (c->dt <= tauf) return;                 /* P_f = 0: no wave flux (DSMC regime) */
-    double Pf = 1.0 - tauf / c->dt;
+    double Pf;
+    if (p->split_mode == ORA_SPLIT_QMC) {
+        Pf = -expm1(-(c->dt / tauf));          /* the flux of Sec. 3.3 at t = dt */
+    } else {
+        if (c->dt <= tauf) return;             /* P_f = 0: no wave flux (DSMC regime) */
+        Pf = 1.0 - tauf / c->dt;
+    }
 
     double Fe[5];
     if (p->flux_mode == ORA_FLUX_KFVS) {
