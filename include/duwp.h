@@ -65,6 +65,7 @@ enum { DUWP_EPS1 = 0, DUWP_EPS12 = 1, DUWP_EPS0 = 2, DUWP_EPS_AVG = 3 }; /* Sec.
 enum { DUWP_FLUX_GKS_EQ = 0, DUWP_FLUX_KFVS = 1 };           /* wave-flux form */
 enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the NTC count */
 enum { DUWP_RESAMPLE_MAXWELL = 0, DUWP_RESAMPLE_CE = 1 };    /* velocity law of re-sampled particles */
+enum { DUWP_SPLIT_P = 0, DUWP_SPLIT_QMC = 1 };              /* wave/particle split fraction */
 
 /*
  * Problem parameters of one instance (Sec. 4 and Appendix A; units nondimensional):
@@ -92,7 +93,13 @@ enum { DUWP_RESAMPLE_MAXWELL = 0, DUWP_RESAMPLE_CE = 1 };    /* velocity law of 
  *                       wave from central differences of the neighbouring cells and the viscosity
  *                       eps mu of the flux; drawn by acceptance-rejection against 1 + 30 B, B the
  *                       largest normalised stress or heat flux; Maxwellian where B > 1/4 and in the
- *                       inflow reservoirs).
+ *                       inflow reservoirs);
+ *   split_mode          the split fraction of Step 2 and the weight of the wave flux (Step 3):
+ *                       DUWP_SPLIT_P (default, Eq. p: P = max(0, 1 - tau/dt), the flux weighted by
+ *                       max(0, 1 - tau_f/dt)) or DUWP_SPLIT_QMC (the multi-scale Boltzmann
+ *                       equation's quantified model competition, Sec. 3.2: particles collide --
+ *                       are absorbed into the wave -- with probability 1 - exp(-dt/tau), and the
+ *                       flux of Sec. 3.3 at t = dt is weighted by 1 - exp(-dt/tau_f)).
  * In a batch all instances must use the same precision.
  */
 typedef struct {
@@ -111,6 +118,7 @@ typedef struct {
     uint64_t capacity;
     int32_t avg_start;
     int32_t resample_mode;
+    int32_t split_mode;
 } duwp_params;
 
 /* Device allocator callbacks: alloc returns device memory of `bytes` bytes usable on `stream`

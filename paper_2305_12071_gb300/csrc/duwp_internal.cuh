@@ -52,6 +52,7 @@ struct InstDev {
     double inv_rho_ref;
     float dtdx_f;
     int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
+    int32_t split_mode;     // 0: Eq. (p), 1: 1 - exp(-dt/tau) (quantified model competition)
     double left[5], right[5];   // reservoir primitive states (rho, u, v, w, T)
 };
 
@@ -226,6 +227,11 @@ __device__ __forceinline__ float tau_estimate(const InstDev &I, float rho, float
 __device__ inline double split_fraction(const InstDev &I, const double *q, bool ok)
 {
     if (!ok) return 0.0;
+    if (I.split_mode == 1) {
+        // Sec. 3.2: a particle collides during the step with probability 1 - exp(-dt/tau)
+        const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
+        return -expm1(-(I.dt / tau));
+    }
     const float t32 = tau_estimate(I, static_cast<float>(q[0]), static_cast<float>(q[4]));
     if (t32 > 1.01f * static_cast<float>(I.dt) && q[0] > 1e-30 && q[4] > 1e-30 && q[4] < 1e30) return 0.0;
     const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
@@ -333,7 +339,7 @@ __device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, co
 {
     for (int k = 0; k < 5; ++k) F[k] = 0.0;
     // P_f = 0 (no wave flux) is decided in single precision when tau_f exceeds dt by over 5%
-    if (flux_is_zero_estimate(I, a, aok, b, bok)) return;
+    if (I.split_mode == 0 && flux_is_zero_estimate(I, a, aok, b, bok)) return;
     double ap[4] = {0, 0, 0, 0}, an[4] = {0, 0, 0, 0}, bp[4] = {0, 0, 0, 0}, bn[4] = {0, 0, 0, 0};
     double la = 0.0, lb = 0.0, ra = 0.0, rb = 0.0, ta = 0.0, tb = 0.0;
     if (aok) {
@@ -362,8 +368,13 @@ __device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, co
     const double p0 = rho0 * I.R * T0;
     const double mu0 = viscosity(I, T0);
     const double tauf = mu0 / p0;
-    if (I.dt <= tauf) return;
-    const double Pf = 1.0 - tauf / I.dt;
+    double Pf;
+    if (I.split_mode == 1) {
+        Pf = -expm1(-(I.dt / tauf));                 // the flux of Sec. 3.3 at t = dt
+    } else {
+        if (I.dt <= tauf) return;
+        Pf = 1.0 - tauf / I.dt;
+    }
     double G[5];
     if (I.flux_mode == 1) {
         G[0] = ra * ap[1] + rb * bn[1];

@@ -24,6 +24,7 @@ EPS = {"eps1": 0, "eps12": 1, "eps0": 2, "eps_avg": 3}
 FLUX = {"gks_eq": 0, "kfvs": 1}
 NTC = {"particle": 0, "total": 1}
 RESAMPLE = {"maxwell": 0, "ce": 1}
+SPLIT = {"p": 0, "qmc": 1}
 
 # Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
 EXPORTS = (
@@ -65,6 +66,7 @@ class Params(C.Structure):
         ("capacity", C.c_uint64),
         ("avg_start", C.c_int32),
         ("resample_mode", C.c_int32),
+        ("split_mode", C.c_int32),
     ]
 
 
@@ -176,6 +178,7 @@ def make_params(p: dict) -> Params:
     s.capacity = int(p.get("capacity", 0))
     s.avg_start = int(p.get("avg_start", 0))
     s.resample_mode = RESAMPLE[p.get("resample_mode", "maxwell")]
+    s.split_mode = SPLIT[p.get("split_mode", "p")]
     return s
 
 

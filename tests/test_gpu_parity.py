@@ -92,6 +92,27 @@ def test_resample_mode_is_validated():
     h = C.c_void_p()
     assert L.duwp_init(C.byref(prm), None, duwp.ALLOC_FN(0), duwp.FREE_FN(0), None, C.byref(h)) == -1
     assert not h.value
+    prm = duwp.make_params(dict(W.config1("fp64"), n_cells=20))
+    prm.split_mode = 2
+    assert L.duwp_init(C.byref(prm), None, duwp.ALLOC_FN(0), duwp.FREE_FN(0), None, C.byref(h)) == -1
+    assert not h.value
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_qmc_split(precision):
+    # split_mode qmc (Sec. 3.2/3.3): every usable cell has P = 1 - exp(-dt/tau) > 0 (absorption and
+    # re-sampling everywhere) and every interface carries a weighted wave flux
+    p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=11, split_mode="qmc")
+    q = dict(W.config1(precision), split_mode="qmc")   # the Mach-3 shock, where Eq. (p) gives P = 0
+    if precision == "fp64":
+        _run_pair(p, [1, 3, 20], REL64, REL64)
+        _run_pair(q, [1, 5, 12], REL64, REL64)
+    else:
+        _run_pair(p, [1, 5], REL32, REL64)
+        _run_pair(q, [1, 4], REL32, REL64)
+    o = O.Oracle(q)
+    o.step(2)
+    assert np.all(o.prim()["P"] > 0) and o.counters()["nabs"].sum() > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
