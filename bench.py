@@ -144,7 +144,10 @@ def kernel_source_hash() -> str:
 
 def profiled_traffic(workload_name: str, updates_per_launch: float):
     """DRAM bytes per launch of the streaming kernel from the committed ncu summary, when it was
-    taken on the current kernel source; scaled by the particle-updates of a launch."""
+    taken on the current kernel source and on this workload (the 64-instance batch, Eq. (p) split);
+    scaled by the particle-updates of a launch."""
+    if workload_name != "batch64":
+        return None, None
     path = os.path.join(ROOT, "profiles", "k_stream_ncu.md")
     try:
         txt = open(path).read()
@@ -178,6 +181,27 @@ def oracle_sample(params_list, sample_idx, min_steps: int = 2, budget_s: float =
         rounds += 1
     dt = time.perf_counter() - t0
     return updates, dt, rounds
+
+
+def _oracle_worker(job):
+    """One process of the all-cores oracle line: oracle_sample on one instance."""
+    params, budget_s = job
+    ups, secs, rounds = oracle_sample([params], [0], budget_s=budget_s)
+    return ups, secs, rounds
+
+
+def oracle_all_cores(params_list, budget_s: float = 10.0):
+    """The oracle on every host core at once: one process per instance (the oracle itself is
+    single-threaded and instances are independent), each timed like oracle_sample.  Processes
+    are spawned (this process already uses the GPU).  Returns (updates, seconds, processes):
+    seconds the longest worker's timed span."""
+    import multiprocessing as mp
+    ncores = max(1, min(os.cpu_count() or 1, len(params_list)))
+    step = max(1, len(params_list) // ncores)
+    jobs = [(params_list[i], budget_s) for i in range(0, len(params_list), step)][:ncores]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    return sum(r[0] for r in res), max(r[1] for r in res), len(jobs)
 
 
 # ---------------------------------------------------------------------------- serving
@@ -282,6 +306,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "serve"])
+    ap.add_argument("--split", default="p", choices=["p", "qmc"],
+                    help="split fraction: Eq. (p) (default) or the QMC variant 1 - exp(-dt/tau)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of --workload serve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -315,6 +341,9 @@ def main():
 
     torch.cuda.set_device(local)
     plist, cfg = workload(args.workload, rank)
+    if args.split != "p":
+        plist = [dict(q, split_mode=args.split) for q in plist]
+        cfg = dict(cfg, split_mode=args.split)
     if args.instances:
         plist = plist[:args.instances]
         cfg = dict(cfg, instances=len(plist), workload=cfg["workload"] + f"_first{len(plist)}")
@@ -402,7 +431,7 @@ def main():
         k_ms = kms[1] / args.steps
         peak, peak_kind = measured_peaks()
         achieved = rec_bytes * 2 * upl / (k_ms * 1e-3) / 1e9
-        traffic, per_upd = profiled_traffic(args.workload, upl)
+        traffic, per_upd = profiled_traffic(args.workload if args.split == "p" else "", upl)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_stream",
                 "algorithmic_bytes_per_update": rec_bytes * 2, "updates_per_launch": upl,
@@ -508,6 +537,14 @@ def main():
         if ups is not None:
             out["cpu_baseline"] = {"value": ups / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": sample, "seconds": secs}
+            # second line: the same oracle on every host core, one process per instance
+            aups, asecs, nproc = oracle_all_cores(plist)
+            out["cpu_baseline_all_cores"] = {
+                "value": aups / asecs, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                "sample": f"{nproc} instances of the batch, one single-threaded oracle process each, "
+                          f"1 untimed + at least 2 timed steps and about 10 s each; value = all their "
+                          f"particle-updates / the longest process's timed span",
+                "seconds": asecs}
         else:
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     if out is not None:

@@ -87,6 +87,42 @@ __host__ __device__ __forceinline__ ds ds_sqrt(ds a)
     const float r = (((a.hi - y2.hi) - y2.lo) + a.lo) / (2.0f * y);
     return ds_fast_two_sum(y, r);
 }
+// v 2^-frac as the nearest double (ties to even), by integer operations only: the same value as
+// static_cast<double>(v) * 2^-frac for |v| < 2^63 and results in the normal range, without the
+// double-precision units (few on this part).
+__host__ __device__ __forceinline__ double fixed_to_double(int64_t v, int frac)
+{
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? (1ull << 63) : 0ull;
+    const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+#ifdef __CUDA_ARCH__
+    const int msb = 63 - __clzll(static_cast<long long>(a));
+#else
+    const int msb = 63 - __builtin_clzll(a);
+#endif
+    int e = msb;
+    uint64_t m;
+    if (msb <= 52) {
+        m = a << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        m = a >> sh;
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1ull;
+            if (m == (1ull << 53)) { m >>= 1; e += 1; }
+        }
+    }
+    const uint64_t bits = sign | (static_cast<uint64_t>(e + 1023 - frac) << 52) | (m & ((1ull << 52) - 1ull));
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(static_cast<long long>(bits));
+#else
+    double d;
+    std::memcpy(&d, &bits, 8);
+    return d;
+#endif
+}
+
 // double-single value of a double (hi the nearest float, lo the nearest float to the rest)
 __host__ __device__ __forceinline__ ds ds_of_double(double x)
 {

@@ -1446,11 +1446,11 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
                 if (update) {
                     const int64_t *aR = E.AR + 4 * (g - 1), *aL = E.AL + 4 * (g + 1), *aS = E.Aself + 5 * g;
                     double dp[5];
-                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + static_cast<double>(aS[0]);
+                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + fixed_to_double(aS[0], 0);
                     for (int k = 0; k < 4; ++k) {
-                        const double sc = (k == 3) ? 0x1p-32 : 0x1p-40;
-                        dp[k + 1] = static_cast<double>(aR[k]) * sc + static_cast<double>(aL[k]) * sc + fsum[k] +
-                                    static_cast<double>(aS[k + 1]) * sc;
+                        const int fr = (k == 3) ? 32 : 40;
+                        dp[k + 1] = fixed_to_double(aR[k], fr) + fixed_to_double(aL[k], fr) + fsum[k] +
+                                    fixed_to_double(aS[k + 1], fr);
                     }
                     const double *Fl = E.flux + 5 * (g - 1), *Fr = E.flux + 5 * g;
                     for (int k = 0; k < 5; ++k) {

@@ -53,3 +53,18 @@ def test_ds_maxwell_matches_double_precision(tmp_path):
     fp_exp = float(line.split("max 2^")[2])
     assert ds_exp < -44.0 and fp_exp < -48.0, line
     assert float(log_rel) < 2.0 ** -44, r.stdout      # -log(1 - u) against long double
+
+
+def test_fixed_to_double_is_the_rounded_conversion(tmp_path):
+    # the exact fixed-point particle sums reach the cell update through fixed_to_double: it must be
+    # bit for bit the double-precision conversion (round to nearest even) times the power of two
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "fixed_to_double_check")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, os.path.join(HERE, "fixed_to_double_check.cu"), "-o", exe],
+                   check=True, capture_output=True)
+    r = subprocess.run([exe, "2000000"], capture_output=True, text=True)
+    tot, bad = map(int, r.stdout.split()[-2:])
+    assert r.returncode == 0 and bad == 0 and tot > 2000000, r.stdout
+
