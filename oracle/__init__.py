@@ -32,6 +32,7 @@ FLUX = {"gks_eq": 0, "kfvs": 1}
 NTC = {"particle": 0, "total": 1}
 RESAMPLE = {"maxwell": 0, "ce": 1}
 SPLIT = {"p": 0, "qmc": 1}
+RECON = {"first": 0, "vanleer": 1}
 
 
 class _State(C.Structure):
@@ -55,6 +56,7 @@ class _Params(C.Structure):
         ("avg_start", C.c_int32),
         ("resample_mode", C.c_int32),
         ("split_mode", C.c_int32),
+        ("recon_mode", C.c_int32),
     ]
 
 
@@ -111,6 +113,7 @@ def lib():
         L.ora_get_consts.argtypes = [vp, P(d)]
         L.ora_get_prim.argtypes = [vp, P(d), P(d), P(d), P(d), P(i32)]
         L.ora_stress_heat.argtypes = [vp, P(d), P(d)]
+        L.ora_recon_pair.argtypes = [P(d), P(d), P(d), P(d), P(d), P(d)]
         L.ora_transport.argtypes = [vp, i64, P(d), P(d)]; L.ora_transport.restype = i64
         L.ora_ce_sample.argtypes = [P(_Params), P(d), P(d), P(d), u32, u32, u32, u32, i64, P(d), P(d)]
         _lib = L
@@ -151,6 +154,7 @@ def make_params(p: dict) -> _Params:
     s.avg_start = int(p.get("avg_start", 0))
     s.resample_mode = RESAMPLE[p.get("resample_mode", "maxwell")]
     s.split_mode = SPLIT[p.get("split_mode", "p")]
+    s.recon_mode = RECON[p.get("recon_mode", "first")]
     return s
 
 
@@ -173,6 +177,14 @@ def ce_sample(params: dict, Wm, W0, Wp, key=(7, 11), cell_id: int = 1, step: int
     lib().ora_ce_sample(C.byref(pr), arr(Wm), arr(W0), arr(Wp), key[0], key[1], cell_id, step, n,
                         xi.ctypes.data_as(C.POINTER(C.c_double)), coef)
     return list(coef), xi.reshape(n, 3)
+
+
+def recon_pair(Wm, W0, W1, W2):
+    """Reconstructed (van Leer) interface states between primitive states W0 and W1."""
+    a = [np.ascontiguousarray(x, np.float64) for x in (Wm, W0, W1, W2)]
+    L, R = np.empty(5), np.empty(5)
+    lib().ora_recon_pair(*[_ptr(x, C.c_double) for x in a], _ptr(L, C.c_double), _ptr(R, C.c_double))
+    return L, R
 
 
 def u53(a: int, b: int) -> float:

@@ -113,6 +113,7 @@ enum { ORA_FLUX_GKS_EQ = 0, ORA_FLUX_KFVS = 1 };
 enum { ORA_NTC_PARTICLE = 0, ORA_NTC_TOTAL = 1 };
 enum { ORA_RESAMPLE_MAXWELL = 0, ORA_RESAMPLE_CE = 1 };
 enum { ORA_SPLIT_P = 0, ORA_SPLIT_QMC = 1 };
+enum { ORA_RECON_FIRST = 0, ORA_RECON_VANLEER = 1 };
 
 typedef struct {
     double gamma, Pr, R;
@@ -130,6 +131,7 @@ typedef struct {
     int32_t avg_start;
     int32_t resample_mode;
     int32_t split_mode;
+    int32_t recon_mode;
 } ora_params;
 
 typedef struct {
@@ -274,12 +276,13 @@ void ora_half_moments(double U, double lam, double Mp[4], double Mm[4])
  * interface equilibrium W0 is built from the right-going half of the left
  * Maxwellian and the left-going half of the right one (GKS_EQ), or the flux is the
  * split kinetic flux of the two halves (KFVS); the NS viscous and heat-flux terms use
- * mu_e = eps * mu(T0) and one-sided differences of the neighbouring cell states; the
+ * mu_e = eps * mu(T0) and one-sided differences of the neighbouring cell states (GL, GR: the
+ * cell states, also when L and R are reconstructed interface states); the
  * whole wave flux is weighted by P_f = max(0, 1 - tau_f/dt) at the interface state
  * (split_mode QMC: by 1 - exp(-dt/tau_f), the weight of Sec. 3.3's flux at t = dt).
  * Returns the flux per unit area (mass, x/y/z momentum, energy). */
 static void wave_flux(const ora_params *p, const ora_consts *c, const ora_prim *L, const ora_prim *Rr,
-                      int viscous_ok, double F[5])
+                      const ora_prim *GL, const ora_prim *GR, int viscous_ok, double F[5])
 {
     for (int k = 0; k < 5; ++k) F[k] = 0.0;
     double MpL[4] = { 0, 0, 0, 0 }, MmL[4] = { 0, 0, 0, 0 };
@@ -327,15 +330,15 @@ static void wave_flux(const ora_params *p, const ora_consts *c, const ora_prim *
         Fe[3] = m0 * W0;
         Fe[4] = U0 * (E0 + p0);
     }
-    if (viscous_ok && L->valid && Rr->valid) {
+    if (viscous_ok && GL->valid && GR->valid) {
         double x = c->dt / tauf;
         double eps = ora_eps(p->eps_mode, x);
         double mue = eps * mu0;
         double kape = 2.5 * p->R * mue / p->Pr;
-        double dU = (Rr->u - L->u) / c->dx;
-        double dV = (Rr->v - L->v) / c->dx;
-        double dW = (Rr->w - L->w) / c->dx;
-        double dT = (Rr->T - L->T) / c->dx;
+        double dU = (GR->u - GL->u) / c->dx;
+        double dV = (GR->v - GL->v) / c->dx;
+        double dW = (GR->w - GL->w) / c->dx;
+        double dT = (GR->T - GL->T) / c->dx;
         double txx = (4.0 / 3.0) * mue * dU;
         double txy = mue * dV;
         double txz = mue * dW;
@@ -355,7 +358,57 @@ void ora_wave_flux(const ora_params *p, const double WL[5], const double WR[5], 
     ora_prim L = { WL[0], WL[1], WL[2], WL[3], WL[4], 0 }, Rr = { WR[0], WR[1], WR[2], WR[3], WR[4], 0 };
     L.valid = (L.rho > 0.0 && L.T > 0.0);
     Rr.valid = (Rr.rho > 0.0 && Rr.T > 0.0);
-    wave_flux(p, &c, &L, &Rr, viscous_ok, F);
+    wave_flux(p, &c, &L, &Rr, &L, &Rr, viscous_ok, F);
+}
+
+/* Second-order wave reconstruction (recon_mode = VANLEER; reading): per primitive variable
+ * (rho, U, V, W, T) the van Leer limited slope s = 2 dl dr / (dl + dr) where the one-sided
+ * differences dl, dr have the same sign, else 0; the interface between cells 0 and 1 sees
+ * W0 + s0/2 on the left and W1 - s1/2 on the right.  use0 / use1 = 0: that cell's slope is 0 (a
+ * reservoir or mirror cell, or an unusable neighbour).  If a reconstructed state has rho <= 0 or
+ * T <= 0 the interface keeps the cell states. */
+static void vl_slopes(const ora_prim *a, const ora_prim *b, const ora_prim *cc, double s[5])
+{
+    const double qa[5] = { a->rho, a->u, a->v, a->w, a->T };
+    const double qb[5] = { b->rho, b->u, b->v, b->w, b->T };
+    const double qc[5] = { cc->rho, cc->u, cc->v, cc->w, cc->T };
+    for (int k = 0; k < 5; ++k) {
+        double dl = qb[k] - qa[k], dr = qc[k] - qb[k];
+        s[k] = (dl * dr > 0.0) ? (2.0 * dl * dr) / (dl + dr) : 0.0;
+    }
+}
+
+static void recon_pair(const ora_prim *Wm, const ora_prim *W0, const ora_prim *W1, const ora_prim *W2, int use0,
+                       int use1, ora_prim *LR, ora_prim *RR)
+{
+    *LR = *W0;
+    *RR = *W1;
+    if (!W0->valid || !W1->valid) return;
+    double s0[5] = { 0, 0, 0, 0, 0 }, s1[5] = { 0, 0, 0, 0, 0 };
+    if (use0 && Wm->valid) vl_slopes(Wm, W0, W1, s0);
+    if (use1 && W2->valid) vl_slopes(W0, W1, W2, s1);
+    ora_prim a = *W0, b = *W1;
+    a.rho = W0->rho + 0.5 * s0[0]; a.u = W0->u + 0.5 * s0[1]; a.v = W0->v + 0.5 * s0[2];
+    a.w = W0->w + 0.5 * s0[3]; a.T = W0->T + 0.5 * s0[4];
+    b.rho = W1->rho - 0.5 * s1[0]; b.u = W1->u - 0.5 * s1[1]; b.v = W1->v - 0.5 * s1[2];
+    b.w = W1->w - 0.5 * s1[3]; b.T = W1->T - 0.5 * s1[4];
+    if (a.rho > 0.0 && a.T > 0.0 && b.rho > 0.0 && b.T > 0.0) { *LR = a; *RR = b; }
+}
+
+/* exported for the pin tests: the reconstructed interface states between W0 and W1 */
+void ora_recon_pair(const double Wm5[5], const double W05[5], const double W15[5], const double W25[5],
+                    double WL[5], double WR[5])
+{
+    ora_prim q[4];
+    const double *src[4] = { Wm5, W05, W15, W25 };
+    for (int j = 0; j < 4; ++j) {
+        q[j].rho = src[j][0]; q[j].u = src[j][1]; q[j].v = src[j][2]; q[j].w = src[j][3]; q[j].T = src[j][4];
+        q[j].valid = (q[j].rho > 0.0 && q[j].T > 0.0);
+    }
+    ora_prim a, b;
+    recon_pair(&q[0], &q[1], &q[2], &q[3], 1, 1, &a, &b);
+    WL[0] = a.rho; WL[1] = a.u; WL[2] = a.v; WL[3] = a.w; WL[4] = a.T;
+    WR[0] = b.rho; WR[1] = b.u; WR[2] = b.v; WR[3] = b.w; WR[4] = b.T;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -804,7 +857,29 @@ int ora_step(void *vh, int32_t nsteps)
                 L = W[f - 1];
                 Rr = W[f];
             }
-            wave_flux(p, c, &L, &Rr, 1, F + 5 * f);
+            ora_prim LR = L, RR = Rr;
+            if (p->recon_mode == ORA_RECON_VANLEER) {
+                /* the states beyond L and R, and whether L and R are cells with a slope */
+                const int per = (p->bc_left == ORA_BC_PERIODIC);
+                ora_prim Wm, W2;
+                memset(&Wm, 0, sizeof Wm);
+                memset(&W2, 0, sizeof W2);
+                int use0 = per || f - 1 >= 0, use1 = per || f < C;
+                if (use0) {
+                    int j = f - 2;
+                    if (j >= 0) Wm = W[j];
+                    else if (per) Wm = W[(j + C) % C];
+                    else Wm = ghost_prim(h, 0, &W[0]);
+                }
+                if (use1) {
+                    int j = f + 1;
+                    if (j < C) W2 = W[j];
+                    else if (per) W2 = W[j % C];
+                    else W2 = ghost_prim(h, 1, &W[C - 1]);
+                }
+                recon_pair(&Wm, &L, &Rr, &W2, use0, use1, &LR, &RR);
+            }
+            wave_flux(p, c, &LR, &RR, &L, &Rr, 1, F + 5 * f);
         }
         if (p->bc_left == ORA_BC_PERIODIC) {
             /* the two boundary interfaces are the same interface */
