@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "serve"])
     ap.add_argument("--split", default="p", choices=["p", "qmc"],
                     help="split fraction: Eq. (p) (default) or the QMC variant 1 - exp(-dt/tau)")
+    ap.add_argument("--recon", default="first", choices=["first", "vanleer"],
+                    help="wave-flux interface states: first order (default) or van Leer reconstruction")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of --workload serve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -344,6 +346,9 @@ def main():
     if args.split != "p":
         plist = [dict(q, split_mode=args.split) for q in plist]
         cfg = dict(cfg, split_mode=args.split)
+    if args.recon != "first":
+        plist = [dict(q, recon_mode=args.recon) for q in plist]
+        cfg = dict(cfg, recon_mode=args.recon)
     if args.instances:
         plist = plist[:args.instances]
         cfg = dict(cfg, instances=len(plist), workload=cfg["workload"] + f"_first{len(plist)}")
@@ -431,7 +436,7 @@ def main():
         k_ms = kms[1] / args.steps
         peak, peak_kind = measured_peaks()
         achieved = rec_bytes * 2 * upl / (k_ms * 1e-3) / 1e9
-        traffic, per_upd = profiled_traffic(args.workload if args.split == "p" else "", upl)
+        traffic, per_upd = profiled_traffic(args.workload if (args.split, args.recon) == ("p", "first") else "", upl)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_stream",
                 "algorithmic_bytes_per_update": rec_bytes * 2, "updates_per_launch": upl,

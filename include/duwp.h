@@ -66,6 +66,7 @@ enum { DUWP_FLUX_GKS_EQ = 0, DUWP_FLUX_KFVS = 1 };           /* wave-flux form *
 enum { DUWP_NTC_PARTICLE = 0, DUWP_NTC_TOTAL = 1 };          /* density in the NTC count */
 enum { DUWP_RESAMPLE_MAXWELL = 0, DUWP_RESAMPLE_CE = 1 };    /* velocity law of re-sampled particles */
 enum { DUWP_SPLIT_P = 0, DUWP_SPLIT_QMC = 1 };              /* wave/particle split fraction */
+enum { DUWP_RECON_FIRST = 0, DUWP_RECON_VANLEER = 1 };       /* wave-flux interface states */
 
 /*
  * Problem parameters of one instance (Sec. 4 and Appendix A; units nondimensional):
@@ -99,7 +100,13 @@ enum { DUWP_SPLIT_P = 0, DUWP_SPLIT_QMC = 1 };              /* wave/particle spl
  *                       max(0, 1 - tau_f/dt)) or DUWP_SPLIT_QMC (the multi-scale Boltzmann
  *                       equation's quantified model competition, Sec. 3.2: particles collide --
  *                       are absorbed into the wave -- with probability 1 - exp(-dt/tau), and the
- *                       flux of Sec. 3.3 at t = dt is weighted by 1 - exp(-dt/tau_f)).
+ *                       flux of Sec. 3.3 at t = dt is weighted by 1 - exp(-dt/tau_f));
+ *   recon_mode          interface states of the wave flux: DUWP_RECON_FIRST (default, the two
+ *                       cell states) or DUWP_RECON_VANLEER (second order: per primitive variable
+ *                       the van Leer limited slope 2 dl dr / (dl + dr) of each cell, zero at
+ *                       extrema and in reservoir / mirror cells, the interface seeing each cell's
+ *                       state plus or minus half its slope; the NS gradients still from the cell
+ *                       states).
  * In a batch all instances must use the same precision.
  */
 typedef struct {
@@ -119,6 +126,7 @@ typedef struct {
     int32_t avg_start;
     int32_t resample_mode;
     int32_t split_mode;
+    int32_t recon_mode;
 } duwp_params;
 
 /* Device allocator callbacks: alloc returns device memory of `bytes` bytes usable on `stream`

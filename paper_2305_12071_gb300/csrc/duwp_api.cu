@@ -58,6 +58,7 @@ int derive_instance(const duwp_params &p, HostInst &o)
         return DUWP_EINVAL;
     if (p.resample_mode != DUWP_RESAMPLE_MAXWELL && p.resample_mode != DUWP_RESAMPLE_CE) return DUWP_EINVAL;
     if (p.split_mode != DUWP_SPLIT_P && p.split_mode != DUWP_SPLIT_QMC) return DUWP_EINVAL;
+    if (p.recon_mode != DUWP_RECON_FIRST && p.recon_mode != DUWP_RECON_VANLEER) return DUWP_EINVAL;
     if (!(p.dt > 0.0) && !(p.cfl > 0.0)) return DUWP_EINVAL;
 
     o.p = p;
@@ -71,6 +72,7 @@ int derive_instance(const duwp_params &p, HostInst &o)
     d.ntc_rate = p.ntc_rate;
     d.resample_mode = p.resample_mode;
     d.split_mode = p.split_mode;
+    d.recon_mode = p.recon_mode;
     d.active = 1;
     d.key0 = static_cast<uint32_t>(p.seed & 0xffffffffu);
     d.key1 = static_cast<uint32_t>(p.seed >> 32);

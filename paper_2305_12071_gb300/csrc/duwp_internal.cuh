@@ -53,6 +53,7 @@ struct InstDev {
     float dtdx_f;
     int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
     int32_t split_mode;     // 0: Eq. (p), 1: 1 - exp(-dt/tau) (quantified model competition)
+    int32_t recon_mode;     // 0: first-order wave states, 1: van Leer limited reconstruction
     double left[5], right[5];   // reservoir primitive states (rho, u, v, w, T)
 };
 
@@ -295,6 +296,36 @@ __device__ inline void half_moments(double U, double lam, double *pos, double *n
     neg[3] = U * neg[2] + 2.0 * h * neg[1];
 }
 
+// Second-order wave reconstruction (recon_mode 1): per primitive variable the van Leer limited
+// slope 2 dl dr / (dl + dr) where the one-sided differences agree in sign, else 0; the interface
+// between cells 0 and 1 sees w0 + s0/2 and w1 - s1/2 (use0 / use1 false: that cell has no slope,
+// being a reservoir or mirror cell); the cell states are kept if either side would lose rho > 0 or
+// T > 0.  Same expressions, in the same order, as the double-precision checker.
+__device__ inline void vl_slopes(const double *qa, const double *qb, const double *qc, double *s)
+{
+    for (int k = 0; k < 5; ++k) {
+        const double dl = qb[k] - qa[k], dr = qc[k] - qb[k];
+        s[k] = (dl * dr > 0.0) ? (2.0 * dl * dr) / (dl + dr) : 0.0;
+    }
+}
+
+__device__ inline void recon_pair(const double *wm, bool okm, const double *w0, bool ok0, const double *w1, bool ok1,
+                                  const double *w2, bool ok2, bool use0, bool use1, double *L, double *R)
+{
+    for (int k = 0; k < 5; ++k) { L[k] = w0[k]; R[k] = w1[k]; }
+    if (!ok0 || !ok1) return;
+    double s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};
+    if (use0 && okm) vl_slopes(wm, w0, w1, s0);
+    if (use1 && ok2) vl_slopes(w0, w1, w2, s1);
+    double a[5], b[5];
+    for (int k = 0; k < 5; ++k) {
+        a[k] = w0[k] + 0.5 * s0[k];
+        b[k] = w1[k] - 0.5 * s1[k];
+    }
+    if (a[0] > 0.0 && a[4] > 0.0 && b[0] > 0.0 && b[4] > 0.0)
+        for (int k = 0; k < 5; ++k) { L[k] = a[k]; R[k] = b[k]; }
+}
+
 // Wave flux through the interface between a left state a and a right state b (per unit area):
 // interface equilibrium from the colliding half-Maxwellians, Euler flux of it (or the split
 // kinetic flux), NS stress and heat flux with mu_e = eps mu(T0), weighted by
@@ -334,8 +365,10 @@ __device__ inline bool flux_is_zero_estimate(const InstDev &I, const double *a, 
     return t32 > 1.05f * static_cast<float>(I.dt);
 }
 
+// ga, gb: the cell states whose difference gives the NS gradients (a, b themselves unless a and b
+// are reconstructed interface states).
 __device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, const double *b, bool bok,
-                                 double *F)
+                                 double *F, const double *ga, const double *gb)
 {
     for (int k = 0; k < 5; ++k) F[k] = 0.0;
     // P_f = 0 (no wave flux) is decided in single precision when tau_f exceeds dt by over 5%
@@ -393,13 +426,13 @@ __device__ inline void wave_flux(const InstDev &I, const double *a, bool aok, co
         const double mue = eps_factor(I.eps_mode, I.dt / tauf) * mu0;
         const double kap = 2.5 * I.R * mue / I.Pr;
         const double inv = 1.0 / I.dx;
-        const double sxx = (4.0 / 3.0) * mue * ((b[1] - a[1]) * inv);
-        const double sxy = mue * ((b[2] - a[2]) * inv);
-        const double sxz = mue * ((b[3] - a[3]) * inv);
+        const double sxx = (4.0 / 3.0) * mue * ((gb[1] - ga[1]) * inv);
+        const double sxy = mue * ((gb[2] - ga[2]) * inv);
+        const double sxz = mue * ((gb[3] - ga[3]) * inv);
         G[1] -= sxx;
         G[2] -= sxy;
         G[3] -= sxz;
-        G[4] -= U0 * sxx + V0 * sxy + W0 * sxz + kap * ((b[4] - a[4]) * inv);
+        G[4] -= U0 * sxx + V0 * sxy + W0 * sxz + kap * ((gb[4] - ga[4]) * inv);
     }
     for (int k = 0; k < 5; ++k) F[k] = Pf * G[k];
 }

@@ -1641,7 +1641,39 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             cok = ghost_prim(I, 1, a, aok, c);
         }
     }
-    wave_flux(I, a, aok, c, cok, E.flux + 5 * g);
+    if (I.recon_mode == 1) {
+        // the states beyond a and c, as the flux sees them, and whether a and c have slopes
+        const bool use0 = periodic || i >= 0, use1 = periodic || i + 1 < I.C;
+        const int g0 = I.cell_base + 1;            // local cell 0
+        double wm[5] = {0, 0, 0, 0, 0}, w2[5] = {0, 0, 0, 0, 0};
+        bool okm = false, ok2 = false;
+        if (use0) {
+            const int j = i - 1;
+            if (j >= 0 || periodic) {
+                const int gj = g0 + ((j + I.C) % I.C);
+                for (int k = 0; k < 5; ++k) wm[k] = E.prim[5 * gj + k];
+                okm = E.valid[gj] != 0;
+            } else {
+                okm = ghost_prim(I, 0, E.prim + 5 * g0, E.valid[g0] != 0, wm);
+            }
+        }
+        if (use1) {
+            const int j = i + 2;
+            if (j < I.C || periodic) {
+                const int gj = g0 + (j % I.C);
+                for (int k = 0; k < 5; ++k) w2[k] = E.prim[5 * gj + k];
+                ok2 = E.valid[gj] != 0;
+            } else {
+                const int gl2 = g0 + I.C - 1;
+                ok2 = ghost_prim(I, 1, E.prim + 5 * gl2, E.valid[gl2] != 0, w2);
+            }
+        }
+        double aR[5], cR[5];
+        recon_pair(wm, okm, a, aok, c, cok, w2, ok2, use0, use1, aR, cR);
+        wave_flux(I, aR, aok, cR, cok, E.flux + 5 * g, a, c);
+    } else {
+        wave_flux(I, a, aok, c, cok, E.flux + 5 * g, a, c);
+    }
     if (advance && i == -1) {
         const uint32_t nxt = I.step + 1u;
         if (static_cast<int64_t>(nxt) > static_cast<int64_t>(I.avg_start)) I.navg += 1;

@@ -25,6 +25,7 @@ FLUX = {"gks_eq": 0, "kfvs": 1}
 NTC = {"particle": 0, "total": 1}
 RESAMPLE = {"maxwell": 0, "ce": 1}
 SPLIT = {"p": 0, "qmc": 1}
+RECON = {"first": 0, "vanleer": 1}
 
 # Every symbol of include/duwp.h (checked by the CPU test-suite against the built library).
 EXPORTS = (
@@ -67,6 +68,7 @@ class Params(C.Structure):
         ("avg_start", C.c_int32),
         ("resample_mode", C.c_int32),
         ("split_mode", C.c_int32),
+        ("recon_mode", C.c_int32),
     ]
 
 
@@ -179,6 +181,7 @@ def make_params(p: dict) -> Params:
     s.avg_start = int(p.get("avg_start", 0))
     s.resample_mode = RESAMPLE[p.get("resample_mode", "maxwell")]
     s.split_mode = SPLIT[p.get("split_mode", "p")]
+    s.recon_mode = RECON[p.get("recon_mode", "first")]
     return s
 
 
