@@ -55,6 +55,13 @@ def workload(name: str, rank: int = 0):
         p["seed"] = 1 + 100_000 * rank
         return [p], {"workload": "sod_1000cells_kn1e-4_fp32", "instances": 1, "cells": 1000, "ppc_ref": 500,
                      "records": "fp32", "cell_state": "fp64"}
+    if name == "sod_sweep":
+        # the paper's Sod Kn sweep (Sec. 4.2, Fig. 5): 100 cells, Kn 1e-5 .. 1e-2, many seeds at once
+        kns = (1e-5, 1e-4, 1e-3, 1e-2)
+        ps = [W.sod(n_cells=100, Kn=kn, ppc_ref=500.0, precision="fp32", seed=1 + s + 100_000 * rank)
+              for kn in kns for s in range(16)]
+        return ps, {"workload": "sod_sweep_100cells_kn1e-5..1e-2_x16_fp32", "instances": len(ps), "cells": 100,
+                    "ppc_ref": 500, "Kn": list(kns), "records": "fp32", "cell_state": "fp64"}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -305,7 +312,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "serve"])
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "sod_sweep", "serve"])
     ap.add_argument("--split", default="p", choices=["p", "qmc"],
                     help="split fraction: Eq. (p) (default) or the QMC variant 1 - exp(-dt/tau)")
     ap.add_argument("--recon", default="first", choices=["first", "vanleer"],
