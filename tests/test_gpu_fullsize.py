@@ -45,3 +45,26 @@ def test_full_batch_sampled_instances_and_invariants():
         assert g.info(b)["steps_done"] == steps, b
     assert total > 1.0e8
     g.close()
+
+
+def test_mach8_single_instance_invariants():
+    # the 1e8-particle Mach-8 shock (1e5 cells): too large for the oracle, so properties that hold at
+    # any size -- a usable state everywhere, the counters consistent, the far fields at the
+    # Rankine-Hugoniot states the instance starts from, the particle load of about 1e8
+    from paper_2305_12071_gb300 import workloads as W
+    plist, _ = bench.workload("mach8", 0)
+    p = plist[0]
+    g = solver(plist)
+    g.set_launch(128, 1)
+    g.step(3)
+    f = g.fields(0)[0]
+    assert np.all(np.isfinite(f)) and np.all(f[:, 0] > 0)
+    c = g.counters(0)
+    assert np.all(c["ncand"] >= c["nacc"]) and np.all(c["nacc"] >= 0) and np.all(c["nabs"] == 0)
+    m = g.moments(0)
+    r2, _, t2 = W.rankine_hugoniot(8.0)
+    up, down = m["rho"][:1000].mean(), m["rho"][-1000:].mean()
+    assert abs(up / p["left"][0] - 1.0) < 0.01 and abs(down / (p["left"][0] * r2) - 1.0) < 0.01, (up, down)
+    assert abs(m["T"][-1000:].mean() / (p["left"][4] * t2) - 1.0) < 0.01
+    assert 0.9e8 < g.num_particles(0) < 1.2e8
+    g.close()
