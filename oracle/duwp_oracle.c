@@ -18,9 +18,12 @@
  *      the per-cell particle moments, wave flux by an NS solver, and the
  *      conservative update Eq. (r1)                                  (Step 3)
  *
- * Readings of points the paper leaves open (wave-flux scheme, flux weight,
- * rounding of particle counts, boundary handling, RNG layout) are listed in
- * the design notes of the repository; each one is marked "reading" below.
+ * Points the paper leaves open are each taken one way and marked "reading"
+ * where they are implemented: the wave-flux scheme of Step 3 (Sec. 3.3 names
+ * only "N-S solvers"), its weight (Eq. p applied at the interface state), the
+ * rounding of particle counts (Step 2), the boundary handling (Sec. 4 gives
+ * none) and the counter layout of the random numbers (the paper draws them
+ * without specifying a generator).
  *
  * Precision: all arithmetic is FP64.  With `fp32 = 1` the particle record
  * (cell-local position and velocity) is STORED in single precision: every
