@@ -308,13 +308,14 @@ int duwp_checkpoint_restore(duwp_handle *h, const void *host_buf, uint64_t bytes
  * duwp_get_particles, into caller-owned DEVICE arrays of n entries (n = duwp_num_particles):
  * cell index, cell-local position, velocity.  Asynchronous on the handle's stream; a count that
  * differs from n is recorded on the device and reported by the next synchronizing call
- * (DUWP_EOVERFLOW), and nothing is written then.  Allocates nothing, on the device or the host:
- * the per-cell start table it needs is a static device array of DUWP_NOALLOC_MAX_CELLS entries
- * (2 MiB, held by every device that loads the library until the process exits); an instance with
- * more cells is rejected with DUWP_EINVAL.  The first call on a device looks that array's address
- * up and keeps it (make that first call before any stream capture).  All calls share the array
- * and each call overwrites it, so calls that overlap on the GPU (from other streams or handles)
- * race on it.  Errors: DUWP_EINVAL, DUWP_ECUDA. */
+ * (DUWP_EOVERFLOW), and the device arrays are then left untouched.  Allocates nothing, on the
+ * device or the host: the per-cell start table it needs is a static device array of
+ * DUWP_NOALLOC_MAX_CELLS + 1 entries (2 MiB, held by every device that loads the library until the
+ * process exits); an instance with more cells is rejected with DUWP_EINVAL.  The calling thread's
+ * current device must be the handle's (DUWP_EINVAL otherwise).  The first call on a device looks
+ * that array's address up and keeps it (make that first call before any stream capture).  All
+ * calls share the array and each call overwrites it, so calls that overlap on the GPU (from other
+ * streams or handles) race on it.  Errors: DUWP_EINVAL, DUWP_ECUDA. */
 #define DUWP_NOALLOC_MAX_CELLS 262144
 int duwp_get_particles_noalloc(duwp_handle *h, int32_t inst, int32_t *dev_cell, double *dev_xl,
                                double *dev_u, double *dev_v, double *dev_w, int64_t n);

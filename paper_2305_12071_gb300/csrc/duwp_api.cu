@@ -899,7 +899,7 @@ int duwp_get_particles(duwp_handle *h, int32_t b, int32_t *cell, double *xl, dou
     double *d_u = d_xl + nb, *d_v = d_u + nb, *d_w = d_v + nb;
     int32_t *d_cell = reinterpret_cast<int32_t *>(d_w + nb);
     cudaError_t e = cudaMemcpyAsync(d_start, start.data(), sizeof(int64_t) * size_t(C), cudaMemcpyHostToDevice, E.stream);
-    if (e == cudaSuccess) e = launch_gather(E.dev, E.fp32, E.parity, b, hi.cell_base + 1, C, d_start, np, d_cell, d_xl, d_u, d_v, d_w, E.stream);
+    if (e == cudaSuccess) e = launch_gather(E.dev, E.fp32, E.parity, b, hi.cell_base + 1, C, d_start, np, nullptr, d_cell, d_xl, d_u, d_v, d_w, E.stream);
     if (e == cudaSuccess && np > 0) {
         e = cudaMemcpyAsync(cell, d_cell, sizeof(int32_t) * size_t(np), cudaMemcpyDeviceToHost, E.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(xl, d_xl, sizeof(double) * size_t(np), cudaMemcpyDeviceToHost, E.stream);

@@ -1711,11 +1711,12 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
 // Gather of the stable sorted list of instance b (inspection).
 // ------------------------------------------------------------------------------------------
 template <typename Rec>
-__global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *start, int64_t total, int32_t *cell,
-                         double *xl, double *u, double *v, double *w)
+__global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *start, int64_t total, const int64_t *gate,
+                         int32_t *cell, double *xl, double *u, double *v, double *w)
 {
     const int t = blockIdx.x;
     if (t >= ncell) return;
+    if (gate && *gate != total) return;     // the count differs from the caller's size: write nothing
     const int g = g0 + t;
     const Rec *in = static_cast<const Rec *>(E.buf[rp]);
     const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
@@ -2091,12 +2092,13 @@ cudaError_t launch_moments(const EngineDev &E, int which, const int64_t *d_base,
 }
 
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
-                          int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s)
+                          int64_t total, const int64_t *gate, int32_t *cell, double *xl, double *u, double *v,
+                          double *w, cudaStream_t s)
 {
     (void)b;
     if (ncell <= 0) return cudaSuccess;
-    if (fp32) k_gather<RecF><<<ncell, 128, 0, s>>>(E, rp, g0, ncell, d_start, total, cell, xl, u, v, w);
-    else k_gather<RecD><<<ncell, 128, 0, s>>>(E, rp, g0, ncell, d_start, total, cell, xl, u, v, w);
+    if (fp32) k_gather<RecF><<<ncell, 128, 0, s>>>(E, rp, g0, ncell, d_start, total, gate, cell, xl, u, v, w);
+    else k_gather<RecD><<<ncell, 128, 0, s>>>(E, rp, g0, ncell, d_start, total, gate, cell, xl, u, v, w);
     return cudaGetLastError();
 }
 

@@ -42,8 +42,11 @@ cudaError_t launch_stress_heat(const EngineDev &E, int fp32, int rp, int g0, int
                                void *tmp, cudaStream_t s);
 size_t stress_tmp_bytes();
 // Gather the stable sorted particle list of instance b into device arrays (debug/inspection).
+// gate: NULL, or a device word that must equal `total` when the kernel runs (otherwise nothing is
+// written).
 cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, int ncell, const int64_t *d_start,
-                          int64_t total, int32_t *cell, double *xl, double *u, double *v, double *w, cudaStream_t s);
+                          int64_t total, const int64_t *gate, int32_t *cell, double *xl, double *u, double *v,
+                          double *w, cudaStream_t s);
 // Kernel attributes (dynamic shared memory) and blocks per SM of the streaming kernel.
 // variant 0: registers unconstrained (<= 128); 1: two 512-thread blocks per SM (<= 64 registers);
 // 2: three (<= 40 registers)

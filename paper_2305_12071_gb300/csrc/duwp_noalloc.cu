@@ -14,10 +14,11 @@
 
 using namespace duwp;
 
-// Start offset of every cell of the inspected instance.  Lives as long as the library is loaded, on
-// every device that loads it (2 MiB each).  Shared by all calls: each call overwrites the entries of
-// the cells it handles; calls that overlap on the GPU race on it.
-static __device__ __align__(256) int64_t g_cell_start[DUWP_NOALLOC_MAX_CELLS];
+// Start offset of every cell of the inspected instance, followed by the instance's particle count
+// (entry ncell).  Lives as long as the library is loaded, on every device that loads it (2 MiB each).
+// Shared by all calls: each call overwrites the entries of the cells it handles; calls that overlap
+// on the GPU race on it.
+static __device__ __align__(256) int64_t g_cell_start[DUWP_NOALLOC_MAX_CELLS + 1];
 
 namespace {
 
@@ -43,8 +44,9 @@ int start_table(int device, int64_t **out)
     return DUWP_OK;
 }
 
-// Exclusive scan of the per-cell particle counts of one instance into the start table (one block);
-// records an overflow if the total differs from the size the caller passed.
+// Exclusive scan of the per-cell particle counts of one instance into the start table (one block),
+// the total in start[ncell]; records an overflow if the total differs from the size the caller
+// passed (the gather that follows then writes nothing).
 __global__ void k_start_scan(EngineDev E, int g0, int ncell, int64_t *start, int64_t expect)
 {
     __shared__ int64_t s_w[32];
@@ -73,7 +75,10 @@ __global__ void k_start_scan(EngineDev E, int g0, int ncell, int64_t *start, int
         if (threadIdx.x == 0) s_carry = carry + tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && s_carry != expect) atomicCAS(E.err, 0, -7);
+    if (threadIdx.x == 0) {
+        start[ncell] = s_carry;
+        if (s_carry != expect) atomicCAS(E.err, 0, -7);
+    }
 }
 
 }  // namespace
@@ -88,20 +93,22 @@ extern "C" int duwp_get_particles_noalloc(duwp_handle *h, int32_t inst, int32_t 
     const int32_t C = hi.p.n_cells;
     if (C > DUWP_NOALLOC_MAX_CELLS) return DUWP_EINVAL;
     if (n < 0 || (n > 0 && (!dev_cell || !dev_xl || !dev_u || !dev_v || !dev_w))) return DUWP_EINVAL;
-    int device = 0;
+    // the table of the handle's device: the symbol's address is looked up with that device current
+    int device = -1;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) {
         set_cuda_error(e, "cudaGetDevice");
         return DUWP_ECUDA;
     }
+    if (device != E.device) return DUWP_EINVAL;
     int64_t *start = nullptr;
     const int rc = start_table(device, &start);
     if (rc != DUWP_OK) return rc;
     k_start_scan<<<1, 1024, 0, E.stream>>>(E.dev, hi.cell_base + 1, C, start, n);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = launch_gather(E.dev, E.fp32, E.parity, inst, hi.cell_base + 1, C, start, n, dev_cell, dev_xl, dev_u, dev_v,
-                          dev_w, E.stream);
+        e = launch_gather(E.dev, E.fp32, E.parity, inst, hi.cell_base + 1, C, start, n, start + C, dev_cell, dev_xl,
+                          dev_u, dev_v, dev_w, E.stream);
     if (e != cudaSuccess) {
         set_cuda_error(e, "duwp_get_particles_noalloc");
         return DUWP_ECUDA;

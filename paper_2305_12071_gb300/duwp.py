@@ -192,10 +192,12 @@ class _TorchAllocator:
         import torch
         self.torch = torch
         self.device = device
+        self.calls = 0          # allocations requested by the library so far
         self.alloc = ALLOC_FN(self._alloc)
         self.free = FREE_FN(self._free)
 
     def _alloc(self, nbytes, stream, ctx):
+        self.calls += 1
         try:
             return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
         except Exception:

@@ -1,7 +1,10 @@
-"""duwp_get_particles_noalloc: the allocation-free particle inspection for callers that cannot
-allocate device memory at that point (inside stream capture, or with a fixed arena handed over at
-set-up).  Through the C ABI it must give exactly what duwp_get_particles gives, on two calls in a
-row (the second call reuses the library's static start table left by the first)."""
+"""duwp_get_particles_noalloc: the particle inspection for callers that cannot allocate device
+memory when they inspect -- code running inside CUDA stream capture (an allocation there breaks the
+capture) and hosts that hand the library a fixed memory arena at set-up and forbid allocations
+afterwards.  Through the C ABI it must give exactly what duwp_get_particles gives, on two calls in a
+row (the second reuses the library's static start table left by the first), without asking the
+handle's allocator for anything; a size that differs from the particle count must leave the caller's
+arrays untouched, and an instance beyond the table's size is refused."""
 import numpy as np
 import pytest
 
@@ -11,22 +14,29 @@ from parity_util import solver
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_noalloc_particles_equal_get_particles(precision):
+def _out(n, fill=float("nan")):
     import torch
-    p = W.sod(n_cells=150, Kn=3e-4, ppc_ref=80, precision=precision, seed=21)
+    out = {"cell": torch.full((n,), -7, dtype=torch.int32, device="cuda")}
+    for k in ("xl", "u", "v", "w"):
+        out[k] = torch.full((n,), fill, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("precision,n_cells", [("fp32", 150), ("fp64", 150), ("fp32", 2500)])
+def test_noalloc_particles_equal_get_particles(precision, n_cells):
+    # 2500 cells: the start-table scan crosses 1024-cell tiles and ends in a ragged one
+    p = W.sod(n_cells=n_cells, Kn=3e-4, ppc_ref=80 if n_cells < 1000 else 12, precision=precision, seed=21)
     s = solver(p)
     s.step(4)
     for call in range(2):
         ref = s.particles()                      # the existing entry point, host arrays
         n = len(ref["cell"])
         assert n > 0
-        torch.cuda.synchronize()
-        out = {"cell": torch.empty(n, dtype=torch.int32, device="cuda")}
-        for k in ("xl", "u", "v", "w"):
-            out[k] = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
+        out = _out(n)
+        before = s._alloc.calls
         s.particles_noalloc(out)
+        assert s._alloc.calls == before          # no allocation requested during the call
         s.sync()
         for k in ref:
             got = out[k].cpu().numpy()
@@ -36,17 +46,27 @@ def test_noalloc_particles_equal_get_particles(precision):
     s.close()
 
 
-def test_noalloc_rejects_wrong_size():
-    import torch
+@pytest.mark.parametrize("delta", [5, -5])
+def test_noalloc_wrong_size_writes_nothing(delta):
     from paper_2305_12071_gb300 import duwp
-    s = solver(W.config1("fp32"))
+    s = solver(W.sod(n_cells=1500, Kn=3e-4, ppc_ref=12, precision="fp32", seed=3))
     s.step(2)
-    n = s.num_particles()
-    out = {"cell": torch.empty(n + 5, dtype=torch.int32, device="cuda")}
-    for k in ("xl", "u", "v", "w"):
-        out[k] = torch.empty(n + 5, dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
+    n = s.num_particles() + delta
+    out = _out(n, fill=12345.0)
     s.particles_noalloc(out)
     with pytest.raises(duwp.DuwpError):
         s.sync()
+    assert bool((out["cell"] == -7).all())
+    for k in ("xl", "u", "v", "w"):
+        assert bool((out[k] == 12345.0).all()), k
+    s.close()
+
+
+def test_noalloc_rejects_instances_beyond_the_table():
+    from paper_2305_12071_gb300 import duwp
+    s = solver(W.sod(n_cells=262_145, Kn=1e-2, ppc_ref=2, precision="fp32", seed=5))
+    out = _out(4)
+    with pytest.raises(duwp.DuwpError) as ei:
+        s.particles_noalloc(out)
+    assert ei.value.status == duwp.EINVAL
     s.close()
