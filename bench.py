@@ -36,37 +36,72 @@ UNIT = "particle-updates/s"
 
 
 # ---------------------------------------------------------------------------- workloads
-def workload(name: str, rank: int = 0):
+def _one_gpu_workload(name: str):
+    """The instances of one GPU's share of the workload and its description."""
     from paper_2305_12071_gb300 import workloads as W
     if name == "batch64":
         ps = W.config3_batch(64, precision="fp32")
-        for i, p in enumerate(ps):
-            p["seed"] = 1000 + i + 100_000 * rank
         return ps, {"workload": "batch64_shock_fp32", "instances": 64, "mach": "U[1.2,8]",
                     "cells": "U[100,4000]", "ppc_ref": "U[100,1000]", "omega": 0.81, "records": "fp32",
                     "cell_state": "fp64"}
     if name == "mach8":
-        p = W.config4("fp32")
-        p["seed"] = 4 + 100_000 * rank
-        return [p], {"workload": "mach8_shock_1e5cells_fp32", "instances": 1, "cells": 100_000, "Kn": 0.1,
-                     "ppc_ref": 415, "omega": 0.68, "records": "fp32", "cell_state": "fp64"}
+        return [W.config4("fp32")], {"workload": "mach8_shock_1e5cells_fp32", "instances": 1, "cells": 100_000,
+                                     "Kn": 0.1, "ppc_ref": 415, "omega": 0.68, "records": "fp32",
+                                     "cell_state": "fp64"}
+    if name == "mach8_fp64":
+        return [W.config4("fp64")], {"workload": "mach8_shock_1e5cells_fp64", "instances": 1, "cells": 100_000,
+                                     "Kn": 0.1, "ppc_ref": 415, "omega": 0.68, "records": "fp64",
+                                     "cell_state": "fp64"}
+    if name == "mach3":
+        return [W.config1("fp64")], {"workload": "mach3_shock_100cells_fp64", "instances": 1, "cells": 100,
+                                     "ppc_ref": 200, "omega": 0.81, "records": "fp64", "cell_state": "fp64"}
     if name == "sod":
-        p = W.config2(Kn=1e-4, precision="fp32")
-        p["seed"] = 1 + 100_000 * rank
-        return [p], {"workload": "sod_1000cells_kn1e-4_fp32", "instances": 1, "cells": 1000, "ppc_ref": 500,
-                     "records": "fp32", "cell_state": "fp64"}
+        return [W.config2(Kn=1e-4, precision="fp32")], {"workload": "sod_1000cells_kn1e-4_fp32", "instances": 1,
+                                                        "cells": 1000, "ppc_ref": 500, "records": "fp32",
+                                                        "cell_state": "fp64"}
+    if name == "sod_kn":
+        # the Sod tube's Kn range (1e-4 .. 1) as one batch: 5 Knudsen numbers x 5 seeds, 1000 cells each
+        kns = (1e-4, 1e-3, 1e-2, 1e-1, 1.0)
+        ps = [W.config2(Kn=kn, precision="fp32", seed=1 + s) for kn in kns for s in range(5)]
+        return ps, {"workload": "sod_1000cells_kn1e-4..1_x5seeds_fp32", "instances": len(ps), "cells": 1000,
+                    "ppc_ref": 500, "Kn": list(kns), "records": "fp32", "cell_state": "fp64"}
     if name == "sod_sweep":
         # the paper's Sod Kn sweep (Sec. 4.2, Fig. 5): 100 cells, Kn 1e-5 .. 1e-2, many seeds at once
         kns = (1e-5, 1e-4, 1e-3, 1e-2)
-        ps = [W.sod(n_cells=100, Kn=kn, ppc_ref=500.0, precision="fp32", seed=1 + s + 100_000 * rank)
+        ps = [W.sod(n_cells=100, Kn=kn, ppc_ref=500.0, precision="fp32", seed=1 + s)
               for kn in kns for s in range(16)]
         return ps, {"workload": "sod_sweep_100cells_kn1e-5..1e-2_x16_fp32", "instances": len(ps), "cells": 100,
                     "ppc_ref": 500, "Kn": list(kns), "records": "fp32", "cell_state": "fp64"}
     raise SystemExit(f"unknown workload {name}")
 
 
+def job(name: str, world: int = 1):
+    """The whole job on `world` GPUs: `world` copies of the one-GPU workload with independent seeds
+    (weak scaling), and its description."""
+    base, cfg = _one_gpu_workload(name)
+    plist = []
+    for c in range(world):
+        for p in base:
+            q = dict(p)
+            q["seed"] = int(p["seed"]) + 100_000 * c
+            plist.append(q)
+    return plist, cfg
+
+
+def workload(name: str, rank: int = 0, world: int = 1):
+    """The instances rank `rank` of `world` runs: whole instances of the job placed on the ranks by
+    their device-memory footprint (no exchange between ranks), and the job's description."""
+    from paper_2305_12071_gb300 import placement
+    plist, cfg = job(name, world)
+    mine = placement.assign(plist, world)[rank]
+    cfg = dict(cfg)
+    if world > 1:
+        cfg["placement"] = "whole instances by footprint (largest first, least-loaded rank)"
+    return [plist[i] for i in mine], cfg
+
+
 def shard(n_items: int, rank: int, world: int):
-    """Items of one rank when a batch is split across ranks (round robin)."""
+    """Items of one rank when a list is split across ranks (round robin)."""
     return list(range(rank, n_items, world))
 
 
@@ -312,7 +347,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "mach8", "sod", "sod_sweep", "serve"])
+    ap.add_argument("--workload", default="batch64",
+                    choices=["batch64", "mach8", "mach8_fp64", "mach3", "sod", "sod_kn", "sod_sweep", "serve"])
     ap.add_argument("--split", default="p", choices=["p", "qmc"],
                     help="split fraction: Eq. (p) (default) or the QMC variant 1 - exp(-dt/tau)")
     ap.add_argument("--recon", default="first", choices=["first", "vanleer"],
@@ -349,7 +385,7 @@ def main():
     from paper_2305_12071_gb300 import duwp
 
     torch.cuda.set_device(local)
-    plist, cfg = workload(args.workload, rank)
+    plist, cfg = workload(args.workload, rank, world)
     if args.split != "p":
         plist = [dict(q, split_mode=args.split) for q in plist]
         cfg = dict(cfg, split_mode=args.split)
@@ -448,7 +484,9 @@ def main():
                 "traffic": traffic, "kernel": "k_stream",
                 "algorithmic_bytes_per_update": rec_bytes * 2, "updates_per_launch": upl,
                 "launch_ms": k_ms, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
-        kernel_share = {n: float(v / max(kms[:5].sum(), 1e-30)) for n, v in zip(duwp.Solver.KERNELS, kms[:5])}
+        slots = duwp.Solver.KERNEL_SLOTS
+        ksum = max(sum(kms[i] for i in slots.values()), 1e-30)
+        kernel_share = {n: float(kms[i] / ksum) for n, i in slots.items()}
         cfg = dict(cfg)
         info0 = sol.info(0)
         cfg.update({"particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
@@ -463,7 +501,7 @@ def main():
                "data": "synthetic (seeded shock/Sod problems shaped like the paper's test cases)",
                "config": cfg, "clocks": clocks, "gpu_launches": 6 * args.steps,
                "step_ms_p50": p50, "step_ms_p99": p99, "serial_ms_per_step": serial_ms,
-               "kernel_ms_per_step": {n: float(v / args.steps) for n, v in zip(duwp.Solver.KERNELS, kms[:5])},
+               "kernel_ms_per_step": {n: float(kms[i] / args.steps) for n, i in slots.items()},
                "kernel_times": "from the same number of steps run kernel by kernel with events around each",
                "kernel_share": kernel_share, "roofline": roof,
                "readout": {"kernel": "k_sh_split + k_sh_sums + k_sh_finish", "what": "normal stress and heat flux of every cell",

@@ -116,6 +116,13 @@ def lib():
         L.ora_recon_pair.argtypes = [P(d), P(d), P(d), P(d), P(d), P(d)]
         L.ora_transport.argtypes = [vp, i64, P(d), P(d)]; L.ora_transport.restype = i64
         L.ora_ce_sample.argtypes = [P(_Params), P(d), P(d), P(d), u32, u32, u32, u32, i64, P(d), P(d)]
+        L.ora_set_range.argtypes = [vp, i32, i32]; L.ora_set_range.restype = C.c_int
+        L.ora_step_first_half.argtypes = [vp]; L.ora_step_first_half.restype = C.c_int
+        L.ora_outbox_count.argtypes = [vp]; L.ora_outbox_count.restype = i64
+        L.ora_outbox.argtypes = [vp, P(i32), P(d), P(d), P(d), P(d)]
+        L.ora_step_second_half.argtypes = [vp, i64, P(i32), P(d), P(d), P(d), P(d),
+                                           i64, P(i32), P(d), P(d), P(d), P(d)]
+        L.ora_step_second_half.restype = C.c_int
         _lib = L
     return _lib
 
@@ -350,7 +357,140 @@ class Oracle:
         lib().ora_stress_heat(self.h, _ptr(Pi, C.c_double), _ptr(Q, C.c_double))
         return {"Pi": Pi, "Q": Q}
 
+    # ---------------------------------------------------------------- domain decomposition
+    def set_range(self, c0: int, c1: int):
+        """Own only cells [c0, c1) (one part of a domain split; before the first step)."""
+        if lib().ora_set_range(self.h, int(c0), int(c1)) != 0:
+            raise ValueError("bad cell range")
+        self.c0, self.c1 = int(c0), int(c1)
+
+    def first_half(self):
+        """Step 1, Step 2 of the owned cells and the transport (Step 3) of their particles."""
+        if lib().ora_step_first_half(self.h) != 0:
+            raise RuntimeError("first half failed")
+
+    def outbox(self) -> dict:
+        """Transported particles whose new cell another part owns, in pre-transport order."""
+        n = int(lib().ora_outbox_count(self.h))
+        if n < 0:
+            raise RuntimeError("no first half taken")
+        cell = np.empty(n, np.int32)
+        xl, u, v, w = (np.empty(n, np.float64) for _ in range(4))
+        lib().ora_outbox(self.h, _ptr(cell, C.c_int32), _ptr(xl, C.c_double), _ptr(u, C.c_double),
+                         _ptr(v, C.c_double), _ptr(w, C.c_double))
+        return {"cell": cell, "xl": xl, "u": u, "v": v, "w": w}
+
+    def second_half(self, lo: dict, hi: dict):
+        """New particle lists of the owned cells from this part's transported particles and those
+        arriving from lower (lo) and higher (hi) parts, then the update of the owned cells."""
+        def args(d):
+            c = np.ascontiguousarray(d["cell"], np.int32)
+            a = [np.ascontiguousarray(d[k], np.float64) for k in ("xl", "u", "v", "w")]
+            return [len(c), _ptr(c, C.c_int32)] + [_ptr(x, C.c_double) for x in a], (c, a)
+        la, keep_lo = args(lo)
+        ha, keep_hi = args(hi)
+        if lib().ora_step_second_half(self.h, *la, *ha) != 0:
+            raise RuntimeError("second half failed (an arriving particle outside the owned range?)")
+
     def transport(self, cell: int, xl: float, u: float):
         x, uu = C.c_double(xl), C.c_double(u)
         d = lib().ora_transport(self.h, cell, C.byref(x), C.byref(uu))
         return int(d), x.value, uu.value
+
+
+# ---------------------------------------------------------------------------- domain decomposition
+def split_ranges(n_cells: int, parts: int):
+    """Contiguous cell ranges [c0, c1) of `parts` parts of nearly equal size."""
+    edges = [(n_cells * r) // parts for r in range(parts + 1)]
+    return [(edges[r], edges[r + 1]) for r in range(parts)]
+
+
+def halo_cells(n_cells: int, c0: int, c1: int, periodic: bool, width: int = 2):
+    """Cells outside [c0, c1) whose states the owned cells read: `width` on each side (the wave flux
+    with the second-order reconstruction reads two; the flux and the NS-corrected sampling one),
+    wrapping at periodic ends."""
+    out = []
+    for k in range(1, width + 1):
+        for c in (c0 - k, c1 - 1 + k):
+            if periodic:
+                c %= n_cells
+            if 0 <= c < n_cells and not (c0 <= c < c1) and c not in out:
+                out.append(c)
+    return out
+
+
+def route(outboxes, ranges, me: int):
+    """Particles arriving in part `me` from every part's outbox (outboxes[r], pre-transport order):
+    (from lower parts, from higher parts), each concatenated in part order."""
+    c0, c1 = ranges[me]
+    lo, hi = [], []
+    for r, box in enumerate(outboxes):
+        if r == me:
+            continue
+        sel = (box["cell"] >= c0) & (box["cell"] < c1)
+        piece = {k: v[sel] for k, v in box.items()}
+        (lo if r < me else hi).append(piece)
+
+    def cat(pieces):
+        if not pieces:
+            return {"cell": np.empty(0, np.int32), **{k: np.empty(0) for k in ("xl", "u", "v", "w")}}
+        return {k: np.concatenate([p[k] for p in pieces]) for k in pieces[0]}
+    return cat(lo), cat(hi)
+
+
+class DomainSplit:
+    """One instance split into `parts` contiguous cell ranges, each held by its own oracle instance
+    that owns only its cells: the host-rank emulation of a one-instance multi-GPU run.  Every step
+    exchanges the states of the cells next to each range (halo) before the first half and the
+    particles that cross into another range between the halves."""
+
+    def __init__(self, params: dict, parts: int):
+        self.C = int(params["n_cells"])
+        self.periodic = params.get("bc_left") == "periodic"
+        self.ranges = split_ranges(self.C, parts)
+        self.parts = []
+        for c0, c1 in self.ranges:
+            o = Oracle(params)
+            o.set_range(c0, c1)
+            self.parts.append(o)
+
+    def psi(self) -> np.ndarray:
+        full = np.zeros((self.C, 5))
+        for o, (c0, c1) in zip(self.parts, self.ranges):
+            full[c0:c1] = o.psi()[c0:c1]
+        return full
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            full = self.psi()
+            for o, (c0, c1) in zip(self.parts, self.ranges):
+                mine = o.psi()
+                view = np.zeros_like(mine)
+                view[c0:c1] = mine[c0:c1]
+                for c in halo_cells(self.C, c0, c1, self.periodic):
+                    view[c] = full[c]
+                o.set_psi(view)
+                o.first_half()
+            boxes = [o.outbox() for o in self.parts]
+            for me, o in enumerate(self.parts):
+                lo, hi = route(boxes, self.ranges, me)
+                o.second_half(lo, hi)
+
+    def particles(self) -> dict:
+        ps = [o.particles() for o in self.parts]
+        return {k: np.concatenate([p[k] for p in ps]) for k in ps[0]}
+
+    def counters(self) -> dict:
+        out = {k: np.zeros(self.C, np.int32) for k in ("ncand", "nacc", "nabs", "nnew")}
+        for o, (c0, c1) in zip(self.parts, self.ranges):
+            c = o.counters()
+            for k in out:
+                out[k][c0:c1] = c[k][c0:c1]
+        return out
+
+    def cmax(self) -> np.ndarray:
+        out = np.zeros(self.C)
+        for o, (c0, c1) in zip(self.parts, self.ranges):
+            out[c0:c1] = o.cmax()[c0:c1]
+        return out
+

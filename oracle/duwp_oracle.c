@@ -623,6 +623,11 @@ typedef struct {
     opart *lastpre;   /* pre-transport array of the last step (source cell in .cell) */
     int64_t *lastdest; /* destination cell of each entry, -1 = left the domain */
     int64_t nlastpre;
+    /* owned cell range [c0, c1): the whole domain, or one part of a domain decomposition (the
+     * other cells' states are only read, as the neighbours of the owned ones) */
+    int32_t c0, c1;
+    double *F;        /* (C+1) x 5 wave flux of the current step (faces c0..c1) */
+    int phase;        /* 1 between the two halves of a step */
 } ora_inst;
 
 static int grow(ora_inst *h, opart **arr, int64_t *cap, int64_t need)
@@ -679,6 +684,9 @@ void *ora_create(const ora_params *p)
     h->last_flux = (double *)calloc((size_t)(C + 1) * 5, sizeof(double));
     h->pre_m = (double *)calloc((size_t)C * 5, sizeof(double));
     h->post_m = (double *)calloc((size_t)C * 5, sizeof(double));
+    h->F = (double *)calloc((size_t)(C + 1) * 5, sizeof(double));
+    h->c0 = 0;
+    h->c1 = C;
     /* Step 1 initial state: Psi_t from the two-state profile (cell centres), Psi_p = 0 (reading). */
     for (int32_t i = 0; i < C; ++i) {
         double xc = p->x_min + ((double)i + 0.5) * h->c.dx;
@@ -696,7 +704,7 @@ void ora_destroy(void *vh)
     if (!h) return;
     free(h->psi); free(h->avg); free(h->cmax); free(h->parts);
     free(h->ncand); free(h->nacc); free(h->nabs); free(h->nnew);
-    free(h->last_flux); free(h->pre_m); free(h->post_m);
+    free(h->last_flux); free(h->pre_m); free(h->post_m); free(h->F);
     free(h->lastpre); free(h->lastdest);
     free(h);
 }
@@ -826,27 +834,34 @@ static int64_t n_resample(const ora_inst *h, uint32_t id, double P, double rho_w
     return (int64_t)floor(x + ora_u53(w[0], w[1]));
 }
 
-typedef struct { opart q; int64_t dest; } moved;
-
-int ora_step(void *vh, int32_t nsteps)
+/* One step is taken in two halves, so that a domain split into parts (each part owning a range
+ * of cells) can exchange the particles that cross into another part between them:
+ *   first half  -- Step 1 (total state, split fraction, wave flux of the faces of the owned cells),
+ *                  Step 2 of the owned cells (and of the inflow reservoirs at the domain's ends),
+ *                  free transport of the resulting pre-transport array (Step 3);
+ *   second half -- the owned cells' new particle lists (stable order by new cell; ties keep the
+ *                  pre-transport order, which is cell-major over the whole domain), the particle
+ *                  flux Eq. (fp), the conservative update Eq. (r1).
+ * A whole-domain instance takes both halves in ora_step with nothing exchanged. */
+static int step_first_half(ora_inst *h)
 {
-    ora_inst *h = (ora_inst *)vh;
     const ora_params *p = &h->p;
     const ora_consts *c = &h->c;
     int32_t C = h->C;
+    const int32_t c0 = h->c0, c1 = h->c1;
     ora_prim *W = (ora_prim *)malloc((size_t)C * sizeof(ora_prim));
     double *P = (double *)malloc((size_t)C * sizeof(double));
-    double *F = (double *)malloc((size_t)(C + 1) * 5 * sizeof(double));
+    double *F = h->F;
     int64_t *start = (int64_t *)malloc((size_t)(C + 1) * sizeof(int64_t));
-    if (!W || !P || !F || !start) { free(W); free(P); free(F); free(start); return -2; }
-    for (int32_t s = 0; s < nsteps; ++s) {
+    if (!W || !P || !start) { free(W); free(P); free(start); return -2; }
+    {
         /* Step 1: total state and the split fraction of every cell */
         for (int32_t i = 0; i < C; ++i) {
             W[i] = prim_of_cons(h->psi + 5 * i, p->R);
             P[i] = pfrac(p, c, &W[i]);
         }
-        /* wave flux at the C+1 interfaces from the start-of-step states */
-        for (int32_t f = 0; f <= C; ++f) {
+        /* wave flux at the faces of the owned cells from the start-of-step states */
+        for (int32_t f = c0; f <= c1; ++f) {
             ora_prim L, Rr;
             if (f == 0) {
                 Rr = W[0];
@@ -884,13 +899,13 @@ int ora_step(void *vh, int32_t nsteps)
             }
             wave_flux(p, c, &LR, &RR, &L, &Rr, 1, F + 5 * f);
         }
-        if (p->bc_left == ORA_BC_PERIODIC) {
+        if (p->bc_left == ORA_BC_PERIODIC && c0 == 0 && c1 == C) {
             /* the two boundary interfaces are the same interface */
             for (int k = 0; k < 5; ++k) F[5 * C + k] = F[k];
         }
-        memcpy(h->last_flux, F, (size_t)(C + 1) * 5 * sizeof(double));
+        memcpy(h->last_flux + 5 * c0, F + 5 * c0, (size_t)(c1 - c0 + 1) * 5 * sizeof(double));
 
-        /* cell starts in the sorted particle array */
+        /* cell starts in the sorted particle array (particles of the owned cells only) */
         for (int32_t i = 0; i <= C; ++i) start[i] = 0;
         for (int64_t q = 0; q < h->np; ++q) start[h->parts[q].cell + 1] += 1;
         for (int32_t i = 0; i < C; ++i) start[i + 1] += start[i];
@@ -901,7 +916,7 @@ int ora_step(void *vh, int32_t nsteps)
         int64_t npre = 0, cpre = 0;
         memset(h->pre_m, 0, (size_t)C * 5 * sizeof(double));
         /* left ghost reservoir (inflow boundary) */
-        if (p->bc_left == ORA_BC_INOUT) {
+        if (p->bc_left == ORA_BC_INOUT && c0 == 0) {
             ora_prim g = ghost_prim(h, 0, &W[0]);
             double Pg = pfrac(p, c, &g);
             int64_t ng = g.valid ? n_resample(h, 0u, Pg, g.rho) : 0;
@@ -912,7 +927,7 @@ int ora_step(void *vh, int32_t nsteps)
                 q->cell = -1;
             }
         }
-        for (int32_t i = 0; i < C; ++i) {
+        for (int32_t i = c0; i < c1; ++i) {
             int64_t n0 = start[i], n1 = start[i + 1];
             int64_t base = npre;
             if (grow(h, &pre, &cpre, npre + (n1 - n0))) return -2;
@@ -954,7 +969,7 @@ int ora_step(void *vh, int32_t nsteps)
             h->nnew[i] = (int32_t)nn;
             for (int64_t q = base; q < npre; ++q) add_phi(h->pre_m + 5 * i, pre + q);
         }
-        if (p->bc_right == ORA_BC_INOUT) {
+        if (p->bc_right == ORA_BC_INOUT && c1 == C) {
             ora_prim g = ghost_prim(h, 1, &W[C - 1]);
             double Pg = pfrac(p, c, &g);
             int64_t ng = g.valid ? n_resample(h, (uint32_t)(C + 1), Pg, g.rho) : 0;
@@ -967,68 +982,169 @@ int ora_step(void *vh, int32_t nsteps)
         }
 
         /* Step 3: free transport; particles leaving the domain are removed */
-        moved *mv = (moved *)malloc((size_t)(npre ? npre : 1) * sizeof(moved));
-        if (!mv) return -2;
+        int64_t *dest = (int64_t *)malloc((size_t)(npre ? npre : 1) * sizeof(int64_t));
+        opart *moved = (opart *)malloc((size_t)(npre ? npre : 1) * sizeof(opart));
+        if (!dest || !moved) { free(dest); free(moved); return -2; }
         int64_t nfar = 0;
         for (int64_t q = 0; q < npre; ++q) {
-            mv[q].q = pre[q];
-            mv[q].dest = transport(h, pre[q].cell, &mv[q].q);
-            if (mv[q].dest >= 0) {
-                int64_t d = mv[q].dest - pre[q].cell;
+            moved[q] = pre[q];
+            dest[q] = transport(h, pre[q].cell, &moved[q]);
+            if (dest[q] >= 0) {
+                int64_t d = dest[q] - pre[q].cell;
                 if (d < -1 || d > 1) ++nfar;
             }
         }
         h->nfar = nfar;
-        /* stable counting sort by the new cell: ties keep the pre-transport order */
-        int64_t *cnt = (int64_t *)calloc((size_t)C + 1, sizeof(int64_t));
-        for (int64_t q = 0; q < npre; ++q)
-            if (mv[q].dest >= 0) cnt[mv[q].dest + 1] += 1;
-        for (int32_t i = 0; i < C; ++i) cnt[i + 1] += cnt[i];
-        int64_t nkeep = cnt[C];
-        if (nkeep > h->cap) {
-            int64_t nc = h->cap ? h->cap : 1024;
-            while (nc < nkeep) nc *= 2;
-            opart *na = (opart *)realloc(h->parts, (size_t)nc * sizeof(opart));
-            if (!na) return -2;
-            h->parts = na;
-            h->cap = nc;
-        }
-        for (int64_t q = 0; q < npre; ++q) {
-            if (mv[q].dest < 0) continue;
-            int64_t pos = cnt[mv[q].dest]++;
-            h->parts[pos] = mv[q].q;
-            h->parts[pos].cell = (int32_t)mv[q].dest;
-        }
-        h->np = nkeep;
-        free(cnt);
         free(h->lastpre);
         free(h->lastdest);
-        h->lastpre = pre;
-        h->lastdest = (int64_t *)malloc((size_t)(npre ? npre : 1) * sizeof(int64_t));
-        if (!h->lastdest) return -2;
-        for (int64_t q = 0; q < npre; ++q) h->lastdest[q] = mv[q].dest;
+        h->lastpre = pre;          /* kept: the pre-transport array of this step */
+        h->lastdest = dest;
         h->nlastpre = npre;
-        free(mv);
+        /* the transported records wait in .cell-less form for the second half */
+        for (int64_t q = 0; q < npre; ++q) moved[q].cell = (int32_t)(dest[q] >= 0 ? dest[q] : -1);
+        free(h->parts);
+        h->parts = moved;
+        h->cap = npre ? npre : 1;
+        h->np = npre;
+    }
+    free(W); free(P); free(start);
+    h->phase = 1;
+    return 0;
+}
 
-        /* particle flux Eq. (fp) = change of the per-cell particle moments over the
-         * transport; wave flux by the NS solver; conservative update Eq. (r1) */
-        memset(h->post_m, 0, (size_t)C * 5 * sizeof(double));
-        for (int64_t q = 0; q < h->np; ++q) add_phi(h->post_m + 5 * h->parts[q].cell, h->parts + q);
-        for (int32_t i = 0; i < C; ++i) {
-            for (int k = 0; k < 5; ++k) {
-                double fp = c->mp_over_dx * (h->post_m[5 * i + k] - h->pre_m[5 * i + k]);
-                double fw = c->dtdx * (F[5 * (i + 1) + k] - F[5 * i + k]);
-                h->psi[5 * i + k] = h->psi[5 * i + k] + fp - fw;
-            }
-        }
-        h->step += 1;
-        if ((int64_t)h->step > (int64_t)p->avg_start) {
-            for (int64_t k = 0; k < (int64_t)C * 5; ++k) h->avg[k] += h->psi[k];
-            h->navg += 1;
+/* The transported records of the first half whose new cell lies outside the owned range, in
+ * pre-transport order (these go to the parts that own those cells). */
+static int outside(const ora_inst *h, int64_t d) { return d >= 0 && (d < h->c0 || d >= h->c1); }
+
+int64_t ora_outbox_count(void *vh)
+{
+    ora_inst *h = (ora_inst *)vh;
+    int64_t n = 0;
+    if (h->phase != 1) return -1;
+    for (int64_t q = 0; q < h->np; ++q) n += outside(h, h->parts[q].cell);
+    return n;
+}
+
+void ora_outbox(void *vh, int32_t *cell, double *xl, double *u, double *v, double *w)
+{
+    ora_inst *h = (ora_inst *)vh;
+    int64_t n = 0;
+    for (int64_t q = 0; q < h->np; ++q) {
+        const opart *r = h->parts + q;
+        if (!outside(h, r->cell)) continue;
+        cell[n] = r->cell; xl[n] = r->xl; u[n] = r->u; v[n] = r->v; w[n] = r->w;
+        ++n;
+    }
+}
+
+/* Second half.  lo / hi: the transported records arriving from parts that own lower / higher cells,
+ * each in the pre-transport order of the whole domain (by source part, then that part's order).
+ * The new list of an owned cell is then [from lower parts] [from this part] [from higher parts],
+ * each in pre-transport order -- the stable order by new cell of the undivided array. */
+static int step_second_half(ora_inst *h, int64_t nlo, const opart *lo, int64_t nhi, const opart *hi)
+{
+    const ora_params *p = &h->p;
+    const ora_consts *c = &h->c;
+    int32_t C = h->C;
+    const int32_t c0 = h->c0, c1 = h->c1;
+    if (h->phase != 1) return -1;
+    const double *F = h->F;
+    opart *mv = h->parts;
+    int64_t nmv = h->np;
+    /* stable counting sort by the new cell over lo ++ own ++ hi */
+    int64_t *cnt = (int64_t *)calloc((size_t)C + 1, sizeof(int64_t));
+    if (!cnt) return -2;
+    for (int64_t q = 0; q < nlo; ++q) {
+        if (lo[q].cell < c0 || lo[q].cell >= c1) { free(cnt); return -1; }
+        cnt[lo[q].cell + 1] += 1;
+    }
+    for (int64_t q = 0; q < nmv; ++q)
+        if (mv[q].cell >= c0 && mv[q].cell < c1) cnt[mv[q].cell + 1] += 1;
+    for (int64_t q = 0; q < nhi; ++q) {
+        if (hi[q].cell < c0 || hi[q].cell >= c1) { free(cnt); return -1; }
+        cnt[hi[q].cell + 1] += 1;
+    }
+    for (int32_t i = 0; i < C; ++i) cnt[i + 1] += cnt[i];
+    int64_t nkeep = cnt[C];
+    opart *np_ = (opart *)malloc((size_t)(nkeep ? nkeep : 1) * sizeof(opart));
+    if (!np_) { free(cnt); return -2; }
+    for (int64_t q = 0; q < nlo; ++q) np_[cnt[lo[q].cell]++] = lo[q];
+    for (int64_t q = 0; q < nmv; ++q)
+        if (mv[q].cell >= c0 && mv[q].cell < c1) np_[cnt[mv[q].cell]++] = mv[q];
+    for (int64_t q = 0; q < nhi; ++q) np_[cnt[hi[q].cell]++] = hi[q];
+    free(cnt);
+    free(h->parts);
+    h->parts = np_;
+    h->cap = nkeep ? nkeep : 1;
+    h->np = nkeep;
+
+    /* particle flux Eq. (fp) = change of the per-cell particle moments over the
+     * transport; wave flux by the NS solver; conservative update Eq. (r1) */
+    memset(h->post_m, 0, (size_t)C * 5 * sizeof(double));
+    for (int64_t q = 0; q < h->np; ++q) add_phi(h->post_m + 5 * h->parts[q].cell, h->parts + q);
+    for (int32_t i = c0; i < c1; ++i) {
+        for (int k = 0; k < 5; ++k) {
+            double fp = c->mp_over_dx * (h->post_m[5 * i + k] - h->pre_m[5 * i + k]);
+            double fw = c->dtdx * (F[5 * (i + 1) + k] - F[5 * i + k]);
+            h->psi[5 * i + k] = h->psi[5 * i + k] + fp - fw;
         }
     }
-    free(W); free(P); free(F); free(start);
+    h->step += 1;
+    if ((int64_t)h->step > (int64_t)p->avg_start) {
+        for (int64_t k = (int64_t)c0 * 5; k < (int64_t)c1 * 5; ++k) h->avg[k] += h->psi[k];
+        h->navg += 1;
+    }
+    h->phase = 0;
     return 0;
+}
+
+int ora_step(void *vh, int32_t nsteps)
+{
+    ora_inst *h = (ora_inst *)vh;
+    if (h->c0 != 0 || h->c1 != h->C || h->phase != 0) return -1;
+    for (int32_t s = 0; s < nsteps; ++s) {
+        int rc = step_first_half(h);
+        if (rc) return rc;
+        rc = step_second_half(h, 0, NULL, 0, NULL);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* Domain decomposition (host-rank emulation): this instance owns cells [c0, c1) of the domain.
+ * Set before the first step, on an instance without particles.  The states of the cells next to
+ * the owned range (two on each side, periodic ends wrapping) must be set by the caller before
+ * every first half (ora_set_psi) from the parts that own them. */
+int ora_set_range(void *vh, int32_t c0, int32_t c1)
+{
+    ora_inst *h = (ora_inst *)vh;
+    if (c0 < 0 || c1 > h->C || c0 >= c1 || h->np != 0 || h->phase != 0) return -1;
+    h->c0 = c0;
+    h->c1 = c1;
+    return 0;
+}
+
+int ora_step_first_half(void *vh)
+{
+    ora_inst *h = (ora_inst *)vh;
+    if (h->phase != 0) return -1;
+    return step_first_half(h);
+}
+
+int ora_step_second_half(void *vh, int64_t nlo, const int32_t *lc, const double *lxl, const double *lu,
+                         const double *lv, const double *lw, int64_t nhi, const int32_t *hc, const double *hxl,
+                         const double *hu, const double *hv, const double *hw)
+{
+    ora_inst *h = (ora_inst *)vh;
+    opart *lo = (opart *)malloc((size_t)(nlo ? nlo : 1) * sizeof(opart));
+    opart *hi = (opart *)malloc((size_t)(nhi ? nhi : 1) * sizeof(opart));
+    if (!lo || !hi) { free(lo); free(hi); return -2; }
+    for (int64_t q = 0; q < nlo; ++q) { lo[q].cell = lc[q]; lo[q].xl = lxl[q]; lo[q].u = lu[q]; lo[q].v = lv[q]; lo[q].w = lw[q]; }
+    for (int64_t q = 0; q < nhi; ++q) { hi[q].cell = hc[q]; hi[q].xl = hxl[q]; hi[q].u = hu[q]; hi[q].v = hv[q]; hi[q].w = hw[q]; }
+    int rc = step_second_half(h, nlo, lo, nhi, hi);
+    free(lo);
+    free(hi);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------- */

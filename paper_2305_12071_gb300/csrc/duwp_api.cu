@@ -164,9 +164,12 @@ Engine::~Engine()
     if (side) cudaStreamSynchronize(side);
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    if (side2) cudaStreamSynchronize(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_join2) cudaEventDestroy(ev_join2);
     if (side) cudaStreamDestroy(side);
+    if (side2) cudaStreamDestroy(side2);
     for (int k = 0; k < 2; ++k) {
         if (mom_ready[k]) cudaEventDestroy(mom_ready[k]);
         if (copy_done[k]) cudaEventDestroy(copy_done[k]);
@@ -201,13 +204,18 @@ int Engine::configure_launch(int threads_, int variant_)
     if (occ <= 0) return DUWP_EINVAL;
     const int occ_c = collide_occupancy(fp32);
     if (occ_c <= 0) return DUWP_EINVAL;
+    const int occ_s = staged_occupancy(fp32);
+    if (occ_s <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    dev.nsm = nsm;
     threads = threads_;
     variant = variant_;
     // collision kernel: persistent blocks, as many as fit, but no more warps than cells
     const int cw = collide_threads() / 32;
     grid_collide = std::max(1, std::min(occ_c * nsm, (G + cw - 1) / cw));
+    // staged-cell kernel: one block per cell, as many persistent blocks as fit, no more than cells
+    grid_staged = std::max(1, std::min(occ_s * nsm, G));
     drop_graphs();
     return DUWP_OK;
 }
@@ -228,8 +236,10 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     if (!params || n < 0) return DUWP_EINVAL;
     DUWP_CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
     DUWP_CU(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    DUWP_CU(cudaStreamCreateWithFlags(&side2, cudaStreamNonBlocking));
     DUWP_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     DUWP_CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    DUWP_CU(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
     std::vector<HostInst> hs(static_cast<size_t>(n));
     int64_t est = 0;
     int64_t cells = 0;
@@ -263,7 +273,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
 
     const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
     const size_t far_item = fp32 ? sizeof(FarItem<RecF>) : sizeof(FarItem<RecD>);
-    const int32_t nblocks = (G + kCellBlock - 1) / kCellBlock;
+    const int32_t nblocks = (G + kCellBlockMin - 1) / kCellBlockMin;   // blocks of the cell kernels at their smallest
     Carver c;
     const size_t o_inst = c.take<InstDev>(max_inst);
     const size_t o_cinst = c.take<int32_t>(G);
@@ -296,7 +306,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_err = c.take<int32_t>(4);
     const size_t o_ticket = c.take<int32_t>(kTickets);
     const size_t o_hdr = c.take<CellHdr>(G);
-    const size_t o_wl = c.take<int32_t>(4 * size_t(G));
+    const size_t o_wl = c.take<int32_t>(kLists * size_t(G));
     // chunks of re-sampled particles: at most one partial chunk per cell plus the re-sampled
     // particles (at most half the slots of a buffer) in full chunks
     const int64_t wls_cap = int64_t(G) + capacity / (2 * kSampleChunk) + 64;
@@ -450,19 +460,27 @@ int Engine::enqueue_step(cudaEvent_t *ev)
     const int rp = parity;
     if (ev) {
         // timed: one kernel after the other, events around each
+        DUWP_CU(cudaEventRecord(ev[6], stream));
+        DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[0], stream));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[1], stream));
         DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 0, prio_hi));
         DUWP_CU(cudaEventRecord(ev[2], stream));
     } else {
-        // the free cells stream on the side stream while the collision kernel runs; the other cells
-        // after it; the side stream joins before the far movers are sorted
+        // the block kernel (cells with many candidates) and the collision kernel (the other cells
+        // that need one) run side by side, and the free cells stream on a third stream meanwhile; the
+        // other cells stream after both collision kernels; every stream joins before the far movers
+        // are sorted
         DUWP_CU(cudaEventRecord(ev_fork, stream));
         DUWP_CU(cudaStreamWaitEvent(side, ev_fork, 0));
+        DUWP_CU(cudaStreamWaitEvent(side2, ev_fork, 0));
+        DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, side2, prio_hi));
+        DUWP_CU(cudaEventRecord(ev_join2, side2));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
         DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, side, 1, prio_lo));
         DUWP_CU(cudaEventRecord(ev_join, side));
+        DUWP_CU(cudaStreamWaitEvent(stream, ev_join2, 0));
         DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 2, prio_hi));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join, 0));
     }
@@ -605,21 +623,25 @@ int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_m
         if (rc == DUWP_OK) ++E.steps_done;
     }
     if (rc == DUWP_OK) rc = E.sync();
-    for (int k = 0; k < kEv; ++k) kernel_ms[k] = 0.0;
+    for (int k = 0; k < DUWP_TIMED_SLOTS; ++k) kernel_ms[k] = 0.0;
     if (rc == DUWP_OK) {
+        // per step: e[6] before the staged-cell kernel, e[0] before the collision kernel, e[1..5]
+        // after the collision, streaming, far-sort, cell and offset kernels
         float span = 0.f;
-        cudaEventElapsedTime(&span, ev[0], ev[kEv * static_cast<size_t>(n) - 1]);
-        kernel_ms[kEv - 1] = span;
+        cudaEventElapsedTime(&span, ev[6], ev[kEv * static_cast<size_t>(n - 1) + 5]);
+        kernel_ms[5] = span;
         for (int32_t s = 0; s < n; ++s) {
             cudaEvent_t *e = ev.data() + kEv * static_cast<size_t>(s);
-            for (int k = 0; k < kEv - 1; ++k) {
+            for (int k = 0; k < 5; ++k) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e[k], e[k + 1]);
                 kernel_ms[k] += ms;
             }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e[6], e[0]);
+            kernel_ms[6] += ms;
             if (step_ms) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e[0], e[kEv - 1]);
+                cudaEventElapsedTime(&ms, e[6], e[5]);
                 step_ms[s] = ms;
             }
         }

@@ -214,6 +214,60 @@ __host__ __device__ __forceinline__ ds ds_turn_cos(const float4 *turn, uint32_t 
     return ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
 }
 
+// The parts of the scattering that depend only on the draw: cos(theta), sin(theta), cos(phi),
+// sin(phi).  Returns false when sin(theta) < 2^-10 (the pair then takes the double-precision path).
+struct DsAngles {
+    ds ct, st, cp, sp;
+};
+
+__host__ __device__ __forceinline__ bool ds_scatter_angles(const float4 *turn, uint32_t v0, uint32_t v1, uint32_t v2,
+                                                           uint32_t v3, DsAngles &g)
+{
+    // cos(theta) = 2 u1 - 1 = n 2^-52 with the integer n = m - 2^52, m = (v0 << 21) | (v1 >> 11); the
+    // factors 1 - cos(theta) = (2^52 - n) 2^-52 and 1 + cos(theta) = (2^52 + n) 2^-52 are formed exactly
+    // as integers, so sin(theta) carries no error amplified by 1 / sin(theta) near the poles
+    const uint64_t m53 = (static_cast<uint64_t>(v0) << 21) | static_cast<uint64_t>(v1 >> 11);
+    const int64_t n = static_cast<int64_t>(m53) - (1ll << 52);
+    g.ct = ds_scale(ds_int53(n), 0x1p-52f);
+    const ds omc = ds_int53((1ll << 52) - n), opc = ds_int53((1ll << 52) + n);
+    // sin(theta) = sqrt((1 - ct)(1 + ct))
+    g.st = ds_scale(ds_sqrt(ds_mul(omc, opc)), 0x1p-52f);
+    if (!(g.st.hi >= 0x1p-10f)) return false;
+    // phi = 2 pi u2
+    ds_turn(turn, v2, v3, g.cp, g.sp);
+    return true;
+}
+
+// The velocities of the pair after the collision from its angles (see ds_scatter).
+__host__ __device__ __forceinline__ bool ds_scatter_apply(float au, float av, float aw, float bu, float bv, float bw,
+                                                          const DsAngles &g, float out[6], ds *unrounded = nullptr)
+{
+    // relative speed c_r of the pair (the differences of two floats are exact pairs)
+    const ds du = ds_two_sum(au, -bu), dv = ds_two_sum(av, -bv), dw = ds_two_sum(aw, -bw);
+    const ds cr = ds_sqrt(ds_add(ds_add(ds_mul(du, du), ds_mul(dv, dv)), ds_mul(dw, dw)));
+    // relative velocity after the collision and the two velocities (a + b)/2 +- c/2
+    const ds crst = ds_mul(cr, g.st);
+    const ds c[3] = {ds_mul(crst, g.cp), ds_mul(crst, g.sp), ds_mul(cr, g.ct)};
+    const float a3[3] = {au, av, aw}, b3[3] = {bu, bv, bw};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ds m = ds_two_sum(a3[k], b3[k]);
+        const ds half_m = {0.5f * m.hi, 0.5f * m.lo};
+        const ds half_c = {0.5f * c[k].hi, 0.5f * c[k].lo};
+        const ds pa = ds_add(half_m, half_c), pb = ds_add(half_m, ds_neg(half_c));
+        const float err = 0x1p-44f * (cr.hi + fabsf(half_m.hi)) + cr.hi * (0x1p-51f / g.st.hi);
+        ok = ok && ds_rounds_to_hi(pa, err) && ds_rounds_to_hi(pb, err);
+        out[k] = pa.hi;
+        out[3 + k] = pb.hi;
+        if (unrounded) {
+            unrounded[k] = pa;
+            unrounded[3 + k] = pb;
+        }
+    }
+    return ok;
+}
+
 // Post-collision velocities of an accepted pair of single-precision records (isotropic VHS
 // scattering, Appendix A): the relative velocity keeps its magnitude c_r and takes the direction
 // with cos(theta) = 2 u1 - 1, phi = 2 pi u2, where u1 = u53(v0, v1) and u2 = u53(v2, v3) (53-bit
@@ -229,43 +283,9 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
                                                     float bv, float bw, uint32_t v0, uint32_t v1, uint32_t v2,
                                                     uint32_t v3, float out[6], ds *unrounded = nullptr)
 {
-    // relative speed c_r of the pair (the differences of two floats are exact pairs)
-    const ds du = ds_two_sum(au, -bu), dv = ds_two_sum(av, -bv), dw = ds_two_sum(aw, -bw);
-    const ds cr = ds_sqrt(ds_add(ds_add(ds_mul(du, du), ds_mul(dv, dv)), ds_mul(dw, dw)));
-    // cos(theta) = 2 u1 - 1 = n 2^-52 with the integer n = m - 2^52, m = (v0 << 21) | (v1 >> 11); the
-    // factors 1 - cos(theta) = (2^52 - n) 2^-52 and 1 + cos(theta) = (2^52 + n) 2^-52 are formed exactly
-    // as integers, so sin(theta) carries no error amplified by 1 / sin(theta) near the poles
-    const uint64_t m53 = (static_cast<uint64_t>(v0) << 21) | static_cast<uint64_t>(v1 >> 11);
-    const int64_t n = static_cast<int64_t>(m53) - (1ll << 52);
-    const ds ct = ds_scale(ds_int53(n), 0x1p-52f);
-    const ds omc = ds_int53((1ll << 52) - n), opc = ds_int53((1ll << 52) + n);
-    // sin(theta) = sqrt((1 - ct)(1 + ct))
-    const ds st = ds_scale(ds_sqrt(ds_mul(omc, opc)), 0x1p-52f);
-    if (!(st.hi >= 0x1p-10f)) return false;
-    // phi = 2 pi u2
-    ds cp, sp;
-    ds_turn(turn, v2, v3, cp, sp);
-    // relative velocity after the collision and the two velocities (a + b)/2 +- c/2
-    const ds crst = ds_mul(cr, st);
-    const ds c[3] = {ds_mul(crst, cp), ds_mul(crst, sp), ds_mul(cr, ct)};
-    const float a3[3] = {au, av, aw}, b3[3] = {bu, bv, bw};
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const ds m = ds_two_sum(a3[k], b3[k]);
-        const ds half_m = {0.5f * m.hi, 0.5f * m.lo};
-        const ds half_c = {0.5f * c[k].hi, 0.5f * c[k].lo};
-        const ds pa = ds_add(half_m, half_c), pb = ds_add(half_m, ds_neg(half_c));
-        const float err = 0x1p-44f * (cr.hi + fabsf(half_m.hi)) + cr.hi * (0x1p-51f / st.hi);
-        ok = ok && ds_rounds_to_hi(pa, err) && ds_rounds_to_hi(pb, err);
-        out[k] = pa.hi;
-        out[3 + k] = pb.hi;
-        if (unrounded) {
-            unrounded[k] = pa;
-            unrounded[3 + k] = pb;
-        }
-    }
-    return ok;
+    DsAngles g;
+    if (!ds_scatter_angles(turn, v0, v1, v2, v3, g)) return false;
+    return ds_scatter_apply(au, av, aw, bu, bv, bw, g, out, unrounded);
 }
 
 // Log table: nodes F_j = 1 + (j - kLogCenter)/256, j = 0..kLogTable-1 (covering [sqrt(1/2), 1.416]),

@@ -15,8 +15,9 @@ namespace duwp {
 
 void set_cuda_error(cudaError_t e, const char *where);
 
-// Events recorded by a timed step: before the collision kernel and after each of the five kernels.
-constexpr int kStepEvents = 6;
+// Events recorded by a timed step: after the staged-cell kernel (before the collision kernel), after
+// each of the five other kernels, and (last) before the staged-cell kernel.
+constexpr int kStepEvents = 7;
 
 struct HostInst {
     duwp_params p;
@@ -48,6 +49,7 @@ struct Engine {
     int32_t threads = 128;      // streaming kernel: threads per block (one warp per cell)
     int32_t variant = 0;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers)
     int32_t grid_collide = 0;   // collision kernel: persistent blocks
+    int32_t grid_staged = 0;    // staged-cell kernel: persistent blocks
 
     // device memory: one slab
     void *slab = nullptr;
@@ -64,6 +66,10 @@ struct Engine {
     // (launched at the lowest priority, so that the collision kernel's blocks are placed first)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the block kernel (cells with many collision candidates) runs beside the collision kernel (the
+    // other cells) on a stream of its own
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_join2 = nullptr;
     int prio_hi = 0, prio_lo = 0;
 
     // device scratch of the profile reads (allocated on first use): the table of instance bases

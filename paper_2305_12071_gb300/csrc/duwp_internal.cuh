@@ -107,6 +107,7 @@ struct EngineDev {
     int32_t far_cap;
     int32_t G_run;             // the step kernels cover cells [0, G_run) (<= G): every resident
                                // instance lies below it, the cells above are unused and clean
+    int32_t nsm;               // SMs of the device (launch shapes of the cell kernels)
     InstDev *inst;
     int32_t *cell_inst;        // instance of each flattened cell, -1 = unused
     double *psi;               // G x 5 total state Psi_t (reservoirs: unused)
@@ -136,24 +137,29 @@ struct EngineDev {
     int32_t *err;              // first device error
     int32_t *ticket;           // collision kernel work counters and list lengths (kTickets, see below)
     CellHdr *hdr;              // G: plan of each cell's particle work in the next step
-    int32_t *wl;               // 4 x G: work lists of the collision kernel (direct cells with up to 8, 16,
-                               // 32 candidates; staged cells)
+    int32_t *wl;               // 5 x G: work lists of the collision kernels (direct cells with up to 8, 16,
+                               // 32 candidates; the other light cells; the heavy cells)
     int2 *wls;                 // sample list: (cell, first index) of chunks of kSampleChunk re-sampled particles
     int32_t wls_cap;           // entries of wls
 };
 
-// ticket[q] (q < 4): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
-// and ticket[kSampleCtr]: length of and next item of the sample list.
-constexpr int kListLen = 4;
-constexpr int kSampleLen = 8;
-constexpr int kSampleCtr = 9;
+// ticket[q] (q < kLists): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
+// and ticket[kSampleCtr]: length of and next item of the sample list.  Lists 0-3 belong to the
+// collision kernel (one warp per cell or less), list kHeavyList to the block kernel (the cells with
+// many collision candidates, one block per cell).
+constexpr int kLists = 5;
+constexpr int kHeavyList = 4;
+constexpr int kListLen = 5;
+constexpr int kSampleLen = 10;
+constexpr int kSampleCtr = 11;
 constexpr int kTickets = 16;
 
 // Re-sampled particles of classes 1 and 4 are drawn by the collision kernel in chunks of this many,
 // spread over all its warps, and written after the arrived positions of the cell's output block.
 constexpr int kSampleChunk = 64;
 
-constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels
+constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels (at most)
+constexpr int kCellBlockMin = 32; // (at least)
 
 // ------------------------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round multiplies words 0

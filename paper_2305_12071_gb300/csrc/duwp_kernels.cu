@@ -463,6 +463,22 @@ __device__ __noinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_
     }
 }
 
+// Scattering with the angle words v already drawn (counter (id, 2k+1, step, COLLIDE)).
+__device__ __forceinline__ void scatter_words(const uint32_t *v, RecD &A, RecD &B, double cr, bool exact)
+{
+    scatter_fp64<RecD>(v, A, B, exact ? cr : rel_speed(A, B));
+}
+__device__ __noinline__ void scatter_words(const uint32_t *v, RecF &A, RecF &B, double cr, bool exact)
+{
+    float o[6];
+    if (ds_scatter(g_turn, A.u, A.v, A.w, B.u, B.v, B.w, v[0], v[1], v[2], v[3], o)) {
+        A.u = o[0]; A.v = o[1]; A.w = o[2];
+        B.u = o[3]; B.v = o[4]; B.w = o[5];
+    } else {
+        scatter_fp64<RecF>(v, A, B, exact ? cr : rel_speed(A, B));
+    }
+}
+
 // The nc candidates of a staged cell list (nc from ntc_candidates), in order; candidate k is drawn
 // in the batch that reaches it.
 // A cell's particle list as collide_list sees it: position x -> record address.
@@ -648,7 +664,7 @@ struct CollideShared {
     int key[kHash];     // list position of the particle held in the slot, -1 = empty
     int own[kHash];     // lowest lane of the current batch whose candidate touches the slot (32 = none)
     int mod[kHash];     // changed by an accepted collision
-    int ab[64];         // picks of a batch (staged cells)
+    int ab[64];         // picks of a batch (warp-level list collisions)
     Rec rec[kHash];
 };
 
@@ -910,6 +926,480 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
     }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Block kernel k_cellblock: one block of kBlockThreads per cell, persistent blocks over the work list
+// of the cells with many collision candidates (the heavy list: staged cells, P > 0, and direct cells,
+// P = 0, whose candidate count is at least kHeavyCandidates; the lighter ones run one warp per cell
+// in the collision kernel).  Step 2 of Sec. 3.4 in the order the paper gives it:
+//   absorption (staged cells): particle k of the arrived list is absorbed into the wave with
+//     probability P (Eq. p); the survivors keep their order, compacted by the whole block into the
+//     first half of the cell's output block;
+//   re-sampling: (1-P) of the wave (Eq. maxsample), after the survivors (staged) or after the
+//     arrived positions in the output block (direct), by the whole block;
+//   NTC collisions (Appendix A) on that list.  Candidate k touches particles a_k, b_k and must see
+//     them as every earlier candidate left them; candidates are taken in windows of kWindow and
+//     executed in rounds: a candidate runs in the first round in which no earlier unfinished
+//     candidate of the window touches either of its particles (each round every unfinished candidate
+//     claims its two particles with atomicMax of (round, -position); the lowest position wins, so the
+//     earliest unfinished candidate always runs and a window needs at most kWindow rounds).  The
+//     candidates that may run in a round are packed into the first threads of the block, so that
+//     only as many warps as there are runnable candidates / 32 execute the scattering.  This is the
+//     sequential result whenever c_max stays fixed.  A candidate whose c_r exceeds c_max raises it,
+//     and every later candidate must use the raised value: the window is first run with the
+//     window's c_max; if any candidate raised it, the records are put back as they were at the
+//     window's start and only the candidates up to the first raising one are run again (the raising
+//     one accepted, as the sequential loop accepts it), and the next window starts after it with the
+//     raised c_max.
+// The records live in a shared-memory table during the collisions: the whole list when it has at
+// most kBlockSlots records (slot = list position), otherwise the particles a window of kWindowHashed
+// candidates touches (hashed by list position); the changed records are written back after each
+// window.
+// ------------------------------------------------------------------------------------------
+constexpr int kBlockThreads = 128;
+constexpr int kPer = 4;                             // window candidates per thread
+constexpr int kWindow = kPer * kBlockThreads;       // candidates per window (table = the whole list)
+constexpr int kWindowHashed = kBlockThreads * 2;    // candidates per window when the touched particles are hashed
+constexpr int kBlockSlots = 1024;      // table slots (the hashed form holds at most 2 x kWindowHashed keys)
+constexpr int kAbsorbPer = 4;          // arrived records per thread in flight in the absorption pass
+constexpr int kHeavyCandidates = 96;   // candidates from which a cell takes the block kernel
+
+template <typename Rec>
+struct BlockShared {
+    int key[kBlockSlots];          // hashed form: list position held by the slot, -1 = empty
+    unsigned own[kBlockSlots];     // claim of the current round: (round << 16) | (0xffff - window position)
+    unsigned char mod[kBlockSlots];// changed in the current window
+    Rec rec[kBlockSlots];          // current values
+    int2 ab[kWindow];              // table slots of each candidate's pair
+    uint2 wa[kWindow];             // acceptance draw
+    float4 sc[kWindow][2];         // scattering: the angle parts (single-precision records) or the draw
+    unsigned char acc[kWindow];    // accepted
+    unsigned char angok[kWindow];  // the angle parts are usable
+    short ready[kWindow];          // the candidates that run in the current round
+    CellHdr hdr;
+    MaxwellCell mc;                // the cell's sampling state
+    CeCell ce;
+    int ce_on;
+    int wsum[kAbsorbPer][kBlockThreads / 32];
+    int item, nn, nc, ok, rmin, nready;
+    double cm_new;
+};
+
+__device__ __forceinline__ int block_insert(int *key, int x, int32_t *err)
+{
+    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> 22;
+    for (int it = 0; it < kBlockSlots; ++it) {
+        const int old = atomicCAS(&key[h], -1, x);
+        if (old == -1 || old == x) return static_cast<int>(h);
+        h = (h + 1u) & (kBlockSlots - 1);
+    }
+    set_err(err, kErrOverflow);
+    return 0;
+}
+
+// What the acceptance test of a window needs, formed once per window.  The single-precision ratio
+// c_r / c_max is taken as c_r * (1 / c_max): within two units in the last place of the quotient,
+// far inside the margin outside of which the single-precision decision is the exact one (the margin
+// covers a 1e-5 relative error of the single-precision power).
+struct WindowConst {
+    double cm, expo;
+    float cm32, cm32_near, inv_cm32, expo_f;
+    bool always, linear;     // Maxwell molecules (exponent 0); hard spheres (exponent 1)
+};
+
+// Candidate c of the window run on the current records.  id, k0: the cell's generator id and the
+// window's first candidate (for the draw of a pair that needs the double-precision scattering).
+template <typename Rec>
+__device__ __forceinline__ void block_run_candidate(const InstDev &I, BlockShared<Rec> &S, int c, const WindowConst &W,
+                                                    bool redo, uint32_t id, uint32_t step, int64_t k0)
+{
+    const int sa = S.ab[c].x, sb = S.ab[c].y;
+    Rec A = S.rec[sa], B = S.rec[sb];
+    const float cr32 = rel_speed_f32(A, B);
+    double cr = 0.0;
+    bool exact = false;
+    if (cr32 > W.cm32_near) {          // possibly above c_max: decide exactly
+        cr = rel_speed(A, B);
+        exact = true;
+    }
+    bool a;
+    const uint32_t w2 = S.wa[c].x, w3 = S.wa[c].y;
+    if (exact && cr > W.cm) {          // c_max raised to c_r: accepted
+        a = true;
+        atomicMin(&S.rmin, c);
+        if (redo) S.cm_new = cr;       // in the rerun only the first raising candidate runs
+    } else if (W.always) {
+        a = true;
+    } else {
+        const float x32 = cr32 * W.inv_cm32;
+        bool decided = false;
+        a = false;
+        if (cr32 > 1e-12f && x32 > 1e-30f) {
+            const float p32 = W.linear ? x32 : exp2f(W.expo_f * log2f(x32));
+            const float m32 = 2e-4f * p32 + 2.5e-7f;
+            const float uf = static_cast<float>(w2 >> 8) * 0x1p-24f;
+            if (uf < p32 - m32) { a = true; decided = true; }
+            else if (uf > p32 + m32) decided = true;
+        }
+        if (!decided) a = accept_exact<Rec>(I, W.expo, A, B, W.cm, w2, w3, cr, exact);
+    }
+    if (a) {
+        bool done = false;
+        if constexpr (sizeof(A.u) == 4) {
+            if (S.angok[c]) {
+                const float4 g0 = S.sc[c][0], g1 = S.sc[c][1];
+                const DsAngles g{{g0.x, g0.y}, {g0.z, g0.w}, {g1.x, g1.y}, {g1.z, g1.w}};
+                float o[6];
+                if (ds_scatter_apply(A.u, A.v, A.w, B.u, B.v, B.w, g, o)) {
+                    A.u = o[0]; A.v = o[1]; A.w = o[2];
+                    B.u = o[3]; B.v = o[4]; B.w = o[5];
+                    done = true;
+                }
+            }
+            if (!done) {
+                uint32_t v[4];
+                draw(I, id, static_cast<uint32_t>(2 * (k0 + c) + 1), step, kCollide, v);
+                scatter_fp64<Rec>(v, A, B, exact ? cr : rel_speed(A, B));
+            }
+        } else {
+            const float4 g0 = S.sc[c][0];
+            const uint32_t v[4] = {__float_as_uint(g0.x), __float_as_uint(g0.y), __float_as_uint(g0.z),
+                                   __float_as_uint(g0.w)};
+            scatter_fp64<Rec>(v, A, B, exact ? cr : rel_speed(A, B));
+        }
+        S.rec[sa] = A;
+        S.rec[sb] = B;
+        S.mod[sa] = 1;
+        S.mod[sb] = 1;
+    }
+    S.acc[c] = a ? 1 : 0;
+}
+
+// One pass of rounds over the window's candidates c < live_end.  Returns when all have run.
+template <typename Rec>
+__device__ void block_rounds(const InstDev &I, BlockShared<Rec> &S, int live_end, const WindowConst &W, bool redo,
+                             uint32_t id, uint32_t step, int64_t k0)
+{
+    const int t = threadIdx.x, lane = t & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    bool undone[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) undone[u] = t + u * kBlockThreads < live_end;
+    int remaining = live_end;
+    for (unsigned round = 1; round <= kWindow + 1 && remaining > 0; ++round) {
+        if (t == 0) S.nready = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int c = t + u * kBlockThreads;
+            if (undone[u]) {
+                const unsigned code = (round << 16) | (0xffffu - static_cast<unsigned>(c));
+                atomicMax(&S.own[S.ab[c].x], code);
+                atomicMax(&S.own[S.ab[c].y], code);
+            }
+        }
+        __syncthreads();
+        // the runnable candidates, appended to the round's list (any order: they touch disjoint particles)
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int c = t + u * kBlockThreads;
+            const unsigned code = (round << 16) | (0xffffu - static_cast<unsigned>(c));
+            const bool rdy = undone[u] && S.own[S.ab[c].x] == code && S.own[S.ab[c].y] == code;
+            const unsigned m = __ballot_sync(0xffffffffu, rdy);
+            if (m) {
+                int pos = 0;
+                if (lane == __ffs(m) - 1) pos = atomicAdd(&S.nready, __popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, __ffs(m) - 1);
+                if (rdy) {
+                    S.ready[pos + __popc(m & lt)] = static_cast<short>(c);
+                    undone[u] = false;
+                }
+            }
+        }
+        __syncthreads();
+        const int total = S.nready;
+        for (int j = t; j < total; j += kBlockThreads)
+            block_run_candidate<Rec>(I, S, S.ready[j], W, redo, id, step, k0);
+        remaining -= total;
+        __syncthreads();
+    }
+}
+
+// The list of a staged cell (its output block) and of a direct cell (the arrived positions, then the
+// re-sampled particles after them in the output block), position -> record address.
+template <typename Rec>
+struct BlockList {
+    const CellHdr *h;       // in shared memory
+    Rec *in;
+    FarItem<Rec> *fs;
+    Rec *blk;
+    bool staged;
+    __device__ __forceinline__ Rec *at(int x) const
+    {
+        if (staged || x >= h->n_in) return blk + x;
+        return arrived_ptr<Rec>(x, *h, in, fs);
+    }
+};
+
+// The nc candidates of a list of N records (written earlier by this block or in place).  The list
+// in memory holds the state at the start of each window: the changed records are written back after
+// every window, and a window rerun after a raise of c_max reloads them from there.
+template <typename Rec>
+__device__ void block_collisions(const EngineDev &E, const InstDev &I, uint32_t id, uint32_t step,
+                                 const BlockList<Rec> &L, int N, int64_t nc, BlockShared<Rec> &S, double &cmax,
+                                 int &nacc)
+{
+    const int t = threadIdx.x;
+    const double expo = 1.0 - 2.0 * I.upsilon;
+    const bool whole = N <= kBlockSlots;          // the whole list in the table, slot = position
+    const int win = whole ? kWindow : kWindowHashed;
+    double cm = cmax;
+    int na = 0;
+    if (N < 2 || nc <= 0) {
+        nacc = 0;
+        return;
+    }
+    if (whole) {
+        for (int x = t; x < N; x += kBlockThreads) {
+            S.rec[x] = ld_rec_rw(L.at(x));
+            S.mod[x] = 0;
+        }
+    }
+    int64_t k_lo = 0;
+    while (k_lo < nc) {
+        const int nw = static_cast<int>(min(static_cast<int64_t>(win), nc - k_lo));
+        if (whole) {
+            for (int x = t; x < N; x += kBlockThreads) S.own[x] = 0u;
+        } else {
+            for (int x = t; x < kBlockSlots; x += kBlockThreads) { S.key[x] = -1; S.own[x] = 0u; S.mod[x] = 0; }
+        }
+        if (t == 0) S.rmin = kWindow;
+        __syncthreads();
+        for (int c = t; c < nw; c += kBlockThreads) {
+            const int64_t k = k_lo + c;
+            uint32_t w[4], v[4];
+            draw(I, id, static_cast<uint32_t>(2 * k), step, kCollide, w);
+            const int a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
+            int b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
+            if (b >= a) ++b;
+            draw(I, id, static_cast<uint32_t>(2 * k + 1), step, kCollide, v);
+            S.wa[c] = make_uint2(w[2], w[3]);
+            if constexpr (sizeof(Rec().u) == 4) {
+                // the scattering angles depend only on the draw: formed here for every candidate at once
+                DsAngles g;
+                const bool ok = ds_scatter_angles(g_turn, v[0], v[1], v[2], v[3], g);
+                S.angok[c] = ok ? 1 : 0;
+                S.sc[c][0] = make_float4(g.ct.hi, g.ct.lo, g.st.hi, g.st.lo);
+                S.sc[c][1] = make_float4(g.cp.hi, g.cp.lo, g.sp.hi, g.sp.lo);
+            } else {
+                S.sc[c][0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                         __uint_as_float(v[3]));
+            }
+            if (whole) S.ab[c] = make_int2(a, b);
+            else S.ab[c] = make_int2(block_insert(S.key, a, E.err), block_insert(S.key, b, E.err));
+        }
+        if (!whole) {
+            __syncthreads();
+            for (int x = t; x < kBlockSlots; x += kBlockThreads) {
+                const int y = S.key[x];
+                if (y >= 0) S.rec[x] = ld_rec_rw(L.at(y));
+            }
+        }
+        __syncthreads();
+        WindowConst W;
+        W.cm = cm;
+        W.expo = expo;
+        W.cm32 = static_cast<float>(cm);
+        W.cm32_near = W.cm32 * 0.99999f;
+        W.inv_cm32 = 1.0f / W.cm32;
+        W.expo_f = static_cast<float>(expo);
+        W.always = (expo == 0.0);
+        W.linear = (I.upsilon == 0.0);
+        block_rounds<Rec>(I, S, nw, W, false, id, step, k_lo);
+        const int r = S.rmin;
+        int upto = nw;
+        if (r < nw) {
+            // the candidates after position r saw c_max before its raise: back to the window's start
+            // (the records in memory) and again up to r only
+            const int n_slots = whole ? N : kBlockSlots;
+            for (int x = t; x < n_slots; x += kBlockThreads) {
+                if (S.mod[x]) S.rec[x] = ld_rec_rw(L.at(whole ? x : S.key[x]));
+                S.mod[x] = 0;
+                S.own[x] = 0u;
+            }
+            __syncthreads();
+            block_rounds<Rec>(I, S, r + 1, W, true, id, step, k_lo);
+            cm = S.cm_new;
+            upto = r + 1;
+        }
+        int mine = 0;
+        for (int c = t; c < upto; c += kBlockThreads) mine += S.acc[c];
+        na += __syncthreads_count(mine == 1) + 2 * __syncthreads_count(mine == 2) +
+              3 * __syncthreads_count(mine == 3) + 4 * __syncthreads_count(mine == 4);
+        const int n_slots = whole ? N : kBlockSlots;
+        for (int x = t; x < n_slots; x += kBlockThreads) {
+            if (S.mod[x]) {
+                st_rec(L.at(whole ? x : S.key[x]), S.rec[x]);
+                S.mod[x] = 0;
+            }
+        }
+        __syncthreads();
+        k_lo += upto;
+    }
+    cmax = cm;
+    nacc = na;
+}
+
+// Staged cell: absorption and compaction of the survivors into the first half of the output block.
+// Returns the survivors.
+template <typename Rec>
+__device__ int block_absorb(const EngineDev &E, const InstDev &I, const CellHdr &h, int g, BlockShared<Rec> &S,
+                            Rec *in, FarItem<Rec> *fs, Rec *stage, uint32_t id, uint32_t step)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const double P = E.P[g];
+    const bool all = !(P < 1.0);                       // u53 < 1 always
+    const uint32_t T = all ? 0u : static_cast<uint32_t>(floor(P * 4294967296.0));
+    int run = 0;
+    for (int base = 0; base < h.n_in; base += kAbsorbPer * kBlockThreads) {
+        Rec v[kAbsorbPer];
+        bool keep[kAbsorbPer];
+#pragma unroll
+        for (int u = 0; u < kAbsorbPer; ++u) {
+            const int k = base + u * kBlockThreads + t;
+            keep[u] = k < h.n_in;
+            if (keep[u]) v[u] = ld_rec_rw(arrived_ptr<Rec>(k, h, in, fs));
+        }
+#pragma unroll
+        for (int u = 0; u < kAbsorbPer; ++u) {
+            const int k = base + u * kBlockThreads + t;
+            if (keep[u] && P > 0.0) {
+                uint32_t w[4];
+                draw(I, id, static_cast<uint32_t>(k), step, kAbsorb, w);
+                keep[u] = !absorbed(w[0], w[1], P, T, all);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep[u]);
+            if (lane == 0) S.wsum[u][warp] = __popc(m);
+        }
+        __syncthreads();
+        int pre = run;
+#pragma unroll
+        for (int u = 0; u < kAbsorbPer; ++u) {
+            int before = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kBlockThreads / 32; ++w) {
+                const int c = S.wsum[u][w];
+                before += (w < warp) ? c : 0;
+                tot += c;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep[u]);
+            if (keep[u]) st_rec(stage + pre + before + __popc(m & lt), v[u]);
+            pre += tot;
+        }
+        run = pre;
+        __syncthreads();
+    }
+    return run;
+}
+
+template <typename Rec>
+__device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *in, Rec *out, FarItem<Rec> *fs)
+{
+    const int t = threadIdx.x;
+    if (t == 0) S.hdr = E.hdr[g];
+    __syncthreads();
+    const CellHdr &h = S.hdr;
+    const InstDev &I = E.inst[h.b];
+    const bool staged = h.cls == kClsStaged;
+    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
+    Rec *blk = out + h.off;
+    // the cell's sampling state, by one thread of the last warp while the others absorb
+    if (t == kBlockThreads - 32 && (!staged || E.valid[g]) && (staged || h.n_new > 0)) {
+        S.mc = maxwell_cell(I, E.prim + 5 * g);
+        S.ce_on = (I.resample_mode == 1) ? (ce_coefs(I, E.prim, E.valid, g, h.i, S.ce) ? 1 : 0) : 0;
+    }
+    int run = h.n_in;
+    if (staged) run = block_absorb<Rec>(E, I, h, g, S, in, fs, blk, id, step);
+    // re-sampled and candidate counts
+    if (t == 0) {
+        if (staged) {
+            const double rho_t = E.psi[5 * g];
+            const double rho_w = rho_t - static_cast<double>(run) * I.mp_over_dx;
+            const int64_t nn = E.valid[g] ? resample_count(I, id, step, E.P[g], rho_w) : 0;
+            const int64_t n_tot = run + nn;
+            S.ok = (n_tot <= h.slots) ? 1 : 0;
+            S.nn = static_cast<int>(nn < h.slots ? nn : h.slots);
+            int64_t nc = 0;
+            if (S.ok) {
+                nc = ntc_candidates(I, id, step, static_cast<int>(n_tot), rho_t, E.cmax[g], E.fmaj[g]);
+                if (nc < 0 || nc > INT32_MAX) {
+                    set_err(E.err, kErrOverflow);
+                    nc = 0;
+                }
+            } else {
+                set_err(E.err, kErrOverflow);
+                E.hdr[g].cls = kClsSkip;
+            }
+            S.nc = static_cast<int>(nc);
+        } else {
+            S.ok = 1;
+            S.nn = h.n_new;
+            S.nc = h.nc;
+        }
+    }
+    __syncthreads();
+    if (!S.ok) return;
+    const int nn = S.nn;
+    const int n_tot = run + nn;
+    if (nn > 0) {
+        const MaxwellCell mc = S.mc;
+        const CeCell *ce = S.ce_on ? &S.ce : nullptr;
+        for (int j = t; j < nn; j += kBlockThreads)
+            st_rec(blk + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc, ce));
+    }
+    __syncthreads();
+    const double cm0 = E.cmax[g];
+    double cmax = cm0;
+    int na = 0;
+    const BlockList<Rec> L{&S.hdr, in, fs, blk, staged};
+    block_collisions<Rec>(E, I, id, step, L, n_tot, S.nc, S, cmax, na);
+    if (t == 0) {
+        E.ncand[g] = S.nc;
+        E.nacc[g] = na;
+        if (staged) {
+            E.nabs[g] = h.n_in - run;
+            E.nnew[g] = nn;
+        }
+        if (cmax != cm0) {
+            E.cmax[g] = cmax;
+            E.fmaj[g] = majorant_factor(I, cmax);
+        }
+    }
+}
+
+template <typename Rec>
+__global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(EngineDev E, int rp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    BlockShared<Rec> &S = *reinterpret_cast<BlockShared<Rec> *>(smraw);
+    Rec *in = static_cast<Rec *>(E.buf[rp]);
+    Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
+    FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
+    const int n_items = E.ticket[kListLen + kHeavyList];
+    const int32_t *list = E.wl + static_cast<size_t>(kHeavyList) * E.G;
+    for (;;) {
+        if (threadIdx.x == 0) S.item = atomicAdd(&E.ticket[kHeavyList], 1);
+        __syncthreads();
+        const int it = S.item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const int g = list[it];
+        const int cls = E.hdr[g].cls;
+        if (cls == kClsStaged || cls == kClsDirect) block_cell<Rec>(E, g, S, in, out, fs);
+        __syncthreads();
+    }
+}
+
 template <typename Rec>
 __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int rp)
 {
@@ -919,9 +1409,9 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *in = static_cast<Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
-    // staged cells and direct cells with more than 32 candidates or with re-sampled particles (one
-    // per warp), then direct cells with up to 32, 16 and 8 candidates (one, two and four per warp);
-    // the next ticket of a list is fetched while the current item runs
+    // direct cells with more than 32 candidates or with re-sampled particles (one per warp), then
+    // direct cells with up to 32, 16 and 8 candidates (one, two and four per warp); the next ticket
+    // of a list is fetched while the current item runs (the other cells: k_cellblock)
     for (int q = 3; q >= 0; --q) {
         const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
         const int n_items = E.ticket[kListLen + q];
@@ -1369,15 +1859,15 @@ __global__ void k_far_sort(EngineDev E)
 // step.  For P = 0 the re-sampled count and the NTC candidate count depend only on cell data and
 // counters, so they are decided here, one thread per cell, instead of inside the particle kernels.
 // ------------------------------------------------------------------------------------------
-template <typename Rec>
-__global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int update)
+template <typename Rec, int B>
+__global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
 {
-    __shared__ int64_t s_w[kCellBlock / 32];
-    const int g = blockIdx.x * kCellBlock + threadIdx.x;
+    __shared__ int64_t s_w[B / 32];
+    const int g = blockIdx.x * B + threadIdx.x;
     int64_t myslots = 0;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (update) E.far_count[0] = 0;
-        for (int q = 0; q < 4; ++q) E.ticket[kListLen + q] = 0;
+        for (int q = 0; q < kLists; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
     }
     if (g < E.G_run) {
@@ -1514,7 +2004,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
     __syncthreads();
     if (threadIdx.x == 0) {
         int64_t s = 0;
-        for (int w = 0; w < kCellBlock / 32; ++w) s += s_w[w];
+        for (int w = 0; w < B / 32; ++w) s += s_w[w];
         E.blocksum[blockIdx.x] = 2 * s;
     }
 }
@@ -1523,22 +2013,40 @@ __global__ void __launch_bounds__(kCellBlock) k_cells(EngineDev E, int q, int up
 // Offsets of the next step's output blocks, the collision kernel's work list, and the wave flux of
 // every interface.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp, int advance)
+// Whether a cell's collisions are long dependency chains, which the block kernel runs in parallel
+// rounds: at least kHeavyCandidates NTC candidates (Appendix A) on a list that fits the block's
+// shared-memory table.  (On longer lists the pairs rarely share a particle and the collision kernel's
+// warp takes them 32 at a time.)  A staged cell is estimated with about (1 - P) of its mass in
+// particles after absorption and re-sampling.  Only the choice of kernel depends on this, never a
+// result.
+__device__ __forceinline__ bool staged_is_heavy(const EngineDev &E, int g)
 {
-    __shared__ int64_t s_w[kCellBlock / 32];
+    const InstDev &I = E.inst[E.hdr[g].b];
+    const double rho_t = E.psi[5 * g];
+    const double n_est = (1.0 - E.P[g]) * fmax(rho_t, 0.0) * I.dx_over_mp;
+    if (!(n_est <= 0.9 * kBlockSlots)) return false;
+    const double rr = (I.ntc_rate == 1) ? rho_t * I.inv_rho_ref : n_est * I.ntc_rr;
+    const double nsel = I.ntc_A * rr * (n_est - 1.0) * E.fmaj[g] * E.cmax[g];
+    return nsel >= static_cast<double>(kHeavyCandidates);
+}
+
+template <int B>
+__global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int advance)
+{
+    __shared__ int64_t s_w[B / 32];
     __shared__ int64_t s_pre;
-    const int g = blockIdx.x * kCellBlock + threadIdx.x;
+    const int g = blockIdx.x * B + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // sum of the slot bounds of all earlier blocks
     int64_t acc = 0;
-    for (int j = threadIdx.x; j < blockIdx.x; j += kCellBlock) acc += E.blocksum[j];
+    for (int j = threadIdx.x; j < blockIdx.x; j += B) acc += E.blocksum[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) s_w[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         int64_t s = 0;
-        for (int w = 0; w < kCellBlock / 32; ++w) s += s_w[w];
+        for (int w = 0; w < B / 32; ++w) s += s_w[w];
         s_pre = s;
     }
     __syncthreads();
@@ -1556,7 +2064,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     bool listed = false;
     int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
-                       // re-sampled, 3 the other direct cells and the staged cells
+                       // re-sampled, 3 the other light cells, kHeavyList the cells with many candidates
     int chunks = 0;
     if (g < E.G_run) {
         const int64_t o = s_pre + wpre + x - v;
@@ -1568,9 +2076,11 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         } else {
             const int cls = E.hdr[g].cls;
             listed = (cls == kClsDirect) || (cls == kClsStaged);
+            if (cls == kClsStaged && staged_is_heavy(E, g)) lq = kHeavyList;
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
-                if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
+                if (nc >= kHeavyCandidates && E.hdr[g].n_in + E.hdr[g].n_new <= kBlockSlots) lq = kHeavyList;
+                else if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
         }
@@ -1595,9 +2105,9 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
             }
         }
     }
-    // work lists of the collision kernel (one atomic per warp and list)
+    // work lists of the collision kernels (one atomic per warp and list)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kLists; ++q) {
         const bool mine = listed && lq == q;
         const unsigned lm = __ballot_sync(0xffffffffu, mine);
         if (lm) {
@@ -1608,7 +2118,7 @@ __global__ void __launch_bounds__(kCellBlock) k_offsets_flux(EngineDev E, int wp
         }
     }
     if (g == 0) {
-        for (int q = 0; q < 4; ++q) E.ticket[q] = 0;
+        for (int q = 0; q < kLists; ++q) E.ticket[q] = 0;
         E.ticket[kSampleCtr] = 0;
     }
     if (g >= E.G_run) return;
@@ -1978,6 +2488,18 @@ int stream_occupancy(int fp32, int variant, int threads)
     return occupancy_of(k_stream<RecD, 1>, threads, smem, mx);
 }
 
+size_t staged_smem_bytes(int fp32)
+{
+    return fp32 ? sizeof(BlockShared<RecF>) : sizeof(BlockShared<RecD>);
+}
+
+int staged_occupancy(int fp32)
+{
+    const size_t smem = staged_smem_bytes(fp32);
+    return fp32 ? occupancy_of(k_cellblock<RecF>, kBlockThreads, smem, smem)
+                : occupancy_of(k_cellblock<RecD>, kBlockThreads, smem, smem);
+}
+
 int collide_occupancy(int fp32)
 {
     const size_t smem = collide_smem_bytes(fp32);
@@ -2013,6 +2535,14 @@ cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaS
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
+{
+    const size_t smem = staged_smem_bytes(fp32);
+    cudaError_t e = fp32 ? launch_prio(k_cellblock<RecF>, grid, kBlockThreads, smem, s, prio, E, rp)
+                         : launch_prio(k_cellblock<RecD>, grid, kBlockThreads, smem, s, prio, E, rp);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s, int phase,
                           int prio)
 {
@@ -2040,18 +2570,41 @@ cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Cells per block of the cell and offset kernels.  Their per-cell work is a chain of double-precision
+// operations (primitive state, Eq. (p), the wave flux), and an SM's double-precision units are few: a
+// small pool is spread over as many SMs as it can fill (two blocks each) instead of a few full blocks.
+static int cell_block(int cells, int nsm)
+{
+    for (int b = kCellBlockMin; b < kCellBlock; b *= 2)
+        if (cells <= b * 2 * nsm) return b;
+    return kCellBlock;
+}
+
+template <typename Rec>
+static cudaError_t launch_cells_b(const EngineDev &E, int b, int grid, int q, int update, cudaStream_t s)
+{
+    if (b == 32) k_cells<Rec, 32><<<grid, 32, 0, s>>>(E, q, update);
+    else if (b == 64) k_cells<Rec, 64><<<grid, 64, 0, s>>>(E, q, update);
+    else if (b == 128) k_cells<Rec, 128><<<grid, 128, 0, s>>>(E, q, update);
+    else k_cells<Rec, kCellBlock><<<grid, kCellBlock, 0, s>>>(E, q, update);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaStream_t s)
 {
-    const int grid = (E.G_run + kCellBlock - 1) / kCellBlock;
-    if (fp32) k_cells<RecF><<<grid, kCellBlock, 0, s>>>(E, q, update);
-    else k_cells<RecD><<<grid, kCellBlock, 0, s>>>(E, q, update);
-    return cudaGetLastError();
+    const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
+    const int grid = (E.G_run + b - 1) / b;
+    return fp32 ? launch_cells_b<RecF>(E, b, grid, q, update, s) : launch_cells_b<RecD>(E, b, grid, q, update, s);
 }
 
 cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStream_t s)
 {
-    const int grid = (E.G_run + kCellBlock - 1) / kCellBlock;
-    k_offsets_flux<<<grid, kCellBlock, 0, s>>>(E, wp, advance);
+    const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
+    const int grid = (E.G_run + b - 1) / b;
+    if (b == 32) k_offsets_flux<32><<<grid, 32, 0, s>>>(E, wp, advance);
+    else if (b == 64) k_offsets_flux<64><<<grid, 64, 0, s>>>(E, wp, advance);
+    else if (b == 128) k_offsets_flux<128><<<grid, 128, 0, s>>>(E, wp, advance);
+    else k_offsets_flux<kCellBlock><<<grid, kCellBlock, 0, s>>>(E, wp, advance);
     return cudaGetLastError();
 }
 

@@ -7,11 +7,15 @@
 
 namespace duwp {
 
-// Collision kernel of one step (cells of the work list): NTC collisions in place, or absorption,
-// re-sampling and collisions into the staged list.  rp = parity of the buffer holding the arrived
+// Collision kernel of one step (direct cells of the work lists): NTC collisions in place, after the
+// re-sampled particles of the cells that have any.  rp = parity of the buffer holding the arrived
 // lists.  grid: persistent CTAs of collide_threads() threads.  prio: scheduling priority of the
 // launch (cudaLaunchAttributePriority; a smaller number is a higher priority).
 cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
+// Staged-cell kernel of one step (cells with P > 0): absorption, re-sampling and collisions into the
+// staged list, one block per cell.  grid: persistent blocks (staged_occupancy() per SM).
+cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
+int staged_occupancy(int fp32);
 // Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).  phase 0:
 // every cell; 1: only the cells that need nothing from the collision kernel (stream class, nothing
 // re-sampled); 2: the other cells.

@@ -267,11 +267,15 @@ class Solver:
         _chk(self.L.duwp_sync(self.h), "duwp_sync")
 
     KERNELS = ("k_collide", "k_stream", "k_far_sort", "k_cells", "k_offsets_flux")
+    TIMED_SLOTS = 7
+    # slot of each kernel in step_timed's kernel_ms (slot 5: the span of all steps)
+    KERNEL_SLOTS = {"k_staged": 6, "k_collide": 0, "k_stream": 1, "k_far_sort": 2, "k_cells": 3, "k_offsets_flux": 4}
 
     def step_timed(self, n: int):
-        """n steps as plain launches with CUDA events around each kernel: returns (kernel_ms[6]: summed
-        over the steps for the kernels named in KERNELS, then the span of all n steps; per-step ms)."""
-        k = np.zeros(6, np.float64)
+        """n steps as plain launches with CUDA events around each kernel: returns (kernel_ms[7]: summed
+        over the steps for the kernels named in KERNELS, then the span of all n steps, then the
+        staged-cell kernel k_staged; per-step ms)."""
+        k = np.zeros(self.TIMED_SLOTS, np.float64)
         st = np.zeros(int(n), np.float64)
         _chk(self.L.duwp_step_timed(self.h, int(n), _dptr(k), _dptr(st)), "duwp_step_timed")
         return k, st
