@@ -247,25 +247,22 @@ def oracle_all_cores(params_list, budget_s: float = 10.0):
 
 
 # ---------------------------------------------------------------------------- serving
-def run_serving(args, rank: int, world: int):
+def serving_run(serve_seconds: float, device: int = 0) -> dict:
     """Continuous batching under Poisson arrivals (50 requests/s of shock and Sod problems, cells
     log-uniform in [100, 1e4], 100-1000 particles per cell, Kn log-uniform in [1e-4, 1]): arrivals
-    are replayed in real time for --serve-seconds, then the server drains; one JSON line with the
-    p50/p99 solve latency (arrival -> result) and the aggregate particle-updates/s."""
-    if rank != 0:
-        return
-    import torch
+    are replayed in real time for serve_seconds, then the server drains.  Returns the p50/p99 solve
+    latency (arrival -> result) and the aggregate particle-updates/s."""
     from paper_2305_12071_gb300 import build as B
     from paper_2305_12071_gb300 import duwp
     from paper_2305_12071_gb300 import workloads as W
     B.build()
-    reqs = W.serving_mix(duration_s=args.serve_seconds, rate_hz=50.0, precision="fp32")
+    reqs = W.serving_mix(duration_s=serve_seconds, rate_hz=50.0, precision="fp32")
     srv = duwp.Server(hbm_budget_bytes=96 << 30, max_slots=128, max_cells=1_000_000, steps_per_launch=10,
-                      precision="fp32", device=int(os.environ.get("LOCAL_RANK", 0)))
+                      precision="fp32", device=device)
     pending, lat, queue_ms, run_ms = {}, [], [], []
     updates, i, failed = 0, 0, 0
     t0 = time.perf_counter()
-    limit = 20.0 * args.serve_seconds + 60.0
+    limit = 20.0 * serve_seconds + 60.0
     while (i < len(reqs) or pending) and time.perf_counter() - t0 < limit:
         now = time.perf_counter() - t0
         while i < len(reqs) and reqs[i][0] <= now:
@@ -288,17 +285,93 @@ def run_serving(args, rank: int, world: int):
     def pct(v, q):
         return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)] if v else None
 
-    print(json.dumps({"metric": "serving solve latency (arrival -> result)", "value": pct(lat_s, 0.5), "unit": "s",
-                      "p50_s": pct(lat_s, 0.5), "p99_s": pct(lat_s, 0.99), "higher_is_better": False,
-                      "requests": len(reqs), "completed": len(lat), "failed": failed,
-                      "unfinished": len(pending), "wall_s": wall,
-                      "particle_updates_per_s": updates / wall if wall > 0 else None,
-                      "queue_ms_p50": pct(sorted(queue_ms), 0.5), "run_ms_p50": pct(sorted(run_ms), 0.5),
-                      "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "serving_poisson50_mixed_fp32", "arrivals_s": args.serve_seconds,
-                                 "rate_hz": 50, "cells": "log-U[100,1e4]", "ppc_ref": "U[100,1000]",
-                                 "Kn": "log-U[1e-4,1]", "shock_steps": 500, "sod_steps": "to t = 0.15 at CFL 0.5",
-                                 "steps_per_launch": 10, "max_slots": 128}}), flush=True)
+    return {"metric": "serving solve latency (arrival -> result)", "value": pct(lat_s, 0.5), "unit": "s",
+            "p50_s": pct(lat_s, 0.5), "p99_s": pct(lat_s, 0.99), "higher_is_better": False,
+            "requests": len(reqs), "completed": len(lat), "failed": failed,
+            "unfinished": len(pending), "wall_s": wall,
+            "particle_updates_per_s": updates / wall if wall > 0 else None,
+            "queue_ms_p50": pct(sorted(queue_ms), 0.5), "run_ms_p50": pct(sorted(run_ms), 0.5),
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_poisson50_mixed_fp32", "arrivals_s": serve_seconds,
+                       "rate_hz": 50, "cells": "log-U[100,1e4]", "ppc_ref": "U[100,1000]",
+                       "Kn": "log-U[1e-4,1]", "shock_steps": 500, "sod_steps": "to t = 0.15 at CFL 0.5",
+                       "steps_per_launch": 10, "max_slots": 128}}
+
+
+def run_serving(args, rank: int, world: int):
+    if rank != 0:
+        return
+    print(json.dumps(serving_run(args.serve_seconds, int(os.environ.get("LOCAL_RANK", 0)))), flush=True)
+
+
+# ---------------------------------------------------------------------------- the other configurations
+# (key, workload, timed steps, warm-up steps): the configurations beside the headline batch, each as
+# the step count it is specified with (configs 1, 2, 4; config 5 is the serving run)
+SECONDARY = (
+    ("config1_mach3_shock_100cells_fp64", "mach3", 500, 5),
+    ("config2_sod_1000cells_kn1e-4..1_fp32", "sod_kn", 2000, 5),
+    ("config2_sod_1000cells_kn1e-4_fp32", "sod", 2000, 5),
+    ("config4_mach8_shock_1e5cells_fp32", "mach8", 200, 3),
+    ("config4_mach8_shock_1e5cells_fp64", "mach8_fp64", 200, 3),
+)
+
+
+def secondary_run(name: str, steps: int, warmup: int, device: int, peak: float, oracle_budget_s: float = 3.0):
+    """One configuration on one GPU: K steps timed as the library runs them (events per step), the
+    kernels timed one by one over up to 20 steps (the streaming kernel's roofline), and the oracle
+    on a bounded sample of the same instances when they are small enough."""
+    import torch
+    from paper_2305_12071_gb300 import autotune, duwp
+    plist, cfg = workload(name)
+    rec_bytes = 16 if plist[0].get("precision", "fp64") == "fp32" else 32
+    sol = duwp.Solver(plist, device=device)
+    sol.step(warmup)
+    sol.sync()
+    (t_best, r_best), _ = autotune.tune(sol)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    u0 = sol.particle_updates()
+    with torch.cuda.stream(sol.stream):
+        evs[0].record()
+    for j in range(steps):
+        sol.step(1)
+        with torch.cuda.stream(sol.stream):
+            evs[j + 1].record()
+    sol.sync()
+    upd = sol.particle_updates() - u0
+    step_ms = sorted(evs[j].elapsed_time(evs[j + 1]) for j in range(steps))
+    span = evs[0].elapsed_time(evs[-1]) / 1e3
+    kt = min(steps, 20)
+    u2 = sol.particle_updates()
+    kms, _ = sol.step_timed(kt)
+    upl = (sol.particle_updates() - u2) / kt
+    slots = duwp.Solver.KERNEL_SLOTS
+    k_ms = kms[slots["k_stream"]] / kt
+    achieved = rec_bytes * 2 * upl / (k_ms * 1e-3) / 1e9
+    out = {"value": upd / span, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * span / steps,
+           "step_ms_p50": step_ms[len(step_ms) // 2],
+           "step_ms_p99": step_ms[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
+           "dtype": "f32" if rec_bytes == 16 else "f64", "config": dict(cfg, launch={"threads": t_best, "reg_capped": r_best}),
+           "particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
+           "kernel_ms_per_step": {n: float(kms[i] / kt) for n, i in slots.items()},
+           "roofline": {"bound": "hbm", "kernel": "k_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "algorithmic_bytes_per_update": rec_bytes * 2,
+                        "updates_per_launch": upl, "launch_ms": k_ms}}
+    sol.close()
+    del sol
+    torch.cuda.empty_cache()
+    # the oracle (one host core) on a bounded sample: one instance per distinct problem, rounds of
+    # one step each until about oracle_budget_s seconds
+    est = sum(int(p["n_cells"]) * float(p["ppc_ref"]) for p in plist[:1])
+    if est <= 2e6:
+        idx = list(range(0, len(plist), max(1, len(plist) // 5)))[:5]
+        ups, secs, rounds = oracle_sample(plist, idx, min_steps=1, budget_s=oracle_budget_s)
+        out["cpu_baseline"] = {"value": ups / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"instances {idx}, 1 untimed + {rounds} timed steps each"}
+    else:
+        out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "not run: the instance exceeds a bounded oracle sample"}
+    return out
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -355,6 +428,10 @@ def main():
                     help="wave-flux interface states: first order (default) or van Leer reconstruction")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of --workload serve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (Mach-3, Sod, Mach-8 FP32/FP64, serving) beside the headline")
+    ap.add_argument("--latency-seconds", type=float, default=1.0,
+                    help="steps run after the timed region for the step-latency percentiles")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--launch", default="", help="streaming-kernel launch shape threads,reg_capped "
                                                  "(skips the autotuner)")
@@ -448,6 +525,22 @@ def main():
         span_all, updates_all = span_s, float(updates)
     value = updates_all / span_all
 
+    # ------------------------------------------------ step latency: further steps, one event each, for
+    # about latency_seconds (p50/p99 over many steps; the throughput above is the K timed steps alone)
+    lat_ms = []
+    t_lat = time.perf_counter()
+    while time.perf_counter() - t_lat < args.latency_seconds and len(lat_ms) < 100_000:
+        chunk = [torch.cuda.Event(enable_timing=True) for _ in range(51)]
+        with torch.cuda.stream(sol.stream):
+            chunk[0].record()
+        for j in range(50):
+            sol.step(1)
+            with torch.cuda.stream(sol.stream):
+                chunk[j + 1].record()
+        sol.sync()
+        lat_ms += [chunk[j].elapsed_time(chunk[j + 1]) for j in range(50)]
+    lat_ms.sort()
+
     # ------------------------------------------------ the same number of steps kernel by kernel, events
     # around each kernel (no overlap): per-kernel times and the streaming kernel's roofline
     u2 = sol.particle_updates()
@@ -499,8 +592,13 @@ def main():
                "warmup": args.warmup, "ms_per_step": 1e3 * span_all / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
                "data": "synthetic (seeded shock/Sod problems shaped like the paper's test cases)",
-               "config": cfg, "clocks": clocks, "gpu_launches": 6 * args.steps,
+               "config": cfg, "clocks": clocks, "gpu_launches": 7 * args.steps,
                "step_ms_p50": p50, "step_ms_p99": p99, "serial_ms_per_step": serial_ms,
+               "step_latency": {"steps": len(lat_ms), "p50_ms": lat_ms[len(lat_ms) // 2] if lat_ms else None,
+                                "p99_ms": lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]
+                                if lat_ms else None,
+                                "note": "steps after the timed region, one event each, for about "
+                                        f"{args.latency_seconds} s"},
                "kernel_ms_per_step": {n: float(kms[i] / args.steps) for n, i in slots.items()},
                "kernel_times": "from the same number of steps run kernel by kernel with events around each",
                "kernel_share": kernel_share, "roofline": roof,
@@ -597,6 +695,21 @@ def main():
                 "seconds": asecs}
         else:
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    # ------------------------------------------------ the other configurations, on this GPU, after the rest
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "batch64" and args.split == "p" \
+            and args.recon == "first" and not args.instances:
+        peak, _ = measured_peaks()
+        configs = {}
+        for key, name, steps, warm in SECONDARY:
+            try:
+                configs[key] = secondary_run(name, steps, warm, local, peak)
+            except Exception as e:          # a configuration that cannot run is reported, not hidden
+                configs[key] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            configs["config5_serving_poisson50"] = serving_run(args.serve_seconds, local)
+        except Exception as e:
+            configs["config5_serving_poisson50"] = {"error": f"{type(e).__name__}: {e}"}
+        out["configs"] = configs
     if out is not None:
         print(json.dumps(out), flush=True)
     if dist is not None:
