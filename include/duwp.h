@@ -321,6 +321,40 @@ int duwp_checkpoint_restore(duwp_handle *h, const void *host_buf, uint64_t bytes
 int duwp_get_particles_noalloc(duwp_handle *h, int32_t inst, int32_t *dev_cell, double *dev_xl,
                                double *dev_u, double *dev_v, double *dev_w, int64_t n);
 
+/* ------------------------------------------------------------------ one instance over several parts */
+
+/* One instance split into `parts` contiguous cell ranges of nearly equal size (part r owns cells
+ * [n_cells r / parts, n_cells (r+1) / parts)), each part an engine of its own -- on the calling
+ * thread's current device, or on devices[r] when `devices` (parts entries) is given -- stepped in
+ * lockstep.  The method is per cell (Sec. 3.4): absorption, re-sampling and collisions act on one
+ * cell's list, the transport moves particles between cells (Step 3), and the update of a cell reads
+ * the wave flux of its two faces (Eq. r1).  So every step each part receives from its neighbours
+ * the particles that crossed into its cells (the run of the neighbour's edge cell moving one cell
+ * across, with its exact moment sums, and the farther movers with their global sort keys) and the
+ * state of the neighbouring edge cell (a one-cell halo, for the flux of the boundary face and the
+ * NS-corrected sampling).  Every cell then sees the list, generator ids and sums of the undivided
+ * run: the results equal duwp_init's bit for bit.  The exchange goes through the host and device
+ * copies (peer copies between GPUs); no kernel waits on another part.
+ * Not supported (DUWP_EINVAL): periodic ends, DUWP_RECON_VANLEER (it reads two cells beyond a face).
+ * Allocation as duwp_init (every part through alloc/free_fn when given).  Errors: DUWP_EINVAL,
+ * DUWP_ENOMEM, DUWP_ECUDA; a run of crossing particles larger than the space reserved for it, or a
+ * full far-mover list, is DUWP_EOVERFLOW from duwp_split_step. */
+typedef struct duwp_split duwp_split;
+int duwp_split_create(const duwp_params *params, int32_t parts, const int32_t *devices, duwp_alloc_fn alloc,
+                      duwp_free_fn free_fn, void *alloc_ctx, duwp_split **out);
+
+/* Synchronizing.  n_steps >= 0 steps of every part (Steps 1-4 of Sec. 3.4, with the exchanges).
+ * Errors: DUWP_EINVAL, DUWP_ECUDA, DUWP_EOVERFLOW and the device errors of the parts. */
+int duwp_split_step(duwp_split *s, int32_t n_steps);
+
+/* Part r: its handle (owned by the split: inspect it with duwp_fields, duwp_get_particles, ...,
+ * whose cell indices are local, cell i being cell c0 + i of the domain; do not step or destroy it)
+ * and its cell range [c0, c1).  Any output pointer may be NULL.  Errors: DUWP_EINVAL. */
+int duwp_split_part(duwp_split *s, int32_t r, duwp_handle **part, int32_t *c0, int32_t *c1);
+
+/* Release every part. */
+int duwp_split_destroy(duwp_split *s);
+
 /* ------------------------------------------------------------------ serving (continuous batching) */
 
 typedef struct duwp_server duwp_server;

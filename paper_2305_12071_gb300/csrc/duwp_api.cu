@@ -127,6 +127,28 @@ int derive_instance(const duwp_params &p, HostInst &o)
     return DUWP_OK;
 }
 
+int derive_part(const duwp_params &p, int32_t c0, int32_t c1, HostInst &o)
+{
+    if (c0 < 0 || c1 > p.n_cells || c0 >= c1) return DUWP_EINVAL;
+    // the split keeps the undivided order between non-periodic ends, with one phantom cell per side
+    // (first-order interface states of the wave flux)
+    if (p.bc_left == DUWP_BC_PERIODIC || p.recon_mode != DUWP_RECON_FIRST) return DUWP_EINVAL;
+    const int rc = derive_instance(p, o);
+    if (rc != DUWP_OK) return rc;
+    o.p.n_cells = c1 - c0;
+    o.d.C = c1 - c0;
+    o.d.id0 = c0;
+    if (c0 > 0) o.d.bc_left = kBcPhantom;
+    if (c1 < p.n_cells) o.d.bc_right = kBcPhantom;
+    double mass = 0.0;
+    for (int32_t i = c0; i < c1; ++i) {
+        const double xc = p.x_min + (static_cast<double>(i) + 0.5) * o.d.dx;
+        mass += (xc < p.x_split ? p.left.rho : p.right.rho) * o.d.dx;
+    }
+    o.est_particles = static_cast<int64_t>(std::ceil(mass / o.d.mp));
+    return DUWP_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // Engine
 // ------------------------------------------------------------------------------------------
@@ -244,12 +266,13 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     int64_t est = 0;
     int64_t cells = 0;
     double max_ppc = 0.0;
+    if (part_c1 >= 0 && n != 1) return DUWP_EINVAL;
     for (int32_t b = 0; b < n; ++b) {
-        const int rc = derive_instance(params[b], hs[b]);
+        const int rc = (part_c1 >= 0) ? derive_part(params[b], part_c0, part_c1, hs[b]) : derive_instance(params[b], hs[b]);
         if (rc != DUWP_OK) return rc;
         if (params[b].precision != params[0].precision) return DUWP_EINVAL;
         est += hs[b].est_particles;
-        cells += params[b].n_cells + 2;
+        cells += hs[b].p.n_cells + 2;
         const double rmax = std::max(params[b].left.rho, params[b].right.rho) / params[b].rho_ref;
         max_ppc = std::max(max_ppc, rmax * params[b].ppc_ref);
     }
@@ -268,7 +291,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     else if (cap_user > 0) cap = static_cast<int64_t>(cap_user);
     if (cap >= (int64_t(1) << 40)) return DUWP_EINVAL;
     capacity = cap;
-    (void)max_ppc;
+
     far_cap = 1 << 16;
 
     const size_t rec = fp32 ? sizeof(RecF) : sizeof(RecD);
@@ -314,8 +337,11 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_wls = c.take<int2>(size_t(wls_cap));
     const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
     const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
-    const size_t o_buf0 = c.take<unsigned char>(rec * size_t(capacity));
-    const size_t o_buf1 = c.take<unsigned char>(rec * size_t(capacity));
+    // each buffer: the output blocks, then (one part of a split domain) the runs arriving in its two
+    // phantom cells from the neighbouring parts
+    if (part_c1 >= 0) pcap = 2 * ((4 * static_cast<int64_t>(std::ceil(max_ppc)) + 1024) / 2);
+    const size_t o_buf0 = c.take<unsigned char>(rec * size_t(capacity + 2 * pcap));
+    const size_t o_buf1 = c.take<unsigned char>(rec * size_t(capacity + 2 * pcap));
     slab_bytes = (c.off + 255) & ~static_cast<size_t>(255);
     slab = dalloc(slab_bytes);
     if (!slab) return DUWP_ENOMEM;
@@ -377,7 +403,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     for (int32_t b = 0; b < n; ++b) {
         rc = add_instance(b, params[b], gb, false);
         if (rc != DUWP_OK) return rc;
-        gb += params[b].n_cells + 2;
+        gb += inst[b].p.n_cells + 2;
     }
     // the instance table in one copy (a copy from pageable memory waits for the stream), then the
     // cells of every instance
@@ -401,10 +427,10 @@ int Engine::add_instance(int slot, const duwp_params &p, int32_t cell_base, bool
 {
     if (slot < 0 || slot >= max_inst) return DUWP_EINVAL;
     HostInst h;
-    int rc = derive_instance(p, h);
+    int rc = (part_c1 >= 0) ? derive_part(p, part_c0, part_c1, h) : derive_instance(p, h);
     if (rc != DUWP_OK) return rc;
     if ((p.precision == DUWP_FP32) != (fp32 == 1)) return DUWP_EINVAL;
-    if (cell_base < 0 || int64_t(cell_base) + p.n_cells + 2 > G) return DUWP_EINVAL;
+    if (cell_base < 0 || int64_t(cell_base) + h.p.n_cells + 2 > G) return DUWP_EINVAL;
     h.cell_base = cell_base;
     h.d.cell_base = cell_base;
     inst[slot] = h;
@@ -455,19 +481,10 @@ int Engine::enqueue_prepare()
     return DUWP_OK;
 }
 
-int Engine::enqueue_step(cudaEvent_t *ev)
+int Engine::enqueue_phase(int ph)
 {
     const int rp = parity;
-    if (ev) {
-        // timed: one kernel after the other, events around each
-        DUWP_CU(cudaEventRecord(ev[6], stream));
-        DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, stream, prio_hi));
-        DUWP_CU(cudaEventRecord(ev[0], stream));
-        DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
-        DUWP_CU(cudaEventRecord(ev[1], stream));
-        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 0, prio_hi));
-        DUWP_CU(cudaEventRecord(ev[2], stream));
-    } else {
+    if (ph == 1) {
         // the block kernel (cells with many candidates) and the collision kernel (the other cells
         // that need one) run side by side, and the free cells stream on a third stream meanwhile; the
         // other cells stream after both collision kernels; every stream joins before the far movers
@@ -483,13 +500,42 @@ int Engine::enqueue_step(cudaEvent_t *ev)
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join2, 0));
         DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 2, prio_hi));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join, 0));
+    } else if (ph == 2) {
+        DUWP_CU(launch_far_sort(dev, fp32, stream));
+        DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
+    } else {
+        DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+        parity = 1 - rp;
+    }
+    return DUWP_OK;
+}
+
+int Engine::enqueue_step(cudaEvent_t *ev)
+{
+    const int rp = parity;
+    if (!ev) {
+        for (int ph = 1; ph <= 3; ++ph) {
+            const int rc = enqueue_phase(ph);
+            if (rc != DUWP_OK) return rc;
+        }
+        return DUWP_OK;
+    }
+    {
+        // timed: one kernel after the other, events around each
+        DUWP_CU(cudaEventRecord(ev[6], stream));
+        DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, stream, prio_hi));
+        DUWP_CU(cudaEventRecord(ev[0], stream));
+        DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
+        DUWP_CU(cudaEventRecord(ev[1], stream));
+        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 0, prio_hi));
+        DUWP_CU(cudaEventRecord(ev[2], stream));
     }
     DUWP_CU(launch_far_sort(dev, fp32, stream));
-    if (ev) DUWP_CU(cudaEventRecord(ev[3], stream));
+    DUWP_CU(cudaEventRecord(ev[3], stream));
     DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
-    if (ev) DUWP_CU(cudaEventRecord(ev[4], stream));
+    DUWP_CU(cudaEventRecord(ev[4], stream));
     DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
-    if (ev) DUWP_CU(cudaEventRecord(ev[5], stream));
+    DUWP_CU(cudaEventRecord(ev[5], stream));
     parity = 1 - rp;
     return DUWP_OK;
 }

@@ -32,6 +32,11 @@ struct HostInst {
 // description.  Returns DUWP_OK or DUWP_EINVAL.
 int derive_instance(const duwp_params &p, HostInst &out);
 
+// The same for the part of the domain of p that owns cells [c0, c1) (a domain split into cell
+// ranges): global mesh, time step and generator ids; the ends that face other parts are phantom
+// ends.  Errors: DUWP_EINVAL (range, periodic ends, second-order reconstruction).
+int derive_part(const duwp_params &p, int32_t c0, int32_t c1, HostInst &out);
+
 struct Engine {
     int device = 0;
     int fp32 = 1;
@@ -50,6 +55,11 @@ struct Engine {
     int32_t variant = 0;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers)
     int32_t grid_collide = 0;   // collision kernel: persistent blocks
     int32_t grid_staged = 0;    // staged-cell kernel: persistent blocks
+    // one part of a split domain: the cells [part_c0, part_c1) of its single instance (part_c1 < 0:
+    // not a part); pcap: slots reserved at the end of each particle buffer for the runs arriving in
+    // each of the two phantom cells
+    int32_t part_c0 = 0, part_c1 = -1;
+    int64_t pcap = 0;
 
     // device memory: one slab
     void *slab = nullptr;
@@ -101,6 +111,9 @@ struct Engine {
     int init_instance_cells(int slot);
     int remove_instance(int slot);
     int enqueue_step(cudaEvent_t *ev = nullptr);   // launches of one step; ev[kStepEvents]: events around kernels
+    // one third of a step's launches: 1 collisions and streaming, 2 far-mover sort and cell update,
+    // 3 offsets and wave flux of the next step (and the parity flip)
+    int enqueue_phase(int ph);
     int enqueue_prepare();             // cell + offset kernels without advancing (start / admission)
     // Cells the step kernels cover, [0, cells) clamped to [1, G]: every active instance must lie
     // below it and the cells above it must be unused (as remove_instance leaves them).  Drops the

@@ -26,6 +26,14 @@ namespace duwp {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.283185307179586;
 
+// Boundary kind of an instance's end that faces another part of the same domain (a domain split into
+// cell ranges): no wall, no reservoir; the cell beyond the end is a phantom of the neighbouring
+// part's edge cell, whose state and incoming particle runs are copied in between the kernels.
+constexpr int kBcPhantom = 4;
+
+// Destination returned by the transport for a particle that left the domain (removed).
+constexpr int64_t kGone = INT64_MIN / 2;
+
 // Device error codes (mirrors of the public status values).
 constexpr int kErrOverflow = -7;
 constexpr int kErrTimeout = -5;
@@ -42,6 +50,8 @@ struct InstDev {
     int32_t bc_left, bc_right;
     int32_t eps_mode, flux_mode, ntc_rate, active;
     uint32_t key0, key1;    // generator key (seed)
+    int32_t id0;            // global index of local cell 0 (0 unless the instance is one part of a
+                            // domain split into cell ranges); generator id of local cell i = id0 + i + 1
     uint32_t step;          // steps completed (advanced once per step, after the cell update)
     int32_t avg_start;
     int64_t navg;           // states accumulated into the time average
@@ -95,7 +105,7 @@ struct alignas(16) CellHdr {
     int32_t i;          // local cell index (-1 and C: reservoirs)
     int32_t C;          // cells of the instance
     float dtdx_f;       // dt/dx of the instance in single precision (transport of FP32 records)
-    int32_t pad;
+    int32_t edges;      // bit 0: the left end faces a phantom cell, bit 1: the right end does
 };
 static_assert(sizeof(CellHdr) == 96, "cell header layout");
 
@@ -187,6 +197,9 @@ __device__ __forceinline__ void draw(const InstDev &I, uint32_t id, uint32_t sub
 {
     philox10(I.key0, I.key1, id, sub, step, purpose, w);
 }
+
+// Generator id of local cell i (-1 and C: the ends) of an instance.
+__device__ __forceinline__ uint32_t cell_id(const InstDev &I, int i) { return static_cast<uint32_t>(I.id0 + i + 1); }
 
 // Uniform in [0,1) with 53 random bits: 32 from the first word, 21 from the second.
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b)

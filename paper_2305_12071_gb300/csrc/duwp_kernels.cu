@@ -86,6 +86,8 @@ __device__ __forceinline__ int64_t apply_walls(const InstDev &I, int64_t dest, T
 {
     const int64_t C = I.C;
     for (int it = 0; it < 64; ++it) {
+        if ((dest < 0 && I.bc_left == kBcPhantom) || (dest >= C && I.bc_right == kBcPhantom))
+            return dest;     // into another part of the domain (phantom side): kept, exported
         if (dest < 0) {
             if (I.bc_left == 1) {
                 dest = -dest - 1;
@@ -96,7 +98,7 @@ __device__ __forceinline__ int64_t apply_walls(const InstDev &I, int64_t dest, T
                 continue;
             }
             if (I.bc_left == 2) { dest = ((dest % C) + C) % C; continue; }
-            return -1;
+            return kGone;
         }
         if (dest >= C) {
             if (I.bc_right == 1) {
@@ -108,17 +110,17 @@ __device__ __forceinline__ int64_t apply_walls(const InstDev &I, int64_t dest, T
                 continue;
             }
             if (I.bc_right == 2) { dest = dest % C; continue; }
-            return -1;
+            return kGone;
         }
         return dest;
     }
-    return -1;   // more than 64 wall reflections within one step: removed
+    return kGone;   // more than 64 wall reflections within one step: removed
 }
 
 __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, double &xl, double &u, bool &refl)
 {
     const double s = __fma_rn(u, I.dtdx, xl);
-    if (!(fabs(s) < 1e15)) return -1;
+    if (!(fabs(s) < 1e15)) return kGone;
     const double fk = floor(s);
     double x = __dsub_rn(s, fk);
     int64_t k = static_cast<int64_t>(fk);
@@ -203,10 +205,10 @@ __device__ __noinline__ bool ce_coefs(const InstDev &I, const double *prim, cons
     double wm[5], wp[5];
     bool okm, okp;
     const bool periodic = (I.bc_left == 2);
-    if (i > 0) { for (int k = 0; k < 5; ++k) wm[k] = W0[k - 5]; okm = valid[g - 1] != 0; }
+    if (i > 0 || I.bc_left == kBcPhantom) { for (int k = 0; k < 5; ++k) wm[k] = W0[k - 5]; okm = valid[g - 1] != 0; }
     else if (periodic) { for (int k = 0; k < 5; ++k) wm[k] = prim[5 * (g + I.C - 1) + k]; okm = valid[g + I.C - 1] != 0; }
     else okm = ghost_prim(I, 0, W0, true, wm);
-    if (i < I.C - 1) { for (int k = 0; k < 5; ++k) wp[k] = W0[k + 5]; okp = valid[g + 1] != 0; }
+    if (i < I.C - 1 || I.bc_right == kBcPhantom) { for (int k = 0; k < 5; ++k) wp[k] = W0[k + 5]; okp = valid[g + 1] != 0; }
     else if (periodic) { for (int k = 0; k < 5; ++k) wp[k] = prim[5 * (g - I.C + 1) + k]; okp = valid[g - I.C + 1] != 0; }
     else okp = ghost_prim(I, 1, W0, true, wp);
     const double *a = okm ? wm : W0, *b = okp ? wp : W0;
@@ -313,7 +315,7 @@ __device__ __noinline__ void sample_run_ce(const InstDev &I, const double *prim,
     CeCell ce;
     const bool on = ce_coefs(I, prim, valid, g, i, ce);
     for (int j = j0 + lane; j < j1; j += 32)
-        st_rec(dst + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), step, mc, on ? &ce : nullptr));
+        st_rec(dst + j, sample_particle<Rec>(I, cell_id(I, i), static_cast<uint32_t>(j), step, mc, on ? &ce : nullptr));
 }
 
 // Lower bound of `key` in the far list ordered by (dest, src, q): first index with (dest, src) >= key.
@@ -703,7 +705,7 @@ __device__ __noinline__ void collide_direct(const EngineDev &E, int g, CollideSh
     const CellHdr *hp = E.hdr + (g >= 0 ? g : 0);
     const InstDev &I = E.inst[g >= 0 ? hp->b : 0];
     const int N = (g >= 0) ? hp->n_in : 0, nc = (g >= 0) ? hp->nc : 0;
-    const uint32_t id = static_cast<uint32_t>(hp->i + 1), step = I.step;
+    const uint32_t id = cell_id(I, hp->i), step = I.step;
     for (int t = l; t < NS; t += Z) { key[t] = -1; own[t] = 32; mod[t] = 0; }
     __syncwarp();
     const bool act = l < nc;
@@ -820,7 +822,7 @@ __device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShare
     const CellHdr *hp = E.hdr + g;
     const InstDev &I = E.inst[hp->b];
     const int nc = hp->nc, n_in = hp->n_in, nn = hp->n_new, i = hp->i;
-    const uint32_t id = static_cast<uint32_t>(i + 1), step = I.step;
+    const uint32_t id = cell_id(I, i), step = I.step;
     Rec *blk = out + hp->off;
     if (nn > 0) {
         if (I.resample_mode == 1) {
@@ -861,7 +863,7 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
+    const uint32_t id = cell_id(I, h.i), step = I.step;
     const double P = E.P[g];
     const bool all = !(P < 1.0);                       // u53 < 1 always
     const uint32_t T = all ? 0u : static_cast<uint32_t>(floor(P * 4294967296.0));
@@ -1311,7 +1313,7 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
     const CellHdr &h = S.hdr;
     const InstDev &I = E.inst[h.b];
     const bool staged = h.cls == kClsStaged;
-    const uint32_t id = static_cast<uint32_t>(h.i + 1), step = I.step;
+    const uint32_t id = cell_id(I, h.i), step = I.step;
     Rec *blk = out + h.off;
     // the cell's sampling state, by one thread of the last warp while the others absorb
     if (t == kBlockThreads - 32 && (!staged || E.valid[g]) && (staged || h.n_new > 0)) {
@@ -1461,7 +1463,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
         }
         const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
         for (int j = j0 + lane; j < j1; j += 32)
-            st_rec(out + off + n_in + j, sample_particle<Rec>(I, static_cast<uint32_t>(i + 1), static_cast<uint32_t>(j), I.step, mc,
+            st_rec(out + off + n_in + j, sample_particle<Rec>(I, cell_id(I, i), static_cast<uint32_t>(j), I.step, mc,
                                                               nullptr));
     }
 }
@@ -1507,7 +1509,7 @@ struct StreamState {
 __device__ __forceinline__ int64_t transport_full(const InstDev &I, int64_t cell, float &xl, float &u, bool &refl)
 {
     const float s = __fmaf_rn(u, I.dtdx_f, xl);
-    if (!(fabsf(s) < 1e15f)) return -1;
+    if (!(fabsf(s) < 1e15f)) return kGone;
     const float fk = floorf(s);
     float x = __fsub_rn(s, fk);
     int64_t k = static_cast<int64_t>(fk);
@@ -1537,7 +1539,7 @@ __device__ __forceinline__ int stream_rare(const EngineDev &E, int g, int k, Rec
     bool refl = false;
     const int64_t d = transport_full(I, ci, v.xl, v.u, refl);
     int c;
-    if (d < 0) c = 4;
+    if (d == kGone) c = 4;
     else if (d == ci) c = 1;
     else if (d == ci - 1) c = 0;
     else if (d == ci + 1) c = 2;
@@ -1572,10 +1574,11 @@ __device__ __forceinline__ int stream_rare(const EngineDev &E, int g, int k, Rec
 }
 
 // Common path of the transport: c in {0, 1, 2} for the same or a neighbouring cell inside the
-// domain; 4 for a particle of an inflow/outflow reservoir (ci = -1 or C) that stays outside the
-// domain on the reservoir's side (discarded: a reservoir keeps only what enters, and its own
+// cells [lo, lo + width) (the domain, and the phantom cell beyond an end that faces another part of
+// a split domain); 4 for a particle of an inflow/outflow reservoir (ci = -1 or C) that stays outside
+// the domain on the reservoir's side (discarded: a reservoir keeps only what enters, and its own
 // moment sums are not used); -1 for everything else (general path).
-__device__ __forceinline__ int move_near(float dtdx, int C, int ci, float &xl, float u)
+__device__ __forceinline__ int move_near(float dtdx, int C, int lo, int width, int ci, float &xl, float u)
 {
     const float s = __fmaf_rn(u, dtdx, xl);
     if (!(fabsf(s) < 1073741824.0f)) return -1;
@@ -1585,14 +1588,14 @@ __device__ __forceinline__ int move_near(float dtdx, int C, int ci, float &xl, f
     if (x >= 1.0f) { x = 0.0f; k += 1; }
     const unsigned dd = static_cast<unsigned>(k + 1);
     const int d = ci + k;                        // |ci| <= 2^30, |k| <= 2^30: no overflow
-    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) {
+    if (dd >= 3u || static_cast<unsigned>(d - lo) >= static_cast<unsigned>(width)) {
         if ((d < 0 && ci < 0) || (d >= C && ci >= C)) return 4;
         return -1;
     }
     xl = x;
     return static_cast<int>(dd);
 }
-__device__ __forceinline__ int move_near(double dtdx, int C, int ci, double &xl, double u)
+__device__ __forceinline__ int move_near(double dtdx, int C, int lo, int width, int ci, double &xl, double u)
 {
     const double s = __fma_rn(u, dtdx, xl);
     if (!(fabs(s) < 1073741824.0)) return -1;
@@ -1602,7 +1605,7 @@ __device__ __forceinline__ int move_near(double dtdx, int C, int ci, double &xl,
     if (x >= 1.0) { x = 0.0; k += 1; }
     const unsigned dd = static_cast<unsigned>(k + 1);
     const int d = ci + k;
-    if (dd >= 3u || static_cast<unsigned>(d) >= static_cast<unsigned>(C)) {
+    if (dd >= 3u || static_cast<unsigned>(d - lo) >= static_cast<unsigned>(width)) {
         if ((d < 0 && ci < 0) || (d >= C && ci >= C)) return 4;
         return -1;
     }
@@ -1731,6 +1734,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
     if constexpr (sizeof(T) == 4) dtdx = hp->dtdx_f;
     else dtdx = E.inst[hp->b].dtdx;
     const int C = hp->C, ci = hp->i;
+    const int lo = -(hp->edges & 1), width = C + (hp->edges & 1) + ((hp->edges >> 1) & 1);
     const unsigned lt = (1u << lane) - 1u;
     StreamState st;
     st.oS = 0;
@@ -1780,7 +1784,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
                 if (base + 32 * u2 >= n) break;
                 int c = 5;
                 if (r < n) {
-                    c = move_near(dtdx, C, ci, v[u2].xl, v[u2].u);
+                    c = move_near(dtdx, C, lo, width, ci, v[u2].xl, v[u2].u);
                     if (c < 0) c = stream_rare<Rec>(E, g, k0 + r, v[u2], acc, st);
                 }
                 const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
@@ -1881,7 +1885,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
         hd.i = 0;
         hd.C = 0;
         hd.dtdx_f = 0.0f;
-        hd.pad = 0;
+        hd.edges = 0;
         const int b = E.cell_inst[g];
         if (b >= 0) {
             const InstDev &I = E.inst[b];
@@ -1891,6 +1895,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
             hd.i = i;
             hd.C = I.C;
             hd.dtdx_f = I.dtdx_f;
+            hd.edges = (I.bc_left == kBcPhantom ? 1 : 0) | (I.bc_right == kBcPhantom ? 2 : 0);
             if (i < 0 || i >= I.C) {
                 const int side = (i < 0) ? 0 : 1;
                 const int bc = side ? I.bc_right : I.bc_left;
@@ -1898,7 +1903,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                     double qg[5];
                     const bool ok = ghost_prim(I, side, qg, false, qg);
                     const double Pg = split_fraction(I, qg, ok);
-                    myslots = ok ? resample_count(I, static_cast<uint32_t>(i + 1), step_next, Pg, qg[0]) : 0;
+                    myslots = ok ? resample_count(I, cell_id(I, i), step_next, Pg, qg[0]) : 0;
                     for (int k = 0; k < 5; ++k) E.prim[5 * g + k] = qg[k];
                     E.valid[g] = ok ? 1 : 0;
                     E.P[g] = Pg;
@@ -1914,7 +1919,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                 if (nf > 0) {
                     const FarItem<Rec> *fs = static_cast<const FarItem<Rec> *>(E.far_sorted);
                     lo = far_lower(fs, nf, g, INT32_MIN);
-                    mid = far_lower(fs, nf, g, g + 2);
+                    mid = far_lower(fs, nf, g, g + 1);
                     const int hi = far_lower(fs, nf, g + 1, INT32_MIN);
                     farn = hi - lo;
                     for (int k = lo; k < hi; ++k) {
@@ -1961,7 +1966,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                 int64_t extra = 0;
                 if (ok) {
                     if (P == 0.0) {
-                        extra = resample_count(I, static_cast<uint32_t>(i + 1), step_next, 0.0,
+                        extra = resample_count(I, cell_id(I, i), step_next, 0.0,
                                                psi[0] - static_cast<double>(arrivals) * I.mp_over_dx);
                     } else {
                         extra = static_cast<int64_t>(floor(((1.0 - P) * fmax(psi[0], 0.0)) * I.dx_over_mp)) + 2;
@@ -1974,7 +1979,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                     hd.cls = kClsStaged;
                 } else {
                     const int64_t n_tot = arrivals + extra;
-                    const int64_t nc = ntc_candidates(I, static_cast<uint32_t>(i + 1), step_next,
+                    const int64_t nc = ntc_candidates(I, cell_id(I, i), step_next,
                                                       static_cast<int>(n_tot), psi[0], E.cmax[g], E.fmaj[g]);
                     hd.n_new = static_cast<int32_t>(extra);
                     if (nc < 0 || n_tot > INT32_MAX) {
@@ -2138,6 +2143,10 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
             const int gg = I.cell_base + I.C;
             for (int k = 0; k < 5; ++k) a[k] = E.prim[5 * gg + k];
             aok = E.valid[gg] != 0;
+        } else if (I.bc_left == kBcPhantom) {
+            // the neighbouring part's edge cell, copied into the phantom cell g
+            for (int k = 0; k < 5; ++k) a[k] = E.prim[5 * g + k];
+            aok = E.valid[g] != 0;
         } else {
             aok = ghost_prim(I, 0, c, cok, a);
         }
@@ -2147,6 +2156,9 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
             const int gg = I.cell_base + 1;
             for (int k = 0; k < 5; ++k) c[k] = E.prim[5 * gg + k];
             cok = E.valid[gg] != 0;
+        } else if (I.bc_right == kBcPhantom) {
+            for (int k = 0; k < 5; ++k) c[k] = E.prim[5 * (g + 1) + k];
+            cok = E.valid[g + 1] != 0;
         } else {
             cok = ghost_prim(I, 1, a, aok, c);
         }
@@ -2208,7 +2220,7 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     for (int k = 0; k < 5; ++k) { E.Aself[5 * g + k] = 0; E.avg[5 * g + k] = 0.0; E.flux[5 * g + k] = 0.0; E.psi[5 * g + k] = 0.0; E.prim[5 * g + k] = 0.0; }
     E.ncand[g] = 0; E.nacc[g] = 0; E.nabs[g] = 0; E.nnew[g] = 0; E.cnt[g] = 0; E.slots[g] = 0; E.valid[g] = 0; E.P[g] = 0.0; E.cmax[g] = 0.0; E.fmaj[g] = 1.0;
     if (i < 0 || i >= I.C) return;
-    const double xc = x_min + (static_cast<double>(i) + 0.5) * I.dx;
+    const double xc = x_min + (static_cast<double>(I.id0 + i) + 0.5) * I.dx;
     const bool left = xc < x_split;
     const double c[5] = {left ? l0 : r0, left ? l1 : r1, left ? l2 : r2, left ? l3 : r3, left ? l4 : r4};
     for (int k = 0; k < 5; ++k) E.psi[5 * g + k] = c[k];
@@ -2234,7 +2246,7 @@ __global__ void k_gather(EngineDev E, int rp, int g0, int ncell, const int64_t *
     int lo = 0, mid = 0, hi = 0;
     if (nf > 0) {
         lo = far_lower(fs, nf, g, INT32_MIN);
-        mid = far_lower(fs, nf, g, g + 2);
+        mid = far_lower(fs, nf, g, g + 1);
         hi = far_lower(fs, nf, g + 1, INT32_MIN);
     }
     const int64_t Rend = E.off[rp][g - 1] + 2 * static_cast<int64_t>(E.slotsb[rp][g - 1]);

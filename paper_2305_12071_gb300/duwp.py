@@ -34,6 +34,7 @@ EXPORTS = (
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
     "duwp_server_destroy", "duwp_get_particles_noalloc", "duwp_stress_heat", "duwp_stress_heat_accumulate",
+    "duwp_split_create", "duwp_split_step", "duwp_split_part", "duwp_split_destroy",
 )
 
 
@@ -146,6 +147,10 @@ def load(path: str = LIB_PATH):
         L.duwp_submit.argtypes = [vp, C.POINTER(Params), i32, C.POINTER(u64)]
         L.duwp_poll.argtypes = [vp, u64, C.POINTER(Result)]
         L.duwp_server_destroy.argtypes = [vp]
+        L.duwp_split_create.argtypes = [C.POINTER(Params), i32, ip, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]
+        L.duwp_split_step.argtypes = [vp, i32]
+        L.duwp_split_part.argtypes = [vp, i32, C.POINTER(vp), ip, ip]
+        L.duwp_split_destroy.argtypes = [vp]
         _lib = L
         return L
 
@@ -391,6 +396,85 @@ class Solver:
     def restore(self, blob: bytes):
         buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
         _chk(self.L.duwp_checkpoint_restore(self.h, buf, len(blob)), "duwp_checkpoint_restore")
+
+
+class _PartView(Solver):
+    """Inspection of one part of a Split (its handle belongs to the split)."""
+
+    def __init__(self, L, h, params: dict, c0: int, c1: int):
+        self.L, self.h = L, h
+        self.params = [dict(params, n_cells=c1 - c0)]
+        self.n = 1
+        self.c0, self.c1 = c0, c1
+
+    def close(self):
+        self.h = None
+
+
+class Split:
+    """One instance split into `parts` contiguous cell ranges stepped in lockstep (duwp_split_*):
+    the exchange of crossing particles and of a one-cell halo every step keeps the results equal to
+    the undivided instance's.  devices: one CUDA device per part (default: all on `device`)."""
+
+    def __init__(self, params: dict, parts: int, device: int = 0, devices=None, torch_alloc: bool = True):
+        import torch
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DUWP library needs a CUDA device")
+        torch.cuda.set_device(device)
+        self.params = params
+        self._alloc = _TorchAllocator(device) if (torch_alloc and devices is None) else None
+        a = self._alloc.alloc if self._alloc else ALLOC_FN()
+        f = self._alloc.free if self._alloc else FREE_FN()
+        dv = None
+        if devices is not None:
+            dv = (C.c_int32 * parts)(*[int(d) for d in devices])
+        pr = make_params(params)
+        h = C.c_void_p()
+        _chk(L.duwp_split_create(C.byref(pr), int(parts), dv, a, f, None, C.byref(h)), "duwp_split_create")
+        self.h, self.L = h, L
+        self.parts = []
+        for r in range(parts):
+            ph, c0, c1 = C.c_void_p(), C.c_int32(), C.c_int32()
+            _chk(L.duwp_split_part(h, r, C.byref(ph), C.byref(c0), C.byref(c1)), "duwp_split_part")
+            self.parts.append(_PartView(L, ph, params, int(c0.value), int(c1.value)))
+
+    def step(self, n: int = 1):
+        _chk(self.L.duwp_split_step(self.h, int(n)), "duwp_split_step")
+
+    def fields(self):
+        return np.concatenate([p.fields()[0] for p in self.parts])
+
+    def particles(self) -> dict:
+        ps = []
+        for p in self.parts:
+            d = p.particles()
+            d["cell"] = d["cell"] + p.c0
+            ps.append(d)
+        return {k: np.concatenate([d[k] for d in ps]) for k in ps[0]}
+
+    def counters(self) -> dict:
+        cs = [p.counters() for p in self.parts]
+        return {k: np.concatenate([c[k] for c in cs]) for k in cs[0]}
+
+    def cmax(self) -> np.ndarray:
+        return np.concatenate([p.cmax() for p in self.parts])
+
+    def particle_updates(self) -> int:
+        return int(sum(p.info(0)["particle_updates"] for p in self.parts))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for p in self.parts:
+                p.close()
+            self.L.duwp_split_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
