@@ -247,7 +247,8 @@ def oracle_all_cores(params_list, budget_s: float = 10.0):
 
 
 # ---------------------------------------------------------------------------- serving
-def serving_run(serve_seconds: float, device: int = 0) -> dict:
+def serving_run(serve_seconds: float, device: int = 0, lanes: int = 1, long_steps: int = 2000,
+                steps_per_launch: int = 32) -> dict:
     """Continuous batching under Poisson arrivals (50 requests/s of shock and Sod problems, cells
     log-uniform in [100, 1e4], 100-1000 particles per cell, Kn log-uniform in [1e-4, 1]): arrivals
     are replayed in real time for serve_seconds, then the server drains.  Returns the p50/p99 solve
@@ -257,8 +258,8 @@ def serving_run(serve_seconds: float, device: int = 0) -> dict:
     from paper_2305_12071_gb300 import workloads as W
     B.build()
     reqs = W.serving_mix(duration_s=serve_seconds, rate_hz=50.0, precision="fp32")
-    srv = duwp.Server(hbm_budget_bytes=96 << 30, max_slots=128, max_cells=1_000_000, steps_per_launch=10,
-                      precision="fp32", device=device)
+    srv = duwp.Server(hbm_budget_bytes=96 << 30, max_slots=128, max_cells=1_000_000, steps_per_launch=steps_per_launch,
+                      precision="fp32", device=device, lanes=lanes, long_steps=long_steps)
     pending, lat, queue_ms, run_ms = {}, [], [], []
     updates, i, failed = 0, 0, 0
     t0 = time.perf_counter()
@@ -295,7 +296,8 @@ def serving_run(serve_seconds: float, device: int = 0) -> dict:
             "config": {"workload": "serving_poisson50_mixed_fp32", "arrivals_s": serve_seconds,
                        "rate_hz": 50, "cells": "log-U[100,1e4]", "ppc_ref": "U[100,1000]",
                        "Kn": "log-U[1e-4,1]", "shock_steps": 500, "sod_steps": "to t = 0.15 at CFL 0.5",
-                       "steps_per_launch": 10, "max_slots": 128}}
+                       "steps_per_launch": steps_per_launch, "max_slots": 128, "lanes": lanes,
+                       "long_steps": long_steps if lanes > 1 else None}}
 
 
 def run_serving(args, rank: int, world: int):
@@ -327,7 +329,7 @@ def secondary_run(name: str, steps: int, warmup: int, device: int, peak: float, 
     sol = duwp.Solver(plist, device=device)
     sol.step(warmup)
     sol.sync()
-    (t_best, r_best), _ = autotune.tune(sol)
+    (t_best, r_best, g_best), _ = autotune.tune(sol)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
     u0 = sol.particle_updates()
@@ -351,7 +353,7 @@ def secondary_run(name: str, steps: int, warmup: int, device: int, peak: float, 
     out = {"value": upd / span, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * span / steps,
            "step_ms_p50": step_ms[len(step_ms) // 2],
            "step_ms_p99": step_ms[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
-           "dtype": "f32" if rec_bytes == 16 else "f64", "config": dict(cfg, launch={"threads": t_best, "reg_capped": r_best}),
+           "dtype": "f32" if rec_bytes == 16 else "f64", "config": dict(cfg, launch={"threads": t_best, "reg_capped": r_best, "groups": g_best}),
            "particles": int(sum(sol.num_particles(i) for i in range(sol.n))),
            "kernel_ms_per_step": {n: float(kms[i] / kt) for n, i in slots.items()},
            "roofline": {"bound": "hbm", "kernel": "k_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -433,7 +435,7 @@ def main():
     ap.add_argument("--latency-seconds", type=float, default=1.0,
                     help="steps run after the timed region for the step-latency percentiles")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--launch", default="", help="streaming-kernel launch shape threads,reg_capped "
+    ap.add_argument("--launch", default="", help="streaming-kernel launch shape threads,reg_capped[,groups] "
                                                  "(skips the autotuner)")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances of the batch")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
@@ -480,13 +482,14 @@ def main():
     sol.sync()
     tuned = None
     if args.launch:
-        t_l, r_l = (int(x) for x in args.launch.split(","))
-        sol.set_launch(t_l, r_l)
-        tuned = {"threads": t_l, "reg_capped": r_l, "candidates_ms": None}
+        knobs = [int(x) for x in args.launch.split(",")]
+        t_l, r_l, g_l = (knobs + [0, 2])[:3] if len(knobs) < 3 else knobs[:3]
+        sol.set_launch(t_l, r_l, g_l)
+        tuned = {"threads": t_l, "reg_capped": r_l, "groups": g_l, "candidates_ms": None}
     elif not args.no_tune:
         from paper_2305_12071_gb300 import autotune
-        (t_best, r_best), tune_ms = autotune.tune(sol)
-        tuned = {"threads": t_best, "reg_capped": r_best, "candidates_ms": tune_ms}
+        (t_best, r_best, g_best), tune_ms = autotune.tune(sol)
+        tuned = {"threads": t_best, "reg_capped": r_best, "groups": g_best, "candidates_ms": tune_ms}
 
     def barrier():
         if dist is not None:

@@ -245,6 +245,22 @@ int duwp_stress_heat(duwp_handle *h, int32_t inst, int32_t which, double *host_P
  * (h), DUWP_ENOMEM (scratch); device errors are reported by the next synchronizing call. */
 int duwp_stress_heat_accumulate(duwp_handle *h);
 
+/* Shock-structure profiles in the paper's normalisation (Sec. 4.1; host arithmetic, no device
+ * work).  From n values per cell of position x, density, temperature, normal stress Pi and heat flux
+ * Q (caller-owned host arrays; the outputs may alias the inputs), with the inflow state
+ * (rho_up, T_up), the outflow state (rho_down, T_down), the inflow mean free path lam_up of
+ * Eq. (lambda) and its factor beta, and the gas constant R:
+ *   DUWP_SHOCK_MA3 (Eq. ma3): rho/rho_up, T/T_up, Pi/p_up, Q/(p_up sqrt(2 R T_up)), x/(sqrt(pi) lam_up/2);
+ *   DUWP_SHOCK_MA8 (Eq. ma8): (rho - rho_up)/(rho_down - rho_up), (T - T_up)/(T_down - T_up),
+ *                             Pi/(rho_up 2 R T_up), Q/(rho_up (2 R T_up)^(3/2)), x/(beta pi lam_up);
+ * p_up = rho_up R T_up.  Any output pointer may be NULL.  Errors: DUWP_EINVAL (kind, n < 0, NULL
+ * inputs for a requested output, non-positive scales). */
+enum { DUWP_SHOCK_MA3 = 0, DUWP_SHOCK_MA8 = 1 };
+int duwp_shock_normalise(int32_t kind, int64_t n, const double *x, const double *rho, const double *T,
+                         const double *Pi, const double *Q, double rho_up, double T_up, double rho_down,
+                         double T_down, double lam_up, double beta, double R, double *x_out, double *rho_out,
+                         double *T_out, double *Pi_out, double *Q_out);
+
 /* Derived constants and sizes of instance `inst` (not synchronizing except steps_done). */
 int duwp_get_info(duwp_handle *h, int32_t inst, duwp_info *out);
 
@@ -260,11 +276,12 @@ const char *duwp_last_cuda_error(void);
 /* ------------------------------------------------------------------ launch configuration */
 
 /* Launch shape of the streaming kernel (one warp per cell): threads per block (multiple of 32,
- * 32..512) and the register budget (reg_capped = 0: up to 128 registers per thread; 1: up to 64,
- * two 512-thread blocks per SM; 2: up to 40, three).  Used by the autotuner; results do not depend
- * on it.
+ * 32..512), the register budget (reg_capped = 0: up to 128 registers per thread; 1: up to 64,
+ * two 512-thread blocks per SM; 2: up to 40, three) and the particles each thread has in flight
+ * (groups = 2 or 3 groups of 32 records per warp loaded before any is processed).  Used by the
+ * autotuner; results do not depend on it.
  * Synchronizing.  Errors: DUWP_EINVAL for shapes the device cannot launch. */
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped);
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped, int32_t groups);
 
 /* Capture the per-step launches in CUDA graphs (on = 1, default) or launch them one by one
  * (on = 0, the plain loop). */
@@ -360,8 +377,11 @@ int duwp_split_destroy(duwp_split *s);
 typedef struct duwp_server duwp_server;
 
 /* hbm_budget_bytes: device memory the server may use for resident instances; max_slots: most
- * instances resident at once; steps_per_launch: steps taken by all resident instances between
- * admissions; precision: record precision of every request; stream: CUDA stream of the worker. */
+ * instances resident at once (per lane); max_cells: cells of the pool (per lane; 0: from the
+ * budget); steps_per_launch: steps taken by all resident instances of a lane between admissions;
+ * precision: record precision of every request; stream: CUDA stream of the first lane's worker;
+ * lanes: 1 (or 0) one engine for every request, 2: requests of at least long_steps steps take a
+ * second engine stepped on a stream of its own beside the first (the budget is split in halves). */
 typedef struct {
     uint64_t hbm_budget_bytes;
     int32_t max_slots;
@@ -369,6 +389,8 @@ typedef struct {
     int32_t steps_per_launch;
     int32_t precision;
     void *stream;
+    int32_t lanes;
+    int32_t long_steps;
 } duwp_server_cfg;
 
 /* Result of one request.  The arrays are owned by the server and stay valid until the request
@@ -384,9 +406,10 @@ typedef struct {
     const double *rho, *u, *T; /* final instantaneous profile (n_cells each) */
 } duwp_result;
 
-/* Create a server with its own worker thread (continuous batching: requests are admitted when
- * a slot and enough of the HBM budget are free, are stepped together with every resident
- * request, and leave as soon as their own step count is reached). */
+/* Create a server with a worker thread per lane (continuous batching: requests are admitted when
+ * a slot and enough of the HBM budget of their lane are free, are stepped together with every
+ * request resident in their lane, and leave as soon as their own step count is reached).
+ * Errors: DUWP_EINVAL (sizes, precision, lanes outside 0..2), DUWP_ENOMEM, DUWP_ECUDA. */
 int duwp_server_create(const duwp_server_cfg *cfg, duwp_alloc_fn alloc, duwp_free_fn free_fn,
                        void *alloc_ctx, duwp_server **out);
 

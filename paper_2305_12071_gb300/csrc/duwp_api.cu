@@ -218,11 +218,11 @@ struct Carver {
 };
 }  // namespace
 
-int Engine::configure_launch(int threads_, int variant_)
+int Engine::configure_launch(int threads_, int variant_, int groups_)
 {
     if (threads_ < 32 || threads_ > 512 || (threads_ & 31)) return DUWP_EINVAL;
-    if (variant_ < 0 || variant_ > 2) return DUWP_EINVAL;
-    const int occ = stream_occupancy(fp32, variant_, threads_);
+    if (variant_ < 0 || variant_ > 2 || groups_ < 2 || groups_ > 3) return DUWP_EINVAL;
+    const int occ = stream_occupancy(fp32, variant_, groups_, threads_);
     if (occ <= 0) return DUWP_EINVAL;
     const int occ_c = collide_occupancy(fp32);
     if (occ_c <= 0) return DUWP_EINVAL;
@@ -233,6 +233,7 @@ int Engine::configure_launch(int threads_, int variant_)
     dev.nsm = nsm;
     threads = threads_;
     variant = variant_;
+    groups = groups_;
     // collision kernel: persistent blocks, as many as fit, but no more warps than cells
     const int cw = collide_threads() / 32;
     grid_collide = std::max(1, std::min(occ_c * nsm, (G + cw - 1) / cw));
@@ -394,7 +395,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     DUWP_CU(cudaMemsetAsync(dev.cell_inst, 0xff, sizeof(int32_t) * size_t(G), stream));
     DUWP_CU(launch_init_turn(stream));
 
-    int rc = configure_launch(threads, variant);
+    int rc = configure_launch(threads, variant, groups);
     if (rc != DUWP_OK) return rc;
 
     inst.assign(static_cast<size_t>(max_inst), HostInst{});
@@ -495,10 +496,10 @@ int Engine::enqueue_phase(int ph)
         DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, side2, prio_hi));
         DUWP_CU(cudaEventRecord(ev_join2, side2));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
-        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, side, 1, prio_lo));
+        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, side, 1, prio_lo));
         DUWP_CU(cudaEventRecord(ev_join, side));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join2, 0));
-        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 2, prio_hi));
+        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, 2, prio_hi));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join, 0));
     } else if (ph == 2) {
         DUWP_CU(launch_far_sort(dev, fp32, stream));
@@ -527,7 +528,7 @@ int Engine::enqueue_step(cudaEvent_t *ev)
         DUWP_CU(cudaEventRecord(ev[0], stream));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[1], stream));
-        DUWP_CU(launch_stream(dev, fp32, variant, rp, threads, stream, 0, prio_hi));
+        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, 0, prio_hi));
         DUWP_CU(cudaEventRecord(ev[2], stream));
     }
     DUWP_CU(launch_far_sort(dev, fp32, stream));
@@ -695,6 +696,40 @@ int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_m
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
     return rc;
+}
+
+int duwp_shock_normalise(int32_t kind, int64_t n, const double *x, const double *rho, const double *T, const double *Pi,
+                         const double *Q, double rho_up, double T_up, double rho_down, double T_down, double lam_up,
+                         double beta, double R, double *x_out, double *rho_out, double *T_out, double *Pi_out,
+                         double *Q_out)
+{
+    if ((kind != DUWP_SHOCK_MA3 && kind != DUWP_SHOCK_MA8) || n < 0) return DUWP_EINVAL;
+    if ((x_out && !x) || (rho_out && !rho) || (T_out && !T) || (Pi_out && !Pi) || (Q_out && !Q)) return DUWP_EINVAL;
+    if (!(rho_up > 0.0) || !(T_up > 0.0) || !(lam_up > 0.0) || !(R > 0.0)) return DUWP_EINVAL;
+    const double p_up = rho_up * R * T_up, s = 2.0 * R * T_up;
+    double xs, r0, rs, t0, ts, ps, qs;
+    if (kind == DUWP_SHOCK_MA3) {
+        xs = 0.5 * std::sqrt(kPi) * lam_up;
+        r0 = 0.0; rs = rho_up;
+        t0 = 0.0; ts = T_up;
+        ps = p_up;
+        qs = p_up * std::sqrt(s);
+    } else {
+        if (!(beta > 0.0) || rho_down == rho_up || T_down == T_up) return DUWP_EINVAL;
+        xs = beta * kPi * lam_up;
+        r0 = rho_up; rs = rho_down - rho_up;
+        t0 = T_up; ts = T_down - T_up;
+        ps = rho_up * s;
+        qs = rho_up * s * std::sqrt(s);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (x_out) x_out[i] = x[i] / xs;
+        if (rho_out) rho_out[i] = (rho[i] - r0) / rs;
+        if (T_out) T_out[i] = (T[i] - t0) / ts;
+        if (Pi_out) Pi_out[i] = Pi[i] / ps;
+        if (Q_out) Q_out[i] = Q[i] / qs;
+    }
+    return DUWP_OK;
 }
 
 int duwp_destroy(duwp_handle *h)
@@ -912,13 +947,13 @@ int duwp_get_info(duwp_handle *h, int32_t b, duwp_info *out)
     return DUWP_OK;
 }
 
-int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped)
+int duwp_set_launch(duwp_handle *h, int32_t threads, int32_t reg_capped, int32_t groups)
 {
     if (!h) return DUWP_EINVAL;
     Engine &E = h->eng;
     const int rc = E.sync();
     if (rc) return rc;
-    return E.configure_launch(threads, reg_capped);
+    return E.configure_launch(threads, reg_capped, groups);
 }
 
 int duwp_use_graphs(duwp_handle *h, int32_t on)

@@ -53,6 +53,7 @@ struct Engine {
     int32_t far_cap = 0;
     int32_t threads = 128;      // streaming kernel: threads per block (one warp per cell)
     int32_t variant = 0;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers)
+    int32_t groups = 2;         // streaming kernel: groups of 32 records per lane in flight (2 or 3)
     int32_t grid_collide = 0;   // collision kernel: persistent blocks
     int32_t grid_staged = 0;    // staged-cell kernel: persistent blocks
     // one part of a split domain: the cells [part_c0, part_c1) of its single instance (part_c1 < 0:
@@ -104,7 +105,7 @@ struct Engine {
     ~Engine();
     int create(const duwp_params *params, int32_t n, int32_t pool_cells, int32_t pool_slots, int64_t capacity_override,
                void *stream_in, duwp_alloc_fn a, duwp_free_fn f, void *ctx);
-    int configure_launch(int threads_, int variant_ = 0);
+    int configure_launch(int threads_, int variant_ = 0, int groups_ = 2);
     // used by create (upload = false: neither the table entry nor the cells yet; create copies the
     // table once and then initialises the cells) and the server
     int add_instance(int slot, const duwp_params &p, int32_t cell_base, bool upload = true);

@@ -1671,12 +1671,13 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
     }
 }
 
-// Groups of 32 records each lane loads before any of them is processed (loads in flight per warp).
-constexpr int kStreamGroups = 2;
 
 // phase: 0 every cell; 1 only the free cells (stream class, nothing re-sampled: they read and write
 // nothing the collision kernel touches, so they may stream while it runs); 2 every other cell.
-template <typename Rec, int kMinBlocks>
+// kMinBlocks: 512-thread blocks per SM the register budget allows; kStreamGroups: groups of 32 records
+// each lane loads before any of them is processed (loads in flight per warp).  Both are launch knobs
+// of the autotuner; results do not depend on them.
+template <typename Rec, int kMinBlocks, int kStreamGroups>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp, int phase)
 {
     using T = decltype(Rec().xl);
@@ -2487,17 +2488,26 @@ static int occupancy_of(K kern, int threads, size_t smem, size_t smem_max)
     return n;
 }
 
-int stream_occupancy(int fp32, int variant, int threads)
+// The streaming kernel for a register budget (variant 0/1/2: 1/2/3 blocks of 512 threads per SM) and
+// 2 or 3 record groups per lane.
+template <typename Rec>
+static void (*stream_kernel(int variant, int groups))(EngineDev, int, int)
+{
+    if (groups == 3) {
+        if (variant == 2) return k_stream<Rec, 3, 3>;
+        if (variant == 1) return k_stream<Rec, 2, 3>;
+        return k_stream<Rec, 1, 3>;
+    }
+    if (variant == 2) return k_stream<Rec, 3, 2>;
+    if (variant == 1) return k_stream<Rec, 2, 2>;
+    return k_stream<Rec, 1, 2>;
+}
+
+int stream_occupancy(int fp32, int variant, int groups, int threads)
 {
     const size_t smem = stream_smem_bytes(fp32, threads), mx = stream_smem_bytes(fp32, 512);
-    if (fp32) {
-        if (variant == 2) return occupancy_of(k_stream<RecF, 3>, threads, smem, mx);
-        if (variant == 1) return occupancy_of(k_stream<RecF, 2>, threads, smem, mx);
-        return occupancy_of(k_stream<RecF, 1>, threads, smem, mx);
-    }
-    if (variant == 2) return occupancy_of(k_stream<RecD, 3>, threads, smem, mx);
-    if (variant == 1) return occupancy_of(k_stream<RecD, 2>, threads, smem, mx);
-    return occupancy_of(k_stream<RecD, 1>, threads, smem, mx);
+    return fp32 ? occupancy_of(stream_kernel<RecF>(variant, groups), threads, smem, mx)
+                : occupancy_of(stream_kernel<RecD>(variant, groups), threads, smem, mx);
 }
 
 size_t staged_smem_bytes(int fp32)
@@ -2555,22 +2565,14 @@ cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaSt
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s, int phase,
-                          int prio)
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups, int rp, int threads, cudaStream_t s,
+                          int phase, int prio)
 {
     const int wpb = threads / 32;
     const int grid = (E.G_run + wpb - 1) / wpb;
     const size_t smem = stream_smem_bytes(fp32, threads);
-    cudaError_t e;
-    if (fp32) {
-        if (variant == 2) e = launch_prio(k_stream<RecF, 3>, grid, threads, smem, s, prio, E, rp, phase);
-        else if (variant == 1) e = launch_prio(k_stream<RecF, 2>, grid, threads, smem, s, prio, E, rp, phase);
-        else e = launch_prio(k_stream<RecF, 1>, grid, threads, smem, s, prio, E, rp, phase);
-    } else {
-        if (variant == 2) e = launch_prio(k_stream<RecD, 3>, grid, threads, smem, s, prio, E, rp, phase);
-        else if (variant == 1) e = launch_prio(k_stream<RecD, 2>, grid, threads, smem, s, prio, E, rp, phase);
-        else e = launch_prio(k_stream<RecD, 1>, grid, threads, smem, s, prio, E, rp, phase);
-    }
+    const cudaError_t e = fp32 ? launch_prio(stream_kernel<RecF>(variant, groups), grid, threads, smem, s, prio, E, rp, phase)
+                               : launch_prio(stream_kernel<RecD>(variant, groups), grid, threads, smem, s, prio, E, rp, phase);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -19,8 +19,8 @@ int staged_occupancy(int fp32);
 // Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).  phase 0:
 // every cell; 1: only the cells that need nothing from the collision kernel (stream class, nothing
 // re-sampled); 2: the other cells.
-cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int rp, int threads, cudaStream_t s, int phase,
-                          int prio);
+cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups, int rp, int threads, cudaStream_t s,
+                          int phase, int prio);
 // Sort of the particles that moved two or more cells.
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
 // Cell kernel: update Psi_t from the step's particle runs and wave flux (update = 1), then the
@@ -53,8 +53,8 @@ cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, i
                           double *w, cudaStream_t s);
 // Kernel attributes (dynamic shared memory) and blocks per SM of the streaming kernel.
 // variant 0: registers unconstrained (<= 128); 1: two 512-thread blocks per SM (<= 64 registers);
-// 2: three (<= 40 registers)
-int stream_occupancy(int fp32, int variant, int threads);
+// 2: three (<= 40 registers); groups: 2 or 3 groups of 32 records per lane in flight
+int stream_occupancy(int fp32, int variant, int groups, int threads);
 size_t stream_smem_bytes(int fp32, int threads);
 // The same for the collision kernel (fixed block size).
 int collide_occupancy(int fp32);

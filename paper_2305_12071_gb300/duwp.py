@@ -34,7 +34,7 @@ EXPORTS = (
     "duwp_num_particles", "duwp_get_particles", "duwp_get_counters", "duwp_get_cmax", "duwp_checkpoint_size",
     "duwp_checkpoint_save", "duwp_checkpoint_restore", "duwp_server_create", "duwp_submit", "duwp_poll",
     "duwp_server_destroy", "duwp_get_particles_noalloc", "duwp_stress_heat", "duwp_stress_heat_accumulate",
-    "duwp_split_create", "duwp_split_step", "duwp_split_part", "duwp_split_destroy",
+    "duwp_split_create", "duwp_split_step", "duwp_split_part", "duwp_split_destroy", "duwp_shock_normalise",
 )
 
 
@@ -82,7 +82,8 @@ class Info(C.Structure):
 
 class ServerCfg(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("max_cells", C.c_int32),
-                ("steps_per_launch", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+                ("steps_per_launch", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p),
+                ("lanes", C.c_int32), ("long_steps", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -133,7 +134,7 @@ def load(path: str = LIB_PATH):
         L.duwp_fields.argtypes = [vp, i32, i32, dp, i32, C.POINTER(i64)]
         L.duwp_get_info.argtypes = [vp, i32, C.POINTER(Info)]
         L.duwp_destroy.argtypes = [vp]
-        L.duwp_set_launch.argtypes = [vp, i32, i32]
+        L.duwp_set_launch.argtypes = [vp, i32, i32, i32]
         L.duwp_use_graphs.argtypes = [vp, i32]
         L.duwp_num_particles.argtypes = [vp, i32, C.POINTER(i64)]
         L.duwp_get_particles.argtypes = [vp, i32, ip, dp, dp, dp, dp, i64]
@@ -151,6 +152,8 @@ def load(path: str = LIB_PATH):
         L.duwp_split_step.argtypes = [vp, i32]
         L.duwp_split_part.argtypes = [vp, i32, C.POINTER(vp), ip, ip]
         L.duwp_split_destroy.argtypes = [vp]
+        L.duwp_shock_normalise.argtypes = [i32, i64, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp, dp]
         _lib = L
         return L
 
@@ -291,8 +294,8 @@ class Solver:
     def use_graphs(self, on: bool):
         _chk(self.L.duwp_use_graphs(self.h, 1 if on else 0), "duwp_use_graphs")
 
-    def set_launch(self, threads: int, reg_capped: int = 0):
-        _chk(self.L.duwp_set_launch(self.h, int(threads), int(reg_capped)), "duwp_set_launch")
+    def set_launch(self, threads: int, reg_capped: int = 0, groups: int = 2):
+        _chk(self.L.duwp_set_launch(self.h, int(threads), int(reg_capped), int(groups)), "duwp_set_launch")
 
     def n_cells(self, inst: int = 0) -> int:
         return int(self.params[inst]["n_cells"])
@@ -481,13 +484,14 @@ class Server:
     """Continuous-batching server (duwp_server_*)."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, max_cells: int = 0, steps_per_launch: int = 10,
-                 precision: str = "fp32", device: int = 0, torch_alloc: bool = True):
+                 precision: str = "fp32", device: int = 0, torch_alloc: bool = True, lanes: int = 1,
+                 long_steps: int = 0):
         import torch
         L = load()
         torch.cuda.set_device(device)
         self.stream = torch.cuda.Stream(device=device)
         cfg = ServerCfg(int(hbm_budget_bytes), int(max_slots), int(max_cells), int(steps_per_launch),
-                        PRECISION[precision], C.c_void_p(self.stream.cuda_stream))
+                        PRECISION[precision], C.c_void_p(self.stream.cuda_stream), int(lanes), int(long_steps))
         self._alloc = _TorchAllocator(device) if torch_alloc else None
         a = self._alloc.alloc if self._alloc else ALLOC_FN()
         f = self._alloc.free if self._alloc else FREE_FN()
@@ -534,19 +538,20 @@ class Server:
 
 def shock_normalised(kind: str, x, rho, T, Pi, Q, up, down, lam_up: float, beta: float = 1.0,
                      R: float = 1.0) -> dict:
-    """Shock-structure profiles in the paper's normalisation (Sec. 4.1).  up, down: (rho, T) of the
-    inflow and outflow states; lam_up: the inflow mean free path of Eq. (lambda); beta its factor.
-      'ma3' (Eq. ma3): rho/rho_up, T/T_up, Pi/p_up, Q/(p_up sqrt(2 R T_up)), x/(sqrt(pi) lam_up / 2);
-      'ma8' (Eq. ma8): (rho - rho_up)/(rho_down - rho_up), (T - T_up)/(T_down - T_up),
-                       Pi/(rho_up 2 R T_up), Q/(rho_up (2 R T_up)^1.5), x/(beta pi lam_up)."""
-    x, rho, T, Pi, Q = (np.asarray(a, np.float64) for a in (x, rho, T, Pi, Q))
+    """Shock-structure profiles in the paper's normalisation (Sec. 4.1, Eqs. ma3 / ma8), computed by
+    duwp_shock_normalise.  up, down: (rho, T) of the inflow and outflow states; lam_up: the inflow
+    mean free path of Eq. (lambda); beta its factor."""
+    kinds = {"ma3": 0, "ma8": 1}
+    if kind not in kinds:
+        raise ValueError(f"unknown normalisation {kind!r} (ma3 | ma8)")
+    L = load()
+    ins = [np.ascontiguousarray(a, np.float64) for a in (x, rho, T, Pi, Q)]
+    n = len(ins[0])
+    if any(len(a) != n for a in ins):
+        raise ValueError("x, rho, T, Pi and Q must have the same length")
+    outs = [np.empty(n, np.float64) for _ in range(5)]
     (r1, T1), (r2, T2) = up, down
-    if kind == "ma3":
-        p1 = r1 * R * T1
-        return {"x": x / (0.5 * np.sqrt(np.pi) * lam_up), "rho": rho / r1, "T": T / T1, "Pi": Pi / p1,
-                "Q": Q / (p1 * np.sqrt(2.0 * R * T1))}
-    if kind == "ma8":
-        s = 2.0 * R * T1
-        return {"x": x / (beta * np.pi * lam_up), "rho": (rho - r1) / (r2 - r1), "T": (T - T1) / (T2 - T1),
-                "Pi": Pi / (r1 * s), "Q": Q / (r1 * s ** 1.5)}
-    raise ValueError(f"unknown normalisation {kind!r} (ma3 | ma8)")
+    _chk(L.duwp_shock_normalise(kinds[kind], n, *[_dptr(a) for a in ins], float(r1), float(T1), float(r2), float(T2),
+                                float(lam_up), float(beta), float(R), *[_dptr(a) for a in outs]),
+         "duwp_shock_normalise")
+    return dict(zip(("x", "rho", "T", "Pi", "Q"), outs))

@@ -229,12 +229,13 @@ def test_time_average_matches_oracle():
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_launch_shape_does_not_change_results(precision):
-    # threads per block (warps per block) and the register budget
+    # threads per block (warps per block), the register budget and the record groups per lane
     p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision=precision, seed=8)
     ref = None
-    for t, r in ((128, 0), (32, 0), (256, 0), (512, 0), (128, 1), (512, 1), (64, 2), (512, 2)):
+    for t, r, g in ((128, 0, 2), (32, 0, 2), (256, 0, 3), (512, 0, 2), (128, 1, 3), (512, 1, 2), (64, 2, 3),
+                    (512, 2, 2), (256, 1, 3)):
         s = solver(p)
-        s.set_launch(t, r)
+        s.set_launch(t, r, g)
         s.step(6)
         got = (s.particles(), s.fields()[0], s.counters())
         s.close()
@@ -242,10 +243,10 @@ def test_launch_shape_does_not_change_results(precision):
             ref = got
             continue
         for k in ref[0]:
-            assert np.array_equal(ref[0][k], got[0][k]), f"{t}/{r}: particles {k}"
-        assert np.array_equal(ref[1], got[1]), f"{t}/{r}: fields"
+            assert np.array_equal(ref[0][k], got[0][k]), f"{t}/{r}/{g}: particles {k}"
+        assert np.array_equal(ref[1], got[1]), f"{t}/{r}/{g}: fields"
         for k in ref[2]:
-            assert np.array_equal(ref[2][k], got[2][k]), f"{t}/{r}: counter {k}"
+            assert np.array_equal(ref[2][k], got[2][k]), f"{t}/{r}/{g}: counter {k}"
 
 
 def test_moments_all_equals_per_instance():

@@ -32,12 +32,12 @@ def _alone(p, n):
     return m
 
 
-def _serve_and_compare(reqs, max_slots, max_cells, first_wave):
+def _serve_and_compare(reqs, max_slots, max_cells, first_wave, lanes=1, long_steps=0):
     from paper_2305_12071_gb300 import build as B
     from paper_2305_12071_gb300 import duwp
     B.build()
     srv = duwp.Server(hbm_budget_bytes=2 << 30, max_slots=max_slots, max_cells=max_cells, steps_per_launch=4,
-                      precision="fp32")
+                      precision="fp32", lanes=lanes, long_steps=long_steps)
     ids = []
     # first wave, then more requests while the first ones are running
     for p, n in reqs[:first_wave]:
@@ -71,6 +71,13 @@ def test_served_results_equal_alone():
     _serve_and_compare(_mix(), max_slots=3, max_cells=2048, first_wave=3)
 
 
+def test_two_lanes_results_equal_alone():
+    # requests of at least 15 steps take the second lane, stepped beside the first on its own stream
+    reqs = _mix()
+    assert any(n >= 15 for _, n in reqs) and any(n < 15 for _, n in reqs)
+    _serve_and_compare(reqs, max_slots=2, max_cells=2048, first_wave=4, lanes=2, long_steps=15)
+
+
 def test_served_results_equal_alone_sparse_pool():
     """A pool far larger than what is resident: the step kernels cover only the cells below the
     highest resident range (in granules of 4096 cells), which grows and shrinks as requests of a few
@@ -95,3 +102,5 @@ def test_server_rejects_oversized_and_unknown():
     with pytest.raises(duwp.DuwpError):
         srv.poll(987654)
     srv.close()
+    with pytest.raises(duwp.DuwpError):
+        duwp.Server(hbm_budget_bytes=256 << 20, max_slots=2, max_cells=1024, lanes=3)
