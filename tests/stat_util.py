@@ -6,10 +6,14 @@ the shock.  So two implementations (or precisions) are compared through ensemble
 distinct seeds: with means m_a, m_b and single-run standard deviations s_a, s_b over K_a, K_b runs,
 per quantity (density, velocity, temperature of the averaged state) and cell,
   d = m_a - m_b,  sigma_d = sqrt(s_a^2 / K_a + s_b^2 / K_b);
-they agree when at most 5 of the 100 cells have |d| > 3 sigma_d (a chance failure of a correct
-pair has probability below 1e-3 per quantity for K >= 16) and, where the ensembles are large
+they agree when at most 3 of the 100 cells have |d| > 3 sigma_d and, where the ensembles are large
 enough that the noise in d is well below 1% (K = 128 each: ~0.5% for the temperature), the
-relative L2 distance |d| / |m_b| is at most 1%.
+relative L2 distance |d| / |m_b| is at most 1%.  Independent cells would put 0.3 of 100 beyond
+3 sigma_d; neighbouring cells of a time-averaged profile are correlated (the shock position
+wanders as a whole), so exceedances come in small clusters: four correct 64-run ensembles (three
+FP64, one FP32-record) against the stored 128-run one had 0, 0, 1 / 0, 2, 0 / 0, 0, 0 / 0, 0, 0
+cells beyond it for density, velocity, temperature, and an ensemble with a 5% larger viscosity
+17, 6, 12.
 """
 import os
 
@@ -19,7 +23,7 @@ from paper_2305_12071_gb300 import workloads as W
 
 STEPS = 500
 AVG_START = 100
-MAX_EXCEED = 5
+MAX_EXCEED = 3
 REL_L2 = 0.01
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shock_mach3_average.txt")
 QUANTITIES = ("rho", "u", "T")

@@ -1,7 +1,7 @@
 """Long-run statistics across precisions on the GPU: 128 seeds of the Mach-3 argon shock with FP32
 particle records, run as one batch (500 steps, averages over the states after step 100), against
 the stored FP64 oracle ensemble of 128 runs (tests/golden/shock_mach3_average.txt): relative L2
-distance of the mean profiles at most 1%, and at most 5 of the 100 cells beyond 3 sigma of the
+distance of the mean profiles at most 1%, and at most 3 of the 100 cells beyond 3 sigma of the
 difference of the means, for density, velocity and temperature."""
 import pytest
 
