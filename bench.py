@@ -177,11 +177,13 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("duwp_kernels.cu", "duwp_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2305_12071_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    """sha256 (first 16 hex) of the streaming kernel's source: the part of csrc/duwp_kernels.cu from
+    its section header to the far-mover sort that follows it."""
+    with open(os.path.join(ROOT, "paper_2305_12071_gb300", "csrc", "duwp_kernels.cu"), encoding="utf-8") as fh:
+        src = fh.read()
+    a = src.index("// Streaming kernel: one warp per cell.")
+    b = src.index("// Far movers: rank sort", a)
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload_name: str, updates_per_launch: float):

@@ -174,9 +174,10 @@ int duwp_sync(duwp_handle *h);
  * receives the summed device time of [0] the collision kernel (collisions of the cells with
  * P = 0 and the re-sampled particles of the cells without collisions), [1] the streaming kernel
  * (transport and sorted runs of every particle), [2] the far-mover sort, [3] the cell update,
- * [4] the offset/flux kernel and [6] the staged-cell kernel (absorption, re-sampling and
- * collisions of the cells with P > 0), and in [5] the device time from the first launch to the
- * end of the last; host_step_ms (n_steps entries, may be NULL) the device time of each step.
+ * [4] the offset/flux kernel and [6] the kernels ahead of the collision kernel (the
+ * re-sampled particles of cells with many of them, then absorption, re-sampling and collisions of
+ * the cells with many collision candidates), and in [5] the device time from the first launch to
+ * the end of the last; host_step_ms (n_steps entries, may be NULL) the device time of each step.
  * Results are identical to duwp_step.  Errors: as duwp_step and duwp_sync. */
 enum { DUWP_TIMED_SLOTS = 7 };
 int duwp_step_timed(duwp_handle *h, int32_t n_steps, double *host_kernel_ms, double *host_step_ms);

@@ -228,6 +228,8 @@ int Engine::configure_launch(int threads_, int variant_, int groups_)
     if (occ_c <= 0) return DUWP_EINVAL;
     const int occ_s = staged_occupancy(fp32);
     if (occ_s <= 0) return DUWP_EINVAL;
+    const int occ_p = sample_occupancy(fp32);
+    if (occ_p <= 0) return DUWP_EINVAL;
     int nsm = 0;
     DUWP_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
     dev.nsm = nsm;
@@ -239,6 +241,7 @@ int Engine::configure_launch(int threads_, int variant_, int groups_)
     grid_collide = std::max(1, std::min(occ_c * nsm, (G + cw - 1) / cw));
     // staged-cell kernel: one block per cell, as many persistent blocks as fit, no more than cells
     grid_staged = std::max(1, std::min(occ_s * nsm, G));
+    grid_sample = std::max(1, occ_p * nsm);
     drop_graphs();
     return DUWP_OK;
 }
@@ -336,6 +339,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const int64_t wls_cap = int64_t(G) + capacity / (2 * kSampleChunk) + 64;
     if (wls_cap > INT32_MAX) return DUWP_EINVAL;
     const size_t o_wls = c.take<int2>(size_t(wls_cap));
+    const size_t o_wlp = c.take<int2>(size_t(wls_cap));
     const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
     const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
     // each buffer: the output blocks, then (one part of a split domain) the runs arriving in its two
@@ -387,6 +391,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.hdr = reinterpret_cast<CellHdr *>(base + o_hdr);
     dev.wl = reinterpret_cast<int32_t *>(base + o_wl);
     dev.wls = reinterpret_cast<int2 *>(base + o_wls);
+    dev.wlp = reinterpret_cast<int2 *>(base + o_wlp);
     dev.wls_cap = static_cast<int32_t>(wls_cap);
     dev.far_app = base + o_fa;
     dev.far_sorted = base + o_fs;
@@ -486,10 +491,12 @@ int Engine::enqueue_phase(int ph)
 {
     const int rp = parity;
     if (ph == 1) {
-        // the block kernel (cells with many candidates) and the collision kernel (the other cells
+        // particles drawn ahead (cells with many to draw), then the block kernel (cells with many
+        // candidates) and the collision kernel (the other cells
         // that need one) run side by side, and the free cells stream on a third stream meanwhile; the
         // other cells stream after both collision kernels; every stream joins before the far movers
         // are sorted
+        DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev_fork, stream));
         DUWP_CU(cudaStreamWaitEvent(side, ev_fork, 0));
         DUWP_CU(cudaStreamWaitEvent(side2, ev_fork, 0));
@@ -524,6 +531,7 @@ int Engine::enqueue_step(cudaEvent_t *ev)
     {
         // timed: one kernel after the other, events around each
         DUWP_CU(cudaEventRecord(ev[6], stream));
+        DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
         DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[0], stream));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));

@@ -150,7 +150,8 @@ struct EngineDev {
     int32_t *wl;               // 5 x G: work lists of the collision kernels (direct cells with up to 8, 16,
                                // 32 candidates; the other light cells; the heavy cells)
     int2 *wls;                 // sample list: (cell, first index) of chunks of kSampleChunk re-sampled particles
-    int32_t wls_cap;           // entries of wls
+    int2 *wlp;                 // the same for the particles drawn ahead of the collision kernels
+    int32_t wls_cap;           // entries of wls (and of wlp)
 };
 
 // ticket[q] (q < kLists): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
@@ -162,6 +163,13 @@ constexpr int kHeavyList = 4;
 constexpr int kListLen = 5;
 constexpr int kSampleLen = 10;
 constexpr int kSampleCtr = 11;
+// ticket[kPreLen] / ticket[kPreCtr]: length of and next item of the list of particles drawn ahead (the
+// re-sampled particles of direct cells with at least kPreSampleMin of them, drawn by k_sample before
+// the collision kernels run; such a cell's header carries kEdgePresampled in `edges`)
+constexpr int kPreLen = 12;
+constexpr int kPreCtr = 13;
+constexpr int kPreSampleMin = 64;
+constexpr int kEdgePresampled = 4;
 constexpr int kTickets = 16;
 
 // Re-sampled particles of classes 1 and 4 are drawn by the collision kernel in chunks of this many,

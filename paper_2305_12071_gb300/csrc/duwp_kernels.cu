@@ -824,7 +824,7 @@ __device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShare
     const int nc = hp->nc, n_in = hp->n_in, nn = hp->n_new, i = hp->i;
     const uint32_t id = cell_id(I, i), step = I.step;
     Rec *blk = out + hp->off;
-    if (nn > 0) {
+    if (nn > 0 && !(hp->edges & kEdgePresampled)) {       // (otherwise drawn ahead by k_sample)
         if (I.resample_mode == 1) {
             sample_run_ce<Rec>(I, E.prim, E.valid, g, i, step, blk + n_in, 0, nn, lane);
         } else {
@@ -1353,7 +1353,7 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
     if (!S.ok) return;
     const int nn = S.nn;
     const int n_tot = run + nn;
-    if (nn > 0) {
+    if (nn > 0 && (staged || !(h.edges & kEdgePresampled))) {   // (otherwise drawn ahead by k_sample)
         const MaxwellCell mc = S.mc;
         const CeCell *ce = S.ce_on ? &S.ce : nullptr;
         for (int j = t; j < nn; j += kBlockThreads)
@@ -1399,6 +1399,44 @@ __global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(EngineDev E, int
         const int cls = E.hdr[g].cls;
         if (cls == kClsStaged || cls == kClsDirect) block_cell<Rec>(E, g, S, in, out, fs);
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Particles drawn ahead (Eq. maxsample, or its NS-corrected option): the re-sampled particles of
+// direct cells with at least kPreSampleMin of them -- every particle of a first step -- in chunks of
+// kSampleChunk over all warps of the GPU, into the positions after the cell's arrived list in its
+// output block, before the collision kernels collide them there.
+// ------------------------------------------------------------------------------------------
+constexpr int kSampleThreads = 256;
+
+template <typename Rec>
+__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(EngineDev E, int rp)
+{
+    const int lane = threadIdx.x & 31;
+    Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
+    const int n_chunks = min(E.ticket[kPreLen], E.wls_cap);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&E.ticket[kPreCtr], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_chunks) break;
+        const int2 it = E.wlp[t];
+        const int g = it.x, j0 = it.y;
+        const CellHdr &h = E.hdr[g];
+        const int b = h.b, n_in = h.n_in, n_new = h.n_new, cls = h.cls, i = h.i;
+        const long long off = h.off;
+        if (cls != kClsDirect) continue;
+        const InstDev &I = E.inst[b];
+        const int j1 = min(j0 + kSampleChunk, n_new);
+        if (I.resample_mode == 1) {
+            sample_run_ce<Rec>(I, E.prim, E.valid, g, i, I.step, out + off + n_in, j0, j1, lane);
+            continue;
+        }
+        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+        for (int j = j0 + lane; j < j1; j += 32)
+            st_rec(out + off + n_in + j, sample_particle<Rec>(I, cell_id(I, i), static_cast<uint32_t>(j), I.step, mc,
+                                                              nullptr));
     }
 }
 
@@ -1874,6 +1912,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
         if (update) E.far_count[0] = 0;
         for (int q = 0; q < kLists; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
+        E.ticket[kPreLen] = 0;
     }
     if (g < E.G_run) {
         CellHdr hd;
@@ -2036,6 +2075,28 @@ __device__ __forceinline__ bool staged_is_heavy(const EngineDev &E, int g)
     return nsel >= static_cast<double>(kHeavyCandidates);
 }
 
+// Chunks of cell g appended to a sample list (lanes of a warp together: one atomic per warp).
+__device__ __forceinline__ void append_chunks(const EngineDev &E, int2 *list, int len_ticket, int g, int chunks, int lane)
+{
+    int incl = chunks;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&E.ticket[len_ticket], total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int first = base + incl - chunks;
+        for (int c = 0; c < chunks; ++c) {
+            if (first + c < E.wls_cap) list[first + c] = make_int2(g, c * kSampleChunk);
+            else set_err(E.err, kErrOverflow);
+        }
+    }
+}
+
 template <int B>
 __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int advance)
 {
@@ -2071,7 +2132,7 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
     bool listed = false;
     int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
                        // re-sampled, 3 the other light cells, kHeavyList the cells with many candidates
-    int chunks = 0;
+    int chunks = 0, pchunks = 0;
     if (g < E.G_run) {
         const int64_t o = s_pre + wpre + x - v;
         E.off[wp][g] = o;
@@ -2089,28 +2150,17 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
                 else if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-        }
-    }
-    // sample list (one atomic per warp): chunk c of cell g starts at particle c * kSampleChunk
-    {
-        int incl = chunks;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total > 0) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&E.ticket[kSampleLen], total);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const int first = base + incl - chunks;
-            for (int c = 0; c < chunks; ++c) {
-                if (first + c < E.wls_cap) E.wls[first + c] = make_int2(g, c * kSampleChunk);
-                else set_err(E.err, kErrOverflow);
+            if (cls == kClsDirect && E.hdr[g].n_new >= kPreSampleMin) {
+                // many particles to draw before the collisions (all of them in a first step): drawn
+                // ahead over the whole GPU instead of by the one warp or block that collides the cell
+                pchunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
+                E.hdr[g].edges |= kEdgePresampled;
             }
         }
     }
+    // sample lists (one atomic per warp): chunk c of cell g starts at particle c * kSampleChunk
+    append_chunks(E, E.wls, kSampleLen, g, chunks, lane);
+    append_chunks(E, E.wlp, kPreLen, g, pchunks, lane);
     // work lists of the collision kernels (one atomic per warp and list)
 #pragma unroll
     for (int q = 0; q < kLists; ++q) {
@@ -2126,6 +2176,7 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
     if (g == 0) {
         for (int q = 0; q < kLists; ++q) E.ticket[q] = 0;
         E.ticket[kSampleCtr] = 0;
+        E.ticket[kPreCtr] = 0;
     }
     if (g >= E.G_run) return;
     const int b = E.cell_inst[g];
@@ -2522,6 +2573,11 @@ int staged_occupancy(int fp32)
                 : occupancy_of(k_cellblock<RecD>, kBlockThreads, smem, smem);
 }
 
+int sample_occupancy(int fp32)
+{
+    return fp32 ? occupancy_of(k_sample<RecF>, kSampleThreads, 0, 0) : occupancy_of(k_sample<RecD>, kSampleThreads, 0, 0);
+}
+
 int collide_occupancy(int fp32)
 {
     const size_t smem = collide_smem_bytes(fp32);
@@ -2548,6 +2604,13 @@ cudaError_t launch_prio(void (*kernel)(Args...), int grid, int threads, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 }  // namespace
+
+cudaError_t launch_sample(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
+{
+    const cudaError_t e = fp32 ? launch_prio(k_sample<RecF>, grid, kSampleThreads, 0, s, prio, E, rp)
+                               : launch_prio(k_sample<RecD>, grid, kSampleThreads, 0, s, prio, E, rp);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
 {

@@ -16,6 +16,10 @@ cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaS
 // staged list, one block per cell.  grid: persistent blocks (staged_occupancy() per SM).
 cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
 int staged_occupancy(int fp32);
+// Particles drawn ahead of the collision kernels (direct cells with many re-sampled particles), in
+// chunks over all warps: persistent blocks (sample_occupancy() per SM).
+cudaError_t launch_sample(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
+int sample_occupancy(int fp32);
 // Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).  phase 0:
 // every cell; 1: only the cells that need nothing from the collision kernel (stream class, nothing
 // re-sampled); 2: the other cells.
