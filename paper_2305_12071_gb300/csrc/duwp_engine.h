@@ -52,7 +52,8 @@ struct Engine {
     int64_t capacity = 0;       // particle slots per buffer
     int32_t far_cap = 0;
     int32_t threads = 128;      // streaming kernel: threads per block (one warp per cell)
-    int32_t variant = 0;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers)
+    int32_t variant = 1;        // streaming-kernel register budget (0: <= 128, 1: <= 64, 2: <= 40 registers);
+                                // the default is the autotuner's usual choice (occupancy sets the kernel's bandwidth)
     int32_t groups = 2;         // streaming kernel: groups of 32 records per lane in flight (2 or 3)
     int32_t grid_collide = 0;   // collision kernel: persistent blocks
     int32_t grid_staged = 0;    // staged-cell kernel: persistent blocks
