@@ -147,28 +147,38 @@ struct EngineDev {
     int32_t *err;              // first device error
     int32_t *ticket;           // collision kernel work counters and list lengths (kTickets, see below)
     CellHdr *hdr;              // G: plan of each cell's particle work in the next step
-    int32_t *wl;               // 5 x G: work lists of the collision kernels (direct cells with up to 8, 16,
-                               // 32 candidates; the other light cells; the heavy cells)
+    int32_t *wl;               // kLists x G: work lists of the collision kernels (the light direct cells,
+                               // the other cells of the collision kernel, the heavy cells)
     int2 *wls;                 // sample list: (cell, first index) of chunks of kSampleChunk re-sampled particles
     int2 *wlp;                 // the same for the particles drawn ahead of the collision kernels
+    int2 *wgrp;                // G/32: the light cells each warp of k_offsets_flux appended to the light
+                               // list (first list position, cells)
+    int2 *wr;                  // G: rounds of the light list (first list position, cells): consecutive
+                               // light cells whose candidates fit in the 32 lanes of a warp
     int32_t wls_cap;           // entries of wls (and of wlp)
 };
 
 // ticket[q] (q < kLists): next item of work list q; ticket[kListLen + q]: its length; ticket[kSampleLen]
-// and ticket[kSampleCtr]: length of and next item of the sample list.  Lists 0-3 belong to the
-// collision kernel (one warp per cell or less), list kHeavyList to the block kernel (the cells with
-// many collision candidates, one block per cell).
-constexpr int kLists = 5;
-constexpr int kHeavyList = 4;
-constexpr int kListLen = 5;
-constexpr int kSampleLen = 10;
-constexpr int kSampleCtr = 11;
+// and ticket[kSampleCtr]: length of and next item of the sample list.  Lists kLightList and kWarpList
+// belong to the collision kernel (the light direct cells, packed several to a warp, and the other
+// cells, one warp each), list kHeavyList to the block kernel (the cells with many collision
+// candidates, one block per cell).
+constexpr int kLists = 3;
+constexpr int kLightList = 0;
+constexpr int kWarpList = 1;
+constexpr int kHeavyList = 2;
+constexpr int kListLen = 3;
+constexpr int kSampleLen = 6;
+constexpr int kSampleCtr = 7;
 // ticket[kPreLen] / ticket[kPreCtr]: length of and next item of the list of particles drawn ahead (the
 // re-sampled particles of direct cells with at least kPreSampleMin of them, drawn by k_sample before
 // the collision kernels run; such a cell's header carries kEdgePresampled in `edges`)
-constexpr int kPreLen = 12;
-constexpr int kPreCtr = 13;
+constexpr int kPreLen = 8;
+constexpr int kPreCtr = 9;
 constexpr int kPreSampleMin = 64;
+// ticket[kRoundLen] / ticket[kRoundCtr]: length of and next item of the round list (wr)
+constexpr int kRoundLen = 10;
+constexpr int kRoundCtr = 11;
 constexpr int kEdgePresampled = 4;
 constexpr int kTickets = 16;
 

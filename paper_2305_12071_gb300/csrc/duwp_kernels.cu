@@ -390,14 +390,19 @@ __device__ __forceinline__ double rel_speed(const Rec &A, const Rec &B)
 // one.  Inside it (and for tiny ratios) c_r and the power are evaluated in double precision.
 // cr / exact: the exact relative speed, computed here when needed.
 // The acceptance decided in double precision (the single-precision test was within its margin): out
-// of line, as it is rare.
+// of line, as it is rare.  Records and results pass by value, so that no caller's record needs an
+// address (a record whose address reaches a call lives in local memory on every path).
+struct AcceptExact {
+    double cr;     // the exact relative speed
+    bool acc;
+};
 template <typename Rec>
-__device__ __noinline__ bool accept_exact(const InstDev &I, double expo, const Rec &A, const Rec &B, double cm,
-                                          uint32_t w2, uint32_t w3, double &cr, bool &exact)
+__device__ __noinline__ AcceptExact accept_exact(const InstDev &I, double expo, Rec A, Rec B, double cm, uint32_t w2,
+                                                 uint32_t w3, double cr, bool exact)
 {
-    if (!exact) { cr = rel_speed(A, B); exact = true; }
+    if (!exact) cr = rel_speed(A, B);
     const double x = cr / cm;
-    return u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo));
+    return AcceptExact{cr, u53(w2, w3) < ((I.upsilon == 0.0) ? x : pow(x, expo))};
 }
 
 template <typename Rec>
@@ -414,20 +419,28 @@ __device__ __forceinline__ bool accept_pair(const InstDev &I, double expo, float
         if (uf < p32 - m32) return true;
         if (uf > p32 + m32) return false;
     }
-    return accept_exact<Rec>(I, expo, A, B, cm, w2, w3, cr, exact);
+    const AcceptExact r = accept_exact<Rec>(I, expo, A, B, cm, w2, w3, cr, exact);
+    cr = r.cr;
+    exact = true;
+    return r.acc;
 }
 
 // Isotropic VHS scattering of an accepted pair (Appendix A) in double precision: the relative
 // velocity keeps its magnitude c_r and takes the direction (theta, phi) with cos(theta) = 2 u1 - 1,
-// phi = 2 pi u2 (u1, u2 from the draw v).
+// phi = 2 pi u2 (u1 = u53(v0, v1), u2 = u53(v2, v3)).  Out of line, records by value.
 template <typename Rec>
-__device__ __noinline__ void scatter_fp64(const uint32_t *v, Rec &A, Rec &B, double cr)
+struct RecPair {
+    Rec a, b;
+};
+template <typename Rec>
+__device__ __noinline__ RecPair<Rec> scatter_fp64(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3, Rec A, Rec B,
+                                                  double cr)
 {
     using T = decltype(A.xl);
-    const double ct = 2.0 * u53(v[0], v[1]) - 1.0;
+    const double ct = 2.0 * u53(v0, v1) - 1.0;
     const double st = sqrt(1.0 - ct * ct);
     double sp, cp;
-    sincos(kTwoPi * u53(v[2], v[3]), &sp, &cp);
+    sincos(kTwoPi * u53(v2, v3), &sp, &cp);
     const double c0 = (cr * st) * cp, c1 = (cr * st) * sp, c2 = cr * ct;
     const double au = A.u, av = A.v, aw = A.w, bu = B.u, bv = B.v, bw = B.w;
     const double m0 = (au + bu) * 0.5, m1 = (av + bv) * 0.5, m2 = (aw + bw) * 0.5;
@@ -437,22 +450,23 @@ __device__ __noinline__ void scatter_fp64(const uint32_t *v, Rec &A, Rec &B, dou
     B.u = store_val(m0 - c0 * 0.5, T());
     B.v = store_val(m1 - c1 * 0.5, T());
     B.w = store_val(m2 - c2 * 0.5, T());
+    return RecPair<Rec>{A, B};
 }
 
 // Scattering of accepted candidate k.  cr / exact: the double-precision relative speed when the
 // caller already has it.  Single-precision records are scattered in double-single arithmetic, which
 // yields the single-precision rounding of the same values as the double-precision evaluation; the
 // few pairs where that cannot be guaranteed take the double-precision path.
-__device__ __forceinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecD &A, RecD &B,
-                                             double cr, bool exact)
+__device__ __forceinline__ RecPair<RecD> scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecD A,
+                                                      RecD B, double cr, bool exact)
 {
     uint32_t v[4];
     draw(I, id, 2u * k + 1u, step, kCollide, v);
-    scatter_fp64<RecD>(v, A, B, exact ? cr : rel_speed(A, B));
+    return scatter_fp64<RecD>(v[0], v[1], v[2], v[3], A, B, exact ? cr : rel_speed(A, B));
 }
 // (one copy, called from every collision loop: inlined five times it crowded the instruction cache)
-__device__ __noinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecF &A, RecF &B,
-                                             double cr, bool exact)
+__device__ __noinline__ RecPair<RecF> scatter_pair(const InstDev &I, uint32_t id, uint32_t k, uint32_t step, RecF A,
+                                                   RecF B, double cr, bool exact)
 {
     uint32_t v[4];
     draw(I, id, 2u * k + 1u, step, kCollide, v);
@@ -460,25 +474,9 @@ __device__ __noinline__ void scatter_pair(const InstDev &I, uint32_t id, uint32_
     if (ds_scatter(g_turn, A.u, A.v, A.w, B.u, B.v, B.w, v[0], v[1], v[2], v[3], o)) {
         A.u = o[0]; A.v = o[1]; A.w = o[2];
         B.u = o[3]; B.v = o[4]; B.w = o[5];
-    } else {
-        scatter_fp64<RecF>(v, A, B, exact ? cr : rel_speed(A, B));
+        return RecPair<RecF>{A, B};
     }
-}
-
-// Scattering with the angle words v already drawn (counter (id, 2k+1, step, COLLIDE)).
-__device__ __forceinline__ void scatter_words(const uint32_t *v, RecD &A, RecD &B, double cr, bool exact)
-{
-    scatter_fp64<RecD>(v, A, B, exact ? cr : rel_speed(A, B));
-}
-__device__ __noinline__ void scatter_words(const uint32_t *v, RecF &A, RecF &B, double cr, bool exact)
-{
-    float o[6];
-    if (ds_scatter(g_turn, A.u, A.v, A.w, B.u, B.v, B.w, v[0], v[1], v[2], v[3], o)) {
-        A.u = o[0]; A.v = o[1]; A.w = o[2];
-        B.u = o[3]; B.v = o[4]; B.w = o[5];
-    } else {
-        scatter_fp64<RecF>(v, A, B, exact ? cr : rel_speed(A, B));
-    }
+    return scatter_fp64<RecF>(v[0], v[1], v[2], v[3], A, B, exact ? cr : rel_speed(A, B));
 }
 
 // The nc candidates of a staged cell list (nc from ntc_candidates), in order; candidate k is drawn
@@ -490,9 +488,33 @@ struct StagedList {
     __device__ __forceinline__ Rec *at(int x) const { return p + x; }
 };
 
+constexpr int kHash = 128;             // slots of a warp's touched-particle table (at most 2 x kMaxDirect keys)
+
+// Slot of list position x in the slots [base, base + size) of the touched-particle table (inserted
+// if absent; `fresh`: by this call).  At most size/2 keys share those slots, so a free slot or the
+// key itself is always found within the probe limit.
+__device__ __forceinline__ int seg_insert(int *key, int base, int size, int x, bool &fresh, int32_t *err)
+{
+    int h = base + static_cast<int>(__umulhi(static_cast<uint32_t>(x) * 2654435761u, static_cast<uint32_t>(size)));
+    for (int it = 0; it < size; ++it) {
+        const int old = atomicCAS(&key[h], -1, x);
+        if (old == -1 || old == x) {
+            fresh = (old == -1);
+            return h;
+        }
+        h = (h + 1 == base + size) ? base : h + 1;
+    }
+    set_err(err, kErrOverflow);
+    fresh = false;
+    return base;
+}
+
+// Batches of up to 32 candidates on a warp; the candidates of a batch that share a particle with a
+// lower lane's are found through a hash of the batch's picks (key: list position, own: the lowest
+// lane touching it), which stays clear between batches.
 template <typename Rec, typename List>
 __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_t step, List list, int N, int64_t nc,
-                                          double &cmax, int &nacc, int *s_ab)
+                                          double &cmax, int &nacc, int *s_key, int *s_own, int32_t *err)
 {
     const int lane = threadIdx.x & 31;
     nacc = 0;
@@ -501,6 +523,11 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
     const float expo_f = static_cast<float>(expo);
     int acc = 0;
     double cm = cmax;
+    for (int t = lane; t < kHash; t += 32) {
+        s_key[t] = -1;
+        s_own[t] = 32;
+    }
+    __syncwarp();
     for (int64_t k0 = 0; k0 < nc;) {
         const int64_t k = k0 + lane;
         const bool act = k < nc;
@@ -514,16 +541,17 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
             w2 = w[2];
             w3 = w[3];
         }
-        s_ab[lane] = act ? static_cast<int>(a) : -1;
-        s_ab[32 + lane] = act ? static_cast<int>(b) : -2;
-        __syncwarp();
-        bool conf = false;
-        for (int j = 0; j < lane; ++j) {
-            const int aj = s_ab[j], bj = s_ab[32 + j];
-            conf |= (static_cast<int>(a) == aj) | (static_cast<int>(a) == bj) | (static_cast<int>(b) == aj) |
-                    (static_cast<int>(b) == bj);
+        int ha = 0, hb = 0;
+        if (act) {
+            bool fresh;
+            ha = seg_insert(s_key, 0, kHash, static_cast<int>(a), fresh, err);
+            hb = seg_insert(s_key, 0, kHash, static_cast<int>(b), fresh, err);
+            atomicMin(&s_own[ha], lane);
+            atomicMin(&s_own[hb], lane);
         }
-        const unsigned cmask = __ballot_sync(0xffffffffu, act && conf);
+        __syncwarp();
+        const bool conf = act && (s_own[ha] < lane || s_own[hb] < lane);
+        const unsigned cmask = __ballot_sync(0xffffffffu, conf);
         const int navail = static_cast<int>(min(static_cast<int64_t>(32), nc - k0));
         const int m1 = cmask ? min(navail, __ffs(cmask) - 1) : navail;
         Rec A, B;
@@ -531,9 +559,12 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
         double cr = 0.0;
         bool exact = false;
         const float cm32 = static_cast<float>(cm);
+        Rec *pA = nullptr, *pB = nullptr;
         if (lane < m1) {
-            A = *list.at(static_cast<int>(a));
-            B = *list.at(static_cast<int>(b));
+            pA = list.at(static_cast<int>(a));
+            pB = list.at(static_cast<int>(b));
+            A = ld_rec_rw(pA);
+            B = ld_rec_rw(pB);
             cr32 = rel_speed_f32(A, B);
             if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
                 cr = rel_speed(A, B);
@@ -548,13 +579,20 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
         if (lane < m) {
             accd = (lane == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
             if (accd) {
-                scatter_pair(I, id, static_cast<uint32_t>(k), step, A, B, cr, exact);
-                *list.at(static_cast<int>(a)) = A;
-                *list.at(static_cast<int>(b)) = B;
+                const RecPair<Rec> r = scatter_pair(I, id, static_cast<uint32_t>(k), step, A, B, cr, exact);
+                st_rec(pA, r.a);
+                st_rec(pB, r.b);
             }
         }
         acc += __popc(__ballot_sync(0xffffffffu, accd));
         if (fr < m) cm = cr_r;
+        __syncwarp();
+        if (act) {
+            s_key[ha] = -1;
+            s_key[hb] = -1;
+            s_own[ha] = 32;
+            s_own[hb] = 32;
+        }
         __syncwarp();
         k0 += m;
     }
@@ -567,20 +605,12 @@ __device__ __noinline__ void collide_list(const InstDev &I, uint32_t id, uint32_
 // sums do not depend on the order of accumulation, so the per-cell flux sums are identical for
 // every launch shape, and the global particle-flux ledger telescopes exactly.
 // ------------------------------------------------------------------------------------------
-// x * 2^S rounded to the nearest integer (halves away from zero), from the bits of the float with
-// integer arithmetic only; |x| must stay below 2^(62-S) (guarded by the caller's range check).
+// x * 2^S rounded to the nearest integer (ties to even): the product by the power of two is exact,
+// then one conversion; |x| must stay below 2^(62-S) (guarded by the caller's range check).
 template <int S>
 __device__ __forceinline__ long long fx_bits(float x)
 {
-    const unsigned bits = __float_as_uint(x);
-    const unsigned be = (bits >> 23) & 0xffu;
-    const unsigned long long mant = (bits & 0x7fffffu) | (be ? 0x800000u : 0u);
-    const int e = static_cast<int>(be ? be : 1u) - 150 + S;   // |x| 2^S = mant 2^e
-    long long v;
-    if (e >= 0) v = static_cast<long long>(mant << e);
-    else if (e > -32) v = static_cast<long long>((mant + (1ull << (-e - 1))) >> (-e));
-    else v = 0;
-    return (bits >> 31) ? -v : v;
+    return __float2ll_rn(__fmul_rn(x, static_cast<float>(1ull << S)));
 }
 __device__ __forceinline__ long long fx_vel(float x) { return fx_bits<40>(x); }
 __device__ __forceinline__ long long fx_vel(double x) { return __double2ll_rn(x * 1099511627776.0); }
@@ -658,143 +688,170 @@ __device__ __forceinline__ Rec *arrived_ptr(int x, const CellHdr &h, Rec *in, FR
 //           maxsample) are written to the first half of the cell's output block and collided there;
 //           the streaming kernel reads this list instead of the arrived runs.
 // ------------------------------------------------------------------------------------------
-constexpr int kHash = 128;             // slots of the touched-particle table (at most 2 x kMaxDirect keys)
 constexpr int kCollideThreads = 128;
 
 template <typename Rec>
 struct CollideShared {
     int key[kHash];     // list position of the particle held in the slot, -1 = empty
-    int own[kHash];     // lowest lane of the current batch whose candidate touches the slot (32 = none)
+    int own[kHash];     // lowest candidate of the current batch that touches the slot (32 = none)
     int mod[kHash];     // changed by an accepted collision
-    int ab[64];         // picks of a batch (warp-level list collisions)
     Rec rec[kHash];
 };
 
-// Slot of list position x in a table of NS slots (inserted if absent).  At most NS/2 keys share
-// the NS slots, so a free slot or the key itself is always found within the probe limit.
-template <int NS>
-__device__ __forceinline__ int hash_insert(int *key, int x, int32_t *err)
+// Position of the n-th (from 0) set bit of m (m has more than n set bits).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 {
-    constexpr int kShift = (NS == 32) ? 27 : ((NS == 64) ? 26 : 25);
-    static_assert(NS == 32 || NS == 64 || NS == 128, "table size");
-    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> kShift;
-    for (int it = 0; it < NS; ++it) {
-        const int old = atomicCAS(&key[h], -1, x);
-        if (old == -1 || old == x) return static_cast<int>(h);
-        h = (h + 1u) & (NS - 1);
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
     }
-    set_err(err, kErrOverflow);
-    return 0;
+    return pos;
 }
 
-// Direct cells, 32/Z per warp: lanes [s Z, (s+1) Z) handle the cell g of segment s (g < 0: none),
-// lane l of the segment candidate l (at most Z candidates), with the segment's own 4Z-slot table.
-// Every ballot is taken by the whole warp and masked to the segment, so each segment follows
-// exactly the batches of a one-cell warp.
-template <typename Rec, int Z>
-__device__ __noinline__ void collide_direct(const EngineDev &E, int g, CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
+// Light direct cells (P = 0, 1..kMaxDirect candidates, nothing re-sampled), packed: the warp holds
+// the cells of list positions t0..n_items-1 (at most 32; one round of pack_rounds) and runs them in
+// rounds.  A round takes the next cells whose candidates fit in the 32 lanes together:
+// cell c on lanes [b_c, b_c + nc_c), lane b_c + k its candidate k, with the table slots
+// [4 b_c, 4 (b_c + nc_c)) to itself.  Each ballot is masked
+// to the cell's lanes, so every cell follows exactly the batches of a cell alone: its candidates
+// drawn at once (the pairs depend only on counters), a batch cut before the first candidate that
+// shares a particle with an earlier one of the batch and after the first whose c_r raises c_max.
+// The touched particles are loaded into the table by the lane that inserted them, collided there
+// in candidate order and the changed ones written back in place (into the arrived runs or the
+// far-mover list, where the streaming kernel reads them).
+template <typename Rec>
+__device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t *list, int t0, int n_items,
+                                               CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
 {
-    constexpr int NS = 4 * Z;
     const int lane = threadIdx.x & 31;
-    const int sb0 = (lane / Z) * Z, l = lane - sb0;
-    const unsigned segmask = (Z == 32) ? 0xffffffffu : (((1u << Z) - 1u) << sb0);
-    int *key = S.key + (lane / Z) * NS;
-    int *own = S.own + (lane / Z) * NS;
-    int *mod = S.mod + (lane / Z) * NS;
-    Rec *rec = S.rec + (lane / Z) * NS;
-    const CellHdr *hp = E.hdr + (g >= 0 ? g : 0);
-    const InstDev &I = E.inst[g >= 0 ? hp->b : 0];
-    const int N = (g >= 0) ? hp->n_in : 0, nc = (g >= 0) ? hp->nc : 0;
-    const uint32_t id = cell_id(I, hp->i), step = I.step;
-    for (int t = l; t < NS; t += Z) { key[t] = -1; own[t] = 32; mod[t] = 0; }
-    __syncwarp();
-    const bool act = l < nc;
-    int sa = 0, sb = 0;
-    uint32_t w2 = 0, w3 = 0;
-    if (act) {
-        uint32_t w[4];
-        draw(I, id, 2u * static_cast<uint32_t>(l), step, kCollide, w);
-        const int a = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
-        int b = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
-        if (b >= a) ++b;
-        w2 = w[2];
-        w3 = w[3];
-        sa = hash_insert<NS>(key, a, E.err);
-        sb = hash_insert<NS>(key, b, E.err);
+    const unsigned upto = 0xffffffffu >> (31 - lane);          // lanes 0..lane
+    int cg = -1, cn = 0;                                        // the chunk's cell at this lane
+    if (t0 + lane < n_items) {
+        cg = list[t0 + lane];
+        const CellHdr *hp = E.hdr + cg;
+        const int nc = hp->nc;
+        if (hp->cls == kClsDirect && hp->n_new == 0 && nc >= 1 && nc <= kMaxDirect) cn = nc;
     }
-    __syncwarp();
-    if (g >= 0) {
-        const CellHdr h = *hp;
-        for (int t = l; t < NS; t += Z) {
-            const int x = key[t];
-            if (x >= 0) rec[t] = ld_rec_rw(arrived_ptr<Rec>(x, h, in, fs));
+    int done = 0;                                               // chunk cells collided so far
+    while (__any_sync(0xffffffffu, lane >= done && cn > 0)) {
+        int x = (lane >= done) ? cn : 0;                        // inclusive candidate count
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-    }
-    __syncwarp();
-    const double expo = 1.0 - 2.0 * I.upsilon;
-    const float expo_f = static_cast<float>(expo);
-    const double cm0 = (g >= 0) ? E.cmax[g] : 0.0;
-    double cm = cm0;
-    int acc = 0;
-    int k0 = 0;
-    while (__any_sync(0xffffffffu, k0 < nc)) {
-        const bool live = act && l >= k0;
-        if (live) { atomicMin(&own[sa], l); atomicMin(&own[sb], l); }
+        const bool inr = lane >= done && x <= 32;
+        const unsigned rm = __ballot_sync(0xffffffffu, inr);
+        const unsigned cells = __ballot_sync(0xffffffffu, inr && cn > 0);
+        const unsigned starts = __reduce_or_sync(0xffffffffu, (inr && cn > 0) ? (1u << (x - cn)) : 0u);
+        const int last = 31 - __clz(rm);
+        const int total = __shfl_sync(0xffffffffu, x, last);
+        done = last + 1;
+        // this lane's cell and candidate
+        const bool act = lane < total;
+        const int sb = act ? 31 - __clz(starts & upto) : 0;
+        const int src = act ? nth_set_bit(cells, __popc(starts & upto) - 1) : 0;
+        const int g = __shfl_sync(0xffffffffu, cg, src);
+        const int cn_src = __shfl_sync(0xffffffffu, cn, src);
+        const int nc = act ? cn_src : 0;
+        const int kc = lane - sb;
+        if (act && !(kc >= 0 && kc < nc && sb + nc <= 32)) set_err(E.err, kErrOverflow);   // (cannot happen)
+        const unsigned segmask = act ? ((0xffffffffu >> (32 - nc)) << sb) : 0u;
+        for (int t = lane; t < 4 * total; t += 32) {
+            S.key[t] = -1;
+            S.own[t] = 32;
+            S.mod[t] = 0;
+        }
         __syncwarp();
-        const bool conf = live && (own[sa] < l || own[sb] < l);
-        const unsigned cmask = (__ballot_sync(0xffffffffu, conf) & segmask) >> sb0;
-        const int end1 = cmask ? __ffs(cmask) - 1 : nc;      // first candidate that shares a particle
-        const bool inb = live && l < end1;
-        Rec A, B;
-        float cr32 = 0.f;
-        double cr = 0.0;
-        bool exact = false;
-        const float cm32 = static_cast<float>(cm);
-        if (inb) {
-            A = rec[sa];
-            B = rec[sb];
-            cr32 = rel_speed_f32(A, B);
-            if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
-                cr = rel_speed(A, B);
-                exact = true;
+        const CellHdr *hp = E.hdr + (act ? g : 0);
+        const InstDev &I = E.inst[act ? hp->b : 0];
+        const uint32_t id = cell_id(I, act ? hp->i : 0), step = I.step;
+        int sa = 0, sc = 0, pa = 0, pb = 0;
+        bool fa = false, fb = false;
+        uint32_t w2 = 0, w3 = 0;
+        if (act) {
+            const int N = hp->n_in;
+            uint32_t w[4];
+            draw(I, id, 2u * static_cast<uint32_t>(kc), step, kCollide, w);
+            pa = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
+            pb = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
+            if (pb >= pa) ++pb;
+            w2 = w[2];
+            w3 = w[3];
+            sa = seg_insert(S.key, 4 * sb, 4 * nc, pa, fa, E.err);
+            sc = seg_insert(S.key, 4 * sb, 4 * nc, pb, fb, E.err);
+            if (fa) S.rec[sa] = ld_rec_rw(arrived_ptr<Rec>(pa, *hp, in, fs));
+            if (fb) S.rec[sc] = ld_rec_rw(arrived_ptr<Rec>(pb, *hp, in, fs));
+        }
+        __syncwarp();
+        const double expo = 1.0 - 2.0 * I.upsilon;
+        const float expo_f = static_cast<float>(expo);
+        const double cm0 = act ? E.cmax[g] : 0.0;
+        double cm = cm0;
+        int acc = 0, k0 = 0;
+        while (__any_sync(0xffffffffu, k0 < nc)) {
+            const bool live = act && kc >= k0;
+            if (live) { atomicMin(&S.own[sa], kc); atomicMin(&S.own[sc], kc); }
+            __syncwarp();
+            const bool conf = live && (S.own[sa] < kc || S.own[sc] < kc);
+            const unsigned cmask = (__ballot_sync(0xffffffffu, conf) & segmask) >> sb;
+            const int end1 = cmask ? __ffs(cmask) - 1 : nc;     // first candidate that shares a particle
+            const bool inb = live && kc < end1;
+            Rec A, B;
+            float cr32 = 0.f;
+            double cr = 0.0;
+            bool exact = false;
+            const float cm32 = static_cast<float>(cm);
+            if (inb) {
+                A = S.rec[sa];
+                B = S.rec[sc];
+                cr32 = rel_speed_f32(A, B);
+                if (cr32 > cm32 * 0.99999f) {      // possibly above c_max: decide exactly
+                    cr = rel_speed(A, B);
+                    exact = true;
+                }
+            }
+            const unsigned rmask = (__ballot_sync(0xffffffffu, inb && exact && cr > cm) & segmask) >> sb;
+            const int fr = rmask ? __ffs(rmask) - 1 : 32;
+            const int end = min(end1, fr + 1);
+            const double cr_r = __shfl_sync(0xffffffffu, cr, sb + (fr < 32 ? fr : 0));
+            bool accd = false;
+            if (live && kc < end) {
+                accd = (kc == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
+                if (accd) {
+                    const RecPair<Rec> r = scatter_pair(I, id, static_cast<uint32_t>(kc), step, A, B, cr, exact);
+                    S.rec[sa] = r.a;
+                    S.rec[sc] = r.b;
+                    S.mod[sa] = 1;
+                    S.mod[sc] = 1;
+                }
+            }
+            acc += __popc(__ballot_sync(0xffffffffu, accd) & segmask);
+            if (fr < end) cm = cr_r;
+            __syncwarp();
+            if (live) { S.own[sa] = 32; S.own[sc] = 32; }
+            __syncwarp();
+            if (k0 < nc) k0 = end;
+        }
+        if (act) {
+            if (fa && S.mod[sa]) st_rec(arrived_ptr<Rec>(pa, *hp, in, fs), S.rec[sa]);
+            if (fb && S.mod[sc]) st_rec(arrived_ptr<Rec>(pb, *hp, in, fs), S.rec[sc]);
+            if (kc == 0) {
+                E.ncand[g] = nc;
+                E.nacc[g] = acc;
+                if (cm != cm0) {
+                    E.cmax[g] = cm;
+                    E.fmaj[g] = majorant_factor(I, cm);
+                }
             }
         }
-        const unsigned rmask = (__ballot_sync(0xffffffffu, inb && exact && cr > cm) & segmask) >> sb0;
-        const int fr = rmask ? __ffs(rmask) - 1 : 32;
-        const int end = min(end1, fr + 1);
-        const double cr_r = __shfl_sync(0xffffffffu, cr, sb0 + (fr < 32 ? fr : 0));
-        bool accd = false;
-        if (live && l < end) {
-            accd = (l == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
-            if (accd) {
-                scatter_pair(I, id, static_cast<uint32_t>(l), step, A, B, cr, exact);
-                rec[sa] = A;
-                rec[sb] = B;
-                mod[sa] = 1;
-                mod[sb] = 1;
-            }
-        }
-        acc += __popc(__ballot_sync(0xffffffffu, accd) & segmask);
-        if (fr < end) cm = cr_r;
         __syncwarp();
-        if (live) { own[sa] = 32; own[sb] = 32; }
-        __syncwarp();
-        if (k0 < nc) k0 = end;
-    }
-    if (g >= 0) {
-        const CellHdr h = *hp;
-        for (int t = l; t < NS; t += Z) {
-            const int x = key[t];
-            if (x >= 0 && mod[t]) st_rec(arrived_ptr<Rec>(x, h, in, fs), rec[t]);
-        }
-        if (l == 0) {
-            E.ncand[g] = nc;
-            E.nacc[g] = acc;
-            if (cm != cm0) {
-                E.cmax[g] = cm;
-                E.fmaj[g] = majorant_factor(I, cm);
-            }
-        }
     }
 }
 
@@ -837,7 +894,7 @@ __device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShare
     const double cm0 = E.cmax[g];
     double cmax = cm0;
     int na = 0;
-    collide_list<Rec>(I, id, step, ArrivedList<Rec>{hp, in, fs, blk}, n_in + nn, nc, cmax, na, S.ab);
+    collide_list<Rec>(I, id, step, ArrivedList<Rec>{hp, in, fs, blk}, n_in + nn, nc, cmax, na, S.key, S.own, E.err);
     if (lane == 0) {
         E.ncand[g] = nc;
         E.nacc[g] = na;
@@ -915,7 +972,7 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
         nc = 0;
     }
     int na = 0;
-    collide_list<Rec>(I, id, step, StagedList<Rec>{stage}, static_cast<int>(n_tot), nc, cmax, na, S.ab);
+    collide_list<Rec>(I, id, step, StagedList<Rec>{stage}, static_cast<int>(n_tot), nc, cmax, na, S.key, S.own, E.err);
     if (lane == 0) {
         E.ncand[g] = static_cast<int32_t>(nc);
         E.nacc[g] = na;
@@ -1043,7 +1100,12 @@ __device__ __forceinline__ void block_run_candidate(const InstDev &I, BlockShare
             if (uf < p32 - m32) { a = true; decided = true; }
             else if (uf > p32 + m32) decided = true;
         }
-        if (!decided) a = accept_exact<Rec>(I, W.expo, A, B, W.cm, w2, w3, cr, exact);
+        if (!decided) {
+            const AcceptExact r = accept_exact<Rec>(I, W.expo, A, B, W.cm, w2, w3, cr, exact);
+            cr = r.cr;
+            exact = true;
+            a = r.acc;
+        }
     }
     if (a) {
         bool done = false;
@@ -1061,13 +1123,16 @@ __device__ __forceinline__ void block_run_candidate(const InstDev &I, BlockShare
             if (!done) {
                 uint32_t v[4];
                 draw(I, id, static_cast<uint32_t>(2 * (k0 + c) + 1), step, kCollide, v);
-                scatter_fp64<Rec>(v, A, B, exact ? cr : rel_speed(A, B));
+                const RecPair<Rec> r = scatter_fp64<Rec>(v[0], v[1], v[2], v[3], A, B, exact ? cr : rel_speed(A, B));
+                A = r.a;
+                B = r.b;
             }
         } else {
             const float4 g0 = S.sc[c][0];
-            const uint32_t v[4] = {__float_as_uint(g0.x), __float_as_uint(g0.y), __float_as_uint(g0.z),
-                                   __float_as_uint(g0.w)};
-            scatter_fp64<Rec>(v, A, B, exact ? cr : rel_speed(A, B));
+            const RecPair<Rec> r = scatter_fp64<Rec>(__float_as_uint(g0.x), __float_as_uint(g0.y), __float_as_uint(g0.z),
+                                                     __float_as_uint(g0.w), A, B, exact ? cr : rel_speed(A, B));
+            A = r.a;
+            B = r.b;
         }
         S.rec[sa] = A;
         S.rec[sb] = B;
@@ -1380,7 +1445,7 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(EngineDev E, int rp)
+__global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(const __grid_constant__ EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     BlockShared<Rec> &S = *reinterpret_cast<BlockShared<Rec> *>(smraw);
@@ -1388,6 +1453,7 @@ __global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(EngineDev E, int
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
     const int n_items = E.ticket[kListLen + kHeavyList];
+    if (n_items == 0) return;                 // (written by the kernel before: the same for every thread)
     const int32_t *list = E.wl + static_cast<size_t>(kHeavyList) * E.G;
     for (;;) {
         if (threadIdx.x == 0) S.item = atomicAdd(&E.ticket[kHeavyList], 1);
@@ -1406,16 +1472,57 @@ __global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(EngineDev E, int
 // Particles drawn ahead (Eq. maxsample, or its NS-corrected option): the re-sampled particles of
 // direct cells with at least kPreSampleMin of them -- every particle of a first step -- in chunks of
 // kSampleChunk over all warps of the GPU, into the positions after the cell's arrived list in its
-// output block, before the collision kernels collide them there.
+// output block, before the collision kernels collide them there.  First the rounds of the light list.
 // ------------------------------------------------------------------------------------------
 constexpr int kSampleThreads = 256;
 
+// Rounds of the light list (one item each for the collision kernel): the light cells of each warp of
+// k_offsets_flux (consecutive in the list), in order, in groups whose candidates fit in the 32
+// lanes of a warp; one descriptor (first position, cells) per round.
+__device__ __forceinline__ void pack_rounds(const EngineDev &E, int grp, int lane)
+{
+    const int2 gr = E.wgrp[grp];
+    if (gr.y <= 0) return;
+    const int32_t *list = E.wl + static_cast<size_t>(kLightList) * E.G;
+    int ncl = 0;
+    if (lane < gr.y) ncl = E.hdr[list[gr.x + lane]].nc;
+    int done = 0, nr = 0;
+    int2 mine = make_int2(0, 0);                       // round `lane` of this group
+    while (__any_sync(0xffffffffu, lane >= done && ncl > 0)) {
+        int x = (lane >= done) ? ncl : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned rm = __ballot_sync(0xffffffffu, lane >= done && x <= 32);
+        const int last = min(31 - __clz(rm), gr.y - 1);
+        if (lane == nr) mine = make_int2(gr.x + done, last + 1 - done);
+        ++nr;
+        done = last + 1;
+    }
+    if (nr > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&E.ticket[kRoundLen], nr);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < nr) {
+            if (base + lane < E.G) E.wr[base + lane] = mine;
+            else set_err(E.err, kErrOverflow);
+        }
+    }
+}
+
 template <typename Rec>
-__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(EngineDev E, int rp)
+__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_constant__ EngineDev E, int rp)
 {
     const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (kSampleThreads / 32);
+    const int n_groups = (E.G_run + 31) / 32;
+    for (int w = blockIdx.x * (kSampleThreads / 32) + (threadIdx.x >> 5); w < n_groups; w += warps)
+        pack_rounds(E, w, lane);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     const int n_chunks = min(E.ticket[kPreLen], E.wls_cap);
+    if (n_chunks == 0) return;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&E.ticket[kPreCtr], 1);
@@ -1441,7 +1548,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(EngineDev E, int r
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int rp)
+__global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_constant__ EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     CollideShared<Rec> &S = reinterpret_cast<CollideShared<Rec> *>(smraw)[threadIdx.x >> 5];
@@ -1449,33 +1556,39 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(EngineDev E, int
     Rec *in = static_cast<Rec *>(E.buf[rp]);
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     FarItem<Rec> *fs = static_cast<FarItem<Rec> *>(E.far_sorted);
-    // direct cells with more than 32 candidates or with re-sampled particles (one per warp), then
-    // direct cells with up to 32, 16 and 8 candidates (one, two and four per warp); the next ticket
-    // of a list is fetched while the current item runs (the other cells: k_cellblock)
-    for (int q = 3; q >= 0; --q) {
-        const int per = (q == 3 || q == 2) ? 1 : (q == 1 ? 2 : 4);
-        const int n_items = E.ticket[kListLen + q];
-        const int32_t *list = E.wl + static_cast<size_t>(q) * E.G;
+    // the other cells of this kernel (direct cells with more than kMaxDirect candidates or with
+    // re-sampled particles, staged cells), one per warp, then the rounds of the light direct cells
+    // (packed by k_sample: one round is one item); the next ticket is fetched while the current item
+    // runs (the heavy cells: k_cellblock)
+    {
+        const int n_items = E.ticket[kListLen + kWarpList];
+        const int32_t *list = E.wl + static_cast<size_t>(kWarpList) * E.G;
         int t = 0;
-        if (lane == 0) t = atomicAdd(&E.ticket[q], per);
+        if (lane == 0) t = atomicAdd(&E.ticket[kWarpList], 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         while (t < n_items) {
             int tn = 0;
-            if (lane == 0) tn = atomicAdd(&E.ticket[q], per);
-            if (q == 3) {
-                const int g = list[t];
-                const CellHdr h = E.hdr[g];
-                if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
-                else if (h.cls == kClsDirect) collide_big<Rec>(E, g, S, in, out, fs);
-            } else {
-                const int me = t + lane / (32 / per);
-                int g = (me < n_items) ? list[me] : -1;
-                if (g >= 0 && E.hdr[g].cls != kClsDirect) g = -1;
-                if (q == 2) collide_direct<Rec, 32>(E, g, S, in, fs);
-                else if (q == 1) collide_direct<Rec, 16>(E, g, S, in, fs);
-                else collide_direct<Rec, 8>(E, g, S, in, fs);
-            }
+            if (lane == 0) tn = atomicAdd(&E.ticket[kWarpList], 1);
+            const int g = list[t];
+            const CellHdr h = E.hdr[g];
+            if (h.cls == kClsStaged) collide_staged<Rec>(E, E.inst[h.b], h, g, S, in, out, fs);
+            else if (h.cls == kClsDirect) collide_big<Rec>(E, g, S, in, out, fs);
             __syncwarp();
+            t = __shfl_sync(0xffffffffu, tn, 0);
+        }
+    }
+    {
+        const int n_rounds = min(E.ticket[kRoundLen], E.G);
+        const int32_t *list = E.wl + static_cast<size_t>(kLightList) * E.G;
+        const int n_light = E.ticket[kListLen + kLightList];
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&E.ticket[kRoundCtr], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        while (t < n_rounds) {
+            int tn = 0;
+            if (lane == 0) tn = atomicAdd(&E.ticket[kRoundCtr], 1);
+            const int2 r = E.wr[t];
+            collide_packed<Rec>(E, list, r.x, min(r.x + min(r.y, 32), n_light), S, in, fs);
             t = __shfl_sync(0xffffffffu, tn, 0);
         }
     }
@@ -1913,6 +2026,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
         for (int q = 0; q < kLists; ++q) E.ticket[kListLen + q] = 0;
         E.ticket[kSampleLen] = 0;
         E.ticket[kPreLen] = 0;
+        E.ticket[kRoundLen] = 0;
     }
     if (g < E.G_run) {
         CellHdr hd;
@@ -2097,87 +2211,10 @@ __device__ __forceinline__ void append_chunks(const EngineDev &E, int2 *list, in
     }
 }
 
-template <int B>
-__global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int advance)
+// Wave flux of the interface after cell g (between local cells i and i+1; -1: the left end), and
+// the instance's step counter advanced once per step.
+__device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int advance)
 {
-    __shared__ int64_t s_w[B / 32];
-    __shared__ int64_t s_pre;
-    const int g = blockIdx.x * B + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // sum of the slot bounds of all earlier blocks
-    int64_t acc = 0;
-    for (int j = threadIdx.x; j < blockIdx.x; j += B) acc += E.blocksum[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) s_w[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t s = 0;
-        for (int w = 0; w < B / 32; ++w) s += s_w[w];
-        s_pre = s;
-    }
-    __syncthreads();
-    // exclusive scan of the slots inside the block
-    const int64_t v = (g < E.G_run) ? 2 * static_cast<int64_t>(E.slots[g]) : 0;
-    int64_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    int64_t wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_w[w];
-    bool listed = false;
-    int lq = 3;        // work list: 0/1/2 direct cells with up to 8/16/32 candidates and nothing
-                       // re-sampled, 3 the other light cells, kHeavyList the cells with many candidates
-    int chunks = 0, pchunks = 0;
-    if (g < E.G_run) {
-        const int64_t o = s_pre + wpre + x - v;
-        E.off[wp][g] = o;
-        E.hdr[g].off = o;
-        if (o + v > E.capacity) {
-            set_err(E.err, kErrOverflow);
-            E.hdr[g].cls = kClsSkip;
-        } else {
-            const int cls = E.hdr[g].cls;
-            listed = (cls == kClsDirect) || (cls == kClsStaged);
-            if (cls == kClsStaged && staged_is_heavy(E, g)) lq = kHeavyList;
-            if (cls == kClsDirect) {
-                const int nc = E.hdr[g].nc;
-                if (nc >= kHeavyCandidates && E.hdr[g].n_in + E.hdr[g].n_new <= kBlockSlots) lq = kHeavyList;
-                else if (E.hdr[g].n_new == 0) lq = (nc <= 8) ? 0 : ((nc <= 16) ? 1 : ((nc <= kMaxDirect) ? 2 : 3));
-            }
-            if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-            if (cls == kClsDirect && E.hdr[g].n_new >= kPreSampleMin) {
-                // many particles to draw before the collisions (all of them in a first step): drawn
-                // ahead over the whole GPU instead of by the one warp or block that collides the cell
-                pchunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-                E.hdr[g].edges |= kEdgePresampled;
-            }
-        }
-    }
-    // sample lists (one atomic per warp): chunk c of cell g starts at particle c * kSampleChunk
-    append_chunks(E, E.wls, kSampleLen, g, chunks, lane);
-    append_chunks(E, E.wlp, kPreLen, g, pchunks, lane);
-    // work lists of the collision kernels (one atomic per warp and list)
-#pragma unroll
-    for (int q = 0; q < kLists; ++q) {
-        const bool mine = listed && lq == q;
-        const unsigned lm = __ballot_sync(0xffffffffu, mine);
-        if (lm) {
-            int base = 0;
-            if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[kListLen + q], __popc(lm));
-            base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
-            if (mine) E.wl[static_cast<size_t>(q) * E.G + base + __popc(lm & ((1u << lane) - 1u))] = g;
-        }
-    }
-    if (g == 0) {
-        for (int q = 0; q < kLists; ++q) E.ticket[q] = 0;
-        E.ticket[kSampleCtr] = 0;
-        E.ticket[kPreCtr] = 0;
-    }
     if (g >= E.G_run) return;
     const int b = E.cell_inst[g];
     if (b < 0) return;
@@ -2252,6 +2289,98 @@ __global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int adv
         const uint32_t nxt = I.step + 1u;
         if (static_cast<int64_t>(nxt) > static_cast<int64_t>(I.avg_start)) I.navg += 1;
         I.step = nxt;
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int advance)
+{
+    __shared__ int64_t s_w[B / 32];
+    __shared__ int64_t s_pre;
+    const int g = blockIdx.x * B + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // sum of the slot bounds of all earlier blocks
+    int64_t acc = 0;
+    for (int j = threadIdx.x; j < blockIdx.x; j += B) acc += E.blocksum[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) s_w[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t s = 0;
+        for (int w = 0; w < B / 32; ++w) s += s_w[w];
+        s_pre = s;
+    }
+    __syncthreads();
+    // exclusive scan of the slots inside the block
+    const int64_t v = (g < E.G_run) ? 2 * static_cast<int64_t>(E.slots[g]) : 0;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    int64_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_w[w];
+    bool listed = false;
+    int lq = kWarpList;   // work list (kLightList: direct cells with up to kMaxDirect candidates and
+                          // nothing re-sampled; kHeavyList: the cells with many candidates)
+    int chunks = 0, pchunks = 0;
+    if (g < E.G_run) {
+        const int64_t o = s_pre + wpre + x - v;
+        E.off[wp][g] = o;
+        E.hdr[g].off = o;
+        if (o + v > E.capacity) {
+            set_err(E.err, kErrOverflow);
+            E.hdr[g].cls = kClsSkip;
+        } else {
+            const int cls = E.hdr[g].cls;
+            listed = (cls == kClsDirect) || (cls == kClsStaged);
+            if (cls == kClsStaged && staged_is_heavy(E, g)) lq = kHeavyList;
+            if (cls == kClsDirect) {
+                const int nc = E.hdr[g].nc;
+                if (nc >= kHeavyCandidates) lq = kHeavyList;
+                else if (E.hdr[g].n_new == 0 && nc <= kMaxDirect) lq = kLightList;
+            }
+            if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
+            if (cls == kClsDirect && E.hdr[g].n_new >= kPreSampleMin) {
+                // many particles to draw before the collisions (all of them in a first step): drawn
+                // ahead over the whole GPU instead of by the one warp or block that collides the cell
+                pchunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
+                E.hdr[g].edges |= kEdgePresampled;
+            }
+        }
+    }
+    // sample lists (one atomic per warp): chunk c of cell g starts at particle c * kSampleChunk
+    append_chunks(E, E.wls, kSampleLen, g, chunks, lane);
+    append_chunks(E, E.wlp, kPreLen, g, pchunks, lane);
+    // work lists of the collision kernels (one atomic per warp and list)
+    int light_base = 0;
+#pragma unroll
+    for (int q = 0; q < kLists; ++q) {
+        const bool mine = listed && lq == q;
+        const unsigned lm = __ballot_sync(0xffffffffu, mine);
+        if (lm) {
+            int base = 0;
+            if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[kListLen + q], __popc(lm));
+            base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
+            if (mine) E.wl[static_cast<size_t>(q) * E.G + base + __popc(lm & ((1u << lane) - 1u))] = g;
+            if (q == kLightList) light_base = base;
+        }
+    }
+    if (g == 0) {
+        for (int q = 0; q < kLists; ++q) E.ticket[q] = 0;
+        E.ticket[kSampleCtr] = 0;
+        E.ticket[kPreCtr] = 0;
+        E.ticket[kRoundCtr] = 0;
+    }
+    interface_flux(E, g, advance);
+    // this warp's light cells (consecutive in the light list), packed into rounds by k_sample
+    {
+        const unsigned lm = __ballot_sync(0xffffffffu, listed && lq == kLightList);
+        if (lane == 0 && g < E.G) E.wgrp[g >> 5] = make_int2(lm ? light_base : 0, __popc(lm));
     }
 }
 

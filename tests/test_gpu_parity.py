@@ -55,6 +55,17 @@ def test_sod_wave_regime_fp64(Kn):
     _run_pair(p, [1, 3, 20], REL64, REL64)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dense_shock_block_kernel_hashed(precision):
+    # P = 0 cells with 100-400 NTC candidates among 1000-2400 particles: the block kernel on lists
+    # longer than its table, the touched particles of each window hashed
+    p = W.shock(8.0, omega=0.81, n_cells=60, ppc_ref=600.0, precision=precision, seed=11)
+    if precision == "fp64":
+        _run_pair(p, [1, 3, 10], REL64, REL64)
+    else:
+        _run_pair(p, [1, 3], REL32, REL64)
+
+
 def test_sod_wave_regime_fp32():
     p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision="fp32", seed=8)
     _run_pair(p, [1, 5], REL32, REL64)
