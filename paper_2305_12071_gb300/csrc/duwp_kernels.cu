@@ -1650,6 +1650,34 @@ struct StreamShared {
     Piece<Rec> piece[6];
 };
 
+// Records of the list in flight: kStreamStages iterations of 32 x groups records, each slot written
+// (by an asynchronous copy) and read by the same lane.
+constexpr int kStreamStages = 3;
+template <typename Rec, int kGroups>
+struct StreamRing {
+    Rec rec[kStreamStages][32 * kGroups];
+};
+
+// Asynchronous 16-byte copy global -> shared (L2 only), its commit and the wait for all but the N
+// most recent groups of this thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Address of position r of a piece of the list (kind 0: arrived runs, stored forward or backward;
+// 1: records in the output block; 2: sorted far-list items).
+template <typename Rec>
+__device__ __forceinline__ const Rec *piece_rec(const Piece<Rec> &pc, int r)
+{
+    if (pc.kind == 2) return &static_cast<const FarItem<Rec> *>(pc.p)[r].rec;
+    return static_cast<const Rec *>(pc.p) + (pc.kind == 0 ? pc.dir * r : r);
+}
+
 struct StreamState {
     int oS, oL, oR;                       // next write offsets in the block: S, L (forward), R (backward)
     int ngone;                            // far movers and removed particles of this lane
@@ -1894,64 +1922,75 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
     st.oR = 2 * slots - 1;
     st.ngone = 0;
     st.range_ok = true;
-    for (int q = 0; q < 6; ++q) {
-        const void *p = SS.piece[q].p;
-        const int n = SS.piece[q].n, k0 = SS.piece[q].k0, dir = SS.piece[q].dir, kind = SS.piece[q].kind;
-        for (int base = 0; base < n; base += 32 * kStreamGroups) {
-            Rec v[kStreamGroups];
-            if (kind == 0) {
-                // the records of the next iteration into L2 now: memory requests in flight without
-                // holding registers (the kernel is bound by requests in flight per SM)
-#pragma unroll
-                for (int u2 = 0; u2 < kStreamGroups; ++u2) {
-                    const int rp = base + 32 * kStreamGroups + 32 * u2 + lane;
-                    if (rp < n) prefetch_l2(static_cast<const Rec *>(p) + dir * rp);
-                }
-            }
-            if (base + 32 * kStreamGroups >= n && q < 5) {
-                // last iteration of this piece: the head of the next non-empty one
-                const int q2 = (q < 4 && SS.piece[q + 1].n == 0) ? q + 2 : q + 1;
-                if (SS.piece[q2].kind == 0) {
-                    const Rec *p2 = static_cast<const Rec *>(SS.piece[q2].p);
-                    const int n2 = SS.piece[q2].n, d2 = SS.piece[q2].dir;
-#pragma unroll
-                    for (int u2 = 0; u2 < kStreamGroups; ++u2) {
-                        const int rp = 32 * u2 + lane;
-                        if (rp < n2) prefetch_l2(p2 + d2 * rp);
-                    }
-                }
-            }
+    // The list, iteration by iteration (32 x groups positions of one piece each): the records of
+    // the iteration kStreamStages - 1 ahead are copied into the warp's ring asynchronously while the
+    // current one is transported, so the loads' latency is not waited for.
+    StreamRing<Rec, kStreamGroups> &RG =
+        reinterpret_cast<StreamRing<Rec, kStreamGroups> *>(s_raw + (blockDim.x >> 5) * sizeof(StreamShared<Rec>))[warp];
+    constexpr int kIt = 32 * kStreamGroups;
+    int qp = 0, bp = 0, sp = 0;                  // producer: piece, offset, stage
+    while (qp < 6 && SS.piece[qp].n == 0) ++qp;
+    int qc = qp, bc = 0, sc = 0;                 // consumer
+    auto issue = [&]() {
+        if (qp < 6) {
+            const Piece<Rec> pc = SS.piece[qp];
 #pragma unroll
             for (int u2 = 0; u2 < kStreamGroups; ++u2) {
-                const int r = base + 32 * u2 + lane;
-                if (r < n) {
-                    if (kind == 0) v[u2] = ld_rec(static_cast<const Rec *>(p) + dir * r);
-                    else if (kind == 1) v[u2] = ld_rec_rw(static_cast<const Rec *>(p) + r);
-                    else v[u2] = static_cast<const FarItem<Rec> *>(p)[r].rec;
+                const int r = bp + 32 * u2 + lane;
+                if (r < pc.n) {
+                    const Rec *src = piece_rec(pc, r);
+                    Rec *dst = &RG.rec[sp][32 * u2 + lane];
+#pragma unroll
+                    for (int h = 0; h < static_cast<int>(sizeof(Rec) / 16); ++h)
+                        cp_async16(reinterpret_cast<char *>(dst) + 16 * h, reinterpret_cast<const char *>(src) + 16 * h);
                 }
             }
-#pragma unroll
-            for (int u2 = 0; u2 < kStreamGroups; ++u2) {
-                const int r = base + 32 * u2 + lane;
-                if (base + 32 * u2 >= n) break;
-                int c = 5;
-                if (r < n) {
-                    c = move_near(dtdx, C, lo, width, ci, v[u2].xl, v[u2].u);
-                    if (c < 0) c = stream_rare<Rec>(E, g, k0 + r, v[u2], acc, st);
-                }
-                const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
-                const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
-                const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
-                const unsigned m = (c == 0) ? mL : ((c == 1) ? mS : mR);
-                const int rk = __popc(m & lt);
-                const int o = (c == 0) ? st.oL + rk : ((c == 1) ? st.oS + rk : st.oR - rk);
-                if (c < 3) st_rec(blk + o, v[u2]);
-                st.oS += __popc(mS);
-                st.oL += __popc(mL);
-                st.oR -= __popc(mR);
+            bp += kIt;
+            if (bp >= pc.n) {
+                bp = 0;
+                do { ++qp; } while (qp < 6 && SS.piece[qp].n == 0);
             }
         }
+        cp_async_commit();                        // (an empty group past the end keeps the count aligned)
+        sp = (sp + 1 == kStreamStages) ? 0 : sp + 1;
+    };
+#pragma unroll
+    for (int s0 = 0; s0 < kStreamStages - 1; ++s0) issue();
+    while (qc < 6) {
+        issue();
+        cp_async_wait<kStreamStages - 1>();       // this iteration's copies (each lane reads its own)
+        const int n = SS.piece[qc].n, k0 = SS.piece[qc].k0;
+        const int base = bc;
+#pragma unroll
+        for (int u2 = 0; u2 < kStreamGroups; ++u2) {
+            const int r = base + 32 * u2 + lane;
+            if (base + 32 * u2 >= n) break;
+            Rec v;
+            int c = 5;
+            if (r < n) {
+                v = RG.rec[sc][32 * u2 + lane];
+                c = move_near(dtdx, C, lo, width, ci, v.xl, v.u);
+                if (c < 0) c = stream_rare<Rec>(E, g, k0 + r, v, acc, st);
+            }
+            const unsigned mL = __ballot_sync(0xffffffffu, c == 0);
+            const unsigned mS = __ballot_sync(0xffffffffu, c == 1);
+            const unsigned mR = __ballot_sync(0xffffffffu, c == 2);
+            const unsigned m = (c == 0) ? mL : ((c == 1) ? mS : mR);
+            const int rk = __popc(m & lt);
+            const int o = (c == 0) ? st.oL + rk : ((c == 1) ? st.oS + rk : st.oR - rk);
+            if (c < 3) st_rec(blk + o, v);
+            st.oS += __popc(mS);
+            st.oL += __popc(mL);
+            st.oR -= __popc(mR);
+        }
+        bc += kIt;
+        if (bc >= n) {
+            bc = 0;
+            do { ++qc; } while (qc < 6 && SS.piece[qc].n == 0);
+        }
+        sc = (sc + 1 == kStreamStages) ? 0 : sc + 1;
     }
+    cp_async_wait<0>();
     __syncwarp();
     // moments of the L and R runs, read back with every lane busy
     const int nLr = st.oL - slots;
@@ -2643,9 +2682,11 @@ __global__ void k_moments(EngineDev E, int which, const int64_t *base, int64_t t
 // ------------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------------
-size_t stream_smem_bytes(int fp32, int threads)
+size_t stream_smem_bytes(int fp32, int threads, int groups)
 {
-    return static_cast<size_t>(threads / 32) * (fp32 ? sizeof(StreamShared<RecF>) : sizeof(StreamShared<RecD>));
+    const size_t ring = (groups == 3) ? (fp32 ? sizeof(StreamRing<RecF, 3>) : sizeof(StreamRing<RecD, 3>))
+                                      : (fp32 ? sizeof(StreamRing<RecF, 2>) : sizeof(StreamRing<RecD, 2>));
+    return static_cast<size_t>(threads / 32) * ((fp32 ? sizeof(StreamShared<RecF>) : sizeof(StreamShared<RecD>)) + ring);
 }
 size_t stress_tmp_bytes() { return sizeof(ShCell); }
 size_t collide_smem_bytes(int fp32)
@@ -2685,7 +2726,7 @@ static void (*stream_kernel(int variant, int groups))(EngineDev, int, int)
 
 int stream_occupancy(int fp32, int variant, int groups, int threads)
 {
-    const size_t smem = stream_smem_bytes(fp32, threads), mx = stream_smem_bytes(fp32, 512);
+    const size_t smem = stream_smem_bytes(fp32, threads, groups), mx = stream_smem_bytes(fp32, 512, 3);
     return fp32 ? occupancy_of(stream_kernel<RecF>(variant, groups), threads, smem, mx)
                 : occupancy_of(stream_kernel<RecD>(variant, groups), threads, smem, mx);
 }
@@ -2762,7 +2803,7 @@ cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups,
 {
     const int wpb = threads / 32;
     const int grid = (E.G_run + wpb - 1) / wpb;
-    const size_t smem = stream_smem_bytes(fp32, threads);
+    const size_t smem = stream_smem_bytes(fp32, threads, groups);
     const cudaError_t e = fp32 ? launch_prio(stream_kernel<RecF>(variant, groups), grid, threads, smem, s, prio, E, rp, phase)
                                : launch_prio(stream_kernel<RecD>(variant, groups), grid, threads, smem, s, prio, E, rp, phase);
     return e != cudaSuccess ? e : cudaGetLastError();

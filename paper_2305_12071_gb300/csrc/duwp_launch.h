@@ -59,7 +59,7 @@ cudaError_t launch_gather(const EngineDev &E, int fp32, int rp, int b, int g0, i
 // variant 0: registers unconstrained (<= 128); 1: two 512-thread blocks per SM (<= 64 registers);
 // 2: three (<= 40 registers); groups: 2 or 3 groups of 32 records per lane in flight
 int stream_occupancy(int fp32, int variant, int groups, int threads);
-size_t stream_smem_bytes(int fp32, int threads);
+size_t stream_smem_bytes(int fp32, int threads, int groups);
 // The same for the collision kernel (fixed block size).
 int collide_occupancy(int fp32);
 size_t collide_smem_bytes(int fp32);
