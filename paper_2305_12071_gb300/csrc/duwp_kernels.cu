@@ -12,6 +12,7 @@
 //                 slot bound and the plan (counts, class) of the next step.
 //   k_offsets     (per cell): output block offsets of the next step (scan of the slot bounds), the
 //                 work list of the collision kernel, and the wave flux at every interface.
+#include <algorithm>
 #include <cstdio>
 
 #include "duwp_dsmath.cuh"
@@ -2726,7 +2727,16 @@ static void (*stream_kernel(int variant, int groups))(EngineDev, int, int)
 
 int stream_occupancy(int fp32, int variant, int groups, int threads)
 {
-    const size_t smem = stream_smem_bytes(fp32, threads, groups), mx = stream_smem_bytes(fp32, 512, 3);
+    // the limit: the largest shape's shared memory, within what a block may opt in to
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t smem = stream_smem_bytes(fp32, threads, groups);
+    if (smem > static_cast<size_t>(optin)) return 0;
+    const size_t mx = std::min(stream_smem_bytes(fp32, 512, 3), static_cast<size_t>(optin));
     return fp32 ? occupancy_of(stream_kernel<RecF>(variant, groups), threads, smem, mx)
                 : occupancy_of(stream_kernel<RecD>(variant, groups), threads, smem, mx);
 }
