@@ -177,13 +177,16 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    """sha256 (first 16 hex) of the streaming kernel's source: the part of csrc/duwp_kernels.cu from
-    its section header to the far-mover sort that follows it."""
+    """sha256 (first 16 hex) of the streaming kernel's source: the fixed-point moment helpers it
+    calls and the part of csrc/duwp_kernels.cu from its section header to the far-mover sort that
+    follows it."""
     with open(os.path.join(ROOT, "paper_2305_12071_gb300", "csrc", "duwp_kernels.cu"), encoding="utf-8") as fh:
         src = fh.read()
+    f0 = src.index("// Exact fixed-point sums of particle moments")
+    f1 = src.index("// Prefetch of the 128-byte line", f0)
     a = src.index("// Streaming kernel: one warp per cell.")
     b = src.index("// Far movers: rank sort", a)
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    return hashlib.sha256((src[f0:f1] + src[a:b]).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload_name: str, updates_per_launch: float):
