@@ -594,7 +594,7 @@ def main():
                     "cells_total": int(sum(p["n_cells"] for p in plist)),
                     "capacity_per_buffer": int(info0["capacity"]),
                     "l2": "inputs larger than L2 (particle records exceed 129 MB)",
-                    "graphs": "one graph per step; the free cells stream beside the collision kernel",
+                    "graphs": "one graph per step; the block kernel runs beside the collision kernel",
                     "launch": tuned})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * span_all / args.steps, "higher_is_better": True,

@@ -183,14 +183,11 @@ void Engine::drop_graphs()
 Engine::~Engine()
 {
     if (cstream) cudaStreamSynchronize(cstream);
-    if (side) cudaStreamSynchronize(side);
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
     if (side2) cudaStreamSynchronize(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
     if (ev_join2) cudaEventDestroy(ev_join2);
-    if (side) cudaStreamDestroy(side);
     if (side2) cudaStreamDestroy(side2);
     for (int k = 0; k < 2; ++k) {
         if (mom_ready[k]) cudaEventDestroy(mom_ready[k]);
@@ -261,10 +258,8 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     }
     if (!params || n < 0) return DUWP_EINVAL;
     DUWP_CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-    DUWP_CU(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
     DUWP_CU(cudaStreamCreateWithFlags(&side2, cudaStreamNonBlocking));
     DUWP_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    DUWP_CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     DUWP_CU(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
     std::vector<HostInst> hs(static_cast<size_t>(n));
     int64_t est = 0;
@@ -495,23 +490,19 @@ int Engine::enqueue_phase(int ph)
 {
     const int rp = parity;
     if (ph == 1) {
-        // particles drawn ahead (cells with many to draw), then the block kernel (cells with many
-        // candidates) and the collision kernel (the other cells
-        // that need one) run side by side, and the free cells stream on a third stream meanwhile; the
-        // other cells stream after both collision kernels; every stream joins before the far movers
-        // are sorted
+        // the light cells' rounds and the particles drawn ahead (cells with many to draw), then the
+        // block kernel (cells with many candidates) and the collision kernel (the other cells that
+        // need one) side by side, then every cell streams in one launch.  (Streaming the cells that
+        // need no collision beside the collision kernels on a third stream was 1.6% slower on the
+        // bench batch once the collision kernel had become short.)
         DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev_fork, stream));
-        DUWP_CU(cudaStreamWaitEvent(side, ev_fork, 0));
         DUWP_CU(cudaStreamWaitEvent(side2, ev_fork, 0));
         DUWP_CU(launch_staged(dev, fp32, rp, grid_staged, side2, prio_hi));
         DUWP_CU(cudaEventRecord(ev_join2, side2));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
-        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, side, 1, prio_lo));
-        DUWP_CU(cudaEventRecord(ev_join, side));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join2, 0));
-        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, 2, prio_hi));
-        DUWP_CU(cudaStreamWaitEvent(stream, ev_join, 0));
+        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, prio_hi));
     } else if (ph == 2) {
         DUWP_CU(launch_far_sort(dev, fp32, stream));
         DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
@@ -540,7 +531,7 @@ int Engine::enqueue_step(cudaEvent_t *ev)
         DUWP_CU(cudaEventRecord(ev[0], stream));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[1], stream));
-        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, 0, prio_hi));
+        DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[2], stream));
     }
     DUWP_CU(launch_far_sort(dev, fp32, stream));

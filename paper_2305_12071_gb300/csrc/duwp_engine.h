@@ -75,14 +75,10 @@ struct Engine {
     int64_t steps_done = 0;
     bool use_graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step starting at read parity 0 / 1
-    // the cells that need nothing from the collision kernel stream on a side stream while it runs
-    // (launched at the lowest priority, so that the collision kernel's blocks are placed first)
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // the block kernel (cells with many collision candidates) runs beside the collision kernel (the
-    // other cells) on a stream of its own
+    // other cells) on a stream of its own, forked from and joined into the step's stream
     cudaStream_t side2 = nullptr;
-    cudaEvent_t ev_join2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join2 = nullptr;
     int prio_hi = 0, prio_lo = 0;
 
     // device scratch of the profile reads (allocated on first use): the table of instance bases

@@ -1852,13 +1852,11 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
 }
 
 
-// phase: 0 every cell; 1 only the free cells (stream class, nothing re-sampled: they read and write
-// nothing the collision kernel touches, so they may stream while it runs); 2 every other cell.
 // kMinBlocks: 512-thread blocks per SM the register budget allows; kStreamGroups: groups of 32 records
 // each lane loads before any of them is processed (loads in flight per warp).  Both are launch knobs
 // of the autotuner; results do not depend on them.
 template <typename Rec, int kMinBlocks, int kStreamGroups>
-__global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp, int phase)
+__global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
 {
     using T = decltype(Rec().xl);
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -1869,10 +1867,6 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp,
     const int wp = 1 - rp;
     const CellHdr *hp = E.hdr + g;
     const int cls = hp->cls;
-    if (phase != 0) {
-        const bool free_cell = (cls == kClsStream) && hp->n_new == 0;
-        if (free_cell != (phase == 1)) return;
-    }
     int n_tot = 0;
     if (cls == kClsStaged) n_tot = hp->n_in - E.nabs[g] + E.nnew[g];
     else if (cls != kClsSkip) n_tot = hp->n_in + hp->n_new;
@@ -2713,7 +2707,7 @@ static int occupancy_of(K kern, int threads, size_t smem, size_t smem_max)
 // The streaming kernel for a register budget (variant 0/1/2: 1/2/3 blocks of 512 threads per SM) and
 // 2 or 3 record groups per lane.
 template <typename Rec>
-static void (*stream_kernel(int variant, int groups))(EngineDev, int, int)
+static void (*stream_kernel(int variant, int groups))(EngineDev, int)
 {
     if (groups == 3) {
         if (variant == 2) return k_stream<Rec, 3, 3>;
@@ -2809,13 +2803,13 @@ cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaSt
 }
 
 cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups, int rp, int threads, cudaStream_t s,
-                          int phase, int prio)
+                          int prio)
 {
     const int wpb = threads / 32;
     const int grid = (E.G_run + wpb - 1) / wpb;
     const size_t smem = stream_smem_bytes(fp32, threads, groups);
-    const cudaError_t e = fp32 ? launch_prio(stream_kernel<RecF>(variant, groups), grid, threads, smem, s, prio, E, rp, phase)
-                               : launch_prio(stream_kernel<RecD>(variant, groups), grid, threads, smem, s, prio, E, rp, phase);
+    const cudaError_t e = fp32 ? launch_prio(stream_kernel<RecF>(variant, groups), grid, threads, smem, s, prio, E, rp)
+                               : launch_prio(stream_kernel<RecD>(variant, groups), grid, threads, smem, s, prio, E, rp);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

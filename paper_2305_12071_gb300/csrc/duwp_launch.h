@@ -20,11 +20,9 @@ int staged_occupancy(int fp32);
 // chunks over all warps: persistent blocks (sample_occupancy() per SM).
 cudaError_t launch_sample(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
 int sample_occupancy(int fp32);
-// Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).  phase 0:
-// every cell; 1: only the cells that need nothing from the collision kernel (stream class, nothing
-// re-sampled); 2: the other cells.
+// Streaming kernel of one step: one warp per cell (transport, L/S/R runs, moment sums).
 cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups, int rp, int threads, cudaStream_t s,
-                          int phase, int prio);
+                          int prio);
 // Sort of the particles that moved two or more cells.
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
 // Cell kernel: update Psi_t from the step's particle runs and wave flux (update = 1), then the
