@@ -111,6 +111,7 @@ int derive_instance(const duwp_params &p, HostInst &o)
     d.ntc_A = d.dt / (2.0 * std::sqrt(2.0) * o.lambda_ref);
     d.ntc_rr = (d.mp / d.dx) / p.rho_ref;
     d.inv_rho_ref = 1.0 / p.rho_ref;
+    d.inv_cv = 1.0 / (1.5 * p.R);
     const duwp_state *st[2] = {&p.left, &p.right};
     for (int s = 0; s < 2; ++s) {
         double *q = s ? d.right : d.left;

@@ -60,6 +60,7 @@ struct InstDev {
     double R, Pr, omega, T_ref, rho_ref, mu_ref, upsilon, c_ref, ntc_A;
     double ntc_rr;          // m_p / (dx rho_ref): particle density ratio per particle
     double inv_rho_ref;
+    double inv_cv;          // 1 / (3/2 R): temperature per unit of specific internal energy
     float dtdx_f;
     int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
     int32_t split_mode;     // 0: Eq. (p), 1: 1 - exp(-dt/tau) (quantified model competition)
@@ -234,16 +235,19 @@ __device__ __forceinline__ uint32_t idx32(uint32_t w, uint32_t n) { return __umu
 // ------------------------------------------------------------------------------------------
 
 // Primitive state from the conservative one (rho, rho U, rho V, rho W, rho E); monatomic gas:
-// rho E = rho |U|^2 / 2 + 3/2 rho R T.  Returns whether the state is usable.
-__device__ inline bool prim_from_cons(const double *psi, double R, double *q)
+// rho E = rho |U|^2 / 2 + 3/2 rho R T.  Returns whether the state is usable.  One division: the
+// quotients are products with 1/rho and 1/(3/2 R), within an ulp of the divisions (the double-precision
+// units are few on this GPU, and a division costs about nine of their operations).
+__device__ inline bool prim_from_cons(const double *psi, double inv_cv, double *q)
 {
     const double rho = psi[0];
     q[0] = rho;
     q[1] = q[2] = q[3] = q[4] = 0.0;
     if (!(rho > 0.0)) return false;
-    const double u = psi[1] / rho, v = psi[2] / rho, w = psi[3] / rho;
-    const double e = psi[4] / rho - 0.5 * (u * u + v * v + w * w);
-    const double T = e / (1.5 * R);
+    const double ir = 1.0 / rho;
+    const double u = psi[1] * ir, v = psi[2] * ir, w = psi[3] * ir;
+    const double e = psi[4] * ir - 0.5 * (u * u + v * v + w * w);
+    const double T = e * inv_cv;
     q[1] = u; q[2] = v; q[3] = w; q[4] = T;
     return (T > 0.0) && isfinite(T) && isfinite(u) && isfinite(v) && isfinite(w);
 }

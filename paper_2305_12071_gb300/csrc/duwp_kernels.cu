@@ -2044,6 +2044,13 @@ __global__ void k_far_sort(EngineDev E)
     s[rank] = me;
 }
 
+// s = a + b as 64-bit integers; false when the sum overflows.
+__device__ __forceinline__ bool add_no_overflow(long long a, long long b, long long &s)
+{
+    s = static_cast<long long>(static_cast<unsigned long long>(a) + static_cast<unsigned long long>(b));
+    return ((a ^ s) & (b ^ s)) >= 0;
+}
+
 // ------------------------------------------------------------------------------------------
 // Cell kernel: Eq. (r1) update, time average, primitive state, P, slot bound and plan of the next
 // step.  For P = 0 the re-sampled count and the NTC candidate count depend only on cell data and
@@ -2129,11 +2136,17 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                 if (update) {
                     const int64_t *aR = E.AR + 4 * (g - 1), *aL = E.AL + 4 * (g + 1), *aS = E.Aself + 5 * g;
                     double dp[5];
-                    dp[0] = static_cast<double>(hd.Rn + hd.Ln + farn) + fixed_to_double(aS[0], 0);
+                    // the three runs' fixed-point sums added as integers and converted once (unless the
+                    // sum would overflow)
+                    dp[0] = static_cast<double>(static_cast<int64_t>(hd.Rn + hd.Ln + farn) + aS[0]);
                     for (int k = 0; k < 4; ++k) {
                         const int fr = (k == 3) ? 32 : 40;
-                        dp[k + 1] = fixed_to_double(aR[k], fr) + fixed_to_double(aL[k], fr) + fsum[k] +
-                                    fixed_to_double(aS[k + 1], fr);
+                        long long s1, s2;
+                        if (add_no_overflow(aR[k], aL[k], s1) && add_no_overflow(s1, aS[k + 1], s2))
+                            dp[k + 1] = fixed_to_double(s2, fr) + fsum[k];
+                        else
+                            dp[k + 1] = fixed_to_double(aR[k], fr) + fixed_to_double(aL[k], fr) + fsum[k] +
+                                        fixed_to_double(aS[k + 1], fr);
                     }
                     const double *Fl = E.flux + 5 * (g - 1), *Fr = E.flux + 5 * g;
                     for (int k = 0; k < 5; ++k) {
@@ -2146,7 +2159,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                     }
                 }
                 double qq[5];
-                const bool ok = prim_from_cons(psi, I.R, qq);
+                const bool ok = prim_from_cons(psi, I.inv_cv, qq);
                 for (int k = 0; k < 5; ++k) E.prim[5 * g + k] = qq[k];
                 E.valid[g] = ok ? 1 : 0;
                 const double P = split_fraction(I, qq, ok);
