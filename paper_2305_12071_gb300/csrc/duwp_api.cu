@@ -112,6 +112,8 @@ int derive_instance(const duwp_params &p, HostInst &o)
     d.ntc_rr = (d.mp / d.dx) / p.rho_ref;
     d.inv_rho_ref = 1.0 / p.rho_ref;
     d.inv_cv = 1.0 / (1.5 * p.R);
+    d.vhs_expo = 1.0 - 2.0 * d.upsilon;
+    d.vhs_expo_f = static_cast<float>(d.vhs_expo);
     const duwp_state *st[2] = {&p.left, &p.right};
     for (int s = 0; s < 2; ++s) {
         double *q = s ? d.right : d.left;

@@ -61,6 +61,8 @@ struct InstDev {
     double ntc_rr;          // m_p / (dx rho_ref): particle density ratio per particle
     double inv_rho_ref;
     double inv_cv;          // 1 / (3/2 R): temperature per unit of specific internal energy
+    double vhs_expo;        // 1 - 2 upsilon: exponent of c_r in the VHS acceptance test (Appendix A)
+    float vhs_expo_f;
     float dtdx_f;
     int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
     int32_t split_mode;     // 0: Eq. (p), 1: 1 - exp(-dt/tau) (quantified model competition)

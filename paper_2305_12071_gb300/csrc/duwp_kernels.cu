@@ -772,16 +772,15 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
         __syncwarp();
         const CellHdr *hp = E.hdr + (act ? g : 0);
         const InstDev &I = E.inst[act ? hp->b : 0];
-        const uint32_t id = cell_id(I, act ? hp->i : 0), step = I.step;
-        int sa = 0, sc = 0, pa = 0, pb = 0;
+        int sa = 0, sc = 0;
         bool fa = false, fb = false;
         uint32_t w2 = 0, w3 = 0;
         if (act) {
             const int N = hp->n_in;
             uint32_t w[4];
-            draw(I, id, 2u * static_cast<uint32_t>(kc), step, kCollide, w);
-            pa = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
-            pb = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
+            draw(I, cell_id(I, hp->i), 2u * static_cast<uint32_t>(kc), I.step, kCollide, w);
+            const int pa = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
+            int pb = static_cast<int>(idx32(w[1], static_cast<uint32_t>(N - 1)));
             if (pb >= pa) ++pb;
             w2 = w[2];
             w3 = w[3];
@@ -791,11 +790,9 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
             if (fb) S.rec[sc] = ld_rec_rw(arrived_ptr<Rec>(pb, *hp, in, fs));
         }
         __syncwarp();
-        const double expo = 1.0 - 2.0 * I.upsilon;
-        const float expo_f = static_cast<float>(expo);
-        const double cm0 = act ? E.cmax[g] : 0.0;
-        double cm = cm0;
+        double cm = act ? E.cmax[g] : 0.0;
         int acc = 0, k0 = 0;
+        bool raised = false;
         while (__any_sync(0xffffffffu, k0 < nc)) {
             const bool live = act && kc >= k0;
             if (live) { atomicMin(&S.own[sa], kc); atomicMin(&S.own[sc], kc); }
@@ -824,9 +821,10 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
             const double cr_r = __shfl_sync(0xffffffffu, cr, sb + (fr < 32 ? fr : 0));
             bool accd = false;
             if (live && kc < end) {
-                accd = (kc == fr) || accept_pair<Rec>(I, expo, expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
+                accd = (kc == fr) || accept_pair<Rec>(I, I.vhs_expo, I.vhs_expo_f, A, B, cr32, cm32, cm, w2, w3, cr, exact);
                 if (accd) {
-                    const RecPair<Rec> r = scatter_pair(I, id, static_cast<uint32_t>(kc), step, A, B, cr, exact);
+                    const RecPair<Rec> r = scatter_pair(I, cell_id(I, hp->i), static_cast<uint32_t>(kc), I.step, A, B,
+                                                        cr, exact);
                     S.rec[sa] = r.a;
                     S.rec[sc] = r.b;
                     S.mod[sa] = 1;
@@ -834,19 +832,22 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
                 }
             }
             acc += __popc(__ballot_sync(0xffffffffu, accd) & segmask);
-            if (fr < end) cm = cr_r;
+            if (fr < end) {
+                cm = cr_r;
+                raised = true;
+            }
             __syncwarp();
             if (live) { S.own[sa] = 32; S.own[sc] = 32; }
             __syncwarp();
             if (k0 < nc) k0 = end;
         }
         if (act) {
-            if (fa && S.mod[sa]) st_rec(arrived_ptr<Rec>(pa, *hp, in, fs), S.rec[sa]);
-            if (fb && S.mod[sc]) st_rec(arrived_ptr<Rec>(pb, *hp, in, fs), S.rec[sc]);
+            if (fa && S.mod[sa]) st_rec(arrived_ptr<Rec>(S.key[sa], *hp, in, fs), S.rec[sa]);
+            if (fb && S.mod[sc]) st_rec(arrived_ptr<Rec>(S.key[sc], *hp, in, fs), S.rec[sc]);
             if (kc == 0) {
                 E.ncand[g] = nc;
                 E.nacc[g] = acc;
-                if (cm != cm0) {
+                if (raised) {
                     E.cmax[g] = cm;
                     E.fmaj[g] = majorant_factor(I, cm);
                 }
@@ -2217,7 +2218,8 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
 
 // ------------------------------------------------------------------------------------------
 // Offsets of the next step's output blocks, the collision kernel's work list, and the wave flux of
-// every interface.
+// every interface.  At 64 registers (a full SM of warps): the double-precision flux, which spills
+// there, runs only where P_f > 0, and the offsets and lists before it are latency-bound.
 // ------------------------------------------------------------------------------------------
 // Whether a cell's collisions are long dependency chains, which the block kernel runs in parallel
 // rounds: at least kHeavyCandidates NTC candidates (Appendix A) on a list that fits the block's
@@ -2340,7 +2342,7 @@ __device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int ad
 }
 
 template <int B>
-__global__ void __launch_bounds__(B) k_offsets_flux(EngineDev E, int wp, int advance)
+__global__ void __launch_bounds__(B, 1024 / B) k_offsets_flux(EngineDev E, int wp, int advance)
 {
     __shared__ int64_t s_w[B / 32];
     __shared__ int64_t s_pre;
