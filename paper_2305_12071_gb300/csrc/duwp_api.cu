@@ -340,6 +340,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     const size_t o_wlp = c.take<int2>(size_t(wls_cap));
     const size_t o_wr = c.take<int2>(size_t(G));
     const size_t o_wgrp = c.take<int2>(size_t(G) / 32 + 1);
+    const size_t o_wlnc = c.take<int32_t>(size_t(G));
     const size_t o_fa = c.take<unsigned char>(far_item * far_cap);
     const size_t o_fs = c.take<unsigned char>(far_item * far_cap);
     // each buffer: the output blocks, then (one part of a split domain) the runs arriving in its two
@@ -394,6 +395,7 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     dev.wlp = reinterpret_cast<int2 *>(base + o_wlp);
     dev.wr = reinterpret_cast<int2 *>(base + o_wr);
     dev.wgrp = reinterpret_cast<int2 *>(base + o_wgrp);
+    dev.wlnc = reinterpret_cast<int32_t *>(base + o_wlnc);
     dev.wls_cap = static_cast<int32_t>(wls_cap);
     dev.far_app = base + o_fa;
     dev.far_sorted = base + o_fs;

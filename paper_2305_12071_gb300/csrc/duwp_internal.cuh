@@ -156,6 +156,7 @@ struct EngineDev {
     int2 *wlp;                 // the same for the particles drawn ahead of the collision kernels
     int2 *wgrp;                // G/32: the light cells each warp of k_offsets_flux appended to the light
                                // list (first list position, cells)
+    int32_t *wlnc;             // G: NTC candidates of each light-list entry
     int2 *wr;                  // G: rounds of the light list (first list position, cells): consecutive
                                // light cells whose candidates fit in the 32 lanes of a warp
     int32_t wls_cap;           // entries of wls (and of wlp)

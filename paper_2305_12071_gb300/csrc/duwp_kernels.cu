@@ -1481,15 +1481,16 @@ constexpr int kSampleThreads = 256;
 // Rounds of the light list (one item each for the collision kernel): the light cells of each warp of
 // k_offsets_flux (consecutive in the list), in order, in groups whose candidates fit in the 32
 // lanes of a warp; one descriptor (first position, cells) per round.
-__device__ __forceinline__ void pack_rounds(const EngineDev &E, int grp, int lane)
+// Returns the number of rounds; lane r < (that number) holds round r in `mine`.
+__device__ __forceinline__ int pack_rounds(const EngineDev &E, int grp, int lane, int2 &mine)
 {
-    const int2 gr = E.wgrp[grp];
-    if (gr.y <= 0) return;
-    const int32_t *list = E.wl + static_cast<size_t>(kLightList) * E.G;
+    mine = make_int2(0, 0);
+    const int n_groups = (E.G_run + 31) / 32;
+    const int2 gr = (grp < n_groups) ? E.wgrp[grp] : make_int2(0, 0);
+    if (gr.y <= 0) return 0;
     int ncl = 0;
-    if (lane < gr.y) ncl = E.hdr[list[gr.x + lane]].nc;
+    if (lane < gr.y) ncl = E.wlnc[gr.x + lane];
     int done = 0, nr = 0;
-    int2 mine = make_int2(0, 0);                       // round `lane` of this group
     while (__any_sync(0xffffffffu, lane >= done && ncl > 0)) {
         int x = (lane >= done) ? ncl : 0;
 #pragma unroll
@@ -1503,25 +1504,36 @@ __device__ __forceinline__ void pack_rounds(const EngineDev &E, int grp, int lan
         ++nr;
         done = last + 1;
     }
-    if (nr > 0) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&E.ticket[kRoundLen], nr);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (lane < nr) {
-            if (base + lane < E.G) E.wr[base + lane] = mine;
-            else set_err(E.err, kErrOverflow);
-        }
-    }
+    return nr;
 }
 
 template <typename Rec>
 __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_constant__ EngineDev E, int rp)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (kSampleThreads / 32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kSampleThreads / 32;
     const int n_groups = (E.G_run + 31) / 32;
-    for (int w = blockIdx.x * (kSampleThreads / 32) + (threadIdx.x >> 5); w < n_groups; w += warps)
-        pack_rounds(E, w, lane);
+    // one group per warp, one atomic per block for the rounds of its warps
+    __shared__ int s_nr[kW], s_base;
+    for (int w0 = blockIdx.x * kW; w0 < n_groups; w0 += gridDim.x * kW) {
+        int2 mine;
+        const int nr = pack_rounds(E, w0 + warp, lane, mine);
+        if (lane == 0) s_nr[warp] = nr;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < kW; ++k) tot += s_nr[k];
+            s_base = tot ? atomicAdd(&E.ticket[kRoundLen], tot) : 0;
+        }
+        __syncthreads();
+        int base = s_base;
+        for (int k = 0; k < warp; ++k) base += s_nr[k];
+        if (lane < nr) {
+            if (base + lane < E.G) E.wr[base + lane] = mine;
+            else set_err(E.err, kErrOverflow);
+        }
+        __syncthreads();
+    }
     Rec *out = static_cast<Rec *>(E.buf[1 - rp]);
     const int n_chunks = min(E.ticket[kPreLen], E.wls_cap);
     if (n_chunks == 0) return;
@@ -2415,8 +2427,12 @@ __global__ void __launch_bounds__(B, 1024 / B) k_offsets_flux(EngineDev E, int w
             int base = 0;
             if (lane == __ffs(lm) - 1) base = atomicAdd(&E.ticket[kListLen + q], __popc(lm));
             base = __shfl_sync(0xffffffffu, base, __ffs(lm) - 1);
-            if (mine) E.wl[static_cast<size_t>(q) * E.G + base + __popc(lm & ((1u << lane) - 1u))] = g;
-            if (q == kLightList) light_base = base;
+            const int pos = base + __popc(lm & ((1u << lane) - 1u));
+            if (mine) E.wl[static_cast<size_t>(q) * E.G + pos] = g;
+            if (q == kLightList) {
+                light_base = base;
+                if (mine) E.wlnc[pos] = E.hdr[g].nc;
+            }
         }
     }
     if (g == 0) {
