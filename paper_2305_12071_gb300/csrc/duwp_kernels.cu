@@ -1018,7 +1018,8 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
 // window.
 // ------------------------------------------------------------------------------------------
 constexpr int kBlockThreads = 128;
-constexpr int kPer = 4;                             // window candidates per thread
+constexpr int kPer = 2;                             // window candidates per thread (window 256: the
+                                                    // smaller tables fit five blocks per SM)
 constexpr int kWindow = kPer * kBlockThreads;       // candidates per window (table = the whole list)
 constexpr int kWindowHashed = kBlockThreads * 2;    // candidates per window when the touched particles are hashed
 constexpr int kBlockSlots = 1024;      // table slots (the hashed form holds at most 2 x kWindowHashed keys)
@@ -1447,7 +1448,7 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kBlockThreads, 4) k_cellblock(const __grid_constant__ EngineDev E, int rp)
+__global__ void __launch_bounds__(kBlockThreads, 5) k_cellblock(const __grid_constant__ EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     BlockShared<Rec> &S = *reinterpret_cast<BlockShared<Rec> *>(smraw);
