@@ -1023,6 +1023,9 @@ constexpr int kPer = 2;                             // window candidates per thr
 constexpr int kWindow = kPer * kBlockThreads;       // candidates per window (table = the whole list)
 constexpr int kWindowHashed = kBlockThreads * 2;    // candidates per window when the touched particles are hashed
 constexpr int kBlockSlots = 1024;      // table slots (the hashed form holds at most 2 x kWindowHashed keys)
+static_assert((kBlockSlots & (kBlockSlots - 1)) == 0 && 4 * kWindowHashed <= kBlockSlots,
+              "hashed table: a power of two, at most half full");
+static_assert(kWindowHashed <= kWindow, "the window arrays hold a hashed window");
 constexpr int kAbsorbPer = 4;          // arrived records per thread in flight in the absorption pass
 constexpr int kHeavyCandidates = 96;   // candidates from which a cell takes the block kernel
 
@@ -1049,7 +1052,7 @@ struct BlockShared {
 
 __device__ __forceinline__ int block_insert(int *key, int x, int32_t *err)
 {
-    uint32_t h = (static_cast<uint32_t>(x) * 2654435761u) >> 22;
+    uint32_t h = __umulhi(static_cast<uint32_t>(x) * 2654435761u, static_cast<uint32_t>(kBlockSlots));
     for (int it = 0; it < kBlockSlots; ++it) {
         const int old = atomicCAS(&key[h], -1, x);
         if (old == -1 || old == x) return static_cast<int>(h);
