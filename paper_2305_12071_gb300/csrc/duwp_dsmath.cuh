@@ -166,33 +166,41 @@ __host__ __device__ __forceinline__ ds ds_int53(int64_t n)
 // x 2^k for a power of two f = 2^k (exact).
 __host__ __device__ __forceinline__ ds ds_scale(ds x, float f) { return {x.hi * f, x.lo * f}; }
 
-// Turn table: cos and sin of 2 pi k / 64, k = 0..63, as double-single pairs (cos hi, cos lo,
+// Turn table: cos and sin of 2 pi k / 128, k = 0..127, as double-single pairs (cos hi, cos lo,
 // sin hi, sin lo).
-constexpr int kTurnTable = 64;
+constexpr int kTurnTable = 128;
 
-// cos and sin of phi = 2 pi u for the 53-bit uniform u = v2 2^-32 + (v3 >> 11) 2^-53: phi = 2 pi (K/64
-// + r) with K = round(64 u), |r| <= 1/128 taken exactly from the bits; cos and sin of 2 pi r from
-// their Taylor series (the omitted terms are below 2^-49 for |2 pi r| <= pi/64) combined with the
-// turn table by the angle-addition formulas.  Absolute error below 2^-45.  ds_turn_parts gives the
-// table entry (C, S) = (cos, sin)(2 pi K/64) and (cx, sx) = (cos, sin)(2 pi r).
+// cos and sin of phi = 2 pi u for the 53-bit uniform u = v2 2^-32 + (v3 >> 11) 2^-53: phi = 2 pi (K/128
+// + r) with K = round(128 u), |r| <= 1/256 taken exactly from the bits; cos and sin of x = 2 pi r from
+// their Taylor series, combined with the turn table by the angle-addition formulas.  For
+// |x| <= pi/128: sin x = x - x^3/6 + x^5/120 (x^7/5040 < 2^-50) and cos x = 1 - x^2/2 + x^4/24 - x^6/720
+// (x^8/8! < 2^-60); x, x^2/2 and x^3/6 are carried as double-single values, the smaller terms in single
+// precision (x^4/24 < 2^-26, x^5/120 < 2^-33).  Absolute error below 2^-46.  ds_turn_parts gives the
+// table entry (C, S) = (cos, sin)(2 pi K/128) and (cx, sx) = (cos, sin)(2 pi r).
 __host__ __device__ __forceinline__ void ds_turn_parts(const float4 *turn, uint32_t v2, uint32_t v3, ds &C, ds &S,
                                                        ds &cx, ds &sx)
 {
     constexpr ds kTwoPiDs = ds_const(6.283185307179586476925286766559);
-    constexpr ds kMinusSixth = ds_const(-1.0 / 6.0);
-    // r 2^32 = d + (v3 >> 11) 2^-21 with d = v2 - K 2^26 (32-bit wrap-around gives the sign)
-    const uint32_t K = (v2 >> 26) + ((v2 >> 25) & 1u);
-    const int32_t d = static_cast<int32_t>(v2 - (K << 26));
-    const int32_t d_hi = d & ~3;
-    const uint32_t r_lo = (static_cast<uint32_t>(d & 3) << 21) | (v3 >> 11);
+    constexpr ds kSixth = ds_const(1.0 / 6.0);
+    // r 2^32 = d + (v3 >> 11) 2^-21 with d = v2 - K 2^25 (32-bit wrap-around gives the sign), |d| <= 2^24
+    const uint32_t K = (v2 >> 25) + ((v2 >> 24) & 1u);
+    const int32_t d = static_cast<int32_t>(v2 - (K << 25));
+    const int32_t d_hi = d & ~1;
+    const uint32_t r_lo = (static_cast<uint32_t>(d & 1) << 21) | (v3 >> 11);
     const ds r = ds_two_sum(static_cast<float>(d_hi) * 0x1p-32f, static_cast<float>(r_lo) * 0x1p-53f);
-    const ds x = ds_mul(kTwoPiDs, r);                                 // |x| <= pi/64
-    const ds x2 = ds_mul(x, x);
-    // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040), cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
-    const float ts = x2.hi * (1.0f / 120.0f - x2.hi * (1.0f / 5040.0f));
-    sx = ds_add(x, ds_mul(ds_mul(x, x2), ds_add(kMinusSixth, {ts, 0.0f})));
-    const float tc = x2.hi * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
-    cx = ds_add({1.0f, 0.0f}, ds_mul(x2, ds_two_sum(-0.5f, tc)));
+    const ds x = ds_mul(kTwoPiDs, r);                                 // |x| <= pi/128
+    ds x2 = ds_two_prod(x.hi, x.hi);                                  // x^2 (the x.lo^2 term is below 2^-48 x^2)
+    x2.lo = fmaf(2.0f * x.hi, x.lo, x2.lo);
+    ds x3 = ds_two_prod(x2.hi, x.hi);                                 // x^3
+    x3.lo = fmaf(x2.lo, x.hi, fmaf(x2.hi, x.lo, x3.lo));
+    ds t3 = ds_two_prod(x3.hi, kSixth.hi);                            // x^3 / 6
+    t3.lo = fmaf(x3.hi, kSixth.lo, fmaf(x3.lo, kSixth.hi, t3.lo));
+    const float ts = (x3.hi * x2.hi) * (1.0f / 120.0f);
+    const ds sa = ds_two_sum(x.hi, -t3.hi);
+    sx = ds_fast_two_sum(sa.hi, ((x.lo - t3.lo) + ts) + sa.lo);
+    const float tc = (x2.hi * x2.hi) * (1.0f / 24.0f - x2.hi * (1.0f / 720.0f));
+    const ds ca = ds_fast_two_sum(1.0f, -0.5f * x2.hi);
+    cx = ds_fast_two_sum(ca.hi, ((-0.5f * x2.lo) + tc) + ca.lo);
     const float4 T = turn[K & (kTurnTable - 1)];
     C = {T.x, T.y};
     S = {T.z, T.w};
@@ -288,49 +296,98 @@ __host__ __device__ __forceinline__ bool ds_scatter(const float4 *turn, float au
     return ds_scatter_apply(au, av, aw, bu, bv, bw, g, out, unrounded);
 }
 
-// Log table: nodes F_j = 1 + (j - kLogCenter)/256, j = 0..kLogTable-1 (covering [sqrt(1/2), 1.416]),
+// Log table: nodes F_j = 1 + (j - kLogCenter)/1024, j = 0..kLogTable-1 (covering [0.707, 1.415]),
 // entries (1/F_j hi, lo, log F_j hi, lo); entry kLogCenter is (1, 0, 0, 0).
-constexpr int kLogTable = 192;
-constexpr int kLogCenter = 75;
+constexpr int kLogTable = 725;
+constexpr int kLogCenter = 300;
+
+__host__ __device__ __forceinline__ int ds_clz64(uint64_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __clzll(static_cast<long long>(x));
+#else
+    return __builtin_clzll(x);
+#endif
+}
 
 // -log(1 - u) for the 53-bit uniform u = u53(a, b) in [0, 1), relative error below 2^-46.
 // 1 - u = n 2^-53 with the integer n = 2^53 - m, m = (a << 21) | (b >> 11); n = 2^e f with f in
-// [0.708, 1.416), F the nearest table node (f - F formed exactly from the integers, |f - F| <= 2^-9),
-// d = (f - F)/F, |d| < 2^-8.5, and
-//   -log(1 - u) = (53 - e) ln 2 - log F - log(1 + d),  log(1 + d) = d - d^2/2 + d^3/3 + d^3 q(d),
-// the last term (below 2^-25 |d|) in single precision.  For u near 0 the node is F = 1 and d = -u
-// exactly, so small results keep their relative accuracy.
+// [0.707, 1.415), F = 1 + k/1024 the nearest table node (|f - F| <= 2^-11; f - F formed exactly from
+// the integers), d = (f - F)/F, |d| < 2^-10.5, and
+//   -log(1 - u) = (53 - e) ln 2 - log F - log(1 + d),  log(1 + d) = d - d^2/2 + d^3/3 - d^4/4 + d^5/5
+// (the omitted terms below 2^-55 |d|), with d, d^2/2 and d^3/3 as double-single values and the two
+// smallest terms in single precision.  For u near 0 the node is F = 1 and d = -u exactly, so small
+// results keep their relative accuracy.
 __host__ __device__ __forceinline__ ds ds_neg_log1m(const float4 *logt, uint32_t a, uint32_t b)
 {
     constexpr ds kLn2 = ds_const(0.69314718055994530941723212145818);
     constexpr ds kThird = ds_const(1.0 / 3.0);
     const uint64_t m = (static_cast<uint64_t>(a) << 21) | static_cast<uint64_t>(b >> 11);
-    const uint64_t n = (1ull << 53) - m;                   // 1 <= n <= 2^53
-#ifdef __CUDA_ARCH__
-    int e = 63 - __clzll(static_cast<long long>(n));        // n = 2^e f0, f0 in [1, 2)
-#else
-    int e = 63 - __builtin_clzll(n);
-#endif
-    const uint64_t r9 = (e >= 9) ? (n >> (e - 9)) : (n << (9 - e));    // floor(f0 512), in [512, 1023]
-    int k = static_cast<int>((r9 + 1) >> 1) - 256;          // round((f0 - 1) 256), in [0, 256]
-    if (k > 106) {                                          // f = f0 / 2
-        e += 1;
-        k = static_cast<int>(((r9 >> 1) + 1) >> 1) - 256;   // round((f - 1) 256), in [-75, 0]
+    const uint64_t n = (1ull << 53) - m;                    // 1 <= n <= 2^53
+    const int lz = ds_clz64(n);                              // n = 2^(63 - lz) f0, f0 in [1, 2), lz >= 10
+    const uint64_t x = n << lz;                              // f0 2^63 (the low lz bits are zero)
+    const uint32_t r11 = static_cast<uint32_t>(x >> 52);     // floor(f0 2048), in [2048, 4095]
+    int k = static_cast<int>((r11 + 1u) >> 1) - 1024;        // round(f0 1024) - 1024, in [0, 1024]
+    int h = 0;
+    if (k > 424) {                                           // f = f0 / 2
+        h = 1;
+        k = static_cast<int>((r11 + 2u) >> 2) - 1024;        // round(f 1024) - 1024, in [-300, 0]
     }
-    // f - F = D 2^-e (e >= 8) or D 2^-8, F = (256 + k) 2^-8; |D| < 2^45
-    const int64_t Fn = 256 + k;
-    const int64_t D = (e >= 8) ? static_cast<int64_t>(n) - (Fn << (e - 8)) : (static_cast<int64_t>(n) << (8 - e)) - Fn;
-    const float scale = bits_f(static_cast<uint32_t>(127 - (e >= 8 ? e : 8)) << 23);   // 2^-max(e, 8), e <= 54
+    // f - F = D 2^-63 with F = (1024 + k)/1024: |D| <= 2^52 and the low 9 bits of D are zero, so its
+    // two 32-bit halves are exact single-precision values
+    const int64_t D = static_cast<int64_t>((x >> h) - (static_cast<uint64_t>(1024 + k) << 53));
+    const float dh = static_cast<float>(static_cast<int32_t>(D >> 32)) * 0x1p-31f;
+    const float dl = static_cast<float>(static_cast<uint32_t>(D)) * 0x1p-63f;
+    const ds t = ds_two_sum(dh, dl);
     const float4 T = logt[k + kLogCenter];
-    const ds t = ds_scale(ds_int53(D), scale);
     const ds d = ds_mul(t, {T.x, T.y});
-    const ds d2 = ds_mul(d, d);
-    const ds d3 = ds_mul(d2, d);
-    const float df = d.hi;
-    const float q = df * (-0.25f + df * (0.2f - df * (1.0f / 6.0f - df * (1.0f / 7.0f))));
-    const ds lp = ds_add(d, ds_add(ds_scale(d2, -0.5f), ds_add(ds_mul(d3, kThird), {d3.hi * q, 0.0f})));
-    const ds lf = ds_add({T.z, T.w}, lp);
-    return ds_add(ds_mul(kLn2, {static_cast<float>(53 - e), 0.0f}), ds_neg(lf));
+    const float p = d.hi;
+    ds d2 = ds_two_prod(p, p);                               // d^2
+    d2.lo = fmaf(2.0f * p, d.lo, d2.lo);
+    ds d3 = ds_two_prod(d2.hi, p);                           // d^3
+    d3.lo = fmaf(d2.lo, p, fmaf(d2.hi, d.lo, d3.lo));
+    ds t3 = ds_two_prod(d3.hi, kThird.hi);                   // d^3 / 3
+    t3.lo = fmaf(d3.hi, kThird.lo, fmaf(d3.lo, kThird.hi, t3.lo));
+    const float tail = (d2.hi * d2.hi) * (-0.25f + 0.2f * p);
+    const ds s1 = ds_two_sum(p, -0.5f * d2.hi);
+    const ds s2 = ds_fast_two_sum(s1.hi, t3.hi);
+    const float lo = ((((d.lo - 0.5f * d2.lo) + t3.lo) + tail) + s1.lo) + s2.lo;
+    const ds lp = ds_fast_two_sum(s2.hi, lo);                // log(1 + d)
+    const float ne = static_cast<float>(lz - 10 - h);        // 53 - e, e = 63 - lz + h
+    ds A = ds_two_prod(ne, kLn2.hi);
+    A.lo = fmaf(ne, kLn2.lo, A.lo);
+    return ds_add(ds_add(A, {-T.z, -T.w}), ds_neg(lp));
+}
+
+// {hi, lo} with hi the single-precision rounding of x and lo that of x - hi (the same pair as
+// ds_of_double), by integer operations only (no double-precision unit), for x = 0 and 2^-70 <= |x| <
+// 2^100; returns false outside that range (the caller then converts in double precision).
+__host__ __device__ __forceinline__ bool ds_of_double_int(double x, ds &out)
+{
+#ifdef __CUDA_ARCH__
+    const uint64_t bx = static_cast<uint64_t>(__double_as_longlong(x));
+#else
+    uint64_t bx;
+    std::memcpy(&bx, &x, 8);
+#endif
+    const uint32_t hi32 = static_cast<uint32_t>(bx >> 32), lo32 = static_cast<uint32_t>(bx);
+    const uint32_t sign = hi32 & 0x80000000u;
+    if ((bx << 1) == 0) {
+        out = {bits_f(sign), 0.0f};
+        return true;
+    }
+    const int e = static_cast<int>((hi32 >> 20) & 0x7ffu) - 1023;    // |x| = 1.m 2^e
+    if (e < -70 || e >= 100) return false;
+    const uint32_t m23 = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);     // the float's 23 fraction bits
+    const uint32_t rest = lo32 & 0x1fffffffu;                         // the 29 bits below them
+    const uint32_t up = (rest > (1u << 28) || (rest == (1u << 28) && (m23 & 1u))) ? 1u : 0u;
+    // rounding up carries into the exponent where the fraction overflows, as it should
+    out.hi = bits_f((sign | (static_cast<uint32_t>(e + 127) << 23) | m23) + up);
+    // |x| - |hi| = (rest - up 2^29) 2^(e-52), rounded to single precision once by the conversion
+    const float r = static_cast<float>(static_cast<int32_t>(rest) - static_cast<int32_t>(up << 29)) *
+                    bits_f(static_cast<uint32_t>(e - 52 + 127) << 23);
+    out.lo = sign ? 0.0f - r : r;
+    return true;
 }
 
 // Velocity components of a Maxwellian sample (Eq. maxsample) for single-precision records:
@@ -338,14 +395,15 @@ __host__ __device__ __forceinline__ ds ds_neg_log1m(const float4 *logt, uint32_t
 // double-single values, (r1, r2) the 53-bit uniforms of words w[4d+2..4d+5] (w = the 14 words after
 // the position's two).  out = the single-precision roundings; returns false when one of them cannot
 // be guaranteed (a value within 2^-43 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary: the
-// double-single error is below 2^-44 of that, the double-precision formula's deviation below
-// 2^-50), then the caller evaluates in double precision.
+// double-single error is below 2^-45 of that, the double-precision formula's deviation below
+// 2^-50), then the caller evaluates in double precision.  kRolled keeps one copy of the component
+// code (for kernels whose loops crowd the instruction cache).
+template <bool kRolled = true>
 __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const float4 *logt, const ds U[3], ds s,
                                                    const uint32_t *w, float out[3], ds *unrounded = nullptr)
 {
     bool ok = true;
-#pragma unroll 1   // one copy of the component code: the sampling loop is large for the instruction cache
-    for (int k = 0; k < 3; ++k) {
+    auto component = [&](int k) {
         const ds cp = ds_turn_cos(turn, w[4 * k], w[4 * k + 1]);
         const ds L = ds_neg_log1m(logt, w[4 * k + 2], w[4 * k + 3]);
         const ds rl = ds_sqrt(L);
@@ -355,7 +413,27 @@ __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const fl
         ok = ok && ds_rounds_to_hi(xi, err);
         out[k] = xi.hi;
         if (unrounded) unrounded[k] = xi;
+    };
+    if (kRolled) {
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) component(k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) component(k);
     }
+    return ok;
+}
+
+// Double-single s = sqrt(2 R T) and U of a cell's Maxwellian from its double-precision state
+// q = (rho, U, V, W, T) without the double-precision unit (ds_of_double_int for R, T and U; 2 R T as a
+// double-single product; relative error of s below 2^-46).  Returns false where a value is outside
+// the integer conversion's range.
+__host__ __device__ __forceinline__ bool ds_maxwell_params(double R, const double *q, ds U[3], ds &s)
+{
+    ds r, t;
+    bool ok = ds_of_double_int(R, r) && ds_of_double_int(q[4], t);
+    for (int d = 0; d < 3; ++d) ok = ds_of_double_int(q[1 + d], U[d]) && ok;
+    s = ds_sqrt(ds_mul(ds_scale(r, 2.0f), t));
     return ok;
 }
 

@@ -21,7 +21,7 @@
 namespace duwp {
 
 // cos and sin of 2 pi k / kTurnTable as double-single pairs (scattering and sampling of
-// single-precision records), and the log table of the sampling (1/F and log F at F = 1 + (j - kLogCenter)/256)
+// single-precision records), and the log table of the sampling (1/F and log F at F = 1 + (j - kLogCenter)/1024)
 __device__ float4 g_turn[kTurnTable];
 __device__ float4 g_logt[kLogTable];
 
@@ -41,7 +41,7 @@ __global__ void k_init_turn()
         g_turn[k] = make_float4(cc.x, cc.y, ss.x, ss.y);
     }
     if (k < kLogTable) {
-        const double F = static_cast<double>(256 + k - kLogCenter) * 0x1p-8;
+        const double F = static_cast<double>(1024 + k - kLogCenter) * 0x1p-10;
         const float2 inv = ds_split(1.0 / F), lg = ds_split(log(F));
         g_logt[k] = make_float4(inv.x, inv.y, lg.x, lg.y);
     }
@@ -142,6 +142,7 @@ struct MaxwellCell {
     double sq;
     ds U[3];
     ds s;
+    const double *qp;       // the cell's primitive state (rho, U, V, W, T) in device memory
 };
 
 // Chapman-Enskog factor of a cell's samples under the NS-corrected option (below).
@@ -152,6 +153,7 @@ struct CeCell {
 __device__ inline MaxwellCell maxwell_cell(const InstDev &I, const double *q)
 {
     MaxwellCell m;
+    m.qp = q;
     for (int k = 0; k < 5; ++k) m.q[k] = q[k];
     m.sq = sqrt(2.0 * I.R * q[4]);
     for (int d = 0; d < 3; ++d) {
@@ -161,6 +163,22 @@ __device__ inline MaxwellCell maxwell_cell(const InstDev &I, const double *q)
     const float h = __double2float_rn(m.sq);
     m.s = {h, __double2float_rn(m.sq - static_cast<double>(h))};
     return m;
+}
+
+// The sampling state of a cell for single-precision records drawn without the NS correction: only
+// the double-single U and s, formed by integer and single-precision operations (the double-precision
+// units are few on this GPU and a chunk of draws is short); q and sq are not set, and a draw that
+// takes the double-precision path reads the state from qp.  Double-precision records (and values
+// outside the integer conversion's range) take the full state.
+template <typename Rec>
+__device__ inline MaxwellCell maxwell_cell_for(const InstDev &I, const double *q)
+{
+    if constexpr (sizeof(Rec) == sizeof(RecF)) {
+        MaxwellCell m;
+        m.qp = q;
+        if (ds_maxwell_params(I.R, q, m.U, m.s)) return m;
+    }
+    return maxwell_cell(I, q);
 }
 
 // Velocities in double precision from the 14 draw words after the position's (w).
@@ -181,6 +199,23 @@ __device__ __noinline__ void maxwell_fp64(const MaxwellCell &mc, const uint32_t 
     maxwell_xi(mc, w, xi);
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = store_val(xi[d], T());
+}
+
+// The same double-precision evaluation for a single-precision record from the cell's state in memory
+// (words w[2..13] of the draw by value, so that the caller keeps them in registers); returns the
+// record's velocities in y, z, w.
+__device__ __noinline__ float4 maxwell_fp64_from(double R, const double *q, uint4 wa, uint4 wb, uint4 wc)
+{
+    const uint32_t w[12] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w, wc.x, wc.y, wc.z, wc.w};
+    const double sq = sqrt(2.0 * R * q[4]);
+    float out[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double r1 = u53(w[4 * d], w[4 * d + 1]);
+        const double r2 = 1.0 - u53(w[4 * d + 2], w[4 * d + 3]);
+        out[d] = __double2float_rn(q[1 + d] + (sq * cos(kTwoPi * r1)) * sqrt(-log(r2)));
+    }
+    return make_float4(0.0f, out[0], out[1], out[2]);
 }
 
 // NS-corrected sampling (resample_mode CE; the first-order Chapman-Enskog form of the equilibrium,
@@ -272,7 +307,7 @@ __device__ __forceinline__ float u53_float(uint32_t a, uint32_t b)
     return __ull2float_rn(m) * 0x1p-53f;
 }
 
-template <typename Rec>
+template <typename Rec, bool kRolled = true>
 __device__ __forceinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
                                            const CeCell *ce)
 {
@@ -293,7 +328,13 @@ __device__ __forceinline__ Rec sample_particle(const InstDev &I, uint32_t id, ui
         // single-precision records: double-single evaluation, double precision only where the
         // rounding of a component cannot be guaranteed
         x = u53_float(w[0], w[1]);
-        if (!ds_maxwell(g_turn, g_logt, mc.U, mc.s, w + 2, xi)) maxwell_fp64<T>(mc, w + 2, xi);
+        if (!ds_maxwell<kRolled>(g_turn, g_logt, mc.U, mc.s, w + 2, xi)) {
+            const float4 f = maxwell_fp64_from(I.R, mc.qp, make_uint4(w[2], w[3], w[4], w[5]),
+                                               make_uint4(w[6], w[7], w[8], w[9]), make_uint4(w[10], w[11], w[12], w[13]));
+            xi[0] = f.y;
+            xi[1] = f.z;
+            xi[2] = f.w;
+        }
     } else {
         x = u53(w[0], w[1]);
         maxwell_fp64<T>(mc, w + 2, xi);
@@ -887,7 +928,7 @@ __device__ __noinline__ void collide_big(const EngineDev &E, int g, CollideShare
         if (I.resample_mode == 1) {
             sample_run_ce<Rec>(I, E.prim, E.valid, g, i, step, blk + n_in, 0, nn, lane);
         } else {
-            const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+            const MaxwellCell mc = maxwell_cell_for<Rec>(I, E.prim + 5 * g);
             for (int j = lane; j < nn; j += 32)
                 st_rec(blk + n_in + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc, nullptr));
         }
@@ -960,7 +1001,7 @@ __device__ __noinline__ void collide_staged(const EngineDev &E, const InstDev &I
         if (I.resample_mode == 1) {
             sample_run_ce<Rec>(I, E.prim, E.valid, g, h.i, step, stage + run, 0, static_cast<int>(nn), lane);
         } else {
-            const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+            const MaxwellCell mc = maxwell_cell_for<Rec>(I, E.prim + 5 * g);
             for (int j = lane; j < nn; j += 32)
                 st_rec(stage + run + j, sample_particle<Rec>(I, id, static_cast<uint32_t>(j), step, mc, nullptr));
         }
@@ -1558,10 +1599,11 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_const
             sample_run_ce<Rec>(I, E.prim, E.valid, g, i, I.step, out + off + n_in, j0, j1, lane);
             continue;
         }
-        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+        // (the draws unrolled here: this kernel's loop is short)
+        const MaxwellCell mc = maxwell_cell_for<Rec>(I, E.prim + 5 * g);
         for (int j = j0 + lane; j < j1; j += 32)
-            st_rec(out + off + n_in + j, sample_particle<Rec>(I, cell_id(I, i), static_cast<uint32_t>(j), I.step, mc,
-                                                              nullptr));
+            st_rec(out + off + n_in + j, sample_particle<Rec, false>(I, cell_id(I, i), static_cast<uint32_t>(j),
+                                                                     I.step, mc, nullptr));
     }
 }
 
@@ -1630,7 +1672,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_con
             sample_run_ce<Rec>(I, E.prim, E.valid, g, i, I.step, out + off + n_in, j0, j1, lane);
             continue;
         }
-        const MaxwellCell mc = maxwell_cell(I, E.prim + 5 * g);
+        const MaxwellCell mc = maxwell_cell_for<Rec>(I, E.prim + 5 * g);
         for (int j = j0 + lane; j < j1; j += 32)
             st_rec(out + off + n_in + j, sample_particle<Rec>(I, cell_id(I, i), static_cast<uint32_t>(j), I.step, mc,
                                                               nullptr));

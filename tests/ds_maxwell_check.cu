@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <random>
 
 #include "duwp_dsmath.cuh"
@@ -30,12 +31,37 @@ int main(int argc, char **argv)
     }
     float4 logt[kLogTable];
     for (int k = 0; k < kLogTable; ++k) {
-        const long double F = (long double)(256 + k - kLogCenter) / 256.0L;
+        const long double F = (long double)(1024 + k - kLogCenter) / 1024.0L;
         const long double inv = 1.0L / F, lg = logl(F);
         const float ih = static_cast<float>(inv), lh = static_cast<float>(lg);
         logt[k] = make_float4(ih, static_cast<float>(inv - ih), lh, static_cast<float>(lg - lh));
     }
     std::mt19937_64 rng(2306);
+    // the integer double -> double-single conversion against the double-precision one, on random bit
+    // patterns over its whole exponent range (ties and carries included by the low bits chosen)
+    for (long t = 0; t < 2000000; ++t) {
+        uint64_t bits = rng();
+        const uint64_t e = static_cast<uint64_t>(1023 - 70 + static_cast<int>(rng() % 170));
+        bits = (bits & 0x800fffffffffffffull) | (e << 52);
+        if (t % 4 == 1) bits = (bits & ~0x1fffffffull) | 0x10000000ull;            // exact tie
+        if (t % 4 == 2) bits |= 0x000fffffe0000000ull;                               // carry into the exponent
+        double x;
+        std::memcpy(&x, &bits, 8);
+        ds a;
+        const ds ref = ds_of_double(x);
+        if (!ds_of_double_int(x, a) || a.hi != ref.hi || a.lo != ref.lo || std::signbit(a.lo) != std::signbit(ref.lo)) {
+            printf("integer conversion differs: %.17g\n", x);
+            return 1;
+        }
+    }
+    {
+        ds a;
+        if (!ds_of_double_int(0.0, a) || a.hi != 0.0f || a.lo != 0.0f || ds_of_double_int(0x1p-71, a) ||
+            ds_of_double_int(0x1p100, a)) {
+            printf("integer conversion range\n");
+            return 1;
+        }
+    }
     std::uniform_real_distribution<double> ud(0.0, 1.0);
     const long n = argc > 1 ? atol(argv[1]) : 100000;
     long nfail = 0, nbad = 0;
@@ -61,16 +87,24 @@ int main(int argc, char **argv)
             }
         }
         const double sq = sqrt(2.0 * R * T);
-        ds U[3];
-        for (int k = 0; k < 3; ++k) {
-            const float h = static_cast<float>(Uc[k]);
-            U[k] = {h, static_cast<float>(Uc[k] - h)};
+        // the cell's double-single parameters as the sampling kernels form them (integer conversions,
+        // s = sqrt(2 R T) in double-single arithmetic); the conversion must equal ds_of_double
+        ds U[3], s;
+        const double q[5] = {1.0, Uc[0], Uc[1], Uc[2], T};
+        if (!ds_maxwell_params(R, q, U, s)) {
+            printf("parameters out of range at %ld\n", t);
+            return 1;
         }
-        const float sh = static_cast<float>(sq);
-        const ds s = {sh, static_cast<float>(sq - sh)};
+        for (int k = 0; k < 3; ++k) {
+            const ds ref = ds_of_double(Uc[k]);
+            if (U[k].hi != ref.hi || U[k].lo != ref.lo) {
+                printf("integer conversion differs at %ld: %.17g\n", t, Uc[k]);
+                return 1;
+            }
+        }
         float out[3];
         ds un[3];
-        const bool ok = ds_maxwell(turn, logt, U, s, w, out, un);
+        const bool ok = (t & 1) ? ds_maxwell<true>(turn, logt, U, s, w, out, un) : ds_maxwell<false>(turn, logt, U, s, w, out, un);
         for (int k = 0; k < 3; ++k) {
             // errors against a long-double evaluation with the same double inputs: of the
             // double-single value (relative to |U| + s sqrt(L)), and of the double-precision formula
