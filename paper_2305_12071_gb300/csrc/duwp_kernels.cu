@@ -2625,27 +2625,40 @@ __global__ void k_sh_sums(EngineDev E, int rp, int g0, int ncell, ShCell *tmp)
     const int n = h.n_in;
     constexpr int kIn = 4;   // records per lane in flight
     if constexpr (sizeof(Rec().u) == 4) {
-        const ds V[3] = {{tmp[g].nu[0], tmp[g].nu[1]}, {tmp[g].nu[2], tmp[g].nu[3]}, {tmp[g].nu[4], tmp[g].nu[5]}};
-        ds f2 = {0.0f, 0.0f}, f3 = {0.0f, 0.0f};
-        for (int k0 = lane; k0 < n; k0 += 32 * kIn) {
-            Rec x[kIn];
+        // single-precision records: c = xi - U formed exactly (TwoSum with the double-single -U) and
+        // rounded once, the two terms in single precision, each lane's sums compensated (TwoSum of
+        // every addition, the errors summed apart); the arrived runs read as contiguous ranges
+        const float v0h = tmp[g].nu[0], v0l = tmp[g].nu[1], v1h = tmp[g].nu[2], v1l = tmp[g].nu[3],
+                    v2h = tmp[g].nu[4], v2l = tmp[g].nu[5];
+        float s2 = 0.0f, e2 = 0.0f, s3 = 0.0f, e3 = 0.0f;
+        auto add = [&](const Rec &r) {
+            const ds ax = ds_two_sum(r.u, v0h), ay = ds_two_sum(r.v, v1h), az = ds_two_sum(r.w, v2h);
+            const float cx = ax.hi + (ax.lo + v0l), cy = ay.hi + (ay.lo + v1l), cz = az.hi + (az.lo + v2l);
+            const float xx = cx * cx;
+            const float c2 = fmaf(cz, cz, fmaf(cy, cy, xx));
+            const float t3 = (0.5f * cx) * c2;
+            const ds a2 = ds_two_sum(s2, xx), a3 = ds_two_sum(s3, t3);
+            s2 = a2.hi;
+            e2 += a2.lo;
+            s3 = a3.hi;
+            e3 += a3.lo;
+        };
+        auto range = [&](const Rec *p, int cnt) {
+            for (int k0 = lane; k0 < cnt; k0 += 32 * kIn) {
+                Rec x[kIn];
 #pragma unroll
-            for (int u = 0; u < kIn; ++u) {
-                const int r = k0 + 32 * u;
-                if (r >= n) break;
-                x[u] = ld_rec(arrived_ptr<Rec>(r, h, in, fs));
-            }
+                for (int u = 0; u < kIn; ++u)
+                    if (k0 + 32 * u < cnt) x[u] = ld_rec(p + k0 + 32 * u);
 #pragma unroll
-            for (int u = 0; u < kIn; ++u) {
-                if (k0 + 32 * u >= n) break;
-                const ds cx = ds_add({x[u].u, 0.0f}, V[0]), cy = ds_add({x[u].v, 0.0f}, V[1]),
-                         cz = ds_add({x[u].w, 0.0f}, V[2]);
-                const ds xx = ds_mul(cx, cx);
-                const ds c2 = ds_add(ds_add(xx, ds_mul(cy, cy)), ds_mul(cz, cz));
-                f2 = ds_add(f2, xx);
-                f3 = ds_add(f3, ds_mul(cx, ds_scale(c2, 0.5f)));
+                for (int u = 0; u < kIn; ++u)
+                    if (k0 + 32 * u < cnt) add(x[u]);
             }
-        }
+        };
+        range(in + (h.Rend - h.Rn), h.Rn);
+        range(in + h.Sa, h.Sn);
+        range(in + h.La, h.Ln);
+        for (int k = lane; k < h.nfb + h.nfa; k += 32) add(fs[h.fb + k].rec);
+        ds f2 = ds_two_sum(s2, e2), f3 = ds_two_sum(s3, e3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             f2 = ds_add(f2, {__shfl_xor_sync(0xffffffffu, f2.hi, o), __shfl_xor_sync(0xffffffffu, f2.lo, o)});
