@@ -717,6 +717,21 @@ __device__ __forceinline__ Rec *arrived_ptr(int x, const CellHdr &h, Rec *in, FR
     return &fs[h.fb + h.nfb + r].rec;
 }
 
+// Record x of a direct cell's list after re-sampling: the arrived positions, then the re-sampled
+// particles after them in the cell's output block blk.
+template <typename Rec, typename FR>
+__device__ __forceinline__ Rec *list_rec(int x, const CellHdr &h, Rec *in, FR *fs, Rec *blk)
+{
+    return x < h.n_in ? arrived_ptr<Rec>(x, h, in, fs) : blk + x;
+}
+
+// Whether a direct cell's re-sampled particles (if any) are in place before the collision kernels
+// run: none, or all drawn ahead by k_sample (kPreSampleMin or more of them).
+__device__ __forceinline__ bool light_resampling(const CellHdr &h)
+{
+    return h.n_new == 0 || h.n_new >= kPreSampleMin;
+}
+
 // ------------------------------------------------------------------------------------------
 // Collision kernel.  Runs before the streaming kernel on the cells of class kClsDirect and
 // kClsStaged (work list built by k_offsets_flux):
@@ -756,7 +771,8 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n)
     return pos;
 }
 
-// Light direct cells (P = 0, 1..kMaxDirect candidates, nothing re-sampled), packed: the warp holds
+// Light direct cells (P = 0, 1..kMaxDirect candidates, nothing re-sampled or every re-sampled particle
+// drawn ahead by k_sample, as in a first step), packed: the warp holds
 // the cells of list positions t0..n_items-1 (at most 32; one round of pack_rounds) and runs them in
 // rounds.  A round takes the next cells whose candidates fit in the 32 lanes together:
 // cell c on lanes [b_c, b_c + nc_c), lane b_c + k its candidate k, with the table slots
@@ -765,11 +781,12 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 // drawn at once (the pairs depend only on counters), a batch cut before the first candidate that
 // shares a particle with an earlier one of the batch and after the first whose c_r raises c_max.
 // The touched particles are loaded into the table by the lane that inserted them, collided there
-// in candidate order and the changed ones written back in place (into the arrived runs or the
-// far-mover list, where the streaming kernel reads them).
+// in candidate order and the changed ones written back in place (into the arrived runs, the
+// far-mover list or the re-sampled positions of the output block, where the streaming kernel reads
+// them).
 template <typename Rec>
 __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t *list, int t0, int n_items,
-                                               CollideShared<Rec> &S, Rec *in, FarItem<Rec> *fs)
+                                               CollideShared<Rec> &S, Rec *in, Rec *out, FarItem<Rec> *fs)
 {
     const int lane = threadIdx.x & 31;
     const unsigned upto = 0xffffffffu >> (31 - lane);          // lanes 0..lane
@@ -778,7 +795,7 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
         cg = list[t0 + lane];
         const CellHdr *hp = E.hdr + cg;
         const int nc = hp->nc;
-        if (hp->cls == kClsDirect && hp->n_new == 0 && nc >= 1 && nc <= kMaxDirect) cn = nc;
+        if (hp->cls == kClsDirect && light_resampling(*hp) && nc >= 1 && nc <= kMaxDirect) cn = nc;
     }
     int done = 0;                                               // chunk cells collided so far
     while (__any_sync(0xffffffffu, lane >= done && cn > 0)) {
@@ -816,8 +833,10 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
         int sa = 0, sc = 0;
         bool fa = false, fb = false;
         uint32_t w2 = 0, w3 = 0;
+        Rec *blk = nullptr;
         if (act) {
-            const int N = hp->n_in;
+            const int N = hp->n_in + hp->n_new;
+            blk = out + hp->off;
             uint32_t w[4];
             draw(I, cell_id(I, hp->i), 2u * static_cast<uint32_t>(kc), I.step, kCollide, w);
             const int pa = static_cast<int>(idx32(w[0], static_cast<uint32_t>(N)));
@@ -827,8 +846,8 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
             w3 = w[3];
             sa = seg_insert(S.key, 4 * sb, 4 * nc, pa, fa, E.err);
             sc = seg_insert(S.key, 4 * sb, 4 * nc, pb, fb, E.err);
-            if (fa) S.rec[sa] = ld_rec_rw(arrived_ptr<Rec>(pa, *hp, in, fs));
-            if (fb) S.rec[sc] = ld_rec_rw(arrived_ptr<Rec>(pb, *hp, in, fs));
+            if (fa) S.rec[sa] = ld_rec_rw(list_rec<Rec>(pa, *hp, in, fs, blk));
+            if (fb) S.rec[sc] = ld_rec_rw(list_rec<Rec>(pb, *hp, in, fs, blk));
         }
         __syncwarp();
         double cm = act ? E.cmax[g] : 0.0;
@@ -883,8 +902,8 @@ __device__ __forceinline__ void collide_packed(const EngineDev &E, const int32_t
             if (k0 < nc) k0 = end;
         }
         if (act) {
-            if (fa && S.mod[sa]) st_rec(arrived_ptr<Rec>(S.key[sa], *hp, in, fs), S.rec[sa]);
-            if (fb && S.mod[sc]) st_rec(arrived_ptr<Rec>(S.key[sc], *hp, in, fs), S.rec[sc]);
+            if (fa && S.mod[sa]) st_rec(list_rec<Rec>(S.key[sa], *hp, in, fs, blk), S.rec[sa]);
+            if (fb && S.mod[sc]) st_rec(list_rec<Rec>(S.key[sc], *hp, in, fs, blk), S.rec[sc]);
             if (kc == 0) {
                 E.ncand[g] = nc;
                 E.nacc[g] = acc;
@@ -1648,7 +1667,7 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_con
             int tn = 0;
             if (lane == 0) tn = atomicAdd(&E.ticket[kRoundCtr], 1);
             const int2 r = E.wr[t];
-            collide_packed<Rec>(E, list, r.x, min(r.x + min(r.y, 32), n_light), S, in, fs);
+            collide_packed<Rec>(E, list, r.x, min(r.x + min(r.y, 32), n_light), S, in, out, fs);
             t = __shfl_sync(0xffffffffu, tn, 0);
         }
     }
@@ -2449,7 +2468,7 @@ __global__ void __launch_bounds__(B, 1024 / B) k_offsets_flux(EngineDev E, int w
             if (cls == kClsDirect) {
                 const int nc = E.hdr[g].nc;
                 if (nc >= kHeavyCandidates) lq = kHeavyList;
-                else if (E.hdr[g].n_new == 0 && nc <= kMaxDirect) lq = kLightList;
+                else if (light_resampling(E.hdr[g]) && nc <= kMaxDirect) lq = kLightList;
             }
             if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
             if (cls == kClsDirect && E.hdr[g].n_new >= kPreSampleMin) {
