@@ -489,29 +489,36 @@ static double ce_gamma(const ora_ce *f, const double xi[3])
     return 1.0 + s / (2.0 * f->prt) + (f->qx * cx / f->prt) * (c2 / (5.0 * f->RT) - 1.0);
 }
 
-/* Maxwellian velocities at (U, V, W, T) from words w[0..11], Eq. (maxsample): per component
- * xi = U + sqrt(2RT) cos(2 pi r1) sqrt(-ln r2), r1 = u53(w[4d], w[4d+1]), r2 = 1 - u53(w[4d+2], w[4d+3]). */
+/* Maxwellian velocities at (U, V, W, T) from words w[0..7], Eq. (maxsample), by the Box-Muller
+ * transform (Box and Muller, Ann. Math. Stat. 29, 1958): a uniform angle 2 pi r1 and the radius
+ * sqrt(2RT) sqrt(-ln r2) give two independent components, the cosine and the sine; the third takes
+ * a second pair of its own and its cosine:
+ *   xi_x = U + (sqrt(2RT) cos(2 pi r1)) sqrt(-ln r2),  xi_y = V + (sqrt(2RT) sin(2 pi r1)) sqrt(-ln r2),
+ *   xi_z = W + (sqrt(2RT) cos(2 pi r3)) sqrt(-ln r4),
+ * r1 = u53(w0, w1), r2 = 1 - u53(w2, w3), r3 = u53(w4, w5), r4 = 1 - u53(w6, w7). */
 static void maxwell_xi(const ora_params *p, const ora_prim *q, const uint32_t *w, double xi[3])
 {
     double sq = sqrt(2.0 * p->R * q->T);
-    double mean[3] = { q->u, q->v, q->w };
-    for (int d = 0; d < 3; ++d) {
-        double r1 = ora_u53(w[4 * d], w[4 * d + 1]);
-        double r2 = 1.0 - ora_u53(w[4 * d + 2], w[4 * d + 3]);
-        xi[d] = mean[d] + (sq * cos(ORA_TWO_PI * r1)) * sqrt(-log(r2));
-    }
+    double r1 = ora_u53(w[0], w[1]);
+    double r2 = 1.0 - ora_u53(w[2], w[3]);
+    double r3 = ora_u53(w[4], w[5]);
+    double r4 = 1.0 - ora_u53(w[6], w[7]);
+    double rad = sqrt(-log(r2));
+    xi[0] = q->u + (sq * cos(ORA_TWO_PI * r1)) * rad;
+    xi[1] = q->v + (sq * sin(ORA_TWO_PI * r1)) * rad;
+    xi[2] = q->w + (sq * cos(ORA_TWO_PI * r3)) * sqrt(-log(r4));
 }
 
 /* Sample j of a cell at state q, Eq. (maxsample); position uniform in the cell (reading).  Words of
- * the counters (id, 4j..4j+3, step, SAMPLE): 0-1 position, 2-13 velocities, 14-15 the acceptance
+ * the counters (id, 4j..4j+2, step, SAMPLE): 0-1 position, 2-9 velocities, 10-11 the acceptance
  * draw of the Chapman-Enskog correction (ce != NULL and on); its attempt a > 0 draws the counters
- * (id, 4j..4j+3, step, SAMPLE + 8a).  After ORA_CE_ATTEMPTS rejections the first Maxwellian
+ * (id, 4j..4j+2, step, SAMPLE + 8a).  After ORA_CE_ATTEMPTS rejections the first Maxwellian
  * candidate is kept. */
 static void sample_particle(const ora_params *p, ora_key key, uint32_t id, uint32_t j, uint32_t step,
                             const ora_prim *q, const ora_ce *ce, opart *out)
 {
-    uint32_t w[16];
-    for (uint32_t t = 0; t < 4; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE, w + 4 * t);
+    uint32_t w[12];
+    for (uint32_t t = 0; t < 3; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE, w + 4 * t);
     double xi[3];
     maxwell_xi(p, q, w + 2, xi);
     if (ce && ce->on) {
@@ -519,10 +526,10 @@ static void sample_particle(const ora_params *p, ora_key key, uint32_t id, uint3
         int accepted = 0;
         for (uint32_t a = 0; a < ORA_CE_ATTEMPTS; ++a) {
             if (a > 0) {
-                for (uint32_t t = 0; t < 4; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE + 8u * a, w + 4 * t);
+                for (uint32_t t = 0; t < 3; ++t) draw(key, id, 4u * j + t, step, ORA_SAMPLE + 8u * a, w + 4 * t);
                 maxwell_xi(p, q, w + 2, xi);
             }
-            if (ora_u53(w[14], w[15]) * ce->A < ce_gamma(ce, xi)) { accepted = 1; break; }
+            if (ora_u53(w[10], w[11]) * ce->A < ce_gamma(ce, xi)) { accepted = 1; break; }
         }
         if (!accepted) { xi[0] = xi0[0]; xi[1] = xi0[1]; xi[2] = xi0[2]; }
         /* the position always comes from the first attempt's words */

@@ -790,16 +790,19 @@ int duwp_moments(duwp_handle *h, int32_t b, int32_t which, double *rho, double *
     const double scale = (which == DUWP_AVERAGED) ? (navg > 0 ? 1.0 / static_cast<double>(navg) : 0.0) : 1.0;
     for (int32_t i = 0; i < n; ++i) {
         const double *c = psi.data() + 5 * size_t(i);
+        // the same arithmetic as the all-instance read-out kernel (one reciprocal per density)
         const double r = c[0] * scale;
         const double mx = c[1] * scale, my = c[2] * scale, mz = c[3] * scale, E5 = c[4] * scale;
-        const double ux = r > 0 ? mx / r : 0.0, uy = r > 0 ? my / r : 0.0, uz = r > 0 ? mz / r : 0.0;
-        const double tt = r > 0 ? (E5 / r - 0.5 * (ux * ux + uy * uy + uz * uz)) / (1.5 * hi.p.R) : 0.0;
+        const double ir = r > 0 ? 1.0 / r : 0.0;
+        const double ux = mx * ir, uy = my * ir, uz = mz * ir;
+        const double tt = r > 0 ? (E5 * ir - 0.5 * (ux * ux + uy * uy + uz * uz)) * hi.d.inv_cv : 0.0;
         if (rho) rho[i] = r;
         if (u) u[i] = ux;
         if (T) T[i] = tt;
         if (wave_frac) {
             const double rt = cur[5 * size_t(i)];
-            wave_frac[i] = rt > 0 ? (rt - static_cast<double>(cnt[i]) * hi.d.mp_over_dx) / rt : 0.0;
+            const double irt = (which == DUWP_AVERAGED) ? (rt > 0 ? 1.0 / rt : 0.0) : ir;
+            wave_frac[i] = rt > 0 ? 1.0 - (static_cast<double>(cnt[i]) * hi.d.mp_over_dx) * irt : 0.0;
         }
     }
     return DUWP_OK;

@@ -214,14 +214,6 @@ __host__ __device__ __forceinline__ void ds_turn(const float4 *turn, uint32_t v2
     sp = ds_add(ds_mul(S, cx), ds_mul(C, sx));
 }
 
-// cos(2 pi u) alone (same evaluation as ds_turn's cp).
-__host__ __device__ __forceinline__ ds ds_turn_cos(const float4 *turn, uint32_t v2, uint32_t v3)
-{
-    ds C, S, cx, sx;
-    ds_turn_parts(turn, v2, v3, C, S, cx, sx);
-    return ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx)));
-}
-
 // The parts of the scattering that depend only on the draw: cos(theta), sin(theta), cos(phi),
 // sin(phi).  Returns false when sin(theta) < 2^-10 (the pair then takes the double-precision path).
 struct DsAngles {
@@ -390,36 +382,42 @@ __host__ __device__ __forceinline__ bool ds_of_double_int(double x, ds &out)
     return true;
 }
 
-// Velocity components of a Maxwellian sample (Eq. maxsample) for single-precision records:
-// xi_d = U_d + (s cos(2 pi r1)) sqrt(-log(1 - r2)), d = 0, 1, 2, with s = sqrt(2 R T), U and s as
-// double-single values, (r1, r2) the 53-bit uniforms of words w[4d+2..4d+5] (w = the 14 words after
-// the position's two).  out = the single-precision roundings; returns false when one of them cannot
-// be guaranteed (a value within 2^-43 (|U_d| + s sqrt(-log(1 - r2))) of a rounding boundary: the
+// Velocity components of a Maxwellian sample (Eq. maxsample) for single-precision records, by the
+// Box-Muller transform: xi_x = U + (s cos(2 pi r1)) sqrt(-log(1 - r2)), xi_y = V + (s sin(2 pi r1))
+// sqrt(-log(1 - r2)), xi_z = W + (s cos(2 pi r3)) sqrt(-log(1 - r4)), with s = sqrt(2 R T), U and s as
+// double-single values, r1..r4 the 53-bit uniforms of words w[0..7] (the 8 words after the
+// position's two).  out = the single-precision roundings; returns false when one of them cannot be
+// guaranteed (a value within 2^-43 (|U_d| + s sqrt(-log(1 - r))) of a rounding boundary: the
 // double-single error is below 2^-45 of that, the double-precision formula's deviation below
-// 2^-50), then the caller evaluates in double precision.  kRolled keeps one copy of the component
-// code (for kernels whose loops crowd the instruction cache).
+// 2^-50), then the caller evaluates in double precision.  kRolled keeps one copy of the radius code
+// (for kernels whose loops crowd the instruction cache).
 template <bool kRolled = true>
 __host__ __device__ __forceinline__ bool ds_maxwell(const float4 *turn, const float4 *logt, const ds U[3], ds s,
                                                    const uint32_t *w, float out[3], ds *unrounded = nullptr)
 {
     bool ok = true;
-    auto component = [&](int k) {
-        const ds cp = ds_turn_cos(turn, w[4 * k], w[4 * k + 1]);
-        const ds L = ds_neg_log1m(logt, w[4 * k + 2], w[4 * k + 3]);
-        const ds rl = ds_sqrt(L);
-        const ds mag = ds_mul(s, rl);
-        const ds xi = ds_add(U[k], ds_mul(mag, cp));
+    auto component = [&](int k, ds mag, ds c) {
+        const ds xi = ds_add(U[k], ds_mul(mag, c));
         const float err = 0x1p-43f * (fabsf(U[k].hi) + mag.hi);
         ok = ok && ds_rounds_to_hi(xi, err);
         out[k] = xi.hi;
         if (unrounded) unrounded[k] = xi;
     };
+    // pair m = 0: angle w[0..1], radius w[2..3] -> x (cosine), y (sine); pair m = 1: angle w[4..5],
+    // radius w[6..7] -> z (cosine)
+    auto pair = [&](int m) {
+        ds C, S, cx, sx;
+        ds_turn_parts(turn, w[4 * m], w[4 * m + 1], C, S, cx, sx);
+        const ds mag = ds_mul(s, ds_sqrt(ds_neg_log1m(logt, w[4 * m + 2], w[4 * m + 3])));
+        component(2 * m, mag, ds_add(ds_mul(C, cx), ds_neg(ds_mul(S, sx))));
+        if (m == 0) component(1, mag, ds_add(ds_mul(S, cx), ds_mul(C, sx)));
+    };
     if (kRolled) {
 #pragma unroll 1
-        for (int k = 0; k < 3; ++k) component(k);
+        for (int m = 0; m < 2; ++m) pair(m);
     } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) component(k);
+        pair(0);
+        pair(1);
     }
     return ok;
 }

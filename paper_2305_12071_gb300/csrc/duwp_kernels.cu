@@ -181,15 +181,19 @@ __device__ inline MaxwellCell maxwell_cell_for(const InstDev &I, const double *q
     return maxwell_cell(I, q);
 }
 
-// Velocities in double precision from the 14 draw words after the position's (w).
+// Velocities in double precision from the 8 draw words after the position's (w), by the Box-Muller
+// transform: the angle 2 pi r1 and the radius sqrt(2RT) sqrt(-ln r2) give the x component (cosine)
+// and the y component (sine); z takes its own angle r3 and radius r4 (cosine).
 __device__ __forceinline__ void maxwell_xi(const MaxwellCell &mc, const uint32_t *w, double out[3])
 {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double r1 = u53(w[4 * d], w[4 * d + 1]);
-        const double r2 = 1.0 - u53(w[4 * d + 2], w[4 * d + 3]);
-        out[d] = mc.q[1 + d] + (mc.sq * cos(kTwoPi * r1)) * sqrt(-log(r2));
-    }
+    const double r1 = u53(w[0], w[1]);
+    const double r2 = 1.0 - u53(w[2], w[3]);
+    const double r3 = u53(w[4], w[5]);
+    const double r4 = 1.0 - u53(w[6], w[7]);
+    const double rad = sqrt(-log(r2));
+    out[0] = mc.q[1] + (mc.sq * cos(kTwoPi * r1)) * rad;
+    out[1] = mc.q[2] + (mc.sq * sin(kTwoPi * r1)) * rad;
+    out[2] = mc.q[3] + (mc.sq * cos(kTwoPi * r3)) * sqrt(-log(r4));
 }
 
 template <typename T>
@@ -202,20 +206,19 @@ __device__ __noinline__ void maxwell_fp64(const MaxwellCell &mc, const uint32_t 
 }
 
 // The same double-precision evaluation for a single-precision record from the cell's state in memory
-// (words w[2..13] of the draw by value, so that the caller keeps them in registers); returns the
+// (words w[2..9] of the draw by value, so that the caller keeps them in registers); returns the
 // record's velocities in y, z, w.
-__device__ __noinline__ float4 maxwell_fp64_from(double R, const double *q, uint4 wa, uint4 wb, uint4 wc)
+__device__ __noinline__ float4 maxwell_fp64_from(double R, const double *q, uint4 wa, uint4 wb)
 {
-    const uint32_t w[12] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w, wc.x, wc.y, wc.z, wc.w};
     const double sq = sqrt(2.0 * R * q[4]);
-    float out[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double r1 = u53(w[4 * d], w[4 * d + 1]);
-        const double r2 = 1.0 - u53(w[4 * d + 2], w[4 * d + 3]);
-        out[d] = __double2float_rn(q[1 + d] + (sq * cos(kTwoPi * r1)) * sqrt(-log(r2)));
-    }
-    return make_float4(0.0f, out[0], out[1], out[2]);
+    const double r1 = u53(wa.x, wa.y);
+    const double r2 = 1.0 - u53(wa.z, wa.w);
+    const double r3 = u53(wb.x, wb.y);
+    const double r4 = 1.0 - u53(wb.z, wb.w);
+    const double rad = sqrt(-log(r2));
+    return make_float4(0.0f, __double2float_rn(q[1] + (sq * cos(kTwoPi * r1)) * rad),
+                       __double2float_rn(q[2] + (sq * sin(kTwoPi * r1)) * rad),
+                       __double2float_rn(q[3] + (sq * cos(kTwoPi * r3)) * sqrt(-log(r4))));
 }
 
 // NS-corrected sampling (resample_mode CE; the first-order Chapman-Enskog form of the equilibrium,
@@ -279,20 +282,20 @@ __device__ __forceinline__ double ce_gamma(const MaxwellCell &mc, const CeCell &
 }
 
 // Velocities of an NS-corrected sample: attempt 0 uses the sample's own words w0 (velocities from
-// w0[2..13], acceptance from w0[14..15]); attempt a > 0 draws the counters (id, 4j..4j+3, step,
+// w0[2..9], acceptance from w0[10..11]); attempt a > 0 draws the counters (id, 4j..4j+2, step,
 // SAMPLE + 8a).  After kCeAttempts rejections the attempt-0 Maxwellian is kept.
 __device__ __noinline__ void ce_xi(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
                                    const CeCell &ce, const uint32_t *w0, double xi[3])
 {
     maxwell_xi(mc, w0 + 2, xi);
-    if (u53(w0[14], w0[15]) * ce.A < ce_gamma(mc, ce, xi)) return;
-    uint32_t w[16];
+    if (u53(w0[10], w0[11]) * ce.A < ce_gamma(mc, ce, xi)) return;
+    uint32_t w[12];
     double t[3];
     for (int a = 1; a < kCeAttempts; ++a) {
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) draw(I, id, 4u * j + k, step, kSample + 8u * static_cast<uint32_t>(a), w + 4 * k);
+        for (uint32_t k = 0; k < 3; ++k) draw(I, id, 4u * j + k, step, kSample + 8u * static_cast<uint32_t>(a), w + 4 * k);
         maxwell_xi(mc, w + 2, t);
-        if (u53(w[14], w[15]) * ce.A < ce_gamma(mc, ce, t)) {
+        if (u53(w[10], w[11]) * ce.A < ce_gamma(mc, ce, t)) {
             xi[0] = t[0]; xi[1] = t[1]; xi[2] = t[2];
             return;
         }
@@ -311,9 +314,9 @@ template <typename Rec, bool kRolled = true>
 __device__ __forceinline__ Rec sample_particle(const InstDev &I, uint32_t id, uint32_t j, uint32_t step, const MaxwellCell &mc,
                                            const CeCell *ce)
 {
-    uint32_t w[16];
+    uint32_t w[12];
 #pragma unroll
-    for (uint32_t t = 0; t < 4; ++t) draw(I, id, 4u * j + t, step, kSample, w + 4 * t);
+    for (uint32_t t = 0; t < 3; ++t) draw(I, id, 4u * j + t, step, kSample, w + 4 * t);
     Rec r;
     using T = decltype(r.xl);
     T x, xi[3];
@@ -330,7 +333,7 @@ __device__ __forceinline__ Rec sample_particle(const InstDev &I, uint32_t id, ui
         x = u53_float(w[0], w[1]);
         if (!ds_maxwell<kRolled>(g_turn, g_logt, mc.U, mc.s, w + 2, xi)) {
             const float4 f = maxwell_fp64_from(I.R, mc.qp, make_uint4(w[2], w[3], w[4], w[5]),
-                                               make_uint4(w[6], w[7], w[8], w[9]), make_uint4(w[10], w[11], w[12], w[13]));
+                                               make_uint4(w[6], w[7], w[8], w[9]));
             xi[0] = f.y;
             xi[1] = f.z;
             xi[2] = f.w;
@@ -2772,15 +2775,19 @@ __global__ void k_moments(EngineDev E, int which, const int64_t *base, int64_t t
     const double *c = (which == 1 ? E.avg : E.psi) + 5 * static_cast<int64_t>(g);
     const int64_t navg = I.navg;
     const double scale = (which == 1) ? (navg > 0 ? 1.0 / static_cast<double>(navg) : 0.0) : 1.0;
+    // one reciprocal per density instead of five divisions (each double-precision instruction holds
+    // an SM sub-partition for 64 cycles on this GPU); the read-out, not a decision of the method
     const double r = c[0] * scale;
     const double mx = c[1] * scale, my = c[2] * scale, mz = c[3] * scale, e5 = c[4] * scale;
-    const double ux = r > 0 ? mx / r : 0.0, uy = r > 0 ? my / r : 0.0, uz = r > 0 ? mz / r : 0.0;
-    const double tt = r > 0 ? (e5 / r - 0.5 * (ux * ux + uy * uy + uz * uz)) / (1.5 * I.R) : 0.0;
+    const double ir = r > 0 ? 1.0 / r : 0.0;
+    const double ux = mx * ir, uy = my * ir, uz = mz * ir;
+    const double tt = r > 0 ? (e5 * ir - 0.5 * (ux * ux + uy * uy + uz * uz)) * I.inv_cv : 0.0;
     const double rt = E.psi[5 * static_cast<int64_t>(g)];
+    const double irt = (which == 1) ? (rt > 0 ? 1.0 / rt : 0.0) : ir;
     out[o] = r;
     out[total + o] = ux;
     out[2 * total + o] = tt;
-    out[3 * total + o] = rt > 0 ? (rt - static_cast<double>(E.cnt[g]) * I.mp_over_dx) / rt : 0.0;
+    out[3 * total + o] = rt > 0 ? 1.0 - (static_cast<double>(E.cnt[g]) * I.mp_over_dx) * irt : 0.0;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -158,11 +158,13 @@ void duwp_server::retire(Lane &L, Request *r)
     }
     for (int32_t i = 0; i < n; ++i) {
         const double *c = psi.data() + 5 * static_cast<size_t>(i);
+        // the same arithmetic as the library's other read-outs (one reciprocal per density)
         const double rho = c[0];
-        const double ux = rho > 0 ? c[1] / rho : 0.0, uy = rho > 0 ? c[2] / rho : 0.0, uz = rho > 0 ? c[3] / rho : 0.0;
+        const double ir = rho > 0 ? 1.0 / rho : 0.0;
+        const double ux = c[1] * ir, uy = c[2] * ir, uz = c[3] * ir;
         r->rho[i] = rho;
         r->u[i] = ux;
-        r->T[i] = rho > 0 ? (c[4] / rho - 0.5 * (ux * ux + uy * uy + uz * uz)) / (1.5 * hi.p.R) : 0.0;
+        r->T[i] = rho > 0 ? (c[4] * ir - 0.5 * (ux * ux + uy * uy + uz * uz)) * hi.d.inv_cv : 0.0;
     }
     eng.remove_instance(r->slot);
     L.cells.give(r->cell_base, n + 2);

@@ -1,8 +1,9 @@
 // Host-side check of the double-single Maxwellian sampling of single-precision records: for random
 // draws and cell states, whenever ds_maxwell reports success its floats must equal the
-// single-precision rounding of the double-precision evaluation of Eq. (maxsample),
-// xi = U + (sqrt(2RT) cos(2 pi r1)) sqrt(-log(1 - r2)), with r1, r2 the 53-bit uniforms of the draw
-// words; the fallback must stay rare.  Also checks -log(1 - u) against long double.
+// single-precision rounding of the double-precision evaluation of Eq. (maxsample) by the Box-Muller
+// pair, xi_x = U + (sqrt(2RT) cos(2 pi r1)) sqrt(-log(1 - r2)), xi_y = V + (sqrt(2RT) sin(2 pi r1))
+// sqrt(-log(1 - r2)), xi_z = W + (sqrt(2RT) cos(2 pi r3)) sqrt(-log(1 - r4)), with r1..r4 the 53-bit
+// uniforms of the draw words; the fallback must stay rare.  Also checks -log(1 - u) against long double.
 // Usage: ds_maxwell_check N  -> prints "n fallbacks mismatches max_log_rel_err"; exit 1 on a mismatch.
 #include <cmath>
 #include <cstdio>
@@ -70,13 +71,15 @@ int main(int argc, char **argv)
     for (long t = 0; t < n; ++t) {
         const double R = 1.0, T = 0.05 + 8.0 * ud(rng);
         const double Uc[3] = {(ud(rng) - 0.5) * 20.0, (t % 3 == 0) ? 0.0 : ud(rng) - 0.5, 0.0};
-        uint32_t w[12];
-        for (int k = 0; k < 12; ++k) w[k] = static_cast<uint32_t>(rng());
+        uint32_t w[8];
+        for (int k = 0; k < 8; ++k) w[k] = static_cast<uint32_t>(rng());
         if (t % 7 == 0) w[2] = 0u;                              // u close to 0 (small -log(1 - u))
         if (t % 11 == 0) w[6] = 0xffffffffu;                    // u close to 1
-        if (t % 13 == 0) { w[10] = 0u; w[11] = static_cast<uint32_t>(t) << 11; }   // tiny u
+        if (t % 13 == 0) { w[6] = 0u; w[7] = static_cast<uint32_t>(t) << 11; }     // tiny u
+        if (t % 997 == 0) w[0] = static_cast<uint32_t>(t) & 0xffu;                 // angle near 0
+        if (t % 991 == 0) w[0] = 0x40000000u + (static_cast<uint32_t>(t) & 0xffu); // near a quarter turn
         // -log(1 - u) against long double
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 2; ++k) {
             const uint32_t a = w[4 * k + 2], b = w[4 * k + 3];
             const ds L = ds_neg_log1m(logt, a, b);
             const long double u = static_cast<long double>(u53_host(a, b));
@@ -105,19 +108,28 @@ int main(int argc, char **argv)
         float out[3];
         ds un[3];
         const bool ok = (t & 1) ? ds_maxwell<true>(turn, logt, U, s, w, out, un) : ds_maxwell<false>(turn, logt, U, s, w, out, un);
+        // the Box-Muller pair (x: cosine, y: sine of the first angle and radius) and z (cosine of the
+        // second), in double precision as the oracle evaluates it, and in long double
+        const double r1 = u53_host(w[0], w[1]), r2 = 1.0 - u53_host(w[2], w[3]);
+        const double r3 = u53_host(w[4], w[5]), r4 = 1.0 - u53_host(w[6], w[7]);
+        const double rad = sqrt(-log(r2));
+        const double fp[3] = {Uc[0] + (sq * cos(6.283185307179586 * r1)) * rad,
+                              Uc[1] + (sq * sin(6.283185307179586 * r1)) * rad,
+                              Uc[2] + (sq * cos(6.283185307179586 * r3)) * sqrt(-log(r4))};
+        const long double kTwoPiL = 6.283185307179586476925286766559L;
+        const long double La = -log1pl(-(long double)u53_host(w[2], w[3])), Lb = -log1pl(-(long double)u53_host(w[6], w[7]));
+        const long double ex[3] = {(long double)Uc[0] + (long double)sq * cosl(kTwoPiL * (long double)r1) * sqrtl(La),
+                                   (long double)Uc[1] + (long double)sq * sinl(kTwoPiL * (long double)r1) * sqrtl(La),
+                                   (long double)Uc[2] + (long double)sq * cosl(kTwoPiL * (long double)r3) * sqrtl(Lb)};
+        const long double Lk[3] = {La, La, Lb};
         for (int k = 0; k < 3; ++k) {
-            // errors against a long-double evaluation with the same double inputs: of the
+            // errors against the long-double evaluation with the same double inputs: of the
             // double-single value (relative to |U| + s sqrt(L)), and of the double-precision formula
-            const long double r1 = u53_host(w[4 * k], w[4 * k + 1]);
-            const long double L = -log1pl(-(long double)u53_host(w[4 * k + 2], w[4 * k + 3]));
-            const long double ex = (long double)Uc[k] + (long double)sq * cosl(6.283185307179586476925286766559L * r1) * sqrtl(L);
-            const long double S = fabsl((long double)Uc[k]) + (long double)sq * sqrtl(L);
+            const long double S = fabsl((long double)Uc[k]) + (long double)sq * sqrtl(Lk[k]);
             if (S > 0) {
-                const long double e = fabsl((long double)un[k].hi + un[k].lo - ex) / S;
+                const long double e = fabsl((long double)un[k].hi + un[k].lo - ex[k]) / S;
                 if (e > max_ds) max_ds = e;
-                const double r2 = 1.0 - u53_host(w[4 * k + 2], w[4 * k + 3]);
-                const double xi = Uc[k] + (sq * cos(6.283185307179586 * (double)r1)) * sqrt(-log(r2));
-                const long double f = fabsl((long double)xi - ex) / S;
+                const long double f = fabsl((long double)fp[k] - ex[k]) / S;
                 if (f > max_fp) max_fp = f;
             }
         }
@@ -126,11 +138,8 @@ int main(int argc, char **argv)
             continue;
         }
         for (int k = 0; k < 3; ++k) {
-            const double r1 = u53_host(w[4 * k], w[4 * k + 1]);
-            const double r2 = 1.0 - u53_host(w[4 * k + 2], w[4 * k + 3]);
-            const double xi = Uc[k] + (sq * cos(6.283185307179586 * r1)) * sqrt(-log(r2));
-            if (out[k] != static_cast<float>(xi)) {
-                if (nbad < 5) printf("mismatch at %ld component %d: %.9g vs %.9g\n", t, k, out[k], static_cast<float>(xi));
+            if (out[k] != static_cast<float>(fp[k])) {
+                if (nbad < 5) printf("mismatch at %ld component %d: %.9g vs %.9g\n", t, k, out[k], static_cast<float>(fp[k]));
                 ++nbad;
             }
         }

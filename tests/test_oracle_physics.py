@@ -35,10 +35,9 @@ def test_workload_shock_states_are_rankine_hugoniot(mach):
     assert (r, p, t) == pytest.approx((gr, gp, gt), rel=1e-14)
 
 
-def test_maxwell_molecule_stress_relaxation_rate(oracle_mod):
-    # omega = 1: every NTC candidate is accepted and the traceless stress of a
-    # homogeneous gas decays exactly as exp(-t p/mu).
+def _stress_relaxation_rate(oracle_mod, seed):
     p = W.uniform(n_cells=4, Kn=1.0, ppc_ref=5000, state=(1, 0, 0, 0, 1), omega=1.0)
+    p["seed"] = seed
     tau = oracle_mod.Oracle(p).consts()["mu_ref"]     # mu/p at rho = T = 1
     p["dt"] = 0.02 * tau
     o = oracle_mod.Oracle(p)
@@ -61,8 +60,15 @@ def test_maxwell_molecule_stress_relaxation_rate(oracle_mod):
         ts.append(k * p["dt"])
         ss.append(np.mean(uu**2) - 0.5 * (np.mean(vv**2) + np.mean(ww**2)))
         o.step(1)
-    rate = -np.polyfit(ts, np.log(ss), 1)[0]
-    assert rate * tau == pytest.approx(1.0, rel=0.04)
+    return -np.polyfit(ts, np.log(ss), 1)[0] * tau
+
+
+def test_maxwell_molecule_stress_relaxation_rate(oracle_mod):
+    # omega = 1: every NTC candidate is accepted and the traceless stress of a
+    # homogeneous gas decays exactly as exp(-t p/mu).  One 20k-particle run estimates the rate to
+    # a few percent (the late stress is small and noisy); three independent runs are averaged.
+    rates = [_stress_relaxation_rate(oracle_mod, seed) for seed in (1, 2, 3)]
+    assert np.mean(rates) == pytest.approx(1.0, rel=0.04), rates
 
 
 @pytest.mark.parametrize("omega,T0", [(0.81, 1.0), (0.81, 2.0), (0.5, 1.0)])
