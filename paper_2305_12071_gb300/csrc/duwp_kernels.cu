@@ -131,10 +131,10 @@ __device__ __forceinline__ int64_t transport(const InstDev &I, int64_t cell, dou
 }
 
 // ------------------------------------------------------------------------------------------
-// Maxwellian sample at the primitive state q (Eq. maxsample): per component
-// xi = U + sqrt(2RT) cos(2 pi r1) sqrt(-ln r2), r2 in (0,1]; position uniform in the cell.
-// Particle j of a cell uses counters (id, 4j..4j+3, step, SAMPLE): uniforms 0 -> position,
-// (1,2) -> x, (3,4) -> y, (5,6) -> z.
+// Maxwellian sample at the primitive state q (Eq. maxsample) by Box-Muller pairs: radius
+// sqrt(2RT) sqrt(-ln r2), r2 in (0,1], angle 2 pi r1 -> x (cosine) and y (sine); z from its own pair
+// (r3, r4) and its cosine; position uniform in the cell.  Particle j of a cell uses counters
+// (id, 4j..4j+2, step, SAMPLE): uniforms 0 -> position, 1 -> r1, 2 -> r2, 3 -> r3, 4 -> r4.
 // ------------------------------------------------------------------------------------------
 // Per-cell part of the sample: the state and sqrt(2RT), also as double-single values.
 struct MaxwellCell {
