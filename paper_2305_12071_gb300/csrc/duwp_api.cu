@@ -114,6 +114,11 @@ int derive_instance(const duwp_params &p, HostInst &o)
     d.inv_cv = 1.0 / (1.5 * p.R);
     d.vhs_expo = 1.0 - 2.0 * d.upsilon;
     d.vhs_expo_f = static_cast<float>(d.vhs_expo);
+    d.mu_ref_f = static_cast<float>(d.mu_ref);
+    d.T_ref_f = static_cast<float>(d.T_ref);
+    d.omega_f = static_cast<float>(d.omega);
+    d.R_f = static_cast<float>(d.R);
+    d.dt_f = static_cast<float>(d.dt);
     const duwp_state *st[2] = {&p.left, &p.right};
     for (int s = 0; s < 2; ++s) {
         double *q = s ? d.right : d.left;

@@ -123,6 +123,52 @@ __host__ __device__ __forceinline__ double fixed_to_double(int64_t v, int frac)
 #endif
 }
 
+// Double-precision bit pattern (host and device).
+__host__ __device__ __forceinline__ long long dbl_bits(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long b;
+    std::memcpy(&b, &x, 8);
+    return b;
+#endif
+}
+
+// static_cast<float>(x) (round to nearest even) by integer operations where the result is a normal
+// float, the conversion instruction otherwise (zero, subnormal results, overflow range, inf, NaN).
+__host__ __device__ __forceinline__ float f32_of_double(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(dbl_bits(x));
+    const int e = static_cast<int>((b >> 52) & 0x7ffu) - 1023;
+    if (e < -126 || e > 127) return static_cast<float>(x);
+    const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
+    const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29), rest = lo & 0x1fffffffu;
+    const uint32_t up = (rest > (1u << 28) || (rest == (1u << 28) && (m23 & 1u))) ? 1u : 0u;
+    return bits_f(((hi & 0x80000000u) | (static_cast<uint32_t>(e + 127) << 23) | m23) + up);
+}
+
+// x > c for a constant c >= +0 and x < c for a constant c > 0, on the bit patterns (false for NaN x, as
+// the floating-point comparison); whether x is +-0; whether x is finite
+__host__ __device__ __forceinline__ bool dbl_gt(double x, double c)
+{
+    const long long bx = dbl_bits(x);
+    return (bx & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll && bx > dbl_bits(c);
+}
+__host__ __device__ __forceinline__ bool dbl_lt(double x, double c)
+{
+    const long long bx = dbl_bits(x);
+    return (bx & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll && bx < dbl_bits(c);
+}
+__host__ __device__ __forceinline__ bool dbl_is_zero(double x)
+{
+    return (static_cast<unsigned long long>(dbl_bits(x)) << 1) == 0;
+}
+__host__ __device__ __forceinline__ bool dbl_finite(double x)
+{
+    return (dbl_bits(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
 // double-single value of a double (hi the nearest float, lo the nearest float to the rest)
 __host__ __device__ __forceinline__ ds ds_of_double(double x)
 {

@@ -21,6 +21,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "duwp_dsmath.cuh"
+
 namespace duwp {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -64,6 +66,9 @@ struct InstDev {
     double vhs_expo;        // 1 - 2 upsilon: exponent of c_r in the VHS acceptance test (Appendix A)
     float vhs_expo_f;
     float dtdx_f;
+    // single-precision copies for the estimates (each double-precision instruction, conversions
+    // included, holds an SM sub-partition for 64 cycles on this GPU)
+    float mu_ref_f, T_ref_f, omega_f, R_f, dt_f;
     int32_t resample_mode;  // 0: Maxwellian re-sampling, 1: with its Chapman-Enskog (NS) correction
     int32_t split_mode;     // 0: Eq. (p), 1: 1 - exp(-dt/tau) (quantified model competition)
     int32_t recon_mode;     // 0: first-order wave states, 1: van Leer limited reconstruction
@@ -224,10 +229,11 @@ __device__ __forceinline__ void draw(const InstDev &I, uint32_t id, uint32_t sub
 __device__ __forceinline__ uint32_t cell_id(const InstDev &I, int i) { return static_cast<uint32_t>(I.id0 + i + 1); }
 
 // Uniform in [0,1) with 53 random bits: 32 from the first word, 21 from the second.
+// (The exact value m 2^-53 is formed by integer operations, without the double-precision unit.)
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b)
 {
     const uint64_t m = (static_cast<uint64_t>(a) << 21) ^ static_cast<uint64_t>(b >> 11);
-    return static_cast<double>(m) * 0x1p-53;
+    return fixed_to_double(static_cast<int64_t>(m), 53);
 }
 
 // Index in [0, n) from a 32-bit word: the high half of the 64-bit product.
@@ -246,13 +252,13 @@ __device__ inline bool prim_from_cons(const double *psi, double inv_cv, double *
     const double rho = psi[0];
     q[0] = rho;
     q[1] = q[2] = q[3] = q[4] = 0.0;
-    if (!(rho > 0.0)) return false;
+    if (!dbl_gt(rho, 0.0)) return false;
     const double ir = 1.0 / rho;
     const double u = psi[1] * ir, v = psi[2] * ir, w = psi[3] * ir;
     const double e = psi[4] * ir - 0.5 * (u * u + v * v + w * w);
     const double T = e * inv_cv;
     q[1] = u; q[2] = v; q[3] = w; q[4] = T;
-    return (T > 0.0) && isfinite(T) && isfinite(u) && isfinite(v) && isfinite(w);
+    return dbl_gt(T, 0.0) && dbl_finite(T) && dbl_finite(u) && dbl_finite(v) && dbl_finite(w);
 }
 
 __device__ inline double viscosity(const InstDev &I, double T) { return I.mu_ref * pow(T / I.T_ref, I.omega); }
@@ -261,8 +267,8 @@ __device__ inline double viscosity(const InstDev &I, double T) { return I.mu_ref
 // change the decision dt <= tau.  Returns 0 when the estimate is not usable (over/underflow).
 __device__ __forceinline__ float tau_estimate(const InstDev &I, float rho, float T)
 {
-    const float mu = static_cast<float>(I.mu_ref) * powf(T / static_cast<float>(I.T_ref), static_cast<float>(I.omega));
-    const float tau = mu / (rho * static_cast<float>(I.R) * T);
+    const float mu = I.mu_ref_f * powf(T / I.T_ref_f, I.omega_f);
+    const float tau = mu / (rho * I.R_f * T);
     return (tau > 0.0f && tau < 1e30f) ? tau : 0.0f;
 }
 
@@ -277,8 +283,8 @@ __device__ inline double split_fraction(const InstDev &I, const double *q, bool 
         const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
         return -expm1(-(I.dt / tau));
     }
-    const float t32 = tau_estimate(I, static_cast<float>(q[0]), static_cast<float>(q[4]));
-    if (t32 > 1.01f * static_cast<float>(I.dt) && q[0] > 1e-30 && q[4] > 1e-30 && q[4] < 1e30) return 0.0;
+    const float t32 = tau_estimate(I, f32_of_double(q[0]), f32_of_double(q[4]));
+    if (t32 > 1.01f * I.dt_f && dbl_gt(q[0], 1e-30) && dbl_gt(q[4], 1e-30) && dbl_lt(q[4], 1e30)) return 0.0;
     const double tau = viscosity(I, q[4]) / (q[0] * I.R * q[4]);
     if (I.dt <= tau) return 0.0;
     return 1.0 - tau / I.dt;
@@ -289,7 +295,9 @@ __device__ inline int64_t resample_count(const InstDev &I, uint32_t id, uint32_t
 {
     uint32_t w[4];
     draw(I, id, 0u, step, kRound, w);
-    const double x = ((1.0 - P) * fmax(rho_w, 0.0)) * I.dx_over_mp;
+    // ((1 - P) max(rho_w, 0)) dx/m_p, with the factor 1 - P = 1 of P = 0 not multiplied (exact)
+    const double rw = dbl_gt(rho_w, 0.0) ? rho_w : 0.0;
+    const double x = (dbl_is_zero(P) ? rw : (1.0 - P) * rw) * I.dx_over_mp;
     return static_cast<int64_t>(floor(x + u53(w[0], w[1])));
 }
 
@@ -379,12 +387,12 @@ __device__ inline void recon_pair(const double *wm, bool okm, const double *w0, 
 __device__ inline bool flux_is_zero_estimate(const InstDev &I, const double *a, bool aok, const double *b, bool bok)
 {
     float r0 = 0.f, m0 = 0.f, my = 0.f, mz = 0.f, e0 = 0.f;
-    const float R = static_cast<float>(I.R);
+    const float R = I.R_f;
     for (int side = 0; side < 2; ++side) {
         const double *s = side ? b : a;
         if (!(side ? bok : aok)) continue;
-        const float rho = static_cast<float>(s[0]), U = static_cast<float>(s[1]), V = static_cast<float>(s[2]),
-                    W = static_cast<float>(s[3]), T = static_cast<float>(s[4]);
+        const float rho = f32_of_double(s[0]), U = f32_of_double(s[1]), V = f32_of_double(s[2]),
+                    W = f32_of_double(s[3]), T = f32_of_double(s[4]);
         const float lam = 1.0f / (2.0f * R * T);
         const float sl = sqrtf(lam);
         const float sg = side ? 1.0f : -1.0f;            // left: u > 0 half; right: u < 0 half
@@ -406,7 +414,7 @@ __device__ inline bool flux_is_zero_estimate(const InstDev &I, const double *a, 
     if (!(th > 1e-3f * (e0 / r0))) return false;
     const float T0 = th / (1.5f * R);
     const float t32 = tau_estimate(I, r0, T0);
-    return t32 > 1.05f * static_cast<float>(I.dt);
+    return t32 > 1.05f * I.dt_f;
 }
 
 // ga, gb: the cell states whose difference gives the NS gradients (a, b themselves unless a and b

@@ -393,9 +393,10 @@ __device__ inline int64_t ntc_candidates(const InstDev &I, uint32_t id, uint32_t
                                          double fmaj)
 {
     if (N < 2) return 0;
-    const double rr = (I.ntc_rate == 1) ? rho_t * I.inv_rho_ref : static_cast<double>(N) * I.ntc_rr;
-    const double nsel = I.ntc_A * rr * (static_cast<double>(N) - 1.0) * fmaj * cmax;
-    if (!(nsel < 1e8)) return -1;
+    // N and N - 1 converted by integer operations (exact)
+    const double rr = (I.ntc_rate == 1) ? rho_t * I.inv_rho_ref : fixed_to_double(N, 0) * I.ntc_rr;
+    const double nsel = I.ntc_A * rr * fixed_to_double(N - 1, 0) * fmaj * cmax;
+    if (!dbl_lt(nsel, 1e8)) return -1;
     uint32_t w[4];
     draw(I, id, 1u, step, kRound, w);
     return static_cast<int64_t>(floor(nsel + u53(w[0], w[1])));
@@ -2219,21 +2220,31 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                     double dp[5];
                     // the three runs' fixed-point sums added as integers and converted once (unless the
                     // sum would overflow)
-                    dp[0] = static_cast<double>(static_cast<int64_t>(hd.Rn + hd.Ln + farn) + aS[0]);
+                    // (conversions by integer operations; the far movers' sums added only where there
+                    // are any, the wave fluxes only where one is nonzero: x + 0 and x - 0 are x)
+                    dp[0] = fixed_to_double(static_cast<int64_t>(hd.Rn + hd.Ln + farn) + aS[0], 0);
                     for (int k = 0; k < 4; ++k) {
                         const int fr = (k == 3) ? 32 : 40;
                         long long s1, s2;
-                        if (add_no_overflow(aR[k], aL[k], s1) && add_no_overflow(s1, aS[k + 1], s2))
-                            dp[k + 1] = fixed_to_double(s2, fr) + fsum[k];
-                        else
+                        if (add_no_overflow(aR[k], aL[k], s1) && add_no_overflow(s1, aS[k + 1], s2)) {
+                            dp[k + 1] = fixed_to_double(s2, fr);
+                            if (farn > 0) dp[k + 1] = dp[k + 1] + fsum[k];
+                        } else {
                             dp[k + 1] = fixed_to_double(aR[k], fr) + fixed_to_double(aL[k], fr) + fsum[k] +
                                         fixed_to_double(aS[k + 1], fr);
+                        }
                     }
                     const double *Fl = E.flux + 5 * (g - 1), *Fr = E.flux + 5 * g;
+                    bool zero_flux = true;
+                    for (int k = 0; k < 5; ++k) zero_flux = zero_flux && dbl_is_zero(Fl[k]) && dbl_is_zero(Fr[k]);
                     for (int k = 0; k < 5; ++k) {
                         const double fp = I.mp_over_dx * dp[k];
-                        const double fw = I.dtdx * (Fr[k] - Fl[k]);
-                        psi[k] = psi[k] + fp - fw;
+                        if (zero_flux) {
+                            psi[k] = psi[k] + fp;
+                        } else {
+                            const double fw = I.dtdx * (Fr[k] - Fl[k]);
+                            psi[k] = psi[k] + fp - fw;
+                        }
                     }
                     if (static_cast<int64_t>(step_next) > static_cast<int64_t>(I.avg_start)) {
                         for (int k = 0; k < 5; ++k) E.avg[5 * g + k] += psi[k];
@@ -2247,9 +2258,9 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                 E.P[g] = P;
                 int64_t extra = 0;
                 if (ok) {
-                    if (P == 0.0) {
+                    if (dbl_is_zero(P)) {
                         extra = resample_count(I, cell_id(I, i), step_next, 0.0,
-                                               psi[0] - static_cast<double>(arrivals) * I.mp_over_dx);
+                                               psi[0] - fixed_to_double(arrivals, 0) * I.mp_over_dx);
                     } else {
                         extra = static_cast<int64_t>(floor(((1.0 - P) * fmax(psi[0], 0.0)) * I.dx_over_mp)) + 2;
                     }
@@ -2257,7 +2268,7 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
                 E.cnt[g] = arrivals;
                 myslots = arrivals + extra;
                 hd.n_in = arrivals;
-                if (P > 0.0) {
+                if (dbl_gt(P, 0.0)) {
                     hd.cls = kClsStaged;
                 } else {
                     const int64_t n_tot = arrivals + extra;

@@ -1,5 +1,8 @@
-// Host-side check of fixed_to_double (the integer-only conversion of the exact fixed-point sums):
-// for edge cases and random 64-bit values it must equal static_cast<double>(v) * 2^-frac.
+// Host-side check of the integer-only conversions and comparisons of the device code: fixed_to_double
+// (the exact fixed-point sums, the 53-bit uniforms, counts) must equal static_cast<double>(v) * 2^-frac
+// for edge cases and random 64-bit values; f32_of_double must equal static_cast<float> and
+// dbl_gt / dbl_lt / dbl_is_zero / dbl_finite the floating-point comparisons on random bit patterns,
+// specials and neighbours of the constants compared against.
 // Usage: fixed_to_double_check N -> prints "n mismatches"; exit status 1 on any mismatch.
 #include <cmath>
 #include <cstdio>
@@ -49,6 +52,43 @@ int main(int argc, char **argv)
         if (rng() & 1) v = -v;
         check(v, fracs[i % 3]);
     }
+    // double -> float and the comparisons, on random bit patterns of every exponent, ties, specials
+    auto checkf = [&](double x) {
+        const float want = static_cast<float>(x), got = f32_of_double(x);
+        ++tot;
+        if (std::memcmp(&want, &got, 4) != 0 && !(std::isnan(want) && std::isnan(got))) {
+            if (bad < 10) std::printf("f32 mismatch x=%.17g want=%.9g got=%.9g\n", x, want, got);
+            ++bad;
+        }
+        const double cs[4] = {0.0, 1e-30, 1e8, 1e30};
+        for (double c : cs) {
+            ++tot;
+            if (dbl_gt(x, c) != (x > c) || (c > 0.0 && dbl_lt(x, c) != (x < c))) {
+                if (bad < 10) std::printf("compare mismatch x=%.17g c=%g\n", x, c);
+                ++bad;
+            }
+        }
+        ++tot;
+        if (dbl_is_zero(x) != (x == 0.0) || dbl_finite(x) != static_cast<bool>(std::isfinite(x))) {
+            if (bad < 10) std::printf("zero/finite mismatch x=%.17g\n", x);
+            ++bad;
+        }
+    };
+    for (long i = 0; i < n; ++i) {
+        uint64_t b = rng();
+        if (i % 3 == 0) b = (b & 0x800fffffffffffffull) | (static_cast<uint64_t>(1023 - 130 + rng() % 262) << 52);
+        if (i % 7 == 0) b = (b & ~0x1fffffffull) | 0x10000000ull;                 // float rounding ties
+        if (i % 11 == 0) b |= 0x000fffffe0000000ull;                                 // carries
+        double x;
+        std::memcpy(&x, &b, 8);
+        checkf(x);
+    }
+    const double sp[] = {0.0, -0.0, 1e-30, 1e30, 1e8, std::nextafter(1e-30, 0.0), std::nextafter(1e-30, 1.0),
+                         std::nextafter(1e30, 0.0), std::nextafter(1e30, 2e30), std::nextafter(1e8, 0.0),
+                         std::nextafter(1e8, 2e8), HUGE_VAL, -HUGE_VAL, std::nan(""), -std::nan(""),
+                         3.4028235677973366e38, 3.4028235677973362e38, 1.1754943508222875e-38,
+                         1.1754942807573643e-38, 5e-324, -5e-324};
+    for (double x : sp) checkf(x);
     std::printf("%ld %ld\n", tot, bad);
     return bad ? 1 : 0;
 }
