@@ -57,6 +57,7 @@ struct Engine {
     int32_t groups = 2;         // streaming kernel: groups of 32 records per lane in flight (2 or 3)
     int32_t grid_collide = 0;   // collision kernel: persistent blocks
     int32_t grid_staged = 0;    // staged-cell kernel: persistent blocks
+    int32_t staged_wide = 0;    // staged-cell kernel at four blocks per SM (small pools)
     int32_t grid_sample = 0;    // drawing-ahead kernel: persistent blocks
     // one part of a split domain: the cells [part_c0, part_c1) of its single instance (part_c1 < 0:
     // not a part); pcap: slots reserved at the end of each particle buffer for the runs arriving in

@@ -1514,8 +1514,8 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
     }
 }
 
-template <typename Rec>
-__global__ void __launch_bounds__(kBlockThreads, 5) k_cellblock(const __grid_constant__ EngineDev E, int rp)
+template <typename Rec, int kMinB>
+__global__ void __launch_bounds__(kBlockThreads, kMinB) k_cellblock(const __grid_constant__ EngineDev E, int rp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     BlockShared<Rec> &S = *reinterpret_cast<BlockShared<Rec> *>(smraw);
@@ -2867,11 +2867,15 @@ size_t staged_smem_bytes(int fp32)
     return fp32 ? sizeof(BlockShared<RecF>) : sizeof(BlockShared<RecD>);
 }
 
-int staged_occupancy(int fp32)
+// The block kernel at five blocks per SM (96 registers) or, wide, four (128 registers, fewer spills).
+int staged_occupancy(int fp32, int wide)
 {
     const size_t smem = staged_smem_bytes(fp32);
-    return fp32 ? occupancy_of(k_cellblock<RecF>, kBlockThreads, smem, smem)
-                : occupancy_of(k_cellblock<RecD>, kBlockThreads, smem, smem);
+    if (wide)
+        return fp32 ? occupancy_of(k_cellblock<RecF, 4>, kBlockThreads, smem, smem)
+                    : occupancy_of(k_cellblock<RecD, 4>, kBlockThreads, smem, smem);
+    return fp32 ? occupancy_of(k_cellblock<RecF, 5>, kBlockThreads, smem, smem)
+                : occupancy_of(k_cellblock<RecD, 5>, kBlockThreads, smem, smem);
 }
 
 int sample_occupancy(int fp32)
@@ -2921,11 +2925,16 @@ cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaS
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
+cudaError_t launch_staged(const EngineDev &E, int fp32, int wide, int rp, int grid, cudaStream_t s, int prio)
 {
     const size_t smem = staged_smem_bytes(fp32);
-    cudaError_t e = fp32 ? launch_prio(k_cellblock<RecF>, grid, kBlockThreads, smem, s, prio, E, rp)
-                         : launch_prio(k_cellblock<RecD>, grid, kBlockThreads, smem, s, prio, E, rp);
+    cudaError_t e;
+    if (wide)
+        e = fp32 ? launch_prio(k_cellblock<RecF, 4>, grid, kBlockThreads, smem, s, prio, E, rp)
+                 : launch_prio(k_cellblock<RecD, 4>, grid, kBlockThreads, smem, s, prio, E, rp);
+    else
+        e = fp32 ? launch_prio(k_cellblock<RecF, 5>, grid, kBlockThreads, smem, s, prio, E, rp)
+                 : launch_prio(k_cellblock<RecD, 5>, grid, kBlockThreads, smem, s, prio, E, rp);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -14,8 +14,9 @@ namespace duwp {
 cudaError_t launch_collide(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
 // Staged-cell kernel of one step (cells with P > 0): absorption, re-sampling and collisions into the
 // staged list, one block per cell.  grid: persistent blocks (staged_occupancy() per SM).
-cudaError_t launch_staged(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
-int staged_occupancy(int fp32);
+// wide: the variant at four blocks per SM with more registers per thread (see staged_occupancy).
+cudaError_t launch_staged(const EngineDev &E, int fp32, int wide, int rp, int grid, cudaStream_t s, int prio);
+int staged_occupancy(int fp32, int wide);
 // Particles drawn ahead of the collision kernels (direct cells with many re-sampled particles), in
 // chunks over all warps: persistent blocks (sample_occupancy() per SM).
 cudaError_t launch_sample(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio);
