@@ -2309,8 +2309,10 @@ __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
 
 // ------------------------------------------------------------------------------------------
 // Offsets of the next step's output blocks, the collision kernel's work list, and the wave flux of
-// every interface.  At 64 registers (a full SM of warps): the double-precision flux, which spills
-// there, runs only where P_f > 0, and the offsets and lists before it are latency-bound.
+// every interface.  With 256-cell blocks (large pools) at 64 registers (a full SM of warps): the
+// double-precision flux, which spills there, runs only where P_f > 0, and the offsets and lists
+// before it are latency-bound.  Smaller blocks (small pools, one or two blocks per SM) take up to
+// 128 registers and keep the flux's double-precision chain out of local memory.
 // ------------------------------------------------------------------------------------------
 // Whether a cell's collisions are long dependency chains, which the block kernel runs in parallel
 // rounds: at least kHeavyCandidates NTC candidates (Appendix A) on a list that fits the block's
@@ -2433,7 +2435,7 @@ __device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int ad
 }
 
 template <int B>
-__global__ void __launch_bounds__(B, 1024 / B) k_offsets_flux(EngineDev E, int wp, int advance)
+__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets_flux(EngineDev E, int wp, int advance)
 {
     __shared__ int64_t s_w[B / 32];
     __shared__ int64_t s_pre;
