@@ -124,12 +124,16 @@ int derive_instance(const duwp_params &p, HostInst &o)
         double *q = s ? d.right : d.left;
         q[0] = st[s]->rho; q[1] = st[s]->u; q[2] = st[s]->v; q[3] = st[s]->w; q[4] = st[s]->T;
     }
-    // particles expected from the initial mass
-    double mass = 0.0;
-    for (int32_t i = 0; i < p.n_cells; ++i) {
-        const double xc = p.x_min + (static_cast<double>(i) + 0.5) * d.dx;
-        mass += (xc < p.x_split ? p.left.rho : p.right.rho) * d.dx;
+    // particles expected from the initial mass (a capacity estimate): the cells whose centre lies
+    // left of x_split are a prefix, found by bisection with the same test as the cell set-up
+    int32_t lo = 0, hi = p.n_cells;
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo) / 2;
+        const double xc = p.x_min + (static_cast<double>(mid) + 0.5) * d.dx;
+        if (xc < p.x_split) lo = mid + 1;
+        else hi = mid;
     }
+    const double mass = (static_cast<double>(lo) * p.left.rho + static_cast<double>(p.n_cells - lo) * p.right.rho) * d.dx;
     o.est_particles = static_cast<int64_t>(std::ceil(mass / d.mp));
     o.active = true;
     return DUWP_OK;
@@ -433,10 +437,21 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
         DUWP_CU(cudaMemcpyAsync(dev.inst, table.data(), sizeof(InstDev) * static_cast<size_t>(n), cudaMemcpyHostToDevice,
                                 stream));
         DUWP_CU(cudaStreamSynchronize(stream));
+        // every instance's cells in one launch per kInitBatch instances
+        std::vector<InitCellsItem> items(static_cast<size_t>(n));
         for (int32_t b = 0; b < n; ++b) {
-            rc = init_instance_cells(b);
-            if (rc != DUWP_OK) return rc;
+            const duwp_params &p = inst[b].p;
+            InitCellsItem &q = items[static_cast<size_t>(b)];
+            cons_of(p.left, p.R, q.lc);
+            cons_of(p.right, p.R, q.rc);
+            q.x_min = p.x_min;
+            q.x_split = p.x_split;
+            q.b = b;
+            q.g0 = inst[b].cell_base;
+            q.n = p.n_cells + 2;
+            q.pad = 0;
         }
+        DUWP_CU(launch_init_cells_batch(dev, items.data(), n, stream));
     }
     rc = enqueue_prepare();
     if (rc != DUWP_OK) return rc;

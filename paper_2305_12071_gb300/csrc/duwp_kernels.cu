@@ -2689,12 +2689,11 @@ __global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets_f
 // ------------------------------------------------------------------------------------------
 // Initial cells of one instance: all wave (Psi_p = 0), Psi_t from the two-state profile.
 // ------------------------------------------------------------------------------------------
-__global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, double l1, double l2, double l3, double l4,
-                             double r0, double r1, double r2, double r3, double r4, double x_min, double x_split)
+// Initial state of cell g = g0 + t of instance b (all wave, no particles; the left or right state by
+// the cell centre's side of x_split).
+__device__ __forceinline__ void init_cell(const EngineDev &E, int b, int g, const double *lc, const double *rc,
+                                          double x_min, double x_split)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int g = g0 + t;
     const InstDev &I = E.inst[b];
     E.cell_inst[g] = b;
     const int i = g - I.cell_base - 1;
@@ -2705,11 +2704,34 @@ __global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, doubl
     if (i < 0 || i >= I.C) return;
     const double xc = x_min + (static_cast<double>(I.id0 + i) + 0.5) * I.dx;
     const bool left = xc < x_split;
-    const double c[5] = {left ? l0 : r0, left ? l1 : r1, left ? l2 : r2, left ? l3 : r3, left ? l4 : r4};
-    for (int k = 0; k < 5; ++k) E.psi[5 * g + k] = c[k];
+    for (int k = 0; k < 5; ++k) E.psi[5 * g + k] = left ? lc[k] : rc[k];
     const double T = left ? I.left[4] : I.right[4];
     E.cmax[g] = 5.0 * sqrt(2.0 * I.R * T);
     E.fmaj[g] = majorant_factor(I, E.cmax[g]);
+}
+
+__global__ void k_init_cells(EngineDev E, int b, int g0, int n, double l0, double l1, double l2, double l3, double l4,
+                             double r0, double r1, double r2, double r3, double r4, double x_min, double x_split)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double lc[5] = {l0, l1, l2, l3, l4}, rc[5] = {r0, r1, r2, r3, r4};
+    init_cell(E, b, g0 + t, lc, rc, x_min, x_split);
+}
+
+struct InitCellsBatch {
+    InitCellsItem it[kInitBatch];
+};
+
+// blockIdx.y: the item (instance); blockIdx.x: cells of that instance
+__global__ void k_init_cells_batch(EngineDev E, const __grid_constant__ InitCellsBatch B, int n_items)
+{
+    const int j = blockIdx.y;
+    if (j >= n_items) return;
+    const InitCellsItem &q = B.it[j];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= q.n) return;
+    init_cell(E, q.b, q.g0 + t, q.lc, q.rc, q.x_min, q.x_split);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -3171,6 +3193,25 @@ cudaError_t launch_init_turn(cudaStream_t s)
 {
     k_init_turn<<<1, (kTurnTable > kLogTable ? kTurnTable : kLogTable), 0, s>>>();
     return cudaGetLastError();
+}
+
+cudaError_t launch_init_cells_batch(const EngineDev &E, const InitCellsItem *items, int n_items, cudaStream_t s)
+{
+    for (int j0 = 0; j0 < n_items; j0 += kInitBatch) {
+        const int m = std::min(kInitBatch, n_items - j0);
+        InitCellsBatch B;
+        int max_n = 0;
+        for (int j = 0; j < m; ++j) {
+            B.it[j] = items[j0 + j];
+            max_n = std::max(max_n, items[j0 + j].n);
+        }
+        if (max_n <= 0) continue;
+        const dim3 grid((max_n + 255) / 256, m);
+        k_init_cells_batch<<<grid, 256, 0, s>>>(E, B, m);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const double *lc, const double *rc, double x_min,

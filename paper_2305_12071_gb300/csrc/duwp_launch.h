@@ -38,6 +38,14 @@ cudaError_t launch_init_turn(cudaStream_t s);
 // Initial state of the cells [g0, g0 + n) of instance b (all wave, no particles).
 cudaError_t launch_init_cells(const EngineDev &E, int b, int g0, int n, const double *left_cons,
                               const double *right_cons, double x_min, double x_split, cudaStream_t s);
+// The same for many instances in one launch (items by value in the kernel's parameters, at most
+// kInitBatch per launch): a batch of instances is set up without a launch per instance.
+struct InitCellsItem {
+    double lc[5], rc[5], x_min, x_split;
+    int32_t b, g0, n, pad;
+};
+constexpr int kInitBatch = 64;
+cudaError_t launch_init_cells_batch(const EngineDev &E, const InitCellsItem *items, int n_items, cudaStream_t s);
 // Profiles (rho, u, T, wave fraction) of every instance into d_out = [4 x total], instance b at
 // d_base[b] (device array of n_inst entries, < 0: skip).
 cudaError_t launch_moments(const EngineDev &E, int which, const int64_t *d_base, int64_t total, double *d_out,
