@@ -66,6 +66,27 @@ def test_dense_shock_block_kernel_hashed(precision):
         _run_pair(p, [1, 3], REL32, REL64)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_staged_rounds_with_cmax_raises(precision):
+    # a Mach-8 shock at small Kn: every cell absorbs (P > 0, staged lists collided in dependency
+    # rounds on one warp), and hot particles meeting cold cells raise c_max inside a batch (the
+    # oracle finds such raises in light staged cells over these steps), so the rerun of a batch up
+    # to its raising candidate is exercised
+    p = W.shock(8.0, omega=0.81, n_cells=80, ppc_ref=60.0, precision=precision, seed=3)
+    p["Kn"] = 0.01
+    o = O.Oracle(p)
+    raised = 0
+    for _ in range(10):
+        cm0, P = o.cmax().copy(), o.prim()["P"].copy()
+        o.step(1)
+        raised += int(((o.cmax() > cm0) & (P > 0) & (o.counters()["ncand"] < 96)).sum())
+    assert raised > 0
+    if precision == "fp64":
+        _run_pair(p, [1, 4, 10], REL64, REL64)
+    else:
+        _run_pair(p, [1, 3, 5], REL32, REL64)
+
+
 def test_sod_wave_regime_fp32():
     p = W.sod(n_cells=120, Kn=3e-4, ppc_ref=150, precision="fp32", seed=8)
     _run_pair(p, [1, 5], REL32, REL64)
