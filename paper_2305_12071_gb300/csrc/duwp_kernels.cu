@@ -48,6 +48,12 @@ __global__ void k_init_turn()
     }
 }
 
+// Programmatic dependent launch: the step's kernels are launched with programmatic stream
+// serialization, so that a kernel's blocks are scheduled while its predecessor's last blocks finish;
+// every step kernel first waits here until the predecessor grid has completed and its memory is
+// visible (a no-op where the launch had no programmatic dependency).
+__device__ __forceinline__ void wait_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void set_err(int32_t *err, int code) { atomicCAS(err, 0, code); }
 
 // ------------------------------------------------------------------------------------------
@@ -1673,6 +1679,7 @@ __device__ void block_cell(const EngineDev &E, int g, BlockShared<Rec> &S, Rec *
 template <typename Rec, int kMinB>
 __global__ void __launch_bounds__(kBlockThreads, kMinB) k_cellblock(const __grid_constant__ EngineDev E, int rp)
 {
+    wait_predecessor();
     extern __shared__ __align__(16) unsigned char smraw[];
     BlockShared<Rec> &S = *reinterpret_cast<BlockShared<Rec> *>(smraw);
     Rec *in = static_cast<Rec *>(E.buf[rp]);
@@ -1734,6 +1741,7 @@ __device__ __forceinline__ int pack_rounds(const EngineDev &E, int grp, int lane
 template <typename Rec>
 __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_constant__ EngineDev E, int rp)
 {
+    wait_predecessor();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kW = kSampleThreads / 32;
     const int n_groups = (E.G_run + 31) / 32;
@@ -1789,6 +1797,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_const
 template <typename Rec>
 __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_constant__ EngineDev E, int rp)
 {
+    wait_predecessor();
     extern __shared__ __align__(16) unsigned char smraw[];
     CollideShared<Rec> &S = reinterpret_cast<CollideShared<Rec> *>(smraw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -2096,6 +2105,7 @@ __device__ __forceinline__ void stream_cell_empty(const EngineDev &E, int g, int
 template <typename Rec, int kMinBlocks, int kStreamGroups>
 __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
 {
+    wait_predecessor();
     using T = decltype(Rec().xl);
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2265,6 +2275,7 @@ __global__ void __launch_bounds__(512, kMinBlocks) k_stream(EngineDev E, int rp)
 template <typename Rec>
 __global__ void k_far_sort(EngineDev E)
 {
+    wait_predecessor();
     const FarItem<Rec> *a = static_cast<const FarItem<Rec> *>(E.far_app);
     FarItem<Rec> *s = static_cast<FarItem<Rec> *>(E.far_sorted);
     int n = *(volatile int32_t *)&E.far_count[0];
@@ -2297,6 +2308,7 @@ __device__ __forceinline__ bool add_no_overflow(long long a, long long b, long l
 template <typename Rec, int B>
 __global__ void __launch_bounds__(B) k_cells(EngineDev E, int q, int update)
 {
+    wait_predecessor();
     __shared__ int64_t s_w[B / 32];
     const int g = blockIdx.x * B + threadIdx.x;
     int64_t myslots = 0;
@@ -2593,6 +2605,7 @@ __device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int ad
 template <int B>
 __global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets_flux(EngineDev E, int wp, int advance)
 {
+    wait_predecessor();
     __shared__ int64_t s_w[B / 32];
     __shared__ int64_t s_pre;
     const int g = blockIdx.x * B + threadIdx.x;
@@ -3071,7 +3084,8 @@ int collide_occupancy(int fp32)
 }
 
 namespace {
-// Launch with a scheduling priority (blocks of higher-priority launches are dispatched first).
+// Launch with a scheduling priority (blocks of higher-priority launches are dispatched first) and
+// programmatic stream serialization (see wait_predecessor).
 template <typename... Args>
 cudaError_t launch_prio(void (*kernel)(Args...), int grid, int threads, size_t smem, cudaStream_t s, int prio,
                         Args... args)
@@ -3081,15 +3095,34 @@ cudaError_t launch_prio(void (*kernel)(Args...), int grid, int threads, size_t s
     cfg.blockDim = dim3(static_cast<unsigned>(threads));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributePriority;
     attr[0].val.priority = prio;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 }  // namespace
 
+
+// Launch with programmatic stream serialization (see wait_predecessor).
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, int threads, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 cudaError_t launch_sample(const EngineDev &E, int fp32, int rp, int grid, cudaStream_t s, int prio)
 {
     const cudaError_t e = fp32 ? launch_prio(k_sample<RecF>, grid, kSampleThreads, 0, s, prio, E, rp)
@@ -3132,8 +3165,8 @@ cudaError_t launch_stream(const EngineDev &E, int fp32, int variant, int groups,
 cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s)
 {
     const int grid = (E.far_cap + 255) / 256;
-    if (fp32) k_far_sort<RecF><<<grid, 256, 0, s>>>(E);
-    else k_far_sort<RecD><<<grid, 256, 0, s>>>(E);
+    if (fp32) launch_pdl(k_far_sort<RecF>, dim3(grid), 256, s, E);
+    else launch_pdl(k_far_sort<RecD>, dim3(grid), 256, s, E);
     return cudaGetLastError();
 }
 
@@ -3150,10 +3183,10 @@ static int cell_block(int cells, int nsm)
 template <typename Rec>
 static cudaError_t launch_cells_b(const EngineDev &E, int b, int grid, int q, int update, cudaStream_t s)
 {
-    if (b == 32) k_cells<Rec, 32><<<grid, 32, 0, s>>>(E, q, update);
-    else if (b == 64) k_cells<Rec, 64><<<grid, 64, 0, s>>>(E, q, update);
-    else if (b == 128) k_cells<Rec, 128><<<grid, 128, 0, s>>>(E, q, update);
-    else k_cells<Rec, kCellBlock><<<grid, kCellBlock, 0, s>>>(E, q, update);
+    if (b == 32) launch_pdl(k_cells<Rec, 32>, dim3(grid), 32, s, E, q, update);
+    else if (b == 64) launch_pdl(k_cells<Rec, 64>, dim3(grid), 64, s, E, q, update);
+    else if (b == 128) launch_pdl(k_cells<Rec, 128>, dim3(grid), 128, s, E, q, update);
+    else launch_pdl(k_cells<Rec, kCellBlock>, dim3(grid), kCellBlock, s, E, q, update);
     return cudaGetLastError();
 }
 
@@ -3168,10 +3201,10 @@ cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStr
 {
     const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
     const int grid = (E.G_run + b - 1) / b;
-    if (b == 32) k_offsets_flux<32><<<grid, 32, 0, s>>>(E, wp, advance);
-    else if (b == 64) k_offsets_flux<64><<<grid, 64, 0, s>>>(E, wp, advance);
-    else if (b == 128) k_offsets_flux<128><<<grid, 128, 0, s>>>(E, wp, advance);
-    else k_offsets_flux<kCellBlock><<<grid, kCellBlock, 0, s>>>(E, wp, advance);
+    if (b == 32) launch_pdl(k_offsets_flux<32>, dim3(grid), 32, s, E, wp, advance);
+    else if (b == 64) launch_pdl(k_offsets_flux<64>, dim3(grid), 64, s, E, wp, advance);
+    else if (b == 128) launch_pdl(k_offsets_flux<128>, dim3(grid), 128, s, E, wp, advance);
+    else launch_pdl(k_offsets_flux<kCellBlock>, dim3(grid), kCellBlock, s, E, wp, advance);
     return cudaGetLastError();
 }
 
