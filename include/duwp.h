@@ -174,7 +174,8 @@ int duwp_sync(duwp_handle *h);
  * receives the summed device time of [0] the collision kernel (collisions of the cells with
  * P = 0 and the re-sampled particles of the cells without collisions), [1] the streaming kernel
  * (transport and sorted runs of every particle), [2] the far-mover sort, [3] the cell update,
- * [4] the offset/flux kernel and [6] the kernels ahead of the collision kernel (the
+ * [4] the offset kernel and the wave-flux kernel (run at the start of the step that applies the
+ * flux, beside the particle kernels in duwp_step) and [6] the kernels ahead of the collision kernel (the
  * re-sampled particles of cells with many of them, then absorption, re-sampling and collisions of
  * the cells with many collision candidates), and in [5] the device time from the first launch to
  * the end of the last; host_step_ms (n_steps entries, may be NULL) the device time of each step.

@@ -200,6 +200,10 @@ Engine::~Engine()
     if (side2) cudaStreamSynchronize(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join2) cudaEventDestroy(ev_join2);
+    if (side3) cudaStreamSynchronize(side3);
+    if (ev_fork3) cudaEventDestroy(ev_fork3);
+    if (ev_join3) cudaEventDestroy(ev_join3);
+    if (side3) cudaStreamDestroy(side3);
     if (side2) cudaStreamDestroy(side2);
     for (int k = 0; k < 2; ++k) {
         if (mom_ready[k]) cudaEventDestroy(mom_ready[k]);
@@ -278,6 +282,9 @@ int Engine::create(const duwp_params *params, int32_t n, int32_t pool_cells, int
     DUWP_CU(cudaStreamCreateWithFlags(&side2, cudaStreamNonBlocking));
     DUWP_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     DUWP_CU(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
+    DUWP_CU(cudaStreamCreateWithFlags(&side3, cudaStreamNonBlocking));
+    DUWP_CU(cudaEventCreateWithFlags(&ev_fork3, cudaEventDisableTiming));
+    DUWP_CU(cudaEventCreateWithFlags(&ev_join3, cudaEventDisableTiming));
     std::vector<HostInst> hs(static_cast<size_t>(n));
     int64_t est = 0;
     int64_t cells = 0;
@@ -508,11 +515,11 @@ int Engine::set_run_extent(int32_t cells)
 
 int Engine::enqueue_prepare()
 {
-    // Recompute the primitive state, P, slot bounds, offsets and flux of every cell from the
-    // current state without advancing: idempotent for instances already running (same inputs and
-    // draws), and the start of a newly added one.
+    // Recompute the primitive state, P, slot bounds and offsets of every cell from the current state
+    // without advancing: idempotent for instances already running (same inputs and draws), and the
+    // start of a newly added one.  (The wave flux is formed at the start of the next step.)
     DUWP_CU(launch_cells(dev, fp32, parity, 0, stream));
-    DUWP_CU(launch_offsets_flux(dev, 1 - parity, 0, stream));
+    DUWP_CU(launch_offsets(dev, 1 - parity, 0, stream));
     return DUWP_OK;
 }
 
@@ -520,6 +527,12 @@ int Engine::enqueue_phase(int ph)
 {
     const int rp = parity;
     if (ph == 1) {
+        // the wave flux of the states of the last cell kernel, on a third stream beside the
+        // particle kernels; the cell kernel of phase 2 waits for it
+        DUWP_CU(cudaEventRecord(ev_fork3, stream));
+        DUWP_CU(cudaStreamWaitEvent(side3, ev_fork3, 0));
+        DUWP_CU(launch_flux(dev, side3, prio_hi));
+        DUWP_CU(cudaEventRecord(ev_join3, side3));
         // the light cells' rounds and the particles drawn ahead (cells with many to draw), then the
         // block kernel (cells with many candidates) and the collision kernel (the other cells that
         // need one) side by side, then every cell streams in one launch.  (Streaming the cells that
@@ -535,9 +548,10 @@ int Engine::enqueue_phase(int ph)
         DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, prio_hi));
     } else if (ph == 2) {
         DUWP_CU(launch_far_sort(dev, fp32, stream));
+        DUWP_CU(cudaStreamWaitEvent(stream, ev_join3, 0));
         DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
     } else {
-        DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+        DUWP_CU(launch_offsets(dev, rp, 1, stream));
         parity = 1 - rp;
     }
     return DUWP_OK;
@@ -554,7 +568,9 @@ int Engine::enqueue_step(cudaEvent_t *ev)
         return DUWP_OK;
     }
     {
-        // timed: one kernel after the other, events around each
+        // timed: one kernel after the other, events around each (ev[7]: before the wave flux)
+        DUWP_CU(cudaEventRecord(ev[7], stream));
+        DUWP_CU(launch_flux(dev, stream, prio_hi));
         DUWP_CU(cudaEventRecord(ev[6], stream));
         DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
         DUWP_CU(launch_staged(dev, fp32, staged_wide, rp, grid_staged, stream, prio_hi));
@@ -568,7 +584,7 @@ int Engine::enqueue_step(cudaEvent_t *ev)
     DUWP_CU(cudaEventRecord(ev[3], stream));
     DUWP_CU(launch_cells(dev, fp32, 1 - rp, 1, stream));
     DUWP_CU(cudaEventRecord(ev[4], stream));
-    DUWP_CU(launch_offsets_flux(dev, rp, 1, stream));
+    DUWP_CU(launch_offsets(dev, rp, 1, stream));
     DUWP_CU(cudaEventRecord(ev[5], stream));
     parity = 1 - rp;
     return DUWP_OK;
@@ -705,10 +721,10 @@ int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_m
     if (rc == DUWP_OK) rc = E.sync();
     for (int k = 0; k < DUWP_TIMED_SLOTS; ++k) kernel_ms[k] = 0.0;
     if (rc == DUWP_OK) {
-        // per step: e[6] before the staged-cell kernel, e[0] before the collision kernel, e[1..5]
-        // after the collision, streaming, far-sort, cell and offset kernels
+        // per step: e[7] before the wave flux, e[6] before the staged-cell kernel, e[0] before the
+        // collision kernel, e[1..5] after the collision, streaming, far-sort, cell and offset kernels
         float span = 0.f;
-        cudaEventElapsedTime(&span, ev[6], ev[kEv * static_cast<size_t>(n - 1) + 5]);
+        cudaEventElapsedTime(&span, ev[7], ev[kEv * static_cast<size_t>(n - 1) + 5]);
         kernel_ms[5] = span;
         for (int32_t s = 0; s < n; ++s) {
             cudaEvent_t *e = ev.data() + kEv * static_cast<size_t>(s);
@@ -720,8 +736,10 @@ int duwp_step_timed(duwp_handle *h, int32_t n, double *kernel_ms, double *step_m
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e[6], e[0]);
             kernel_ms[6] += ms;
+            cudaEventElapsedTime(&ms, e[7], e[6]);     // the wave flux, with the offsets in [4]
+            kernel_ms[4] += ms;
             if (step_ms) {
-                cudaEventElapsedTime(&ms, e[6], e[5]);
+                cudaEventElapsedTime(&ms, e[7], e[5]);
                 step_ms[s] = ms;
             }
         }

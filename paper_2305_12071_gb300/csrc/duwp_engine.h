@@ -17,7 +17,7 @@ void set_cuda_error(cudaError_t e, const char *where);
 
 // Events recorded by a timed step: after the staged-cell kernel (before the collision kernel), after
 // each of the five other kernels, and (last) before the staged-cell kernel.
-constexpr int kStepEvents = 7;
+constexpr int kStepEvents = 8;
 
 struct HostInst {
     duwp_params p;
@@ -80,6 +80,8 @@ struct Engine {
     // other cells) on a stream of its own, forked from and joined into the step's stream
     cudaStream_t side2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join2 = nullptr;
+    cudaStream_t side3 = nullptr;                        // the wave flux beside a step's particle kernels
+    cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
     int prio_hi = 0, prio_lo = 0;
 
     // device scratch of the profile reads (allocated on first use): the table of instance bases

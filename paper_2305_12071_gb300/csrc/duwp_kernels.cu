@@ -11,7 +11,9 @@
 //   k_cells       (per cell): conservative update Eq. (r1), time average, primitive state, P, the
 //                 slot bound and the plan (counts, class) of the next step.
 //   k_offsets     (per cell): output block offsets of the next step (scan of the slot bounds), the
-//                 work list of the collision kernel, and the wave flux at every interface.
+//                 work lists of the collision kernels.
+//   k_flux        (per interface): the wave flux from the cell kernel's states, at the start of the
+//                 step that applies it, beside that step's particle kernels.
 #include <algorithm>
 #include <type_traits>
 #include <cstdio>
@@ -2523,7 +2525,7 @@ __device__ __forceinline__ void append_chunks(const EngineDev &E, int2 *list, in
 
 // Wave flux of the interface after cell g (between local cells i and i+1; -1: the left end), and
 // the instance's step counter advanced once per step.
-__device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int advance)
+__device__ __forceinline__ void interface_flux(const EngineDev &E, int g)
 {
     if (g >= E.G_run) return;
     const int b = E.cell_inst[g];
@@ -2595,15 +2597,24 @@ __device__ __forceinline__ void interface_flux(const EngineDev &E, int g, int ad
     } else {
         wave_flux(I, a, aok, c, cok, E.flux + 5 * g, a, c);
     }
-    if (advance && i == -1) {
-        const uint32_t nxt = I.step + 1u;
-        if (static_cast<int64_t>(nxt) > static_cast<int64_t>(I.avg_start)) I.navg += 1;
-        I.step = nxt;
-    }
+}
+
+// End of a step: the instance's step counter (and the count of averaged states) advance, once per
+// instance (by the thread of its left reservoir cell).
+__device__ __forceinline__ void step_advance(const EngineDev &E, int g)
+{
+    if (g >= E.G_run) return;
+    const int b = E.cell_inst[g];
+    if (b < 0) return;
+    InstDev &I = E.inst[b];
+    if (g - I.cell_base - 1 != -1) return;
+    const uint32_t nxt = I.step + 1u;
+    if (static_cast<int64_t>(nxt) > static_cast<int64_t>(I.avg_start)) I.navg += 1;
+    I.step = nxt;
 }
 
 template <int B>
-__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets_flux(EngineDev E, int wp, int advance)
+__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets(EngineDev E, int wp, int advance)
 {
     wait_predecessor();
     __shared__ int64_t s_w[B / 32];
@@ -2691,12 +2702,22 @@ __global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets_f
         E.ticket[kPreCtr] = 0;
         E.ticket[kRoundCtr] = 0;
     }
-    interface_flux(E, g, advance);
+    if (advance) step_advance(E, g);
     // this warp's light cells (consecutive in the light list), packed into rounds by k_sample
     {
         const unsigned lm = __ballot_sync(0xffffffffu, listed && lq == kLightList);
         if (lane == 0 && g < E.G) E.wgrp[g >> 5] = make_int2(lm ? light_base : 0, __popc(lm));
     }
+}
+
+// Wave flux at every interface (Sec. 3.3) from the primitive states of the cell kernel: run at the
+// start of the step that applies it (by the cell kernel), on a side stream beside that step's
+// collision and streaming kernels, which neither read the flux nor write the states it reads.
+template <int B>
+__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_flux(EngineDev E)
+{
+    wait_predecessor();
+    interface_flux(E, blockIdx.x * B + threadIdx.x);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -3197,15 +3218,27 @@ cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaSt
     return fp32 ? launch_cells_b<RecF>(E, b, grid, q, update, s) : launch_cells_b<RecD>(E, b, grid, q, update, s);
 }
 
-cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStream_t s)
+cudaError_t launch_offsets(const EngineDev &E, int wp, int advance, cudaStream_t s)
 {
     const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
     const int grid = (E.G_run + b - 1) / b;
-    if (b == 32) launch_pdl(k_offsets_flux<32>, dim3(grid), 32, s, E, wp, advance);
-    else if (b == 64) launch_pdl(k_offsets_flux<64>, dim3(grid), 64, s, E, wp, advance);
-    else if (b == 128) launch_pdl(k_offsets_flux<128>, dim3(grid), 128, s, E, wp, advance);
-    else launch_pdl(k_offsets_flux<kCellBlock>, dim3(grid), kCellBlock, s, E, wp, advance);
+    if (b == 32) launch_pdl(k_offsets<32>, dim3(grid), 32, s, E, wp, advance);
+    else if (b == 64) launch_pdl(k_offsets<64>, dim3(grid), 64, s, E, wp, advance);
+    else if (b == 128) launch_pdl(k_offsets<128>, dim3(grid), 128, s, E, wp, advance);
+    else launch_pdl(k_offsets<kCellBlock>, dim3(grid), kCellBlock, s, E, wp, advance);
     return cudaGetLastError();
+}
+
+cudaError_t launch_flux(const EngineDev &E, cudaStream_t s, int prio)
+{
+    const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
+    const int grid = (E.G_run + b - 1) / b;
+    cudaError_t e;
+    if (b == 32) e = launch_prio(k_flux<32>, grid, 32, 0, s, prio, E);
+    else if (b == 64) e = launch_prio(k_flux<64>, grid, 64, 0, s, prio, E);
+    else if (b == 128) e = launch_prio(k_flux<128>, grid, 128, 0, s, prio, E);
+    else e = launch_prio(k_flux<kCellBlock>, grid, kCellBlock, 0, s, prio, E);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_stress_heat(const EngineDev &E, int fp32, int rp, int g0, int ncell, int accumulate, double *out,

@@ -30,9 +30,11 @@ cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s);
 // primitive state, P and the slot bound of the next step (draws keyed with step index
 // inst.step + (update ? 1 : 0)).  q = parity of the runs just written.
 cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaStream_t s);
-// Offsets of the next step's output blocks (write parity wp) and the wave flux at every
-// interface; advance = 1 also advances the per-instance step counters.
-cudaError_t launch_offsets_flux(const EngineDev &E, int wp, int advance, cudaStream_t s);
+// Offsets of the next step's output blocks (write parity wp) and the collision work lists;
+// advance = 1 also advances the per-instance step counters.
+cudaError_t launch_offsets(const EngineDev &E, int wp, int advance, cudaStream_t s);
+// Wave flux at every interface from the current primitive states (read by the next cell kernel).
+cudaError_t launch_flux(const EngineDev &E, cudaStream_t s, int prio);
 // Turn table of the double-single scattering (idempotent; once per engine).
 cudaError_t launch_init_turn(cudaStream_t s);
 // Initial state of the cells [g0, g0 + n) of instance b (all wave, no particles).
