@@ -1781,7 +1781,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(const __grid_const
         const CellHdr &h = E.hdr[g];
         const int b = h.b, n_in = h.n_in, n_new = h.n_new, cls = h.cls, i = h.i;
         const long long off = h.off;
-        if (cls != kClsDirect) continue;
+        if (cls != kClsDirect && cls != kClsStream) continue;
         const InstDev &I = E.inst[b];
         const int j1 = min(j0 + kSampleChunk, n_new);
         if (I.resample_mode == 1) {
@@ -2666,12 +2666,16 @@ __global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets(E
                 if (nc >= kHeavyCandidates) lq = kHeavyList;
                 else if (light_resampling(E.hdr[g]) && nc <= kMaxDirect) lq = kLightList;
             }
-            if (cls == kClsStream || cls == kClsReservoir) chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-            if (cls == kClsDirect && E.hdr[g].n_new >= kPreSampleMin) {
-                // many particles to draw before the collisions (all of them in a first step): drawn
-                // ahead over the whole GPU instead of by the one warp or block that collides the cell
+            const bool many = E.hdr[g].n_new >= kPreSampleMin;
+            // the few re-sampled particles of cells without collisions, and every reservoir's, are
+            // drawn in the collision kernel's tail (beside the collisions)
+            if (cls == kClsReservoir || (cls == kClsStream && !many))
+                chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
+            if ((cls == kClsDirect || cls == kClsStream) && many) {
+                // many particles to draw (all of them in a first step): drawn ahead over the whole
+                // GPU instead of by the one warp or block that collides the cell
                 pchunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-                E.hdr[g].edges |= kEdgePresampled;
+                if (cls == kClsDirect) E.hdr[g].edges |= kEdgePresampled;
             }
         }
     }
