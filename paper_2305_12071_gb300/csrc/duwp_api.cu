@@ -629,6 +629,9 @@ int Engine::step(int32_t n)
 int Engine::sync()
 {
     if (cstream) DUWP_CU(cudaStreamSynchronize(cstream));
+    // (the flux stream's work is joined into the step's stream before the cell kernel; synchronized
+    // here too for a sequence of phases cut short by an error)
+    if (side3) DUWP_CU(cudaStreamSynchronize(side3));
     DUWP_CU(cudaStreamSynchronize(stream));
     int32_t e = 0;
     DUWP_CU(cudaMemcpy(&e, dev.err, sizeof e, cudaMemcpyDeviceToHost));
