@@ -1274,7 +1274,7 @@ struct BlockShared {
     CeCell ce;
     int ce_on;
     int wsum[kAbsorbPer][kBlockThreads / 32];
-    int item, nn, nc, ok, rmin, nready;
+    int item, nn, nc, ok, rmin, nready[2];     // nready: the round's list length, by round parity
     double cm_new;
 };
 
@@ -1386,9 +1386,9 @@ __device__ void block_rounds(const InstDev &I, BlockShared<Rec> &S, int live_end
     bool undone[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) undone[u] = t + u * kBlockThreads < live_end;
-    int remaining = live_end;
-    for (unsigned round = 1; round <= kWindow + 1 && remaining > 0; ++round) {
-        if (t == 0) S.nready = 0;
+    // each round: the ready check of the claims made before it, a barrier, then the runs beside
+    // the claims of the next round (the runs touch the records, the claims only own), a barrier
+    auto claim = [&](unsigned round) {
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const int c = t + u * kBlockThreads;
@@ -1398,7 +1398,16 @@ __device__ void block_rounds(const InstDev &I, BlockShared<Rec> &S, int live_end
                 atomicMax(&S.own[S.ab[c].y], code);
             }
         }
-        __syncthreads();
+    };
+    claim(1u);
+    if (t == 0) {
+        S.nready[0] = 0;
+        S.nready[1] = 0;
+    }
+    __syncthreads();
+    int remaining = live_end;
+    for (unsigned round = 1; round <= kWindow + 1 && remaining > 0; ++round) {
+        const int par = static_cast<int>(round & 1u);
         // the runnable candidates, appended to the round's list (any order: they touch disjoint particles)
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
@@ -1408,7 +1417,7 @@ __device__ void block_rounds(const InstDev &I, BlockShared<Rec> &S, int live_end
             const unsigned m = __ballot_sync(0xffffffffu, rdy);
             if (m) {
                 int pos = 0;
-                if (lane == __ffs(m) - 1) pos = atomicAdd(&S.nready, __popc(m));
+                if (lane == __ffs(m) - 1) pos = atomicAdd(&S.nready[par], __popc(m));
                 pos = __shfl_sync(0xffffffffu, pos, __ffs(m) - 1);
                 if (rdy) {
                     S.ready[pos + __popc(m & lt)] = static_cast<short>(c);
@@ -1417,9 +1426,11 @@ __device__ void block_rounds(const InstDev &I, BlockShared<Rec> &S, int live_end
             }
         }
         __syncthreads();
-        const int total = S.nready;
+        const int total = S.nready[par];
+        if (t == 0) S.nready[par ^ 1] = 0;          // the next round's list (last read a round ago)
         for (int j = t; j < total; j += kBlockThreads)
             block_run_candidate<Rec>(I, S, S.ready[j], W, redo, id, step, k0);
+        claim(round + 1u);
         remaining -= total;
         __syncthreads();
     }
