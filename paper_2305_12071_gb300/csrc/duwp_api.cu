@@ -533,16 +533,15 @@ int Engine::enqueue_phase(int ph)
         DUWP_CU(cudaStreamWaitEvent(side3, ev_fork3, 0));
         DUWP_CU(launch_flux(dev, side3, prio_hi));
         DUWP_CU(cudaEventRecord(ev_join3, side3));
-        // the light cells' rounds and the particles drawn ahead (cells with many to draw), then the
-        // block kernel (cells with many candidates) and the collision kernel (the other cells that
-        // need one) side by side, then every cell streams in one launch.  (Streaming the cells that
-        // need no collision beside the collision kernels on a third stream was 1.6% slower on the
-        // bench batch once the collision kernel had become short.)
-        DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
-        DUWP_CU(cudaEventRecord(ev_fork, stream));
-        DUWP_CU(cudaStreamWaitEvent(side2, ev_fork, 0));
+        // the block kernel (cells with many candidates, which draw their own re-sampled particles)
+        // on a second stream from the start; beside it the light cells' rounds and the particles
+        // drawn ahead, then the collision kernel (the other cells that need one); then every cell
+        // streams in one launch.  (Streaming the cells that need no collision beside the collision
+        // kernels was 1.6% slower on the bench batch once the collision kernel had become short.)
+        DUWP_CU(cudaStreamWaitEvent(side2, ev_fork3, 0));
         DUWP_CU(launch_staged(dev, fp32, staged_wide, rp, grid_staged, side2, prio_hi));
         DUWP_CU(cudaEventRecord(ev_join2, side2));
+        DUWP_CU(launch_sample(dev, fp32, rp, grid_sample, stream, prio_hi));
         DUWP_CU(launch_collide(dev, fp32, rp, grid_collide, stream, prio_hi));
         DUWP_CU(cudaStreamWaitEvent(stream, ev_join2, 0));
         DUWP_CU(launch_stream(dev, fp32, variant, groups, rp, threads, stream, prio_hi));

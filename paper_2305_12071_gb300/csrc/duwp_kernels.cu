@@ -2682,9 +2682,11 @@ __global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets(E
             // drawn in the collision kernel's tail (beside the collisions)
             if (cls == kClsReservoir || (cls == kClsStream && !many))
                 chunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
-            if ((cls == kClsDirect || cls == kClsStream) && many) {
+            if ((cls == kClsDirect || cls == kClsStream) && many && lq != kHeavyList) {
                 // many particles to draw (all of them in a first step): drawn ahead over the whole
-                // GPU instead of by the one warp or block that collides the cell
+                // GPU instead of by the one warp that collides the cell.  (The block kernel's cells
+                // draw their own: that kernel then depends on nothing of the sampling kernel and
+                // starts beside it.)
                 pchunks = (E.hdr[g].n_new + kSampleChunk - 1) / kSampleChunk;
                 if (cls == kClsDirect) E.hdr[g].edges |= kEdgePresampled;
             }
