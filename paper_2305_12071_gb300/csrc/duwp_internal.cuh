@@ -200,6 +200,7 @@ constexpr int kSampleChunk = 64;
 
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels (at most)
 constexpr int kCellBlockMin = 32; // (at least)
+constexpr int kCellBlockLarge = 64;   // cells per block of the cell kernel on a large pool
 
 // ------------------------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round multiplies words 0

@@ -2625,16 +2625,18 @@ __device__ __forceinline__ void step_advance(const EngineDev &E, int g)
 }
 
 template <int B>
-__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets(EngineDev E, int wp, int advance)
+__global__ void __launch_bounds__(B, (B < 256) ? 512 / B : 1024 / B) k_offsets(EngineDev E, int wp, int advance,
+                                                                                 int per)
 {
     wait_predecessor();
     __shared__ int64_t s_w[B / 32];
     __shared__ int64_t s_pre;
     const int g = blockIdx.x * B + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // sum of the slot bounds of all earlier blocks
+    // sum of the slot bounds of all earlier blocks (the cell kernel's block sums, `per` of its
+    // blocks to one of these)
     int64_t acc = 0;
-    for (int j = threadIdx.x; j < blockIdx.x; j += B) acc += E.blocksum[j];
+    for (int j = threadIdx.x; j < blockIdx.x * per; j += B) acc += E.blocksum[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) s_w[warp] = acc;
@@ -3208,14 +3210,25 @@ cudaError_t launch_far_sort(const EngineDev &E, int fp32, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Cells per block of the cell and offset kernels.  Their per-cell work is a chain of double-precision
-// operations (primitive state, Eq. (p), the wave flux), and an SM's double-precision units are few: a
-// small pool is spread over as many SMs as it can fill (two blocks each) instead of a few full blocks.
+// Cells per block of the offset and flux kernels (and of the cell kernel on small pools).  Their
+// per-cell work is a chain of double-precision operations (primitive state, Eq. (p), the wave flux),
+// and an SM's double-precision units are few: a small pool is spread over as many SMs as it can fill
+// (two blocks each) instead of a few full blocks.
 static int cell_block(int cells, int nsm)
 {
     for (int b = kCellBlockMin; b < kCellBlock; b *= 2)
         if (cells <= b * 2 * nsm) return b;
     return kCellBlock;
+}
+
+// Cells per block of the cell kernel alone: on a large pool, blocks of kCellBlockLarge instead of
+// kCellBlock spread its double-precision chains evenly over the SMs' sub-partitions (all blocks are
+// resident at once; with 256-cell blocks some SMs hold a block more than others).  The offset
+// kernel keeps its own blocks and reads the cell kernel's block sums in their units.
+static int cells_kernel_block(int cells, int nsm)
+{
+    const int b = cell_block(cells, nsm);
+    return b == kCellBlock ? kCellBlockLarge : b;
 }
 
 template <typename Rec>
@@ -3230,19 +3243,21 @@ static cudaError_t launch_cells_b(const EngineDev &E, int b, int grid, int q, in
 
 cudaError_t launch_cells(const EngineDev &E, int fp32, int q, int update, cudaStream_t s)
 {
-    const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
+    const int b = cells_kernel_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
     const int grid = (E.G_run + b - 1) / b;
     return fp32 ? launch_cells_b<RecF>(E, b, grid, q, update, s) : launch_cells_b<RecD>(E, b, grid, q, update, s);
 }
 
 cudaError_t launch_offsets(const EngineDev &E, int wp, int advance, cudaStream_t s)
 {
-    const int b = cell_block(E.G_run, E.nsm > 0 ? E.nsm : 1);
+    const int nsm = E.nsm > 0 ? E.nsm : 1;
+    const int b = cell_block(E.G_run, nsm);
+    const int per = b / cells_kernel_block(E.G_run, nsm);
     const int grid = (E.G_run + b - 1) / b;
-    if (b == 32) launch_pdl(k_offsets<32>, dim3(grid), 32, s, E, wp, advance);
-    else if (b == 64) launch_pdl(k_offsets<64>, dim3(grid), 64, s, E, wp, advance);
-    else if (b == 128) launch_pdl(k_offsets<128>, dim3(grid), 128, s, E, wp, advance);
-    else launch_pdl(k_offsets<kCellBlock>, dim3(grid), kCellBlock, s, E, wp, advance);
+    if (b == 32) launch_pdl(k_offsets<32>, dim3(grid), 32, s, E, wp, advance, per);
+    else if (b == 64) launch_pdl(k_offsets<64>, dim3(grid), 64, s, E, wp, advance, per);
+    else if (b == 128) launch_pdl(k_offsets<128>, dim3(grid), 128, s, E, wp, advance, per);
+    else launch_pdl(k_offsets<kCellBlock>, dim3(grid), kCellBlock, s, E, wp, advance, per);
     return cudaGetLastError();
 }
 
