@@ -201,6 +201,8 @@ constexpr int kSampleChunk = 64;
 constexpr int kCellBlock = 256;   // cells per block of the cell / offset kernels (at most)
 constexpr int kCellBlockMin = 32; // (at least)
 constexpr int kCellBlockLarge = 64;   // cells per block of the cell kernel on a large pool
+static_assert(kCellBlock % kCellBlockLarge == 0 && kCellBlockLarge >= kCellBlockMin,
+              "the offset kernel reads whole cell-kernel blocks");
 
 // ------------------------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round multiplies words 0
