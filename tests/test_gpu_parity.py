@@ -219,6 +219,28 @@ def test_batch_equals_alone():
     b.close()
 
 
+def test_large_pool_cell_blocks_change_no_result():
+    # past 2 x 128 x SMs flattened cells the cell kernel runs in smaller blocks than the offset
+    # kernel (which then reads several of its block sums per block): the small instances of such a
+    # batch (a ragged cell count) must equal the same instances alone, where both kernels share one
+    # block size
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    big = W.uniform(n_cells=2 * 128 * nsm + 777, ppc_ref=4, precision="fp32", seed=21)
+    ps = [W.sod(n_cells=90, Kn=1e-3, ppc_ref=100, precision="fp32", seed=9), big, W.config1("fp32")]
+    b = solver(ps)
+    b.step(6)
+    for i in (0, 2):
+        a = solver(ps[i])
+        a.step(6)
+        pa, pb = a.particles(), b.particles(i)
+        for k in pa:
+            assert np.array_equal(pa[k], pb[k]), f"instance {i} field {k}"
+        assert np.array_equal(a.fields()[0], b.fields(i)[0])
+        a.close()
+    b.close()
+
+
 def test_graphs_and_plain_launches_agree():
     p = W.sod(n_cells=100, Kn=1e-3, ppc_ref=100, precision="fp32", seed=12)
     a = solver(p, graphs=True)
